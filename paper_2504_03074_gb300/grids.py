@@ -1,0 +1,422 @@
+"""Seeded synthetic inputs: overset grid descriptions, Gaussian sources and sound speeds.
+
+This module is the stand-in for the paper's grid generator (Ogen, Sec. 3.1): it builds
+component grids from analytic mappings x = G_g(r), classifies their points as
+discretization / interpolation / unused (Sec. 3.1), cuts holes, finds donor stencils
+and the tensor-product Lagrange weights of width p+1 (Sec. 3.1), and evaluates the
+Gaussian source of Eq. (gaussianSource, Sec. 6).  It holds none of the WaveHoltz
+arithmetic (no difference operator, no time stepping, no filter): its outputs are
+the *input data* that both the CUDA library and the CPU oracle consume.
+
+Array conventions shared by every consumer:
+
+* a grid has ``n = (n0, n1)`` points along parameter axes 0 and 1 (boundary points
+  included, ghost points excluded; a periodic axis lists each point once);
+* compact per-grid arrays have shape ``(n1, n0)`` in C order, i.e. flat index
+  ``j * n0 + i`` with ``i`` (axis 0) fastest;
+* ghost width is ``order // 2`` on non-periodic axes and 0 on periodic ones; the
+  "extended" arrays (metrics) have shape ``(n1 + 2 g1, n0 + 2 g0)`` and start at
+  index ``(-g1, -g0)``;
+* sides are numbered ``[axis0-lo, axis0-hi, axis1-lo, axis1-hi]``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# point classification (Sec. 3.1): discretization, interpolation, unused; Dirichlet
+# boundary points are discretization points whose value the boundary condition sets.
+UNUSED, DISC, INTERP, DIRICHLET = 0, 1, 2, 3
+# boundary condition per side
+BC_NONE, BC_DIRICHLET, BC_NEUMANN, BC_PERIODIC = 0, 1, 2, 3
+# grid kinds
+CARTESIAN, CURVILINEAR = 0, 1
+
+
+@dataclass
+class Grid:
+    """One component grid G_g of an overset grid (Sec. 3.1)."""
+
+    name: str
+    kind: int
+    n: tuple                      # (n0, n1) points per axis
+    bc: list                      # 4 side codes
+    h: tuple                      # Cartesian: physical spacing; curvilinear: parameter spacing
+    mask: np.ndarray              # int8 (n1, n0)
+    xy: np.ndarray                # float64 (2, n1, n0) physical coordinates
+    orthogonal: bool = True       # grid lines meet at right angles (a12 == 0 identically)
+    rx: np.ndarray | None = None  # float64 (4, n1+2g1, n0+2g0): dr1/dx, dr1/dy, dr2/dx, dr2/dy
+    origin: tuple = (0.0, 0.0)    # Cartesian: coordinates of point (0, 0)
+
+    def ghosts(self, order):
+        return tuple(0 if self.bc[2 * a] == BC_PERIODIC else order // 2 for a in (0, 1))
+
+    @property
+    def npts(self):
+        return self.n[0] * self.n[1]
+
+
+@dataclass
+class Interp:
+    """Interpolation data (Sec. 3.1): each receiver gets a (p+1)^2 donor stencil.
+
+    The donor stencil's lower corner is ``(donor_i0, donor_j0)`` in the donor grid's
+    index space (wrapping on periodic axes); the tensor-product weights are
+    ``wx[k, a] * wy[k, b]`` for donor point ``(i0 + a, j0 + b)``.
+    """
+
+    recv_grid: np.ndarray
+    recv_i: np.ndarray
+    recv_j: np.ndarray
+    donor_grid: np.ndarray
+    donor_i0: np.ndarray
+    donor_j0: np.ndarray
+    wx: np.ndarray
+    wy: np.ndarray
+
+    @property
+    def n(self):
+        return int(self.recv_grid.shape[0])
+
+    @staticmethod
+    def empty(order):
+        z = np.zeros(0, np.int32)
+        w = np.zeros((0, order + 1))
+        return Interp(z, z, z, z, z, z, w, w)
+
+
+@dataclass
+class Problem:
+    """A Helmholtz problem c^2 Lap u + omega^2 u = f on an overset grid (Eq. HelmholtzBVP)."""
+
+    grids: list
+    interp: Interp
+    order: int
+    omega: float
+    f: list                       # per-grid compact forcing, float64 (n1, n0)
+    c2: list | None = None        # per-grid compact c(x)^2, or None for c = 1
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_active(self):
+        return int(sum(int(np.count_nonzero(g.mask != UNUSED)) for g in self.grids))
+
+    @property
+    def n_total(self):
+        return int(sum(g.npts for g in self.grids))
+
+    def split(self, vec):
+        """Split a concatenated compact vector into per-grid (n1, n0) views."""
+        out, o = [], 0
+        for g in self.grids:
+            out.append(vec[o:o + g.npts].reshape(g.n[1], g.n[0]))
+            o += g.npts
+        return out
+
+
+# ----------------------------------------------------------------------------------
+# Lagrange weights (Sec. 3.1: tensor-product Lagrange interpolation of width p+1)
+# ----------------------------------------------------------------------------------
+
+def lagrange_weights(xi, width):
+    """Weights of the Lagrange polynomial through nodes 0..width-1 evaluated at xi."""
+    xi = np.asarray(xi, dtype=np.float64)
+    w = np.ones(xi.shape + (width,))
+    for a in range(width):
+        for b in range(width):
+            if b != a:
+                w[..., a] *= (xi - b) / (a - b)
+    return w
+
+
+# ----------------------------------------------------------------------------------
+# Component grids
+# ----------------------------------------------------------------------------------
+
+def cartesian_grid(name, n0, n1, x0, x1, y0, y1, bc, order):
+    """Axis-aligned Cartesian grid on [x0,x1]x[y0,y1] with n0 x n1 points."""
+    hx, hy = (x1 - x0) / (n0 - 1), (y1 - y0) / (n1 - 1)
+    i = np.arange(n0)
+    j = np.arange(n1)
+    X = x0 + hx * i[None, :] + 0.0 * j[:, None]
+    Y = y0 + hy * j[:, None] + 0.0 * i[None, :]
+    mask = np.full((n1, n0), DISC, np.int8)
+    for s, code in enumerate(bc):
+        if code == BC_DIRICHLET:
+            if s == 0:
+                mask[:, 0] = DIRICHLET
+            elif s == 1:
+                mask[:, -1] = DIRICHLET
+            elif s == 2:
+                mask[0, :] = DIRICHLET
+            else:
+                mask[-1, :] = DIRICHLET
+    return Grid(name, CARTESIAN, (n0, n1), list(bc), (hx, hy), mask, np.stack([X, Y]),
+                True, None, (x0, y0))
+
+
+def annulus_grid(name, nth, nr, r_in, width, beta, order, inner_bc=BC_NEUMANN):
+    """Body-fitted annulus r(s) = r_in + width (e^{beta s}-1)/(e^beta-1), theta = 2 pi t.
+
+    Axis 0 is the angle t in [0, 1) (periodic, nth points, no duplicate), axis 1 the
+    radial parameter s in [0, 1] (nr points).  Side axis1-lo (s = 0) is the body; the
+    outer p/2 lines are interpolation points.  The inverse metrics are analytic and
+    are evaluated on ghost lines too (the mapping extends smoothly past s = 0, 1).
+    """
+    g1 = order // 2
+    dt_, ds = 1.0 / nth, 1.0 / (nr - 1)
+    t = np.arange(nth) * dt_
+    s_ext = np.arange(-g1, nr + g1) * ds
+    eb = math.exp(beta) - 1.0
+
+    def radius(s):
+        return r_in + width * (np.exp(beta * s) - 1.0) / eb
+
+    def dradius(s):
+        return width * beta * np.exp(beta * s) / eb
+
+    th = 2.0 * np.pi * t
+    R = radius(s_ext)[:, None]
+    Rs = dradius(s_ext)[:, None]
+    c, s_ = np.cos(th)[None, :], np.sin(th)[None, :]
+    rx = np.empty((4, nr + 2 * g1, nth))
+    rx[0] = -s_ / (2.0 * np.pi * R)   # dt/dx
+    rx[1] = c / (2.0 * np.pi * R)     # dt/dy
+    rx[2] = c / Rs                    # ds/dx
+    rx[3] = s_ / Rs                   # ds/dy
+    Rin = R[g1:g1 + nr]
+    X = Rin * c
+    Y = Rin * s_
+    mask = np.full((nr, nth), DISC, np.int8)
+    mask[nr - order // 2:, :] = INTERP
+    if inner_bc == BC_DIRICHLET:
+        mask[0, :] = DIRICHLET
+    bc = [BC_PERIODIC, BC_PERIODIC, inner_bc, BC_NONE]
+    g = Grid(name, CURVILINEAR, (nth, nr), bc, (dt_, ds), mask, np.stack([X, Y]), True, rx)
+    g.mapping = dict(r_in=r_in, width=width, beta=beta)
+    return g
+
+
+def sheared_torus_grid(name, n0, n1, amp_x, amp_y, order):
+    """Doubly periodic non-orthogonal grid x = r1 + ax sin(2 pi r2), y = r2 + ay sin(2 pi r1).
+
+    A flat torus: no physical boundary, all points discretization points, and the mixed
+    derivative term of the mapped Laplacian is present everywhere (tests).
+    """
+    d0, d1 = 1.0 / n0, 1.0 / n1
+    r1 = np.arange(n0) * d0
+    r2 = np.arange(n1) * d1
+    R1, R2 = np.meshgrid(r1, r2)
+    x_r1 = np.ones_like(R1)
+    x_r2 = 2.0 * np.pi * amp_x * np.cos(2.0 * np.pi * R2)
+    y_r1 = 2.0 * np.pi * amp_y * np.cos(2.0 * np.pi * R1)
+    y_r2 = np.ones_like(R1)
+    det = x_r1 * y_r2 - x_r2 * y_r1
+    rx = np.stack([y_r2 / det, -x_r2 / det, -y_r1 / det, x_r1 / det])
+    X = R1 + amp_x * np.sin(2.0 * np.pi * R2)
+    Y = R2 + amp_y * np.sin(2.0 * np.pi * R1)
+    mask = np.full((n1, n0), DISC, np.int8)
+    g = Grid(name, CURVILINEAR, (n0, n1), [BC_PERIODIC] * 4, (d0, d1), mask,
+             np.stack([X, Y]), False, rx)
+    g.mapping = dict(amp_x=amp_x, amp_y=amp_y)
+    return g
+
+
+# ----------------------------------------------------------------------------------
+# Overset assembly: hole cutting, classification, donor search (Ogen stand-in)
+# ----------------------------------------------------------------------------------
+
+def _annulus_param(gA, x, y):
+    """Fractional (i, j) index of physical points in the annulus parameter space."""
+    m = gA.mapping
+    th = np.mod(np.arctan2(y, x), 2.0 * np.pi)
+    ti = th / (2.0 * np.pi) * gA.n[0]
+    r = np.hypot(x, y)
+    eb = math.exp(m["beta"]) - 1.0
+    s = np.log1p((r - m["r_in"]) * eb / m["width"]) / m["beta"]
+    return ti, s * (gA.n[1] - 1)
+
+
+def _cart_param(gB, x, y):
+    return (x - gB.origin[0]) / gB.h[0], (y - gB.origin[1]) / gB.h[1]
+
+
+def _donors(fi, fj, donor, order, clamp_j_hi, periodic_i):
+    """Lower-corner indices of the width-(p+1) stencil nearest the point, shifted inward."""
+    w = order + 1
+    i0 = np.rint(fi).astype(np.int64) - order // 2
+    j0 = np.rint(fj).astype(np.int64) - order // 2
+    if not periodic_i:
+        i0 = np.clip(i0, 0, donor.n[0] - w)
+    j0 = np.clip(j0, 0, clamp_j_hi - w + 1)
+    return i0, j0, lagrange_weights(fi - i0, w), lagrange_weights(fj - j0, w)
+
+
+def disk_in_square(nb, nth, nr, order, box=2.0, r_in=0.5, width=0.3, beta=1.5,
+                   r_cut=0.65):
+    """Cartesian background [-box, box]^2 (nb^2 points, Dirichlet) + stretched annulus.
+
+    Background points with |x| < r_cut are cut out; those within p/2 index layers
+    (box neighbourhood) of a background discretization point become interpolation
+    points, the rest unused.  The annulus's outer p/2 lines are interpolation points
+    (donors on the background).  Donor stencils contain only discretization points
+    (explicit interpolation).  Returns (grids, interp).
+    """
+    B = cartesian_grid("background", nb, nb, -box, box, -box, box, [BC_DIRICHLET] * 4, order)
+    A = annulus_grid("annulus", nth, nr, r_in, width, beta, order)
+    X, Y = B.xy
+    inside = np.hypot(X, Y) < r_cut
+    active = ~inside
+    half = order // 2
+    near = np.zeros_like(active)
+    pad = np.pad(active, half)
+    for dj in range(-half, half + 1):
+        for di in range(-half, half + 1):
+            near |= pad[half + dj:half + dj + nb, half + di:half + di + nb]
+    B.mask[inside & near] = INTERP
+    B.mask[inside & ~near] = UNUSED
+
+    recv = []
+    # background receivers <- annulus donors
+    jb, ib = np.nonzero(B.mask == INTERP)
+    fi, fj = _annulus_param(A, X[jb, ib], Y[jb, ib])
+    last_disc = nr - 1 - half
+    i0, j0, wx, wy = _donors(fi, fj, A, order, last_disc, True)
+    recv.append((0, ib, jb, 1, i0, j0, wx, wy))
+    # annulus receivers <- background donors
+    ja, ia = np.nonzero(A.mask == INTERP)
+    XA, YA = A.xy
+    fi, fj = _cart_param(B, XA[ja, ia], YA[ja, ia])
+    i0, j0, wx, wy = _donors(fi, fj, B, order, nb - 1, False)
+    recv.append((1, ia, ja, 0, i0, j0, wx, wy))
+
+    cols = list(zip(*recv))
+    interp = Interp(
+        np.concatenate([np.full(len(r[1]), r[0], np.int32) for r in recv]),
+        np.concatenate(cols[1]).astype(np.int32), np.concatenate(cols[2]).astype(np.int32),
+        np.concatenate([np.full(len(r[1]), r[3], np.int32) for r in recv]),
+        np.concatenate(cols[4]).astype(np.int32), np.concatenate(cols[5]).astype(np.int32),
+        np.concatenate(cols[6]), np.concatenate(cols[7]))
+    grids = [B, A]
+    check_explicit_interp(grids, interp, order)
+    return grids, interp
+
+
+def check_explicit_interp(grids, interp, order):
+    """Every donor must be a discretization (or Dirichlet) point: explicit interpolation."""
+    w = order + 1
+    for k in range(interp.n):
+        d = grids[interp.donor_grid[k]]
+        ii = interp.donor_i0[k] + np.arange(w)
+        jj = interp.donor_j0[k] + np.arange(w)
+        if d.bc[0] == BC_PERIODIC:
+            ii = np.mod(ii, d.n[0])
+        if d.bc[2] == BC_PERIODIC:
+            jj = np.mod(jj, d.n[1])
+        if ii.min() < 0 or ii.max() >= d.n[0] or jj.min() < 0 or jj.max() >= d.n[1]:
+            raise ValueError(f"receiver {k}: donor stencil out of range")
+        m = d.mask[np.ix_(jj, ii)]
+        if not np.all((m == DISC) | (m == DIRICHLET)):
+            raise ValueError(f"receiver {k}: donor stencil touches a non-discretization point")
+
+
+# ----------------------------------------------------------------------------------
+# Sources and coefficients
+# ----------------------------------------------------------------------------------
+
+def gaussian(xy, x0, amp=1.0, b=200.0):
+    """f(x) = amp * exp(-b |x - x0|^2) (Eq. gaussianSource without the cos(omega t))."""
+    d2 = (xy[0] - x0[0]) ** 2 + (xy[1] - x0[1]) ** 2
+    return amp * np.exp(-b * d2)
+
+
+def bumps_c2(xy, centers, amp=0.2, width=0.2):
+    """c(x)^2 with c = 1 + amp * sum_i exp(-|x - x_i|^2 / width^2)."""
+    c = np.ones_like(xy[0])
+    for x0 in centers:
+        c += amp * np.exp(-((xy[0] - x0[0]) ** 2 + (xy[1] - x0[1]) ** 2) / width ** 2)
+    return c * c
+
+
+def _seeded_point_in_background(rng, lo, hi, rmin):
+    while True:
+        p = rng.uniform(lo, hi, size=2)
+        if math.hypot(p[0], p[1]) >= rmin:
+            return p
+
+
+# ----------------------------------------------------------------------------------
+# The workloads: unit square (64^2), disk-in-square (1024^2 + 2048x64), and scaled
+# versions of the same recipes for tests.
+# ----------------------------------------------------------------------------------
+
+def unit_square_problem(n=64, order=2, omega=10.0, seed=0, bc=BC_DIRICHLET):
+    """Single Cartesian grid on [0,1]^2 with n^2 points, Gaussian at x0 ~ U[0.3,0.7]^2."""
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(0.3, 0.7, size=2)
+    g = cartesian_grid("square", n, n, 0.0, 1.0, 0.0, 1.0, [bc] * 4, order)
+    f = gaussian(g.xy, x0, 1.0, 200.0)
+    return Problem([g], Interp.empty(order), order, omega, [f], None,
+                   name=f"unit-square-{n}x{n}-o{order}", meta=dict(x0=x0.tolist(), seed=seed))
+
+
+def channel_problem(n=32, order=4, omega=7.0, seed=0, bc=BC_NEUMANN):
+    """Cartesian channel: periodic in x on [0, 1), walls y = 0, 1 with condition ``bc``."""
+    rng = np.random.default_rng(seed)
+    g = cartesian_grid("channel", n, n, 0.0, (n - 1) / n, 0.0, 1.0,
+                       [BC_PERIODIC, BC_PERIODIC, bc, bc], order)
+    x0 = rng.uniform(0.3, 0.7, size=2)
+    f = gaussian(g.xy, x0, 1.0, 30.0)
+    return Problem([g], Interp.empty(order), order, omega, [f], None,
+                   name=f"channel-{n}x{n}-o{order}-bc{bc}", meta=dict(x0=x0.tolist()))
+
+
+def disk_problem(nb=1024, nth=2048, nr=64, order=4, omega=40.0, seed=0, n_src=1,
+                 c_bumps=0, box=2.0, width=0.3, r_cut=0.65):
+    """Disk-in-square overset problem: Gaussian source(s) seeded in the background.
+
+    Coarse test grids need a wider annulus (``width``) and cut radius ``r_cut`` so that
+    the overlap still holds a full donor stencil.
+    """
+    rng = np.random.default_rng(seed)
+    grids, interp = disk_in_square(nb, nth, nr, order, box=box, width=width, r_cut=r_cut)
+    srcs = [_seeded_point_in_background(rng, -1.5, 1.5, 1.0) for _ in range(n_src)]
+    f = []
+    for g in grids:
+        fg = np.zeros(g.mask.shape)
+        for x0 in srcs:
+            fg += gaussian(g.xy, x0, 1.0, 200.0)
+        f.append(fg)
+    c2 = None
+    centers = []
+    if c_bumps:
+        centers = [_seeded_point_in_background(rng, -1.8, 1.8, 0.8) for _ in range(c_bumps)]
+        c2 = [bumps_c2(g.xy, centers) for g in grids]
+    return Problem(grids, interp, order, omega, f, c2,
+                   name=f"disk-in-square-{nb}^2+{nth}x{nr}-o{order}",
+                   meta=dict(sources=[s.tolist() for s in srcs], seed=seed,
+                             bumps=[c.tolist() for c in centers]))
+
+
+def sheared_torus_problem(n0=32, n1=28, order=4, omega=9.0, seed=0):
+    """One non-orthogonal, doubly periodic curvilinear grid (mixed terms everywhere)."""
+    rng = np.random.default_rng(seed)
+    g = sheared_torus_grid("torus", n0, n1, 0.1, 0.08, order)
+    x0 = rng.uniform(0.3, 0.7, size=2)
+    f = gaussian(g.xy, x0, 1.0, 30.0)
+    return Problem([g], Interp.empty(order), order, omega, [f], None,
+                   name=f"sheared-torus-{n0}x{n1}-o{order}", meta=dict(x0=x0.tolist()))
+
+
+def random_state(problem, seed):
+    """A seeded random vector on the active points (zero on unused points)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for g in problem.grids:
+        v = rng.standard_normal(g.mask.shape)
+        v[g.mask == UNUSED] = 0.0
+        out.append(v.ravel())
+    return np.concatenate(out)
