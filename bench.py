@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""WaveHoltz benchmark: GLUP/s of one WaveHoltz iteration on one GB300.
+
+A step is one WaveHoltz iteration (the hot path: M = Np * Nt time steps of the explicit
+scheme on every component grid, ghost rules, overset interpolation, the fused time
+filter; Algorithm 1/2) on the disk-in-square overset workload: Cartesian background
+[-2, 2]^2 at 1024^2 + stretched annulus 2048 x 64 around r = 0.5 (width 0.3), order 4,
+Neumann on the cylinder, Dirichlet on the box, c = 1, omega = 40, one seeded Gaussian
+source, 5x5 Lagrange interpolation, FP64.  Steps chain as fixed-point iterations
+v <- W_h(v, f).  GLUP = active-point time-step updates.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs under torchrun: the single solve does not shard (replicas only), each rank
+runs an independent replica (own seed) and value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WaveHoltz GLUP/s (one WaveHoltz iteration, FP64, disk-in-square 1024^2+2048x64 o4)"
+WORKLOAD = ("disk-in-square overset: background [-2,2]^2 1024^2 + annulus 2048x64 "
+            "(r 0.5..0.8, stretched), order 4, Neumann cylinder / Dirichlet box, c=1, "
+            "omega=40, 1 seeded Gaussian, 5x5 Lagrange interpolation, Np=1")
+L2_BYTES = 129 * 1024 * 1024
+
+
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_sha():
+    p = os.path.join(ROOT, "paper_2504_03074_gb300", "csrc", "wh_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from profiles/traffic.txt if it was captured
+    from the current kernel source (sha match), else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    sha = kernel_sha()
+    for line in open(p):
+        f = line.split("#")[0].split()
+        if len(f) == 3 and f[0] == kernel and f[1] == sha:
+            return float(f[2])
+    return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
+
+
+# FP64 peak of a GB300 for the ALU roofline: 1.25 TFLOP/s (FMA = 2 FLOP), the pool's
+# stated figure for this part.
+FP64_PEAK_TFLOPS = 1.25
+# Algorithmic FP64 FLOP per active-point update of the order-4 march with the fused
+# filter: 4 additions pairing symmetric neighbours + 7 multiply-adds (5 stencil
+# coefficients, the forcing term, the filter) = 4 + 14.
+FLOP_PER_LUP_O4 = 18.0
+
+
+def cpu_baseline(problem, sample):
+    """Time the CPU oracle (as it stands, single thread) on a bounded sample."""
+    from oracle import oracle as O
+    from paper_2504_03074_gb300 import grids as G
+    orc = O.Oracle(problem)
+    v = G.random_state(problem, 1)
+    t0 = time.perf_counter()
+    orc.iterate(v, True)
+    dt = time.perf_counter() - t0
+    lups = problem.n_active * orc.time.M
+    return {"value": lups / dt / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+            "sample": sample, "seconds": dt}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the host cores, same metric/unit/config; each
+    step is one oracle WaveHoltz iteration on the half-resolution sample of the workload
+    (512^2 + 1024x32, same recipe, omega = 40), so the whole run stays within minutes."""
+    r, w, _ = rank_info()
+    if r != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2504_03074_gb300 import grids as G
+    prob = G.disk_problem(nb=512, nth=1024, nr=32, order=4, omega=40.0, seed=0)
+    orc = O.Oracle(prob)
+    v = orc.zeros()
+    for _ in range(args.warmup):
+        v = orc.iterate(v, True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v = orc.iterate(v, True)
+    el = time.perf_counter() - t0
+    lups = prob.n_active * orc.time.M * args.steps
+    val = lups / el / 1e9
+    sample = ("one oracle WaveHoltz iteration per step on the half-resolution sample "
+              "(512^2 + 1024x32 annulus, order 4, omega 40, M=%d steps)" % orc.time.M)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GLUP/s",
+        "n_gpus": w, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": val,
+                         "unit": "GLUP/s"},
+        "e2e": {"value": val, "unit": "GLUP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="small workload (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = rank_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2504_03074_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2504_03074_gb300 import grids as G
+    from paper_2504_03074_gb300 import waveholtz as WH
+
+    if args.small:
+        prob = G.disk_problem(nb=256, nth=512, nr=16, order=4, omega=20.0, seed=rank)
+    else:
+        prob = G.disk_problem(nb=1024, nth=2048, nr=64, order=4, omega=40.0, seed=rank)
+    stream = torch.cuda.Stream()
+    s = WH.Solver(prob, stream=stream)
+    ti = s.prepare()
+    n = prob.n_total
+    lups = ti.n_active * ti.M
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    va = torch.zeros(n, dtype=torch.float64, device="cuda")
+    vb = torch.empty_like(va)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 0)):
+            s.iterate(va, vb, True)
+            va, vb = vb, va
+        stream.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))  # L2 flush between timed iterations (untimed)
+                ev[k][0].record(stream)
+                s.iterate(va, vb, True)
+                ev[k][1].record(stream)
+                va, vb = vb, va
+            stream.synchronize()
+            torch.cuda.synchronize()
+        launches = s.last_launch_count() * args.steps
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = lups * args.steps * world / t_max / 1e9
+
+    # end-to-end through the public API with host buffers (pinned), copies inside
+    hin = torch.zeros(n, dtype=torch.float64).pin_memory()
+    hout = torch.empty(n, dtype=torch.float64).pin_memory()
+    hin.copy_(va.cpu())
+    e2e_ms = []
+    for k in range(max(3, min(args.steps, 5))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.iterate_host_buffers(hin, hout, True)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        hin, hout = hout, hin
+    e2e_t = statistics.median(e2e_ms) / 1e3
+    e2e_val = lups * world / e2e_t / 1e9
+
+    # per-kernel device times of the same iteration (events around every launch)
+    prof = s.profile_iteration(va, vb, True)
+    march_ms, march_n = prof["march"]
+    avg_march_s = march_ms / march_n / 1e3
+    flops_per_launch = FLOP_PER_LUP_O4 * ti.n_active  # every launch updates all points
+    achieved = flops_per_launch / avg_march_s / 1e12
+    total_prof = sum(v[0] for v in prof.values())
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": recorded_traffic("march_kernel"),
+                "kernel": "march_kernel<double,4>", "avg_launch_us": avg_march_s * 1e6,
+                "flop_per_launch": flops_per_launch,
+                "share_of_iteration": march_ms / total_prof,
+                "peak_source": "GB300 FP64 1.25 TFLOP/s (pool figure; FMA=2)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.small:
+        cpu = cpu_baseline(prob, "one full oracle WaveHoltz iteration (M=%d steps) of the "
+                                 "same workload, single thread" % ti.M)
+    out = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.small else "small 256^2+512x16 o4",
+                   "M": ti.M, "Nt": ti.Nt, "dt": ti.dt, "n_active": ti.n_active,
+                   "n_total": ti.n_total, "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GLUP/s", "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": n * 8, "ms_per_step": e2e_t * 1e3},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "kernels_ms_per_iteration": {k: v[0] for k, v in prof.items()},
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * waveholtz.h -- C ABI of libwaveholtz: one WaveHoltz iteration (and the solvers that
+ * drive it) on an overset grid, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (Appelo, Banks, Henshaw, Schwendeman, "An optimal O(N) Helmholtz solver for
+ * complex geometry using WaveHoltz and overset grids"):
+ *   Solve  c(x)^2 Lap u + omega^2 u = f  in Omega,  B u = 0 on the boundary
+ *   (Eq. HelmholtzBVP, Sec. 2.1) by iterating the WaveHoltz map (Algorithm 1, Sec. 2.2)
+ *       v <- W_h(v, f) = (2/Tbar) sum_n sigma_n dt (cos(omega_e t^n) - alpha/2) W^n
+ *   where W^n solves the explicit scheme D+tD-t W = c^2 L_h W - f cos(omega_e t)
+ *   (Eq. WaveSchemeexplicit, Sec. 4.2) with W^0 = v, marched over Np periods by
+ *   Algorithm 2 (advance every grid, apply boundary conditions, interpolate; Sec. 3.2),
+ *   with the explicit time correction of Recipe OmegaTildeExplicit (App. B.1) and the
+ *   adjusted filter parameter alpha_d (Eq. alphad).  The fixed point is the discrete
+ *   Helmholtz solution; it is reached by the fixed-point iteration or by GMRES on
+ *   (I - S) v = b, A v = v - W_h(v, 0), b = W_h(0, f) (Eqs. WaveHoltzLinearSystem and
+ *   MevalII, Sec. 4.3).
+ *
+ * Conventions (every entry point):
+ *   - Every function returns a wh_status; negative values are errors and
+ *     wh_last_error(ctx) then holds a one-line message.  No call aborts the process.
+ *   - A context owns every device allocation it makes; wh_destroy frees them.  Calls on
+ *     one context are not thread-safe.  Work is issued on the context's stream
+ *     (wh_set_stream); calls that return host data synchronise that stream.
+ *   - Grid arrays passed to wh_add_grid / wh_set_forcing are HOST arrays that the
+ *     library copies; the caller keeps ownership.
+ *   - "Compact vectors" are the concatenation over grids (in wh_add_grid order) of
+ *     n0*n1 values per grid, row-major with axis 0 fastest (index j*n0 + i).  Values at
+ *     unused points are ignored on input and written as 0 on output.
+ *   - Ghost width is order/2 on non-periodic axes and 0 on periodic axes.  "Extended"
+ *     arrays cover indices i in [-g0, n0+g0), j in [-g1, n1+g1), same ordering.
+ *   - Boundary data g is zero (homogeneous Dirichlet / Neumann conditions).
+ */
+#ifndef WAVEHOLTZ_H
+#define WAVEHOLTZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wh_ctx wh_ctx;
+
+typedef enum {
+  WH_OK = 0,
+  WH_ERR_ARG = -1,           /* invalid argument (null pointer, bad size or code) */
+  WH_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  WH_ERR_STATE = -3,         /* call out of order (e.g. wh_iterate before wh_prepare) */
+  WH_ERR_DIVERGED = -4,      /* residual became NaN/Inf or grew without bound */
+  WH_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+  WH_ERR_NOT_CONVERGED = -6, /* solver hit its iteration limit above tolerance */
+  WH_ERR_GRID = -7,          /* inconsistent grid description or interpolation data */
+  WH_ERR_NOMEM = -8          /* device or host allocation failed */
+} wh_status;
+
+/* Point classification (Sec. 3.1).  Dirichlet points are boundary points whose value
+ * the boundary condition sets. */
+enum { WH_UNUSED = 0, WH_DISC = 1, WH_INTERP = 2, WH_DIRICHLET = 3 };
+/* Boundary condition of a side; sides are [axis0-lo, axis0-hi, axis1-lo, axis1-hi]. */
+enum { WH_BC_NONE = 0, WH_BC_DIRICHLET = 1, WH_BC_NEUMANN = 2, WH_BC_PERIODIC = 3 };
+/* Grid kinds: axis-aligned Cartesian, or curvilinear given by inverse metrics. */
+enum { WH_CARTESIAN = 0, WH_CURVILINEAR = 1 };
+/* Arithmetic of the wave march.  WH_FP32 keeps the state, forcing and stencil weights in
+ * FP32; the filter accumulator, interpolation weights and all reductions stay FP64. */
+enum { WH_FP64 = 0, WH_FP32 = 1 };
+/* Solvers for wh_solve. */
+enum { WH_FPI = 0, WH_GMRES = 1 };
+
+typedef struct {
+  int32_t order;      /* spatial order p: 2 or 4 (Sec. 3.2) */
+  int32_t periods;    /* Np >= 1: Tbar = Np * T (Algorithm 1) */
+  double cfl;         /* fraction in (0, 1] of the explicit stability limit */
+  int32_t alpha_mode; /* 0: alpha_d of Eq. alphad (default); 1: alpha = 1/2 */
+  int32_t precision;  /* WH_FP64 (default) or WH_FP32 */
+} wh_options;
+
+/* One component grid (Sec. 3.1).  All pointers are host pointers, read during the call.
+ *   n[2]        points per axis, boundary points included, ghosts excluded; a periodic
+ *               axis lists each point once.  n >= 2*order + 1 on non-periodic axes.
+ *   kind        WH_CARTESIAN: spacing h[] is physical, metrics are the identity.
+ *               WH_CURVILINEAR: h[] is the parameter spacing, rx gives the metrics.
+ *   bc[4]       per-side WH_BC_*; periodic sides come in pairs.  A Neumann side may only
+ *               meet periodic or interpolation sides.
+ *   orthogonal  1 if the grid lines are orthogonal (the mixed coefficient a12 is then
+ *               identically zero and dropped); grids with a Dirichlet or Neumann side
+ *               must be orthogonal.
+ *   mask        n0*n1 int8 WH_UNUSED / WH_DISC / WH_INTERP / WH_DIRICHLET.
+ *   rx          curvilinear only: 4 extended arrays, dr1/dx, dr1/dy, dr2/dx, dr2/dy.
+ *   c2          n0*n1 values of c(x)^2 > 0, or NULL for c = 1. */
+typedef struct {
+  int32_t n[2];
+  int32_t kind;
+  int32_t bc[4];
+  int32_t orthogonal;
+  double h[2];
+  const int8_t *mask;
+  const double *rx;
+  const double *c2;
+} wh_grid_desc;
+
+/* Interpolation data (Sec. 3.1): receiver k in grid recv_grid[k] at (recv_i, recv_j)
+ * takes sum_{a,b} wx[k][a] wy[k][b] u_donor(i0 + a, j0 + b), a, b = 0..order, from grid
+ * donor_grid[k] with lower corner (donor_i0, donor_j0) (wrapping on periodic axes).
+ * Every donor must be a WH_DISC or WH_DIRICHLET point (explicit interpolation); every
+ * receiver must be a WH_INTERP point; each WH_INTERP point must be listed once.  Host
+ * pointers; wx, wy are [n][order+1] FP64. */
+typedef struct {
+  int64_t n;
+  const int32_t *recv_grid, *recv_i, *recv_j;
+  const int32_t *donor_grid, *donor_i0, *donor_j0;
+  const double *wx, *wy;
+} wh_interp_desc;
+
+/* Time setup of one frequency (Recipe OmegaTildeExplicit, Eq. alphad). */
+typedef struct {
+  double omega;      /* requested frequency */
+  double dt;         /* (2/omega) sin(pi/Nt) */
+  double omega_e;    /* 2 pi / (Nt dt) */
+  double alpha;      /* alpha_d or 1/2 */
+  double dt_max;     /* cfl * largest stable dt (frozen coefficients) */
+  double Tbar;       /* Np * Nt * dt */
+  int32_t Nt;        /* time steps per period */
+  int32_t M;         /* Np * Nt time steps per WaveHoltz iteration */
+  int64_t n_active;  /* discretization + interpolation + Dirichlet points */
+  int64_t n_total;   /* length of a compact vector */
+} wh_time_info;
+
+typedef struct {
+  int32_t iterations;   /* WaveHoltz iterations (FPI) or GMRES matrix-vector products */
+  int32_t converged;    /* 1 if the tolerance was met */
+  double residual;      /* final relative residual: FPI ||v_k - v_{k-1}|| / ||v_k||,
+                           GMRES ||b - A v|| / ||b|| (Sec. 6.1) */
+  double seconds;       /* wall time of the solve */
+  int32_t n_history;    /* entries written to history (<= history_cap) */
+} wh_stats;
+
+/* Fill *opt with order 4, Np = 1, cfl 0.9, alpha_d, FP64. */
+wh_status wh_options_default(wh_options *opt);
+
+/* Create a context on the current CUDA device.  *out receives the handle. */
+wh_status wh_create(const wh_options *opt, wh_ctx **out);
+
+/* Free every device and host resource of ctx (NULL is a no-op). */
+void wh_destroy(wh_ctx *ctx);
+
+/* Message of the last failing call on ctx (never NULL). */
+const char *wh_last_error(const wh_ctx *ctx);
+
+/* Issue all further work on this cudaStream_t (NULL = legacy default stream). */
+wh_status wh_set_stream(wh_ctx *ctx, void *stream);
+
+/* Add one component grid (Sec. 3.1); *grid_id receives its index (0, 1, ...).
+ * Errors: WH_ERR_ARG, WH_ERR_GRID (unsupported boundary combination or bad mask). */
+wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *grid, int32_t *grid_id);
+
+/* Set the interpolation data for all receivers (replaces earlier data).  Validated
+ * against the masks: WH_ERR_GRID on any violation. */
+wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *interp);
+
+/* Forcing f(x) of grid grid_id (host, n0*n1): the right-hand side of
+ * c^2 Lap u + omega^2 u = f; the scheme applies -f cos(omega_e t). */
+wh_status wh_set_forcing(wh_ctx *ctx, int32_t grid_id, const double *f);
+
+/* Prepare frequency omega: the operator coefficients of the mapping method
+ * (a_kl, b_k; Sec. 3.1) and the stability bound on the device, the time setup, the
+ * per-point stencil weights, and the per-step tables.  Must follow the last
+ * wh_add_grid / wh_set_interp / wh_set_forcing.  *info (may be NULL) receives the
+ * time setup. */
+wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info);
+
+/* ONE WaveHoltz iteration v_out = W_h(v_in, f) (forcing = 1) or W_h(v_in, 0)
+ * (forcing = 0): the hot path.  v_in, v_out: DEVICE compact vectors of n_total FP64
+ * values (may not alias).  Asynchronous on the context stream. */
+wh_status wh_iterate(wh_ctx *ctx, int32_t forcing, const double *v_in, double *v_out);
+
+/* Same as wh_iterate with HOST vectors: copies v_in to the device, iterates, copies the
+ * result back and synchronises. */
+wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, double *v_out);
+
+/* Solve to relative tolerance tol with WH_FPI (Algorithm 1) or WH_GMRES (restarted,
+ * classical Gram-Schmidt applied twice, Sec. 4.3).  u: DEVICE compact vector, the
+ * initial guess on entry and the solution on exit.  history (host, may be NULL)
+ * receives up to history_cap relative residuals.  Returns WH_ERR_NOT_CONVERGED (u still
+ * holds the last iterate) when max_it is reached, WH_ERR_DIVERGED on NaN/Inf. */
+wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
+                   double *u, wh_stats *stats, double *history, int32_t history_cap);
+
+/* FP64 inner products <x, y> over n entries of two DEVICE vectors (the GMRES reduction:
+ * warp-shuffle partial sums, then one deterministic pass).  *out is a host scalar. */
+wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, double *out);
+
+/* Measurement aid: one WaveHoltz iteration like wh_iterate, but launched without the CUDA
+ * graph and with a CUDA event recorded on the context stream before every kernel, so
+ * that each kernel's device time can be read.  ms[4] and counts[4] (host) receive the
+ * summed milliseconds and launch counts of: [0] the march kernel, [1] the ghost-rule +
+ * interpolation kernel, [2] the input kernel, [3] the output kernel.  Synchronises. */
+wh_status wh_profile_iteration(wh_ctx *ctx, int32_t forcing, const double *v_in, double *v_out,
+                               double *ms, int32_t *counts);
+
+/* Time setup of the last wh_prepare. */
+wh_status wh_get_time_info(const wh_ctx *ctx, wh_time_info *info);
+
+/* Number of kernel launches issued by the last wh_iterate / wh_solve call. */
+int64_t wh_last_launch_count(const wh_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVEHOLTZ_H */

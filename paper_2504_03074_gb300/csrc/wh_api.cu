@@ -1,0 +1,995 @@
+// wh_api.cu -- host side of libwaveholtz: the C ABI declared in include/waveholtz.h.
+//
+// Responsibilities: validate and upload the overset grid description, prepare one
+// frequency (operator coefficients and stability bound on the device, the explicit time
+// correction of Recipe OmegaTildeExplicit, alpha_d of Eq. alphad, per-point stencil
+// weights, per-step tables), issue one WaveHoltz iteration as a CUDA graph of
+// 2M + 1 kernels (M time steps of Algorithm 2) plus an input and an output kernel, and
+// drive the fixed-point iteration (Algorithm 1) or GMRES (Sec. 4.3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/waveholtz.h"
+#include "wh_internal.h"
+
+using namespace wh;
+
+namespace {
+
+struct HostGrid {
+  wh_grid_desc d;
+  std::vector<int8_t> mask;
+  std::vector<double> rx, c2, f;
+  int g0 = 0, g1 = 0;
+};
+
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct wh_ctx {
+  wh_options opt{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+  std::vector<HostGrid> grids;
+  // interpolation (host copies)
+  int64_t nrecv = 0;
+  std::vector<int32_t> rg, ri, rj, dg, di, dj;
+  std::vector<double> wx, wy;
+  // device layout
+  bool dirty = true;
+  bool prepared = false;
+  int64_t total = 0;     // extended points, all grids (with alignment gaps)
+  int64_t ncompact = 0;  // compact vector length
+  int64_t nactive = 0;
+  int64_t nplanes5 = 0, nweights = 0;
+  std::vector<DevGrid> hgrids;
+  std::vector<Tile> htiles;
+  std::vector<BcItem> hbc;
+  std::vector<int32_t> hbc_grid, hbc_axis, hbc_hi;
+  std::vector<void *> allocs;
+  DevGrid *d_grids = nullptr;
+  Tile *d_tiles = nullptr;
+  int8_t *d_mask = nullptr;
+  void *d_Wa = nullptr, *d_Wb = nullptr, *d_F = nullptr, *d_Wt = nullptr;
+  double *d_V = nullptr, *d_c2 = nullptr, *d_rx = nullptr, *d_coef = nullptr;
+  BcItem *d_bc = nullptr;
+  int32_t *d_bc_grid = nullptr, *d_bc_axis = nullptr, *d_bc_hi = nullptr;
+  int32_t *d_didx = nullptr;
+  double *d_dw = nullptr;
+  int64_t *d_ridx = nullptr;
+  unsigned long long *d_smax = nullptr;
+  // time setup
+  wh_time_info ti{};
+  std::vector<double> fc, wf;  // per step n: forcing factor, filter weight of level n
+  // graphs for forcing off / on
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // solver workspace
+  double *d_q = nullptr;  // Krylov basis
+  int64_t q_cap = 0;
+  double *d_work = nullptr;  // 3 vectors
+  double *d_partial = nullptr, *d_red = nullptr;
+  int partial_blocks = 0, red_cap = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+wh_status fail(wh_ctx *c, wh_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, WH_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+template <typename T>
+wh_status dalloc(wh_ctx *ctx, T **p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(ctx, WH_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T),
+                cudaGetErrorString(e));
+  ctx->allocs.push_back((void *)*p);
+  e = cudaMemset(*p, 0, n * sizeof(T));
+  if (e != cudaSuccess) return fail(ctx, WH_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return WH_OK;
+}
+
+void free_device(wh_ctx *ctx) {
+  for (int k = 0; k < 2; ++k)
+    if (ctx->gexec[k]) {
+      cudaGraphExecDestroy(ctx->gexec[k]);
+      ctx->gexec[k] = nullptr;
+    }
+  for (void *p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->d_grids = nullptr;
+  ctx->d_q = nullptr;
+  ctx->q_cap = 0;
+  ctx->d_work = nullptr;
+  ctx->d_partial = ctx->d_red = nullptr;
+  ctx->red_cap = 0;
+}
+
+inline int64_t ext_index(const DevGrid &G, int i, int j) {
+  return G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+}
+
+bool is_fp32(const wh_ctx *c) { return c->opt.precision == WH_FP32; }
+size_t tsize(const wh_ctx *c) { return is_fp32(c) ? sizeof(float) : sizeof(double); }
+
+// Build the device layout, upload everything that does not depend on omega.
+wh_status build_layout(wh_ctx *ctx) {
+  free_device(ctx);
+  const int order = ctx->opt.order, R = order / 2;
+  int64_t off = 0, coff = 0, k5 = 0, woff = 0, nact = 0;
+  ctx->hgrids.clear();
+  ctx->htiles.clear();
+  for (size_t g = 0; g < ctx->grids.size(); ++g) {
+    const HostGrid &H = ctx->grids[g];
+    DevGrid G{};
+    G.n0 = H.d.n[0];
+    G.n1 = H.d.n[1];
+    G.g0 = H.g0;
+    G.g1 = H.g1;
+    G.pitch = (int32_t)(((G.n0 + 2 * G.g0) + 31) / 32 * 32);
+    G.per0 = H.d.bc[0] == WH_BC_PERIODIC;
+    G.per1 = H.d.bc[2] == WH_BC_PERIODIC;
+    G.kind = H.d.kind;
+    G.ortho = H.d.orthogonal;
+    G.h0 = H.d.h[0];
+    G.h1 = H.d.h[1];
+    G.ext = (int64_t)G.pitch * (G.n1 + 2 * G.g1);
+    G.base = off;
+    off += (G.ext + 31) / 32 * 32;
+    G.cbase = coff;
+    coff += (int64_t)G.n0 * G.n1;
+    bool varc = !H.c2.empty();
+    if (G.kind == WH_CARTESIAN && !varc) {
+      G.stencil = kConstCross;
+      G.nw = 0;
+    } else if (G.kind == WH_CARTESIAN || G.ortho) {
+      G.stencil = kPointCross;
+      G.nw = 4 * R + 1;
+    } else {
+      G.stencil = kPointBox;
+      G.nw = (2 * R + 1) * (2 * R + 1);
+    }
+    G.wbase = woff;
+    woff += (int64_t)G.nw * G.ext;
+    G.kbase = -1;
+    if (G.kind == WH_CURVILINEAR) {
+      G.kbase = k5;
+      k5 += 5 * G.ext;
+    }
+    for (size_t q = 0; q < H.mask.size(); ++q) nact += H.mask[q] != WH_UNUSED;
+    for (int j0 = 0; j0 < G.n1; j0 += kTileY)
+      for (int i0 = 0; i0 < G.n0; i0 += kTileX) ctx->htiles.push_back(Tile{(int32_t)g, i0, j0, 0});
+    ctx->hgrids.push_back(G);
+  }
+  ctx->total = off;
+  ctx->ncompact = coff;
+  ctx->nactive = nact;
+  ctx->nplanes5 = k5;
+  ctx->nweights = woff;
+
+  // host staging of extended arrays
+  std::vector<int8_t> mask(off, 0);
+  std::vector<double> c2(off, 1.0), f(off, 0.0), rx(std::max<int64_t>(k5, 1), 0.0);
+  for (size_t g = 0; g < ctx->grids.size(); ++g) {
+    const HostGrid &H = ctx->grids[g];
+    const DevGrid &G = ctx->hgrids[g];
+    for (int j = 0; j < G.n1; ++j)
+      for (int i = 0; i < G.n0; ++i) {
+        int64_t p = ext_index(G, i, j), c = (int64_t)j * G.n0 + i;
+        mask[p] = H.mask[c];
+        if (!H.c2.empty()) c2[p] = H.c2[c];
+        if (!H.f.empty()) f[p] = H.f[c];
+      }
+    if (G.kind == WH_CURVILINEAR) {
+      const int e0 = G.n0 + 2 * G.g0, e1 = G.n1 + 2 * G.g1;
+      const int64_t E = (int64_t)e0 * e1;
+      for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < e1; ++j)
+          for (int i = 0; i < e0; ++i)
+            rx[G.kbase + k * G.ext + (int64_t)j * G.pitch + i] = H.rx[k * E + (int64_t)j * e0 + i];
+    }
+  }
+
+  // ghost-rule items
+  ctx->hbc.clear();
+  ctx->hbc_grid.clear();
+  ctx->hbc_axis.clear();
+  ctx->hbc_hi.clear();
+  for (size_t g = 0; g < ctx->grids.size(); ++g) {
+    const HostGrid &H = ctx->grids[g];
+    const DevGrid &G = ctx->hgrids[g];
+    for (int s = 0; s < 4; ++s) {
+      const int code = H.d.bc[s];
+      if (code != WH_BC_DIRICHLET && code != WH_BC_NEUMANN) continue;
+      const int a = s / 2, hi = s % 2, nt = a == 0 ? G.n1 : G.n0, nn = a == 0 ? G.n0 : G.n1;
+      for (int t = 0; t < nt; ++t) {
+        auto pt = [&](int k) {
+          int nrm = hi ? nn - 1 - k : k;
+          return a == 0 ? ext_index(G, nrm, t) : ext_index(G, t, nrm);
+        };
+        const int8_t m = mask[pt(0)];
+        BcItem it{};
+        if (code == WH_BC_NEUMANN) {
+          if (m != WH_DISC) continue;
+          it.type = order == 2 ? 0 : 1;
+        } else {
+          if (m != WH_DIRICHLET || order == 2) continue;
+          it.type = 2;
+        }
+        for (int k = 0; k < 4; ++k) {
+          it.u[k] = pt(k);
+          if (k > 0 || code == WH_BC_NEUMANN) {
+            const int8_t mk = mask[pt(k)];
+            if (k <= (order == 2 ? 1 : 3) && mk != WH_DISC && mk != WH_DIRICHLET)
+              return fail(ctx, WH_ERR_GRID,
+                          "grid %zu side %d: ghost rule at %d reads a non-discretization point",
+                          g, s, t);
+          }
+        }
+        it.g[0] = pt(-1);
+        it.g[1] = order == 4 ? pt(-2) : pt(-1);
+        ctx->hbc.push_back(it);
+        ctx->hbc_grid.push_back((int32_t)g);
+        ctx->hbc_axis.push_back(a);
+        ctx->hbc_hi.push_back(hi);
+      }
+    }
+  }
+
+  // interpolation: absolute donor indices and full tensor weights
+  const int w = order + 1, ND = w * w;
+  std::vector<int32_t> didx((size_t)std::max<int64_t>(ctx->nrecv, 1) * ND, 0);
+  std::vector<double> dw((size_t)std::max<int64_t>(ctx->nrecv, 1) * ND, 0.0);
+  std::vector<int64_t> ridx((size_t)std::max<int64_t>(ctx->nrecv, 1), 0);
+  std::vector<int> seen(off, 0);
+  if (off > INT32_MAX) return fail(ctx, WH_ERR_ARG, "grid too large for 32-bit donor indices");
+  for (int64_t r = 0; r < ctx->nrecv; ++r) {
+    const int rgr = ctx->rg[r], dgr = ctx->dg[r];
+    const DevGrid &RG = ctx->hgrids[rgr], &DG = ctx->hgrids[dgr];
+    if (ctx->ri[r] < 0 || ctx->ri[r] >= RG.n0 || ctx->rj[r] < 0 || ctx->rj[r] >= RG.n1)
+      return fail(ctx, WH_ERR_GRID, "receiver %lld outside its grid", (long long)r);
+    const int64_t q = ext_index(RG, ctx->ri[r], ctx->rj[r]);
+    if (mask[q] != WH_INTERP)
+      return fail(ctx, WH_ERR_GRID, "receiver %lld is not an interpolation point", (long long)r);
+    if (seen[q]++)
+      return fail(ctx, WH_ERR_GRID, "receiver %lld listed twice", (long long)r);
+    ridx[r] = q;
+    for (int b = 0; b < w; ++b)
+      for (int a = 0; a < w; ++a) {
+        int ii = ctx->di[r] + a, jj = ctx->dj[r] + b;
+        if (DG.per0) ii = ((ii % DG.n0) + DG.n0) % DG.n0;
+        if (DG.per1) jj = ((jj % DG.n1) + DG.n1) % DG.n1;
+        if (ii < 0 || ii >= DG.n0 || jj < 0 || jj >= DG.n1)
+          return fail(ctx, WH_ERR_GRID, "receiver %lld: donor (%d,%d) outside grid %d",
+                      (long long)r, ii, jj, dgr);
+        const int64_t p = ext_index(DG, ii, jj);
+        if (mask[p] != WH_DISC && mask[p] != WH_DIRICHLET)
+          return fail(ctx, WH_ERR_GRID,
+                      "receiver %lld: donor (%d,%d) of grid %d is not a discretization point",
+                      (long long)r, ii, jj, dgr);
+        didx[r * ND + b * w + a] = (int32_t)p;
+        dw[r * ND + b * w + a] = ctx->wx[r * w + a] * ctx->wy[r * w + b];
+      }
+  }
+  for (size_t g = 0; g < ctx->grids.size(); ++g) {
+    const DevGrid &G = ctx->hgrids[g];
+    for (int j = 0; j < G.n1; ++j)
+      for (int i = 0; i < G.n0; ++i) {
+        int64_t p = ext_index(G, i, j);
+        if (mask[p] == WH_INTERP && !seen[p])
+          return fail(ctx, WH_ERR_GRID, "interpolation point (%d,%d) of grid %zu has no donor",
+                      i, j, g);
+      }
+  }
+
+  // device allocations
+  wh_status st;
+  const size_t ts = tsize(ctx);
+  if ((st = dalloc(ctx, &ctx->d_grids, ctx->hgrids.size())) ||
+      (st = dalloc(ctx, &ctx->d_tiles, ctx->htiles.size())) ||
+      (st = dalloc(ctx, &ctx->d_mask, off)) ||
+      (st = dalloc(ctx, (char **)&ctx->d_Wa, off * ts)) ||
+      (st = dalloc(ctx, (char **)&ctx->d_Wb, off * ts)) ||
+      (st = dalloc(ctx, (char **)&ctx->d_F, off * ts)) ||
+      (st = dalloc(ctx, (char **)&ctx->d_Wt, ctx->nweights * ts)) ||
+      (st = dalloc(ctx, &ctx->d_V, off)) || (st = dalloc(ctx, &ctx->d_c2, off)) ||
+      (st = dalloc(ctx, &ctx->d_rx, std::max<int64_t>(k5, 1))) ||
+      (st = dalloc(ctx, &ctx->d_coef, std::max<int64_t>(k5, 1))) ||
+      (st = dalloc(ctx, &ctx->d_bc, ctx->hbc.size())) ||
+      (st = dalloc(ctx, &ctx->d_bc_grid, ctx->hbc.size())) ||
+      (st = dalloc(ctx, &ctx->d_bc_axis, ctx->hbc.size())) ||
+      (st = dalloc(ctx, &ctx->d_bc_hi, ctx->hbc.size())) ||
+      (st = dalloc(ctx, &ctx->d_didx, didx.size())) || (st = dalloc(ctx, &ctx->d_dw, dw.size())) ||
+      (st = dalloc(ctx, &ctx->d_ridx, ridx.size())) || (st = dalloc(ctx, &ctx->d_smax, 1)))
+    return st;
+  CK(cudaMemcpy(ctx->d_tiles, ctx->htiles.data(), ctx->htiles.size() * sizeof(Tile),
+                cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_mask, mask.data(), off, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_c2, c2.data(), off * sizeof(double), cudaMemcpyHostToDevice));
+  if (is_fp32(ctx)) {
+    std::vector<float> ff(f.begin(), f.end());
+    CK(cudaMemcpy(ctx->d_F, ff.data(), off * sizeof(float), cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(ctx->d_F, f.data(), off * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (k5) CK(cudaMemcpy(ctx->d_rx, rx.data(), k5 * sizeof(double), cudaMemcpyHostToDevice));
+  if (!ctx->hbc.empty()) {
+    CK(cudaMemcpy(ctx->d_bc, ctx->hbc.data(), ctx->hbc.size() * sizeof(BcItem),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bc_grid, ctx->hbc_grid.data(), ctx->hbc.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bc_axis, ctx->hbc_axis.data(), ctx->hbc.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bc_hi, ctx->hbc_hi.data(), ctx->hbc.size() * 4, cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(ctx->d_didx, didx.data(), didx.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_dw, dw.data(), dw.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_ridx, ridx.data(), ridx.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_grids, ctx->hgrids.data(), ctx->hgrids.size() * sizeof(DevGrid),
+                cudaMemcpyHostToDevice));
+  ctx->dirty = false;
+  return WH_OK;
+}
+
+// Optional per-launch event recording (wh_profile_iteration): an event is recorded on the
+// stream before every launch, and the kind of the launch is remembered.
+struct Prof {
+  std::vector<cudaEvent_t> *ev = nullptr;
+  std::vector<int> *kind = nullptr;
+  size_t next = 0;
+  void mark(cudaStream_t s, int k) {
+    if (!ev) return;
+    cudaEventRecord((*ev)[next++], s);
+    kind->push_back(k);
+  }
+};
+
+wh_status launch_steps(wh_ctx *ctx, int forcing, Prof *prof = nullptr) {
+  // the body of one iteration after init: t = 0 ghost rules + interpolation, then M steps
+  const int order = ctx->opt.order;
+  const bool f32 = is_fp32(ctx);
+  cudaStream_t s = ctx->stream;
+  const double fs = forcing ? 1.0 : 0.0;
+  const int nbc = (int)ctx->hbc.size();
+  const int bc_blocks = (nbc + 255) / 256;
+  const int lanes = order == 4 ? 8 : 4;
+  const int g_blocks = (int)((ctx->nrecv * lanes + 255) / 256);
+  const int bg_blocks = bc_blocks + g_blocks;
+  const int ntiles = (int)ctx->htiles.size();
+  void *Wa = ctx->d_Wa, *Wb = ctx->d_Wb;
+  const int M = ctx->ti.M;
+  Prof none;
+  Prof &P = prof ? *prof : none;
+  auto bcg = [&](void *W, int n) {
+    if (bg_blocks == 0) return;
+    P.mark(s, 1);
+    launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx, ctx->d_dw,
+                     ctx->d_ridx, (int)ctx->nrecv, W, ctx->d_F,
+                     fs * std::cos(ctx->ti.omega_e * n * ctx->ti.dt), ctx->d_V, ctx->wf[n]);
+  };
+  bcg(Wa, 0);
+  // first step: W^1 = (sum w W^0)/2 - dt^2/2 f
+  P.mark(s, 0);
+  launch_march(f32, order, true, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask, Wa, Wb,
+               ctx->d_F, ctx->d_Wt, ctx->d_V, fs * 0.5 * ctx->ti.dt * ctx->ti.dt, ctx->wf[1]);
+  bcg(Wb, 1);
+  for (int n = 1; n < M; ++n) {
+    void *cur = (n & 1) ? Wb : Wa;
+    void *oth = (n & 1) ? Wa : Wb;
+    P.mark(s, 0);
+    launch_march(f32, order, false, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask, cur, oth,
+                 ctx->d_F, ctx->d_Wt, ctx->d_V, fs * ctx->fc[n], ctx->wf[n + 1]);
+    bcg(oth, n + 1);
+  }
+  return WH_OK;
+}
+
+wh_status build_graph(wh_ctx *ctx, int forcing) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  wh_status st = launch_steps(ctx, forcing);
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (st != WH_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(ctx, WH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->gexec[forcing], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return fail(ctx, WH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return WH_OK;
+}
+
+wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
+  forcing = forcing ? 1 : 0;
+  if (!ctx->gexec[forcing]) {
+    wh_status st = build_graph(ctx, forcing);
+    if (st) return st;
+  }
+  const int blk = 256;
+  const int64_t nb = (ctx->total + blk - 1) / blk;
+  const int ng = (int)ctx->hgrids.size();
+  launch_init(is_fp32(ctx), (unsigned)nb, ctx->stream, ctx->d_grids, ng, ctx->d_mask, vin,
+              ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
+  CK(cudaGetLastError());
+  CK(cudaGraphLaunch(ctx->gexec[forcing], ctx->stream));
+  const int64_t nc = (ctx->ncompact + blk - 1) / blk;
+  launch_finish((unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V, vout,
+                ctx->ncompact);
+  CK(cudaGetLastError());
+  ctx->launches += 2 + 2 * (int64_t)ctx->ti.M + 1;
+  return WH_OK;
+}
+
+// ---- reductions ----
+wh_status ensure_red(wh_ctx *ctx, int nv) {
+  if (ctx->partial_blocks == 0) {
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ctx->partial_blocks = sms * 4;
+  }
+  if (nv > ctx->red_cap) {
+    wh_status st;
+    if ((st = dalloc(ctx, &ctx->d_partial, (size_t)nv * ctx->partial_blocks)) ||
+        (st = dalloc(ctx, &ctx->d_red, (size_t)nv)))
+      return st;
+    ctx->red_cap = nv;
+  }
+  return WH_OK;
+}
+
+// out[k] = <X_k, y>, k < nv, on the device (d_red) and copied to host `out`.
+wh_status multidot(wh_ctx *ctx, const double *X, int64_t ldx, int nv, const double *y, int64_t n,
+                   double *out_host) {
+  wh_status st = ensure_red(ctx, nv);
+  if (st) return st;
+  int nb = (int)std::min<int64_t>(ctx->partial_blocks, (n + kRedThreads - 1) / kRedThreads);
+  if (nb < 1) nb = 1;
+  launch_multidot(nb, ctx->stream, X, ldx, nv, y, n, ctx->d_partial, ctx->d_red);
+  CK(cudaGetLastError());
+  ctx->launches += 2;
+  if (out_host) {
+    CK(cudaMemcpyAsync(out_host, ctx->d_red, nv * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return WH_OK;
+}
+
+wh_status ensure_stream(wh_ctx *ctx) {
+  if (ctx->stream) return WH_OK;
+  if (!ctx->own_stream) CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+  ctx->stream = ctx->own_stream;
+  return WH_OK;
+}
+
+unsigned grid1d(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)std::min<int64_t>(b, 152 * 16);
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+wh_status wh_options_default(wh_options *opt) {
+  if (!opt) return WH_ERR_ARG;
+  opt->order = 4;
+  opt->periods = 1;
+  opt->cfl = 0.9;
+  opt->alpha_mode = 0;
+  opt->precision = WH_FP64;
+  return WH_OK;
+}
+
+wh_status wh_create(const wh_options *opt, wh_ctx **out) {
+  if (!out) return WH_ERR_ARG;
+  *out = nullptr;
+  wh_options o;
+  wh_options_default(&o);
+  if (opt) o = *opt;
+  if ((o.order != 2 && o.order != 4) || o.periods < 1 || !(o.cfl > 0.0 && o.cfl <= 1.0) ||
+      (o.alpha_mode != 0 && o.alpha_mode != 1) ||
+      (o.precision != WH_FP64 && o.precision != WH_FP32))
+    return WH_ERR_ARG;
+  wh_ctx *ctx = new (std::nothrow) wh_ctx();
+  if (!ctx) return WH_ERR_NOMEM;
+  ctx->opt = o;
+  // the context's own stream is created on first device use, so that grid description
+  // and validation work without a GPU
+  *out = ctx;
+  return WH_OK;
+}
+
+void wh_destroy(wh_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_device(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+const char *wh_last_error(const wh_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+wh_status wh_set_stream(wh_ctx *ctx, void *stream) {
+  if (!ctx) return WH_ERR_ARG;
+  if (!stream && !ctx->own_stream) {
+    wh_status st = ensure_stream(ctx);
+    if (st) return st;
+  }
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
+  if (s != ctx->stream) {
+    for (int k = 0; k < 2; ++k)
+      if (ctx->gexec[k]) {
+        cudaGraphExecDestroy(ctx->gexec[k]);
+        ctx->gexec[k] = nullptr;
+      }
+  }
+  ctx->stream = s;
+  return WH_OK;
+}
+
+wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *gd, int32_t *grid_id) {
+  if (!ctx || !gd || !gd->mask) return fail(ctx, WH_ERR_ARG, "null grid description");
+  const int order = ctx->opt.order;
+  const int *bc = gd->bc;
+  for (int s = 0; s < 4; ++s)
+    if (bc[s] < WH_BC_NONE || bc[s] > WH_BC_PERIODIC)
+      return fail(ctx, WH_ERR_ARG, "bad boundary code %d", bc[s]);
+  if ((bc[0] == WH_BC_PERIODIC) != (bc[1] == WH_BC_PERIODIC) ||
+      (bc[2] == WH_BC_PERIODIC) != (bc[3] == WH_BC_PERIODIC))
+    return fail(ctx, WH_ERR_GRID, "periodic sides must come in pairs");
+  if (gd->kind != WH_CARTESIAN && gd->kind != WH_CURVILINEAR)
+    return fail(ctx, WH_ERR_ARG, "bad grid kind");
+  if (gd->kind == WH_CURVILINEAR && !gd->rx)
+    return fail(ctx, WH_ERR_ARG, "curvilinear grid without metrics");
+  if (!(gd->h[0] > 0) || !(gd->h[1] > 0)) return fail(ctx, WH_ERR_ARG, "non-positive spacing");
+  for (int a = 0; a < 2; ++a) {
+    const bool per = bc[2 * a] == WH_BC_PERIODIC;
+    if (gd->n[a] < (per ? order + 1 : 2 * order + 1))
+      return fail(ctx, WH_ERR_ARG, "grid too small along axis %d", a);
+  }
+  bool phys = false, neu = false;
+  for (int s = 0; s < 4; ++s) {
+    phys |= bc[s] == WH_BC_DIRICHLET || bc[s] == WH_BC_NEUMANN;
+    neu |= bc[s] == WH_BC_NEUMANN;
+  }
+  if (gd->kind == WH_CURVILINEAR && !gd->orthogonal && phys)
+    return fail(ctx, WH_ERR_GRID, "non-orthogonal grid with a Dirichlet or Neumann side");
+  if (neu)
+    for (int s = 0; s < 4; ++s)
+      for (int s2 = 0; s2 < 4; ++s2)
+        if (s / 2 != s2 / 2 && bc[s] == WH_BC_NEUMANN &&
+            (bc[s2] == WH_BC_DIRICHLET || bc[s2] == WH_BC_NEUMANN))
+          return fail(ctx, WH_ERR_GRID, "a Neumann side meets another physical side");
+  HostGrid H;
+  H.d = *gd;
+  const int64_t n = (int64_t)gd->n[0] * gd->n[1];
+  H.mask.assign(gd->mask, gd->mask + n);
+  for (int64_t q = 0; q < n; ++q)
+    if (H.mask[q] < WH_UNUSED || H.mask[q] > WH_DIRICHLET)
+      return fail(ctx, WH_ERR_GRID, "bad mask value %d", (int)H.mask[q]);
+  H.g0 = bc[0] == WH_BC_PERIODIC ? 0 : order / 2;
+  H.g1 = bc[2] == WH_BC_PERIODIC ? 0 : order / 2;
+  if (gd->kind == WH_CURVILINEAR) {
+    const int64_t E = (int64_t)(gd->n[0] + 2 * H.g0) * (gd->n[1] + 2 * H.g1);
+    H.rx.assign(gd->rx, gd->rx + 4 * E);
+    for (double v : H.rx)
+      if (!std::isfinite(v)) return fail(ctx, WH_ERR_GRID, "non-finite metric");
+  }
+  if (gd->c2) {
+    H.c2.assign(gd->c2, gd->c2 + n);
+    for (double v : H.c2)
+      if (!(v > 0) || !std::isfinite(v)) return fail(ctx, WH_ERR_ARG, "c^2 must be positive");
+  }
+  ctx->grids.push_back(std::move(H));
+  ctx->dirty = true;
+  ctx->prepared = false;
+  if (grid_id) *grid_id = (int32_t)ctx->grids.size() - 1;
+  return WH_OK;
+}
+
+wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *it) {
+  if (!ctx || !it || it->n < 0) return fail(ctx, WH_ERR_ARG, "null interpolation data");
+  const int w = ctx->opt.order + 1;
+  const int64_t n = it->n;
+  if (n > 0 && (!it->recv_grid || !it->recv_i || !it->recv_j || !it->donor_grid ||
+                !it->donor_i0 || !it->donor_j0 || !it->wx || !it->wy))
+    return fail(ctx, WH_ERR_ARG, "null interpolation array");
+  for (int64_t r = 0; r < n; ++r) {
+    if (it->recv_grid[r] < 0 || it->recv_grid[r] >= (int)ctx->grids.size() ||
+        it->donor_grid[r] < 0 || it->donor_grid[r] >= (int)ctx->grids.size())
+      return fail(ctx, WH_ERR_GRID, "receiver %lld: bad grid index", (long long)r);
+    if (it->recv_grid[r] == it->donor_grid[r])
+      return fail(ctx, WH_ERR_GRID, "receiver %lld interpolates from its own grid", (long long)r);
+    for (int a = 0; a < w; ++a)
+      if (!std::isfinite(it->wx[r * w + a]) || !std::isfinite(it->wy[r * w + a]))
+        return fail(ctx, WH_ERR_GRID, "receiver %lld: non-finite weight", (long long)r);
+  }
+  ctx->nrecv = n;
+  ctx->rg.assign(it->recv_grid, it->recv_grid + n);
+  ctx->ri.assign(it->recv_i, it->recv_i + n);
+  ctx->rj.assign(it->recv_j, it->recv_j + n);
+  ctx->dg.assign(it->donor_grid, it->donor_grid + n);
+  ctx->di.assign(it->donor_i0, it->donor_i0 + n);
+  ctx->dj.assign(it->donor_j0, it->donor_j0 + n);
+  ctx->wx.assign(it->wx, it->wx + n * w);
+  ctx->wy.assign(it->wy, it->wy + n * w);
+  ctx->dirty = true;
+  ctx->prepared = false;
+  return WH_OK;
+}
+
+wh_status wh_set_forcing(wh_ctx *ctx, int32_t gid, const double *f) {
+  if (!ctx || !f || gid < 0 || gid >= (int)ctx->grids.size())
+    return fail(ctx, WH_ERR_ARG, "bad forcing arguments");
+  HostGrid &H = ctx->grids[gid];
+  const int64_t n = (int64_t)H.d.n[0] * H.d.n[1];
+  H.f.assign(f, f + n);
+  for (double v : H.f)
+    if (!std::isfinite(v)) return fail(ctx, WH_ERR_ARG, "non-finite forcing");
+  ctx->dirty = true;
+  ctx->prepared = false;
+  return WH_OK;
+}
+
+wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
+  if (!ctx) return WH_ERR_ARG;
+  if (!(omega > 0) || !std::isfinite(omega)) return fail(ctx, WH_ERR_ARG, "omega must be > 0");
+  if (ctx->grids.empty()) return fail(ctx, WH_ERR_STATE, "no grids");
+  for (size_t g = 0; g < ctx->grids.size(); ++g)
+    for (size_t q = 0; q < ctx->grids[g].mask.size(); ++q)
+      if (ctx->grids[g].mask[q] == WH_INTERP && ctx->nrecv == 0)
+        return fail(ctx, WH_ERR_GRID, "interpolation points but no interpolation data");
+  wh_status st;
+  if ((st = ensure_stream(ctx))) return st;
+  if (ctx->dirty && (st = build_layout(ctx))) return st;
+  for (int k = 0; k < 2; ++k)
+    if (ctx->gexec[k]) {
+      cudaGraphExecDestroy(ctx->gexec[k]);
+      ctx->gexec[k] = nullptr;
+    }
+  const int order = ctx->opt.order;
+  cudaStream_t s = ctx->stream;
+  // (a2) operator coefficients and the frozen-coefficient bound
+  CK(cudaMemsetAsync(ctx->d_smax, 0, sizeof(unsigned long long), s));
+  for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
+    const DevGrid &G = ctx->hgrids[g];
+    dim3 tb(32, 8), gb((G.n0 + 31) / 32, (G.n1 + 7) / 8);
+    launch_coef(order, gb, tb, s, ctx->d_grids, (int)g, ctx->d_mask, ctx->d_rx, ctx->d_c2,
+                ctx->d_coef, ctx->d_smax);
+  }
+  CK(cudaGetLastError());
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, ctx->d_smax, sizeof bits, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double smax;
+  std::memcpy(&smax, &bits, sizeof smax);
+  if (!(smax > 0) || !std::isfinite(smax))
+    return fail(ctx, WH_ERR_GRID, "no discretization point (stability bound %g)", smax);
+  // (a1) time setup: Recipe OmegaTildeExplicit, alpha_d
+  const double Cp = order == 2 ? 1.0 : std::sqrt(3.0) / 2.0;
+  const double dtmax = ctx->opt.cfl * Cp / std::sqrt(smax);
+  int Nt = (int)std::ceil(2.0 * M_PI / (omega * dtmax));
+  if (Nt < 2) Nt = 2;
+  double dt = 2.0 / omega * std::sin(M_PI / Nt);
+  while (dt > dtmax) {
+    ++Nt;
+    dt = 2.0 / omega * std::sin(M_PI / Nt);
+  }
+  const int M = ctx->opt.periods * Nt;
+  wh_time_info &ti = ctx->ti;
+  ti.omega = omega;
+  ti.dt = dt;
+  ti.omega_e = 2.0 * M_PI / (Nt * dt);
+  ti.alpha = ctx->opt.alpha_mode ? 0.5 : std::tan(ti.omega_e * dt / 2) / std::tan(ti.omega_e * dt);
+  ti.dt_max = dtmax;
+  ti.Tbar = M * dt;
+  ti.Nt = Nt;
+  ti.M = M;
+  ti.n_active = ctx->nactive;
+  ti.n_total = ctx->ncompact;
+  // per-step tables: forcing factor dt^2 cos(omega_e t^n), filter weight of level n
+  ctx->fc.assign(M + 1, 0.0);
+  ctx->wf.assign(M + 1, 0.0);
+  for (int n = 0; n <= M; ++n) {
+    const double cn = std::cos(ti.omega_e * n * dt);
+    ctx->fc[n] = dt * dt * cn;
+    const double sig = (n == 0 || n == M) ? 0.5 : 1.0;
+    ctx->wf[n] = (2.0 / M) * sig * (cn - ti.alpha / 2.0);
+  }
+  // stencil weights
+  const double dt2 = dt * dt;
+  for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
+    DevGrid &G = ctx->hgrids[g];
+    if (G.stencil == kConstCross) {
+      const double c2 = 1.0, x = dt2 * c2 / (G.h0 * G.h0), y = dt2 * c2 / (G.h1 * G.h1);
+      if (order == 2) {
+        G.cw[0] = 2.0 - 2.0 * x - 2.0 * y;
+        G.cw[1] = x;
+        G.cw[2] = 0.0;
+        G.cw[3] = y;
+        G.cw[4] = 0.0;
+      } else {
+        G.cw[0] = 2.0 - 2.5 * x - 2.5 * y;
+        G.cw[1] = 16.0 / 12.0 * x;
+        G.cw[2] = -1.0 / 12.0 * x;
+        G.cw[3] = 16.0 / 12.0 * y;
+        G.cw[4] = -1.0 / 12.0 * y;
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(ctx->d_grids, ctx->hgrids.data(), ctx->hgrids.size() * sizeof(DevGrid),
+                     cudaMemcpyHostToDevice, s));
+  for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
+    const DevGrid &G = ctx->hgrids[g];
+    if (G.stencil == kConstCross) continue;
+    dim3 tb(32, 8), gb((G.n0 + 31) / 32, (G.n1 + 7) / 8);
+    launch_weight(is_fp32(ctx), order, gb, tb, s, ctx->d_grids, (int)g, ctx->d_mask,
+                  ctx->d_coef, ctx->d_c2, ctx->d_Wt, dt2);
+  }
+  const int nbc = (int)ctx->hbc.size();
+  if (nbc)
+    launch_bc_coef(nbc, s, ctx->d_bc, ctx->d_bc_grid, ctx->d_bc_axis, ctx->d_bc_hi, ctx->d_grids,
+                   ctx->d_coef, ctx->d_c2);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  ctx->prepared = true;
+  if (info) *info = ti;
+  return WH_OK;
+}
+
+wh_status wh_iterate(wh_ctx *ctx, int32_t forcing, const double *vin, double *vout) {
+  if (!ctx || !vin || !vout) return fail(ctx, WH_ERR_ARG, "null vector");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  if (vin == vout) return fail(ctx, WH_ERR_ARG, "v_in and v_out alias");
+  ctx->launches = 0;
+  return iterate_device(ctx, forcing, vin, vout);
+}
+
+wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *vin, double *vout) {
+  if (!ctx || !vin || !vout) return fail(ctx, WH_ERR_ARG, "null vector");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  wh_status st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, 3 * (size_t)ctx->ncompact))) return st;
+  const size_t bytes = ctx->ncompact * sizeof(double);
+  ctx->launches = 0;
+  CK(cudaMemcpyAsync(ctx->d_work, vin, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  if ((st = iterate_device(ctx, forcing, ctx->d_work, ctx->d_work + ctx->ncompact))) return st;
+  CK(cudaMemcpyAsync(vout, ctx->d_work + ctx->ncompact, bytes, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return WH_OK;
+}
+
+wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, double *out) {
+  if (!ctx || !x || !y || !out || n < 0) return fail(ctx, WH_ERR_ARG, "bad wh_dot arguments");
+  ctx->launches = 0;
+  return multidot(ctx, x, 0, 1, y, n, out);
+}
+
+wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
+                   double *u, wh_stats *stats, double *history, int32_t history_cap) {
+  if (!ctx || !u || !(tol > 0) || max_it < 1 || (method != WH_FPI && method != WH_GMRES))
+    return fail(ctx, WH_ERR_ARG, "bad wh_solve arguments");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  if (method == WH_GMRES && (restart < 1 || restart > 1000))
+    return fail(ctx, WH_ERR_ARG, "restart must be in [1, 1000]");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = ctx->ncompact;
+  wh_status st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, 3 * (size_t)n))) return st;
+  double *w0 = ctx->d_work, *w1 = ctx->d_work + n, *w2 = ctx->d_work + 2 * n;
+  cudaStream_t s = ctx->stream;
+  int nh = 0;
+  auto hist = [&](double r) {
+    if (history && nh < history_cap) history[nh] = r;
+    ++nh;
+  };
+  ctx->launches = 0;
+  wh_stats S{};
+  auto finish = [&](wh_status code) {
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    S.n_history = std::min(nh, history_cap < 0 ? 0 : history_cap);
+    if (stats) *stats = S;
+    return code;
+  };
+  if (method == WH_FPI) {
+    for (int k = 0; k < max_it; ++k) {
+      if ((st = iterate_device(ctx, 1, u, w0))) return finish(st);
+      launch_sub(grid1d(n), s, w0, u, w1, n);
+      CK(cudaMemcpyAsync(u, w0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      double d[2];
+      if ((st = multidot(ctx, w1, 0, 1, w1, n, &d[0]))) return finish(st);
+      if ((st = multidot(ctx, u, 0, 1, u, n, &d[1]))) return finish(st);
+      const double r = std::sqrt(d[0]) / std::max(std::sqrt(d[1]), 1e-300);
+      S.iterations = k + 1;
+      S.residual = r;
+      hist(r);
+      if (!std::isfinite(r)) return finish(fail(ctx, WH_ERR_DIVERGED, "FPI residual is %g", r));
+      if (r <= tol) {
+        S.converged = 1;
+        return finish(WH_OK);
+      }
+    }
+    return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "FPI: %d iterations, residual %g", max_it,
+                       S.residual));
+  }
+  // GMRES(m) on A v = v - W_h(v, 0), b = W_h(0, f)
+  const int m = restart;
+  if (ctx->q_cap < (int64_t)(m + 1) * n) {
+    if ((st = dalloc(ctx, &ctx->d_q, (size_t)(m + 1) * n))) return finish(st);
+    ctx->q_cap = (int64_t)(m + 1) * n;
+  }
+  double *Q = ctx->d_q;
+  CK(cudaMemsetAsync(w0, 0, n * sizeof(double), s));
+  if ((st = iterate_device(ctx, 1, w0, w2))) return finish(st);  // w2 = b
+  double bb;
+  if ((st = multidot(ctx, w2, 0, 1, w2, n, &bb))) return finish(st);
+  const double bnorm = std::sqrt(bb);
+  if (!(bnorm > 0)) {
+    CK(cudaMemsetAsync(u, 0, n * sizeof(double), s));
+    S.converged = 1;
+    return finish(WH_OK);
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
+  int its = 0;
+  double rel = 1.0;
+  if ((st = ensure_red(ctx, m + 1))) return finish(st);
+  while (true) {
+    // r = b - A u = b - u + W_h(u, 0)
+    if ((st = iterate_device(ctx, 0, u, w0))) return finish(st);
+    ++its;
+    launch_sub(grid1d(n), s, w2, u, w1, n);  // w1 = b - u
+    launch_axpby(grid1d(n), s, 1.0, w0, 1.0, w1, n);  // w1 += W_h(u, 0)
+    double rr;
+    if ((st = multidot(ctx, w1, 0, 1, w1, n, &rr))) return finish(st);
+    const double beta = std::sqrt(rr);
+    rel = beta / bnorm;
+    hist(rel);
+    S.iterations = its;
+    S.residual = rel;
+    if (!std::isfinite(rel)) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual %g", rel));
+    if (rel <= tol) {
+      S.converged = 1;
+      return finish(WH_OK);
+    }
+    if (its >= max_it)
+      return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", its, rel));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    launch_axpby(grid1d(n), s, 1.0 / beta, w1, 0.0, Q, n);
+    int k = 0, kk = 0;
+    for (k = 0; k < m; ++k) {
+      double *qk = Q + (int64_t)k * n, *w = Q + (int64_t)(k + 1) * n;
+      if ((st = iterate_device(ctx, 0, qk, w0))) return finish(st);
+      ++its;
+      launch_sub(grid1d(n), s, qk, w0, w, n);  // w = q_k - W_h(q_k, 0)
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        // h = Q^T w lands in d_red (device) and in h (host)
+        if ((st = multidot(ctx, Q, n, k + 1, w, n, h.data()))) return finish(st);
+        launch_multi_axpy(grid1d(n), s, Q, n, k + 1, ctx->d_red, w, n);
+        for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] += h[i];
+      }
+      double ww;
+      if ((st = multidot(ctx, w, 0, 1, w, n, &ww))) return finish(st);
+      double hk1 = std::sqrt(ww);
+      if (hk1 > 0) launch_axpby(grid1d(n), s, 0.0, w, 1.0 / hk1, w, n);
+      for (int i = 0; i < k; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + k] + sn[i] * H[(size_t)(i + 1) * m + k];
+        H[(size_t)(i + 1) * m + k] = -sn[i] * H[(size_t)i * m + k] + cs[i] * H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = t;
+      }
+      const double hkk = H[(size_t)k * m + k];
+      const double den = std::hypot(hkk, hk1);
+      cs[k] = hkk / den;
+      sn[k] = hk1 / den;
+      H[(size_t)k * m + k] = den;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      rel = std::fabs(g[k + 1]) / bnorm;
+      hist(rel);
+      S.iterations = its;
+      S.residual = rel;
+      kk = k + 1;
+      if (!std::isfinite(rel)) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual %g", rel));
+      if (rel <= tol || its >= max_it || hk1 == 0) break;
+    }
+    for (int i = kk - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int j = i + 1; j < kk; ++j) t -= H[(size_t)i * m + j] * y[j];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(ctx->d_red, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gemv_acc(grid1d(n), s, Q, n, kk, ctx->d_red, u, n);
+    CK(cudaGetLastError());
+  }
+}
+
+wh_status wh_profile_iteration(wh_ctx *ctx, int32_t forcing, const double *vin, double *vout,
+                               double *ms, int32_t *counts) {
+  if (!ctx || !vin || !vout || !ms || !counts) return fail(ctx, WH_ERR_ARG, "null argument");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  const size_t need = 2 * (size_t)ctx->ti.M + 8;
+  static thread_local std::vector<cudaEvent_t> ev;
+  while (ev.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ev.push_back(e);
+  }
+  std::vector<int> kind;
+  Prof P;
+  P.ev = &ev;
+  P.kind = &kind;
+  const int blk = 256;
+  const int ng = (int)ctx->hgrids.size();
+  cudaStream_t s = ctx->stream;
+  P.mark(s, 2);
+  launch_init(is_fp32(ctx), (unsigned)((ctx->total + blk - 1) / blk), s, ctx->d_grids, ng,
+              ctx->d_mask, vin, ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
+  wh_status st = launch_steps(ctx, forcing ? 1 : 0, &P);
+  if (st) return st;
+  P.mark(s, 3);
+  launch_finish((unsigned)((ctx->ncompact + blk - 1) / blk), s, ctx->d_grids, ng, ctx->d_mask,
+                ctx->d_V, vout, ctx->ncompact);
+  CK(cudaEventRecord(ev[P.next], s));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(ev[P.next]));
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = 0.0;
+    counts[k] = 0;
+  }
+  for (size_t q = 0; q < kind.size(); ++q) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
+    ms[kind[q]] += t;
+    counts[kind[q]] += 1;
+  }
+  ctx->launches = (int64_t)kind.size();
+  return WH_OK;
+}
+
+wh_status wh_get_time_info(const wh_ctx *ctx, wh_time_info *info) {
+  if (!ctx || !info) return WH_ERR_ARG;
+  if (!ctx->prepared) return WH_ERR_STATE;
+  *info = ctx->ti;
+  return WH_OK;
+}
+
+int64_t wh_last_launch_count(const wh_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// wh_internal.h -- device-side data structures of libwaveholtz (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wh {
+
+constexpr int kMaxOrder = 4;
+constexpr int kTileX = 32;  // march tile: 32 x 8 points, one point per thread
+constexpr int kTileY = 8;
+
+// Stencil storage of a grid in the march kernels.
+enum StencilKind : int32_t {
+  kConstCross = 0,  // Cartesian, constant c: weights in DevGrid::cw
+  kPointCross = 1,  // per-point weights on the 2p+1 cross (orthogonal grids, c(x))
+  kPointBox = 2     // per-point weights on the (p+1)^2 box (non-orthogonal grids)
+};
+
+// One component grid in device memory.  Extended arrays (ghosts included) are stored
+// row-major with row stride `pitch`; element (i, j), i in [-g0, n0+g0), starts at
+// base + (j + g1) * pitch + (i + g0).
+struct DevGrid {
+  int32_t n0, n1, g0, g1;
+  int32_t pitch;
+  int32_t per0, per1;       // periodic axes
+  int32_t stencil;          // StencilKind
+  int32_t nw;               // weights per point (per-point stencils)
+  int32_t kind;             // WH_CARTESIAN / WH_CURVILINEAR
+  int32_t ortho;
+  int32_t pad_;
+  int64_t base;             // offset of the extended array in the state arrays
+  int64_t ext;              // pitch * (n1 + 2 g1)
+  int64_t cbase;            // offset in compact vectors
+  int64_t wbase;            // offset of weight plane 0 in the weight array (stride ext)
+  int64_t kbase;            // offset of coefficient plane 0 (5 planes, stride ext)
+  double h0, h1;
+  // constant cross weights (kConstCross), dt^2 folded in, centre includes the "2":
+  // [centre, axis0 offset 1, axis0 offset 2, axis1 offset 1, axis1 offset 2]
+  double cw[5];
+};
+
+// One ghost-rule item: the ghost points next to one boundary point (Sec. 3.2 ghost
+// rules; see the library source for the formulas).
+struct BcItem {
+  int64_t u[4];      // state indices of U0..U3 (boundary point and three inward)
+  int64_t g[2];      // state indices of G1, G2 (G2 unused at order 2)
+  int32_t type;      // 0: Neumann order 2, 1: Neumann order 4, 2: Dirichlet order 4
+  int32_t pad_;
+  double A2, B1;     // Dirichlet order 4: a_nn/(12 h^2), +-b_n/(12 h) (c^2 folded)
+  double inv;        // 1 / (11 A2 - 3 B1)
+};
+
+// One tile of the march: a 32 x 8 block of one grid.
+struct Tile {
+  int32_t grid, i0, j0, pad_;
+};
+
+// Host launchers (wh_kernels.cu).  T is double unless fp32 is set; pointers typed void
+// carry T arrays.
+void launch_march(bool fp32, int order, bool first, int ntiles, cudaStream_t s,
+                  const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
+                  void *Wout, const void *F, const void *Wt, double *V, double fc, double wf);
+void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
+                      int nbc, int bc_blocks, const int32_t *didx, const double *dw,
+                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos,
+                      double *V, double wf);
+void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
+                 const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
+                 double w0);
+void launch_finish(unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
+                   const int8_t *mask, const double *V, double *vout, int64_t ncompact);
+void launch_coef(int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids, int gidx,
+                 const int8_t *mask, const double *rx, const double *c2, double *coef,
+                 unsigned long long *smax);
+void launch_weight(bool fp32, int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids,
+                   int gidx, const int8_t *mask, const double *coef, const double *c2, void *Wt,
+                   double dt2);
+void launch_bc_coef(int nbc, cudaStream_t s, BcItem *bc, const int32_t *ig, const int32_t *ia,
+                    const int32_t *ih, const DevGrid *grids, const double *coef,
+                    const double *c2);
+constexpr int kRedThreads = 256;
+void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
+                     const double *y, int64_t n, double *partial, double *out);
+void launch_multi_axpy(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
+                       const double *h, double *y, int64_t n);
+void launch_axpby(unsigned nb, cudaStream_t s, double a, const double *x, double b, double *y,
+                  int64_t n);
+void launch_sub(unsigned nb, cudaStream_t s, const double *x, const double *z, double *y,
+                int64_t n);
+void launch_gemv_acc(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
+                     const double *c, double *y, int64_t n);
+
+}  // namespace wh

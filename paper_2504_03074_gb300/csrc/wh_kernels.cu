@@ -1,0 +1,557 @@
+// wh_kernels.cu -- CUDA kernels of one WaveHoltz iteration on an overset grid (sm_103a).
+//
+// Per time step (Algorithm 2, Sec. 3.2) the library launches
+//   march_kernel      advance every discretization point of every grid (explicit
+//                     scheme, Eq. WaveSchemeexplicit) and fold the new level into the
+//                     time-filter accumulator (Eq. updateDiscreteExplicit);
+//   bc_gather_kernel  ghost-point rules of every physical side, and the overset
+//                     interpolation of every receiver (tensor-product Lagrange, Sec. 3.1)
+//                     with its filter contribution.
+// The two parts of bc_gather_kernel are independent: ghost rules read only
+// discretization/Dirichlet points of the new level and donors are never ghosts.
+//
+// GB300 note: FP64 throughput is ~2 FMA/clk/SM, so these kernels are FP64-ALU bound;
+// the weights fold dt^2, c(x)^2 and the "2 W^n" of the leapfrog into one per-point
+// stencil so that an order-4 point costs 11 FP64 instructions (9 stencil FMAs, the
+// forcing FMA and the filter FMA).
+#include <cstdint>
+
+#include "wh_internal.h"
+
+namespace wh {
+
+__device__ __forceinline__ int wrap(int i, int n, int per) {
+  if (per) {
+    i = i < 0 ? i + n : i;
+    i = i >= n ? i - n : i;
+  }
+  return i;
+}
+
+// Arithmetic of the march.  T is the state type (double or float); the accumulator V is
+// always double.
+template <typename T, int ORDER, bool FIRST>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles,
+                 const int8_t *__restrict__ mask, const T *__restrict__ Wn, T *Wnm1_out,
+                 const T *__restrict__ F, const T *__restrict__ Wt, double *__restrict__ V,
+                 T fc, double wf) {
+  // FIRST: W^1 = (sum_k w_k W^0_k)/2 - fc f  (fc = dt^2/2 * forcing), written to Wnm1_out.
+  // else : W^{n+1} = sum_k w_k W^n_k - W^{n-1} - fc f  (fc = dt^2 cos(omega_e t^n)),
+  //        W^{n-1} read from and W^{n+1} written to Wnm1_out.
+  const Tile t = tiles[blockIdx.x];
+  const DevGrid &G = grids[t.grid];
+  const int i = t.i0 + (int)threadIdx.x;
+  const int j = t.j0 + (int)threadIdx.y;
+  if (i >= G.n0 || j >= G.n1) return;
+  const int64_t row = G.base + (int64_t)(j + G.g1) * G.pitch + G.g0;
+  const int64_t p = row + i;
+  if (mask[p] != 1) return;  // WH_DISC only; Dirichlet values stay 0
+  constexpr int R = ORDER / 2;
+  // neighbour columns / rows (wrapping on periodic axes)
+  int64_t cols[2 * R + 1];
+  int64_t rows[2 * R + 1];
+#pragma unroll
+  for (int k = -R; k <= R; ++k) {
+    cols[k + R] = row + wrap(i + k, G.n0, G.per0);
+    rows[k + R] = (int64_t)(wrap(j + k, G.n1, G.per1) + G.g1) * G.pitch + G.base + G.g0 + i;
+  }
+  T acc;
+  if (G.stencil == kConstCross) {
+    const T wc = (T)G.cw[0];
+    const T Wc = Wn[p];
+    if (FIRST) {
+      acc = wc * Wc;
+    } else {
+      acc = wc * Wc - Wnm1_out[p];
+    }
+    acc += (T)G.cw[1] * (Wn[cols[R - 1]] + Wn[cols[R + 1]]);
+    acc += (T)G.cw[3] * (Wn[rows[R - 1]] + Wn[rows[R + 1]]);
+    if (ORDER == 4) {
+      acc += (T)G.cw[2] * (Wn[cols[0]] + Wn[cols[4]]);
+      acc += (T)G.cw[4] * (Wn[rows[0]] + Wn[rows[4]]);
+    }
+  } else if (G.stencil == kPointCross) {
+    // plane order: centre, axis 0 offsets -R..-1, 1..R, axis 1 offsets -R..-1, 1..R
+    const int64_t q = G.wbase + (p - G.base);
+    const int64_t E = G.ext;
+    acc = Wt[q] * Wn[p];
+    if (!FIRST) acc -= Wnm1_out[p];
+    int pl = 1;
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {
+      if (k == 0) continue;
+      acc += Wt[q + pl * E] * Wn[cols[k + R]];
+      ++pl;
+    }
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {
+      if (k == 0) continue;
+      acc += Wt[q + pl * E] * Wn[rows[k + R]];
+      ++pl;
+    }
+  } else {
+    // box: plane (b + R) * (2R + 1) + (a + R) holds the weight of offset (a, b)
+    const int64_t q = G.wbase + (p - G.base);
+    const int64_t E = G.ext;
+    acc = FIRST ? (T)0 : -Wnm1_out[p];
+#pragma unroll
+    for (int b = -R; b <= R; ++b) {
+      const int jj = wrap(j + b, G.n1, G.per1);
+      const int64_t rb = G.base + (int64_t)(jj + G.g1) * G.pitch + G.g0;
+#pragma unroll
+      for (int a = -R; a <= R; ++a) {
+        const int ii = wrap(i + a, G.n0, G.per0);
+        acc += Wt[q + ((b + R) * (2 * R + 1) + (a + R)) * E] * Wn[rb + ii];
+      }
+    }
+  }
+  if (FIRST) acc *= (T)0.5;
+  acc -= fc * F[p];
+  Wnm1_out[p] = acc;
+  V[p] += wf * (double)acc;
+}
+
+// Ghost rules and overset interpolation for one time level W (both at time t).
+//   BC items [0, nbc): one thread each.
+//   receivers: LANES lanes per receiver (warp-cooperative gather), donors split
+//   across the lanes, partial sums combined with xor shuffles.
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256)
+    bc_gather_kernel(const BcItem *__restrict__ bc, int nbc, int bc_blocks,
+                     const int32_t *__restrict__ didx, const double *__restrict__ dw,
+                     const int64_t *__restrict__ ridx, int nrecv, T *W,
+                     const T *__restrict__ F, double fcos, double *__restrict__ V,
+                     double wf) {
+  if ((int)blockIdx.x < bc_blocks) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nbc) return;
+    const BcItem it = bc[k];
+    const double U0 = (double)W[it.u[0]], U1 = (double)W[it.u[1]];
+    if (it.type == 0) {  // Neumann, order 2: D0 W = 0
+      W[it.g[0]] = (T)U1;
+      return;
+    }
+    const double U2 = (double)W[it.u[2]], U3 = (double)W[it.u[3]];
+    const double E = -10.0 * U0 + 10.0 * U1 - 5.0 * U2 + U3;  // G2 = 5 G1 + E (D+^5 = 0)
+    double G1;
+    if (it.type == 1) {  // Neumann, order 4: 8(U1 - G1) - (U2 - G2) = 0
+      G1 = (18.0 * U1 - 10.0 * U0 - 6.0 * U2 + U3) * (1.0 / 3.0);
+    } else {  // Dirichlet, order 4: c^2 (a_nn D_nn + b_n D_n) W = f cos
+      const double Fb = (double)F[it.u[0]] * fcos;
+      G1 = (Fb - it.A2 * (-30.0 * U0 + 16.0 * U1 - U2) - it.B1 * (8.0 * U1 - U2) +
+            (it.A2 - it.B1) * E) * it.inv;
+    }
+    W[it.g[0]] = (T)G1;
+    W[it.g[1]] = (T)(5.0 * G1 + E);
+    return;
+  }
+  constexpr int ND = (ORDER + 1) * (ORDER + 1);
+  constexpr int LANES = ORDER == 4 ? 8 : 4;
+  const int gtid = (blockIdx.x - bc_blocks) * blockDim.x + threadIdx.x;
+  const int r = gtid / LANES;
+  const int lane = threadIdx.x % LANES;
+  // all lanes of a receiver group take part in the shuffles, so compute even when the
+  // receiver index is past the end and only skip the final store
+  const bool live = r < nrecv;
+  double s = 0.0;
+  if (live) {
+    const int32_t *di = didx + (int64_t)r * ND;
+    const double *wi = dw + (int64_t)r * ND;
+#pragma unroll
+    for (int d = lane; d < ND; d += LANES) s = fma(wi[d], (double)W[di[d]], s);
+  }
+#pragma unroll
+  for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LANES);
+  if (live && lane == 0) {
+    const int64_t q = ridx[r];
+    W[q] = (T)s;
+    V[q] += wf * (double)(T)s;
+  }
+}
+
+// W^0 = v on discretization and interpolation points, 0 elsewhere (ghosts included);
+// V = w_0 W^0 on discretization points, 0 elsewhere.  One thread per extended point.
+template <typename T>
+__global__ void init_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                            const int8_t *__restrict__ mask, const double *__restrict__ v,
+                            T *W0, double *V, int64_t total, double w0) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  int g = 0;
+  while (g + 1 < ngrids && p >= grids[g + 1].base) ++g;
+  const DevGrid &G = grids[g];
+  const int64_t o = p - G.base;
+  const int j = (int)(o / G.pitch) - G.g1;
+  const int i = (int)(o % G.pitch) - G.g0;
+  const int8_t m = mask[p];
+  double val = 0.0;
+  if ((m == 1 || m == 2) && i >= 0 && i < G.n0 && j >= 0 && j < G.n1)
+    val = v[G.cbase + (int64_t)j * G.n0 + i];
+  W0[p] = (T)val;
+  V[p] = m == 1 ? w0 * (double)(T)val : 0.0;
+}
+
+// v_out (compact) = V at active points, 0 at unused points.
+__global__ void finish_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                              const int8_t *__restrict__ mask, const double *__restrict__ V,
+                              double *vout, int64_t ncompact) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncompact) return;
+  int g = 0;
+  while (g + 1 < ngrids && c >= grids[g + 1].cbase) ++g;
+  const DevGrid &G = grids[g];
+  const int64_t o = c - G.cbase;
+  const int j = (int)(o / G.n0), i = (int)(o % G.n0);
+  const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+  vout[c] = mask[p] != 0 ? V[p] : 0.0;
+}
+
+// ---------------------------------------------------------------------------------
+// Operator precompute (mapping method, Sec. 3.1): per point a11, a12, a22, b1, b2 with
+// c(x)^2 folded in, and the frozen-coefficient spectral bound
+//   s = a11/dr1^2 + a22/dr2^2 + 2|a12|/(dr1 dr2)   (max over discretization points).
+// ---------------------------------------------------------------------------------
+
+template <int ORDER>
+__device__ __forceinline__ double d1(const double *a, const DevGrid &G, int i, int j,
+                                     int axis) {
+  // first derivative of an extended array along an axis: D0 or D0 (1 - h^2/6 D+D-)
+  auto at = [&](int ii, int jj) {
+    ii = wrap(ii, G.n0, G.per0);
+    jj = wrap(jj, G.n1, G.per1);
+    return a[(int64_t)(jj + G.g1) * G.pitch + (ii + G.g0)];
+  };
+  const double h = axis == 0 ? G.h0 : G.h1;
+  const int di = axis == 0, dj = axis == 1;
+  if (ORDER == 2) return (at(i + di, j + dj) - at(i - di, j - dj)) / (2.0 * h);
+  return (8.0 * (at(i + di, j + dj) - at(i - di, j - dj)) -
+          (at(i + 2 * di, j + 2 * dj) - at(i - 2 * di, j - 2 * dj))) / (12.0 * h);
+}
+
+template <int ORDER>
+__global__ void coef_kernel(const DevGrid *__restrict__ grids, int gidx,
+                            const int8_t *__restrict__ mask, const double *__restrict__ rx,
+                            const double *__restrict__ c2, double *coef,
+                            unsigned long long *smax_bits) {
+  const DevGrid &G = grids[gidx];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= G.n0 || j >= G.n1) return;
+  const int64_t o = (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+  const int8_t m = mask[G.base + o];
+  if (m != 1 && m != 3) return;
+  const double cc = c2[G.base + o];
+  double s;
+  if (G.kind == 0) {
+    s = cc * (1.0 / (G.h0 * G.h0) + 1.0 / (G.h1 * G.h1));
+  } else {
+    const int64_t E = G.ext;
+    const double *r = rx + G.kbase;  // 4 metric planes dr_k/dx_m at plane 2k+m
+    double rr[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rr[k] = r[k * E + o];
+    const double a11 = rr[0] * rr[0] + rr[1] * rr[1];
+    const double a12 = rr[0] * rr[2] + rr[1] * rr[3];
+    const double a22 = rr[2] * rr[2] + rr[3] * rr[3];
+    double b[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      double acc = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < 2; ++mm)
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+          acc += rr[2 * l + mm] * d1<ORDER>(r + (2 * k + mm) * E, G, i, j, l);
+      b[k] = acc;
+    }
+    double *cf = coef + G.kbase;
+    cf[o] = cc * a11;
+    cf[E + o] = cc * a12;
+    cf[2 * E + o] = cc * a22;
+    cf[3 * E + o] = cc * b[0];
+    cf[4 * E + o] = cc * b[1];
+    s = cc * (a11 / (G.h0 * G.h0) + a22 / (G.h1 * G.h1));
+    if (!G.ortho) s += 2.0 * cc * fabs(a12) / (G.h0 * G.h1);
+  }
+  if (m == 1) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(s));
+}
+
+// Per-point stencil weights (dt^2 folded, centre + 2).  Cartesian grids with c(x) use
+// the cross with a11 = a22 = c^2 (physical spacing), no first-derivative terms.
+template <typename T, int ORDER>
+__global__ void weight_kernel(const DevGrid *__restrict__ grids, int gidx,
+                              const int8_t *__restrict__ mask, const double *__restrict__ coef,
+                              const double *__restrict__ c2, T *Wt, double dt2) {
+  const DevGrid &G = grids[gidx];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= G.n0 || j >= G.n1) return;
+  const int64_t o = (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+  if (mask[G.base + o] != 1) return;
+  constexpr int R = ORDER / 2;
+  const int64_t E = G.ext;
+  double A1, A2, B1 = 0.0, B2 = 0.0, A12 = 0.0;
+  if (G.kind == 0) {
+    A1 = A2 = c2[G.base + o];
+  } else {
+    const double *cf = coef + G.kbase;
+    A1 = cf[o];
+    A12 = G.ortho ? 0.0 : cf[E + o];
+    A2 = cf[2 * E + o];
+    B1 = cf[3 * E + o];
+    B2 = cf[4 * E + o];
+  }
+  // 1-D weights: second derivative D2[k], first derivative D1[k], offsets -R..R
+  double D2[2 * R + 1], D1[2 * R + 1];
+  if (ORDER == 2) {
+    D2[0] = 1.0; D2[1] = -2.0; D2[2] = 1.0;
+    D1[0] = -0.5; D1[1] = 0.0; D1[2] = 0.5;
+  } else {
+    D2[0] = -1.0 / 12; D2[1] = 16.0 / 12; D2[2] = -30.0 / 12; D2[3] = 16.0 / 12; D2[4] = -1.0 / 12;
+    D1[0] = 1.0 / 12; D1[1] = -8.0 / 12; D1[2] = 0.0; D1[3] = 8.0 / 12; D1[4] = -1.0 / 12;
+  }
+  const double h0 = G.h0, h1 = G.h1;
+  T *w = Wt + G.wbase + o;
+  if (G.stencil == kPointCross) {
+    double wc = 2.0 + dt2 * (A1 * D2[R] / (h0 * h0) + A2 * D2[R] / (h1 * h1));
+    w[0] = (T)wc;
+    int pl = 1;
+    for (int k = -R; k <= R; ++k) {
+      if (k == 0) continue;
+      w[pl * E] = (T)(dt2 * (A1 * D2[k + R] / (h0 * h0) + B1 * D1[k + R] / h0));
+      ++pl;
+    }
+    for (int k = -R; k <= R; ++k) {
+      if (k == 0) continue;
+      w[pl * E] = (T)(dt2 * (A2 * D2[k + R] / (h1 * h1) + B2 * D1[k + R] / h1));
+      ++pl;
+    }
+  } else {
+    for (int b = -R; b <= R; ++b)
+      for (int a = -R; a <= R; ++a) {
+        double v = 2.0 * A12 * D1[a + R] * D1[b + R] / (h0 * h1);
+        if (b == 0) v += A1 * D2[a + R] / (h0 * h0) + B1 * D1[a + R] / h0;
+        if (a == 0) v += A2 * D2[b + R] / (h1 * h1) + B2 * D1[b + R] / h1;
+        v *= dt2;
+        if (a == 0 && b == 0) v += 2.0;
+        w[((b + R) * (2 * R + 1) + (a + R)) * E] = (T)v;
+      }
+  }
+}
+
+// Dirichlet order-4 item coefficients from the operator coefficients of the boundary
+// point: A2 = a_nn/(12 h^2), B1 = sgn b_n/(12 h) (sgn = -1 on a high side).
+__global__ void bc_coef_kernel(BcItem *bc, int nbc, const int32_t *__restrict__ item_grid,
+                               const int32_t *__restrict__ item_axis,
+                               const int32_t *__restrict__ item_hi,
+                               const DevGrid *__restrict__ grids,
+                               const double *__restrict__ coef, const double *__restrict__ c2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nbc || bc[k].type != 2) return;
+  const DevGrid &G = grids[item_grid[k]];
+  const int a = item_axis[k];
+  const int64_t p = bc[k].u[0];
+  const double h = a == 0 ? G.h0 : G.h1;
+  double ann, bn;
+  if (G.kind == 0) {
+    ann = c2[p];
+    bn = 0.0;
+  } else {
+    const int64_t o = G.kbase + (p - G.base);
+    ann = coef[o + (a == 0 ? 0 : 2) * G.ext];
+    bn = coef[o + (3 + a) * G.ext];
+  }
+  const double sgn = item_hi[k] ? -1.0 : 1.0;
+  bc[k].A2 = ann / (12.0 * h * h);
+  bc[k].B1 = sgn * bn / (12.0 * h);
+  bc[k].inv = 1.0 / (11.0 * bc[k].A2 - 3.0 * bc[k].B1);
+}
+
+// ---------------------------------------------------------------------------------
+// Reductions for GMRES (Sec. 4.3): FP64, warp-shuffle partial sums per block, then one
+// deterministic second pass.  `nv` vectors X[k] (stride ldx) against y.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double s) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    multidot_partial(const double *__restrict__ X, int64_t ldx, int nv,
+                     const double *__restrict__ y, int64_t n, double *partial) {
+  // partial[k * gridDim.x + block] = sum over this block's grid-stride share
+  __shared__ double red[kRedThreads / 32];
+  for (int k = 0; k < nv; ++k) {
+    const double *x = X + k * ldx;
+    double s = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+      s = fma(x[q], y[q], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : 0.0;
+      t = warp_sum(t);
+      if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    partial_finish(const double *__restrict__ partial, int nblocks, int nv, double *out) {
+  // one block per vector, fixed order
+  __shared__ double red[kRedThreads / 32];
+  const int k = blockIdx.x;
+  if (k >= nv) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)k * nblocks + b];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < kRedThreads / 32 ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) out[k] = t;
+  }
+}
+
+// y -= sum_k h[k] X[k]   (h on the device)
+__global__ void multi_axpy(const double *__restrict__ X, int64_t ldx, int nv,
+                           const double *__restrict__ h, double *y, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double s = y[q];
+    for (int k = 0; k < nv; ++k) s = fma(-h[k], X[k * ldx + q], s);
+    y[q] = s;
+  }
+}
+
+// y = a x + b y
+__global__ void axpby(double a, const double *__restrict__ x, double b, double *y, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = a * x[q] + b * y[q];
+}
+
+// y = x - z
+__global__ void sub(const double *__restrict__ x, const double *__restrict__ z, double *y,
+                    int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = x[q] - z[q];
+}
+
+// y += X^T c  (c on the device, nv entries)
+__global__ void gemv_acc(const double *__restrict__ X, int64_t ldx, int nv,
+                         const double *__restrict__ c, double *y, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double s = y[q];
+    for (int k = 0; k < nv; ++k) s = fma(c[k], X[k * ldx + q], s);
+    y[q] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers (the only entry points the host code uses).
+// ---------------------------------------------------------------------------------
+
+void launch_march(bool fp32, int order, bool first, int ntiles, cudaStream_t s,
+                  const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
+                  void *Wout, const void *F, const void *Wt, double *V, double fc, double wf) {
+  const dim3 tb(kTileX, kTileY);
+#define WH_MARCH(T, O, FI)                                                                  \
+  march_kernel<T, O, FI><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const T *)Wn, (T *)Wout, \
+                                               (const T *)F, (const T *)Wt, V, (T)fc, wf)
+  if (fp32) {
+    if (order == 4) { if (first) WH_MARCH(float, 4, true); else WH_MARCH(float, 4, false); }
+    else            { if (first) WH_MARCH(float, 2, true); else WH_MARCH(float, 2, false); }
+  } else {
+    if (order == 4) { if (first) WH_MARCH(double, 4, true); else WH_MARCH(double, 4, false); }
+    else            { if (first) WH_MARCH(double, 2, true); else WH_MARCH(double, 2, false); }
+  }
+#undef WH_MARCH
+}
+
+void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
+                      int nbc, int bc_blocks, const int32_t *didx, const double *dw,
+                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos,
+                      double *V, double wf) {
+#define WH_BCG(T, O)                                                                      \
+  bc_gather_kernel<T, O><<<blocks, 256, 0, s>>>(bc, nbc, bc_blocks, didx, dw, ridx, nrecv, \
+                                                (T *)W, (const T *)F, fcos, V, wf)
+  if (fp32) { if (order == 4) WH_BCG(float, 4); else WH_BCG(float, 2); }
+  else      { if (order == 4) WH_BCG(double, 4); else WH_BCG(double, 2); }
+#undef WH_BCG
+}
+
+void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
+                 const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
+                 double w0) {
+  if (fp32)
+    init_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (float *)W0, V, total, w0);
+  else
+    init_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (double *)W0, V, total, w0);
+}
+
+void launch_finish(unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
+                   const int8_t *mask, const double *V, double *vout, int64_t ncompact) {
+  finish_kernel<<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, vout, ncompact);
+}
+
+void launch_coef(int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids, int gidx,
+                 const int8_t *mask, const double *rx, const double *c2, double *coef,
+                 unsigned long long *smax) {
+  if (order == 4) coef_kernel<4><<<gb, tb, 0, s>>>(grids, gidx, mask, rx, c2, coef, smax);
+  else coef_kernel<2><<<gb, tb, 0, s>>>(grids, gidx, mask, rx, c2, coef, smax);
+}
+
+void launch_weight(bool fp32, int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids,
+                   int gidx, const int8_t *mask, const double *coef, const double *c2, void *Wt,
+                   double dt2) {
+  if (fp32) {
+    if (order == 4) weight_kernel<float, 4><<<gb, tb, 0, s>>>(grids, gidx, mask, coef, c2, (float *)Wt, dt2);
+    else weight_kernel<float, 2><<<gb, tb, 0, s>>>(grids, gidx, mask, coef, c2, (float *)Wt, dt2);
+  } else {
+    if (order == 4) weight_kernel<double, 4><<<gb, tb, 0, s>>>(grids, gidx, mask, coef, c2, (double *)Wt, dt2);
+    else weight_kernel<double, 2><<<gb, tb, 0, s>>>(grids, gidx, mask, coef, c2, (double *)Wt, dt2);
+  }
+}
+
+void launch_bc_coef(int nbc, cudaStream_t s, BcItem *bc, const int32_t *ig, const int32_t *ia,
+                    const int32_t *ih, const DevGrid *grids, const double *coef,
+                    const double *c2) {
+  bc_coef_kernel<<<(nbc + 255) / 256, 256, 0, s>>>(bc, nbc, ig, ia, ih, grids, coef, c2);
+}
+
+void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
+                     const double *y, int64_t n, double *partial, double *out) {
+  multidot_partial<<<nb, kRedThreads, 0, s>>>(X, ldx, nv, y, n, partial);
+  partial_finish<<<nv, kRedThreads, 0, s>>>(partial, nb, nv, out);
+}
+
+void launch_multi_axpy(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
+                       const double *h, double *y, int64_t n) {
+  multi_axpy<<<nb, 256, 0, s>>>(X, ldx, nv, h, y, n);
+}
+
+void launch_axpby(unsigned nb, cudaStream_t s, double a, const double *x, double b, double *y,
+                  int64_t n) {
+  axpby<<<nb, 256, 0, s>>>(a, x, b, y, n);
+}
+
+void launch_sub(unsigned nb, cudaStream_t s, const double *x, const double *z, double *y,
+                int64_t n) {
+  sub<<<nb, 256, 0, s>>>(x, z, y, n);
+}
+
+void launch_gemv_acc(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
+                     const double *c, double *y, int64_t n) {
+  gemv_acc<<<nb, 256, 0, s>>>(X, ldx, nv, c, y, n);
+}
+
+}  // namespace wh

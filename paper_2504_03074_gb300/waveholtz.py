@@ -1,0 +1,234 @@
+"""Thin ctypes binding to libwaveholtz (C ABI: ``include/waveholtz.h``).
+
+Argument marshalling only: every step of a WaveHoltz iteration runs in the library's
+CUDA kernels.  PyTorch provides device memory and the stream.  There is no CPU path:
+if the shared library cannot be loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import grids as G
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libwaveholtz.so")
+_lib = None
+
+WH_OK = 0
+STATUS = {0: "WH_OK", -1: "WH_ERR_ARG", -2: "WH_ERR_CUDA", -3: "WH_ERR_STATE",
+          -4: "WH_ERR_DIVERGED", -5: "WH_ERR_TIMEOUT", -6: "WH_ERR_NOT_CONVERGED",
+          -7: "WH_ERR_GRID", -8: "WH_ERR_NOMEM"}
+FP64, FP32 = 0, 1
+FPI, GMRES = 0, 1
+
+
+class WHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("order", C.c_int32), ("periods", C.c_int32), ("cfl", C.c_double),
+                ("alpha_mode", C.c_int32), ("precision", C.c_int32)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 2), ("kind", C.c_int32), ("bc", C.c_int32 * 4),
+                ("orthogonal", C.c_int32), ("h", C.c_double * 2), ("mask", C.c_void_p),
+                ("rx", C.c_void_p), ("c2", C.c_void_p)]
+
+
+class InterpDesc(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in
+                                     ("recv_grid", "recv_i", "recv_j", "donor_grid", "donor_i0",
+                                      "donor_j0", "wx", "wy")]
+
+
+class TimeInfo(C.Structure):
+    _fields_ = [("omega", C.c_double), ("dt", C.c_double), ("omega_e", C.c_double),
+                ("alpha", C.c_double), ("dt_max", C.c_double), ("Tbar", C.c_double),
+                ("Nt", C.c_int32), ("M", C.c_int32), ("n_active", C.c_int64),
+                ("n_total", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
+                ("seconds", C.c_double), ("n_history", C.c_int32)]
+
+
+EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
+           "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
+           "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
+           "wh_profile_iteration"]
+
+
+def lib_path():
+    return _LIB_PATH
+
+
+def lib():
+    """Load libwaveholtz.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libwaveholtz.so not built ({_LIB_PATH}); run "
+                           "paper_2504_03074_gb300.build.build() -- there is no CPU fallback")
+    L = C.CDLL(_LIB_PATH)
+    vp, st = C.c_void_p, C.c_int
+    L.wh_options_default.argtypes = [C.POINTER(Options)]
+    L.wh_create.argtypes = [C.POINTER(Options), C.POINTER(vp)]
+    L.wh_destroy.argtypes = [vp]
+    L.wh_destroy.restype = None
+    L.wh_last_error.argtypes = [vp]
+    L.wh_last_error.restype = C.c_char_p
+    L.wh_set_stream.argtypes = [vp, vp]
+    L.wh_add_grid.argtypes = [vp, C.POINTER(GridDesc), C.POINTER(C.c_int32)]
+    L.wh_set_interp.argtypes = [vp, C.POINTER(InterpDesc)]
+    L.wh_set_forcing.argtypes = [vp, C.c_int32, vp]
+    L.wh_prepare.argtypes = [vp, C.c_double, C.POINTER(TimeInfo)]
+    L.wh_iterate.argtypes = [vp, C.c_int32, vp, vp]
+    L.wh_iterate_host.argtypes = [vp, C.c_int32, vp, vp]
+    L.wh_solve.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, vp,
+                           C.POINTER(Stats), vp, C.c_int32]
+    L.wh_dot.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_double)]
+    L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
+    L.wh_profile_iteration.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_int32)]
+    L.wh_last_launch_count.argtypes = [vp]
+    L.wh_last_launch_count.restype = C.c_int64
+    for name in EXPORTS:
+        if name not in ("wh_destroy", "wh_last_error", "wh_last_launch_count"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+class Solver:
+    """One overset Helmholtz problem in libwaveholtz (one context)."""
+
+    def __init__(self, problem, periods=1, cfl=0.9, alpha_mode=0, precision=FP64, stream=None):
+        self.L = lib()
+        self.problem = problem
+        opt = Options()
+        self.L.wh_options_default(C.byref(opt))
+        opt.order, opt.periods, opt.cfl = problem.order, periods, cfl
+        opt.alpha_mode, opt.precision = alpha_mode, precision
+        h = C.c_void_p()
+        self._check(self.L.wh_create(C.byref(opt), C.byref(h)), None)
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+        for gi, g in enumerate(problem.grids):
+            mask = np.ascontiguousarray(g.mask, np.int8)
+            rx = None if g.rx is None else np.ascontiguousarray(g.rx, np.float64)
+            c2 = None if problem.c2 is None else np.ascontiguousarray(problem.c2[gi], np.float64)
+            d = GridDesc()
+            d.n[0], d.n[1] = g.n
+            d.kind = g.kind
+            for s in range(4):
+                d.bc[s] = g.bc[s]
+            d.orthogonal = int(g.orthogonal)
+            d.h[0], d.h[1] = g.h
+            d.mask, d.rx, d.c2 = _ptr(mask), _ptr(rx), _ptr(c2)
+            gid = C.c_int32()
+            self._check(self.L.wh_add_grid(self.h, C.byref(d), C.byref(gid)))
+            f = np.ascontiguousarray(problem.f[gi], np.float64)
+            self._check(self.L.wh_set_forcing(self.h, gid.value, _ptr(f)))
+        it = problem.interp
+        arrs = [np.ascontiguousarray(a, np.int32) for a in
+                (it.recv_grid, it.recv_i, it.recv_j, it.donor_grid, it.donor_i0, it.donor_j0)]
+        ws = [np.ascontiguousarray(a, np.float64) for a in (it.wx, it.wy)]
+        d = InterpDesc(it.n, *[_ptr(a) for a in arrs + ws])
+        self._check(self.L.wh_set_interp(self.h, C.byref(d)))
+        self.info = None
+
+    def _check(self, status, h=0):
+        if status != WH_OK:
+            msg = "" if h is None else self.L.wh_last_error(self.h).decode()
+            raise WHError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.wh_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_stream(self, stream):
+        """Issue work on a torch.cuda.Stream (or a raw cudaStream_t integer)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self.L.wh_set_stream(self.h, C.c_void_p(raw)))
+
+    def prepare(self, omega=None):
+        ti = TimeInfo()
+        self._check(self.L.wh_prepare(self.h, self.problem.omega if omega is None else omega,
+                                      C.byref(ti)))
+        self.info = ti
+        return ti
+
+    @property
+    def n_total(self):
+        return self.problem.n_total
+
+    def iterate(self, v_in, v_out, forcing=True):
+        """v_out = W_h(v_in, f or 0): device tensors (float64, n_total, contiguous)."""
+        self._check(self.L.wh_iterate(self.h, 1 if forcing else 0, _ptr(v_in), _ptr(v_out)))
+        return v_out
+
+    def iterate_host(self, v_in, forcing=True):
+        """Host numpy in, host numpy out (copies inside the call)."""
+        v = np.ascontiguousarray(v_in, np.float64)
+        out = np.empty_like(v)
+        self._check(self.L.wh_iterate_host(self.h, 1 if forcing else 0, _ptr(v), _ptr(out)))
+        return out
+
+    def iterate_host_buffers(self, v_in, v_out, forcing=True):
+        """Same with caller-owned (e.g. pinned torch CPU) buffers."""
+        self._check(self.L.wh_iterate_host(self.h, 1 if forcing else 0, _ptr(v_in), _ptr(v_out)))
+        return v_out
+
+    def solve(self, u, method=GMRES, tol=1e-8, max_it=500, restart=50, history_cap=2000):
+        """Solve in place on device tensor u (initial guess in, solution out)."""
+        st = Stats()
+        hist = np.zeros(max(history_cap, 1))
+        status = self.L.wh_solve(self.h, method, tol, max_it, restart, _ptr(u), C.byref(st),
+                                 _ptr(hist), history_cap)
+        if status not in (WH_OK, -6):
+            self._check(status)
+        st.history = hist[:st.n_history].copy()
+        st.status = STATUS.get(status, status)
+        return st
+
+    def dot(self, x, y):
+        out = C.c_double()
+        self._check(self.L.wh_dot(self.h, _ptr(x), _ptr(y), x.numel(), C.byref(out)))
+        return out.value
+
+    def profile_iteration(self, v_in, v_out, forcing=True):
+        """Per-kernel device times (ms) and launch counts of one un-graphed iteration:
+        dict(march=(ms, n), bc_gather=(ms, n), init=(ms, n), finish=(ms, n))."""
+        ms = (C.c_double * 4)()
+        cnt = (C.c_int32 * 4)()
+        self._check(self.L.wh_profile_iteration(self.h, 1 if forcing else 0, _ptr(v_in),
+                                                _ptr(v_out), ms, cnt))
+        names = ("march", "bc_gather", "init", "finish")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(names)}
+
+    def last_launch_count(self):
+        return int(self.L.wh_last_launch_count(self.h))
