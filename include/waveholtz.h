@@ -187,8 +187,9 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, doub
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
                    double *u, wh_stats *stats, double *history, int32_t history_cap);
 
-/* FP64 inner products <x, y> over n entries of two DEVICE vectors (the GMRES reduction:
- * warp-shuffle partial sums, then one deterministic pass).  *out is a host scalar. */
+/* FP64 inner product <x, y> over n entries of two DEVICE vectors (the GMRES reduction:
+ * warp-shuffle partial sums, then one deterministic pass).  *out is a host scalar.  n = 0
+ * gives 0 (x, y may then be NULL). */
 wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, double *out);
 
 /* Measurement aid: one WaveHoltz iteration like wh_iterate, but launched without the CUDA

@@ -796,8 +796,13 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *vin, doubl
 }
 
 wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, double *out) {
-  if (!ctx || !x || !y || !out || n < 0) return fail(ctx, WH_ERR_ARG, "bad wh_dot arguments");
+  if (!ctx || !out || n < 0 || (n > 0 && (!x || !y)))
+    return fail(ctx, WH_ERR_ARG, "bad wh_dot arguments");
   ctx->launches = 0;
+  if (n == 0) {
+    *out = 0.0;
+    return WH_OK;
+  }
   return multidot(ctx, x, 0, 1, y, n, out);
 }
 

@@ -132,8 +132,13 @@ class Solver:
         h = C.c_void_p()
         self._check(self.L.wh_create(C.byref(opt), C.byref(h)), None)
         self.h = h
-        if stream is not None:
-            self.set_stream(stream)
+        # The library works on one CUDA stream: a dedicated torch stream unless the caller
+        # names one.  Each call is ordered after the caller's current stream and the
+        # caller's stream is ordered after the call (no host synchronisation).
+        import torch
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.set_stream(self.stream)
         for gi, g in enumerate(problem.grids):
             mask = np.ascontiguousarray(g.mask, np.int8)
             rx = None if g.rx is None else np.ascontiguousarray(g.rx, np.float64)
@@ -171,9 +176,16 @@ class Solver:
     __del__ = close
 
     def set_stream(self, stream):
-        """Issue work on a torch.cuda.Stream (or a raw cudaStream_t integer)."""
+        """Issue work on a torch.cuda.Stream."""
         raw = getattr(stream, "cuda_stream", stream)
         self._check(self.L.wh_set_stream(self.h, C.c_void_p(raw)))
+        self.stream = stream
+
+    def _enter(self):
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def _leave(self):
+        self._torch.cuda.current_stream().wait_stream(self.stream)
 
     def prepare(self, omega=None):
         ti = TimeInfo()
@@ -188,18 +200,22 @@ class Solver:
 
     def iterate(self, v_in, v_out, forcing=True):
         """v_out = W_h(v_in, f or 0): device tensors (float64, n_total, contiguous)."""
+        self._enter()
         self._check(self.L.wh_iterate(self.h, 1 if forcing else 0, _ptr(v_in), _ptr(v_out)))
+        self._leave()
         return v_out
 
     def iterate_host(self, v_in, forcing=True):
         """Host numpy in, host numpy out (copies inside the call)."""
         v = np.ascontiguousarray(v_in, np.float64)
         out = np.empty_like(v)
+        self._enter()
         self._check(self.L.wh_iterate_host(self.h, 1 if forcing else 0, _ptr(v), _ptr(out)))
         return out
 
     def iterate_host_buffers(self, v_in, v_out, forcing=True):
         """Same with caller-owned (e.g. pinned torch CPU) buffers."""
+        self._enter()
         self._check(self.L.wh_iterate_host(self.h, 1 if forcing else 0, _ptr(v_in), _ptr(v_out)))
         return v_out
 
@@ -207,8 +223,10 @@ class Solver:
         """Solve in place on device tensor u (initial guess in, solution out)."""
         st = Stats()
         hist = np.zeros(max(history_cap, 1))
+        self._enter()
         status = self.L.wh_solve(self.h, method, tol, max_it, restart, _ptr(u), C.byref(st),
                                  _ptr(hist), history_cap)
+        self._leave()
         if status not in (WH_OK, -6):
             self._check(status)
         st.history = hist[:st.n_history].copy()
@@ -217,6 +235,7 @@ class Solver:
 
     def dot(self, x, y):
         out = C.c_double()
+        self._enter()
         self._check(self.L.wh_dot(self.h, _ptr(x), _ptr(y), x.numel(), C.byref(out)))
         return out.value
 
@@ -225,6 +244,7 @@ class Solver:
         dict(march=(ms, n), bc_gather=(ms, n), init=(ms, n), finish=(ms, n))."""
         ms = (C.c_double * 4)()
         cnt = (C.c_int32 * 4)()
+        self._enter()
         self._check(self.L.wh_profile_iteration(self.h, 1 if forcing else 0, _ptr(v_in),
                                                 _ptr(v_out), ms, cnt))
         names = ("march", "bc_gather", "init", "finish")
