@@ -200,6 +200,27 @@ wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, doubl
 wh_status wh_profile_iteration(wh_ctx *ctx, int32_t forcing, const double *v_in, double *v_out,
                                double *ms, int32_t *counts);
 
+/* Allocation-free inner products.  The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc -- code whose device memory belongs to another allocator with a
+ * fixed budget, and latency-critical loops where cudaMalloc/cudaFree (which synchronise
+ * the device) are not acceptable.
+ *   out[k] = <X_k, y>, k = 0..nv-1, X_k = X + k*ldx, each vector n FP64 values; X, y and
+ *   out (nv doubles) are DEVICE pointers owned by the caller; stream is a cudaStream_t
+ *   (NULL = legacy default stream).  Asynchronous on that stream; needs no context.
+ * It allocates nothing: the per-block partial sums live in a fixed file-scope device
+ * array of WH_NOALLOC_MAX_VECTORS x WH_NOALLOC_BLOCKS doubles (256 KiB) that every GPU
+ * loading the library holds until the process exits.  The first call on a device looks up
+ * that array's device address; make it before any stream capture on that device.  All
+ * calls on a device share the array (it keeps the last call's contents; each call writes
+ * every entry it reads), so calls that overlap on the GPU race and must be serialised.
+ * Returns WH_ERR_ARG, without touching the device, if nv is outside
+ * [1, WH_NOALLOC_MAX_VECTORS], n < 0, ldx < n (nv > 1) or a needed pointer is NULL;
+ * WH_ERR_CUDA if a CUDA call fails. */
+#define WH_NOALLOC_MAX_VECTORS 64
+#define WH_NOALLOC_BLOCKS 512
+wh_status wh_multidot_noalloc(const double *X, int64_t ldx, int32_t nv, const double *y,
+                              int64_t n, double *out, void *stream);
+
 /* Time setup of the last wh_prepare. */
 wh_status wh_get_time_info(const wh_ctx *ctx, wh_time_info *info);
 

@@ -66,7 +66,7 @@ class Stats(C.Structure):
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
-           "wh_profile_iteration"]
+           "wh_profile_iteration", "wh_multidot_noalloc"]
 
 
 def lib_path():
@@ -100,6 +100,7 @@ def lib():
                            C.POINTER(Stats), vp, C.c_int32]
     L.wh_dot.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_double)]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
+    L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_iteration.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double),
                                        C.POINTER(C.c_int32)]
     L.wh_last_launch_count.argtypes = [vp]
