@@ -67,6 +67,11 @@ enum { WH_CARTESIAN = 0, WH_CURVILINEAR = 1 };
 enum { WH_FP64 = 0, WH_FP32 = 1 };
 /* Solvers for wh_solve. */
 enum { WH_FPI = 0, WH_GMRES = 1 };
+/* How an iteration is launched.  WH_LAUNCH_GRAPH (default): a CUDA graph of per-phase
+ * kernels (2M + 1 launches).  WH_LAUNCH_PERSISTENT: one cooperative kernel per WaveHoltz
+ * iteration, bounded grid-wide barriers between the march and the ghost-rule +
+ * interpolation phase of every time step.  Both compute the same values. */
+enum { WH_LAUNCH_PERSISTENT = 0, WH_LAUNCH_GRAPH = 1 };
 
 typedef struct {
   int32_t order;      /* spatial order p: 2 or 4 (Sec. 3.2) */
@@ -74,6 +79,9 @@ typedef struct {
   double cfl;         /* fraction in (0, 1] of the explicit stability limit */
   int32_t alpha_mode; /* 0: alpha_d of Eq. alphad (default); 1: alpha = 1/2 */
   int32_t precision;  /* WH_FP64 (default) or WH_FP32 */
+  int32_t launch_mode;  /* WH_LAUNCH_GRAPH (default) or WH_LAUNCH_PERSISTENT */
+  uint64_t barrier_spin_limit;  /* polls before a grid barrier of the persistent kernel
+                                   gives up (WH_ERR_TIMEOUT); 0 = default (2^22, ~1 s) */
 } wh_options;
 
 /* One component grid (Sec. 3.1).  All pointers are host pointers, read during the call.
@@ -136,7 +144,7 @@ typedef struct {
   int32_t n_history;    /* entries written to history (<= history_cap) */
 } wh_stats;
 
-/* Fill *opt with order 4, Np = 1, cfl 0.9, alpha_d, FP64. */
+/* Fill *opt with order 4, Np = 1, cfl 0.9, alpha_d, FP64, graph launch. */
 wh_status wh_options_default(wh_options *opt);
 
 /* Create a context on the current CUDA device.  *out receives the handle. */
@@ -172,7 +180,9 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info);
 
 /* ONE WaveHoltz iteration v_out = W_h(v_in, f) (forcing = 1) or W_h(v_in, 0)
  * (forcing = 0): the hot path.  v_in, v_out: DEVICE compact vectors of n_total FP64
- * values (may not alias).  Asynchronous on the context stream. */
+ * values (may not alias).  Asynchronous on the context stream.  A persistent launch whose
+ * grid barrier timed out is reported as WH_ERR_TIMEOUT by a later call on the context
+ * (the next synchronising call at the latest); the context stays usable. */
 wh_status wh_iterate(wh_ctx *ctx, int32_t forcing, const double *v_in, double *v_out);
 
 /* Same as wh_iterate with HOST vectors: copies v_in to the device, iterates, copies the
@@ -192,13 +202,14 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
  * gives 0 (x, y may then be NULL). */
 wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, double *out);
 
-/* Measurement aid: one WaveHoltz iteration like wh_iterate, but launched without the CUDA
- * graph and with a CUDA event recorded on the context stream before every kernel, so
- * that each kernel's device time can be read.  ms[4] and counts[4] (host) receive the
- * summed milliseconds and launch counts of: [0] the march kernel, [1] the ghost-rule +
- * interpolation kernel, [2] the input kernel, [3] the output kernel.  Synchronises. */
-wh_status wh_profile_iteration(wh_ctx *ctx, int32_t forcing, const double *v_in, double *v_out,
-                               double *ms, int32_t *counts);
+/* Measurement aid: the device time of each kernel of the iteration, from graph-captured
+ * bursts of `reps` back-to-back launches (warm L2, no host gaps) on the prepared problem.
+ * ms[4] and counts[4] (host) receive the average milliseconds per launch and the launches
+ * per iteration of: [0] the march kernel, [1] the ghost-rule + interpolation kernel,
+ * [2] the input kernel, [3] the output kernel.  The bursts run on the context's internal
+ * working buffers and leave them unspecified (every wh_iterate rebuilds them from its
+ * input).  Synchronises. */
+wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts);
 
 /* Allocation-free inner products.  The paper has no counterpart: this serves callers that
  * cannot call cudaMalloc -- code whose device memory belongs to another allocator with a

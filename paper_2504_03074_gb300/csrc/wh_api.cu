@@ -85,6 +85,17 @@ struct wh_ctx {
   double *d_partial = nullptr, *d_red = nullptr;
   int partial_blocks = 0, red_cap = 0;
   int64_t launches = 0;
+  int march_blocks = 0;
+  // persistent path
+  int iter_blocks = 0;
+  double *d_steps = nullptr;  // [3][M+1]: fc, cos, wf
+  int64_t steps_cap = 0;
+  GridBarrier *d_bar = nullptr;
+  int *h_err = nullptr;       // pinned copy of the barrier error flag
+  bool persistent = true;
+  unsigned long long opt_spin_limit = 1ull << 22;
+  cudaEvent_t err_ev = nullptr;
+  bool err_pending = false;
 };
 
 namespace {
@@ -133,6 +144,9 @@ void free_device(wh_ctx *ctx) {
   ctx->d_work = nullptr;
   ctx->d_partial = ctx->d_red = nullptr;
   ctx->red_cap = 0;
+  ctx->d_steps = nullptr;
+  ctx->steps_cap = 0;
+  ctx->d_bar = nullptr;
 }
 
 inline int64_t ext_index(const DevGrid &G, int i, int j) {
@@ -187,8 +201,18 @@ wh_status build_layout(wh_ctx *ctx) {
       k5 += 5 * G.ext;
     }
     for (size_t q = 0; q < H.mask.size(); ++q) nact += H.mask[q] != WH_UNUSED;
-    for (int j0 = 0; j0 < G.n1; j0 += kTileY)
-      for (int i0 = 0; i0 < G.n0; i0 += kTileX) ctx->htiles.push_back(Tile{(int32_t)g, i0, j0, 0});
+    // march tiles: only those holding a discretization or interpolation point
+    const int TY = kTileY * kPY;
+    for (int j0 = 0; j0 < G.n1; j0 += TY)
+      for (int i0 = 0; i0 < G.n0; i0 += kTileX) {
+        bool need = false;
+        for (int j = j0; j < std::min(j0 + TY, G.n1) && !need; ++j)
+          for (int i = i0; i < std::min(i0 + kTileX, G.n0) && !need; ++i) {
+            const int8_t m = H.mask[(size_t)j * G.n0 + i];
+            need = m == WH_DISC || m == WH_INTERP;
+          }
+        if (need) ctx->htiles.push_back(Tile{(int32_t)g, i0, j0, 0});
+      }
     ctx->hgrids.push_back(G);
   }
   ctx->total = off;
@@ -355,24 +379,20 @@ wh_status build_layout(wh_ctx *ctx) {
   CK(cudaMemcpy(ctx->d_ridx, ridx.data(), ridx.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_grids, ctx->hgrids.data(), ctx->hgrids.size() * sizeof(DevGrid),
                 cudaMemcpyHostToDevice));
+  {
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ctx->march_blocks = sms * march_blocks_per_sm(is_fp32(ctx), order);
+    ctx->iter_blocks = sms * iteration_blocks_per_sm(is_fp32(ctx), order);
+    CK(cudaGetLastError());
+  }
+  if ((st = dalloc(ctx, &ctx->d_bar, 1))) return st;
   ctx->dirty = false;
   return WH_OK;
 }
 
-// Optional per-launch event recording (wh_profile_iteration): an event is recorded on the
-// stream before every launch, and the kind of the launch is remembered.
-struct Prof {
-  std::vector<cudaEvent_t> *ev = nullptr;
-  std::vector<int> *kind = nullptr;
-  size_t next = 0;
-  void mark(cudaStream_t s, int k) {
-    if (!ev) return;
-    cudaEventRecord((*ev)[next++], s);
-    kind->push_back(k);
-  }
-};
-
-wh_status launch_steps(wh_ctx *ctx, int forcing, Prof *prof = nullptr) {
+wh_status launch_steps(wh_ctx *ctx, int forcing) {
   // the body of one iteration after init: t = 0 ghost rules + interpolation, then M steps
   const int order = ctx->opt.order;
   const bool f32 = is_fp32(ctx);
@@ -384,29 +404,27 @@ wh_status launch_steps(wh_ctx *ctx, int forcing, Prof *prof = nullptr) {
   const int g_blocks = (int)((ctx->nrecv * lanes + 255) / 256);
   const int bg_blocks = bc_blocks + g_blocks;
   const int ntiles = (int)ctx->htiles.size();
+  const int nblocks = std::min(ntiles, ctx->march_blocks);
   void *Wa = ctx->d_Wa, *Wb = ctx->d_Wb;
   const int M = ctx->ti.M;
-  Prof none;
-  Prof &P = prof ? *prof : none;
   auto bcg = [&](void *W, int n) {
     if (bg_blocks == 0) return;
-    P.mark(s, 1);
     launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx, ctx->d_dw,
                      ctx->d_ridx, (int)ctx->nrecv, W, ctx->d_F,
-                     fs * std::cos(ctx->ti.omega_e * n * ctx->ti.dt), ctx->d_V, ctx->wf[n]);
+                     fs * std::cos(ctx->ti.omega_e * n * ctx->ti.dt));
   };
   bcg(Wa, 0);
   // first step: W^1 = (sum w W^0)/2 - dt^2/2 f
-  P.mark(s, 0);
-  launch_march(f32, order, true, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask, Wa, Wb,
-               ctx->d_F, ctx->d_Wt, ctx->d_V, fs * 0.5 * ctx->ti.dt * ctx->ti.dt, ctx->wf[1]);
+  launch_march(f32, order, true, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask,
+               Wa, Wb, ctx->d_F, ctx->d_Wt, ctx->d_V, fs * 0.5 * ctx->ti.dt * ctx->ti.dt,
+               ctx->wf[1], ctx->wf[0]);
   bcg(Wb, 1);
   for (int n = 1; n < M; ++n) {
     void *cur = (n & 1) ? Wb : Wa;
     void *oth = (n & 1) ? Wa : Wb;
-    P.mark(s, 0);
-    launch_march(f32, order, false, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask, cur, oth,
-                 ctx->d_F, ctx->d_Wt, ctx->d_V, fs * ctx->fc[n], ctx->wf[n + 1]);
+    launch_march(f32, order, false, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask,
+                 cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, fs * ctx->fc[n], ctx->wf[n + 1],
+                 ctx->wf[n]);
     bcg(oth, n + 1);
   }
   return WH_OK;
@@ -429,8 +447,65 @@ wh_status build_graph(wh_ctx *ctx, int forcing) {
   return WH_OK;
 }
 
+// A timed-out grid barrier of an earlier persistent launch is reported by the first
+// call that finds its flag copied back.
+wh_status check_timeout(wh_ctx *ctx, bool wait) {
+  if (!ctx->err_pending) return WH_OK;
+  if (wait) {
+    CK(cudaEventSynchronize(ctx->err_ev));
+  } else if (cudaEventQuery(ctx->err_ev) != cudaSuccess) {
+    return WH_OK;
+  }
+  ctx->err_pending = false;
+  if (*ctx->h_err)
+    return fail(ctx, WH_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
+  return WH_OK;
+}
+
+wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
+  wh_status st = check_timeout(ctx, false);
+  if (st) return st;
+  const int M = ctx->ti.M;
+  IterArgs A{};
+  A.grids = ctx->d_grids;
+  A.ngrids = (int)ctx->hgrids.size();
+  A.ntiles = (int)ctx->htiles.size();
+  A.tiles = ctx->d_tiles;
+  A.mask = ctx->d_mask;
+  A.Wa = ctx->d_Wa;
+  A.Wb = ctx->d_Wb;
+  A.F = ctx->d_F;
+  A.Wt = ctx->d_Wt;
+  A.V = ctx->d_V;
+  A.bc = ctx->d_bc;
+  A.nbc = (int64_t)ctx->hbc.size();
+  A.didx = ctx->d_didx;
+  A.dw = ctx->d_dw;
+  A.ridx = ctx->d_ridx;
+  A.nrecv = ctx->nrecv;
+  A.fc = ctx->d_steps;
+  A.cosn = ctx->d_steps + (M + 1);
+  A.wf = ctx->d_steps + 2 * (M + 1);
+  A.fs = forcing ? 1.0 : 0.0;
+  A.dt2 = ctx->ti.dt * ctx->ti.dt;
+  A.M = M;
+  A.total = ctx->total;
+  A.ncompact = ctx->ncompact;
+  A.spin_limit = ctx->opt_spin_limit;
+  CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), ctx->stream));
+  CK(launch_iteration(is_fp32(ctx), ctx->opt.order, ctx->iter_blocks, ctx->stream, A, vin, vout,
+                      ctx->d_bar));
+  CK(cudaMemcpyAsync(ctx->h_err, &ctx->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaEventRecord(ctx->err_ev, ctx->stream));
+  ctx->err_pending = true;
+  ctx->launches += 1;
+  return WH_OK;
+}
+
 wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
   forcing = forcing ? 1 : 0;
+  if (ctx->persistent) return iterate_persistent(ctx, forcing, vin, vout);
   if (!ctx->gexec[forcing]) {
     wh_status st = build_graph(ctx, forcing);
     if (st) return st;
@@ -443,7 +518,8 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   CK(cudaGetLastError());
   CK(cudaGraphLaunch(ctx->gexec[forcing], ctx->stream));
   const int64_t nc = (ctx->ncompact + blk - 1) / blk;
-  launch_finish((unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V, vout,
+  launch_finish(is_fp32(ctx), (unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V,
+                (ctx->ti.M % 2 == 0) ? ctx->d_Wa : ctx->d_Wb, ctx->wf[ctx->ti.M], vout,
                 ctx->ncompact);
   CK(cudaGetLastError());
   ctx->launches += 2 + 2 * (int64_t)ctx->ti.M + 1;
@@ -482,6 +558,7 @@ wh_status multidot(wh_ctx *ctx, const double *X, int64_t ldx, int nv, const doub
     CK(cudaMemcpyAsync(out_host, ctx->d_red, nv * sizeof(double), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return check_timeout(ctx, true);
   }
   return WH_OK;
 }
@@ -512,6 +589,8 @@ wh_status wh_options_default(wh_options *opt) {
   opt->cfl = 0.9;
   opt->alpha_mode = 0;
   opt->precision = WH_FP64;
+  opt->launch_mode = WH_LAUNCH_GRAPH;
+  opt->barrier_spin_limit = 0;
   return WH_OK;
 }
 
@@ -523,11 +602,14 @@ wh_status wh_create(const wh_options *opt, wh_ctx **out) {
   if (opt) o = *opt;
   if ((o.order != 2 && o.order != 4) || o.periods < 1 || !(o.cfl > 0.0 && o.cfl <= 1.0) ||
       (o.alpha_mode != 0 && o.alpha_mode != 1) ||
-      (o.precision != WH_FP64 && o.precision != WH_FP32))
+      (o.precision != WH_FP64 && o.precision != WH_FP32) ||
+      (o.launch_mode != WH_LAUNCH_PERSISTENT && o.launch_mode != WH_LAUNCH_GRAPH))
     return WH_ERR_ARG;
   wh_ctx *ctx = new (std::nothrow) wh_ctx();
   if (!ctx) return WH_ERR_NOMEM;
   ctx->opt = o;
+  ctx->persistent = o.launch_mode == WH_LAUNCH_PERSISTENT;
+  if (o.barrier_spin_limit) ctx->opt_spin_limit = o.barrier_spin_limit;
   // the context's own stream is created on first device use, so that grid description
   // and validation work without a GPU
   *out = ctx;
@@ -538,6 +620,8 @@ void wh_destroy(wh_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   free_device(ctx);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  if (ctx->err_ev) cudaEventDestroy(ctx->err_ev);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
 }
@@ -731,6 +815,28 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
     const double sig = (n == 0 || n == M) ? 0.5 : 1.0;
     ctx->wf[n] = (2.0 / M) * sig * (cn - ti.alpha / 2.0);
   }
+  // the same tables on the device for the persistent kernel: fc, cos, wf
+  if (ctx->steps_cap < 3 * (int64_t)(M + 1)) {
+    if ((st = dalloc(ctx, &ctx->d_steps, 3 * (size_t)(M + 1)))) return st;
+    ctx->steps_cap = 3 * (int64_t)(M + 1);
+  }
+  {
+    std::vector<double> tab(3 * (size_t)(M + 1));
+    for (int n = 0; n <= M; ++n) {
+      tab[n] = ctx->fc[n];
+      tab[(M + 1) + n] = std::cos(ti.omega_e * n * dt);
+      tab[2 * (M + 1) + n] = ctx->wf[n];
+    }
+    CK(cudaMemcpy(ctx->d_steps, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!ctx->h_err) {
+    CK(cudaMallocHost(&ctx->h_err, sizeof(int)));
+    *ctx->h_err = 0;
+  }
+  if (!ctx->err_ev) CK(cudaEventCreateWithFlags(&ctx->err_ev, cudaEventDisableTiming));
+  ctx->err_pending = false;
+  if (ctx->persistent && ctx->iter_blocks < 1)
+    return fail(ctx, WH_ERR_CUDA, "the persistent kernel cannot be resident on this device");
   // stencil weights
   const double dt2 = dt * dt;
   for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
@@ -792,7 +898,7 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *vin, doubl
   CK(cudaMemcpyAsync(vout, ctx->d_work + ctx->ncompact, bytes, cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  return WH_OK;
+  return check_timeout(ctx, true);
 }
 
 wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, double *out) {
@@ -945,46 +1051,72 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
   }
 }
 
-wh_status wh_profile_iteration(wh_ctx *ctx, int32_t forcing, const double *vin, double *vout,
-                               double *ms, int32_t *counts) {
-  if (!ctx || !vin || !vout || !ms || !counts) return fail(ctx, WH_ERR_ARG, "null argument");
+wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts) {
+  if (!ctx || !ms || !counts || reps < 1 || reps > 10000)
+    return fail(ctx, WH_ERR_ARG, "bad wh_profile_kernels arguments");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
-  const size_t need = 2 * (size_t)ctx->ti.M + 8;
-  static thread_local std::vector<cudaEvent_t> ev;
-  while (ev.size() < need) {
-    cudaEvent_t e;
-    CK(cudaEventCreate(&e));
-    ev.push_back(e);
-  }
-  std::vector<int> kind;
-  Prof P;
-  P.ev = &ev;
-  P.kind = &kind;
+  const int order = ctx->opt.order;
+  const bool f32 = is_fp32(ctx);
+  cudaStream_t s = ctx->stream;
+  const int nbc = (int)ctx->hbc.size();
+  const int bc_blocks = (nbc + 255) / 256;
+  const int lanes = order == 4 ? 8 : 4;
+  const int bg_blocks = bc_blocks + (int)((ctx->nrecv * lanes + 255) / 256);
+  const int ntiles = (int)ctx->htiles.size();
+  const int nblocks = std::min(ntiles, ctx->march_blocks);
   const int blk = 256;
   const int ng = (int)ctx->hgrids.size();
-  cudaStream_t s = ctx->stream;
-  P.mark(s, 2);
-  launch_init(is_fp32(ctx), (unsigned)((ctx->total + blk - 1) / blk), s, ctx->d_grids, ng,
-              ctx->d_mask, vin, ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
-  wh_status st = launch_steps(ctx, forcing ? 1 : 0, &P);
-  if (st) return st;
-  P.mark(s, 3);
-  launch_finish((unsigned)((ctx->ncompact + blk - 1) / blk), s, ctx->d_grids, ng, ctx->d_mask,
-                ctx->d_V, vout, ctx->ncompact);
-  CK(cudaEventRecord(ev[P.next], s));
-  CK(cudaGetLastError());
-  CK(cudaEventSynchronize(ev[P.next]));
-  for (int k = 0; k < 4; ++k) {
-    ms[k] = 0.0;
-    counts[k] = 0;
-  }
-  for (size_t q = 0; q < kind.size(); ++q) {
+  // four bursts of `reps` back-to-back launches, each captured in a graph
+  auto burst = [&](int kind) {
+    for (int r = 0; r < reps; ++r) {
+      void *cur = (r & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (r & 1) ? ctx->d_Wa : ctx->d_Wb;
+      if (kind == 0)
+        launch_march(f32, order, false, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles,
+                     ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->fc[1],
+                     ctx->wf[2], ctx->wf[1]);
+      else if (kind == 1 && bg_blocks)
+        launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx,
+                         ctx->d_dw, ctx->d_ridx, (int)ctx->nrecv, oth, ctx->d_F, 1.0);
+      else if (kind == 2)
+        launch_init(f32, (unsigned)((ctx->total + blk - 1) / blk), s, ctx->d_grids, ng,
+                    ctx->d_mask, ctx->d_work, ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
+      else if (kind == 3)
+        launch_finish(f32, (unsigned)((ctx->ncompact + blk - 1) / blk), s, ctx->d_grids, ng,
+                      ctx->d_mask, ctx->d_V, ctx->d_Wa, ctx->wf[1], ctx->d_work + ctx->ncompact,
+                      ctx->ncompact);
+    }
+  };
+  wh_status st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, 3 * (size_t)ctx->ncompact))) return st;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int per_iter[4] = {ctx->ti.M, bg_blocks ? ctx->ti.M + 1 : 0, 1, 1};
+  for (int kind = 0; kind < 4; ++kind) {
+    ms[kind] = 0.0;
+    counts[kind] = per_iter[kind];
+    if (per_iter[kind] == 0) continue;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    burst(kind);
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, WH_ERR_CUDA, "profile graph: %s", cudaGetErrorString(e));
+    CK(cudaGraphLaunch(ge, s));  // warm-up
+    CK(cudaEventRecord(e0, s));
+    CK(cudaGraphLaunch(ge, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
     float t = 0.f;
-    CK(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
-    ms[kind[q]] += t;
-    counts[kind[q]] += 1;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    ms[kind] = (double)t / reps;
+    cudaGraphExecDestroy(ge);
   }
-  ctx->launches = (int64_t)kind.size();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->launches = 8 * (int64_t)reps;
   return WH_OK;
 }
 

@@ -6,8 +6,9 @@
 namespace wh {
 
 constexpr int kMaxOrder = 4;
-constexpr int kTileX = 32;  // march tile: 32 x 8 points, one point per thread
+constexpr int kTileX = 32;  // march block: 32 x 8 threads
 constexpr int kTileY = 8;
+constexpr int kPY = 4;      // points per thread along axis 1: a 32 x 32 tile per block
 
 // Stencil storage of a grid in the march kernels.
 enum StencilKind : int32_t {
@@ -50,25 +51,67 @@ struct BcItem {
   double inv;        // 1 / (11 A2 - 3 B1)
 };
 
-// One tile of the march: a 32 x 8 block of one grid.
+// One tile of the march: a 32 x (8 kPY) block of points of one grid.
 struct Tile {
   int32_t grid, i0, j0, pad_;
 };
 
+// Grid-wide barrier state of the persistent kernel (zeroed before every launch); each
+// word on its own 128-byte line.
+struct GridBarrier {
+  unsigned count[32];
+  unsigned gen[32];
+  int err[32];
+  int tile_ctr[2][32];  // dynamic tile tickets of the march phase, one slot per step parity
+};
+
+// Everything the persistent iteration kernel reads (device pointers, per-step tables).
+struct IterArgs {
+  const DevGrid *grids;
+  int ngrids;
+  int ntiles;
+  const Tile *tiles;
+  const int8_t *mask;
+  void *Wa, *Wb;
+  const void *F, *Wt;
+  double *V;
+  const BcItem *bc;
+  int64_t nbc;
+  const int32_t *didx;
+  const double *dw;
+  const int64_t *ridx;
+  int64_t nrecv;
+  const double *fc;    // dt^2 cos(omega_e t^n), n = 0..M
+  const double *cosn;  // cos(omega_e t^n)
+  const double *wf;    // filter weights, n = 0..M
+  double fs;           // 1 with forcing, 0 without
+  double dt2;
+  int M;
+  int pad_;
+  int64_t total, ncompact;
+  unsigned long long spin_limit;
+};
+
 // Host launchers (wh_kernels.cu).  T is double unless fp32 is set; pointers typed void
 // carry T arrays.
-void launch_march(bool fp32, int order, bool first, int ntiles, cudaStream_t s,
+void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
-                  void *Wout, const void *F, const void *Wt, double *V, double fc, double wf);
+                  void *Wout, const void *F, const void *Wt, double *V, double fc,
+                  double wf_new, double wf_cur);
+int march_blocks_per_sm(bool fp32, int order);
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
-                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos,
-                      double *V, double wf);
+                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos);
+int iteration_blocks_per_sm(bool fp32, int order);
+cudaError_t launch_iteration(bool fp32, int order, int nblocks, cudaStream_t s,
+                             const IterArgs &A, const double *v_in, double *v_out,
+                             GridBarrier *bar);
 void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
                  const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
                  double w0);
-void launch_finish(unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
-                   const int8_t *mask, const double *V, double *vout, int64_t ncompact);
+void launch_finish(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
+                   const int8_t *mask, const double *V, const void *WM, double wf_last,
+                   double *vout, int64_t ncompact);
 void launch_coef(int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids, int gidx,
                  const int8_t *mask, const double *rx, const double *c2, double *coef,
                  unsigned long long *smax);

@@ -28,132 +28,135 @@ __device__ __forceinline__ int wrap(int i, int n, int per) {
   return i;
 }
 
-// Arithmetic of the march.  T is the state type (double or float); the accumulator V is
-// always double.
+// Row offset of row jj in a grid (wrapping on a periodic axis, clamped to the extended
+// rows otherwise: clamped rows only feed points that are not stored).
+__device__ __forceinline__ int64_t row_off(const DevGrid &G, int jj) {
+  jj = wrap(jj, G.n1, G.per1);
+  jj = jj < -G.g1 ? -G.g1 : (jj >= G.n1 + G.g1 ? G.n1 + G.g1 - 1 : jj);
+  return G.base + (int64_t)(jj + G.g1) * G.pitch + G.g0;
+}
+
+// ---------------------------------------------------------------------------------
+// Per-point arithmetic shared by the graph path and the persistent kernel.
+// ---------------------------------------------------------------------------------
+
+// One time step at point (i, j) of grid G (Eq. WaveSchemeexplicit), fused with the filter:
+//   FIRST: W^1 = (sum_k w_k W^0_k)/2 - fc f            (fc = dt^2/2, or 0 without forcing)
+//   else : W^{n+1} = sum_k w_k W^n_k - W^{n-1} - fc f   (fc = dt^2 cos(omega_e t^n))
+// W^{n+1} is written over W^{n-1} (Wout).  Discretization points: V += wf_new W^{n+1}.
+// Interpolation points: V += wf_cur W^n (their level-n values are final when the march
+// runs).  The weights fold dt^2, c(x)^2 and the leapfrog "2 W^n" into one stencil, so an
+// order-4 point costs 11 FP64 FMAs.
+// The state arrays (Wn, Wout, V) are written inside the persistent kernel, so they are
+// never declared __restrict__: their loads must not take the non-coherent read-only path.
 template <typename T, int ORDER, bool FIRST>
-__global__ void __launch_bounds__(kTileX *kTileY)
-    march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles,
-                 const int8_t *__restrict__ mask, const T *__restrict__ Wn, T *Wnm1_out,
-                 const T *__restrict__ F, const T *__restrict__ Wt, double *__restrict__ V,
-                 T fc, double wf) {
-  // FIRST: W^1 = (sum_k w_k W^0_k)/2 - fc f  (fc = dt^2/2 * forcing), written to Wnm1_out.
-  // else : W^{n+1} = sum_k w_k W^n_k - W^{n-1} - fc f  (fc = dt^2 cos(omega_e t^n)),
-  //        W^{n-1} read from and W^{n+1} written to Wnm1_out.
-  const Tile t = tiles[blockIdx.x];
-  const DevGrid &G = grids[t.grid];
-  const int i = t.i0 + (int)threadIdx.x;
-  const int j = t.j0 + (int)threadIdx.y;
-  if (i >= G.n0 || j >= G.n1) return;
-  const int64_t row = G.base + (int64_t)(j + G.g1) * G.pitch + G.g0;
-  const int64_t p = row + i;
-  if (mask[p] != 1) return;  // WH_DISC only; Dirichlet values stay 0
+__device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
+                                            const int8_t *__restrict__ mask,
+                                            const T *Wn, T *Wout,
+                                            const T *__restrict__ F, const T *__restrict__ Wt,
+                                            double *V, T fc, double wf_new, double wf_cur) {
   constexpr int R = ORDER / 2;
-  // neighbour columns / rows (wrapping on periodic axes)
-  int64_t cols[2 * R + 1];
-  int64_t rows[2 * R + 1];
-#pragma unroll
-  for (int k = -R; k <= R; ++k) {
-    cols[k + R] = row + wrap(i + k, G.n0, G.per0);
-    rows[k + R] = (int64_t)(wrap(j + k, G.n1, G.per1) + G.g1) * G.pitch + G.base + G.g0 + i;
+  const int64_t row = row_off(G, j);
+  const int64_t p = row + i;
+  const int8_t mk = mask[p];
+  if (mk == 2) {
+    V[p] = fma(wf_cur, (double)Wn[p], V[p]);
+    return;
   }
-  T acc;
+  if (mk != 1) return;
+  T a;
   if (G.stencil == kConstCross) {
-    const T wc = (T)G.cw[0];
-    const T Wc = Wn[p];
-    if (FIRST) {
-      acc = wc * Wc;
-    } else {
-      acc = wc * Wc - Wnm1_out[p];
-    }
-    acc += (T)G.cw[1] * (Wn[cols[R - 1]] + Wn[cols[R + 1]]);
-    acc += (T)G.cw[3] * (Wn[rows[R - 1]] + Wn[rows[R + 1]]);
+    const T c0 = (T)G.cw[0], x1 = (T)G.cw[1], y1 = (T)G.cw[3];
+    const int64_t up = row_off(G, j + 1) + i, dn = row_off(G, j - 1) + i;
+    const int im = wrap(i - 1, G.n0, G.per0), ip = wrap(i + 1, G.n0, G.per0);
+    a = FIRST ? c0 * Wn[p] : fma(c0, Wn[p], -Wout[p]);
+    a = fma(x1, Wn[row + im], a);
+    a = fma(x1, Wn[row + ip], a);
+    a = fma(y1, Wn[dn], a);
+    a = fma(y1, Wn[up], a);
     if (ORDER == 4) {
-      acc += (T)G.cw[2] * (Wn[cols[0]] + Wn[cols[4]]);
-      acc += (T)G.cw[4] * (Wn[rows[0]] + Wn[rows[4]]);
+      const T x2 = (T)G.cw[2], y2 = (T)G.cw[4];
+      const int64_t up2 = row_off(G, j + 2) + i, dn2 = row_off(G, j - 2) + i;
+      const int im2 = wrap(i - 2, G.n0, G.per0), ip2 = wrap(i + 2, G.n0, G.per0);
+      a = fma(x2, Wn[row + im2], a);
+      a = fma(x2, Wn[row + ip2], a);
+      a = fma(y2, Wn[dn2], a);
+      a = fma(y2, Wn[up2], a);
     }
   } else if (G.stencil == kPointCross) {
-    // plane order: centre, axis 0 offsets -R..-1, 1..R, axis 1 offsets -R..-1, 1..R
-    const int64_t q = G.wbase + (p - G.base);
-    const int64_t E = G.ext;
-    acc = Wt[q] * Wn[p];
-    if (!FIRST) acc -= Wnm1_out[p];
+    // planes: centre, axis-0 offsets -R..-1, 1..R, axis-1 offsets -R..-1, 1..R
+    const int64_t q = G.wbase + (p - G.base), E = G.ext;
+    a = FIRST ? Wt[q] * Wn[p] : fma(Wt[q], Wn[p], -Wout[p]);
     int pl = 1;
 #pragma unroll
     for (int k = -R; k <= R; ++k) {
       if (k == 0) continue;
-      acc += Wt[q + pl * E] * Wn[cols[k + R]];
+      a = fma(Wt[q + pl * E], Wn[row + wrap(i + k, G.n0, G.per0)], a);
       ++pl;
     }
 #pragma unroll
     for (int k = -R; k <= R; ++k) {
       if (k == 0) continue;
-      acc += Wt[q + pl * E] * Wn[rows[k + R]];
+      a = fma(Wt[q + pl * E], Wn[row_off(G, j + k) + i], a);
       ++pl;
     }
   } else {
     // box: plane (b + R) * (2R + 1) + (a + R) holds the weight of offset (a, b)
-    const int64_t q = G.wbase + (p - G.base);
-    const int64_t E = G.ext;
-    acc = FIRST ? (T)0 : -Wnm1_out[p];
+    const int64_t q = G.wbase + (p - G.base), E = G.ext;
+    a = FIRST ? (T)0 : -Wout[p];
 #pragma unroll
     for (int b = -R; b <= R; ++b) {
-      const int jj = wrap(j + b, G.n1, G.per1);
-      const int64_t rb = G.base + (int64_t)(jj + G.g1) * G.pitch + G.g0;
+      const int64_t rb = row_off(G, j + b);
 #pragma unroll
-      for (int a = -R; a <= R; ++a) {
-        const int ii = wrap(i + a, G.n0, G.per0);
-        acc += Wt[q + ((b + R) * (2 * R + 1) + (a + R)) * E] * Wn[rb + ii];
-      }
+      for (int aa = -R; aa <= R; ++aa)
+        a = fma(Wt[q + ((b + R) * (2 * R + 1) + (aa + R)) * E], Wn[rb + wrap(i + aa, G.n0, G.per0)],
+                a);
     }
   }
-  if (FIRST) acc *= (T)0.5;
-  acc -= fc * F[p];
-  Wnm1_out[p] = acc;
-  V[p] += wf * (double)acc;
+  if (FIRST) a *= (T)0.5;
+  a = fma(-fc, F[p], a);
+  Wout[p] = a;
+  V[p] = fma(wf_new, (double)a, V[p]);
 }
 
-// Ghost rules and overset interpolation for one time level W (both at time t).
-//   BC items [0, nbc): one thread each.
-//   receivers: LANES lanes per receiver (warp-cooperative gather), donors split
-//   across the lanes, partial sums combined with xor shuffles.
-template <typename T, int ORDER>
-__global__ void __launch_bounds__(256)
-    bc_gather_kernel(const BcItem *__restrict__ bc, int nbc, int bc_blocks,
-                     const int32_t *__restrict__ didx, const double *__restrict__ dw,
-                     const int64_t *__restrict__ ridx, int nrecv, T *W,
-                     const T *__restrict__ F, double fcos, double *__restrict__ V,
-                     double wf) {
-  if ((int)blockIdx.x < bc_blocks) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nbc) return;
-    const BcItem it = bc[k];
-    const double U0 = (double)W[it.u[0]], U1 = (double)W[it.u[1]];
-    if (it.type == 0) {  // Neumann, order 2: D0 W = 0
-      W[it.g[0]] = (T)U1;
-      return;
-    }
-    const double U2 = (double)W[it.u[2]], U3 = (double)W[it.u[3]];
-    const double E = -10.0 * U0 + 10.0 * U1 - 5.0 * U2 + U3;  // G2 = 5 G1 + E (D+^5 = 0)
-    double G1;
-    if (it.type == 1) {  // Neumann, order 4: 8(U1 - G1) - (U2 - G2) = 0
-      G1 = (18.0 * U1 - 10.0 * U0 - 6.0 * U2 + U3) * (1.0 / 3.0);
-    } else {  // Dirichlet, order 4: c^2 (a_nn D_nn + b_n D_n) W = f cos
-      const double Fb = (double)F[it.u[0]] * fcos;
-      G1 = (Fb - it.A2 * (-30.0 * U0 + 16.0 * U1 - U2) - it.B1 * (8.0 * U1 - U2) +
-            (it.A2 - it.B1) * E) * it.inv;
-    }
-    W[it.g[0]] = (T)G1;
-    W[it.g[1]] = (T)(5.0 * G1 + E);
+// Ghost rule of one boundary point (ghost-point rules for g = 0; see the library notes):
+//   type 0, Neumann order 2: D0 W = 0 -> G1 = U1;
+//   type 1, Neumann order 4: 8(U1 - G1) - (U2 - G2) = 0 and D+^5 G2 = 0;
+//   type 2, Dirichlet order 4: c^2 (a_nn D_nn + b_n D_n) W_b = f_b cos(omega_e t) and
+//   D+^5 G2 = 0, solved as G1 = (F - A2(-30U0 + 16U1 - U2) - B1(8U1 - U2) + (A2 - B1) E) /
+//   (11 A2 - 3 B1), G2 = 5 G1 + E with E = -10U0 + 10U1 - 5U2 + U3.
+template <typename T>
+__device__ __forceinline__ void bc_item(const BcItem &it, T *W, const T *__restrict__ F,
+                                        double fcos) {
+  const double U0 = (double)W[it.u[0]], U1 = (double)W[it.u[1]];
+  if (it.type == 0) {
+    W[it.g[0]] = (T)U1;
     return;
   }
+  const double U2 = (double)W[it.u[2]], U3 = (double)W[it.u[3]];
+  const double E = -10.0 * U0 + 10.0 * U1 - 5.0 * U2 + U3;
+  double G1;
+  if (it.type == 1) {
+    G1 = (18.0 * U1 - 10.0 * U0 - 6.0 * U2 + U3) * (1.0 / 3.0);
+  } else {
+    const double Fb = (double)F[it.u[0]] * fcos;
+    G1 = (Fb - it.A2 * (-30.0 * U0 + 16.0 * U1 - U2) - it.B1 * (8.0 * U1 - U2) +
+          (it.A2 - it.B1) * E) * it.inv;
+  }
+  W[it.g[0]] = (T)G1;
+  W[it.g[1]] = (T)(5.0 * G1 + E);
+}
+
+// Warp-cooperative gather of receiver r: LANES lanes split its (p+1)^2 donors and combine
+// their partial sums with xor shuffles.  Every lane of the warp must call this (live may be
+// false); lane 0 of the group stores the value.
+template <typename T, int ORDER>
+__device__ __forceinline__ void gather_group(int r, int lane, bool live,
+                                             const int32_t *__restrict__ didx,
+                                             const double *__restrict__ dw,
+                                             const int64_t *__restrict__ ridx, T *W) {
   constexpr int ND = (ORDER + 1) * (ORDER + 1);
   constexpr int LANES = ORDER == 4 ? 8 : 4;
-  const int gtid = (blockIdx.x - bc_blocks) * blockDim.x + threadIdx.x;
-  const int r = gtid / LANES;
-  const int lane = threadIdx.x % LANES;
-  // all lanes of a receiver group take part in the shuffles, so compute even when the
-  // receiver index is past the end and only skip the final store
-  const bool live = r < nrecv;
   double s = 0.0;
   if (live) {
     const int32_t *di = didx + (int64_t)r * ND;
@@ -163,21 +166,59 @@ __global__ void __launch_bounds__(256)
   }
 #pragma unroll
   for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LANES);
-  if (live && lane == 0) {
-    const int64_t q = ridx[r];
-    W[q] = (T)s;
-    V[q] += wf * (double)(T)s;
+  if (live && lane == 0) W[ridx[r]] = (T)s;
+}
+
+// ---------------------------------------------------------------------------------
+// Graph path: one launch per phase.
+// ---------------------------------------------------------------------------------
+template <typename T, int ORDER, bool FIRST>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
+                 const int8_t *__restrict__ mask, const T *Wn, T *Wout,
+                 const T *__restrict__ F, const T *__restrict__ Wt, double *V, T fc,
+                 double wf_new, double wf_cur) {
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const Tile t = tiles[tile];
+    const DevGrid &G = grids[t.grid];
+    const int i = t.i0 + (int)threadIdx.x;
+    if (i >= G.n0) continue;
+#pragma unroll
+    for (int m = 0; m < kPY; ++m) {
+      const int j = t.j0 + (int)threadIdx.y + m * kTileY;
+      if (j < G.n1)
+        march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wout, F, Wt, V, fc, wf_new, wf_cur);
+    }
   }
+}
+
+// Ghost rules (blocks [0, bc_blocks)) and interpolation (the remaining blocks) of one
+// time level W.  The two are independent: ghost rules read only discretization/Dirichlet
+// points and donors are never ghosts or receivers.
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256)
+    bc_gather_kernel(const BcItem *__restrict__ bc, int nbc, int bc_blocks,
+                     const int32_t *__restrict__ didx, const double *__restrict__ dw,
+                     const int64_t *__restrict__ ridx, int nrecv, T *W,
+                     const T *__restrict__ F, double fcos) {
+  if ((int)blockIdx.x < bc_blocks) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nbc) bc_item<T>(bc[k], W, F, fcos);
+    return;
+  }
+  constexpr int LANES = ORDER == 4 ? 8 : 4;
+  const int gtid = (blockIdx.x - bc_blocks) * blockDim.x + threadIdx.x;
+  const int r = gtid / LANES;
+  gather_group<T, ORDER>(r, threadIdx.x % LANES, r < nrecv, didx, dw, ridx, W);
 }
 
 // W^0 = v on discretization and interpolation points, 0 elsewhere (ghosts included);
 // V = w_0 W^0 on discretization points, 0 elsewhere.  One thread per extended point.
 template <typename T>
-__global__ void init_kernel(const DevGrid *__restrict__ grids, int ngrids,
-                            const int8_t *__restrict__ mask, const double *__restrict__ v,
-                            T *W0, double *V, int64_t total, double w0) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= total) return;
+__device__ __forceinline__ void init_point(const DevGrid *__restrict__ grids, int ngrids,
+                                           const int8_t *__restrict__ mask,
+                                           const double *v, T *W0, double *V,
+                                           int64_t p, double w0) {
   int g = 0;
   while (g + 1 < ngrids && p >= grids[g + 1].base) ++g;
   const DevGrid &G = grids[g];
@@ -192,19 +233,167 @@ __global__ void init_kernel(const DevGrid *__restrict__ grids, int ngrids,
   V[p] = m == 1 ? w0 * (double)(T)val : 0.0;
 }
 
-// v_out (compact) = V at active points, 0 at unused points.
-__global__ void finish_kernel(const DevGrid *__restrict__ grids, int ngrids,
-                              const int8_t *__restrict__ mask, const double *__restrict__ V,
-                              double *vout, int64_t ncompact) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncompact) return;
+template <typename T>
+__global__ void init_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                            const int8_t *__restrict__ mask, const double *__restrict__ v,
+                            T *W0, double *V, int64_t total, double w0) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < total) init_point<T>(grids, ngrids, mask, v, W0, V, p, w0);
+}
+
+// v_out (compact) = V at active points, 0 at unused points; interpolation points first
+// receive the filter contribution wf_last * W^M of the last level.
+template <typename T>
+__device__ __forceinline__ void finish_point(const DevGrid *__restrict__ grids, int ngrids,
+                                             const int8_t *__restrict__ mask, const double *V,
+                                             const T *WM, double wf_last,
+                                             double *vout, int64_t c) {
   int g = 0;
   while (g + 1 < ngrids && c >= grids[g + 1].cbase) ++g;
   const DevGrid &G = grids[g];
   const int64_t o = c - G.cbase;
   const int j = (int)(o / G.n0), i = (int)(o % G.n0);
   const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
-  vout[c] = mask[p] != 0 ? V[p] : 0.0;
+  const int8_t m = mask[p];
+  vout[c] = m == 2 ? fma(wf_last, (double)WM[p], V[p]) : (m != 0 ? V[p] : 0.0);
+}
+
+template <typename T>
+__global__ void finish_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                              const int8_t *__restrict__ mask, const double *__restrict__ V,
+                              const T *__restrict__ WM, double wf_last, double *vout,
+                              int64_t ncompact) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncompact) finish_point<T>(grids, ngrids, mask, V, WM, wf_last, vout, c);
+}
+
+// ---------------------------------------------------------------------------------
+// Persistent path: one cooperative launch runs a whole WaveHoltz iteration -- init, the
+// t = 0 ghost rules and interpolation, M steps of (march | grid barrier | ghost rules +
+// interpolation | grid barrier), and the output -- so that no step pays a kernel launch,
+// ramp-up or tail.  All blocks are co-resident (cooperative launch).  The grid barrier
+// spins a bounded number of times; on timeout it records an error and every block leaves
+// the kernel, and the host returns WH_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblocks,
+                                          unsigned long long spin_limit) {
+  // one arrival counter and a generation word; the last arriver resets the counter and
+  // advances the generation, the others poll it (bounded)
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile unsigned *vgen = &b->gen[0];
+    volatile int *verr = &b->err[0];
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&b->count[0], 1u) == nblocks - 1) {
+      b->count[0] = 0;
+      __threadfence();
+      atomicAdd(&b->gen[0], 1u);
+    } else {
+      unsigned long long it = 0;
+      while (*vgen == g) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (++it > spin_limit) {
+          atomicExch(&b->err[0], 1);
+          ok = 0;
+          break;
+        }
+        if (it > 4096) __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    iteration_kernel(IterArgs A, const double *__restrict__ v_in, double *v_out,
+                     GridBarrier *bar) {
+  constexpr int LANES = ORDER == 4 ? 8 : 4;
+  const unsigned nb = gridDim.x;
+  const int tid = threadIdx.y * kTileX + threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * (kTileX * kTileY) + tid;
+  const int64_t nthreads = (int64_t)nb * (kTileX * kTileY);
+  const T *F = (const T *)A.F;
+  const T *Wt = (const T *)A.Wt;
+  T *Wa = (T *)A.Wa, *Wb = (T *)A.Wb;
+  const int M = A.M;
+  // init: W^0 = v, V = w_0 W^0
+  for (int64_t p = gtid; p < A.total; p += nthreads)
+    init_point<T>(A.grids, A.ngrids, A.mask, v_in, Wa, A.V, p, A.wf[0]);
+  if (!grid_sync(bar, nb, A.spin_limit)) return;
+  // ghost rules and interpolation run side by side: thread slots [0, nbc32) take ghost
+  // items, the following nrecv * LANES slots the receivers; nbc32 and nthreads are
+  // multiples of 32, so every warp is wholly in one part and the trip count is uniform
+  const int64_t nbc32 = (A.nbc + 31) / 32 * 32;
+  const int64_t slots = nbc32 + A.nrecv * LANES;
+  const int64_t rounds = (slots + nthreads - 1) / nthreads;
+  auto bc_gather = [&](T *W, double fcos) {
+    for (int64_t rd = 0; rd < rounds; ++rd) {
+      const int64_t u = rd * nthreads + gtid;
+      if (u < nbc32) {
+        if (u < A.nbc) bc_item<T>(A.bc[u], W, F, fcos);
+      } else {
+        const int64_t g = u - nbc32;
+        const int64_t r = g / LANES;
+        gather_group<T, ORDER>((int)r, (int)(g % LANES), r < A.nrecv, A.didx, A.dw, A.ridx, W);
+      }
+    }
+  };
+  __shared__ int s_next;
+  bc_gather(Wa, A.fs);
+  if (!grid_sync(bar, nb, A.spin_limit)) return;
+  for (int n = 0; n < M; ++n) {
+    T *cur = (n & 1) ? Wb : Wa;
+    T *oth = (n & 1) ? Wa : Wb;
+    const double fc = n == 0 ? 0.5 * A.fs * A.dt2 : A.fs * A.fc[n];
+    // dynamic tiles: a ticket counter per step parity; the other parity's counter (last
+    // used one step ago, idle until after the next barrier) is reset here
+    int *ctr = &bar->tile_ctr[n & 1][0];
+    if (blockIdx.x == 0 && tid == 0) bar->tile_ctr[(n + 1) & 1][0] = 0;
+    if (tid == 0) s_next = atomicAdd(ctr, 1);
+    __syncthreads();
+    int tile = s_next;
+    __syncthreads();
+    while (tile < A.ntiles) {
+      if (tid == 0) s_next = atomicAdd(ctr, 1);  // next ticket, in flight during this tile
+      const Tile t = A.tiles[tile];
+      const DevGrid &G = A.grids[t.grid];
+      const int i = t.i0 + (int)threadIdx.x;
+      // no early exit: every thread reaches the block barriers below
+      if (i < G.n0) {
+#pragma unroll
+        for (int m = 0; m < kPY; ++m) {
+          const int j = t.j0 + (int)threadIdx.y + m * kTileY;
+          if (j >= G.n1) continue;
+          if (n == 0)
+            march_point<T, ORDER, true>(G, i, j, A.mask, cur, oth, F, Wt, A.V, (T)fc, A.wf[1],
+                                        A.wf[0]);
+          else
+            march_point<T, ORDER, false>(G, i, j, A.mask, cur, oth, F, Wt, A.V, (T)fc,
+                                         A.wf[n + 1], A.wf[n]);
+        }
+      }
+      __syncthreads();
+      tile = s_next;
+      __syncthreads();
+    }
+    if (!grid_sync(bar, nb, A.spin_limit)) return;
+    bc_gather(oth, A.fs * A.cosn[n + 1]);
+    if (!grid_sync(bar, nb, A.spin_limit)) return;
+  }
+  // output (the last level sits in Wa when M is even)
+  const T *WM = (M % 2 == 0) ? Wa : Wb;
+  for (int64_t c = gtid; c < A.ncompact; c += nthreads)
+    finish_point<T>(A.grids, A.ngrids, A.mask, A.V, WM, A.wf[M], v_out, c);
 }
 
 // ---------------------------------------------------------------------------------
@@ -460,13 +649,15 @@ __global__ void gemv_acc(const double *__restrict__ X, int64_t ldx, int nv,
 // Host launchers (the only entry points the host code uses).
 // ---------------------------------------------------------------------------------
 
-void launch_march(bool fp32, int order, bool first, int ntiles, cudaStream_t s,
+void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
-                  void *Wout, const void *F, const void *Wt, double *V, double fc, double wf) {
+                  void *Wout, const void *F, const void *Wt, double *V, double fc,
+                  double wf_new, double wf_cur) {
   const dim3 tb(kTileX, kTileY);
-#define WH_MARCH(T, O, FI)                                                                  \
-  march_kernel<T, O, FI><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const T *)Wn, (T *)Wout, \
-                                               (const T *)F, (const T *)Wt, V, (T)fc, wf)
+#define WH_MARCH(T, O, FI)                                                                 \
+  march_kernel<T, O, FI><<<nblocks, tb, 0, s>>>(grids, tiles, ntiles, mask, (const T *)Wn, \
+                                                (T *)Wout, (const T *)F, (const T *)Wt, V,  \
+                                                (T)fc, wf_new, wf_cur)
   if (fp32) {
     if (order == 4) { if (first) WH_MARCH(float, 4, true); else WH_MARCH(float, 4, false); }
     else            { if (first) WH_MARCH(float, 2, true); else WH_MARCH(float, 2, false); }
@@ -479,11 +670,10 @@ void launch_march(bool fp32, int order, bool first, int ntiles, cudaStream_t s,
 
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
-                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos,
-                      double *V, double wf) {
+                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos) {
 #define WH_BCG(T, O)                                                                      \
   bc_gather_kernel<T, O><<<blocks, 256, 0, s>>>(bc, nbc, bc_blocks, didx, dw, ridx, nrecv, \
-                                                (T *)W, (const T *)F, fcos, V, wf)
+                                                (T *)W, (const T *)F, fcos)
   if (fp32) { if (order == 4) WH_BCG(float, 4); else WH_BCG(float, 2); }
   else      { if (order == 4) WH_BCG(double, 4); else WH_BCG(double, 2); }
 #undef WH_BCG
@@ -498,9 +688,53 @@ void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grid
     init_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (double *)W0, V, total, w0);
 }
 
-void launch_finish(unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
-                   const int8_t *mask, const double *V, double *vout, int64_t ncompact) {
-  finish_kernel<<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, vout, ncompact);
+void launch_finish(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
+                   const int8_t *mask, const double *V, const void *WM, double wf_last,
+                   double *vout, int64_t ncompact) {
+  if (fp32)
+    finish_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, (const float *)WM, wf_last,
+                                                vout, ncompact);
+  else
+    finish_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, (const double *)WM,
+                                                 wf_last, vout, ncompact);
+}
+
+int march_blocks_per_sm(bool fp32, int order) {
+  int nb = 0;
+  const int threads = kTileX * kTileY;
+  if (fp32) {
+    if (order == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_kernel<float, 4, false>, threads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_kernel<float, 2, false>, threads, 0);
+  } else {
+    if (order == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_kernel<double, 4, false>, threads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_kernel<double, 2, false>, threads, 0);
+  }
+  return nb > 0 ? nb : 1;
+}
+
+int iteration_blocks_per_sm(bool fp32, int order) {
+  int nb = 0;
+  const int threads = kTileX * kTileY;
+  if (fp32) {
+    if (order == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, iteration_kernel<float, 4>, threads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, iteration_kernel<float, 2>, threads, 0);
+  } else {
+    if (order == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, iteration_kernel<double, 4>, threads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, iteration_kernel<double, 2>, threads, 0);
+  }
+  return nb;
+}
+
+cudaError_t launch_iteration(bool fp32, int order, int nblocks, cudaStream_t s,
+                             const IterArgs &A, const double *v_in, double *v_out,
+                             GridBarrier *bar) {
+  IterArgs a = A;
+  void *args[] = {(void *)&a, (void *)&v_in, (void *)&v_out, (void *)&bar};
+  const dim3 tb(kTileX, kTileY), gb(nblocks);
+  const void *fn;
+  if (fp32) fn = order == 4 ? (const void *)iteration_kernel<float, 4> : (const void *)iteration_kernel<float, 2>;
+  else fn = order == 4 ? (const void *)iteration_kernel<double, 4> : (const void *)iteration_kernel<double, 2>;
+  return cudaLaunchCooperativeKernel(fn, gb, tb, args, 0, s);
 }
 
 void launch_coef(int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids, int gidx,

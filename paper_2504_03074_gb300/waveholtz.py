@@ -23,6 +23,7 @@ STATUS = {0: "WH_OK", -1: "WH_ERR_ARG", -2: "WH_ERR_CUDA", -3: "WH_ERR_STATE",
           -7: "WH_ERR_GRID", -8: "WH_ERR_NOMEM"}
 FP64, FP32 = 0, 1
 FPI, GMRES = 0, 1
+PERSISTENT, GRAPH = 0, 1
 
 
 class WHError(RuntimeError):
@@ -33,7 +34,8 @@ class WHError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("order", C.c_int32), ("periods", C.c_int32), ("cfl", C.c_double),
-                ("alpha_mode", C.c_int32), ("precision", C.c_int32)]
+                ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("launch_mode", C.c_int32),
+                ("barrier_spin_limit", C.c_uint64)]
 
 
 class GridDesc(C.Structure):
@@ -66,7 +68,7 @@ class Stats(C.Structure):
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
-           "wh_profile_iteration", "wh_multidot_noalloc"]
+           "wh_profile_kernels", "wh_multidot_noalloc"]
 
 
 def lib_path():
@@ -101,8 +103,8 @@ def lib():
     L.wh_dot.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_double)]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
-    L.wh_profile_iteration.argtypes = [vp, C.c_int32, vp, vp, C.POINTER(C.c_double),
-                                       C.POINTER(C.c_int32)]
+    L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int32)]
     L.wh_last_launch_count.argtypes = [vp]
     L.wh_last_launch_count.restype = C.c_int64
     for name in EXPORTS:
@@ -123,13 +125,15 @@ def _ptr(a):
 class Solver:
     """One overset Helmholtz problem in libwaveholtz (one context)."""
 
-    def __init__(self, problem, periods=1, cfl=0.9, alpha_mode=0, precision=FP64, stream=None):
+    def __init__(self, problem, periods=1, cfl=0.9, alpha_mode=0, precision=FP64, stream=None,
+                 launch_mode=GRAPH, barrier_spin_limit=0):
         self.L = lib()
         self.problem = problem
         opt = Options()
         self.L.wh_options_default(C.byref(opt))
         opt.order, opt.periods, opt.cfl = problem.order, periods, cfl
         opt.alpha_mode, opt.precision = alpha_mode, precision
+        opt.launch_mode, opt.barrier_spin_limit = launch_mode, barrier_spin_limit
         h = C.c_void_p()
         self._check(self.L.wh_create(C.byref(opt), C.byref(h)), None)
         self.h = h
@@ -240,14 +244,13 @@ class Solver:
         self._check(self.L.wh_dot(self.h, _ptr(x), _ptr(y), x.numel(), C.byref(out)))
         return out.value
 
-    def profile_iteration(self, v_in, v_out, forcing=True):
-        """Per-kernel device times (ms) and launch counts of one un-graphed iteration:
+    def profile_kernels(self, reps=50):
+        """Average device ms per launch and launches per iteration of each kernel:
         dict(march=(ms, n), bc_gather=(ms, n), init=(ms, n), finish=(ms, n))."""
         ms = (C.c_double * 4)()
         cnt = (C.c_int32 * 4)()
         self._enter()
-        self._check(self.L.wh_profile_iteration(self.h, 1 if forcing else 0, _ptr(v_in),
-                                                _ptr(v_out), ms, cnt))
+        self._check(self.L.wh_profile_kernels(self.h, reps, ms, cnt))
         names = ("march", "bc_gather", "init", "finish")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(names)}
 

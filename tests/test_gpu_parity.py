@@ -58,11 +58,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", ["persistent", "graph"])
 @pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
-def test_iteration_parity(torch, W, oracle_mod, name, make, kw):
+def test_iteration_parity(torch, W, oracle_mod, name, make, kw, mode):
     prob = make()
     orc = oracle_mod.Oracle(prob, **kw)
-    s = W.Solver(prob, **kw)
+    s = W.Solver(prob, launch_mode=W.PERSISTENT if mode == "persistent" else W.GRAPH, **kw)
     ti = s.prepare()
     assert (ti.Nt, ti.M) == (orc.time.Nt, orc.time.M)
     assert abs(ti.dt - orc.time.dt) <= 1e-15 * orc.time.dt
@@ -123,6 +124,28 @@ def test_determinism_and_zero(torch, W):
     c = s.iterate_host(v, True)
     assert np.array_equal(a, c)
     assert s.last_launch_count() == 2 * s.info.M + 3
+    p = W.Solver(prob, launch_mode=W.PERSISTENT)
+    p.prepare()
+    d = gpu_iterate(torch, p, v, True)
+    assert p.last_launch_count() == 1  # one persistent launch per iteration
+    assert np.max(np.abs(d - a)) <= 1e-13 * np.max(np.abs(a))
+
+
+def test_barrier_timeout_is_reported(torch, W):
+    """A grid barrier that runs out of polls makes every block leave the persistent
+    kernel; the call reports WH_ERR_TIMEOUT and the GPU context stays usable."""
+    prob = G.disk_problem(nb=64, nth=128, nr=12, order=4, omega=5.0, width=0.8, r_cut=0.75)
+    s = W.Solver(prob, launch_mode=W.PERSISTENT, barrier_spin_limit=1)
+    s.prepare()
+    v = G.random_state(prob, 1)
+    with pytest.raises(W.WHError) as e:
+        s.iterate_host(v, True)
+    assert e.value.status == -5
+    ok = W.Solver(prob, launch_mode=W.PERSISTENT)
+    ok.prepare()
+    out = ok.iterate_host(v, True)
+    assert np.all(np.isfinite(out))
+    assert float(torch.ones(4, device="cuda").sum()) == 4.0
 
 
 def test_gmres_reaches_direct_solution(torch, W):
