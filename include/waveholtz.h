@@ -136,12 +136,15 @@ typedef struct {
 } wh_time_info;
 
 typedef struct {
-  int32_t iterations;   /* WaveHoltz iterations (FPI) or GMRES matrix-vector products */
+  int32_t iterations;   /* WaveHoltz iterations (FPI) or matrix-vector products (GMRES):
+                           products_fp64 + products_fp32 */
   int32_t converged;    /* 1 if the tolerance was met */
   double residual;      /* final relative residual: FPI ||v_k - v_{k-1}|| / ||v_k||,
-                           GMRES ||b - A v|| / ||b|| (Sec. 6.1) */
+                           GMRES ||b - A v|| / ||b|| with the FP64 march (Sec. 6.1) */
   double seconds;       /* wall time of the solve */
   int32_t n_history;    /* entries written to history (<= history_cap) */
+  int32_t products_fp64;  /* wave solves with the FP64 march */
+  int32_t products_fp32;  /* wave solves with the FP32 march */
 } wh_stats;
 
 /* Fill *opt with order 4, Np = 1, cfl 0.9, alpha_d, FP64, graph launch. */
@@ -192,8 +195,13 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, doub
 /* Solve to relative tolerance tol with WH_FPI (Algorithm 1) or WH_GMRES (restarted,
  * classical Gram-Schmidt applied twice, Sec. 4.3).  u: DEVICE compact vector, the
  * initial guess on entry and the solution on exit.  history (host, may be NULL)
- * receives up to history_cap relative residuals.  Returns WH_ERR_NOT_CONVERGED (u still
- * holds the last iterate) when max_it is reached, WH_ERR_DIVERGED on NaN/Inf. */
+ * receives up to history_cap relative residuals.  max_it bounds the wave solves.
+ * On a WH_FP32 context, WH_GMRES is mixed-precision iterative refinement: b and every
+ * outer residual b - A u use the FP64 march; each correction A d = r is one GMRES(restart)
+ * cycle with the FP32 march (to 1e-4 relative); the orthogonalisation, the updates and
+ * all reductions are FP64.  WH_FPI iterates with the context's march.  Returns
+ * WH_ERR_NOT_CONVERGED (u holds the last iterate) when max_it is reached,
+ * WH_ERR_DIVERGED on NaN/Inf or a growing refinement residual. */
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
                    double *u, wh_stats *stats, double *history, int32_t history_cap);
 

@@ -32,10 +32,13 @@ struct HostGrid {
   int g0 = 0, g1 = 0;
 };
 
-template <typename T>
-struct DBuf {
-  T *p = nullptr;
-  size_t n = 0;
+// The arrays of one march precision: state levels, forcing, stencil weights and the two
+// captured iteration graphs (forcing off / on).
+struct MarchSet {
+  void *Wa = nullptr, *Wb = nullptr, *F = nullptr, *Wt = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  bool fp32 = false, present = false;
+  int march_blocks = 0, iter_blocks = 0;
 };
 
 }  // namespace
@@ -65,7 +68,11 @@ struct wh_ctx {
   DevGrid *d_grids = nullptr;
   Tile *d_tiles = nullptr;
   int8_t *d_mask = nullptr;
+  // the active march set's arrays (mirrors of set[active]); set[0] is FP64, set[1] the
+  // FP32 march of WH_FP32 contexts
   void *d_Wa = nullptr, *d_Wb = nullptr, *d_F = nullptr, *d_Wt = nullptr;
+  MarchSet set[2];
+  int active = 0;
   double *d_V = nullptr, *d_c2 = nullptr, *d_rx = nullptr, *d_coef = nullptr;
   BcItem *d_bc = nullptr;
   int32_t *d_bc_grid = nullptr, *d_bc_axis = nullptr, *d_bc_hi = nullptr;
@@ -76,8 +83,7 @@ struct wh_ctx {
   // time setup
   wh_time_info ti{};
   std::vector<double> fc, wf;  // per step n: forcing factor, filter weight of level n
-  // graphs for forcing off / on
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+
   // solver workspace
   double *d_q = nullptr;  // Krylov basis
   int64_t q_cap = 0;
@@ -99,6 +105,8 @@ struct wh_ctx {
 };
 
 namespace {
+
+constexpr int kWorkVectors = 5;
 
 wh_status fail(wh_ctx *c, wh_status s, const char *fmt, ...) {
   char buf[512];
@@ -130,12 +138,21 @@ wh_status dalloc(wh_ctx *ctx, T **p, size_t n) {
   return WH_OK;
 }
 
+void drop_graphs(wh_ctx *ctx) {
+  for (auto &S : ctx->set)
+    for (auto &g : S.gexec)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
 void free_device(wh_ctx *ctx) {
-  for (int k = 0; k < 2; ++k)
-    if (ctx->gexec[k]) {
-      cudaGraphExecDestroy(ctx->gexec[k]);
-      ctx->gexec[k] = nullptr;
-    }
+  drop_graphs(ctx);
+  for (auto &S : ctx->set) {
+    S.Wa = S.Wb = S.F = S.Wt = nullptr;
+    S.present = false;
+  }
   for (void *p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->d_grids = nullptr;
@@ -153,8 +170,20 @@ inline int64_t ext_index(const DevGrid &G, int i, int j) {
   return G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
 }
 
-bool is_fp32(const wh_ctx *c) { return c->opt.precision == WH_FP32; }
-size_t tsize(const wh_ctx *c) { return is_fp32(c) ? sizeof(float) : sizeof(double); }
+bool is_fp32(const wh_ctx *c) { return c->set[c->active].fp32; }
+
+// Make march set k (0: FP64, 1: FP32) the one the launch code uses.
+void use_set(wh_ctx *c, int k) {
+  c->active = k;
+  const MarchSet &S = c->set[k];
+  c->d_Wa = S.Wa;
+  c->d_Wb = S.Wb;
+  c->d_F = S.F;
+  c->d_Wt = S.Wt;
+  c->march_blocks = S.march_blocks;
+  c->iter_blocks = S.iter_blocks;
+}
+int default_set(const wh_ctx *c) { return c->opt.precision == WH_FP32 ? 1 : 0; }
 
 // Build the device layout, upload everything that does not depend on omega.
 wh_status build_layout(wh_ctx *ctx) {
@@ -338,14 +367,21 @@ wh_status build_layout(wh_ctx *ctx) {
 
   // device allocations
   wh_status st;
-  const size_t ts = tsize(ctx);
+  for (int k = 0; k < 2; ++k) {
+    MarchSet &S = ctx->set[k];
+    S.fp32 = k == 1;
+    S.present = k == 0 || ctx->opt.precision == WH_FP32;
+    if (!S.present) continue;
+    const size_t ts = S.fp32 ? sizeof(float) : sizeof(double);
+    if ((st = dalloc(ctx, (char **)&S.Wa, off * ts)) ||
+        (st = dalloc(ctx, (char **)&S.Wb, off * ts)) ||
+        (st = dalloc(ctx, (char **)&S.F, off * ts)) ||
+        (st = dalloc(ctx, (char **)&S.Wt, ctx->nweights * ts)))
+      return st;
+  }
   if ((st = dalloc(ctx, &ctx->d_grids, ctx->hgrids.size())) ||
       (st = dalloc(ctx, &ctx->d_tiles, ctx->htiles.size())) ||
       (st = dalloc(ctx, &ctx->d_mask, off)) ||
-      (st = dalloc(ctx, (char **)&ctx->d_Wa, off * ts)) ||
-      (st = dalloc(ctx, (char **)&ctx->d_Wb, off * ts)) ||
-      (st = dalloc(ctx, (char **)&ctx->d_F, off * ts)) ||
-      (st = dalloc(ctx, (char **)&ctx->d_Wt, ctx->nweights * ts)) ||
       (st = dalloc(ctx, &ctx->d_V, off)) || (st = dalloc(ctx, &ctx->d_c2, off)) ||
       (st = dalloc(ctx, &ctx->d_rx, std::max<int64_t>(k5, 1))) ||
       (st = dalloc(ctx, &ctx->d_coef, std::max<int64_t>(k5, 1))) ||
@@ -360,11 +396,10 @@ wh_status build_layout(wh_ctx *ctx) {
                 cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_mask, mask.data(), off, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_c2, c2.data(), off * sizeof(double), cudaMemcpyHostToDevice));
-  if (is_fp32(ctx)) {
+  CK(cudaMemcpy(ctx->set[0].F, f.data(), off * sizeof(double), cudaMemcpyHostToDevice));
+  if (ctx->set[1].present) {
     std::vector<float> ff(f.begin(), f.end());
-    CK(cudaMemcpy(ctx->d_F, ff.data(), off * sizeof(float), cudaMemcpyHostToDevice));
-  } else {
-    CK(cudaMemcpy(ctx->d_F, f.data(), off * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->set[1].F, ff.data(), off * sizeof(float), cudaMemcpyHostToDevice));
   }
   if (k5) CK(cudaMemcpy(ctx->d_rx, rx.data(), k5 * sizeof(double), cudaMemcpyHostToDevice));
   if (!ctx->hbc.empty()) {
@@ -383,10 +418,14 @@ wh_status build_layout(wh_ctx *ctx) {
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ctx->march_blocks = sms * march_blocks_per_sm(is_fp32(ctx), order);
-    ctx->iter_blocks = sms * iteration_blocks_per_sm(is_fp32(ctx), order);
+    for (auto &S : ctx->set) {
+      if (!S.present) continue;
+      S.march_blocks = sms * march_blocks_per_sm(S.fp32, order);
+      S.iter_blocks = sms * iteration_blocks_per_sm(S.fp32, order);
+    }
     CK(cudaGetLastError());
   }
+  use_set(ctx, default_set(ctx));
   if ((st = dalloc(ctx, &ctx->d_bar, 1))) return st;
   ctx->dirty = false;
   return WH_OK;
@@ -440,7 +479,7 @@ wh_status build_graph(wh_ctx *ctx, int forcing) {
     return st;
   }
   if (e != cudaSuccess) return fail(ctx, WH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&ctx->gexec[forcing], graph, 0);
+  e = cudaGraphInstantiate(&ctx->set[ctx->active].gexec[forcing], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess)
     return fail(ctx, WH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
@@ -506,7 +545,7 @@ wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double
 wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
   forcing = forcing ? 1 : 0;
   if (ctx->persistent) return iterate_persistent(ctx, forcing, vin, vout);
-  if (!ctx->gexec[forcing]) {
+  if (!ctx->set[ctx->active].gexec[forcing]) {
     wh_status st = build_graph(ctx, forcing);
     if (st) return st;
   }
@@ -516,7 +555,7 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   launch_init(is_fp32(ctx), (unsigned)nb, ctx->stream, ctx->d_grids, ng, ctx->d_mask, vin,
               ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
   CK(cudaGetLastError());
-  CK(cudaGraphLaunch(ctx->gexec[forcing], ctx->stream));
+  CK(cudaGraphLaunch(ctx->set[ctx->active].gexec[forcing], ctx->stream));
   const int64_t nc = (ctx->ncompact + blk - 1) / blk;
   launch_finish(is_fp32(ctx), (unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V,
                 (ctx->ti.M % 2 == 0) ? ctx->d_Wa : ctx->d_Wb, ctx->wf[ctx->ti.M], vout,
@@ -573,6 +612,113 @@ wh_status ensure_stream(wh_ctx *ctx) {
 unsigned grid1d(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (unsigned)std::min<int64_t>(b, 152 * 16);
+}
+
+}  // namespace
+
+namespace {
+
+// ---- GMRES (Sec. 4.3): A v = v - W_h(v, 0) with the active march set ----
+struct SolveLog {
+  double *history = nullptr;
+  int cap = 0, n = 0;
+  int products[2] = {0, 0};  // FP64 / FP32 march products
+  void add(double r) {
+    if (history && n < cap) history[n] = r;
+    ++n;
+  }
+};
+
+// y = A x = x - W_h(x, 0) (w0 is scratch)
+wh_status apply_A(wh_ctx *ctx, const double *x, double *y, double *w0, SolveLog &L) {
+  wh_status st = iterate_device(ctx, 0, x, w0);
+  if (st) return st;
+  L.products[ctx->active] += 1;
+  launch_sub(grid1d(ctx->ncompact), ctx->stream, x, w0, y, ctx->ncompact);
+  return WH_OK;
+}
+
+// One restart cycle of GMRES(m) on A x = rhs, starting from x, classical Gram-Schmidt
+// applied twice, Givens rotations; stops early when the residual estimate drops to
+// tol_abs or the product budget runs out.  scale converts residual norms into the
+// relative values written to the log.
+wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero, int m,
+                      double tol_abs, int budget, double scale, SolveLog &L, double *res_out,
+                      bool *finite) {
+  const int64_t n = ctx->ncompact;
+  cudaStream_t s = ctx->stream;
+  double *w0 = ctx->d_work, *r = ctx->d_work + n;
+  double *Q = ctx->d_q;
+  wh_status st;
+  *finite = true;
+  if (x_is_zero) {
+    CK(cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    if ((st = apply_A(ctx, x, r, w0, L))) return st;
+    launch_axpby(grid1d(n), s, 1.0, rhs, -1.0, r, n);  // r = rhs - A x
+    --budget;
+  }
+  double rr;
+  if ((st = multidot(ctx, r, 0, 1, r, n, &rr))) return st;
+  const double beta = std::sqrt(rr);
+  *res_out = beta;
+  L.add(beta * scale);
+  if (!std::isfinite(beta)) {
+    *finite = false;
+    return WH_OK;
+  }
+  if (beta <= tol_abs || budget <= 0) return WH_OK;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m), h(m + 1);
+  g[0] = beta;
+  launch_axpby(grid1d(n), s, 1.0 / beta, r, 0.0, Q, n);
+  int kk = 0;
+  for (int k = 0; k < m && budget > 0; ++k) {
+    double *qk = Q + (int64_t)k * n, *w = Q + (int64_t)(k + 1) * n;
+    if ((st = apply_A(ctx, qk, w, w0, L))) return st;
+    --budget;
+    for (int pass = 0; pass < 2; ++pass) {
+      // h = Q^T w lands in d_red (device) and in h (host)
+      if ((st = multidot(ctx, Q, n, k + 1, w, n, h.data()))) return st;
+      launch_multi_axpy(grid1d(n), s, Q, n, k + 1, ctx->d_red, w, n);
+      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] += h[i];
+    }
+    double ww;
+    if ((st = multidot(ctx, w, 0, 1, w, n, &ww))) return st;
+    const double hk1 = std::sqrt(ww);
+    if (hk1 > 0) launch_axpby(grid1d(n), s, 0.0, w, 1.0 / hk1, w, n);
+    for (int i = 0; i < k; ++i) {
+      const double t = cs[i] * H[(size_t)i * m + k] + sn[i] * H[(size_t)(i + 1) * m + k];
+      H[(size_t)(i + 1) * m + k] = -sn[i] * H[(size_t)i * m + k] + cs[i] * H[(size_t)(i + 1) * m + k];
+      H[(size_t)i * m + k] = t;
+    }
+    const double hkk = H[(size_t)k * m + k];
+    const double den = std::hypot(hkk, hk1);
+    cs[k] = hkk / den;
+    sn[k] = hk1 / den;
+    H[(size_t)k * m + k] = den;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    kk = k + 1;
+    const double est = std::fabs(g[k + 1]);
+    *res_out = est;
+    L.add(est * scale);
+    if (!std::isfinite(est)) {
+      *finite = false;
+      return WH_OK;
+    }
+    if (est <= tol_abs || hk1 == 0) break;
+  }
+  for (int i = kk - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int j = i + 1; j < kk; ++j) t -= H[(size_t)i * m + j] * y[j];
+    y[i] = t / H[(size_t)i * m + i];
+  }
+  if (kk) {
+    CK(cudaMemcpyAsync(ctx->d_red, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gemv_acc(grid1d(n), s, Q, n, kk, ctx->d_red, x, n);
+  }
+  CK(cudaGetLastError());
+  return WH_OK;
 }
 
 }  // namespace
@@ -635,13 +781,7 @@ wh_status wh_set_stream(wh_ctx *ctx, void *stream) {
     if (st) return st;
   }
   cudaStream_t s = stream ? (cudaStream_t)stream : ctx->own_stream;
-  if (s != ctx->stream) {
-    for (int k = 0; k < 2; ++k)
-      if (ctx->gexec[k]) {
-        cudaGraphExecDestroy(ctx->gexec[k]);
-        ctx->gexec[k] = nullptr;
-      }
-  }
+  if (s != ctx->stream) drop_graphs(ctx);
   ctx->stream = s;
   return WH_OK;
 }
@@ -761,11 +901,7 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
   wh_status st;
   if ((st = ensure_stream(ctx))) return st;
   if (ctx->dirty && (st = build_layout(ctx))) return st;
-  for (int k = 0; k < 2; ++k)
-    if (ctx->gexec[k]) {
-      cudaGraphExecDestroy(ctx->gexec[k]);
-      ctx->gexec[k] = nullptr;
-    }
+  drop_graphs(ctx);
   const int order = ctx->opt.order;
   cudaStream_t s = ctx->stream;
   // (a2) operator coefficients and the frozen-coefficient bound
@@ -864,8 +1000,10 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
     const DevGrid &G = ctx->hgrids[g];
     if (G.stencil == kConstCross) continue;
     dim3 tb(32, 8), gb((G.n0 + 31) / 32, (G.n1 + 7) / 8);
-    launch_weight(is_fp32(ctx), order, gb, tb, s, ctx->d_grids, (int)g, ctx->d_mask,
-                  ctx->d_coef, ctx->d_c2, ctx->d_Wt, dt2);
+    for (const auto &S : ctx->set)
+      if (S.present)
+        launch_weight(S.fp32, order, gb, tb, s, ctx->d_grids, (int)g, ctx->d_mask, ctx->d_coef,
+                      ctx->d_c2, S.Wt, dt2);
   }
   const int nbc = (int)ctx->hbc.size();
   if (nbc)
@@ -890,7 +1028,7 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *vin, doubl
   if (!ctx || !vin || !vout) return fail(ctx, WH_ERR_ARG, "null vector");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   wh_status st;
-  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, 3 * (size_t)ctx->ncompact))) return st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)ctx->ncompact))) return st;
   const size_t bytes = ctx->ncompact * sizeof(double);
   ctx->launches = 0;
   CK(cudaMemcpyAsync(ctx->d_work, vin, bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -917,39 +1055,42 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
   if (!ctx || !u || !(tol > 0) || max_it < 1 || (method != WH_FPI && method != WH_GMRES))
     return fail(ctx, WH_ERR_ARG, "bad wh_solve arguments");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
-  if (method == WH_GMRES && (restart < 1 || restart > 1000))
-    return fail(ctx, WH_ERR_ARG, "restart must be in [1, 1000]");
+  if (method == WH_GMRES && (restart < 1 || restart > 4000))
+    return fail(ctx, WH_ERR_ARG, "restart must be in [1, 4000]");
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = ctx->ncompact;
   wh_status st;
-  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, 3 * (size_t)n))) return st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
+  // work vectors: [0] scratch, [1] cycle residual, [2] b, [3] outer residual, [4] correction
   double *w0 = ctx->d_work, *w1 = ctx->d_work + n, *w2 = ctx->d_work + 2 * n;
   cudaStream_t s = ctx->stream;
-  int nh = 0;
-  auto hist = [&](double r) {
-    if (history && nh < history_cap) history[nh] = r;
-    ++nh;
-  };
   ctx->launches = 0;
+  SolveLog L;
+  L.history = history;
+  L.cap = history_cap < 0 ? 0 : history_cap;
   wh_stats S{};
   auto finish = [&](wh_status code) {
+    use_set(ctx, default_set(ctx));
     S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    S.n_history = std::min(nh, history_cap < 0 ? 0 : history_cap);
+    S.n_history = std::min(L.n, L.cap);
+    S.products_fp64 = L.products[0];
+    S.products_fp32 = L.products[1];
+    S.iterations = L.products[0] + L.products[1];
     if (stats) *stats = S;
     return code;
   };
-  if (method == WH_FPI) {
+  if (method == WH_FPI) {  // Algorithm 1 with the context's march precision
     for (int k = 0; k < max_it; ++k) {
       if ((st = iterate_device(ctx, 1, u, w0))) return finish(st);
+      L.products[ctx->active] += 1;
       launch_sub(grid1d(n), s, w0, u, w1, n);
       CK(cudaMemcpyAsync(u, w0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       double d[2];
       if ((st = multidot(ctx, w1, 0, 1, w1, n, &d[0]))) return finish(st);
       if ((st = multidot(ctx, u, 0, 1, u, n, &d[1]))) return finish(st);
       const double r = std::sqrt(d[0]) / std::max(std::sqrt(d[1]), 1e-300);
-      S.iterations = k + 1;
       S.residual = r;
-      hist(r);
+      L.add(r);
       if (!std::isfinite(r)) return finish(fail(ctx, WH_ERR_DIVERGED, "FPI residual is %g", r));
       if (r <= tol) {
         S.converged = 1;
@@ -959,15 +1100,17 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "FPI: %d iterations, residual %g", max_it,
                        S.residual));
   }
-  // GMRES(m) on A v = v - W_h(v, 0), b = W_h(0, f)
   const int m = restart;
   if (ctx->q_cap < (int64_t)(m + 1) * n) {
     if ((st = dalloc(ctx, &ctx->d_q, (size_t)(m + 1) * n))) return finish(st);
     ctx->q_cap = (int64_t)(m + 1) * n;
   }
-  double *Q = ctx->d_q;
+  if ((st = ensure_red(ctx, m + 1))) return finish(st);
+  // b = W_h(0, f) with the FP64 march (residuals stay in FP64)
+  use_set(ctx, 0);
   CK(cudaMemsetAsync(w0, 0, n * sizeof(double), s));
-  if ((st = iterate_device(ctx, 1, w0, w2))) return finish(st);  // w2 = b
+  if ((st = iterate_device(ctx, 1, w0, w2))) return finish(st);
+  L.products[0] += 1;
   double bb;
   if ((st = multidot(ctx, w2, 0, 1, w2, n, &bb))) return finish(st);
   const double bnorm = std::sqrt(bb);
@@ -976,78 +1119,70 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     S.converged = 1;
     return finish(WH_OK);
   }
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 1), h2(m + 1);
-  int its = 0;
-  double rel = 1.0;
-  if ((st = ensure_red(ctx, m + 1))) return finish(st);
+  double *b = w2;
+  if (default_set(ctx) == 0) {
+    // FP64 GMRES(m): restart cycles, each starting from the true residual
+    while (true) {
+      double res;
+      bool fin;
+      const int budget = max_it - (L.products[0] + L.products[1]);
+      if ((st = gmres_cycle(ctx, b, u, false, m, tol * bnorm, budget, 1.0 / bnorm, L, &res, &fin)))
+        return finish(st);
+      S.residual = res / bnorm;
+      if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual is not finite"));
+      if (res <= tol * bnorm) {
+        // the cycle's last value may be the Givens estimate: confirm with a true residual
+        double *rr = ctx->d_work + n;
+        if ((st = apply_A(ctx, u, rr, w0, L))) return finish(st);
+        launch_axpby(grid1d(n), s, 1.0, b, -1.0, rr, n);
+        double r2;
+        if ((st = multidot(ctx, rr, 0, 1, rr, n, &r2))) return finish(st);
+        S.residual = std::sqrt(r2) / bnorm;
+        L.add(S.residual);
+        if (S.residual <= tol) {
+          S.converged = 1;
+          return finish(WH_OK);
+        }
+      }
+      if (L.products[0] + L.products[1] >= max_it)
+        return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
+                           S.residual));
+    }
+  }
+  // FP32 march: iterative refinement.  Outer residual r = b - A u with the FP64 march;
+  // the correction A d = r by one GMRES cycle with the FP32 march (to 1e-4 relative or
+  // the cycle's end); u += d.
+  double *r = ctx->d_work + 3 * n, *d = ctx->d_work + 4 * n;
+  double prev = 1e300;
   while (true) {
-    // r = b - A u = b - u + W_h(u, 0)
-    if ((st = iterate_device(ctx, 0, u, w0))) return finish(st);
-    ++its;
-    launch_sub(grid1d(n), s, w2, u, w1, n);  // w1 = b - u
-    launch_axpby(grid1d(n), s, 1.0, w0, 1.0, w1, n);  // w1 += W_h(u, 0)
-    double rr;
-    if ((st = multidot(ctx, w1, 0, 1, w1, n, &rr))) return finish(st);
-    const double beta = std::sqrt(rr);
-    rel = beta / bnorm;
-    hist(rel);
-    S.iterations = its;
-    S.residual = rel;
-    if (!std::isfinite(rel)) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual %g", rel));
-    if (rel <= tol) {
+    use_set(ctx, 0);
+    if ((st = apply_A(ctx, u, r, w0, L))) return finish(st);
+    launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);  // r = b - A u
+    double r2;
+    if ((st = multidot(ctx, r, 0, 1, r, n, &r2))) return finish(st);
+    const double rn = std::sqrt(r2);
+    S.residual = rn / bnorm;
+    L.add(S.residual);
+    if (!std::isfinite(rn) || rn > 10.0 * prev)
+      return finish(fail(ctx, WH_ERR_DIVERGED, "refinement residual %g", S.residual));
+    if (S.residual <= tol) {
       S.converged = 1;
       return finish(WH_OK);
     }
-    if (its >= max_it)
-      return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", its, rel));
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    launch_axpby(grid1d(n), s, 1.0 / beta, w1, 0.0, Q, n);
-    int k = 0, kk = 0;
-    for (k = 0; k < m; ++k) {
-      double *qk = Q + (int64_t)k * n, *w = Q + (int64_t)(k + 1) * n;
-      if ((st = iterate_device(ctx, 0, qk, w0))) return finish(st);
-      ++its;
-      launch_sub(grid1d(n), s, qk, w0, w, n);  // w = q_k - W_h(q_k, 0)
-      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-        // h = Q^T w lands in d_red (device) and in h (host)
-        if ((st = multidot(ctx, Q, n, k + 1, w, n, h.data()))) return finish(st);
-        launch_multi_axpy(grid1d(n), s, Q, n, k + 1, ctx->d_red, w, n);
-        for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] += h[i];
-      }
-      double ww;
-      if ((st = multidot(ctx, w, 0, 1, w, n, &ww))) return finish(st);
-      double hk1 = std::sqrt(ww);
-      if (hk1 > 0) launch_axpby(grid1d(n), s, 0.0, w, 1.0 / hk1, w, n);
-      for (int i = 0; i < k; ++i) {
-        const double t = cs[i] * H[(size_t)i * m + k] + sn[i] * H[(size_t)(i + 1) * m + k];
-        H[(size_t)(i + 1) * m + k] = -sn[i] * H[(size_t)i * m + k] + cs[i] * H[(size_t)(i + 1) * m + k];
-        H[(size_t)i * m + k] = t;
-      }
-      const double hkk = H[(size_t)k * m + k];
-      const double den = std::hypot(hkk, hk1);
-      cs[k] = hkk / den;
-      sn[k] = hk1 / den;
-      H[(size_t)k * m + k] = den;
-      g[k + 1] = -sn[k] * g[k];
-      g[k] = cs[k] * g[k];
-      rel = std::fabs(g[k + 1]) / bnorm;
-      hist(rel);
-      S.iterations = its;
-      S.residual = rel;
-      kk = k + 1;
-      if (!std::isfinite(rel)) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual %g", rel));
-      if (rel <= tol || its >= max_it || hk1 == 0) break;
-    }
-    for (int i = kk - 1; i >= 0; --i) {
-      double t = g[i];
-      for (int j = i + 1; j < kk; ++j) t -= H[(size_t)i * m + j] * y[j];
-      y[i] = t / H[(size_t)i * m + i];
-    }
-    CK(cudaMemcpyAsync(ctx->d_red, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_gemv_acc(grid1d(n), s, Q, n, kk, ctx->d_red, u, n);
-    CK(cudaGetLastError());
+    if (L.products[0] + L.products[1] >= max_it)
+      return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "refinement: %d products, residual %g",
+                         max_it, S.residual));
+    prev = rn;
+    use_set(ctx, 1);
+    CK(cudaMemsetAsync(d, 0, n * sizeof(double), s));
+    double res;
+    bool fin;
+    const int left = max_it - (L.products[0] + L.products[1]);
+    if ((st = gmres_cycle(ctx, r, d, true, m, std::max(1e-4 * rn, 0.5 * tol * bnorm), left,
+                          1.0 / bnorm, L, &res, &fin)))
+      return finish(st);
+    if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "inner GMRES residual is not finite"));
+    launch_axpby(grid1d(n), s, 1.0, d, 1.0, u, n);  // u += d
   }
 }
 
@@ -1087,7 +1222,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
     }
   };
   wh_status st;
-  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, 3 * (size_t)ctx->ncompact))) return st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)ctx->ncompact))) return st;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

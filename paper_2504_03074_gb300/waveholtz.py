@@ -62,7 +62,8 @@ class TimeInfo(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
-                ("seconds", C.c_double), ("n_history", C.c_int32)]
+                ("seconds", C.c_double), ("n_history", C.c_int32), ("products_fp64", C.c_int32),
+                ("products_fp32", C.c_int32)]
 
 
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",

@@ -1,0 +1,80 @@
+"""FP32-march form (WH_FP32): the wave march runs in FP32 while the filter accumulator,
+the interpolation weights, the GMRES orthogonalisation and all residuals stay FP64.
+
+Stated bounds (checked here against the FP64 CPU oracle):
+* one WaveHoltz iteration: relative max-norm error <= 1e-4;
+* GMRES by mixed-precision iterative refinement to residual 1e-9: relative max-norm error
+  <= 1e-6 against the direct solution of the discrete Helmholtz system."""
+import numpy as np
+import pytest
+
+from paper_2504_03074_gb300 import grids as G
+
+pytestmark = pytest.mark.gpu
+ITER_BOUND = 1e-4
+SOLVE_BOUND = 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available()
+    return T
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2504_03074_gb300 import build
+    build.build()
+    from paper_2504_03074_gb300 import waveholtz
+    return waveholtz
+
+
+CASES = [
+    ("square64-o2", lambda: G.unit_square_problem(64, 2, 10.0)),
+    ("channel-neumann-o4", lambda: G.channel_problem(45, 4, 5.0, bc=G.BC_NEUMANN)),
+    ("torus-o4", lambda: G.sheared_torus_problem(40, 36, 4)),
+    ("disk-o4", lambda: G.disk_problem(nb=128, nth=256, nr=16, order=4, omega=10.0)),
+    ("disk-o4-cx", lambda: G.disk_problem(nb=96, nth=192, nr=16, order=4, omega=6.0, c_bumps=8,
+                                          width=0.6, r_cut=0.7)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_fp32_iteration_within_bound(torch, W, oracle_mod, name, make):
+    prob = make()
+    orc = oracle_mod.Oracle(prob)
+    act = orc.active()
+    for mode in (W.GRAPH, W.PERSISTENT):
+        s = W.Solver(prob, precision=W.FP32, launch_mode=mode)
+        s.prepare()
+        for seed, forcing in ((1, True), (2, False)):
+            v = G.random_state(prob, seed)
+            ref = orc.iterate(v, forcing)
+            vi = torch.from_numpy(v).cuda()
+            vo = torch.empty_like(vi)
+            s.iterate(vi, vo, forcing)
+            got = vo.cpu().numpy()
+            err = np.max(np.abs(got - ref)[act]) / np.max(np.abs(ref)[act])
+            assert err <= ITER_BOUND, (name, mode, forcing, err)
+            assert np.all(got[~act] == 0.0)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("square48-o4", lambda: G.unit_square_problem(48, 4, 10.0)),
+    ("disk-o4", lambda: G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, width=0.8,
+                                       r_cut=0.75)),
+], ids=["square48-o4", "disk-o4"])
+def test_fp32_refinement_reaches_1e6(torch, W, name, make):
+    import dhs
+    prob = make()
+    U = dhs.solve(prob)
+    act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
+    s = W.Solver(prob, precision=W.FP32)
+    s.prepare()
+    u = torch.zeros(prob.n_total, dtype=torch.float64, device="cuda")
+    st = s.solve(u, W.GMRES, tol=1e-9, max_it=2000, restart=200)
+    assert st.converged == 1, (st.status, st.residual)
+    assert st.products_fp32 > st.products_fp64 > 0
+    err = np.max(np.abs(u.cpu().numpy() - U)[act]) / np.max(np.abs(U)[act])
+    assert err <= SOLVE_BOUND, err
