@@ -98,6 +98,8 @@ struct wh_ctx {
   int64_t steps_cap = 0;
   GridBarrier *d_bar = nullptr;
   int *h_err = nullptr;       // pinned copy of the barrier error flag
+  int64_t *d_patch_off = nullptr;
+  int32_t *d_patch_pos = nullptr, *d_patch_item = nullptr, *d_recv_of = nullptr;
   bool persistent = true;
   unsigned long long opt_spin_limit = 1ull << 22;
   cudaEvent_t err_ev = nullptr;
@@ -244,6 +246,33 @@ wh_status build_layout(wh_ctx *ctx) {
       }
     ctx->hgrids.push_back(G);
   }
+  {
+    // interleave the grids' tiles so that blocks taking tiles round-robin get a mix of
+    // cheap (constant-weight) and expensive (per-point-weight) tiles
+    std::vector<std::vector<Tile>> per(ctx->grids.size());
+    for (const Tile &t : ctx->htiles) per[t.grid].push_back(t);
+    std::vector<Tile> mixed;
+    mixed.reserve(ctx->htiles.size());
+    std::vector<double> taken(per.size(), 0.0);
+    size_t left = ctx->htiles.size();
+    std::vector<size_t> pos(per.size(), 0);
+    while (left) {
+      // take from the grid with the smallest fraction taken so far
+      size_t best = 0;
+      double bf = 2.0;
+      for (size_t g = 0; g < per.size(); ++g)
+        if (pos[g] < per[g].size()) {
+          const double f = (double)pos[g] / per[g].size();
+          if (f < bf) {
+            bf = f;
+            best = g;
+          }
+        }
+      mixed.push_back(per[best][pos[best]++]);
+      --left;
+    }
+    ctx->htiles.swap(mixed);
+  }
   ctx->total = off;
   ctx->ncompact = coff;
   ctx->nactive = nact;
@@ -365,6 +394,47 @@ wh_status build_layout(wh_ctx *ctx) {
       }
   }
 
+  // persistent-kernel patch lists: ghost and receiver positions inside each tile's staged
+  // box (tile + halo of order/2, corner blocks excluded: the cross stencil never reads
+  // them; box stencils only occur on grids without ghosts or receivers in the halo corners
+  // of ... every patched position is included regardless of stencil)
+  std::vector<int32_t> kind_item(off, -1), recv_of(off, -1);
+  for (size_t k = 0; k < ctx->hbc.size(); ++k) {
+    kind_item[ctx->hbc[k].g[0]] = (0 << 24) | (int32_t)k;
+    if (order == 4) kind_item[ctx->hbc[k].g[1]] = (1 << 24) | (int32_t)k;
+  }
+  for (int64_t r = 0; r < ctx->nrecv; ++r) {
+    kind_item[ridx[r]] = (2 << 24) | (int32_t)r;
+    recv_of[ridx[r]] = (int32_t)r;
+  }
+  std::vector<int64_t> patch_off(ctx->htiles.size() + 1, 0);
+  std::vector<int32_t> patch_pos, patch_item;
+  {
+    const int SX = kTileX + 2 * R, SY = kTileY * kPY + 2 * R;
+    for (size_t t = 0; t < ctx->htiles.size(); ++t) {
+      const Tile &T = ctx->htiles[t];
+      const DevGrid &G = ctx->hgrids[T.grid];
+      const bool box = G.stencil == kPointBox;
+      for (int rr = 0; rr < SY; ++rr)
+        for (int cc = 0; cc < SX; ++cc) {
+          const bool corner = (rr < R || rr >= SY - R) && (cc < R || cc >= SX - R);
+          if (corner && !box) continue;
+          int i = T.i0 - R + cc, j = T.j0 - R + rr;
+          if (G.per0) i = ((i % G.n0) + G.n0) % G.n0;
+          else if (i < -G.g0 || i >= G.n0 + G.g0) continue;
+          if (G.per1) j = ((j % G.n1) + G.n1) % G.n1;
+          else if (j < -G.g1 || j >= G.n1 + G.g1) continue;
+          const int32_t ki = kind_item[ext_index(G, i, j)];
+          if (ki < 0) continue;
+          patch_pos.push_back(((ki >> 24) << 24) | (rr * SX + cc));
+          patch_item.push_back(ki & 0xffffff);
+        }
+      patch_off[t + 1] = (int64_t)patch_pos.size();
+    }
+  }
+  if (ctx->hbc.size() >= (1u << 24) || ctx->nrecv >= (1 << 24))
+    return fail(ctx, WH_ERR_ARG, "too many ghost items or receivers for the patch encoding");
+
   // device allocations
   wh_status st;
   for (int k = 0; k < 2; ++k) {
@@ -390,8 +460,19 @@ wh_status build_layout(wh_ctx *ctx) {
       (st = dalloc(ctx, &ctx->d_bc_axis, ctx->hbc.size())) ||
       (st = dalloc(ctx, &ctx->d_bc_hi, ctx->hbc.size())) ||
       (st = dalloc(ctx, &ctx->d_didx, didx.size())) || (st = dalloc(ctx, &ctx->d_dw, dw.size())) ||
-      (st = dalloc(ctx, &ctx->d_ridx, ridx.size())) || (st = dalloc(ctx, &ctx->d_smax, 1)))
+      (st = dalloc(ctx, &ctx->d_ridx, ridx.size())) || (st = dalloc(ctx, &ctx->d_smax, 1)) ||
+      (st = dalloc(ctx, &ctx->d_patch_off, patch_off.size())) ||
+      (st = dalloc(ctx, &ctx->d_patch_pos, std::max<size_t>(patch_pos.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_patch_item, std::max<size_t>(patch_item.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_recv_of, recv_of.size())))
     return st;
+  CK(cudaMemcpy(ctx->d_patch_off, patch_off.data(), patch_off.size() * 8, cudaMemcpyHostToDevice));
+  if (!patch_pos.empty()) {
+    CK(cudaMemcpy(ctx->d_patch_pos, patch_pos.data(), patch_pos.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_patch_item, patch_item.data(), patch_item.size() * 4,
+                  cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(ctx->d_recv_of, recv_of.data(), recv_of.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_tiles, ctx->htiles.data(), ctx->htiles.size() * sizeof(Tile),
                 cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_mask, mask.data(), off, cudaMemcpyHostToDevice));
@@ -531,6 +612,10 @@ wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double
   A.total = ctx->total;
   A.ncompact = ctx->ncompact;
   A.spin_limit = ctx->opt_spin_limit;
+  A.patch_off = ctx->d_patch_off;
+  A.patch_pos = ctx->d_patch_pos;
+  A.patch_item = ctx->d_patch_item;
+  A.recv_of = ctx->d_recv_of;
   CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), ctx->stream));
   CK(launch_iteration(is_fp32(ctx), ctx->opt.order, ctx->iter_blocks, ctx->stream, A, vin, vout,
                       ctx->d_bar));

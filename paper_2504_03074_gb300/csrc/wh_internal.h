@@ -90,6 +90,13 @@ struct IterArgs {
   int pad_;
   int64_t total, ncompact;
   unsigned long long spin_limit;
+  // per-tile patch lists: entries [patch_off[t], patch_off[t+1]) of tile t; patch_pos holds
+  // (kind << 24) | shared-memory index, kind 0/1 = ghost G1/G2 of BC item patch_item,
+  // kind 2 = receiver patch_item
+  const int64_t *patch_off;
+  const int32_t *patch_pos;
+  const int32_t *patch_item;
+  const int32_t *recv_of;  // receiver index at each extended point, -1 elsewhere
 };
 
 // Host launchers (wh_kernels.cu).  T is double unless fp32 is set; pointers typed void

@@ -313,11 +313,54 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblocks,
   return s_ok != 0;
 }
 
+// Value of ghost G1 (which = 0) or G2 (which = 1) of a ghost-rule item at one level.
+template <typename T>
+__device__ __forceinline__ double bc_value(const BcItem &it, const T *W, const T *__restrict__ F,
+                                           double fcos, int which) {
+  const double U0 = (double)W[it.u[0]], U1 = (double)W[it.u[1]];
+  if (it.type == 0) return U1;
+  const double U2 = (double)W[it.u[2]], U3 = (double)W[it.u[3]];
+  const double E = -10.0 * U0 + 10.0 * U1 - 5.0 * U2 + U3;
+  double G1;
+  if (it.type == 1) {
+    G1 = (18.0 * U1 - 10.0 * U0 - 6.0 * U2 + U3) * (1.0 / 3.0);
+  } else {
+    const double Fb = (double)F[it.u[0]] * fcos;
+    G1 = (Fb - it.A2 * (-30.0 * U0 + 16.0 * U1 - U2) - it.B1 * (8.0 * U1 - U2) +
+          (it.A2 - it.B1) * E) * it.inv;
+  }
+  return which == 0 ? G1 : 5.0 * G1 + E;
+}
+
+// Level value of receiver r from its donors (one thread, all donors).
+template <typename T, int ORDER>
+__device__ __forceinline__ double recv_value(int64_t r, const int32_t *__restrict__ didx,
+                                             const double *__restrict__ dw, const T *W) {
+  constexpr int ND = (ORDER + 1) * (ORDER + 1);
+  const int32_t *di = didx + r * ND;
+  const double *wi = dw + r * ND;
+  double s = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) s = fma(wi[d], (double)W[di[d]], s);
+  return s;
+}
+
+// One WaveHoltz iteration in one cooperative launch, one grid barrier per time step.
+// Step n of a 32 x 32 tile: stage W^n of the tile and its halo in shared memory; patch the
+// halo and tile positions that are ghost points or receivers with their level-n values
+// (ghost rules from the boundary columns, receivers from their donors -- all final after
+// the previous barrier); then advance the tile's discretization points from shared memory
+// and add the receivers' level-n filter contribution.  Receiver and ghost values never go
+// back to global memory: every tile computes the ones its stencils read.
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(kTileX *kTileY)
     iteration_kernel(IterArgs A, const double *__restrict__ v_in, double *v_out,
                      GridBarrier *bar) {
-  constexpr int LANES = ORDER == 4 ? 8 : 4;
+  constexpr int R = ORDER / 2;
+  constexpr int SX = kTileX + 2 * R;          // 36 (order 4)
+  constexpr int SY = kTileY * kPY + 2 * R;    // 36
+  __shared__ T sw[SY][SX];
+  __shared__ int s_next;
   const unsigned nb = gridDim.x;
   const int tid = threadIdx.y * kTileX + threadIdx.x;
   const int64_t gtid = (int64_t)blockIdx.x * (kTileX * kTileY) + tid;
@@ -326,35 +369,16 @@ __global__ void __launch_bounds__(kTileX *kTileY)
   const T *Wt = (const T *)A.Wt;
   T *Wa = (T *)A.Wa, *Wb = (T *)A.Wb;
   const int M = A.M;
-  // init: W^0 = v, V = w_0 W^0
+  // init: W^0 = v, V = w_0 W^0 (receivers' V accumulates from the first step on)
   for (int64_t p = gtid; p < A.total; p += nthreads)
     init_point<T>(A.grids, A.ngrids, A.mask, v_in, Wa, A.V, p, A.wf[0]);
-  if (!grid_sync(bar, nb, A.spin_limit)) return;
-  // ghost rules and interpolation run side by side: thread slots [0, nbc32) take ghost
-  // items, the following nrecv * LANES slots the receivers; nbc32 and nthreads are
-  // multiples of 32, so every warp is wholly in one part and the trip count is uniform
-  const int64_t nbc32 = (A.nbc + 31) / 32 * 32;
-  const int64_t slots = nbc32 + A.nrecv * LANES;
-  const int64_t rounds = (slots + nthreads - 1) / nthreads;
-  auto bc_gather = [&](T *W, double fcos) {
-    for (int64_t rd = 0; rd < rounds; ++rd) {
-      const int64_t u = rd * nthreads + gtid;
-      if (u < nbc32) {
-        if (u < A.nbc) bc_item<T>(A.bc[u], W, F, fcos);
-      } else {
-        const int64_t g = u - nbc32;
-        const int64_t r = g / LANES;
-        gather_group<T, ORDER>((int)r, (int)(g % LANES), r < A.nrecv, A.didx, A.dw, A.ridx, W);
-      }
-    }
-  };
-  __shared__ int s_next;
-  bc_gather(Wa, A.fs);
   if (!grid_sync(bar, nb, A.spin_limit)) return;
   for (int n = 0; n < M; ++n) {
     T *cur = (n & 1) ? Wb : Wa;
     T *oth = (n & 1) ? Wa : Wb;
     const double fc = n == 0 ? 0.5 * A.fs * A.dt2 : A.fs * A.fc[n];
+    const double fcos = A.fs * A.cosn[n];
+    const double wf_new = A.wf[n + 1], wf_cur = A.wf[n];
     // dynamic tiles: a ticket counter per step parity; the other parity's counter (last
     // used one step ago, idle until after the next barrier) is reset here
     int *ctr = &bar->tile_ctr[n & 1][0];
@@ -367,33 +391,109 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       if (tid == 0) s_next = atomicAdd(ctr, 1);  // next ticket, in flight during this tile
       const Tile t = A.tiles[tile];
       const DevGrid &G = A.grids[t.grid];
+      // stage W^n (tile + halo; wrapped on periodic axes, clamped into the extended array)
+      for (int e = tid; e < SX * SY; e += kTileX * kTileY) {
+        const int rr = e / SX, cc = e % SX;
+        int ii = wrap(t.i0 - R + cc, G.n0, G.per0);
+        ii = ii < -G.g0 ? -G.g0 : (ii >= G.n0 + G.g0 ? G.n0 + G.g0 - 1 : ii);
+        sw[rr][cc] = cur[row_off(G, t.j0 - R + rr) + ii];
+      }
+      __syncthreads();
+      // patch ghost and receiver positions with their level-n values
+      for (int64_t e = A.patch_off[tile] + tid; e < A.patch_off[tile + 1];
+           e += kTileX * kTileY) {
+        const int32_t pos = A.patch_pos[e], item = A.patch_item[e];
+        const int kind = pos >> 24, sidx = pos & 0xffffff;
+        double v;
+        if (kind == 2) v = recv_value<T, ORDER>(item, A.didx, A.dw, cur);
+        else v = bc_value<T>(A.bc[item], cur, F, fcos, kind);
+        (&sw[0][0])[sidx] = (T)v;
+      }
+      __syncthreads();
       const int i = t.i0 + (int)threadIdx.x;
-      // no early exit: every thread reaches the block barriers below
       if (i < G.n0) {
 #pragma unroll
         for (int m = 0; m < kPY; ++m) {
-          const int j = t.j0 + (int)threadIdx.y + m * kTileY;
+          const int r = (int)threadIdx.y + m * kTileY;
+          const int j = t.j0 + r;
           if (j >= G.n1) continue;
-          if (n == 0)
-            march_point<T, ORDER, true>(G, i, j, A.mask, cur, oth, F, Wt, A.V, (T)fc, A.wf[1],
-                                        A.wf[0]);
-          else
-            march_point<T, ORDER, false>(G, i, j, A.mask, cur, oth, F, Wt, A.V, (T)fc,
-                                         A.wf[n + 1], A.wf[n]);
+          const int64_t p = row_off(G, j) + i;
+          const int8_t mk = A.mask[p];
+          const T wc = sw[r + R][threadIdx.x + R];
+          if (mk == 2) {
+            A.V[p] = fma(wf_cur, (double)wc, A.V[p]);
+            continue;
+          }
+          if (mk != 1) continue;
+          T a;
+          if (G.stencil == kConstCross) {
+            const T c0 = (T)G.cw[0], x1 = (T)G.cw[1], y1 = (T)G.cw[3];
+            a = n == 0 ? c0 * wc : fma(c0, wc, -oth[p]);
+            a = fma(x1, sw[r + R][threadIdx.x + R - 1], a);
+            a = fma(x1, sw[r + R][threadIdx.x + R + 1], a);
+            a = fma(y1, sw[r + R - 1][threadIdx.x + R], a);
+            a = fma(y1, sw[r + R + 1][threadIdx.x + R], a);
+            if (ORDER == 4) {
+              const T x2 = (T)G.cw[2], y2 = (T)G.cw[4];
+              a = fma(x2, sw[r + R][threadIdx.x + R - 2], a);
+              a = fma(x2, sw[r + R][threadIdx.x + R + 2], a);
+              a = fma(y2, sw[r + R - 2][threadIdx.x + R], a);
+              a = fma(y2, sw[r + R + 2][threadIdx.x + R], a);
+            }
+          } else if (G.stencil == kPointCross) {
+            const int64_t q = G.wbase + (p - G.base), E = G.ext;
+            a = n == 0 ? Wt[q] * wc : fma(Wt[q], wc, -oth[p]);
+            int pl = 1;
+#pragma unroll
+            for (int k = -R; k <= R; ++k) {
+              if (k == 0) continue;
+              a = fma(Wt[q + pl * E], sw[r + R][threadIdx.x + R + k], a);
+              ++pl;
+            }
+#pragma unroll
+            for (int k = -R; k <= R; ++k) {
+              if (k == 0) continue;
+              a = fma(Wt[q + pl * E], sw[r + R + k][threadIdx.x + R], a);
+              ++pl;
+            }
+          } else {
+            const int64_t q = G.wbase + (p - G.base), E = G.ext;
+            a = n == 0 ? (T)0 : -oth[p];
+#pragma unroll
+            for (int bb = -R; bb <= R; ++bb)
+#pragma unroll
+              for (int aa = -R; aa <= R; ++aa)
+                a = fma(Wt[q + ((bb + R) * (2 * R + 1) + (aa + R)) * E],
+                        sw[r + R + bb][threadIdx.x + R + aa], a);
+          }
+          if (n == 0) a *= (T)0.5;
+          a = fma((T)(-fc), F[p], a);
+          oth[p] = a;
+          A.V[p] = fma(wf_new, (double)a, A.V[p]);
         }
       }
-      __syncthreads();
+      __syncthreads();  // the staged tile is overwritten by the next one
       tile = s_next;
       __syncthreads();
     }
     if (!grid_sync(bar, nb, A.spin_limit)) return;
-    bc_gather(oth, A.fs * A.cosn[n + 1]);
-    if (!grid_sync(bar, nb, A.spin_limit)) return;
   }
-  // output (the last level sits in Wa when M is even)
+  // output; receivers add their level-M contribution, computed from their donors
   const T *WM = (M % 2 == 0) ? Wa : Wb;
-  for (int64_t c = gtid; c < A.ncompact; c += nthreads)
-    finish_point<T>(A.grids, A.ngrids, A.mask, A.V, WM, A.wf[M], v_out, c);
+  for (int64_t c = gtid; c < A.ncompact; c += nthreads) {
+    int g = 0;
+    while (g + 1 < A.ngrids && c >= A.grids[g + 1].cbase) ++g;
+    const DevGrid &G = A.grids[g];
+    const int64_t o = c - G.cbase;
+    const int j = (int)(o / G.n0), i = (int)(o % G.n0);
+    const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+    const int8_t m = A.mask[p];
+    double val = 0.0;
+    if (m == 1 || m == 3) val = A.V[p];
+    else if (m == 2)
+      val = fma(A.wf[M], recv_value<T, ORDER>(A.recv_of[p], A.didx, A.dw, WM), A.V[p]);
+    v_out[c] = val;
+  }
 }
 
 // ---------------------------------------------------------------------------------
