@@ -102,6 +102,8 @@ typedef struct {
   int32_t kind;
   int32_t bc[4];
   int32_t orthogonal;
+  int32_t instance;  /* independent problem this grid belongs to (batching): 0 for the
+                        first grid, then equal to or one more than the previous grid's */
   double h[2];
   const int8_t *mask;
   const double *rx;
@@ -174,7 +176,13 @@ wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *interp);
  * c^2 Lap u + omega^2 u = f; the scheme applies -f cos(omega_e t). */
 wh_status wh_set_forcing(wh_ctx *ctx, int32_t grid_id, const double *f);
 
-/* Prepare frequency omega: the operator coefficients of the mapping method
+/* Prepare one frequency per instance (batching: several independent Helmholtz problems,
+ * each with its own grids, omega, time step, Nt and alpha, advanced by the same kernel
+ * launches; an instance stops after its own M steps).  omegas: host array of one value per
+ * instance; infos (host, may be NULL) receives one time setup per instance. */
+wh_status wh_prepare_batch(wh_ctx *ctx, const double *omegas, wh_time_info *infos);
+
+/* Prepare frequency omega (every instance): the operator coefficients of the mapping method
  * (a_kl, b_k; Sec. 3.1) and the stability bound on the device, the time setup, the
  * per-point stencil weights, and the per-step tables.  Must follow the last
  * wh_add_grid / wh_set_interp / wh_set_forcing.  *info (may be NULL) receives the

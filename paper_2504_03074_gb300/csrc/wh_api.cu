@@ -80,9 +80,18 @@ struct wh_ctx {
   double *d_dw = nullptr;
   int64_t *d_ridx = nullptr;
   unsigned long long *d_smax = nullptr;
-  // time setup
+  // time setup: one per instance (ti mirrors instance 0)
   wh_time_info ti{};
-  std::vector<double> fc, wf;  // per step n: forcing factor, filter weight of level n
+  int ninst = 1;
+  std::vector<wh_time_info> iti;
+  std::vector<int64_t> icstart, icend, inact;  // compact segment and active points
+  std::vector<InstDev> hinst;                  // device structs (device table pointers)
+  std::vector<int8_t> iactive;
+  InstDev *d_inst = nullptr;
+  double *d_tabs = nullptr;
+  int64_t tabs_cap = 0;
+  int32_t *d_rinst = nullptr;
+  int maxM = 0;
 
   // solver workspace
   double *d_q = nullptr;  // Krylov basis
@@ -94,8 +103,6 @@ struct wh_ctx {
   int march_blocks = 0;
   // persistent path
   int iter_blocks = 0;
-  double *d_steps = nullptr;  // [3][M+1]: fc, cos, wf
-  int64_t steps_cap = 0;
   GridBarrier *d_bar = nullptr;
   int *h_err = nullptr;       // pinned copy of the barrier error flag
   int64_t *d_patch_off = nullptr;
@@ -163,8 +170,8 @@ void free_device(wh_ctx *ctx) {
   ctx->d_work = nullptr;
   ctx->d_partial = ctx->d_red = nullptr;
   ctx->red_cap = 0;
-  ctx->d_steps = nullptr;
-  ctx->steps_cap = 0;
+  ctx->d_tabs = nullptr;
+  ctx->tabs_cap = 0;
   ctx->d_bar = nullptr;
 }
 
@@ -276,6 +283,24 @@ wh_status build_layout(wh_ctx *ctx) {
   ctx->total = off;
   ctx->ncompact = coff;
   ctx->nactive = nact;
+  // instances: contiguous runs of grids
+  ctx->ninst = 0;
+  ctx->icstart.clear();
+  ctx->icend.clear();
+  ctx->inact.clear();
+  for (size_t g = 0; g < ctx->grids.size(); ++g) {
+    const int k = ctx->grids[g].d.instance;
+    if (k == ctx->ninst) {
+      ctx->icstart.push_back(ctx->hgrids[g].cbase);
+      ctx->icend.push_back(ctx->hgrids[g].cbase);
+      ctx->inact.push_back(0);
+      ++ctx->ninst;
+    }
+    ctx->hgrids[g].inst = k;
+    ctx->icend[k] = ctx->hgrids[g].cbase + (int64_t)ctx->hgrids[g].n0 * ctx->hgrids[g].n1;
+    for (int8_t m : ctx->grids[g].mask) ctx->inact[k] += m != WH_UNUSED;
+  }
+  ctx->iactive.assign(ctx->ninst, 1);
   ctx->nplanes5 = k5;
   ctx->nweights = woff;
 
@@ -340,6 +365,7 @@ wh_status build_layout(wh_ctx *ctx) {
         }
         it.g[0] = pt(-1);
         it.g[1] = order == 4 ? pt(-2) : pt(-1);
+        it.inst = ctx->hgrids[g].inst;
         ctx->hbc.push_back(it);
         ctx->hbc_grid.push_back((int32_t)g);
         ctx->hbc_axis.push_back(a);
@@ -360,6 +386,8 @@ wh_status build_layout(wh_ctx *ctx) {
     const DevGrid &RG = ctx->hgrids[rgr], &DG = ctx->hgrids[dgr];
     if (ctx->ri[r] < 0 || ctx->ri[r] >= RG.n0 || ctx->rj[r] < 0 || ctx->rj[r] >= RG.n1)
       return fail(ctx, WH_ERR_GRID, "receiver %lld outside its grid", (long long)r);
+    if (RG.inst != DG.inst)
+      return fail(ctx, WH_ERR_GRID, "receiver %lld interpolates across instances", (long long)r);
     const int64_t q = ext_index(RG, ctx->ri[r], ctx->rj[r]);
     if (mask[q] != WH_INTERP)
       return fail(ctx, WH_ERR_GRID, "receiver %lld is not an interpolation point", (long long)r);
@@ -460,7 +488,10 @@ wh_status build_layout(wh_ctx *ctx) {
       (st = dalloc(ctx, &ctx->d_bc_axis, ctx->hbc.size())) ||
       (st = dalloc(ctx, &ctx->d_bc_hi, ctx->hbc.size())) ||
       (st = dalloc(ctx, &ctx->d_didx, didx.size())) || (st = dalloc(ctx, &ctx->d_dw, dw.size())) ||
-      (st = dalloc(ctx, &ctx->d_ridx, ridx.size())) || (st = dalloc(ctx, &ctx->d_smax, 1)) ||
+      (st = dalloc(ctx, &ctx->d_ridx, ridx.size())) ||
+      (st = dalloc(ctx, &ctx->d_smax, (size_t)ctx->ninst)) ||
+      (st = dalloc(ctx, &ctx->d_inst, (size_t)ctx->ninst)) ||
+      (st = dalloc(ctx, &ctx->d_rinst, ridx.size())) ||
       (st = dalloc(ctx, &ctx->d_patch_off, patch_off.size())) ||
       (st = dalloc(ctx, &ctx->d_patch_pos, std::max<size_t>(patch_pos.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_patch_item, std::max<size_t>(patch_item.size(), 1))) ||
@@ -473,6 +504,11 @@ wh_status build_layout(wh_ctx *ctx) {
                   cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpy(ctx->d_recv_of, recv_of.data(), recv_of.size() * 4, cudaMemcpyHostToDevice));
+  {
+    std::vector<int32_t> rinst(ridx.size(), 0);
+    for (int64_t r = 0; r < ctx->nrecv; ++r) rinst[r] = ctx->hgrids[ctx->rg[r]].inst;
+    CK(cudaMemcpy(ctx->d_rinst, rinst.data(), rinst.size() * 4, cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(ctx->d_tiles, ctx->htiles.data(), ctx->htiles.size() * sizeof(Tile),
                 cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_mask, mask.data(), off, cudaMemcpyHostToDevice));
@@ -513,7 +549,8 @@ wh_status build_layout(wh_ctx *ctx) {
 }
 
 wh_status launch_steps(wh_ctx *ctx, int forcing) {
-  // the body of one iteration after init: t = 0 ghost rules + interpolation, then M steps
+  // the body of one iteration after init: level-0 ghost rules + interpolation, then the
+  // steps n = 0 .. maxM-1 (each instance stops after its own M steps)
   const int order = ctx->opt.order;
   const bool f32 = is_fp32(ctx);
   cudaStream_t s = ctx->stream;
@@ -526,25 +563,18 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
   const int ntiles = (int)ctx->htiles.size();
   const int nblocks = std::min(ntiles, ctx->march_blocks);
   void *Wa = ctx->d_Wa, *Wb = ctx->d_Wb;
-  const int M = ctx->ti.M;
-  auto bcg = [&](void *W, int n) {
+  auto bcg = [&](void *W, int level) {
     if (bg_blocks == 0) return;
     launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx, ctx->d_dw,
-                     ctx->d_ridx, (int)ctx->nrecv, W, ctx->d_F,
-                     fs * std::cos(ctx->ti.omega_e * n * ctx->ti.dt));
+                     ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, W, ctx->d_F, ctx->d_inst, level,
+                     fs);
   };
   bcg(Wa, 0);
-  // first step: W^1 = (sum w W^0)/2 - dt^2/2 f
-  launch_march(f32, order, true, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask,
-               Wa, Wb, ctx->d_F, ctx->d_Wt, ctx->d_V, fs * 0.5 * ctx->ti.dt * ctx->ti.dt,
-               ctx->wf[1], ctx->wf[0]);
-  bcg(Wb, 1);
-  for (int n = 1; n < M; ++n) {
+  for (int n = 0; n < ctx->maxM; ++n) {
     void *cur = (n & 1) ? Wb : Wa;
     void *oth = (n & 1) ? Wa : Wb;
-    launch_march(f32, order, false, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask,
-                 cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, fs * ctx->fc[n], ctx->wf[n + 1],
-                 ctx->wf[n]);
+    launch_march(f32, order, n == 0, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask,
+                 cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst, n, fs);
     bcg(oth, n + 1);
   }
   return WH_OK;
@@ -585,7 +615,6 @@ wh_status check_timeout(wh_ctx *ctx, bool wait) {
 wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
   wh_status st = check_timeout(ctx, false);
   if (st) return st;
-  const int M = ctx->ti.M;
   IterArgs A{};
   A.grids = ctx->d_grids;
   A.ngrids = (int)ctx->hgrids.size();
@@ -603,12 +632,10 @@ wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double
   A.dw = ctx->d_dw;
   A.ridx = ctx->d_ridx;
   A.nrecv = ctx->nrecv;
-  A.fc = ctx->d_steps;
-  A.cosn = ctx->d_steps + (M + 1);
-  A.wf = ctx->d_steps + 2 * (M + 1);
+  A.inst = ctx->d_inst;
+  A.rinst = ctx->d_rinst;
   A.fs = forcing ? 1.0 : 0.0;
-  A.dt2 = ctx->ti.dt * ctx->ti.dt;
-  A.M = M;
+  A.M = ctx->maxM;
   A.total = ctx->total;
   A.ncompact = ctx->ncompact;
   A.spin_limit = ctx->opt_spin_limit;
@@ -638,15 +665,14 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   const int64_t nb = (ctx->total + blk - 1) / blk;
   const int ng = (int)ctx->hgrids.size();
   launch_init(is_fp32(ctx), (unsigned)nb, ctx->stream, ctx->d_grids, ng, ctx->d_mask, vin,
-              ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
+              ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst);
   CK(cudaGetLastError());
   CK(cudaGraphLaunch(ctx->set[ctx->active].gexec[forcing], ctx->stream));
   const int64_t nc = (ctx->ncompact + blk - 1) / blk;
   launch_finish(is_fp32(ctx), (unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V,
-                (ctx->ti.M % 2 == 0) ? ctx->d_Wa : ctx->d_Wb, ctx->wf[ctx->ti.M], vout,
-                ctx->ncompact);
+                ctx->d_Wa, ctx->d_Wb, ctx->d_inst, vout, ctx->ncompact);
   CK(cudaGetLastError());
-  ctx->launches += 2 + 2 * (int64_t)ctx->ti.M + 1;
+  ctx->launches += 2 + 2 * (int64_t)ctx->maxM + 1;
   return WH_OK;
 }
 
@@ -904,6 +930,12 @@ wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *gd, int32_t *grid_id) {
         if (s / 2 != s2 / 2 && bc[s] == WH_BC_NEUMANN &&
             (bc[s2] == WH_BC_DIRICHLET || bc[s2] == WH_BC_NEUMANN))
           return fail(ctx, WH_ERR_GRID, "a Neumann side meets another physical side");
+  const int prev = ctx->grids.empty() ? -1 : ctx->grids.back().d.instance;
+  if (gd->instance != prev && gd->instance != prev + 1)
+    return fail(ctx, WH_ERR_ARG, "instance ids must be contiguous: got %d after %d",
+                gd->instance, prev);
+  if (ctx->grids.empty() && gd->instance != 0)
+    return fail(ctx, WH_ERR_ARG, "the first grid belongs to instance 0");
   HostGrid H;
   H.d = *gd;
   const int64_t n = (int64_t)gd->n[0] * gd->n[1];
@@ -975,9 +1007,10 @@ wh_status wh_set_forcing(wh_ctx *ctx, int32_t gid, const double *f) {
   return WH_OK;
 }
 
-wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
-  if (!ctx) return WH_ERR_ARG;
-  if (!(omega > 0) || !std::isfinite(omega)) return fail(ctx, WH_ERR_ARG, "omega must be > 0");
+// Prepare one frequency per instance: (a2) the operator coefficients and the per-instance
+// frozen-coefficient stability bounds on the device, (a1) the time setup of each instance
+// (Recipe OmegaTildeExplicit, alpha_d), the device step tables and the stencil weights.
+static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   if (ctx->grids.empty()) return fail(ctx, WH_ERR_STATE, "no grids");
   for (size_t g = 0; g < ctx->grids.size(); ++g)
     for (size_t q = 0; q < ctx->grids[g].mask.size(); ++q)
@@ -987,10 +1020,12 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
   if ((st = ensure_stream(ctx))) return st;
   if (ctx->dirty && (st = build_layout(ctx))) return st;
   drop_graphs(ctx);
-  const int order = ctx->opt.order;
+  const int order = ctx->opt.order, K = ctx->ninst;
+  for (int k = 0; k < K; ++k)
+    if (!(omegas[k] > 0) || !std::isfinite(omegas[k]))
+      return fail(ctx, WH_ERR_ARG, "omega of instance %d must be > 0", k);
   cudaStream_t s = ctx->stream;
-  // (a2) operator coefficients and the frozen-coefficient bound
-  CK(cudaMemsetAsync(ctx->d_smax, 0, sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(ctx->d_smax, 0, K * sizeof(unsigned long long), s));
   for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
     const DevGrid &G = ctx->hgrids[g];
     dim3 tb(32, 8), gb((G.n0 + 31) / 32, (G.n1 + 7) / 8);
@@ -998,58 +1033,74 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
                 ctx->d_coef, ctx->d_smax);
   }
   CK(cudaGetLastError());
-  unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(&bits, ctx->d_smax, sizeof bits, cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned long long> bits(K, 0);
+  CK(cudaMemcpyAsync(bits.data(), ctx->d_smax, K * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  double smax;
-  std::memcpy(&smax, &bits, sizeof smax);
-  if (!(smax > 0) || !std::isfinite(smax))
-    return fail(ctx, WH_ERR_GRID, "no discretization point (stability bound %g)", smax);
-  // (a1) time setup: Recipe OmegaTildeExplicit, alpha_d
   const double Cp = order == 2 ? 1.0 : std::sqrt(3.0) / 2.0;
-  const double dtmax = ctx->opt.cfl * Cp / std::sqrt(smax);
-  int Nt = (int)std::ceil(2.0 * M_PI / (omega * dtmax));
-  if (Nt < 2) Nt = 2;
-  double dt = 2.0 / omega * std::sin(M_PI / Nt);
-  while (dt > dtmax) {
-    ++Nt;
-    dt = 2.0 / omega * std::sin(M_PI / Nt);
-  }
-  const int M = ctx->opt.periods * Nt;
-  wh_time_info &ti = ctx->ti;
-  ti.omega = omega;
-  ti.dt = dt;
-  ti.omega_e = 2.0 * M_PI / (Nt * dt);
-  ti.alpha = ctx->opt.alpha_mode ? 0.5 : std::tan(ti.omega_e * dt / 2) / std::tan(ti.omega_e * dt);
-  ti.dt_max = dtmax;
-  ti.Tbar = M * dt;
-  ti.Nt = Nt;
-  ti.M = M;
-  ti.n_active = ctx->nactive;
-  ti.n_total = ctx->ncompact;
-  // per-step tables: forcing factor dt^2 cos(omega_e t^n), filter weight of level n
-  ctx->fc.assign(M + 1, 0.0);
-  ctx->wf.assign(M + 1, 0.0);
-  for (int n = 0; n <= M; ++n) {
-    const double cn = std::cos(ti.omega_e * n * dt);
-    ctx->fc[n] = dt * dt * cn;
-    const double sig = (n == 0 || n == M) ? 0.5 : 1.0;
-    ctx->wf[n] = (2.0 / M) * sig * (cn - ti.alpha / 2.0);
-  }
-  // the same tables on the device for the persistent kernel: fc, cos, wf
-  if (ctx->steps_cap < 3 * (int64_t)(M + 1)) {
-    if ((st = dalloc(ctx, &ctx->d_steps, 3 * (size_t)(M + 1)))) return st;
-    ctx->steps_cap = 3 * (int64_t)(M + 1);
-  }
-  {
-    std::vector<double> tab(3 * (size_t)(M + 1));
-    for (int n = 0; n <= M; ++n) {
-      tab[n] = ctx->fc[n];
-      tab[(M + 1) + n] = std::cos(ti.omega_e * n * dt);
-      tab[2 * (M + 1) + n] = ctx->wf[n];
+  ctx->iti.assign(K, wh_time_info{});
+  ctx->maxM = 0;
+  int64_t tab_len = 0;
+  for (int k = 0; k < K; ++k) {
+    double smax;
+    std::memcpy(&smax, &bits[k], sizeof smax);
+    if (!(smax > 0) || !std::isfinite(smax))
+      return fail(ctx, WH_ERR_GRID, "instance %d has no discretization point", k);
+    const double omega = omegas[k];
+    const double dtmax = ctx->opt.cfl * Cp / std::sqrt(smax);
+    int Nt = (int)std::ceil(2.0 * M_PI / (omega * dtmax));
+    if (Nt < 2) Nt = 2;
+    double dt = 2.0 / omega * std::sin(M_PI / Nt);
+    while (dt > dtmax) {
+      ++Nt;
+      dt = 2.0 / omega * std::sin(M_PI / Nt);
     }
-    CK(cudaMemcpy(ctx->d_steps, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+    wh_time_info &ti = ctx->iti[k];
+    ti.omega = omega;
+    ti.dt = dt;
+    ti.Nt = Nt;
+    ti.M = ctx->opt.periods * Nt;
+    ti.omega_e = 2.0 * M_PI / (Nt * dt);
+    ti.alpha = ctx->opt.alpha_mode ? 0.5
+                                   : std::tan(ti.omega_e * dt / 2) / std::tan(ti.omega_e * dt);
+    ti.dt_max = dtmax;
+    ti.Tbar = ti.M * dt;
+    ti.n_active = ctx->inact[k];
+    ti.n_total = ctx->icend[k] - ctx->icstart[k];
+    ctx->maxM = std::max(ctx->maxM, ti.M);
+    tab_len += 3 * (int64_t)(ti.M + 1);
   }
+  ctx->ti = ctx->iti[0];
+  // device tables: per instance fc[0..M], cos[0..M], wf[0..M]
+  if (ctx->tabs_cap < tab_len) {
+    if ((st = dalloc(ctx, &ctx->d_tabs, (size_t)tab_len))) return st;
+    ctx->tabs_cap = tab_len;
+  }
+  std::vector<double> tab((size_t)tab_len);
+  ctx->hinst.assign(K, InstDev{});
+  int64_t o = 0;
+  for (int k = 0; k < K; ++k) {
+    const wh_time_info &ti = ctx->iti[k];
+    const int M = ti.M;
+    for (int n = 0; n <= M; ++n) {
+      const double cn = std::cos(ti.omega_e * n * ti.dt);
+      const double sig = (n == 0 || n == M) ? 0.5 : 1.0;
+      tab[o + n] = ti.dt * ti.dt * cn;                                  // forcing factor
+      tab[o + (M + 1) + n] = cn;                                        // cos(omega_e t^n)
+      tab[o + 2 * (M + 1) + n] = (2.0 / M) * sig * (cn - ti.alpha / 2.0);  // filter weight
+    }
+    InstDev &I = ctx->hinst[k];
+    I.fc = ctx->d_tabs + o;
+    I.cosn = ctx->d_tabs + o + (M + 1);
+    I.wf = ctx->d_tabs + o + 2 * (M + 1);
+    I.dt2 = ti.dt * ti.dt;
+    I.M = M;
+    I.active = 1;
+    o += 3 * (int64_t)(M + 1);
+  }
+  ctx->iactive.assign(K, 1);
+  CK(cudaMemcpy(ctx->d_tabs, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_inst, ctx->hinst.data(), K * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (!ctx->h_err) {
     CK(cudaMallocHost(&ctx->h_err, sizeof(int)));
     *ctx->h_err = 0;
@@ -1058,25 +1109,24 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
   ctx->err_pending = false;
   if (ctx->persistent && ctx->iter_blocks < 1)
     return fail(ctx, WH_ERR_CUDA, "the persistent kernel cannot be resident on this device");
-  // stencil weights
-  const double dt2 = dt * dt;
+  // stencil weights, each grid with its instance's dt
   for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
     DevGrid &G = ctx->hgrids[g];
-    if (G.stencil == kConstCross) {
-      const double c2 = 1.0, x = dt2 * c2 / (G.h0 * G.h0), y = dt2 * c2 / (G.h1 * G.h1);
-      if (order == 2) {
-        G.cw[0] = 2.0 - 2.0 * x - 2.0 * y;
-        G.cw[1] = x;
-        G.cw[2] = 0.0;
-        G.cw[3] = y;
-        G.cw[4] = 0.0;
-      } else {
-        G.cw[0] = 2.0 - 2.5 * x - 2.5 * y;
-        G.cw[1] = 16.0 / 12.0 * x;
-        G.cw[2] = -1.0 / 12.0 * x;
-        G.cw[3] = 16.0 / 12.0 * y;
-        G.cw[4] = -1.0 / 12.0 * y;
-      }
+    if (G.stencil != kConstCross) continue;
+    const double dt2 = ctx->hinst[G.inst].dt2;
+    const double x = dt2 / (G.h0 * G.h0), y = dt2 / (G.h1 * G.h1);
+    if (order == 2) {
+      G.cw[0] = 2.0 - 2.0 * x - 2.0 * y;
+      G.cw[1] = x;
+      G.cw[2] = 0.0;
+      G.cw[3] = y;
+      G.cw[4] = 0.0;
+    } else {
+      G.cw[0] = 2.0 - 2.5 * x - 2.5 * y;
+      G.cw[1] = 16.0 / 12.0 * x;
+      G.cw[2] = -1.0 / 12.0 * x;
+      G.cw[3] = 16.0 / 12.0 * y;
+      G.cw[4] = -1.0 / 12.0 * y;
     }
   }
   CK(cudaMemcpyAsync(ctx->d_grids, ctx->hgrids.data(), ctx->hgrids.size() * sizeof(DevGrid),
@@ -1088,7 +1138,7 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
     for (const auto &S : ctx->set)
       if (S.present)
         launch_weight(S.fp32, order, gb, tb, s, ctx->d_grids, (int)g, ctx->d_mask, ctx->d_coef,
-                      ctx->d_c2, S.Wt, dt2);
+                      ctx->d_c2, S.Wt, ctx->hinst[G.inst].dt2);
   }
   const int nbc = (int)ctx->hbc.size();
   if (nbc)
@@ -1097,7 +1147,43 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   ctx->prepared = true;
-  if (info) *info = ti;
+  return WH_OK;
+}
+
+// Mark instances active (1) or skipped (0) for the following iterations.
+static wh_status set_active(wh_ctx *ctx, const std::vector<int8_t> &act) {
+  bool changed = false;
+  for (int k = 0; k < ctx->ninst; ++k)
+    if ((int)act[k] != ctx->hinst[k].active) {
+      ctx->hinst[k].active = act[k];
+      changed = true;
+    }
+  if (changed)
+    CK(cudaMemcpyAsync(ctx->d_inst, ctx->hinst.data(), ctx->ninst * sizeof(InstDev),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  ctx->iactive = act;
+  return WH_OK;
+}
+
+wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
+  if (!ctx) return WH_ERR_ARG;
+  if (!(omega > 0) || !std::isfinite(omega)) return fail(ctx, WH_ERR_ARG, "omega must be > 0");
+  if (ctx->grids.empty()) return fail(ctx, WH_ERR_STATE, "no grids");
+  const int K = ctx->grids.back().d.instance + 1;
+  std::vector<double> om(K, omega);
+  wh_status st = prepare_instances(ctx, om.data());
+  if (st) return st;
+  if (info) *info = ctx->ti;
+  return WH_OK;
+}
+
+wh_status wh_prepare_batch(wh_ctx *ctx, const double *omegas, wh_time_info *infos) {
+  if (!ctx || !omegas) return fail(ctx, WH_ERR_ARG, "null omegas");
+  if (ctx->grids.empty()) return fail(ctx, WH_ERR_STATE, "no grids");
+  wh_status st = prepare_instances(ctx, omegas);
+  if (st) return st;
+  if (infos)
+    for (int k = 0; k < ctx->ninst; ++k) infos[k] = ctx->iti[k];
   return WH_OK;
 }
 
@@ -1292,18 +1378,18 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
       void *cur = (r & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (r & 1) ? ctx->d_Wa : ctx->d_Wb;
       if (kind == 0)
         launch_march(f32, order, false, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles,
-                     ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->fc[1],
-                     ctx->wf[2], ctx->wf[1]);
+                     ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst, 1, 1.0);
       else if (kind == 1 && bg_blocks)
         launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx,
-                         ctx->d_dw, ctx->d_ridx, (int)ctx->nrecv, oth, ctx->d_F, 1.0);
+                         ctx->d_dw, ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, oth, ctx->d_F,
+                         ctx->d_inst, 1, 1.0);
       else if (kind == 2)
         launch_init(f32, (unsigned)((ctx->total + blk - 1) / blk), s, ctx->d_grids, ng,
-                    ctx->d_mask, ctx->d_work, ctx->d_Wa, ctx->d_V, ctx->total, ctx->wf[0]);
+                    ctx->d_mask, ctx->d_work, ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst);
       else if (kind == 3)
         launch_finish(f32, (unsigned)((ctx->ncompact + blk - 1) / blk), s, ctx->d_grids, ng,
-                      ctx->d_mask, ctx->d_V, ctx->d_Wa, ctx->wf[1], ctx->d_work + ctx->ncompact,
-                      ctx->ncompact);
+                      ctx->d_mask, ctx->d_V, ctx->d_Wa, ctx->d_Wb, ctx->d_inst,
+                      ctx->d_work + ctx->ncompact, ctx->ncompact);
     }
   };
   wh_status st;
@@ -1311,7 +1397,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int per_iter[4] = {ctx->ti.M, bg_blocks ? ctx->ti.M + 1 : 0, 1, 1};
+  const int per_iter[4] = {ctx->maxM, bg_blocks ? ctx->maxM + 1 : 0, 1, 1};
   for (int kind = 0; kind < 4; ++kind) {
     ms[kind] = 0.0;
     counts[kind] = per_iter[kind];

@@ -28,7 +28,7 @@ struct DevGrid {
   int32_t nw;               // weights per point (per-point stencils)
   int32_t kind;             // WH_CARTESIAN / WH_CURVILINEAR
   int32_t ortho;
-  int32_t pad_;
+  int32_t inst;             // instance (independent Helmholtz problem) of this grid
   int64_t base;             // offset of the extended array in the state arrays
   int64_t ext;              // pitch * (n1 + 2 g1)
   int64_t cbase;            // offset in compact vectors
@@ -46,9 +46,19 @@ struct BcItem {
   int64_t u[4];      // state indices of U0..U3 (boundary point and three inward)
   int64_t g[2];      // state indices of G1, G2 (G2 unused at order 2)
   int32_t type;      // 0: Neumann order 2, 1: Neumann order 4, 2: Dirichlet order 4
-  int32_t pad_;
+  int32_t inst;      // instance of the item's grid
   double A2, B1;     // Dirichlet order 4: a_nn/(12 h^2), +-b_n/(12 h) (c^2 folded)
   double inv;        // 1 / (11 A2 - 3 B1)
+};
+
+// Time tables of one instance on the device (Recipe OmegaTildeExplicit per instance).
+struct InstDev {
+  const double *fc;    // dt^2 cos(omega_e t^n), n = 0..M
+  const double *cosn;  // cos(omega_e t^n)
+  const double *wf;    // filter weights of level n
+  double dt2;
+  int M;               // steps of one iteration; steps n >= M are skipped
+  int active;          // 0: the instance is skipped entirely (converged in a batched solve)
 };
 
 // One tile of the march: a 32 x (8 kPY) block of points of one grid.
@@ -81,12 +91,10 @@ struct IterArgs {
   const double *dw;
   const int64_t *ridx;
   int64_t nrecv;
-  const double *fc;    // dt^2 cos(omega_e t^n), n = 0..M
-  const double *cosn;  // cos(omega_e t^n)
-  const double *wf;    // filter weights, n = 0..M
-  double fs;           // 1 with forcing, 0 without
-  double dt2;
-  int M;
+  const InstDev *inst;
+  const int32_t *rinst;  // instance of each receiver
+  double fs;             // 1 with forcing, 0 without
+  int M;                 // largest instance M
   int pad_;
   int64_t total, ncompact;
   unsigned long long spin_limit;
@@ -103,22 +111,23 @@ struct IterArgs {
 // carry T arrays.
 void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
-                  void *Wout, const void *F, const void *Wt, double *V, double fc,
-                  double wf_new, double wf_cur);
+                  void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
+                  int n, double fs);
 int march_blocks_per_sm(bool fp32, int order);
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
-                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos);
+                      const int64_t *ridx, const int32_t *rinst, int nrecv, void *W,
+                      const void *F, const InstDev *inst, int level, double fs);
 int iteration_blocks_per_sm(bool fp32, int order);
 cudaError_t launch_iteration(bool fp32, int order, int nblocks, cudaStream_t s,
                              const IterArgs &A, const double *v_in, double *v_out,
                              GridBarrier *bar);
 void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
                  const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
-                 double w0);
+                 const InstDev *inst);
 void launch_finish(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
-                   const int8_t *mask, const double *V, const void *WM, double wf_last,
-                   double *vout, int64_t ncompact);
+                   const int8_t *mask, const double *V, const void *Wa, const void *Wb,
+                   const InstDev *inst, double *vout, int64_t ncompact);
 void launch_coef(int order, dim3 gb, dim3 tb, cudaStream_t s, const DevGrid *grids, int gidx,
                  const int8_t *mask, const double *rx, const double *c2, double *coef,
                  unsigned long long *smax);

@@ -172,15 +172,20 @@ __device__ __forceinline__ void gather_group(int r, int lane, bool live,
 // ---------------------------------------------------------------------------------
 // Graph path: one launch per phase.
 // ---------------------------------------------------------------------------------
+// Step n of every active instance with n < M (FIRST: n = 0).
 template <typename T, int ORDER, bool FIRST>
 __global__ void __launch_bounds__(kTileX *kTileY)
     march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
                  const int8_t *__restrict__ mask, const T *Wn, T *Wout,
-                 const T *__restrict__ F, const T *__restrict__ Wt, double *V, T fc,
-                 double wf_new, double wf_cur) {
+                 const T *__restrict__ F, const T *__restrict__ Wt, double *V,
+                 const InstDev *__restrict__ inst, int n, double fs) {
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const Tile t = tiles[tile];
     const DevGrid &G = grids[t.grid];
+    const InstDev &I = inst[G.inst];
+    if (!I.active || n >= I.M) continue;
+    const T fc = (T)(FIRST ? 0.5 * fs * I.dt2 : fs * I.fc[n]);
+    const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
     const int i = t.i0 + (int)threadIdx.x;
     if (i >= G.n0) continue;
 #pragma unroll
@@ -195,21 +200,31 @@ __global__ void __launch_bounds__(kTileX *kTileY)
 // Ghost rules (blocks [0, bc_blocks)) and interpolation (the remaining blocks) of one
 // time level W.  The two are independent: ghost rules read only discretization/Dirichlet
 // points and donors are never ghosts or receivers.
+// Level `level` of every active instance with level <= M.
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256)
     bc_gather_kernel(const BcItem *__restrict__ bc, int nbc, int bc_blocks,
                      const int32_t *__restrict__ didx, const double *__restrict__ dw,
-                     const int64_t *__restrict__ ridx, int nrecv, T *W,
-                     const T *__restrict__ F, double fcos) {
+                     const int64_t *__restrict__ ridx, const int32_t *__restrict__ rinst,
+                     int nrecv, T *W, const T *__restrict__ F,
+                     const InstDev *__restrict__ inst, int level, double fs) {
   if ((int)blockIdx.x < bc_blocks) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nbc) bc_item<T>(bc[k], W, F, fcos);
+    if (k >= nbc) return;
+    const BcItem it = bc[k];
+    const InstDev &I = inst[it.inst];
+    if (I.active && level <= I.M) bc_item<T>(it, W, F, fs * I.cosn[level]);
     return;
   }
   constexpr int LANES = ORDER == 4 ? 8 : 4;
   const int gtid = (blockIdx.x - bc_blocks) * blockDim.x + threadIdx.x;
   const int r = gtid / LANES;
-  gather_group<T, ORDER>(r, threadIdx.x % LANES, r < nrecv, didx, dw, ridx, W);
+  bool live = r < nrecv;
+  if (live) {
+    const InstDev &I = inst[rinst[r]];
+    live = I.active && level <= I.M;
+  }
+  gather_group<T, ORDER>(r, threadIdx.x % LANES, live, didx, dw, ridx, W);
 }
 
 // W^0 = v on discretization and interpolation points, 0 elsewhere (ghosts included);
@@ -218,10 +233,13 @@ template <typename T>
 __device__ __forceinline__ void init_point(const DevGrid *__restrict__ grids, int ngrids,
                                            const int8_t *__restrict__ mask,
                                            const double *v, T *W0, double *V,
-                                           int64_t p, double w0) {
+                                           int64_t p, const InstDev *__restrict__ inst) {
   int g = 0;
   while (g + 1 < ngrids && p >= grids[g + 1].base) ++g;
   const DevGrid &G = grids[g];
+  const InstDev &I = inst[G.inst];
+  if (!I.active) return;
+  const double w0 = I.wf[0];
   const int64_t o = p - G.base;
   const int j = (int)(o / G.pitch) - G.g1;
   const int i = (int)(o % G.pitch) - G.g0;
@@ -236,35 +254,40 @@ __device__ __forceinline__ void init_point(const DevGrid *__restrict__ grids, in
 template <typename T>
 __global__ void init_kernel(const DevGrid *__restrict__ grids, int ngrids,
                             const int8_t *__restrict__ mask, const double *__restrict__ v,
-                            T *W0, double *V, int64_t total, double w0) {
+                            T *W0, double *V, int64_t total, const InstDev *__restrict__ inst) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < total) init_point<T>(grids, ngrids, mask, v, W0, V, p, w0);
+  if (p < total) init_point<T>(grids, ngrids, mask, v, W0, V, p, inst);
 }
 
 // v_out (compact) = V at active points, 0 at unused points; interpolation points first
-// receive the filter contribution wf_last * W^M of the last level.
+// receive the filter contribution wf_M W^M of their instance's last level M (in Wa when
+// M is even).  Inactive instances leave v_out untouched.
 template <typename T>
 __device__ __forceinline__ void finish_point(const DevGrid *__restrict__ grids, int ngrids,
                                              const int8_t *__restrict__ mask, const double *V,
-                                             const T *WM, double wf_last,
-                                             double *vout, int64_t c) {
+                                             const T *Wa, const T *Wb,
+                                             const InstDev *__restrict__ inst, double *vout,
+                                             int64_t c) {
   int g = 0;
   while (g + 1 < ngrids && c >= grids[g + 1].cbase) ++g;
   const DevGrid &G = grids[g];
+  const InstDev &I = inst[G.inst];
+  if (!I.active) return;
   const int64_t o = c - G.cbase;
   const int j = (int)(o / G.n0), i = (int)(o % G.n0);
   const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
   const int8_t m = mask[p];
-  vout[c] = m == 2 ? fma(wf_last, (double)WM[p], V[p]) : (m != 0 ? V[p] : 0.0);
+  const T *WM = (I.M % 2 == 0) ? Wa : Wb;
+  vout[c] = m == 2 ? fma(I.wf[I.M], (double)WM[p], V[p]) : (m != 0 ? V[p] : 0.0);
 }
 
 template <typename T>
 __global__ void finish_kernel(const DevGrid *__restrict__ grids, int ngrids,
                               const int8_t *__restrict__ mask, const double *__restrict__ V,
-                              const T *__restrict__ WM, double wf_last, double *vout,
-                              int64_t ncompact) {
+                              const T *Wa, const T *Wb, const InstDev *__restrict__ inst,
+                              double *vout, int64_t ncompact) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < ncompact) finish_point<T>(grids, ngrids, mask, V, WM, wf_last, vout, c);
+  if (c < ncompact) finish_point<T>(grids, ngrids, mask, V, Wa, Wb, inst, vout, c);
 }
 
 // ---------------------------------------------------------------------------------
@@ -371,14 +394,11 @@ __global__ void __launch_bounds__(kTileX *kTileY)
   const int M = A.M;
   // init: W^0 = v, V = w_0 W^0 (receivers' V accumulates from the first step on)
   for (int64_t p = gtid; p < A.total; p += nthreads)
-    init_point<T>(A.grids, A.ngrids, A.mask, v_in, Wa, A.V, p, A.wf[0]);
+    init_point<T>(A.grids, A.ngrids, A.mask, v_in, Wa, A.V, p, A.inst);
   if (!grid_sync(bar, nb, A.spin_limit)) return;
   for (int n = 0; n < M; ++n) {
     T *cur = (n & 1) ? Wb : Wa;
     T *oth = (n & 1) ? Wa : Wb;
-    const double fc = n == 0 ? 0.5 * A.fs * A.dt2 : A.fs * A.fc[n];
-    const double fcos = A.fs * A.cosn[n];
-    const double wf_new = A.wf[n + 1], wf_cur = A.wf[n];
     // dynamic tiles: a ticket counter per step parity; the other parity's counter (last
     // used one step ago, idle until after the next barrier) is reset here
     int *ctr = &bar->tile_ctr[n & 1][0];
@@ -391,6 +411,16 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       if (tid == 0) s_next = atomicAdd(ctr, 1);  // next ticket, in flight during this tile
       const Tile t = A.tiles[tile];
       const DevGrid &G = A.grids[t.grid];
+      const InstDev &I = A.inst[G.inst];
+      if (!I.active || n >= I.M) {  // block-uniform: skip the whole tile
+        __syncthreads();
+        tile = s_next;
+        __syncthreads();
+        continue;
+      }
+      const double fc = n == 0 ? 0.5 * A.fs * I.dt2 : A.fs * I.fc[n];
+      const double fcos = A.fs * I.cosn[n];
+      const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
       // stage W^n (tile + halo; wrapped on periodic axes, clamped into the extended array)
       for (int e = tid; e < SX * SY; e += kTileX * kTileY) {
         const int rr = e / SX, cc = e % SX;
@@ -479,11 +509,13 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     if (!grid_sync(bar, nb, A.spin_limit)) return;
   }
   // output; receivers add their level-M contribution, computed from their donors
-  const T *WM = (M % 2 == 0) ? Wa : Wb;
   for (int64_t c = gtid; c < A.ncompact; c += nthreads) {
     int g = 0;
     while (g + 1 < A.ngrids && c >= A.grids[g + 1].cbase) ++g;
     const DevGrid &G = A.grids[g];
+    const InstDev &I = A.inst[G.inst];
+    if (!I.active) continue;
+    const T *WM = (I.M % 2 == 0) ? Wa : Wb;
     const int64_t o = c - G.cbase;
     const int j = (int)(o / G.n0), i = (int)(o % G.n0);
     const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
@@ -491,7 +523,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     double val = 0.0;
     if (m == 1 || m == 3) val = A.V[p];
     else if (m == 2)
-      val = fma(A.wf[M], recv_value<T, ORDER>(A.recv_of[p], A.didx, A.dw, WM), A.V[p]);
+      val = fma(I.wf[I.M], recv_value<T, ORDER>(A.recv_of[p], A.didx, A.dw, WM), A.V[p]);
     v_out[c] = val;
   }
 }
@@ -563,7 +595,7 @@ __global__ void coef_kernel(const DevGrid *__restrict__ grids, int gidx,
     s = cc * (a11 / (G.h0 * G.h0) + a22 / (G.h1 * G.h1));
     if (!G.ortho) s += 2.0 * cc * fabs(a12) / (G.h0 * G.h1);
   }
-  if (m == 1) atomicMax(smax_bits, (unsigned long long)__double_as_longlong(s));
+  if (m == 1) atomicMax(smax_bits + G.inst, (unsigned long long)__double_as_longlong(s));
 }
 
 // Per-point stencil weights (dt^2 folded, centre + 2).  Cartesian grids with c(x) use
@@ -751,13 +783,13 @@ __global__ void gemv_acc(const double *__restrict__ X, int64_t ldx, int nv,
 
 void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
-                  void *Wout, const void *F, const void *Wt, double *V, double fc,
-                  double wf_new, double wf_cur) {
+                  void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
+                  int n, double fs) {
   const dim3 tb(kTileX, kTileY);
 #define WH_MARCH(T, O, FI)                                                                 \
   march_kernel<T, O, FI><<<nblocks, tb, 0, s>>>(grids, tiles, ntiles, mask, (const T *)Wn, \
                                                 (T *)Wout, (const T *)F, (const T *)Wt, V,  \
-                                                (T)fc, wf_new, wf_cur)
+                                                inst, n, fs)
   if (fp32) {
     if (order == 4) { if (first) WH_MARCH(float, 4, true); else WH_MARCH(float, 4, false); }
     else            { if (first) WH_MARCH(float, 2, true); else WH_MARCH(float, 2, false); }
@@ -770,10 +802,11 @@ void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cud
 
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
-                      const int64_t *ridx, int nrecv, void *W, const void *F, double fcos) {
-#define WH_BCG(T, O)                                                                      \
-  bc_gather_kernel<T, O><<<blocks, 256, 0, s>>>(bc, nbc, bc_blocks, didx, dw, ridx, nrecv, \
-                                                (T *)W, (const T *)F, fcos)
+                      const int64_t *ridx, const int32_t *rinst, int nrecv, void *W,
+                      const void *F, const InstDev *inst, int level, double fs) {
+#define WH_BCG(T, O)                                                                   \
+  bc_gather_kernel<T, O><<<blocks, 256, 0, s>>>(bc, nbc, bc_blocks, didx, dw, ridx, rinst, \
+                                                nrecv, (T *)W, (const T *)F, inst, level, fs)
   if (fp32) { if (order == 4) WH_BCG(float, 4); else WH_BCG(float, 2); }
   else      { if (order == 4) WH_BCG(double, 4); else WH_BCG(double, 2); }
 #undef WH_BCG
@@ -781,22 +814,23 @@ void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const Bc
 
 void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
                  const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
-                 double w0) {
+                 const InstDev *inst) {
   if (fp32)
-    init_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (float *)W0, V, total, w0);
+    init_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (float *)W0, V, total, inst);
   else
-    init_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (double *)W0, V, total, w0);
+    init_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (double *)W0, V, total,
+                                               inst);
 }
 
 void launch_finish(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
-                   const int8_t *mask, const double *V, const void *WM, double wf_last,
-                   double *vout, int64_t ncompact) {
+                   const int8_t *mask, const double *V, const void *Wa, const void *Wb,
+                   const InstDev *inst, double *vout, int64_t ncompact) {
   if (fp32)
-    finish_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, (const float *)WM, wf_last,
-                                                vout, ncompact);
+    finish_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, (const float *)Wa,
+                                                (const float *)Wb, inst, vout, ncompact);
   else
-    finish_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, (const double *)WM,
-                                                 wf_last, vout, ncompact);
+    finish_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, V, (const double *)Wa,
+                                                 (const double *)Wb, inst, vout, ncompact);
 }
 
 int march_blocks_per_sm(bool fp32, int order) {

@@ -49,6 +49,7 @@ class Grid:
     orthogonal: bool = True       # grid lines meet at right angles (a12 == 0 identically)
     rx: np.ndarray | None = None  # float64 (4, n1+2g1, n0+2g0): dr1/dx, dr1/dy, dr2/dx, dr2/dy
     origin: tuple = (0.0, 0.0)    # Cartesian: coordinates of point (0, 0)
+    instance: int = 0             # independent problem of a batch
 
     def ghosts(self, order):
         return tuple(0 if self.bc[2 * a] == BC_PERIODIC else order // 2 for a in (0, 1))
@@ -409,6 +410,51 @@ def sheared_torus_problem(n0=32, n1=28, order=4, omega=9.0, seed=0):
     f = gaussian(g.xy, x0, 1.0, 30.0)
     return Problem([g], Interp.empty(order), order, omega, [f], None,
                    name=f"sheared-torus-{n0}x{n1}-o{order}", meta=dict(x0=x0.tolist()))
+
+
+def batch_problems(problems):
+    """Concatenate independent problems (same order p) into one batch: grid k of problem i
+    keeps its data and gets instance i; the batch's omega is the list of omegas."""
+    import copy
+    order = problems[0].order
+    grids, f, c2, recv = [], [], [], []
+    any_c2 = any(p.c2 is not None for p in problems)
+    goff = 0
+    for k, p in enumerate(problems):
+        assert p.order == order
+        for gi, g in enumerate(p.grids):
+            g2 = copy.copy(g)
+            g2.instance = k
+            grids.append(g2)
+            f.append(p.f[gi])
+            c2.append(p.c2[gi] if p.c2 is not None else np.ones(g.mask.shape))
+        it = p.interp
+        recv.append((it.recv_grid + goff, it.recv_i, it.recv_j, it.donor_grid + goff,
+                     it.donor_i0, it.donor_j0, it.wx, it.wy))
+        goff += len(p.grids)
+    cols = list(zip(*recv))
+    interp = Interp(*[np.concatenate(c).astype(np.int32) for c in cols[:6]],
+                    np.concatenate(cols[6]), np.concatenate(cols[7]))
+    return Problem(grids, interp, order, [p.omega for p in problems], f,
+                   c2 if any_c2 else None, name=f"batch-{len(problems)}",
+                   meta=dict(members=[p.name for p in problems],
+                             sizes=[p.n_total for p in problems]))
+
+
+def batch_disk_problem(n_inst=256, seed=0, nb_range=(256, 1024), omega_range=(10.0, 50.0),
+                       order=4, src_range=(1, 4), width=0.3, r_cut=0.65):
+    """Uneven batch of disk-in-square problems: background N ~ U{nb_range} (N^2 points),
+    annulus 2N x N/16, omega ~ U[omega_range], 1-4 seeded Gaussian sources each."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(n_inst):
+        nb = int(rng.integers(nb_range[0], nb_range[1] + 1))
+        om = float(rng.uniform(*omega_range))
+        ns = int(rng.integers(src_range[0], src_range[1] + 1))
+        probs.append(disk_problem(nb=nb, nth=2 * nb, nr=max(nb // 16, 8 + order), order=order,
+                                  omega=om, seed=int(rng.integers(1 << 30)), n_src=ns,
+                                  width=width, r_cut=r_cut))
+    return batch_problems(probs), probs
 
 
 def random_state(problem, seed):

@@ -40,7 +40,8 @@ class Options(C.Structure):
 
 class GridDesc(C.Structure):
     _fields_ = [("n", C.c_int32 * 2), ("kind", C.c_int32), ("bc", C.c_int32 * 4),
-                ("orthogonal", C.c_int32), ("h", C.c_double * 2), ("mask", C.c_void_p),
+                ("orthogonal", C.c_int32), ("instance", C.c_int32), ("h", C.c_double * 2),
+                ("mask", C.c_void_p),
                 ("rx", C.c_void_p), ("c2", C.c_void_p)]
 
 
@@ -69,7 +70,7 @@ class Stats(C.Structure):
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
-           "wh_profile_kernels", "wh_multidot_noalloc"]
+           "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch"]
 
 
 def lib_path():
@@ -97,6 +98,7 @@ def lib():
     L.wh_set_interp.argtypes = [vp, C.POINTER(InterpDesc)]
     L.wh_set_forcing.argtypes = [vp, C.c_int32, vp]
     L.wh_prepare.argtypes = [vp, C.c_double, C.POINTER(TimeInfo)]
+    L.wh_prepare_batch.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(TimeInfo)]
     L.wh_iterate.argtypes = [vp, C.c_int32, vp, vp]
     L.wh_iterate_host.argtypes = [vp, C.c_int32, vp, vp]
     L.wh_solve.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, vp,
@@ -155,6 +157,7 @@ class Solver:
             for s in range(4):
                 d.bc[s] = g.bc[s]
             d.orthogonal = int(g.orthogonal)
+            d.instance = int(getattr(g, "instance", 0))
             d.h[0], d.h[1] = g.h
             d.mask, d.rx, d.c2 = _ptr(mask), _ptr(rx), _ptr(c2)
             gid = C.c_int32()
@@ -194,10 +197,21 @@ class Solver:
         self._torch.cuda.current_stream().wait_stream(self.stream)
 
     def prepare(self, omega=None):
+        """Prepare one frequency (a list: one per instance of a batch); returns the time
+        setup (a list of them for a batch)."""
+        om = self.problem.omega if omega is None else omega
+        if isinstance(om, (list, tuple, np.ndarray)):
+            k = len(om)
+            arr = (C.c_double * k)(*[float(x) for x in om])
+            infos = (TimeInfo * k)()
+            self._check(self.L.wh_prepare_batch(self.h, arr, infos))
+            self.infos = list(infos)
+            self.info = self.infos[0]
+            return self.infos
         ti = TimeInfo()
-        self._check(self.L.wh_prepare(self.h, self.problem.omega if omega is None else omega,
-                                      C.byref(ti)))
+        self._check(self.L.wh_prepare(self.h, om, C.byref(ti)))
         self.info = ti
+        self.infos = [ti]
         return ti
 
     @property

@@ -52,6 +52,7 @@ def _desc(W, g):
     for s in range(4):
         d.bc[s] = g.bc[s]
     d.orthogonal = int(g.orthogonal)
+    d.instance = int(getattr(g, "instance", 0))
     d.h[0], d.h[1] = g.h
     keep = [np.ascontiguousarray(g.mask, np.int8)]
     d.mask = keep[0].ctypes.data
@@ -108,6 +109,11 @@ def test_grid_validation_on_host(W):
         d, keep = _desc(W, g)
         assert L.wh_add_grid(h, C.byref(d), C.byref(gid)) == 0
     assert gid.value == 1
+    # instance ids must start at 0 and be contiguous
+    g = G.cartesian_grid("c", 16, 16, 0, 1, 0, 1, [1, 1, 1, 1], 4)
+    g.instance = 3
+    d, keep = _desc(W, g)
+    assert L.wh_add_grid(h, C.byref(d), C.byref(gid)) == -1
     # interpolation with an out-of-range grid index: rejected on the host
     it = prob.interp
     rg = np.ascontiguousarray(it.recv_grid, np.int32).copy()
