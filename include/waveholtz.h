@@ -213,6 +213,15 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, doub
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
                    double *u, wh_stats *stats, double *history, int32_t history_cap);
 
+/* Batched solve: one GMRES per instance (restart cycles of the same length), all advancing
+ * in lockstep around one batched wave solve per Arnoldi step; an instance that reaches
+ * ||b_k - A_k u_k|| <= tol ||b_k|| (checked with the FP64 march) is switched off in the
+ * kernels.  FP32 contexts refine each instance as wh_solve does.  u: DEVICE compact vector
+ * of all instances (initial guess in, solutions out); stats: host array of one entry per
+ * instance (seconds is the whole batch's).  max_it bounds the batched wave solves. */
+wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,
+                         wh_stats *stats);
+
 /* FP64 inner product <x, y> over n entries of two DEVICE vectors (the GMRES reduction:
  * warp-shuffle partial sums, then one deterministic pass).  *out is a host scalar.  n = 0
  * gives 0 (x, y may then be NULL). */

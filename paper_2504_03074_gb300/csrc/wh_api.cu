@@ -720,6 +720,21 @@ wh_status ensure_stream(wh_ctx *ctx) {
   return WH_OK;
 }
 
+// Mark instances active (1) or skipped (0) for the following iterations.
+wh_status set_active(wh_ctx *ctx, const std::vector<int8_t> &act) {
+  bool changed = false;
+  for (int k = 0; k < ctx->ninst; ++k)
+    if ((int)act[k] != ctx->hinst[k].active) {
+      ctx->hinst[k].active = act[k];
+      changed = true;
+    }
+  if (changed)
+    CK(cudaMemcpyAsync(ctx->d_inst, ctx->hinst.data(), ctx->ninst * sizeof(InstDev),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  ctx->iactive = act;
+  return WH_OK;
+}
+
 unsigned grid1d(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (unsigned)std::min<int64_t>(b, 152 * 16);
@@ -827,6 +842,130 @@ wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero,
   if (kk) {
     CK(cudaMemcpyAsync(ctx->d_red, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_gemv_acc(grid1d(n), s, Q, n, kk, ctx->d_red, x, n);
+  }
+  CK(cudaGetLastError());
+  return WH_OK;
+}
+
+// ---- batched GMRES: one GMRES per instance, all advancing in lockstep around one
+// batched wave solve per Arnoldi step (instances that are done are switched off) ----
+struct InstGmres {
+  int64_t off = 0, len = 0;
+  double bnorm = 0.0, tol_abs = 0.0, res = 0.0;
+  bool converged = false, in_cycle = false, finite = true;
+  int kk = 0, products = 0, products32 = 0;
+  std::vector<double> H, cs, sn, g, y;
+};
+
+// y = A x on the instances marked in `act` (w0 scratch); products counted per instance
+wh_status apply_A_batch(wh_ctx *ctx, const double *x, double *y, double *w0,
+                        std::vector<InstGmres> &I, const std::vector<int8_t> &act) {
+  wh_status st = set_active(ctx, act);
+  if (st) return st;
+  if ((st = iterate_device(ctx, 0, x, w0))) return st;
+  for (size_t k = 0; k < I.size(); ++k)
+    if (act[k]) (ctx->active == 1 ? I[k].products32 : I[k].products) += 1;
+  launch_sub(grid1d(ctx->ncompact), ctx->stream, x, w0, y, ctx->ncompact);
+  return WH_OK;
+}
+
+// One lockstep restart cycle on A x = rhs for the instances with in_cycle set; each keeps
+// going until its residual estimate reaches its tol_abs, then leaves the cycle.
+wh_status gmres_cycle_batch(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero, int m,
+                            int &budget, std::vector<InstGmres> &I) {
+  const int64_t n = ctx->ncompact;
+  const int K = (int)I.size();
+  cudaStream_t s = ctx->stream;
+  double *w0 = ctx->d_work, *r = ctx->d_work + n;
+  double *Q = ctx->d_q;
+  wh_status st;
+  std::vector<int8_t> act(K, 0);
+  for (int k = 0; k < K; ++k) act[k] = I[k].in_cycle;
+  if (x_is_zero) {
+    CK(cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    if ((st = apply_A_batch(ctx, x, r, w0, I, act))) return st;
+    launch_axpby(grid1d(n), s, 1.0, rhs, -1.0, r, n);
+    --budget;
+  }
+  for (int k = 0; k < K; ++k) {
+    InstGmres &G = I[k];
+    if (!G.in_cycle) continue;
+    double rr;
+    if ((st = multidot(ctx, r + G.off, 0, 1, r + G.off, G.len, &rr))) return st;
+    const double beta = std::sqrt(rr);
+    G.res = beta;
+    G.kk = 0;
+    if (!std::isfinite(beta)) G.finite = false;
+    if (!std::isfinite(beta) || beta <= G.tol_abs) {
+      G.in_cycle = false;
+      continue;
+    }
+    G.H.assign((size_t)(m + 1) * m, 0.0);
+    G.cs.assign(m, 0.0);
+    G.sn.assign(m, 0.0);
+    G.g.assign(m + 1, 0.0);
+    G.y.assign(m, 0.0);
+    G.g[0] = beta;
+    launch_axpby(grid1d(G.len), s, 1.0 / beta, r + G.off, 0.0, Q + G.off, G.len);
+  }
+  std::vector<double> h(m + 1);
+  std::vector<int8_t> live(K);
+  for (int k = 0; k < K; ++k) live[k] = I[k].in_cycle;
+  for (int j = 0; j < m && budget > 0; ++j) {
+    bool any = false;
+    for (int k = 0; k < K; ++k) any |= live[k] != 0;
+    if (!any) break;
+    if ((st = apply_A_batch(ctx, Q + (int64_t)j * n, Q + (int64_t)(j + 1) * n, w0, I, live)))
+      return st;
+    --budget;
+    for (int k = 0; k < K; ++k) {
+      if (!live[k]) continue;
+      InstGmres &G = I[k];
+      double *Qs = Q + G.off, *w = Q + (int64_t)(j + 1) * n + G.off;
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((st = multidot(ctx, Qs, n, j + 1, w, G.len, h.data()))) return st;
+        launch_multi_axpy(grid1d(G.len), s, Qs, n, j + 1, ctx->d_red, w, G.len);
+        for (int i = 0; i <= j; ++i) G.H[(size_t)i * m + j] += h[i];
+      }
+      double ww;
+      if ((st = multidot(ctx, w, 0, 1, w, G.len, &ww))) return st;
+      const double hk1 = std::sqrt(ww);
+      if (hk1 > 0) launch_axpby(grid1d(G.len), s, 0.0, w, 1.0 / hk1, w, G.len);
+      for (int i = 0; i < j; ++i) {
+        const double t = G.cs[i] * G.H[(size_t)i * m + j] + G.sn[i] * G.H[(size_t)(i + 1) * m + j];
+        G.H[(size_t)(i + 1) * m + j] =
+            -G.sn[i] * G.H[(size_t)i * m + j] + G.cs[i] * G.H[(size_t)(i + 1) * m + j];
+        G.H[(size_t)i * m + j] = t;
+      }
+      const double hjj = G.H[(size_t)j * m + j];
+      const double den = std::hypot(hjj, hk1);
+      G.cs[j] = hjj / den;
+      G.sn[j] = hk1 / den;
+      G.H[(size_t)j * m + j] = den;
+      G.g[j + 1] = -G.sn[j] * G.g[j];
+      G.g[j] = G.cs[j] * G.g[j];
+      G.kk = j + 1;
+      G.res = std::fabs(G.g[j + 1]);
+      if (!std::isfinite(G.res)) {
+        G.finite = false;
+        live[k] = 0;
+      } else if (G.res <= G.tol_abs || hk1 == 0) {
+        live[k] = 0;
+      }
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    InstGmres &G = I[k];
+    if (!G.in_cycle || G.kk == 0 || !G.finite) continue;
+    for (int i = G.kk - 1; i >= 0; --i) {
+      double t = G.g[i];
+      for (int jj = i + 1; jj < G.kk; ++jj) t -= G.H[(size_t)i * m + jj] * G.y[jj];
+      G.y[i] = t / G.H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(ctx->d_red, G.y.data(), G.kk * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gemv_acc(grid1d(G.len), s, Q + G.off, n, G.kk, ctx->d_red, x + G.off, G.len);
+    CK(cudaStreamSynchronize(s));  // d_red is reused by the next instance
   }
   CK(cudaGetLastError());
   return WH_OK;
@@ -1150,21 +1289,6 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   return WH_OK;
 }
 
-// Mark instances active (1) or skipped (0) for the following iterations.
-static wh_status set_active(wh_ctx *ctx, const std::vector<int8_t> &act) {
-  bool changed = false;
-  for (int k = 0; k < ctx->ninst; ++k)
-    if ((int)act[k] != ctx->hinst[k].active) {
-      ctx->hinst[k].active = act[k];
-      changed = true;
-    }
-  if (changed)
-    CK(cudaMemcpyAsync(ctx->d_inst, ctx->hinst.data(), ctx->ninst * sizeof(InstDev),
-                       cudaMemcpyHostToDevice, ctx->stream));
-  ctx->iactive = act;
-  return WH_OK;
-}
-
 wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
   if (!ctx) return WH_ERR_ARG;
   if (!(omega > 0) || !std::isfinite(omega)) return fail(ctx, WH_ERR_ARG, "omega must be > 0");
@@ -1355,6 +1479,131 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "inner GMRES residual is not finite"));
     launch_axpby(grid1d(n), s, 1.0, d, 1.0, u, n);  // u += d
   }
+}
+
+wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,
+                         wh_stats *stats) {
+  if (!ctx || !u || !(tol > 0) || max_it < 1 || restart < 1 || restart > 4000)
+    return fail(ctx, WH_ERR_ARG, "bad wh_solve_batch arguments");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = ctx->ncompact;
+  const int K = ctx->ninst, m = restart;
+  cudaStream_t s = ctx->stream;
+  wh_status st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
+  if (ctx->q_cap < (int64_t)(m + 1) * n) {
+    if ((st = dalloc(ctx, &ctx->d_q, (size_t)(m + 1) * n))) return st;
+    ctx->q_cap = (int64_t)(m + 1) * n;
+  }
+  if ((st = ensure_red(ctx, m + 1))) return st;
+  ctx->launches = 0;
+  std::vector<InstGmres> I(K);
+  for (int k = 0; k < K; ++k) {
+    I[k].off = ctx->icstart[k];
+    I[k].len = ctx->icend[k] - ctx->icstart[k];
+  }
+  double *w0 = ctx->d_work, *b = ctx->d_work + 2 * n, *r = ctx->d_work + 3 * n,
+         *d = ctx->d_work + 4 * n;
+  std::vector<int8_t> all(K, 1);
+  auto finish = [&](wh_status code) {
+    std::vector<int8_t> on(K, 1);
+    set_active(ctx, on);
+    use_set(ctx, default_set(ctx));
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats)
+      for (int k = 0; k < K; ++k) {
+        wh_stats &S = stats[k];
+        S = wh_stats{};
+        S.products_fp64 = I[k].products;
+        S.products_fp32 = I[k].products32;
+        S.iterations = I[k].products + I[k].products32;
+        S.converged = I[k].converged;
+        S.residual = I[k].bnorm > 0 ? I[k].res / I[k].bnorm : 0.0;
+        S.seconds = sec;
+      }
+    return code;
+  };
+  // b = W_h(0, f) with the FP64 march, all instances
+  use_set(ctx, 0);
+  CK(cudaMemsetAsync(w0, 0, n * sizeof(double), s));
+  if ((st = set_active(ctx, all)) || (st = iterate_device(ctx, 1, w0, b))) return finish(st);
+  for (int k = 0; k < K; ++k) {
+    I[k].products += 1;
+    double bb;
+    if ((st = multidot(ctx, b + I[k].off, 0, 1, b + I[k].off, I[k].len, &bb))) return finish(st);
+    I[k].bnorm = std::sqrt(bb);
+    if (!(I[k].bnorm > 0)) {
+      I[k].converged = true;
+      CK(cudaMemsetAsync(u + I[k].off, 0, I[k].len * sizeof(double), s));
+    }
+  }
+  int budget = max_it - 1;
+  auto all_done = [&]() {
+    for (auto &G : I)
+      if (!G.converged) return false;
+    return true;
+  };
+  if (default_set(ctx) == 0) {
+    while (!all_done() && budget > 0) {
+      for (auto &G : I) {
+        G.in_cycle = !G.converged;
+        G.tol_abs = tol * G.bnorm;
+      }
+      if ((st = gmres_cycle_batch(ctx, b, u, false, m, budget, I))) return finish(st);
+      for (auto &G : I)
+        if (!G.finite) return finish(fail(ctx, WH_ERR_DIVERGED, "batched GMRES: non-finite"));
+      // confirm with true residuals at the start of the next cycle; here a separate check
+      std::vector<int8_t> act(K, 0);
+      for (int k = 0; k < K; ++k) act[k] = !I[k].converged;
+      if ((st = apply_A_batch(ctx, u, r, w0, I, act))) return finish(st);
+      --budget;
+      launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);
+      for (int k = 0; k < K; ++k) {
+        if (!act[k]) continue;
+        double rr;
+        if ((st = multidot(ctx, r + I[k].off, 0, 1, r + I[k].off, I[k].len, &rr)))
+          return finish(st);
+        I[k].res = std::sqrt(rr);
+        if (I[k].res <= tol * I[k].bnorm) I[k].converged = true;
+      }
+    }
+  } else {
+    // FP32 march: per-instance iterative refinement, lockstep
+    while (budget > 0) {
+      use_set(ctx, 0);
+      std::vector<int8_t> act(K, 0);
+      for (int k = 0; k < K; ++k) act[k] = !I[k].converged;
+      if ((st = apply_A_batch(ctx, u, r, w0, I, act))) return finish(st);
+      --budget;
+      launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);
+      for (int k = 0; k < K; ++k) {
+        if (!act[k]) continue;
+        double rr;
+        if ((st = multidot(ctx, r + I[k].off, 0, 1, r + I[k].off, I[k].len, &rr)))
+          return finish(st);
+        I[k].res = std::sqrt(rr);
+        if (!std::isfinite(I[k].res))
+          return finish(fail(ctx, WH_ERR_DIVERGED, "batched refinement: non-finite"));
+        if (I[k].res <= tol * I[k].bnorm) I[k].converged = true;
+      }
+      if (all_done() || budget <= 0) break;
+      use_set(ctx, 1);
+      CK(cudaMemsetAsync(d, 0, n * sizeof(double), s));
+      for (auto &G : I) {
+        G.in_cycle = !G.converged;
+        G.tol_abs = std::max(1e-4 * G.res, 0.5 * tol * G.bnorm);
+      }
+      const double *rc = r;
+      if ((st = gmres_cycle_batch(ctx, rc, d, true, m, budget, I))) return finish(st);
+      for (int k = 0; k < K; ++k)
+        if (!I[k].converged)
+          launch_axpby(grid1d(I[k].len), s, 1.0, d + I[k].off, 1.0, u + I[k].off, I[k].len);
+    }
+  }
+  if (all_done()) return finish(WH_OK);
+  return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "batched GMRES: budget of %d wave solves used",
+                     max_it));
 }
 
 wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts) {

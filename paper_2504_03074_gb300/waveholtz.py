@@ -70,7 +70,7 @@ class Stats(C.Structure):
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
-           "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch"]
+           "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch"]
 
 
 def lib_path():
@@ -104,6 +104,7 @@ def lib():
     L.wh_solve.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, vp,
                            C.POINTER(Stats), vp, C.c_int32]
     L.wh_dot.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_double)]
+    L.wh_solve_batch.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(Stats)]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -252,6 +253,20 @@ class Solver:
         st.history = hist[:st.n_history].copy()
         st.status = STATUS.get(status, status)
         return st
+
+    def solve_batch(self, u, tol=1e-8, max_it=500, restart=50):
+        """Batched solve of every instance in place on device tensor u; list of Stats."""
+        k = len(self.infos)
+        st = (Stats * k)()
+        self._enter()
+        status = self.L.wh_solve_batch(self.h, tol, max_it, restart, _ptr(u), st)
+        self._leave()
+        if status not in (WH_OK, -6):
+            self._check(status)
+        out = list(st)
+        for x in out:
+            x.status = STATUS.get(status, status)
+        return out
 
     def dot(self, x, y):
         out = C.c_double()

@@ -59,3 +59,25 @@ def test_batched_iteration_matches_each_instance(torch, W, oracle_mod, batch, mo
             err = np.max(np.abs(seg - ref)[act]) / np.max(np.abs(ref)[act])
             assert err <= tol, (k, forcing, err)
             off += p.n_total
+
+
+@pytest.mark.parametrize("prec,tol,bound", [("fp64", 1e-11, 1e-8), ("fp32", 1e-11, 1e-6)])
+def test_batched_solve_reaches_each_direct_solution(torch, W, batch, prec, tol, bound):
+    import dhs
+    bp, probs = batch
+    s = W.Solver(bp, precision=W.FP32 if prec == "fp32" else W.FP64)
+    s.prepare()
+    u = torch.zeros(bp.n_total, dtype=torch.float64, device="cuda")
+    stats = s.solve_batch(u, tol=tol, max_it=3000, restart=300)
+    assert all(st.converged == 1 for st in stats), [(st.residual, st.iterations) for st in stats]
+    sol = u.cpu().numpy()
+    off = 0
+    for k, p in enumerate(probs):
+        U = dhs.solve(p)
+        act = np.concatenate([(g.mask != 0).ravel() for g in p.grids])
+        seg = sol[off:off + p.n_total]
+        err = np.max(np.abs(seg - U)[act]) / np.max(np.abs(U)[act])
+        assert err <= bound, (k, err, stats[k].iterations)
+        off += p.n_total
+    if prec == "fp32":
+        assert all(st.products_fp32 > st.products_fp64 for st in stats)
