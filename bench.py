@@ -149,6 +149,99 @@ def cpu_baseline(problem, sample):
             "sample": sample, "seconds": dt}
 
 
+def time_iterations(WH, torch, solver, n_total, stream, flush, reps, warm=2):
+    """Device time (s) per WaveHoltz iteration, CUDA events on the library's stream, L2
+    flushed between iterations."""
+    a = torch.zeros(n_total, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            solver.iterate(a, b, True)
+            a, b = b, a
+        tot = 0.0
+        for k in range(reps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.iterate(a, b, True)
+            e1.record(stream)
+            a, b = b, a
+            stream.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+    return tot / reps
+
+
+def measure_forms(WH, G, torch, prob, stream, flush, rank):
+    """The FP32-march form on the same workload, the 256-instance batch (batched FP32 and
+    FP64 iterations vs plain per-instance FP64 iterations on a sample of instances), and
+    time to 1e-6 relative error on the 64^2 unit square."""
+    out = {}
+    s32 = WH.Solver(prob, stream=stream, precision=WH.FP32)
+    ti = s32.prepare()
+    t32 = time_iterations(WH, torch, s32, prob.n_total, stream, flush, 5)
+    out["fp32_march"] = {"value": ti.n_active * ti.M / t32 / 1e9, "unit": "GLUP/s",
+                         "ms_per_iteration": t32 * 1e3,
+                         "workload": "same disk-in-square workload, FP32 march, FP64 filter"}
+    s32.close()
+    # batch: 256 disk-in-square instances, N ~ U{256..1024}, annulus 2N x N/16,
+    # omega ~ U[10, 50], 1-4 sources
+    t0 = time.perf_counter()
+    bp, probs = G.batch_disk_problem(256, seed=100 + rank)
+    gen_s = time.perf_counter() - t0
+    res = {"instances": len(probs), "points": bp.n_total,
+           "active_points": int(sum(p.n_active for p in probs)), "generate_s": gen_s}
+    for name, prec in (("fp32", WH.FP32), ("fp64", WH.FP64)):
+        sb = WH.Solver(bp, stream=stream, precision=prec)
+        infos = sb.prepare()
+        lups = sum(t.n_active * t.M for t in infos)
+        tb = time_iterations(WH, torch, sb, bp.n_total, stream, flush, 2, warm=1)
+        res[f"batched_{name}"] = {"value": lups / tb / 1e9, "unit": "GLUP/s",
+                                  "s_per_iteration": tb}
+        sb.close()
+        del sb
+    # plain FP64, one instance at a time, on 8 seeded instances (GLUP/s by LUP count)
+    rng = __import__("numpy").random.default_rng(7)
+    pick = rng.choice(len(probs), size=8, replace=False)
+    tl, ll = 0.0, 0
+    for k in pick:
+        sp = WH.Solver(probs[k], stream=stream)
+        tk = sp.prepare()
+        tl += time_iterations(WH, torch, sp, probs[k].n_total, stream, flush, 1, warm=1)
+        ll += tk.n_active * tk.M
+        sp.close()
+    res["plain_fp64_per_instance"] = {"value": ll / tl / 1e9, "unit": "GLUP/s",
+                                      "sample": "8 seeded instances, one at a time"}
+    res["speedup_batched_fp32_vs_plain_fp64"] = res["batched_fp32"]["value"] / \
+        res["plain_fp64_per_instance"]["value"]
+    out["batch_256"] = res
+    del bp, probs
+    # time to 1e-6 relative error, 64^2 unit square, order 2, omega 10
+    sq = G.unit_square_problem(64, 2, 10.0, seed=0)
+    ref = WH.Solver(sq, stream=stream)
+    ref.prepare()
+    uref = torch.zeros(sq.n_total, dtype=torch.float64, device="cuda")
+    ref.solve(uref, WH.GMRES, tol=1e-13, max_it=400, restart=200)
+    solve = {}
+    for name, prec, tol in (("fp64_gmres", WH.FP64, 1e-7), ("fp32_refined_gmres", WH.FP32, 1e-7)):
+        sv = WH.Solver(sq, stream=stream, precision=prec)
+        sv.prepare()
+        u = torch.zeros_like(uref)
+        sv.solve(u, WH.GMRES, tol=tol, max_it=400, restart=200)  # warm-up (graphs)
+        u.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = sv.solve(u, WH.GMRES, tol=tol, max_it=400, restart=200)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        err = float((u - uref).abs().max() / uref.abs().max())
+        solve[name] = {"seconds": el, "rel_err_vs_reference": err, "wave_solves": st.iterations,
+                       "residual": st.residual}
+    solve["workload"] = ("64^2 unit square, order 2, omega 10, residual 1e-7; reference: FP64 "
+                         "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
+    out["solve_unit_square"] = solve
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on the host cores, same metric/unit/config; each
     step is one oracle WaveHoltz iteration on the half-resolution sample of the workload
@@ -193,6 +286,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small workload (profiling)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32 / batched / solve-time measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -284,6 +379,10 @@ def main():
                 "share_of_iteration": march_ms * march_n / total_prof,
                 "peak_source": "GB300 FP64 1.25 TFLOP/s (pool figure; FMA=2)"}
 
+    forms = None
+    if not args.no_forms and not args.small:
+        forms = measure_forms(WH, G, torch, prob, stream, flush, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.small:
         cpu = cpu_baseline(prob, "one full oracle WaveHoltz iteration (M=%d steps) of the "
@@ -303,6 +402,7 @@ def main():
                 "d2h_bytes_per_step": n * 8, "ms_per_step": e2e_t * 1e3},
         "clocks": clk.summary(),
         "gpu_launches": launches,
+        "forms": forms,
         "kernels_ms_per_iteration": {k: v[0] * v[1] for k, v in prof.items()},
         "kernels_us_per_launch": {k: v[0] * 1e3 for k, v in prof.items()},
     }
