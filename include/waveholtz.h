@@ -222,6 +222,30 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
 wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,
                          wh_stats *stats);
 
+/* Differentiation (single-instance contexts; FP64 march, also on WH_FP32 contexts).
+ * The paper has no adjoint; this is the exact transpose of the implemented discrete map:
+ * with C the constraint map (ghost rules and interpolation), D the restriction to
+ * discretization points and A the march stencil, W_h(v, 0) = S v = sum_n w_n M X^n with
+ * X^0 = C E v, X^1 = C D (A X^0 / 2), X^{n+1} = C D (A X^n - X^{n-1}).
+ *
+ * wh_apply_adjoint: w_out = S^T w_in (DEVICE compact vectors; <S v, w> = <v, S^T w>).
+ *
+ * wh_adjoint: for a converged solution u of (I - S) u = b(f) and the gradient g = dJ/du of
+ * a scalar misfit J(u) (DEVICE compact vectors), solves (I - S)^T lam = g by GMRES(restart)
+ * to relative residual tol (lam: DEVICE compact, output), then returns
+ *   grad_c2 = dJ/d(c^2) and grad_f = dJ/df  (DEVICE compact, one value per grid point)
+ * from a reverse sweep whose forward states (the march from u with forcing) are recomputed
+ * from checkpoints every 16 time steps.  The time step is held fixed (it changes only when
+ * Nt does).  Synchronises. */
+wh_status wh_apply_adjoint(wh_ctx *ctx, const double *w_in, double *w_out);
+wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, int32_t max_it,
+                     int32_t restart, double *lam, double *grad_c2, double *grad_f,
+                     wh_stats *stats);
+
+/* Replace c(x)^2 of grid grid_id (host, n0*n1, > 0; NULL: c = 1).  Takes effect at the next
+ * wh_prepare. */
+wh_status wh_set_coefficient(wh_ctx *ctx, int32_t grid_id, const double *c2);
+
 /* FP64 inner product <x, y> over n entries of two DEVICE vectors (the GMRES reduction:
  * warp-shuffle partial sums, then one deterministic pass).  *out is a host scalar.  n = 0
  * gives 0 (x, y may then be NULL). */

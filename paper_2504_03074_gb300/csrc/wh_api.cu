@@ -92,6 +92,15 @@ struct wh_ctx {
   int64_t tabs_cap = 0;
   int32_t *d_rinst = nullptr;
   int maxM = 0;
+  // differentiation: transpose constraint lists (CSR over extended source points) and
+  // buffers; built on the first adjoint call after wh_prepare
+  bool adj_ready = false;
+  bool adjoint_mode = false;  // apply_A uses S^T (adjoint GMRES)
+  int64_t *d_roff = nullptr, *d_rpos = nullptr;
+  double *d_rcoef = nullptr;
+  double *d_adj = nullptr;   // lam, Y, Z x3, gc2, gf (extended)
+  double *d_ckpt = nullptr;  // checkpoints and segment states
+  int64_t ckpt_cap = 0;
 
   // solver workspace
   double *d_q = nullptr;  // Krylov basis
@@ -172,6 +181,10 @@ void free_device(wh_ctx *ctx) {
   ctx->red_cap = 0;
   ctx->d_tabs = nullptr;
   ctx->tabs_cap = 0;
+  ctx->adj_ready = false;
+  ctx->d_roff = ctx->d_rpos = nullptr;
+  ctx->d_rcoef = ctx->d_adj = ctx->d_ckpt = nullptr;
+  ctx->ckpt_cap = 0;
   ctx->d_bar = nullptr;
 }
 
@@ -756,8 +769,10 @@ struct SolveLog {
 };
 
 // y = A x = x - W_h(x, 0) (w0 is scratch)
+wh_status apply_adjoint(wh_ctx *ctx, const double *x, double *y);
+
 wh_status apply_A(wh_ctx *ctx, const double *x, double *y, double *w0, SolveLog &L) {
-  wh_status st = iterate_device(ctx, 0, x, w0);
+  wh_status st = ctx->adjoint_mode ? apply_adjoint(ctx, x, w0) : iterate_device(ctx, 0, x, w0);
   if (st) return st;
   L.products[ctx->active] += 1;
   launch_sub(grid1d(ctx->ncompact), ctx->stream, x, w0, y, ctx->ncompact);
@@ -967,6 +982,229 @@ wh_status gmres_cycle_batch(wh_ctx *ctx, const double *rhs, double *x, bool x_is
     launch_gemv_acc(grid1d(G.len), s, Q + G.off, n, G.kk, ctx->d_red, x + G.off, G.len);
     CK(cudaStreamSynchronize(s));  // d_red is reused by the next instance
   }
+  CK(cudaGetLastError());
+  return WH_OK;
+}
+
+// ---- differentiation (single-instance contexts, FP64 march) ----
+constexpr int kCkptEvery = 16;  // forward states are recomputed from checkpoints this far apart
+
+wh_status adj_setup(wh_ctx *ctx) {
+  if (ctx->adj_ready) return WH_OK;
+  const int order = ctx->opt.order;
+  const int64_t total = ctx->total;
+  // the 2x2 solve coefficients of the ghost items live on the device (bc_coef_kernel)
+  std::vector<BcItem> bc(ctx->hbc.size());
+  if (!bc.empty())
+    CK(cudaMemcpy(bc.data(), ctx->d_bc, bc.size() * sizeof(BcItem), cudaMemcpyDeviceToHost));
+  // entries (source point, constrained position, coefficient)
+  struct Ent {
+    int64_t src, pos;
+    double c;
+  };
+  std::vector<Ent> ent;
+  const double e5[4] = {-10.0, 10.0, -5.0, 1.0};  // E = sum e5_k U_k, G2 = 5 G1 + E
+  for (const BcItem &it : bc) {
+    double a[4] = {0, 0, 0, 0};
+    if (it.type == 0) {
+      a[1] = 1.0;
+    } else if (it.type == 1) {
+      a[0] = -10.0 / 3; a[1] = 18.0 / 3; a[2] = -6.0 / 3; a[3] = 1.0 / 3;
+    } else {
+      a[0] = (20 * it.A2 + 10 * it.B1) * it.inv;
+      a[1] = (-6 * it.A2 - 18 * it.B1) * it.inv;
+      a[2] = (-4 * it.A2 + 6 * it.B1) * it.inv;
+      a[3] = (it.A2 - it.B1) * it.inv;
+    }
+    for (int k = 0; k < 4; ++k) {
+      if (a[k] != 0.0) ent.push_back({it.u[k], it.g[0], a[k]});
+      if (order == 4 && it.type != 0) {
+        const double b = 5.0 * a[k] + e5[k];
+        if (b != 0.0) ent.push_back({it.u[k], it.g[1], b});
+      }
+    }
+  }
+  const int ND = (order + 1) * (order + 1);
+  {
+    std::vector<int32_t> didx((size_t)ctx->nrecv * ND);
+    std::vector<double> dw((size_t)ctx->nrecv * ND);
+    std::vector<int64_t> ridx((size_t)ctx->nrecv);
+    if (ctx->nrecv) {
+      CK(cudaMemcpy(didx.data(), ctx->d_didx, didx.size() * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(dw.data(), ctx->d_dw, dw.size() * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(ridx.data(), ctx->d_ridx, ridx.size() * 8, cudaMemcpyDeviceToHost));
+    }
+    for (int64_t r = 0; r < ctx->nrecv; ++r)
+      for (int d = 0; d < ND; ++d) ent.push_back({didx[r * ND + d], ridx[r], dw[r * ND + d]});
+  }
+  std::vector<int64_t> off(total + 1, 0), pos(ent.size());
+  std::vector<double> coef(ent.size());
+  for (const Ent &e : ent) off[e.src + 1]++;
+  for (int64_t q = 0; q < total; ++q) off[q + 1] += off[q];
+  std::vector<int64_t> fill(off.begin(), off.end() - 1);
+  for (const Ent &e : ent) {
+    const int64_t k = fill[e.src]++;
+    pos[k] = e.pos;
+    coef[k] = e.c;
+  }
+  wh_status st;
+  if ((st = dalloc(ctx, &ctx->d_roff, off.size())) ||
+      (st = dalloc(ctx, &ctx->d_rpos, std::max<size_t>(pos.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_rcoef, std::max<size_t>(coef.size(), 1))) ||
+      (!ctx->d_adj && (st = dalloc(ctx, &ctx->d_adj, 7 * (size_t)total))))
+    return st;
+  CK(cudaMemcpy(ctx->d_roff, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+  if (!pos.empty()) {
+    CK(cudaMemcpy(ctx->d_rpos, pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_rcoef, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice));
+  }
+  ctx->adj_ready = true;
+  return WH_OK;
+}
+
+// Host copy of instance 0's time tables.
+void host_tables(const wh_ctx *ctx, std::vector<double> &fc, std::vector<double> &cosn,
+                 std::vector<double> &wf) {
+  const wh_time_info &ti = ctx->iti[0];
+  const int M = ti.M;
+  fc.resize(M + 1);
+  cosn.resize(M + 1);
+  wf.resize(M + 1);
+  for (int n = 0; n <= M; ++n) {
+    const double cn = std::cos(ti.omega_e * n * ti.dt);
+    const double sig = (n == 0 || n == M) ? 0.5 : 1.0;
+    fc[n] = ti.dt * ti.dt * cn;
+    cosn[n] = cn;
+    wf[n] = (2.0 / M) * sig * (cn - ti.alpha / 2.0);
+  }
+}
+
+// One forward time step n (march + ghost rules/interpolation of level n+1) on the FP64 set.
+void forward_step(wh_ctx *ctx, int n, double fs) {
+  const int order = ctx->opt.order;
+  cudaStream_t s = ctx->stream;
+  const int nbc = (int)ctx->hbc.size();
+  const int bc_blocks = (nbc + 255) / 256;
+  const int bg_blocks = bc_blocks + (int)((ctx->nrecv * (order == 4 ? 8 : 4) + 255) / 256);
+  const int ntiles = (int)ctx->htiles.size();
+  void *cur = (n & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (n & 1) ? ctx->d_Wa : ctx->d_Wb;
+  launch_march(false, order, n == 0, std::min(ntiles, ctx->march_blocks), ntiles, s, ctx->d_grids,
+               ctx->d_tiles, ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst,
+               n, fs);
+  if (bg_blocks)
+    launch_bc_gather(false, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx, ctx->d_dw,
+                     ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, oth, ctx->d_F, ctx->d_inst,
+                     n + 1, fs);
+}
+
+// The reverse sweep.  lam: extended adjoint source.  Without gradients: Z^0 = S^T lam is
+// left in the returned buffer.  With gradients (u != nullptr, compact): the forward states
+// of the march from u (forcing on) are recomputed from checkpoints and d(lam . W_h)/dc^2,
+// d(lam . W_h)/df are accumulated (extended) into gc2, gf.
+wh_status adj_sweep(wh_ctx *ctx, const double *lam, double **z0_out, const double *u,
+                    double *gc2, double *gf) {
+  const int order = ctx->opt.order, M = ctx->iti[0].M;
+  const int64_t total = ctx->total;
+  cudaStream_t s = ctx->stream;
+  const int ng = (int)ctx->hgrids.size();
+  std::vector<double> fc, cosn, wf;
+  host_tables(ctx, fc, cosn, wf);
+  double *Y = ctx->d_adj + total;
+  double *Zb[3] = {ctx->d_adj + 2 * total, ctx->d_adj + 3 * total, ctx->d_adj + 4 * total};
+  CK(cudaMemsetAsync(Zb[0], 0, total * sizeof(double), s));
+  CK(cudaMemsetAsync(Zb[1], 0, total * sizeof(double), s));
+  const bool grad = u != nullptr;
+  const int nseg = (M + kCkptEvery - 1) / kCkptEvery;
+  double *ck = nullptr, *seg = nullptr;
+  wh_status st;
+  if (grad) {
+    // checkpoints: (X^s, X^{s-1}) at s = 0, 16, ...; segment states X^s .. X^{s+16}
+    const int64_t need = (2 * (int64_t)nseg + kCkptEvery + 1) * total;
+    if (ctx->ckpt_cap < need) {
+      if ((st = dalloc(ctx, &ctx->d_ckpt, (size_t)need))) return st;
+      ctx->ckpt_cap = need;
+    }
+    ck = ctx->d_ckpt;
+    seg = ctx->d_ckpt + 2 * (int64_t)nseg * total;
+    // forward march from u with forcing, saving checkpoints
+    launch_init(false, (unsigned)((total + 255) / 256), s, ctx->d_grids, ng, ctx->d_mask, u,
+                ctx->d_Wa, ctx->d_V, total, ctx->d_inst);
+    const int bc_blocks = ((int)ctx->hbc.size() + 255) / 256;
+    const int bg_blocks = bc_blocks + (int)((ctx->nrecv * (order == 4 ? 8 : 4) + 255) / 256);
+    if (bg_blocks)
+      launch_bc_gather(false, order, bg_blocks, s, ctx->d_bc, (int)ctx->hbc.size(), bc_blocks,
+                       ctx->d_didx, ctx->d_dw, ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv,
+                       ctx->d_Wa, ctx->d_F, ctx->d_inst, 0, 1.0);
+    for (int n = 0; n < M; ++n) {
+      if (n % kCkptEvery == 0) {
+        const int k = n / kCkptEvery;
+        void *cur = (n & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (n & 1) ? ctx->d_Wa : ctx->d_Wb;
+        CK(cudaMemcpyAsync(ck + (2 * k) * total, cur, total * 8, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ck + (2 * k + 1) * total, oth, total * 8, cudaMemcpyDeviceToDevice, s));
+      }
+      forward_step(ctx, n, 1.0);
+    }
+    CK(cudaGetLastError());
+  }
+  // level M
+  int iz_new = 2, iz1 = 0, iz2 = 1;  // Z^{n+1} in Zb[iz1], Z^{n+2} in Zb[iz2]
+  launch_adj_step(order, s, ctx->d_grids, ng, ctx->d_mask, (const double *)ctx->d_Wt, lam, wf[M],
+                  1.0, Zb[iz1], Zb[iz2], Y, total, nullptr, ctx->d_c2, 0.0, gc2, gf);
+  if (grad)
+    launch_adj_bc_grad(s, ctx->d_bc, (int)ctx->hbc.size(), Y, (const double *)ctx->d_F, ctx->d_c2,
+                       cosn[M], gc2, gf);
+  launch_adj_ct(s, ctx->d_mask, Y, ctx->d_roff, ctx->d_rpos, ctx->d_rcoef, Zb[iz_new], total);
+  // rotate: Z^{M+2} <- Z^{M+1}, Z^{M+1} <- Z^M
+  int t = iz2;
+  iz2 = iz1;
+  iz1 = iz_new;
+  iz_new = t;
+  for (int sidx = nseg - 1; sidx >= 0; --sidx) {
+    const int s0 = sidx * kCkptEvery, e0 = std::min(s0 + kCkptEvery - 1, M - 1);
+    if (grad) {
+      // restore X^{s0}, X^{s0-1} and recompute X^{s0} .. X^{e0} into the segment buffer
+      void *cur = (s0 & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (s0 & 1) ? ctx->d_Wa : ctx->d_Wb;
+      CK(cudaMemcpyAsync(cur, ck + (2 * sidx) * total, total * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(oth, ck + (2 * sidx + 1) * total, total * 8, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(seg, cur, total * 8, cudaMemcpyDeviceToDevice, s));
+      for (int n = s0; n < e0; ++n) {
+        forward_step(ctx, n, 1.0);
+        void *nxt = ((n + 1) & 1) ? ctx->d_Wb : ctx->d_Wa;
+        CK(cudaMemcpyAsync(seg + (int64_t)(n + 1 - s0) * total, nxt, total * 8,
+                           cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    for (int n = e0; n >= s0; --n) {
+      const double sc = n == 0 ? 0.5 : 1.0;
+      const double fcn = n == 0 ? 0.5 * ctx->iti[0].dt * ctx->iti[0].dt : fc[n];
+      const double *Xn = grad ? seg + (int64_t)(n - s0) * total : nullptr;
+      launch_adj_step(order, s, ctx->d_grids, ng, ctx->d_mask, (const double *)ctx->d_Wt, lam,
+                      wf[n], sc, Zb[iz1], Zb[iz2], Y, total, Xn, ctx->d_c2, fcn, gc2, gf);
+      if (grad)
+        launch_adj_bc_grad(s, ctx->d_bc, (int)ctx->hbc.size(), Y, (const double *)ctx->d_F,
+                           ctx->d_c2, cosn[n], gc2, gf);
+      launch_adj_ct(s, ctx->d_mask, Y, ctx->d_roff, ctx->d_rpos, ctx->d_rcoef, Zb[iz_new], total);
+      t = iz2;
+      iz2 = iz1;
+      iz1 = iz_new;
+      iz_new = t;
+    }
+  }
+  CK(cudaGetLastError());
+  *z0_out = Zb[iz1];
+  return WH_OK;
+}
+
+// y = S^T x for compact x, y (the zero-forcing map's transpose)
+wh_status apply_adjoint(wh_ctx *ctx, const double *x, double *y) {
+  wh_status st = adj_setup(ctx);
+  if (st) return st;
+  const int ng = (int)ctx->hgrids.size();
+  double *lam = ctx->d_adj;
+  launch_compact_to_ext(ctx->stream, ctx->d_grids, ng, ctx->d_mask, x, lam, ctx->total);
+  double *z0;
+  if ((st = adj_sweep(ctx, lam, &z0, nullptr, nullptr, nullptr))) return st;
+  launch_ext_to_compact(ctx->stream, ctx->d_grids, ng, ctx->d_mask, z0, y, ctx->ncompact, 1);
   CK(cudaGetLastError());
   return WH_OK;
 }
@@ -1286,6 +1524,7 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   ctx->prepared = true;
+  ctx->adj_ready = false;
   return WH_OK;
 }
 
@@ -1604,6 +1843,112 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
   if (all_done()) return finish(WH_OK);
   return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "batched GMRES: budget of %d wave solves used",
                      max_it));
+}
+
+static wh_status adj_check(wh_ctx *ctx) {
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  if (ctx->ninst != 1) return fail(ctx, WH_ERR_ARG, "differentiation needs a single instance");
+  return WH_OK;
+}
+
+wh_status wh_apply_adjoint(wh_ctx *ctx, const double *w_in, double *w_out) {
+  if (!ctx || !w_in || !w_out || w_in == w_out) return fail(ctx, WH_ERR_ARG, "bad vectors");
+  wh_status st = adj_check(ctx);
+  if (st) return st;
+  use_set(ctx, 0);
+  st = apply_adjoint(ctx, w_in, w_out);
+  use_set(ctx, default_set(ctx));
+  return st;
+}
+
+wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, int32_t max_it,
+                     int32_t restart, double *lam, double *grad_c2, double *grad_f,
+                     wh_stats *stats) {
+  if (!ctx || !u || !g || !lam || !grad_c2 || !grad_f || !(tol > 0) || max_it < 1 ||
+      restart < 1 || restart > 4000)
+    return fail(ctx, WH_ERR_ARG, "bad wh_adjoint arguments");
+  wh_status st = adj_check(ctx);
+  if (st) return st;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = ctx->ncompact, total = ctx->total;
+  const int ng = (int)ctx->hgrids.size();
+  cudaStream_t s = ctx->stream;
+  use_set(ctx, 0);
+  if ((st = adj_setup(ctx))) return st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
+  if (ctx->q_cap < (int64_t)(restart + 1) * n) {
+    if ((st = dalloc(ctx, &ctx->d_q, (size_t)(restart + 1) * n))) return st;
+    ctx->q_cap = (int64_t)(restart + 1) * n;
+  }
+  if ((st = ensure_red(ctx, restart + 1))) return st;
+  SolveLog L;
+  wh_stats S{};
+  auto finish = [&](wh_status code) {
+    ctx->adjoint_mode = false;
+    use_set(ctx, default_set(ctx));
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    S.products_fp64 = L.products[0];
+    S.iterations = L.products[0];
+    if (stats) *stats = S;
+    return code;
+  };
+  // (I - S^T) lam = g by GMRES; lam starts at 0
+  ctx->adjoint_mode = true;
+  CK(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
+  double gg;
+  if ((st = multidot(ctx, g, 0, 1, g, n, &gg))) return finish(st);
+  const double gnorm = std::sqrt(gg);
+  if (gnorm > 0) {
+    while (true) {
+      double res;
+      bool fin;
+      const int budget = max_it - L.products[0];
+      if ((st = gmres_cycle(ctx, g, lam, false, restart, tol * gnorm, budget, 1.0 / gnorm, L,
+                            &res, &fin)))
+        return finish(st);
+      S.residual = res / gnorm;
+      if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "adjoint GMRES residual not finite"));
+      if (S.residual <= tol) {
+        S.converged = 1;
+        break;
+      }
+      if (L.products[0] >= max_it)
+        return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "adjoint GMRES: %d products, residual %g",
+                           max_it, S.residual));
+    }
+  } else {
+    S.converged = 1;
+  }
+  ctx->adjoint_mode = false;
+  // gradient sweep: d(lam . W_h(u, f))/d theta
+  double *lam_ext = ctx->d_adj, *gc2 = ctx->d_adj + 5 * total, *gf = ctx->d_adj + 6 * total;
+  launch_compact_to_ext(s, ctx->d_grids, ng, ctx->d_mask, lam, lam_ext, total);
+  CK(cudaMemsetAsync(gc2, 0, total * sizeof(double), s));
+  CK(cudaMemsetAsync(gf, 0, total * sizeof(double), s));
+  double *z0;
+  if ((st = adj_sweep(ctx, lam_ext, &z0, u, gc2, gf))) return finish(st);
+  launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, gc2, grad_c2, n, 0);
+  launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, gf, grad_f, n, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return finish(WH_OK);
+}
+
+wh_status wh_set_coefficient(wh_ctx *ctx, int32_t gid, const double *c2) {
+  if (!ctx || gid < 0 || gid >= (int)ctx->grids.size())
+    return fail(ctx, WH_ERR_ARG, "bad wh_set_coefficient arguments");
+  HostGrid &H = ctx->grids[gid];
+  const int64_t n = (int64_t)H.d.n[0] * H.d.n[1];
+  if (!c2) {
+    H.c2.clear();
+  } else {
+    H.c2.assign(c2, c2 + n);
+    for (double v : H.c2)
+      if (!(v > 0) || !std::isfinite(v)) return fail(ctx, WH_ERR_ARG, "c^2 must be positive");
+  }
+  ctx->dirty = true;
+  ctx->prepared = false;
+  return WH_OK;
 }
 
 wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts) {

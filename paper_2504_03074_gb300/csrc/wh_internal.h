@@ -137,6 +137,19 @@ void launch_weight(bool fp32, int order, dim3 gb, dim3 tb, cudaStream_t s, const
 void launch_bc_coef(int nbc, cudaStream_t s, BcItem *bc, const int32_t *ig, const int32_t *ia,
                     const int32_t *ih, const DevGrid *grids, const double *coef,
                     const double *c2);
+void launch_adj_step(int order, cudaStream_t s, const DevGrid *grids, int ngrids,
+                     const int8_t *mask, const double *Wt, const double *lam, double wn,
+                     double sc, const double *Z1, const double *Z2, double *Y, int64_t total,
+                     const double *Xn, const double *c2, double fc, double *gc2, double *gf);
+void launch_adj_ct(cudaStream_t s, const int8_t *mask, const double *Y, const int64_t *roff,
+                   const int64_t *rpos, const double *rcoef, double *Z, int64_t total);
+void launch_adj_bc_grad(cudaStream_t s, const BcItem *bc, int nbc, const double *Y,
+                        const double *F, const double *c2, double fcos, double *gc2,
+                        double *gf);
+void launch_compact_to_ext(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
+                           const double *v, double *x, int64_t total);
+void launch_ext_to_compact(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
+                           const double *x, double *v, int64_t ncompact, int disc_only);
 constexpr int kRedThreads = 256;
 void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
                      const double *y, int64_t n, double *partial, double *out);

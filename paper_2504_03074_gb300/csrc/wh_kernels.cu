@@ -529,6 +529,204 @@ __global__ void __launch_bounds__(kTileX *kTileY)
 }
 
 // ---------------------------------------------------------------------------------
+// Differentiation: the exact transpose of the discrete iteration map (FP64).
+// With C the constraint map (ghost rules + interpolation), D the restriction to
+// discretization points and A the stencil operator (rows of the march), the forward map is
+//   X^0 = C E v,  X^1 = C D(A X^0 / 2 - ...),  X^{n+1} = C D(A X^n - X^{n-1} - ...),
+//   W_h = sum_n w_n M X^n.
+// Its transpose runs backwards: Y^n = w_n M lam + s_n A^T Z^{n+1} - Z^{n+2} (s_0 = 1/2),
+// Z^n = D C^T Y^n, and S^T lam = Z^0.
+// ---------------------------------------------------------------------------------
+
+// locate the grid and (i, j) of extended point p; false on padding
+__device__ __forceinline__ bool ext_locate(const DevGrid *__restrict__ grids, int ngrids,
+                                           int64_t p, int &g, int &i, int &j) {
+  g = 0;
+  while (g + 1 < ngrids && p >= grids[g + 1].base) ++g;
+  const DevGrid &G = grids[g];
+  const int64_t o = p - G.base;
+  if (o >= G.ext) return false;
+  j = (int)(o / G.pitch) - G.g1;
+  i = (int)(o % G.pitch) - G.g0;
+  return i < G.n0 + G.g0;
+}
+
+// Z value of a neighbour (i, j) if it is inside the grid's discretization range (else 0;
+// Z vanishes off discretization points anyway)
+__device__ __forceinline__ bool nb_index(const DevGrid &G, int i, int j, int64_t &p) {
+  if (G.per0) i = wrap(i, G.n0, 1);
+  else if (i < 0 || i >= G.n0) return false;
+  if (G.per1) j = wrap(j, G.n1, 1);
+  else if (j < 0 || j >= G.n1) return false;
+  p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+  return true;
+}
+
+// Y = w_n lam (active points) + s (A^T Z1) - Z2 at every extended point.  In gradient mode
+// (Xn != nullptr) discretization points also add the parameter gradients of the step
+// n -> n+1: gf -= fc Z1, gc2 += s Z1 ((A Xn) - 2 Xn) / c^2.
+template <int ORDER>
+__global__ void adj_step_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                                const int8_t *__restrict__ mask, const double *__restrict__ Wt,
+                                const double *__restrict__ lam, double wn, double sc,
+                                const double *__restrict__ Z1, const double *__restrict__ Z2,
+                                double *Y, int64_t total, const double *__restrict__ Xn,
+                                const double *__restrict__ c2, double fc, double *gc2,
+                                double *gf) {
+  constexpr int R = ORDER / 2;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  int g, i, j;
+  if (!ext_locate(grids, ngrids, q, g, i, j)) {
+    Y[q] = 0.0;
+    return;
+  }
+  const DevGrid &G = grids[g];
+  const int8_t mk = mask[q];
+  double at = 0.0;  // (A^T Z1)[q] = sum_o A[q - o, q] Z1[q - o]
+  if (G.stencil == kConstCross) {
+    // constant symmetric weights: A^T Z = A Z
+    const double cw[5] = {G.cw[0], G.cw[1], G.cw[2], G.cw[3], G.cw[4]};
+    int64_t pn;
+    if (nb_index(G, i, j, pn)) at += cw[0] * Z1[pn];
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+      const double wx = cw[k], wy = cw[2 + k];
+      if (nb_index(G, i - k, j, pn)) at += wx * Z1[pn];
+      if (nb_index(G, i + k, j, pn)) at += wx * Z1[pn];
+      if (nb_index(G, i, j - k, pn)) at += wy * Z1[pn];
+      if (nb_index(G, i, j + k, pn)) at += wy * Z1[pn];
+    }
+  } else if (G.stencil == kPointCross) {
+    const int64_t E = G.ext;
+    int64_t pn;
+    if (nb_index(G, i, j, pn)) at += Wt[G.wbase + (pn - G.base)] * Z1[pn];
+    int pl = 1;
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {  // axis-0 offset k of row p = q - k
+      if (k == 0) continue;
+      if (nb_index(G, i - k, j, pn)) at += Wt[G.wbase + (pn - G.base) + pl * E] * Z1[pn];
+      ++pl;
+    }
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {
+      if (k == 0) continue;
+      if (nb_index(G, i, j - k, pn)) at += Wt[G.wbase + (pn - G.base) + pl * E] * Z1[pn];
+      ++pl;
+    }
+  } else {
+    const int64_t E = G.ext;
+#pragma unroll
+    for (int b = -R; b <= R; ++b)
+#pragma unroll
+      for (int a = -R; a <= R; ++a) {
+        int64_t pn;
+        if (nb_index(G, i - a, j - b, pn))
+          at += Wt[G.wbase + (pn - G.base) + ((b + R) * (2 * R + 1) + (a + R)) * E] * Z1[pn];
+      }
+  }
+  const bool active = mk == 1 || mk == 2 || mk == 3;
+  Y[q] = (active ? wn * lam[q] : 0.0) + sc * at - Z2[q];
+  if (Xn && mk == 1) {
+    // (A Xn)[q] - 2 Xn[q]: the dt^2 c^2 L_h part of row q, divided by c^2 below
+    double ax;
+    if (G.stencil == kConstCross) {
+      ax = (G.cw[0] - 2.0) * Xn[q];
+      for (int k = 1; k <= R; ++k) {
+        ax += G.cw[k] * (Xn[row_off(G, j) + wrap(i - k, G.n0, G.per0)] +
+                         Xn[row_off(G, j) + wrap(i + k, G.n0, G.per0)]);
+        ax += G.cw[2 + k] * (Xn[row_off(G, j - k) + i] + Xn[row_off(G, j + k) + i]);
+      }
+    } else if (G.stencil == kPointCross) {
+      const int64_t w0 = G.wbase + (q - G.base), E = G.ext;
+      ax = (Wt[w0] - 2.0) * Xn[q];
+      int pl = 1;
+      for (int k = -R; k <= R; ++k) {
+        if (k == 0) continue;
+        ax += Wt[w0 + pl * E] * Xn[row_off(G, j) + wrap(i + k, G.n0, G.per0)];
+        ++pl;
+      }
+      for (int k = -R; k <= R; ++k) {
+        if (k == 0) continue;
+        ax += Wt[w0 + pl * E] * Xn[row_off(G, j + k) + i];
+        ++pl;
+      }
+    } else {
+      const int64_t w0 = G.wbase + (q - G.base), E = G.ext;
+      ax = -2.0 * Xn[q];
+      for (int b = -R; b <= R; ++b)
+        for (int a = -R; a <= R; ++a)
+          ax += Wt[w0 + ((b + R) * (2 * R + 1) + (a + R)) * E] *
+                Xn[row_off(G, j + b) + wrap(i + a, G.n0, G.per0)];
+    }
+    const double z = Z1[q];
+    gc2[q] += sc * z * ax / c2[q];
+    gf[q] -= fc * z;
+  }
+}
+
+// Z = D C^T Y: discretization points gather Y from the constrained positions (ghosts,
+// receivers) that read them, with the constraint coefficients; everything else is 0.
+__global__ void adj_ct_kernel(const int8_t *__restrict__ mask, const double *__restrict__ Y,
+                              const int64_t *__restrict__ roff, const int64_t *__restrict__ rpos,
+                              const double *__restrict__ rcoef, double *Z, int64_t total) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  if (mask[q] != 1) {
+    Z[q] = 0.0;
+    return;
+  }
+  double z = Y[q];
+  for (int64_t e = roff[q]; e < roff[q + 1]; ++e) z = fma(rcoef[e], Y[rpos[e]], z);
+  Z[q] = z;
+}
+
+// Gradient terms of the Dirichlet order-4 compatibility rule at one level: with
+// t = Y[G1] + 5 Y[G2], gf[b] += fcos inv t and gc2[b] -= F_b fcos inv t / c^2_b.
+__global__ void adj_bc_grad_kernel(const BcItem *__restrict__ bc, int nbc,
+                                   const double *__restrict__ Y, const double *__restrict__ F,
+                                   const double *__restrict__ c2, double fcos, double *gc2,
+                                   double *gf) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nbc) return;
+  const BcItem it = bc[k];
+  if (it.type != 2) return;
+  const double t = Y[it.g[0]] + 5.0 * Y[it.g[1]];
+  const int64_t b = it.u[0];
+  gf[b] += fcos * it.inv * t;
+  gc2[b] -= F[b] * fcos * it.inv * t / c2[b];
+}
+
+// compact <-> extended copies at active points
+__global__ void compact_to_ext_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                                      const int8_t *__restrict__ mask, const double *__restrict__ v,
+                                      double *x, int64_t total) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  int g, i, j;
+  double val = 0.0;
+  if (ext_locate(grids, ngrids, p, g, i, j) && mask[p] != 0 && i >= 0 && i < grids[g].n0 &&
+      j >= 0 && j < grids[g].n1)
+    val = v[grids[g].cbase + (int64_t)j * grids[g].n0 + i];
+  x[p] = val;
+}
+
+__global__ void ext_to_compact_kernel(const DevGrid *__restrict__ grids, int ngrids,
+                                      const int8_t *__restrict__ mask, const double *__restrict__ x,
+                                      double *v, int64_t ncompact, int disc_only) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncompact) return;
+  int g = 0;
+  while (g + 1 < ngrids && c >= grids[g + 1].cbase) ++g;
+  const DevGrid &G = grids[g];
+  const int64_t o = c - G.cbase;
+  const int j = (int)(o / G.n0), i = (int)(o % G.n0);
+  const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
+  const int8_t m = mask[p];
+  v[c] = (disc_only ? m == 1 : m != 0) ? x[p] : 0.0;
+}
+
+// ---------------------------------------------------------------------------------
 // Operator precompute (mapping method, Sec. 3.1): per point a11, a12, a22, b1, b2 with
 // c(x)^2 folded in, and the frozen-coefficient spectral bound
 //   s = a11/dr1^2 + a22/dr2^2 + 2|a12|/(dr1 dr2)   (max over discretization points).
@@ -894,6 +1092,43 @@ void launch_bc_coef(int nbc, cudaStream_t s, BcItem *bc, const int32_t *ig, cons
                     const int32_t *ih, const DevGrid *grids, const double *coef,
                     const double *c2) {
   bc_coef_kernel<<<(nbc + 255) / 256, 256, 0, s>>>(bc, nbc, ig, ia, ih, grids, coef, c2);
+}
+
+void launch_adj_step(int order, cudaStream_t s, const DevGrid *grids, int ngrids,
+                     const int8_t *mask, const double *Wt, const double *lam, double wn,
+                     double sc, const double *Z1, const double *Z2, double *Y, int64_t total,
+                     const double *Xn, const double *c2, double fc, double *gc2, double *gf) {
+  const unsigned nb = (unsigned)((total + 255) / 256);
+  if (order == 4)
+    adj_step_kernel<4><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, total,
+                                          Xn, c2, fc, gc2, gf);
+  else
+    adj_step_kernel<2><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, total,
+                                          Xn, c2, fc, gc2, gf);
+}
+
+void launch_adj_ct(cudaStream_t s, const int8_t *mask, const double *Y, const int64_t *roff,
+                   const int64_t *rpos, const double *rcoef, double *Z, int64_t total) {
+  adj_ct_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(mask, Y, roff, rpos, rcoef, Z,
+                                                                total);
+}
+
+void launch_adj_bc_grad(cudaStream_t s, const BcItem *bc, int nbc, const double *Y,
+                        const double *F, const double *c2, double fcos, double *gc2,
+                        double *gf) {
+  if (nbc) adj_bc_grad_kernel<<<(nbc + 255) / 256, 256, 0, s>>>(bc, nbc, Y, F, c2, fcos, gc2, gf);
+}
+
+void launch_compact_to_ext(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
+                           const double *v, double *x, int64_t total) {
+  compact_to_ext_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(grids, ngrids, mask, v, x,
+                                                                        total);
+}
+
+void launch_ext_to_compact(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
+                           const double *x, double *v, int64_t ncompact, int disc_only) {
+  ext_to_compact_kernel<<<(unsigned)((ncompact + 255) / 256), 256, 0, s>>>(
+      grids, ngrids, mask, x, v, ncompact, disc_only);
 }
 
 void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int nv,

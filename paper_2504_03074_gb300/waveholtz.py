@@ -70,7 +70,8 @@ class Stats(C.Structure):
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
-           "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch"]
+           "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
+           "wh_set_coefficient"]
 
 
 def lib_path():
@@ -105,6 +106,10 @@ def lib():
                            C.POINTER(Stats), vp, C.c_int32]
     L.wh_dot.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(C.c_double)]
     L.wh_solve_batch.argtypes = [vp, C.c_double, C.c_int32, C.c_int32, vp, C.POINTER(Stats)]
+    L.wh_apply_adjoint.argtypes = [vp, vp, vp]
+    L.wh_adjoint.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32, vp, vp, vp,
+                             C.POINTER(Stats)]
+    L.wh_set_coefficient.argtypes = [vp, C.c_int32, vp]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -267,6 +272,38 @@ class Solver:
         for x in out:
             x.status = STATUS.get(status, status)
         return out
+
+    def apply_adjoint(self, w_in, w_out):
+        """w_out = S^T w_in (device tensors)."""
+        self._enter()
+        self._check(self.L.wh_apply_adjoint(self.h, _ptr(w_in), _ptr(w_out)))
+        self._leave()
+        return w_out
+
+    def adjoint(self, u, g, tol=1e-10, max_it=1000, restart=200):
+        """Adjoint solve and gradients for dJ/du = g at solution u (device tensors):
+        returns (lam, grad_c2, grad_f, stats)."""
+        torch = self._torch
+        lam = torch.zeros_like(u)
+        gc2 = torch.zeros_like(u)
+        gf = torch.zeros_like(u)
+        st = Stats()
+        self._enter()
+        status = self.L.wh_adjoint(self.h, _ptr(u), _ptr(g), tol, max_it, restart, _ptr(lam),
+                                   _ptr(gc2), _ptr(gf), C.byref(st))
+        self._leave()
+        self._check(status)
+        return lam, gc2, gf, st
+
+    def set_coefficient(self, gid, c2):
+        """Replace c(x)^2 of one grid (host array or None); re-run prepare() afterwards."""
+        arr = None if c2 is None else np.ascontiguousarray(c2, np.float64)
+        self._check(self.L.wh_set_coefficient(self.h, gid, _ptr(arr)))
+
+    def set_forcing(self, gid, f):
+        """Replace the forcing of one grid (host array); re-run prepare() afterwards."""
+        arr = np.ascontiguousarray(f, np.float64)
+        self._check(self.L.wh_set_forcing(self.h, gid, _ptr(arr)))
 
     def dot(self, x, y):
         out = C.c_double()

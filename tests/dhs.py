@@ -217,3 +217,67 @@ def solve(problem, omega=None):
         blk = U[lay.off[gi]:lay.off[gi] + e[0] * e[1]].reshape(e[1], e[0])
         out.append(blk[gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]].ravel())
     return np.concatenate(out)
+
+
+def adjoint_gradients(problem, P, d, omega=None):
+    """Gradients of J = 0.5 |P U - d|^2 for the direct discrete solution U with respect to
+    c^2 and f at every grid point, by the transpose solve of the assembled system
+    (independent of the WaveHoltz code):  A^T mu = E^T P^T (P U - d), and
+      dJ/d c2_p = -sum_rows mu_r (dA/dc2_p U)_r,  dJ/d f_p = sum_rows mu_r d rhs_r / d f_p.
+    Rows that scale with c2_p: the discretization row of p (its c^2 L_h part) and the
+    compatibility ghost rows of a Dirichlet boundary point p (order 4).  Returns
+    (U, J, grad_c2, grad_f) as compact vectors."""
+    omega = problem.omega if omega is None else omega
+    A, rhs, lay = assemble(problem, omega)
+    lu = spla.splu(A.tocsc())
+    Uext = lu.solve(rhs)
+    # compact <-> extended maps
+    idx = []
+    for gi, g in enumerate(problem.grids):
+        for j in range(g.n[1]):
+            for i in range(g.n[0]):
+                idx.append(lay.idx(gi, i, j))
+    idx = np.array(idx)
+    U = Uext[idx]
+    r = P @ U - d
+    J = 0.5 * float(r @ r)
+    src = np.zeros(lay.N)
+    src[idx] = P.T @ r
+    mu = lu.solve(src, trans="T")
+    AU = A @ Uext
+    # which rows scale with which point's c^2, and which rows carry f
+    n = len(idx)
+    gc2 = np.zeros(n)
+    gf = np.zeros(n)
+    comp = {}  # extended index of a compact point -> compact position
+    for k, q in enumerate(idx):
+        comp[q] = k
+    c2 = None if problem.c2 is None else np.concatenate([c.ravel() for c in problem.c2])
+    off = 0
+    for gi, g in enumerate(problem.grids):
+        for j in range(g.n[1]):
+            for i in range(g.n[0]):
+                k = off + j * g.n[0] + i
+                q = idx[k]
+                c2p = 1.0 if c2 is None else c2[k]
+                if g.mask[j, i] == G.DISC:
+                    gc2[k] -= mu[q] * (AU[q] - omega ** 2 * Uext[q]) / c2p
+                    gf[k] += mu[q]
+        # Dirichlet order-4 compatibility rows: ghost G1 row of boundary point b
+        if problem.order == 4:
+            for s_ in range(4):
+                if g.bc[s_] != G.BC_DIRICHLET:
+                    continue
+                a, hi = s_ // 2, s_ % 2
+                for t in range(g.n[1 - a]):
+                    bi, bj = ((g.n[0] - 1 if hi else 0), t) if a == 0 else (t, (g.n[1] - 1 if hi else 0))
+                    if g.mask[bj, bi] != G.DIRICHLET:
+                        continue
+                    gpos = lay.idx(gi, bi - 1 if (a == 0 and not hi) else (bi + 1 if a == 0 else bi),
+                                   bj - 1 if (a == 1 and not hi) else (bj + 1 if a == 1 else bj))
+                    k = off + bj * g.n[0] + bi
+                    c2p = 1.0 if c2 is None else c2[k]
+                    gc2[k] -= mu[gpos] * AU[gpos] / c2p
+                    gf[k] += mu[gpos]
+        off += g.npts
+    return U, J, gc2, gf

@@ -1,0 +1,154 @@
+"""Differentiation form: the transposed WaveHoltz map and gradients of a receiver misfit.
+
+* transposition: <S v, w> = <v, S^T w> to 1e-12 relative, S the zero-forcing iteration map;
+* gradients of J = 0.5 |P u - d|^2 (P: bilinear sampling at receivers on a circle of radius
+  1.5, d: data from a perturbed c) w.r.t. c(x)^2 and f against central finite differences
+  in random directions (1e-6 relative) and against an independent adjoint of the direct
+  discrete Helmholtz system (tests/dhs.py)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2504_03074_gb300 import grids as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available()
+    return T
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2504_03074_gb300 import build
+    build.build()
+    from paper_2504_03074_gb300 import waveholtz
+    return waveholtz
+
+
+CASES = [
+    ("square-o2", lambda: G.unit_square_problem(24, 2, 10.0)),
+    ("square-o4", lambda: G.unit_square_problem(24, 4, 10.0)),
+    ("channel-neumann-o4", lambda: G.channel_problem(24, 4, 5.0, bc=G.BC_NEUMANN)),
+    ("torus-o4-box", lambda: G.sheared_torus_problem(24, 20, 4)),
+    ("disk-o2", lambda: G.disk_problem(nb=48, nth=96, nr=10, order=2, omega=4.0, width=0.8,
+                                       r_cut=0.75)),
+    ("disk-o4", lambda: G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, width=0.8,
+                                       r_cut=0.75)),
+    ("disk-o4-cx", lambda: G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, c_bumps=8,
+                                          width=0.8, r_cut=0.75)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_transposition(torch, W, name, make):
+    prob = make()
+    s = W.Solver(prob)
+    s.prepare()
+    rng = np.random.default_rng(1)
+    act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
+    v = rng.standard_normal(prob.n_total) * act
+    w = rng.standard_normal(prob.n_total) * act
+    vt = torch.from_numpy(v).cuda()
+    wt = torch.from_numpy(w).cuda()
+    sv = torch.empty_like(vt)
+    stw = torch.empty_like(wt)
+    s.iterate(vt, sv, False)
+    s.apply_adjoint(wt, stw)
+    torch.cuda.synchronize()
+    lhs = float(sv.cpu().numpy() @ w)
+    rhs = float(v @ stw.cpu().numpy())
+    scale = np.linalg.norm(sv.cpu().numpy()) * np.linalg.norm(w)
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
+
+
+def receivers(prob, n=16, radius=1.5):
+    """Bilinear sampling matrix of n points on a circle, from the background grid."""
+    g = prob.grids[0]
+    th = 2 * np.pi * (np.arange(n) + 0.5) / n
+    xs, ys = radius * np.cos(th), radius * np.sin(th)
+    rows, cols, vals = [], [], []
+    for k, (x, y) in enumerate(zip(xs, ys)):
+        fi, fj = (x - g.origin[0]) / g.h[0], (y - g.origin[1]) / g.h[1]
+        i0, j0 = int(np.floor(fi)), int(np.floor(fj))
+        a, b = fi - i0, fj - j0
+        for di, dj, wgt in ((0, 0, (1 - a) * (1 - b)), (1, 0, a * (1 - b)), (0, 1, (1 - a) * b),
+                            (1, 1, a * b)):
+            rows.append(k)
+            cols.append((j0 + dj) * g.n[0] + (i0 + di))
+            vals.append(wgt)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, prob.n_total))
+
+
+@pytest.fixture(scope="module")
+def misfit_problem():
+    prob = G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, c_bumps=8, width=0.8,
+                          r_cut=0.75, seed=5)
+    P = receivers(prob)
+    # data from a perturbed speed: c^2 scaled by 1.05 inside a blob
+    import copy
+    pert = copy.deepcopy(prob)
+    pert.c2 = [c * (1 + 0.05 * np.exp(-((g.xy[0] - 0.9) ** 2 + (g.xy[1] + 0.4) ** 2) / 0.3))
+               for c, g in zip(prob.c2, prob.grids)]
+    import dhs
+    d = P @ dhs.solve(pert)
+    return prob, P, d
+
+
+def solve_u(torch, W, prob, c2=None, f=None):
+    s = W.Solver(prob)
+    if c2 is not None:
+        for gi, c in enumerate(prob.split(c2)):
+            s.set_coefficient(gi, c)
+    if f is not None:
+        for gi, ff in enumerate(prob.split(f)):
+            s.set_forcing(gi, ff)
+    ti = s.prepare()
+    u = torch.zeros(prob.n_total, dtype=torch.float64, device="cuda")
+    st = s.solve(u, W.GMRES, tol=1e-13, max_it=800, restart=400)
+    assert st.converged == 1, (st.status, st.residual)
+    return s, u, ti
+
+
+def test_gradient_vs_finite_differences_and_direct_adjoint(torch, W, misfit_problem):
+    import dhs
+    prob, P, d = misfit_problem
+    s, u, ti = solve_u(torch, W, prob)
+    un = u.cpu().numpy()
+    r = P @ un - d
+    g = torch.from_numpy(P.T @ r).cuda()
+    lam, gc2, gf, st = s.adjoint(u, g, tol=1e-13, max_it=800, restart=400)
+    assert st.converged == 1
+    gc2 = gc2.cpu().numpy()
+    gf = gf.cpu().numpy()
+    # independent adjoint of the direct discrete system
+    U, J0, gc2_d, gf_d = dhs.adjoint_gradients(prob, P, d)
+    assert np.max(np.abs(un - U)) <= 1e-9 * np.max(np.abs(U))
+    assert np.linalg.norm(gc2 - gc2_d) <= 1e-6 * np.linalg.norm(gc2_d)
+    assert np.linalg.norm(gf - gf_d) <= 1e-6 * np.linalg.norm(gf_d)
+    # central finite differences in random directions
+    c2 = np.concatenate([c.ravel() for c in prob.c2])
+    f = np.concatenate([x.ravel() for x in prob.f])
+    rng = np.random.default_rng(2)
+
+    def J_of(c2v, fv):
+        s2, u2, ti2 = solve_u(torch, W, prob, c2=c2v, f=fv)
+        assert ti2.M == ti.M
+        rr = P @ u2.cpu().numpy() - d
+        return 0.5 * float(rr @ rr)
+
+    for kind in ("c2", "c2", "f", "f"):
+        dirn = rng.standard_normal(prob.n_total)
+        if kind == "c2":
+            eps = 1e-5
+            jp, jm = J_of(c2 + eps * dirn * c2, f), J_of(c2 - eps * dirn * c2, f)
+            pred = float(gc2 @ (dirn * c2))
+        else:
+            eps = 1e-5 * np.max(np.abs(f))
+            jp, jm = J_of(c2, f + eps * dirn), J_of(c2, f - eps * dirn)
+            pred = float(gf @ dirn)
+        fd = (jp - jm) / (2 * eps)
+        assert abs(fd - pred) <= 1e-6 * max(abs(fd), abs(pred)) + 1e-14, (kind, fd, pred)
