@@ -82,6 +82,10 @@ typedef struct {
   int32_t launch_mode;  /* WH_LAUNCH_GRAPH (default) or WH_LAUNCH_PERSISTENT */
   uint64_t barrier_spin_limit;  /* polls before a grid barrier of the persistent kernel
                                    gives up (WH_ERR_TIMEOUT); 0 = default (2^22, ~1 s) */
+  uint64_t trajectory_bytes;    /* wh_adjoint keeps the whole forward trajectory (M + 1
+                                   states) in device memory when it needs at most this
+                                   many bytes, else recomputes it from checkpoints every
+                                   16 steps; 0 = default (half the free device memory) */
 } wh_options;
 
 /* One component grid (Sec. 3.1).  All pointers are host pointers, read during the call.
@@ -234,9 +238,14 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
  * a scalar misfit J(u) (DEVICE compact vectors), solves (I - S)^T lam = g by GMRES(restart)
  * to relative residual tol (lam: DEVICE compact, output), then returns
  *   grad_c2 = dJ/d(c^2) and grad_f = dJ/df  (DEVICE compact, one value per grid point)
- * from a reverse sweep whose forward states (the march from u with forcing) are recomputed
- * from checkpoints every 16 time steps.  The time step is held fixed (it changes only when
- * Nt does).  Synchronises. */
+ * from one reverse sweep over the forward states (the march from u with forcing): all of
+ * them kept in device memory (see wh_options.trajectory_bytes; the buffer stays with the
+ * context), else recomputed from checkpoints every 16 time steps.  The time step is held fixed (it changes only when
+ * Nt does); the fixed point is the discrete Helmholtz solution at omega whatever the time
+ * step (Sec. 2, the omega-tilde recipe), so these are also the gradients of that solution.
+ * Errors: WH_ERR_NOT_CONVERGED when max_it products end above tol (lam then holds the last
+ * iterate and grad_c2, grad_f the gradients for it); WH_ERR_STATE before wh_prepare;
+ * WH_ERR_ARG on a context with several instances.  Synchronises. */
 wh_status wh_apply_adjoint(wh_ctx *ctx, const double *w_in, double *w_out);
 wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, int32_t max_it,
                      int32_t restart, double *lam, double *grad_c2, double *grad_f,

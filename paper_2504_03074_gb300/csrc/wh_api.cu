@@ -92,15 +92,19 @@ struct wh_ctx {
   int64_t tabs_cap = 0;
   int32_t *d_rinst = nullptr;
   int maxM = 0;
-  // differentiation: transpose constraint lists (CSR over extended source points) and
-  // buffers; built on the first adjoint call after wh_prepare
+  // differentiation: transpose constraint lists (CSR over the discretization points that
+  // constrained positions read: d_fq the points, d_roff their entry ranges) and buffers;
+  // built on the first adjoint call after wh_prepare
   bool adj_ready = false;
   bool adjoint_mode = false;  // apply_A uses S^T (adjoint GMRES)
-  int64_t *d_roff = nullptr, *d_rpos = nullptr;
+  int64_t nfix = 0;
+  int64_t *d_fq = nullptr, *d_roff = nullptr, *d_rpos = nullptr;
   double *d_rcoef = nullptr;
   double *d_adj = nullptr;   // lam, Y, Z x3, gc2, gf (extended)
   double *d_ckpt = nullptr;  // checkpoints and segment states
   int64_t ckpt_cap = 0;
+  double *d_traj = nullptr;  // the whole forward trajectory X^0 .. X^M (when it fits)
+  int64_t traj_cap = 0;
 
   // solver workspace
   double *d_q = nullptr;  // Krylov basis
@@ -156,6 +160,19 @@ wh_status dalloc(wh_ctx *ctx, T **p, size_t n) {
   return WH_OK;
 }
 
+// Free one buffer from dalloc before the context is reset.
+template <typename T>
+void dfree(wh_ctx *ctx, T **p) {
+  if (!*p) return;
+  for (size_t k = 0; k < ctx->allocs.size(); ++k)
+    if (ctx->allocs[k] == (void *)*p) {
+      ctx->allocs.erase(ctx->allocs.begin() + k);
+      break;
+    }
+  cudaFree(*p);
+  *p = nullptr;
+}
+
 void drop_graphs(wh_ctx *ctx) {
   for (auto &S : ctx->set)
     for (auto &g : S.gexec)
@@ -182,9 +199,10 @@ void free_device(wh_ctx *ctx) {
   ctx->d_tabs = nullptr;
   ctx->tabs_cap = 0;
   ctx->adj_ready = false;
-  ctx->d_roff = ctx->d_rpos = nullptr;
-  ctx->d_rcoef = ctx->d_adj = ctx->d_ckpt = nullptr;
-  ctx->ckpt_cap = 0;
+  ctx->nfix = 0;
+  ctx->d_fq = ctx->d_roff = ctx->d_rpos = nullptr;
+  ctx->d_rcoef = ctx->d_adj = ctx->d_ckpt = ctx->d_traj = nullptr;
+  ctx->ckpt_cap = ctx->traj_cap = 0;
   ctx->d_bar = nullptr;
 }
 
@@ -1037,24 +1055,38 @@ wh_status adj_setup(wh_ctx *ctx) {
     for (int64_t r = 0; r < ctx->nrecv; ++r)
       for (int d = 0; d < ND; ++d) ent.push_back({didx[r * ND + d], ridx[r], dw[r * ND + d]});
   }
-  std::vector<int64_t> off(total + 1, 0), pos(ent.size());
-  std::vector<double> coef(ent.size());
-  for (const Ent &e : ent) off[e.src + 1]++;
-  for (int64_t q = 0; q < total; ++q) off[q + 1] += off[q];
-  std::vector<int64_t> fill(off.begin(), off.end() - 1);
+  // CSR over source points; only discretization sources are kept (D zeroes the rest)
+  std::vector<int8_t> mask(total);
+  CK(cudaMemcpy(mask.data(), ctx->d_mask, total, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> cnt(total, 0);
+  for (const Ent &e : ent)
+    if (mask[e.src] == WH_DISC) cnt[e.src]++;
+  std::vector<int64_t> fq, off(1, 0), first(total, -1);
+  for (int64_t q = 0; q < total; ++q)
+    if (cnt[q]) {
+      first[q] = off.back();
+      fq.push_back(q);
+      off.push_back(off.back() + cnt[q]);
+    }
+  std::vector<int64_t> pos(off.back());
+  std::vector<double> coef(off.back());
   for (const Ent &e : ent) {
-    const int64_t k = fill[e.src]++;
+    if (mask[e.src] != WH_DISC) continue;
+    const int64_t k = first[e.src]++;
     pos[k] = e.pos;
     coef[k] = e.c;
   }
+  ctx->nfix = (int64_t)fq.size();
   wh_status st;
-  if ((st = dalloc(ctx, &ctx->d_roff, off.size())) ||
+  if ((st = dalloc(ctx, &ctx->d_fq, std::max<size_t>(fq.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_roff, off.size())) ||
       (st = dalloc(ctx, &ctx->d_rpos, std::max<size_t>(pos.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_rcoef, std::max<size_t>(coef.size(), 1))) ||
       (!ctx->d_adj && (st = dalloc(ctx, &ctx->d_adj, 7 * (size_t)total))))
     return st;
   CK(cudaMemcpy(ctx->d_roff, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
-  if (!pos.empty()) {
+  if (!fq.empty()) {
+    CK(cudaMemcpy(ctx->d_fq, fq.data(), fq.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_rpos, pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_rcoef, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice));
   }
@@ -1079,28 +1111,43 @@ void host_tables(const wh_ctx *ctx, std::vector<double> &fc, std::vector<double>
   }
 }
 
-// One forward time step n (march + ghost rules/interpolation of level n+1) on the FP64 set.
-void forward_step(wh_ctx *ctx, int n, double fs) {
+// One forward time step n on the FP64 set: X^{n+1} into Wout from Wn = X^n and
+// Wprev = X^{n-1} (march, then ghost rules and interpolation of level n+1).
+void forward_step(wh_ctx *ctx, int n, const double *Wn, const double *Wprev, double *Wout) {
   const int order = ctx->opt.order;
   cudaStream_t s = ctx->stream;
   const int nbc = (int)ctx->hbc.size();
   const int bc_blocks = (nbc + 255) / 256;
   const int bg_blocks = bc_blocks + (int)((ctx->nrecv * (order == 4 ? 8 : 4) + 255) / 256);
   const int ntiles = (int)ctx->htiles.size();
-  void *cur = (n & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (n & 1) ? ctx->d_Wa : ctx->d_Wb;
   launch_march(false, order, n == 0, std::min(ntiles, ctx->march_blocks), ntiles, s, ctx->d_grids,
-               ctx->d_tiles, ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst,
-               n, fs);
+               ctx->d_tiles, ctx->d_mask, Wn, Wout, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst,
+               n, 1.0, Wprev);
   if (bg_blocks)
     launch_bc_gather(false, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx, ctx->d_dw,
-                     ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, oth, ctx->d_F, ctx->d_inst,
-                     n + 1, fs);
+                     ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, Wout, ctx->d_F, ctx->d_inst,
+                     n + 1, 1.0);
+}
+
+// X^0 = C E u into W (input kernel, then ghost rules and interpolation of level 0).
+void forward_start(wh_ctx *ctx, const double *u, double *W) {
+  const int order = ctx->opt.order;
+  cudaStream_t s = ctx->stream;
+  const int ng = (int)ctx->hgrids.size();
+  launch_init(false, (unsigned)((ctx->total + 255) / 256), s, ctx->d_grids, ng, ctx->d_mask, u, W,
+              ctx->d_V, ctx->total, ctx->d_inst);
+  const int bc_blocks = ((int)ctx->hbc.size() + 255) / 256;
+  const int bg_blocks = bc_blocks + (int)((ctx->nrecv * (order == 4 ? 8 : 4) + 255) / 256);
+  if (bg_blocks)
+    launch_bc_gather(false, order, bg_blocks, s, ctx->d_bc, (int)ctx->hbc.size(), bc_blocks,
+                     ctx->d_didx, ctx->d_dw, ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, W,
+                     ctx->d_F, ctx->d_inst, 0, 1.0);
 }
 
 // The reverse sweep.  lam: extended adjoint source.  Without gradients: Z^0 = S^T lam is
 // left in the returned buffer.  With gradients (u != nullptr, compact): the forward states
-// of the march from u (forcing on) are recomputed from checkpoints and d(lam . W_h)/dc^2,
-// d(lam . W_h)/df are accumulated (extended) into gc2, gf.
+// X^n of the march from u (forcing on) are kept whole or recomputed from checkpoints, and
+// d(lam . W_h)/df and c^2 d(lam . W_h)/dc^2 are accumulated (extended) into gf, gc2.
 wh_status adj_sweep(wh_ctx *ctx, const double *lam, double **z0_out, const double *u,
                     double *gc2, double *gf) {
   const int order = ctx->opt.order, M = ctx->iti[0].M;
@@ -1115,75 +1162,98 @@ wh_status adj_sweep(wh_ctx *ctx, const double *lam, double **z0_out, const doubl
   CK(cudaMemsetAsync(Zb[1], 0, total * sizeof(double), s));
   const bool grad = u != nullptr;
   const int nseg = (M + kCkptEvery - 1) / kCkptEvery;
+  const double *F = (const double *)ctx->d_F;
+  bool whole = false;
   double *ck = nullptr, *seg = nullptr;
   wh_status st;
   if (grad) {
-    // checkpoints: (X^s, X^{s-1}) at s = 0, 16, ...; segment states X^s .. X^{s+16}
-    const int64_t need = (2 * (int64_t)nseg + kCkptEvery + 1) * total;
+    const int64_t need = (int64_t)(M + 1) * total;
+    uint64_t cap = ctx->opt.trajectory_bytes;
+    if (!cap) {
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      cap = (uint64_t)fr / 2 + (uint64_t)ctx->traj_cap * 8;  // a held buffer counts as free
+    }
+    whole = (uint64_t)need * 8 <= cap;
+    if (whole && ctx->traj_cap < need) {
+      dfree(ctx, &ctx->d_traj);
+      ctx->traj_cap = 0;
+      if ((st = dalloc(ctx, &ctx->d_traj, (size_t)need))) return st;
+      ctx->traj_cap = need;
+    }
+  }
+  if (grad && whole) {
+    // X^n in slot n: the march writes each level into its own slot
+    double *X = ctx->d_traj;
+    forward_start(ctx, u, X);
+    for (int n = 0; n < M; ++n)
+      forward_step(ctx, n, X + (int64_t)n * total, X + (int64_t)(n ? n - 1 : 0) * total,
+                   X + (int64_t)(n + 1) * total);
+    CK(cudaGetLastError());
+  } else if (grad) {
+    // checkpoints (X^s, X^{s-1}) at s = 0, 16, ...; a segment buffer for X^{s-1} .. X^{s+16}
+    const int64_t need = (2 * (int64_t)nseg + kCkptEvery + 2) * total;
     if (ctx->ckpt_cap < need) {
+      dfree(ctx, &ctx->d_ckpt);
+      ctx->ckpt_cap = 0;
       if ((st = dalloc(ctx, &ctx->d_ckpt, (size_t)need))) return st;
       ctx->ckpt_cap = need;
     }
     ck = ctx->d_ckpt;
     seg = ctx->d_ckpt + 2 * (int64_t)nseg * total;
-    // forward march from u with forcing, saving checkpoints
-    launch_init(false, (unsigned)((total + 255) / 256), s, ctx->d_grids, ng, ctx->d_mask, u,
-                ctx->d_Wa, ctx->d_V, total, ctx->d_inst);
-    const int bc_blocks = ((int)ctx->hbc.size() + 255) / 256;
-    const int bg_blocks = bc_blocks + (int)((ctx->nrecv * (order == 4 ? 8 : 4) + 255) / 256);
-    if (bg_blocks)
-      launch_bc_gather(false, order, bg_blocks, s, ctx->d_bc, (int)ctx->hbc.size(), bc_blocks,
-                       ctx->d_didx, ctx->d_dw, ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv,
-                       ctx->d_Wa, ctx->d_F, ctx->d_inst, 0, 1.0);
+    double *Wa = (double *)ctx->d_Wa, *Wb = (double *)ctx->d_Wb;
+    forward_start(ctx, u, Wa);
     for (int n = 0; n < M; ++n) {
+      double *cur = (n & 1) ? Wb : Wa, *oth = (n & 1) ? Wa : Wb;
       if (n % kCkptEvery == 0) {
         const int k = n / kCkptEvery;
-        void *cur = (n & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (n & 1) ? ctx->d_Wa : ctx->d_Wb;
         CK(cudaMemcpyAsync(ck + (2 * k) * total, cur, total * 8, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(ck + (2 * k + 1) * total, oth, total * 8, cudaMemcpyDeviceToDevice, s));
       }
-      forward_step(ctx, n, 1.0);
+      forward_step(ctx, n, cur, oth, oth);
     }
     CK(cudaGetLastError());
   }
+  int s0 = 0;  // first level of the current segment (checkpoint mode)
+  auto state = [&](int k) -> const double * {
+    if (whole) return ctx->d_traj + (int64_t)k * total;
+    return seg + (int64_t)(k - s0 + 1) * total;  // X^{s0-1} .. X^{e0+1}
+  };
   // level M
   int iz_new = 2, iz1 = 0, iz2 = 1;  // Z^{n+1} in Zb[iz1], Z^{n+2} in Zb[iz2]
   launch_adj_step(order, s, ctx->d_grids, ng, ctx->d_mask, (const double *)ctx->d_Wt, lam, wf[M],
-                  1.0, Zb[iz1], Zb[iz2], Y, total, nullptr, ctx->d_c2, 0.0, gc2, gf);
-  if (grad)
-    launch_adj_bc_grad(s, ctx->d_bc, (int)ctx->hbc.size(), Y, (const double *)ctx->d_F, ctx->d_c2,
-                       cosn[M], gc2, gf);
-  launch_adj_ct(s, ctx->d_mask, Y, ctx->d_roff, ctx->d_rpos, ctx->d_rcoef, Zb[iz_new], total);
+                  1.0, Zb[iz1], Zb[iz2], Y, Zb[iz_new], total, nullptr, nullptr, nullptr, F, 0.0,
+                  gc2, gf);
+  launch_adj_post(s, ctx->d_fq, ctx->d_roff, ctx->d_rpos, ctx->d_rcoef, Y, Zb[iz_new], ctx->nfix,
+                  ctx->d_bc, (int)ctx->hbc.size(), F, cosn[M], grad ? gc2 : nullptr, gf);
   // rotate: Z^{M+2} <- Z^{M+1}, Z^{M+1} <- Z^M
   int t = iz2;
   iz2 = iz1;
   iz1 = iz_new;
   iz_new = t;
   for (int sidx = nseg - 1; sidx >= 0; --sidx) {
-    const int s0 = sidx * kCkptEvery, e0 = std::min(s0 + kCkptEvery - 1, M - 1);
-    if (grad) {
-      // restore X^{s0}, X^{s0-1} and recompute X^{s0} .. X^{e0} into the segment buffer
-      void *cur = (s0 & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (s0 & 1) ? ctx->d_Wa : ctx->d_Wb;
-      CK(cudaMemcpyAsync(cur, ck + (2 * sidx) * total, total * 8, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(oth, ck + (2 * sidx + 1) * total, total * 8, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(seg, cur, total * 8, cudaMemcpyDeviceToDevice, s));
-      for (int n = s0; n < e0; ++n) {
-        forward_step(ctx, n, 1.0);
-        void *nxt = ((n + 1) & 1) ? ctx->d_Wb : ctx->d_Wa;
-        CK(cudaMemcpyAsync(seg + (int64_t)(n + 1 - s0) * total, nxt, total * 8,
-                           cudaMemcpyDeviceToDevice, s));
-      }
+    s0 = sidx * kCkptEvery;
+    const int e0 = std::min(s0 + kCkptEvery - 1, M - 1);
+    if (grad && !whole) {
+      // restore X^{s0}, X^{s0-1} and recompute X^{s0+1} .. X^{e0+1} into the segment slots
+      CK(cudaMemcpyAsync(seg, ck + (2 * sidx + 1) * total, total * 8, cudaMemcpyDeviceToDevice,
+                         s));
+      CK(cudaMemcpyAsync(seg + total, ck + (2 * sidx) * total, total * 8,
+                         cudaMemcpyDeviceToDevice, s));
+      for (int n = s0; n <= e0; ++n)
+        forward_step(ctx, n, state(n), state(n - 1), (double *)state(n + 1));
     }
     for (int n = e0; n >= s0; --n) {
       const double sc = n == 0 ? 0.5 : 1.0;
       const double fcn = n == 0 ? 0.5 * ctx->iti[0].dt * ctx->iti[0].dt : fc[n];
-      const double *Xn = grad ? seg + (int64_t)(n - s0) * total : nullptr;
+      const double *Xp = grad && n > 0 ? state(n - 1) : nullptr;
+      const double *Xn = grad ? state(n) : nullptr, *Xx = grad ? state(n + 1) : nullptr;
       launch_adj_step(order, s, ctx->d_grids, ng, ctx->d_mask, (const double *)ctx->d_Wt, lam,
-                      wf[n], sc, Zb[iz1], Zb[iz2], Y, total, Xn, ctx->d_c2, fcn, gc2, gf);
-      if (grad)
-        launch_adj_bc_grad(s, ctx->d_bc, (int)ctx->hbc.size(), Y, (const double *)ctx->d_F,
-                           ctx->d_c2, cosn[n], gc2, gf);
-      launch_adj_ct(s, ctx->d_mask, Y, ctx->d_roff, ctx->d_rpos, ctx->d_rcoef, Zb[iz_new], total);
+                      wf[n], sc, Zb[iz1], Zb[iz2], Y, Zb[iz_new], total, Xp, Xn, Xx, F, fcn, gc2,
+                      gf);
+      launch_adj_post(s, ctx->d_fq, ctx->d_roff, ctx->d_rpos, ctx->d_rcoef, Y, Zb[iz_new],
+                      ctx->nfix, ctx->d_bc, (int)ctx->hbc.size(), F, cosn[n],
+                      grad ? gc2 : nullptr, gf);
       t = iz2;
       iz2 = iz1;
       iz1 = iz_new;
@@ -1225,6 +1295,7 @@ wh_status wh_options_default(wh_options *opt) {
   opt->precision = WH_FP64;
   opt->launch_mode = WH_LAUNCH_GRAPH;
   opt->barrier_spin_limit = 0;
+  opt->trajectory_bytes = 0;
   return WH_OK;
 }
 
@@ -1912,9 +1983,7 @@ wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, 
         S.converged = 1;
         break;
       }
-      if (L.products[0] >= max_it)
-        return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "adjoint GMRES: %d products, residual %g",
-                           max_it, S.residual));
+      if (L.products[0] >= max_it) break;  // gradients of the last lam, then NOT_CONVERGED
     }
   } else {
     S.converged = 1;
@@ -1927,10 +1996,14 @@ wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, 
   CK(cudaMemsetAsync(gf, 0, total * sizeof(double), s));
   double *z0;
   if ((st = adj_sweep(ctx, lam_ext, &z0, u, gc2, gf))) return finish(st);
-  launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, gc2, grad_c2, n, 0);
+  // the sweep accumulates c^2 dJ/dc^2
+  launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, gc2, grad_c2, n, 0, ctx->d_c2);
   launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, gf, grad_f, n, 0);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  if (!S.converged)
+    return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "adjoint GMRES: %d products, residual %g",
+                       max_it, S.residual));
   return finish(WH_OK);
 }
 

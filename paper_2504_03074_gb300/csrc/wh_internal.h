@@ -112,7 +112,7 @@ struct IterArgs {
 void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
                   void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
-                  int n, double fs);
+                  int n, double fs, const void *Wprev = nullptr);  // W^{n-1}: Wout if null
 int march_blocks_per_sm(bool fp32, int order);
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
@@ -139,17 +139,20 @@ void launch_bc_coef(int nbc, cudaStream_t s, BcItem *bc, const int32_t *ig, cons
                     const double *c2);
 void launch_adj_step(int order, cudaStream_t s, const DevGrid *grids, int ngrids,
                      const int8_t *mask, const double *Wt, const double *lam, double wn,
-                     double sc, const double *Z1, const double *Z2, double *Y, int64_t total,
-                     const double *Xn, const double *c2, double fc, double *gc2, double *gf);
-void launch_adj_ct(cudaStream_t s, const int8_t *mask, const double *Y, const int64_t *roff,
-                   const int64_t *rpos, const double *rcoef, double *Z, int64_t total);
-void launch_adj_bc_grad(cudaStream_t s, const BcItem *bc, int nbc, const double *Y,
-                        const double *F, const double *c2, double fcos, double *gc2,
-                        double *gf);
+                     double sc, const double *Z1, const double *Z2, double *Y, double *Znew,
+                     int64_t total, const double *Xprev, const double *Xn, const double *Xnext,
+                     const double *F, double fc, double *gc2, double *gf);
+// Z += the constraint part of D C^T Y at the listed points; with gc2 non-null also the
+// Dirichlet compatibility gradient terms of this level (fcos = cos(omega_e t^n)).
+void launch_adj_post(cudaStream_t s, const int64_t *fq, const int64_t *foff, const int64_t *rpos,
+                     const double *rcoef, const double *Y, double *Z, int64_t nfix,
+                     const BcItem *bc, int nbc, const double *F, double fcos, double *gc2,
+                     double *gf);
 void launch_compact_to_ext(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
                            const double *v, double *x, int64_t total);
 void launch_ext_to_compact(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
-                           const double *x, double *v, int64_t ncompact, int disc_only);
+                           const double *x, double *v, int64_t ncompact, int disc_only,
+                           const double *div = nullptr);
 constexpr int kRedThreads = 256;
 void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
                      const double *y, int64_t n, double *partial, double *out);

@@ -52,7 +52,7 @@ __device__ __forceinline__ int64_t row_off(const DevGrid &G, int jj) {
 template <typename T, int ORDER, bool FIRST>
 __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
                                             const int8_t *__restrict__ mask,
-                                            const T *Wn, T *Wout,
+                                            const T *Wn, const T *Wprev, T *Wout,
                                             const T *__restrict__ F, const T *__restrict__ Wt,
                                             double *V, T fc, double wf_new, double wf_cur) {
   constexpr int R = ORDER / 2;
@@ -69,7 +69,7 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
     const T c0 = (T)G.cw[0], x1 = (T)G.cw[1], y1 = (T)G.cw[3];
     const int64_t up = row_off(G, j + 1) + i, dn = row_off(G, j - 1) + i;
     const int im = wrap(i - 1, G.n0, G.per0), ip = wrap(i + 1, G.n0, G.per0);
-    a = FIRST ? c0 * Wn[p] : fma(c0, Wn[p], -Wout[p]);
+    a = FIRST ? c0 * Wn[p] : fma(c0, Wn[p], -Wprev[p]);
     a = fma(x1, Wn[row + im], a);
     a = fma(x1, Wn[row + ip], a);
     a = fma(y1, Wn[dn], a);
@@ -86,7 +86,7 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
   } else if (G.stencil == kPointCross) {
     // planes: centre, axis-0 offsets -R..-1, 1..R, axis-1 offsets -R..-1, 1..R
     const int64_t q = G.wbase + (p - G.base), E = G.ext;
-    a = FIRST ? Wt[q] * Wn[p] : fma(Wt[q], Wn[p], -Wout[p]);
+    a = FIRST ? Wt[q] * Wn[p] : fma(Wt[q], Wn[p], -Wprev[p]);
     int pl = 1;
 #pragma unroll
     for (int k = -R; k <= R; ++k) {
@@ -103,7 +103,7 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
   } else {
     // box: plane (b + R) * (2R + 1) + (a + R) holds the weight of offset (a, b)
     const int64_t q = G.wbase + (p - G.base), E = G.ext;
-    a = FIRST ? (T)0 : -Wout[p];
+    a = FIRST ? (T)0 : -Wprev[p];
 #pragma unroll
     for (int b = -R; b <= R; ++b) {
       const int64_t rb = row_off(G, j + b);
@@ -176,7 +176,7 @@ __device__ __forceinline__ void gather_group(int r, int lane, bool live,
 template <typename T, int ORDER, bool FIRST>
 __global__ void __launch_bounds__(kTileX *kTileY)
     march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
-                 const int8_t *__restrict__ mask, const T *Wn, T *Wout,
+                 const int8_t *__restrict__ mask, const T *Wn, const T *Wprev, T *Wout,
                  const T *__restrict__ F, const T *__restrict__ Wt, double *V,
                  const InstDev *__restrict__ inst, int n, double fs) {
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     for (int m = 0; m < kPY; ++m) {
       const int j = t.j0 + (int)threadIdx.y + m * kTileY;
       if (j < G.n1)
-        march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wout, F, Wt, V, fc, wf_new, wf_cur);
+        march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wprev, Wout, F, Wt, V, fc, wf_new,
+                                     wf_cur);
     }
   }
 }
@@ -544,10 +545,11 @@ __device__ __forceinline__ bool ext_locate(const DevGrid *__restrict__ grids, in
   g = 0;
   while (g + 1 < ngrids && p >= grids[g + 1].base) ++g;
   const DevGrid &G = grids[g];
-  const int64_t o = p - G.base;
-  if (o >= G.ext) return false;
-  j = (int)(o / G.pitch) - G.g1;
-  i = (int)(o % G.pitch) - G.g0;
+  const int64_t o64 = p - G.base;
+  if (o64 >= G.ext) return false;
+  const int o = (int)o64;  // the whole state is below 2^31 entries (checked at layout)
+  j = o / G.pitch - G.g1;
+  i = o - (j + G.g1) * G.pitch - G.g0;
   return i < G.n0 + G.g0;
 }
 
@@ -562,56 +564,82 @@ __device__ __forceinline__ bool nb_index(const DevGrid &G, int i, int j, int64_t
   return true;
 }
 
-// Y = w_n lam (active points) + s (A^T Z1) - Z2 at every extended point.  In gradient mode
-// (Xn != nullptr) discretization points also add the parameter gradients of the step
-// n -> n+1: gf -= fc Z1, gc2 += s Z1 ((A Xn) - 2 Xn) / c^2.
+// Neighbour (i + di, j + dj) of point q = (i, j): plain offsets for interior points (every
+// neighbour of the stencil inside the discretization range, no wrap), else nb_index.
+__device__ __forceinline__ bool nbr(const DevGrid &G, int64_t q, int i, int j, int di, int dj,
+                                    bool interior, int64_t &p) {
+  if (interior) {
+    p = q + di + (int64_t)dj * G.pitch;
+    return true;
+  }
+  return nb_index(G, i + di, j + dj, p);
+}
+
+// One reverse step at every extended point q:
+//   Y = w_n lam (active points) + s (A^T Z1) - Z2,  Znew = D Y (Y at discretization points,
+//   0 elsewhere; the constraint part of C^T is added afterwards by adj_post_kernel).
+// In gradient mode (Xn != nullptr; Xprev, Xn, Xnext the forward states n-1, n, n+1, Xprev
+// null at n = 0) discretization points also add the parameter gradients of the step
+// n -> n+1: gf -= fc Z1, c^2 gc2 += s Z1 ((A Xn) - 2 Xn) (gc2 is accumulated times c^2
+// and divided by it when the sweep ends).
 template <int ORDER>
 __global__ void adj_step_kernel(const DevGrid *__restrict__ grids, int ngrids,
                                 const int8_t *__restrict__ mask, const double *__restrict__ Wt,
                                 const double *__restrict__ lam, double wn, double sc,
                                 const double *__restrict__ Z1, const double *__restrict__ Z2,
-                                double *Y, int64_t total, const double *__restrict__ Xn,
-                                const double *__restrict__ c2, double fc, double *gc2,
-                                double *gf) {
+                                double *__restrict__ Y, double *__restrict__ Znew, int64_t total,
+                                const double *__restrict__ Xprev, const double *__restrict__ Xn,
+                                const double *__restrict__ Xnext, const double *__restrict__ F,
+                                double fc, double *gc2, double *gf) {
   constexpr int R = ORDER / 2;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= total) return;
   int g, i, j;
   if (!ext_locate(grids, ngrids, q, g, i, j)) {
     Y[q] = 0.0;
+    Znew[q] = 0.0;
     return;
   }
   const DevGrid &G = grids[g];
   const int8_t mk = mask[q];
+  if (mk == 0 && i >= 0 && i < G.n0 && j >= 0 && j < G.n1) {
+    // unused point inside the grid: not a discretization point and not a constrained
+    // position (those are receivers and ghost lines), so its Y is never read
+    Y[q] = 0.0;
+    Znew[q] = 0.0;
+    return;
+  }
+  const bool interior = i >= R && i < G.n0 - R && j >= R && j < G.n1 - R;
   double at = 0.0;  // (A^T Z1)[q] = sum_o A[q - o, q] Z1[q - o]
   if (G.stencil == kConstCross) {
     // constant symmetric weights: A^T Z = A Z
-    const double cw[5] = {G.cw[0], G.cw[1], G.cw[2], G.cw[3], G.cw[4]};
     int64_t pn;
-    if (nb_index(G, i, j, pn)) at += cw[0] * Z1[pn];
+    if (nbr(G, q, i, j, 0, 0, interior, pn)) at += G.cw[0] * Z1[pn];
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
-      const double wx = cw[k], wy = cw[2 + k];
-      if (nb_index(G, i - k, j, pn)) at += wx * Z1[pn];
-      if (nb_index(G, i + k, j, pn)) at += wx * Z1[pn];
-      if (nb_index(G, i, j - k, pn)) at += wy * Z1[pn];
-      if (nb_index(G, i, j + k, pn)) at += wy * Z1[pn];
+      const double wx = G.cw[k], wy = G.cw[2 + k];
+      if (nbr(G, q, i, j, -k, 0, interior, pn)) at += wx * Z1[pn];
+      if (nbr(G, q, i, j, k, 0, interior, pn)) at += wx * Z1[pn];
+      if (nbr(G, q, i, j, 0, -k, interior, pn)) at += wy * Z1[pn];
+      if (nbr(G, q, i, j, 0, k, interior, pn)) at += wy * Z1[pn];
     }
   } else if (G.stencil == kPointCross) {
     const int64_t E = G.ext;
     int64_t pn;
-    if (nb_index(G, i, j, pn)) at += Wt[G.wbase + (pn - G.base)] * Z1[pn];
+    if (nbr(G, q, i, j, 0, 0, interior, pn)) at += Wt[G.wbase + (pn - G.base)] * Z1[pn];
     int pl = 1;
 #pragma unroll
     for (int k = -R; k <= R; ++k) {  // axis-0 offset k of row p = q - k
       if (k == 0) continue;
-      if (nb_index(G, i - k, j, pn)) at += Wt[G.wbase + (pn - G.base) + pl * E] * Z1[pn];
+      if (nbr(G, q, i, j, -k, 0, interior, pn))
+        at += Wt[G.wbase + (pn - G.base) + pl * E] * Z1[pn];
       ++pl;
     }
 #pragma unroll
     for (int k = -R; k <= R; ++k) {
       if (k == 0) continue;
-      if (nb_index(G, i, j - k, pn)) at += Wt[G.wbase + (pn - G.base) + pl * E] * Z1[pn];
+      if (nbr(G, q, i, j, 0, -k, interior, pn))
+        at += Wt[G.wbase + (pn - G.base) + pl * E] * Z1[pn];
       ++pl;
     }
   } else {
@@ -621,83 +649,68 @@ __global__ void adj_step_kernel(const DevGrid *__restrict__ grids, int ngrids,
 #pragma unroll
       for (int a = -R; a <= R; ++a) {
         int64_t pn;
-        if (nb_index(G, i - a, j - b, pn))
+        if (nbr(G, q, i, j, -a, -b, interior, pn))
           at += Wt[G.wbase + (pn - G.base) + ((b + R) * (2 * R + 1) + (a + R)) * E] * Z1[pn];
       }
   }
   const bool active = mk == 1 || mk == 2 || mk == 3;
-  Y[q] = (active ? wn * lam[q] : 0.0) + sc * at - Z2[q];
+  const double y = fma(sc, at, active ? fma(wn, lam[q], -Z2[q]) : -Z2[q]);
+  Y[q] = y;
+  Znew[q] = mk == 1 ? y : 0.0;
   if (Xn && mk == 1) {
-    // (A Xn)[q] - 2 Xn[q]: the dt^2 c^2 L_h part of row q, divided by c^2 below
-    double ax;
-    if (G.stencil == kConstCross) {
-      ax = (G.cw[0] - 2.0) * Xn[q];
-      for (int k = 1; k <= R; ++k) {
-        ax += G.cw[k] * (Xn[row_off(G, j) + wrap(i - k, G.n0, G.per0)] +
-                         Xn[row_off(G, j) + wrap(i + k, G.n0, G.per0)]);
-        ax += G.cw[2 + k] * (Xn[row_off(G, j - k) + i] + Xn[row_off(G, j + k) + i]);
-      }
-    } else if (G.stencil == kPointCross) {
-      const int64_t w0 = G.wbase + (q - G.base), E = G.ext;
-      ax = (Wt[w0] - 2.0) * Xn[q];
-      int pl = 1;
-      for (int k = -R; k <= R; ++k) {
-        if (k == 0) continue;
-        ax += Wt[w0 + pl * E] * Xn[row_off(G, j) + wrap(i + k, G.n0, G.per0)];
-        ++pl;
-      }
-      for (int k = -R; k <= R; ++k) {
-        if (k == 0) continue;
-        ax += Wt[w0 + pl * E] * Xn[row_off(G, j + k) + i];
-        ++pl;
-      }
-    } else {
-      const int64_t w0 = G.wbase + (q - G.base), E = G.ext;
-      ax = -2.0 * Xn[q];
-      for (int b = -R; b <= R; ++b)
-        for (int a = -R; a <= R; ++a)
-          ax += Wt[w0 + ((b + R) * (2 * R + 1) + (a + R)) * E] *
-                Xn[row_off(G, j + b) + wrap(i + a, G.n0, G.per0)];
-    }
+    // (A X^n)[q] - 2 X^n[q] from the forward step itself, which at a discretization point
+    // is X^{n+1} = A X^n - X^{n-1} - fc F (n > 0) or X^1 = A X^0 / 2 - fc F (n = 0)
+    const double xn = Xn[q], fx = fma(fc, F[q], Xnext[q]);
+    const double ax = Xprev ? fx + Xprev[q] - 2.0 * xn : 2.0 * (fx - xn);
     const double z = Z1[q];
-    gc2[q] += sc * z * ax / c2[q];
+    gc2[q] = fma(sc * z, ax, gc2[q]);  // divided by c^2 once, after the sweep
     gf[q] -= fc * z;
   }
 }
 
-// Z = D C^T Y: discretization points gather Y from the constrained positions (ghosts,
-// receivers) that read them, with the constraint coefficients; everything else is 0.
-__global__ void adj_ct_kernel(const int8_t *__restrict__ mask, const double *__restrict__ Y,
-                              const int64_t *__restrict__ roff, const int64_t *__restrict__ rpos,
-                              const double *__restrict__ rcoef, double *Z, int64_t total) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= total) return;
-  if (mask[q] != 1) {
-    Z[q] = 0.0;
+// After adj_step_kernel, two independent jobs split by block (no launch of its own each):
+//  * blocks [0, fix_blocks): the constraint part of Z = D C^T Y.  Each listed discretization
+//    point adds the Y values of the constrained positions (ghosts, receivers) that read it,
+//    times the constraint coefficients; 8 lanes share a point's entries (a background donor
+//    point sits in the donor blocks of dozens of receivers) and combine them with xor
+//    shuffles.  Constrained positions are never discretization points, so Y there is final.
+//  * the remaining blocks (gradient mode): the gradient terms of the Dirichlet order-4
+//    compatibility rule at this level.  With t = Y[G1] + 5 Y[G2]: gf[b] += fcos inv t and
+//    c^2_b gc2[b] -= F_b fcos inv t (times c^2, like adj_step_kernel).
+constexpr int kFixLanes = 8;
+__global__ void adj_post_kernel(const int64_t *__restrict__ fq, const int64_t *__restrict__ foff,
+                                const int64_t *__restrict__ rpos,
+                                const double *__restrict__ rcoef, const double *__restrict__ Y,
+                                double *__restrict__ Z, int64_t nfix, int fix_blocks,
+                                const BcItem *__restrict__ bc, int nbc,
+                                const double *__restrict__ F, double fcos, double *gc2,
+                                double *gf) {
+  if ((int)blockIdx.x < fix_blocks) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = t / kFixLanes;
+    const int lane = (int)(t % kFixLanes);
+    const bool live = k < nfix;
+    double z = 0.0;
+    if (live)
+      for (int64_t e = foff[k] + lane; e < foff[k + 1]; e += kFixLanes)
+        z = fma(rcoef[e], Y[rpos[e]], z);
+#pragma unroll
+    for (int off = kFixLanes / 2; off > 0; off >>= 1)
+      z += __shfl_xor_sync(0xffffffffu, z, off, kFixLanes);
+    if (live && lane == 0) Z[fq[k]] += z;
     return;
   }
-  double z = Y[q];
-  for (int64_t e = roff[q]; e < roff[q + 1]; ++e) z = fma(rcoef[e], Y[rpos[e]], z);
-  Z[q] = z;
-}
-
-// Gradient terms of the Dirichlet order-4 compatibility rule at one level: with
-// t = Y[G1] + 5 Y[G2], gf[b] += fcos inv t and gc2[b] -= F_b fcos inv t / c^2_b.
-__global__ void adj_bc_grad_kernel(const BcItem *__restrict__ bc, int nbc,
-                                   const double *__restrict__ Y, const double *__restrict__ F,
-                                   const double *__restrict__ c2, double fcos, double *gc2,
-                                   double *gf) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = ((int)blockIdx.x - fix_blocks) * blockDim.x + threadIdx.x;
   if (k >= nbc) return;
   const BcItem it = bc[k];
   if (it.type != 2) return;
   const double t = Y[it.g[0]] + 5.0 * Y[it.g[1]];
   const int64_t b = it.u[0];
   gf[b] += fcos * it.inv * t;
-  gc2[b] -= F[b] * fcos * it.inv * t / c2[b];
+  gc2[b] -= F[b] * fcos * it.inv * t;
 }
 
-// compact <-> extended copies at active points
+// compact <-> extended copies at active points (ext -> compact optionally divides by div)
 __global__ void compact_to_ext_kernel(const DevGrid *__restrict__ grids, int ngrids,
                                       const int8_t *__restrict__ mask, const double *__restrict__ v,
                                       double *x, int64_t total) {
@@ -713,7 +726,8 @@ __global__ void compact_to_ext_kernel(const DevGrid *__restrict__ grids, int ngr
 
 __global__ void ext_to_compact_kernel(const DevGrid *__restrict__ grids, int ngrids,
                                       const int8_t *__restrict__ mask, const double *__restrict__ x,
-                                      double *v, int64_t ncompact, int disc_only) {
+                                      double *v, int64_t ncompact, int disc_only,
+                                      const double *__restrict__ div) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncompact) return;
   int g = 0;
@@ -723,7 +737,8 @@ __global__ void ext_to_compact_kernel(const DevGrid *__restrict__ grids, int ngr
   const int j = (int)(o / G.n0), i = (int)(o % G.n0);
   const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
   const int8_t m = mask[p];
-  v[c] = (disc_only ? m == 1 : m != 0) ? x[p] : 0.0;
+  const bool on = disc_only ? m == 1 : m != 0;
+  v[c] = on ? (div ? x[p] / div[p] : x[p]) : 0.0;
 }
 
 // ---------------------------------------------------------------------------------
@@ -982,12 +997,13 @@ __global__ void gemv_acc(const double *__restrict__ X, int64_t ldx, int nv,
 void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
                   void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
-                  int n, double fs) {
+                  int n, double fs, const void *Wprev) {
   const dim3 tb(kTileX, kTileY);
+  if (!Wprev) Wprev = Wout;
 #define WH_MARCH(T, O, FI)                                                                 \
   march_kernel<T, O, FI><<<nblocks, tb, 0, s>>>(grids, tiles, ntiles, mask, (const T *)Wn, \
-                                                (T *)Wout, (const T *)F, (const T *)Wt, V,  \
-                                                inst, n, fs)
+                                                (const T *)Wprev, (T *)Wout, (const T *)F, \
+                                                (const T *)Wt, V, inst, n, fs)
   if (fp32) {
     if (order == 4) { if (first) WH_MARCH(float, 4, true); else WH_MARCH(float, 4, false); }
     else            { if (first) WH_MARCH(float, 2, true); else WH_MARCH(float, 2, false); }
@@ -1096,27 +1112,28 @@ void launch_bc_coef(int nbc, cudaStream_t s, BcItem *bc, const int32_t *ig, cons
 
 void launch_adj_step(int order, cudaStream_t s, const DevGrid *grids, int ngrids,
                      const int8_t *mask, const double *Wt, const double *lam, double wn,
-                     double sc, const double *Z1, const double *Z2, double *Y, int64_t total,
-                     const double *Xn, const double *c2, double fc, double *gc2, double *gf) {
+                     double sc, const double *Z1, const double *Z2, double *Y, double *Znew,
+                     int64_t total, const double *Xprev, const double *Xn, const double *Xnext,
+                     const double *F, double fc, double *gc2, double *gf) {
   const unsigned nb = (unsigned)((total + 255) / 256);
   if (order == 4)
-    adj_step_kernel<4><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, total,
-                                          Xn, c2, fc, gc2, gf);
+    adj_step_kernel<4><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, Znew,
+                                          total, Xprev, Xn, Xnext, F, fc, gc2, gf);
   else
-    adj_step_kernel<2><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, total,
-                                          Xn, c2, fc, gc2, gf);
+    adj_step_kernel<2><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, Znew,
+                                          total, Xprev, Xn, Xnext, F, fc, gc2, gf);
 }
 
-void launch_adj_ct(cudaStream_t s, const int8_t *mask, const double *Y, const int64_t *roff,
-                   const int64_t *rpos, const double *rcoef, double *Z, int64_t total) {
-  adj_ct_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(mask, Y, roff, rpos, rcoef, Z,
-                                                                total);
-}
-
-void launch_adj_bc_grad(cudaStream_t s, const BcItem *bc, int nbc, const double *Y,
-                        const double *F, const double *c2, double fcos, double *gc2,
-                        double *gf) {
-  if (nbc) adj_bc_grad_kernel<<<(nbc + 255) / 256, 256, 0, s>>>(bc, nbc, Y, F, c2, fcos, gc2, gf);
+void launch_adj_post(cudaStream_t s, const int64_t *fq, const int64_t *foff, const int64_t *rpos,
+                     const double *rcoef, const double *Y, double *Z, int64_t nfix,
+                     const BcItem *bc, int nbc, const double *F, double fcos, double *gc2,
+                     double *gf) {
+  const int fix_blocks = (int)((nfix * kFixLanes + 255) / 256);
+  const int bc_blocks = gc2 ? (nbc + 255) / 256 : 0;
+  if (fix_blocks + bc_blocks)
+    adj_post_kernel<<<fix_blocks + bc_blocks, 256, 0, s>>>(fq, foff, rpos, rcoef, Y, Z, nfix,
+                                                            fix_blocks, bc, gc2 ? nbc : 0, F, fcos,
+                                                            gc2, gf);
 }
 
 void launch_compact_to_ext(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
@@ -1126,9 +1143,10 @@ void launch_compact_to_ext(cudaStream_t s, const DevGrid *grids, int ngrids, con
 }
 
 void launch_ext_to_compact(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
-                           const double *x, double *v, int64_t ncompact, int disc_only) {
+                           const double *x, double *v, int64_t ncompact, int disc_only,
+                           const double *div) {
   ext_to_compact_kernel<<<(unsigned)((ncompact + 255) / 256), 256, 0, s>>>(
-      grids, ngrids, mask, x, v, ncompact, disc_only);
+      grids, ngrids, mask, x, v, ncompact, disc_only, div);
 }
 
 void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int nv,

@@ -35,7 +35,7 @@ class WHError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("order", C.c_int32), ("periods", C.c_int32), ("cfl", C.c_double),
                 ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("launch_mode", C.c_int32),
-                ("barrier_spin_limit", C.c_uint64)]
+                ("barrier_spin_limit", C.c_uint64), ("trajectory_bytes", C.c_uint64)]
 
 
 class GridDesc(C.Structure):
@@ -135,7 +135,7 @@ class Solver:
     """One overset Helmholtz problem in libwaveholtz (one context)."""
 
     def __init__(self, problem, periods=1, cfl=0.9, alpha_mode=0, precision=FP64, stream=None,
-                 launch_mode=GRAPH, barrier_spin_limit=0):
+                 launch_mode=GRAPH, barrier_spin_limit=0, trajectory_bytes=0):
         self.L = lib()
         self.problem = problem
         opt = Options()
@@ -143,6 +143,7 @@ class Solver:
         opt.order, opt.periods, opt.cfl = problem.order, periods, cfl
         opt.alpha_mode, opt.precision = alpha_mode, precision
         opt.launch_mode, opt.barrier_spin_limit = launch_mode, barrier_spin_limit
+        opt.trajectory_bytes = trajectory_bytes
         h = C.c_void_p()
         self._check(self.L.wh_create(C.byref(opt), C.byref(h)), None)
         self.h = h
@@ -282,7 +283,9 @@ class Solver:
 
     def adjoint(self, u, g, tol=1e-10, max_it=1000, restart=200):
         """Adjoint solve and gradients for dJ/du = g at solution u (device tensors):
-        returns (lam, grad_c2, grad_f, stats)."""
+        returns (lam, grad_c2, grad_f, stats).  Like solve(), an adjoint GMRES that stops
+        above tol returns with stats.converged == 0 (the gradients are then those of the
+        last lam) instead of raising."""
         torch = self._torch
         lam = torch.zeros_like(u)
         gc2 = torch.zeros_like(u)
@@ -292,7 +295,9 @@ class Solver:
         status = self.L.wh_adjoint(self.h, _ptr(u), _ptr(g), tol, max_it, restart, _ptr(lam),
                                    _ptr(gc2), _ptr(gf), C.byref(st))
         self._leave()
-        self._check(status)
+        if status not in (WH_OK, -6):
+            self._check(status)
+        st.status = STATUS.get(status, status)
         return lam, gc2, gf, st
 
     def set_coefficient(self, gid, c2):
@@ -323,3 +328,83 @@ class Solver:
 
     def last_launch_count(self):
         return int(self.L.wh_last_launch_count(self.h))
+
+
+_autograd_fn = None
+
+
+def _waveholtz_fn():
+    """torch.autograd.Function for u = WaveHoltz fixed point of (c^2, f) (built on first use)."""
+    global _autograd_fn
+    if _autograd_fn is not None:
+        return _autograd_fn
+    import torch
+
+    class WaveHoltzFixedPoint(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, c2, f, owner):
+            owner._load(c2, f)
+            u = torch.zeros(owner.problem.n_total, dtype=torch.float64, device=c2.device)
+            st = owner.solver.solve(u, GMRES, owner.tol, owner.max_it, owner.restart)
+            if not st.converged:
+                raise WHError(-6, f"forward solve stopped at residual {st.residual:.3e}")
+            owner.forward_stats = st
+            fctx.owner = owner
+            fctx.save_for_backward(c2, f, u)
+            return u
+
+        @staticmethod
+        def backward(fctx, gu):
+            owner = fctx.owner
+            c2, f, u = fctx.saved_tensors
+            owner._load(c2, f)
+            g = gu.detach().to(torch.float64).contiguous()
+            _, gc2, gf, st = owner.solver.adjoint(u, g, owner.adj_tol, owner.max_it,
+                                                  owner.restart)
+            if not st.converged:
+                raise WHError(-6, f"adjoint solve stopped at residual {st.residual:.3e}")
+            owner.adjoint_stats = st
+            return (gc2 if fctx.needs_input_grad[0] else None,
+                    gf if fctx.needs_input_grad[1] else None, None)
+
+    _autograd_fn = WaveHoltzFixedPoint
+    return _autograd_fn
+
+
+class DifferentiableSolve:
+    """u(c^2, f): the converged WaveHoltz solution as a differentiable torch function.
+
+    ``c2`` and ``f`` are compact float64 device tensors (n_total, every grid point, the
+    values at non-discretization points are ignored).  The forward pass loads them into one
+    library context, prepares the time setup and runs GMRES on (I - S) v = b; the backward
+    pass runs the adjoint GMRES on (I - S^T) lam = dJ/du and the checkpointed reverse sweep
+    (``wh_adjoint``), which returns dJ/dc^2 and dJ/df of the discrete map.  The fixed point
+    is the discrete Helmholtz solution at omega whatever the time step (the explicit
+    omega-tilde recipe makes 4/dt^2 sin^2(omega-tilde dt/2) = omega^2), so the gradient is
+    that of the discrete Helmholtz solution, although dt itself moves with max c^2."""
+
+    def __init__(self, problem, tol=1e-12, adj_tol=None, max_it=1000, restart=200, **solver_kw):
+        self.problem = problem
+        self.solver = Solver(problem, **solver_kw)
+        self.tol, self.max_it, self.restart = tol, max_it, restart
+        self.adj_tol = tol if adj_tol is None else adj_tol
+        self._loaded = None
+        self.forward_stats = self.adjoint_stats = None
+
+    def _load(self, c2, f):
+        key = (c2.data_ptr(), c2._version, f.data_ptr(), f._version)
+        if key == self._loaded:
+            return
+        c2h = c2.detach().to("cpu", self.solver._torch.float64).numpy()
+        fh = f.detach().to("cpu", self.solver._torch.float64).numpy()
+        for gi, (cg, fg) in enumerate(zip(self.problem.split(c2h), self.problem.split(fh))):
+            self.solver.set_coefficient(gi, cg)
+            self.solver.set_forcing(gi, fg)
+        self.solver.prepare()
+        self._loaded = key
+
+    def __call__(self, c2, f):
+        return _waveholtz_fn().apply(c2, f, self)
+
+    def close(self):
+        self.solver.close()

@@ -152,3 +152,46 @@ def test_gradient_vs_finite_differences_and_direct_adjoint(torch, W, misfit_prob
             pred = float(gf @ dirn)
         fd = (jp - jm) / (2 * eps)
         assert abs(fd - pred) <= 1e-6 * max(abs(fd), abs(pred)) + 1e-14, (kind, fd, pred)
+
+
+def test_autograd_function(torch, W, misfit_problem):
+    """torch.autograd through DifferentiableSolve equals the explicit adjoint call and the
+    direct-system adjoint."""
+    import dhs
+    prob, P, d = misfit_problem
+    ds = W.DifferentiableSolve(prob, tol=1e-13, max_it=800, restart=400)
+    c2 = torch.from_numpy(np.concatenate([c.ravel() for c in prob.c2])).cuda().requires_grad_()
+    f = torch.from_numpy(np.concatenate([x.ravel() for x in prob.f])).cuda().requires_grad_()
+    Pt = torch.from_numpy(P.toarray()).cuda()
+    dt = torch.from_numpy(d).cuda()
+    u = ds(c2, f)
+    J = 0.5 * ((Pt @ u - dt) ** 2).sum()
+    J.backward()
+    U, J0, gc2_d, gf_d = dhs.adjoint_gradients(prob, P, d)
+    assert abs(J.item() - J0) <= 1e-9 * J0
+    g1 = c2.grad.cpu().numpy()
+    g2 = f.grad.cpu().numpy()
+    assert np.linalg.norm(g1 - gc2_d) <= 1e-6 * np.linalg.norm(gc2_d)
+    assert np.linalg.norm(g2 - gf_d) <= 1e-6 * np.linalg.norm(gf_d)
+    assert ds.forward_stats.converged == 1 and ds.adjoint_stats.converged == 1
+    ds.close()
+
+
+@pytest.mark.parametrize("name,make", [CASES[1], CASES[2], CASES[6]], ids=[CASES[1][0], CASES[2][0], CASES[6][0]])
+def test_checkpointed_sweep_matches_whole_trajectory(torch, W, name, make):
+    """Forward states recomputed from checkpoints (trajectory_bytes=1) give the gradients of
+    the whole stored trajectory."""
+    prob = make()
+    out = []
+    for tb in (0, 1):
+        s = W.Solver(prob, trajectory_bytes=tb)
+        ti = s.prepare()
+        rng = np.random.default_rng(3)
+        act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
+        u = torch.from_numpy(rng.standard_normal(prob.n_total) * act).cuda()
+        g = torch.from_numpy(rng.standard_normal(prob.n_total) * act).cuda()
+        lam, gc2, gf, st = s.adjoint(u, g, 1e-10, 40, 40)
+        out.append((lam.cpu().numpy(), gc2.cpu().numpy(), gf.cpu().numpy()))
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a)), name
