@@ -172,9 +172,10 @@ def time_iterations(WH, torch, solver, n_total, stream, flush, reps, warm=2):
 
 
 def measure_forms(WH, G, torch, prob, stream, flush, rank):
-    """The FP32-march form on the same workload, the 256-instance batch (batched FP32 and
-    FP64 iterations vs plain per-instance FP64 iterations on a sample of instances), and
-    time to 1e-6 relative error on the 64^2 unit square."""
+    """The FP32-march form on the same workload, the differentiation form (S^T and one
+    gradient sweep), the 256-instance batch (batched FP32 and FP64 iterations vs plain
+    per-instance FP64 iterations on a sample of instances), and time to 1e-6 relative error
+    on the 64^2 unit square."""
     out = {}
     s32 = WH.Solver(prob, stream=stream, precision=WH.FP32)
     ti = s32.prepare()
@@ -183,6 +184,43 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
                          "ms_per_iteration": t32 * 1e3,
                          "workload": "same disk-in-square workload, FP32 march, FP64 filter"}
     s32.close()
+    # differentiation form: the transposed map S^T (the product of the adjoint GMRES) and
+    # one gradient sweep (forward march from u kept whole in HBM, reverse sweep with the
+    # c^2 and f gradients); g = 0 makes the adjoint GMRES return at once, so the call times
+    # the sweep alone
+    sa = WH.Solver(prob, stream=stream)
+    ta = sa.prepare()
+    n = prob.n_total
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    zero = torch.zeros_like(x)
+
+    def timed(fn, reps, warm=2):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                fn()
+            tot = 0.0
+            for k in range(reps):
+                flush.fill_(float(k))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                stream.synchronize()
+                tot += e0.elapsed_time(e1) / 1e3
+        return tot / reps
+
+    tf = time_iterations(WH, torch, sa, n, stream, flush, 5)
+    tt = timed(lambda: sa.apply_adjoint(x, y), 5)
+    tg = timed(lambda: sa.adjoint(x, zero, 1e-8, 10, 10), 3)
+    out["adjoint"] = {"transpose_apply": {"value": ta.n_active * ta.M / tt / 1e9,
+                                          "unit": "GLUP/s", "ms": tt * 1e3,
+                                          "vs_forward_iteration": tt / tf},
+                      "gradient_sweep": {"ms": tg * 1e3, "vs_forward_iteration": tg / tf},
+                      "workload": "same disk-in-square workload, FP64"}
+    sa.close()
+    del x, y, zero
     # batch: 256 disk-in-square instances, N ~ U{256..1024}, annulus 2N x N/16,
     # omega ~ U[10, 50], 1-4 sources
     t0 = time.perf_counter()

@@ -120,6 +120,9 @@ struct wh_ctx {
   int *h_err = nullptr;       // pinned copy of the barrier error flag
   int64_t *d_patch_off = nullptr;
   int32_t *d_patch_pos = nullptr, *d_patch_item = nullptr, *d_recv_of = nullptr;
+  int64_t *d_dep_off = nullptr;  // dataflow dependencies of each tile (CSR)
+  int32_t *d_dep_tile = nullptr;
+  int32_t *d_tile_done = nullptr;  // steps completed by each tile in the current launch
   bool persistent = true;
   unsigned long long opt_spin_limit = 1ull << 22;
   cudaEvent_t err_ev = nullptr;
@@ -494,6 +497,62 @@ wh_status build_layout(wh_ctx *ctx) {
   if (ctx->hbc.size() >= (1u << 24) || ctx->nrecv >= (1 << 24))
     return fail(ctx, WH_ERR_ARG, "too many ghost items or receivers for the patch encoding");
 
+  // persistent-kernel dataflow dependencies: tile t at step n reads level-n values owned by
+  // the tiles in deps(t) -- its staged box (halo included), the sources of the ghost rules
+  // and the donors of the receivers it patches, and itself (W^{n-1} at its own points).  The
+  // lists are closed under reversal: t also waits for every tile that reads t's points, so
+  // W^{n+1} never overwrites a W^{n-1} value that a reader still needs.
+  std::vector<int64_t> dep_off(ctx->htiles.size() + 1, 0);
+  std::vector<int32_t> dep_tile;
+  {
+    const int ntl = (int)ctx->htiles.size();
+    std::vector<int32_t> owner(off, -1);
+    for (int t = 0; t < ntl; ++t) {
+      const Tile &T = ctx->htiles[t];
+      const DevGrid &G = ctx->hgrids[T.grid];
+      for (int j = T.j0; j < std::min(T.j0 + kTileY * kPY, G.n1); ++j)
+        for (int i = T.i0; i < std::min(T.i0 + kTileX, G.n0); ++i) owner[ext_index(G, i, j)] = t;
+    }
+    std::vector<std::vector<int32_t>> dep(ntl);
+    const int SX = kTileX + 2 * R, SY = kTileY * kPY + 2 * R;
+    for (int t = 0; t < ntl; ++t) {
+      const Tile &T = ctx->htiles[t];
+      const DevGrid &G = ctx->hgrids[T.grid];
+      std::vector<int32_t> &d = dep[t];
+      auto add = [&](int64_t p) {
+        if (p >= 0 && p < off && owner[p] >= 0) d.push_back(owner[p]);
+      };
+      d.push_back(t);
+      for (int rr = 0; rr < SY; ++rr)
+        for (int cc = 0; cc < SX; ++cc) {
+          int i = T.i0 - R + cc, j = T.j0 - R + rr;
+          if (G.per0) i = ((i % G.n0) + G.n0) % G.n0;
+          else if (i < -G.g0 || i >= G.n0 + G.g0) continue;
+          if (G.per1) j = ((j % G.n1) + G.n1) % G.n1;
+          else if (j < -G.g1 || j >= G.n1 + G.g1) continue;
+          add(ext_index(G, i, j));
+        }
+      for (int64_t e = patch_off[t]; e < patch_off[t + 1]; ++e) {
+        const int kind = patch_pos[e] >> 24, item = patch_item[e];
+        if (kind == 2)
+          for (int k = 0; k < ND; ++k) add(didx[(int64_t)item * ND + k]);
+        else
+          for (int k = 0; k < 4; ++k) add(ctx->hbc[item].u[k]);
+      }
+    }
+    std::vector<std::vector<int32_t>> rev(ntl);
+    for (int t = 0; t < ntl; ++t)
+      for (int32_t x : dep[t]) rev[x].push_back(t);
+    for (int t = 0; t < ntl; ++t) {
+      std::vector<int32_t> &d = dep[t];
+      d.insert(d.end(), rev[t].begin(), rev[t].end());
+      std::sort(d.begin(), d.end());
+      d.erase(std::unique(d.begin(), d.end()), d.end());
+      dep_tile.insert(dep_tile.end(), d.begin(), d.end());
+      dep_off[t + 1] = (int64_t)dep_tile.size();
+    }
+  }
+
   // device allocations
   wh_status st;
   for (int k = 0; k < 2; ++k) {
@@ -526,7 +585,10 @@ wh_status build_layout(wh_ctx *ctx) {
       (st = dalloc(ctx, &ctx->d_patch_off, patch_off.size())) ||
       (st = dalloc(ctx, &ctx->d_patch_pos, std::max<size_t>(patch_pos.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_patch_item, std::max<size_t>(patch_item.size(), 1))) ||
-      (st = dalloc(ctx, &ctx->d_recv_of, recv_of.size())))
+      (st = dalloc(ctx, &ctx->d_recv_of, recv_of.size())) ||
+      (st = dalloc(ctx, &ctx->d_dep_off, dep_off.size())) ||
+      (st = dalloc(ctx, &ctx->d_dep_tile, std::max<size_t>(dep_tile.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_tile_done, std::max<size_t>(ctx->htiles.size(), 1))))
     return st;
   CK(cudaMemcpy(ctx->d_patch_off, patch_off.data(), patch_off.size() * 8, cudaMemcpyHostToDevice));
   if (!patch_pos.empty()) {
@@ -535,6 +597,9 @@ wh_status build_layout(wh_ctx *ctx) {
                   cudaMemcpyHostToDevice));
   }
   CK(cudaMemcpy(ctx->d_recv_of, recv_of.data(), recv_of.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_dep_off, dep_off.data(), dep_off.size() * 8, cudaMemcpyHostToDevice));
+  if (!dep_tile.empty())
+    CK(cudaMemcpy(ctx->d_dep_tile, dep_tile.data(), dep_tile.size() * 4, cudaMemcpyHostToDevice));
   {
     std::vector<int32_t> rinst(ridx.size(), 0);
     for (int64_t r = 0; r < ctx->nrecv; ++r) rinst[r] = ctx->hgrids[ctx->rg[r]].inst;
@@ -674,6 +739,9 @@ wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double
   A.patch_pos = ctx->d_patch_pos;
   A.patch_item = ctx->d_patch_item;
   A.recv_of = ctx->d_recv_of;
+  A.dep_off = ctx->d_dep_off;
+  A.dep_tile = ctx->d_dep_tile;
+  A.tile_done = ctx->d_tile_done;
   CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBarrier), ctx->stream));
   CK(launch_iteration(is_fp32(ctx), ctx->opt.order, ctx->iter_blocks, ctx->stream, A, vin, vout,
                       ctx->d_bar));

@@ -72,7 +72,7 @@ struct GridBarrier {
   unsigned count[32];
   unsigned gen[32];
   int err[32];
-  int tile_ctr[2][32];  // dynamic tile tickets of the march phase, one slot per step parity
+  unsigned long long ticket[16];  // dataflow tickets: ticket k is step k / ntiles, tile k % ntiles
 };
 
 // Everything the persistent iteration kernel reads (device pointers, per-step tables).
@@ -105,6 +105,11 @@ struct IterArgs {
   const int32_t *patch_pos;
   const int32_t *patch_item;
   const int32_t *recv_of;  // receiver index at each extended point, -1 elsewhere
+  // dataflow: tile t at step n waits until tile_done[d] >= n for d in
+  // dep_tile[dep_off[t] .. dep_off[t+1]), and sets tile_done[t] = n + 1 when done
+  const int64_t *dep_off;
+  const int32_t *dep_tile;
+  int32_t *tile_done;
 };
 
 // Host launchers (wh_kernels.cu).  T is double unless fp32 is set; pointers typed void
