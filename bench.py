@@ -316,6 +316,25 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(case):
+    """A fixed small workload for ncu captures (no timing, no JSON line)."""
+    import torch
+    from paper_2504_03074_gb300 import build as B
+    B.build()
+    from paper_2504_03074_gb300 import grids as G, waveholtz as WH
+    bp, _ = G.batch_disk_problem(16, seed=100)
+    s = WH.Solver(bp, precision=WH.FP32 if case.startswith("fp32") else WH.FP64)
+    s.prepare()
+    a = torch.zeros(bp.n_total, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(3):
+        s.iterate(a, b, True)
+        a, b = b, a
+    torch.cuda.synchronize()
+    print(f"profile case {case}: {bp.n_total} points, 3 iterations")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,9 +345,15 @@ def main():
     ap.add_argument("--small", action="store_true", help="small workload (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32 / batched / solve-time measurements")
+    ap.add_argument("--profile-case", choices=["fp32_batch16", "fp64_batch16"],
+                    help="profiling aid: run 3 iterations of a 16-instance disk-in-square "
+                         "batch (8.4 M points, HBM resident) in one precision and exit "
+                         "without a bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
 
     import numpy as np
     import torch

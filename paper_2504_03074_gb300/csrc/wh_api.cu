@@ -39,6 +39,10 @@ struct MarchSet {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   bool fp32 = false, present = false;
   int march_blocks = 0, iter_blocks = 0;
+  // TMA-staged march: tensor maps of the fast grids over this set's arrays
+  CUtensorMap *maps = nullptr;
+  bool tma = false;
+  int tma_blocks = 0;
 };
 
 }  // namespace
@@ -62,6 +66,12 @@ struct wh_ctx {
   int64_t nplanes5 = 0, nweights = 0;
   std::vector<DevGrid> hgrids;
   std::vector<Tile> htiles;
+  // march tiles split for the TMA-staged march: fast (non-periodic constant-weight grids,
+  // pad_ = the grid's map slot) and general
+  std::vector<Tile> hftiles, hgtiles;
+  std::vector<int32_t> fast_grids;  // grid of each map slot
+  Tile *d_ftiles = nullptr, *d_gtiles = nullptr;
+  int *d_err = nullptr;  // TMA march control: [0] sticky error flag, [1] ticket, [2] blocks done
   std::vector<BcItem> hbc;
   std::vector<int32_t> hbc_grid, hbc_axis, hbc_hi;
   std::vector<void *> allocs;
@@ -89,6 +99,7 @@ struct wh_ctx {
   std::vector<int8_t> iactive;
   InstDev *d_inst = nullptr;
   double *d_tabs = nullptr;
+  float *d_ftabs = nullptr;  // per instance fc[0..M] rounded to FP32
   int64_t tabs_cap = 0;
   int32_t *d_rinst = nullptr;
   int maxM = 0;
@@ -200,6 +211,7 @@ void free_device(wh_ctx *ctx) {
   ctx->d_partial = ctx->d_red = nullptr;
   ctx->red_cap = 0;
   ctx->d_tabs = nullptr;
+  ctx->d_ftabs = nullptr;
   ctx->tabs_cap = 0;
   ctx->adj_ready = false;
   ctx->nfix = 0;
@@ -227,6 +239,60 @@ void use_set(wh_ctx *c, int k) {
   c->iter_blocks = S.iter_blocks;
 }
 int default_set(const wh_ctx *c) { return c->opt.precision == WH_FP32 ? 1 : 0; }
+
+// Tensor maps of the TMA-staged march: per fast grid, over its extended arrays (width pitch,
+// height n1 + 2 g1, rows pitch elements apart), boxes of kBoxX columns starting at extended
+// column i0: W^n with halo (tile rows + 2R) from either state array, W^{n-1} (tile rows)
+// from either, F, V (FP64) and the mask (kMaskBoxX bytes).  Out-of-range parts of a box
+// are zero-filled.
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+wh_status encode_maps(wh_ctx *ctx, MarchSet &S, int order) {
+  static EncodeTiled encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(ctx, WH_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    encode = (EncodeTiled)fn;
+  }
+  const int R = order / 2, TY = kTileY * kPY;
+  const size_t ts = S.fp32 ? 4 : 8;
+  const CUtensorMapDataType dt = S.fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  std::vector<CUtensorMap> maps(ctx->fast_grids.size() * kMapsPerGrid);
+  for (size_t k = 0; k < ctx->fast_grids.size(); ++k) {
+    const DevGrid &G = ctx->hgrids[ctx->fast_grids[k]];
+    const cuuint64_t dims[2] = {(cuuint64_t)G.pitch, (cuuint64_t)(G.n1 + 2 * G.g1)};
+    const cuuint32_t estr[2] = {1, 1};
+    auto enc = [&](int which, CUtensorMapDataType type, size_t es, void *base, int bx, int by) {
+      const cuuint64_t strides[1] = {(cuuint64_t)G.pitch * es};
+      const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+      void *addr = (char *)base + (size_t)G.base * es;
+      return encode(&maps[k * kMapsPerGrid + which], type, 2, addr, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
+    CUresult r = CUDA_SUCCESS;
+    if (!r) r = enc(kMapWaHalo, dt, ts, S.Wa, kBoxX, TY + 2 * R);
+    if (!r) r = enc(kMapWbHalo, dt, ts, S.Wb, kBoxX, TY + 2 * R);
+    if (!r) r = enc(kMapWaCtr, dt, ts, S.Wa, kBoxX, TY);
+    if (!r) r = enc(kMapWbCtr, dt, ts, S.Wb, kBoxX, TY);
+    if (!r) r = enc(kMapF, dt, ts, S.F, kBoxX, TY);
+    if (!r) r = enc(kMapV, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, ctx->d_V, kBoxX, TY);
+    if (!r) r = enc(kMapMask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, ctx->d_mask, kMaskBoxX, TY);
+    if (r) return fail(ctx, WH_ERR_CUDA, "tensor map of grid %d: error %d", ctx->fast_grids[k], (int)r);
+  }
+  wh_status st;
+  if ((st = dalloc(ctx, &S.maps, std::max<size_t>(maps.size(), 1)))) return st;
+  CK(cudaMemcpy(S.maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+  return WH_OK;
+}
 
 // Build the device layout, upload everything that does not depend on omega.
 wh_status build_layout(wh_ctx *ctx) {
@@ -313,6 +379,31 @@ wh_status build_layout(wh_ctx *ctx) {
       --left;
     }
     ctx->htiles.swap(mixed);
+  }
+  {
+    // TMA-staged march: tiles of non-periodic constant-weight grids whose ghost width is the
+    // stencil radius (every TMA box then starts at a 16-byte aligned extended column)
+    ctx->hftiles.clear();
+    ctx->hgtiles.clear();
+    ctx->fast_grids.clear();
+    std::vector<int32_t> slot(ctx->hgrids.size(), -1);
+    for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
+      const DevGrid &G = ctx->hgrids[g];
+      if (G.stencil == kConstCross && !G.per0 && !G.per1 && G.g0 == R && G.g1 == R &&
+          G.base % 32 == 0 && G.pitch % 32 == 0) {
+        slot[g] = (int32_t)ctx->fast_grids.size();
+        ctx->fast_grids.push_back((int32_t)g);
+      }
+    }
+    for (const Tile &t : ctx->htiles) {
+      if (slot[t.grid] >= 0 && t.i0 % 32 == 0) {
+        Tile f = t;
+        f.pad_ = slot[t.grid];
+        ctx->hftiles.push_back(f);
+      } else {
+        ctx->hgtiles.push_back(t);
+      }
+    }
   }
   ctx->total = off;
   ctx->ncompact = coff;
@@ -569,6 +660,9 @@ wh_status build_layout(wh_ctx *ctx) {
   }
   if ((st = dalloc(ctx, &ctx->d_grids, ctx->hgrids.size())) ||
       (st = dalloc(ctx, &ctx->d_tiles, ctx->htiles.size())) ||
+      (st = dalloc(ctx, &ctx->d_ftiles, std::max<size_t>(ctx->hftiles.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_gtiles, std::max<size_t>(ctx->hgtiles.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_err, 3)) ||
       (st = dalloc(ctx, &ctx->d_mask, off)) ||
       (st = dalloc(ctx, &ctx->d_V, off)) || (st = dalloc(ctx, &ctx->d_c2, off)) ||
       (st = dalloc(ctx, &ctx->d_rx, std::max<int64_t>(k5, 1))) ||
@@ -607,6 +701,12 @@ wh_status build_layout(wh_ctx *ctx) {
   }
   CK(cudaMemcpy(ctx->d_tiles, ctx->htiles.data(), ctx->htiles.size() * sizeof(Tile),
                 cudaMemcpyHostToDevice));
+  if (!ctx->hftiles.empty())
+    CK(cudaMemcpy(ctx->d_ftiles, ctx->hftiles.data(), ctx->hftiles.size() * sizeof(Tile),
+                  cudaMemcpyHostToDevice));
+  if (!ctx->hgtiles.empty())
+    CK(cudaMemcpy(ctx->d_gtiles, ctx->hgtiles.data(), ctx->hgtiles.size() * sizeof(Tile),
+                  cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_mask, mask.data(), off, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_c2, c2.data(), off * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->set[0].F, f.data(), off * sizeof(double), cudaMemcpyHostToDevice));
@@ -635,6 +735,11 @@ wh_status build_layout(wh_ctx *ctx) {
       if (!S.present) continue;
       S.march_blocks = sms * march_blocks_per_sm(S.fp32, order);
       S.iter_blocks = sms * iteration_blocks_per_sm(S.fp32, order);
+      S.tma = S.fp32 && !ctx->hftiles.empty();
+      if (S.tma) {
+        S.tma_blocks = sms * march_tma_blocks_per_sm(S.fp32, order);
+        if ((st = encode_maps(ctx, S, order))) return st;
+      }
     }
     CK(cudaGetLastError());
   }
@@ -642,6 +747,25 @@ wh_status build_layout(wh_ctx *ctx) {
   if ((st = dalloc(ctx, &ctx->d_bar, 1))) return st;
   ctx->dirty = false;
   return WH_OK;
+}
+
+// One march step of the active set: the TMA-staged kernel when the set has tensor maps,
+// else march_kernel.
+void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs) {
+  const MarchSet &S = ctx->set[ctx->active];
+  const int order = ctx->opt.order;
+  if (S.tma) {
+    const int nf = (int)ctx->hftiles.size(), ngn = (int)ctx->hgtiles.size();
+    launch_march_tma(S.fp32, order, n == 0, std::min(S.tma_blocks, nf + ngn), ctx->stream,
+                     ctx->d_grids, ctx->d_ftiles, nf, S.maps, ctx->d_gtiles, ngn, ctx->d_mask,
+                     S.Wa, S.Wb, S.F, S.Wt, ctx->d_V, ctx->d_inst, n, fs, ctx->d_err,
+                     ctx->opt_spin_limit);
+    return;
+  }
+  const int ntiles = (int)ctx->htiles.size();
+  launch_march(S.fp32, order, n == 0, std::min(ntiles, ctx->march_blocks), ntiles, ctx->stream,
+               ctx->d_grids, ctx->d_tiles, ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt,
+               ctx->d_V, ctx->d_inst, n, fs);
 }
 
 wh_status launch_steps(wh_ctx *ctx, int forcing) {
@@ -656,8 +780,6 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
   const int lanes = order == 4 ? 8 : 4;
   const int g_blocks = (int)((ctx->nrecv * lanes + 255) / 256);
   const int bg_blocks = bc_blocks + g_blocks;
-  const int ntiles = (int)ctx->htiles.size();
-  const int nblocks = std::min(ntiles, ctx->march_blocks);
   void *Wa = ctx->d_Wa, *Wb = ctx->d_Wb;
   auto bcg = [&](void *W, int level) {
     if (bg_blocks == 0) return;
@@ -669,8 +791,7 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
   for (int n = 0; n < ctx->maxM; ++n) {
     void *cur = (n & 1) ? Wb : Wa;
     void *oth = (n & 1) ? Wa : Wb;
-    launch_march(f32, order, n == 0, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles, ctx->d_mask,
-                 cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst, n, fs);
+    march_step(ctx, n, cur, oth, fs);
     bcg(oth, n + 1);
   }
   return WH_OK;
@@ -704,7 +825,8 @@ wh_status check_timeout(wh_ctx *ctx, bool wait) {
   }
   ctx->err_pending = false;
   if (*ctx->h_err)
-    return fail(ctx, WH_ERR_TIMEOUT, "a grid barrier of the persistent kernel timed out");
+    return fail(ctx, WH_ERR_TIMEOUT,
+                "a bounded wait timed out (persistent grid barrier or TMA stage of the march)");
   return WH_OK;
 }
 
@@ -756,6 +878,7 @@ wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double
 wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
   forcing = forcing ? 1 : 0;
   if (ctx->persistent) return iterate_persistent(ctx, forcing, vin, vout);
+  if (wh_status st = check_timeout(ctx, false)) return st;
   if (!ctx->set[ctx->active].gexec[forcing]) {
     wh_status st = build_graph(ctx, forcing);
     if (st) return st;
@@ -766,7 +889,15 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   launch_init(is_fp32(ctx), (unsigned)nb, ctx->stream, ctx->d_grids, ng, ctx->d_mask, vin,
               ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst);
   CK(cudaGetLastError());
+  if (ctx->set[ctx->active].tma)  // tickets start at zero (the kernel also leaves them so)
+    CK(cudaMemsetAsync(ctx->d_err + 1, 0, 2 * sizeof(int), ctx->stream));
   CK(cudaGraphLaunch(ctx->set[ctx->active].gexec[forcing], ctx->stream));
+  if (ctx->set[ctx->active].tma) {
+    // the TMA stages' bounded waits leave a sticky flag; reported by a later call
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->err_ev, ctx->stream));
+    ctx->err_pending = true;
+  }
   const int64_t nc = (ctx->ncompact + blk - 1) / blk;
   launch_finish(is_fp32(ctx), (unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V,
                 ctx->d_Wa, ctx->d_Wb, ctx->d_inst, vout, ctx->ncompact);
@@ -1590,9 +1721,12 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   // device tables: per instance fc[0..M], cos[0..M], wf[0..M]
   if (ctx->tabs_cap < tab_len) {
     if ((st = dalloc(ctx, &ctx->d_tabs, (size_t)tab_len))) return st;
+    if ((st = dalloc(ctx, &ctx->d_ftabs, (size_t)tab_len / 3))) return st;
     ctx->tabs_cap = tab_len;
   }
   std::vector<double> tab((size_t)tab_len);
+  std::vector<float> ftab((size_t)tab_len / 3);  // fc rounded to FP32, per instance
+  int64_t fo = 0;
   ctx->hinst.assign(K, InstDev{});
   int64_t o = 0;
   for (int k = 0; k < K; ++k) {
@@ -1610,12 +1744,17 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
     I.cosn = ctx->d_tabs + o + (M + 1);
     I.wf = ctx->d_tabs + o + 2 * (M + 1);
     I.dt2 = ti.dt * ti.dt;
+    for (int n = 0; n <= M; ++n) ftab[fo + n] = (float)tab[o + n];
+    I.fcf = ctx->d_ftabs + fo;
+    I.dt2hf = (float)(0.5 * I.dt2);
+    fo += M + 1;
     I.M = M;
     I.active = 1;
     o += 3 * (int64_t)(M + 1);
   }
   ctx->iactive.assign(K, 1);
   CK(cudaMemcpy(ctx->d_tabs, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_ftabs, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_inst, ctx->hinst.data(), K * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (!ctx->h_err) {
     CK(cudaMallocHost(&ctx->h_err, sizeof(int)));
@@ -1644,6 +1783,7 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
       G.cw[3] = 16.0 / 12.0 * y;
       G.cw[4] = -1.0 / 12.0 * y;
     }
+    for (int k = 0; k < 5; ++k) G.cwf[k] = (float)G.cw[k];
   }
   CK(cudaMemcpyAsync(ctx->d_grids, ctx->hgrids.data(), ctx->hgrids.size() * sizeof(DevGrid),
                      cudaMemcpyHostToDevice, s));
@@ -2112,8 +2252,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
     for (int r = 0; r < reps; ++r) {
       void *cur = (r & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (r & 1) ? ctx->d_Wa : ctx->d_Wb;
       if (kind == 0)
-        launch_march(f32, order, false, nblocks, ntiles, s, ctx->d_grids, ctx->d_tiles,
-                     ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst, 1, 1.0);
+        march_step(ctx, 1 + (r & 1), cur, oth, 1.0);
       else if (kind == 1 && bg_blocks)
         launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx,
                          ctx->d_dw, ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, oth, ctx->d_F,

@@ -1,6 +1,7 @@
 // wh_internal.h -- device-side data structures of libwaveholtz (not part of the ABI).
 #pragma once
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only; maps are encoded through the runtime entry point)
 #include <cuda_runtime.h>
 
 namespace wh {
@@ -38,6 +39,7 @@ struct DevGrid {
   // constant cross weights (kConstCross), dt^2 folded in, centre includes the "2":
   // [centre, axis0 offset 1, axis0 offset 2, axis1 offset 1, axis1 offset 2]
   double cw[5];
+  float cwf[5];  // the same weights rounded to FP32 (the FP32 march reads these)
 };
 
 // One ghost-rule item: the ghost points next to one boundary point (Sec. 3.2 ghost
@@ -59,12 +61,22 @@ struct InstDev {
   double dt2;
   int M;               // steps of one iteration; steps n >= M are skipped
   int active;          // 0: the instance is skipped entirely (converged in a batched solve)
+  const float *fcf;    // fc rounded to FP32 (the FP32 march reads these)
+  float dt2hf;         // dt^2 / 2 rounded to FP32 (first step)
 };
 
-// One tile of the march: a 32 x (8 kPY) block of points of one grid.
+// One tile of the march: a 32 x (8 kPY) block of points of one grid.  For tiles of the
+// TMA-staged march, pad_ is the index of the grid's block of tensor maps.
 struct Tile {
   int32_t grid, i0, j0, pad_;
 };
+
+// TMA-staged march (non-periodic grids with constant cross weights, ghost width = order/2):
+// per grid 7 tensor maps over its extended arrays; every box is kBoxX elements wide starting
+// at extended column i0 (= grid column i0 - order/2, 16-byte aligned since i0 % 32 == 0).
+enum { kMapWaHalo = 0, kMapWbHalo, kMapWaCtr, kMapWbCtr, kMapF, kMapV, kMapMask, kMapsPerGrid };
+constexpr int kBoxX = 36;      // state/forcing/filter box columns (tile 32 + halo 2 x 2)
+constexpr int kMaskBoxX = 48;  // mask box columns (bytes; 16-byte multiple covering 2 + 32)
 
 // Grid-wide barrier state of the persistent kernel (zeroed before every launch); each
 // word on its own 128-byte line.
@@ -119,6 +131,17 @@ void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cud
                   void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
                   int n, double fs, const void *Wprev = nullptr);  // W^{n-1}: Wout if null
 int march_blocks_per_sm(bool fp32, int order);
+// TMA-staged march, one launch per step: each block walks a strided share of the fast tiles
+// (double-buffered TMA boxes on mbarriers, bounded waits), then takes general tiles by
+// ticket (as launch_march).  Same arithmetic, in the same order.  ctl: int[3] in device memory, zero before the first
+// launch (error flag, ticket counter, blocks done; the kernel leaves the last two at zero).
+size_t march_tma_smem(bool fp32, int order);
+int march_tma_blocks_per_sm(bool fp32, int order);
+void launch_march_tma(bool fp32, int order, bool first, int nblocks, cudaStream_t s,
+                      const DevGrid *grids, const Tile *ftiles, int nfast, const CUtensorMap *maps,
+                      const Tile *gtiles, int ngen, const int8_t *mask, void *Wa, void *Wb,
+                      const void *F, const void *Wt, double *V, const InstDev *inst, int n,
+                      double fs, int *ctl, unsigned long long spin_limit);
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
                       const int64_t *ridx, const int32_t *rinst, int nrecv, void *W,

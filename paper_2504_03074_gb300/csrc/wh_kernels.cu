@@ -56,6 +56,32 @@ __device__ __forceinline__ double to_f64(float x) {
   return (double)x;
 }
 
+// Constant cross weight k and forcing factor of step n in the march precision.  The FP32
+// values are rounded once on the host: converting FP64 to FP32 in the kernel is an FP64-pipe
+// instruction on this part, several times the cost of a DFMA, and was most of that pipe's
+// load in the FP32 march.  Same values as converting here.
+template <typename T>
+__device__ __forceinline__ T grid_w(const DevGrid &G, int k);
+template <>
+__device__ __forceinline__ double grid_w<double>(const DevGrid &G, int k) {
+  return G.cw[k];
+}
+template <>
+__device__ __forceinline__ float grid_w<float>(const DevGrid &G, int k) {
+  return G.cwf[k];
+}
+template <typename T>
+__device__ __forceinline__ T step_fc(const InstDev &I, int n, double fs, bool first);
+template <>
+__device__ __forceinline__ double step_fc<double>(const InstDev &I, int n, double fs,
+                                                  bool first) {
+  return first ? 0.5 * fs * I.dt2 : fs * I.fc[n];
+}
+template <>
+__device__ __forceinline__ float step_fc<float>(const InstDev &I, int n, double fs, bool first) {
+  return fs == 0.0 ? 0.0f : (first ? I.dt2hf : I.fcf[n]);  // fs is 0 or 1
+}
+
 // ---------------------------------------------------------------------------------
 // Per-point arithmetic shared by the graph path and the persistent kernel.
 // ---------------------------------------------------------------------------------
@@ -86,7 +112,7 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
   if (mk != 1) return;
   T a;
   if (G.stencil == kConstCross) {
-    const T c0 = (T)G.cw[0], x1 = (T)G.cw[1], y1 = (T)G.cw[3];
+    const T c0 = grid_w<T>(G, 0), x1 = grid_w<T>(G, 1), y1 = grid_w<T>(G, 3);
     const int64_t up = row_off(G, j + 1) + i, dn = row_off(G, j - 1) + i;
     const int im = wrap(i - 1, G.n0, G.per0), ip = wrap(i + 1, G.n0, G.per0);
     a = FIRST ? c0 * Wn[p] : fma(c0, Wn[p], -Wprev[p]);
@@ -95,7 +121,7 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
     a = fma(y1, Wn[dn], a);
     a = fma(y1, Wn[up], a);
     if (ORDER == 4) {
-      const T x2 = (T)G.cw[2], y2 = (T)G.cw[4];
+      const T x2 = grid_w<T>(G, 2), y2 = grid_w<T>(G, 4);
       const int64_t up2 = row_off(G, j + 2) + i, dn2 = row_off(G, j - 2) + i;
       const int im2 = wrap(i - 2, G.n0, G.per0), ip2 = wrap(i + 2, G.n0, G.per0);
       a = fma(x2, Wn[row + im2], a);
@@ -204,7 +230,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     const DevGrid &G = grids[t.grid];
     const InstDev &I = inst[G.inst];
     if (!I.active || n >= I.M) continue;
-    const T fc = (T)(FIRST ? 0.5 * fs * I.dt2 : fs * I.fc[n]);
+    const T fc = step_fc<T>(I, n, fs, FIRST);
     const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
     const int i = t.i0 + (int)threadIdx.x;
     if (i >= G.n0) continue;
@@ -215,8 +241,8 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       // latency-bound FP32 march, -5% for the ALU-bound FP64 march, which keeps march_point.
       const int64_t pitch = G.pitch, n1 = G.n1;
       const int64_t b0 = G.base + (int64_t)G.g1 * pitch + G.g0 + i;
-      const T c0 = (T)G.cw[0], x1 = (T)G.cw[1], x2 = (T)G.cw[2];
-      const T y1 = (T)G.cw[3], y2 = (T)G.cw[4];
+      const T c0 = grid_w<T>(G, 0), x1 = grid_w<T>(G, 1), x2 = grid_w<T>(G, 2);
+      const T y1 = grid_w<T>(G, 3), y2 = grid_w<T>(G, 4);
 #pragma unroll
       for (int m = 0; m < kPY; ++m) {
         const int j = t.j0 + (int)threadIdx.y + m * kTileY;
@@ -252,6 +278,258 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       if (j < G.n1)
         march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wprev, Wout, F, Wt, V, fc, wf_new,
                                      wf_cur);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// TMA-staged march.  A block of the fast role walks its share of the fast tiles with two
+// shared-memory stages: while it computes tile k from one stage, the five boxes of tile k+1
+// (W^n with halo, W^{n-1}, F, V, mask) arrive in the other through cp.async.bulk.tensor on
+// that stage's mbarrier.  Out-of-range box parts are zero-filled and only feed points that
+// are not computed.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Shared-memory stages of the TMA-staged march: tiles prefetched while one is computed.
+constexpr int kTmaStages = 2;
+
+// Byte layout of one stage (every box 128-byte aligned).
+template <typename T, int ORDER>
+struct TmaStage {
+  static constexpr int HY = kTileY * kPY + ORDER;  // tile rows + halo 2 x order/2
+  static constexpr int kWnBytes = kBoxX * HY * (int)sizeof(T);
+  static constexpr int kCtrBytes = kBoxX * kTileY * kPY * (int)sizeof(T);
+  static constexpr int kVBytes = kBoxX * kTileY * kPY * 8;
+  static constexpr int kMBytes = kMaskBoxX * kTileY * kPY;
+  static constexpr int kWn = 0;
+  static constexpr int kWp = (kWnBytes + 127) / 128 * 128;
+  static constexpr int kF = kWp + (kCtrBytes + 127) / 128 * 128;
+  static constexpr int kV = kF + (kCtrBytes + 127) / 128 * 128;
+  static constexpr int kM = kV + (kVBytes + 127) / 128 * 128;
+  static constexpr int kBytes = kM + (kMBytes + 127) / 128 * 128;
+  static constexpr uint32_t kTx = kWnBytes + 2 * kCtrBytes + kVBytes + kMBytes;
+  static constexpr size_t kSmem =
+      kTmaStages * (size_t)kBytes + 128 + 8 * kTmaStages;  // + alignment, the mbarriers
+};
+
+// Per-tile scalars of the TMA-staged march, read one tile ahead by the issuing thread.
+template <typename T>
+struct TmaTileInfo {
+  int64_t p0;     // state index of the tile's first point (grid point (i0, j0))
+  int64_t pitch;
+  double wf_new, wf_cur;
+  T fc, c0, x1, x2, y1, y2;
+  int ni, nj;     // points of the tile inside the grid (ragged edges)
+  int live;       // 0: the tile's instance is past its M or switched off
+};
+
+// Every block first walks its strided share of the fast tiles (blockIdx.x, + gridDim.x, ...;
+// the next tile is known, so its copies and its scalars are fetched while the current one is
+// computed), then takes general tiles by ticket, so blocks that finish early absorb the
+// costlier tiles.  ctl[0]: sticky error flag; ctl[1]: next general ticket; ctl[2]: blocks
+// done (the last one resets ctl[1] and ctl[2] for the next launch).
+template <typename T, int ORDER, bool FIRST>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    march_tma_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ ftiles,
+                     int nfast, const CUtensorMap *__restrict__ maps,
+                     const Tile *__restrict__ gtiles, int ngen, const int8_t *__restrict__ mask,
+                     T *Wa, T *Wb, const T *__restrict__ F, const T *__restrict__ Wt, double *V,
+                     const InstDev *__restrict__ inst, int n, double fs, int *ctl,
+                     unsigned long long spin_limit) {
+  using S = TmaStage<T, ORDER>;
+  constexpr int R = ORDER / 2;
+  const T *Wn = (n & 1) ? Wb : Wa;
+  T *Wout = (n & 1) ? Wa : Wb;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  uint64_t *bar = (uint64_t *)(sm + kTmaStages * S::kBytes);
+  __shared__ int s_next, s_fail;
+  __shared__ TmaTileInfo<T> s_info[kTmaStages];
+  const int tid = threadIdx.y * kTileX + threadIdx.x;
+  const int nb = (int)gridDim.x;
+  const int nmy = nfast > (int)blockIdx.x ? (nfast - 1 - (int)blockIdx.x) / nb + 1 : 0;
+  // thread 0: fetch the scalars of this block's k-th fast tile and start its copies, both
+  // into stage k % kTmaStages
+  auto issue = [&](int k) {
+    const int stage = k % kTmaStages;
+    const Tile t = ftiles[blockIdx.x + k * nb];
+    const DevGrid &G = grids[t.grid];
+    const InstDev &I = inst[G.inst];
+    TmaTileInfo<T> &f = s_info[stage];
+    f.live = I.active && n < I.M;
+    if (!f.live) {
+      mbar_arrive_tx(&bar[stage], 0);  // nothing to copy: completes the phase
+      return;
+    }
+    f.pitch = G.pitch;
+    f.p0 = G.base + (int64_t)(t.j0 + R) * G.pitch + (t.i0 + R);
+    f.wf_new = I.wf[n + 1];
+    f.wf_cur = I.wf[n];
+    f.fc = step_fc<T>(I, n, fs, FIRST);
+    f.c0 = grid_w<T>(G, 0);
+    f.x1 = grid_w<T>(G, 1);
+    f.x2 = grid_w<T>(G, 2);
+    f.y1 = grid_w<T>(G, 3);
+    f.y2 = grid_w<T>(G, 4);
+    f.ni = min(kTileX, G.n0 - t.i0);
+    f.nj = min(kTileY * kPY, G.n1 - t.j0);
+    unsigned char *st = sm + stage * S::kBytes;
+    const CUtensorMap *mp = maps + (int64_t)t.pad_ * kMapsPerGrid;
+    const int x = t.i0, yh = t.j0, yc = t.j0 + R;  // extended coordinates (ghost width R)
+    fence_proxy_async_smem();  // the stage's earlier generic reads precede the new copies
+    mbar_arrive_tx(&bar[stage], S::kTx);
+    tma_load_2d(st + S::kWn, mp + ((n & 1) ? kMapWbHalo : kMapWaHalo), x, yh, &bar[stage]);
+    tma_load_2d(st + S::kWp, mp + ((n & 1) ? kMapWaCtr : kMapWbCtr), x, yc, &bar[stage]);
+    tma_load_2d(st + S::kF, mp + kMapF, x, yc, &bar[stage]);
+    tma_load_2d(st + S::kV, mp + kMapV, x, yc, &bar[stage]);
+    tma_load_2d(st + S::kM, mp + kMapMask, x, yc, &bar[stage]);
+  };
+  if (tid == 0) {
+    for (int q = 0; q < kTmaStages; ++q) mbar_init(&bar[q], 1);
+    mbar_init_fence();
+    s_fail = 0;
+    for (int q = 0; q < kTmaStages - 1 && q < nmy; ++q) issue(q);
+  }
+  __syncthreads();
+  for (int k = 0; k < nmy; ++k) {
+    const int stage = k % kTmaStages;
+    // refill the stage read in iteration k - 1
+    if (tid == 0 && k + kTmaStages - 1 < nmy) issue(k + kTmaStages - 1);
+    unsigned long long it = 0;
+    while (!mbar_try_wait(&bar[stage], (uint32_t)((k / kTmaStages) & 1))) {
+      if (++it > spin_limit) {
+        s_fail = 1;
+        break;
+      }
+    }
+    __syncthreads();
+    if (s_fail) {
+      // give the copies still in flight a bounded time to land, then report and leave
+      if (tid == 0) {
+        atomicExch(&ctl[0], 1);
+        for (int q = k; q < k + kTmaStages && q < nmy; ++q) {
+          unsigned long long w = 0;
+          while (!mbar_try_wait(&bar[q % kTmaStages], (uint32_t)((q / kTmaStages) & 1)) &&
+                 ++w < spin_limit) {
+          }
+        }
+      }
+      return;
+    }
+    const TmaTileInfo<T> &f = s_info[stage];
+    const int li = (int)threadIdx.x;
+    if (f.live && li < f.ni) {
+      const unsigned char *st = sm + stage * S::kBytes;
+      const T *sWn = (const T *)(st + S::kWn);
+      const T *sWp = (const T *)(st + S::kWp);
+      const T *sF = (const T *)(st + S::kF);
+      const double *sV = (const double *)(st + S::kV);
+      const int8_t *sM = (const int8_t *)(st + S::kM);
+      const T fc = f.fc, c0 = f.c0, x1 = f.x1, x2 = f.x2, y1 = f.y1, y2 = f.y2;
+      const double wf_new = f.wf_new, wf_cur = f.wf_cur;
+      const int64_t pitch = f.pitch, p0 = f.p0 + li;
+      const int c = li + R;  // box column of the thread's grid column
+#pragma unroll
+      for (int m = 0; m < kPY; ++m) {
+        const int lj = (int)threadIdx.y + m * kTileY;
+        if (lj >= f.nj) continue;
+        const int8_t mk = sM[lj * kMaskBoxX + c];
+        const int64_t p = p0 + (int64_t)lj * pitch;
+        const T *w = sWn + (lj + R) * kBoxX + c;
+        const int q = lj * kBoxX + c;
+        if (mk == 2) {
+          V[p] = fma(wf_cur, to_f64(w[0]), sV[q]);
+          continue;
+        }
+        if (mk != 1) continue;
+        T a = FIRST ? c0 * w[0] : fma(c0, w[0], -sWp[q]);
+        a = fma(x1, w[-1], a);
+        a = fma(x1, w[1], a);
+        a = fma(y1, w[-kBoxX], a);
+        a = fma(y1, w[kBoxX], a);
+        if (ORDER == 4) {
+          a = fma(x2, w[-2], a);
+          a = fma(x2, w[2], a);
+          a = fma(y2, w[-2 * kBoxX], a);
+          a = fma(y2, w[2 * kBoxX], a);
+        }
+        if (FIRST) a *= (T)0.5;
+        a = fma(-fc, sF[q], a);
+        Wout[p] = a;
+        V[p] = fma(wf_new, to_f64(a), sV[q]);
+      }
+    }
+    __syncthreads();  // this stage is read; it is refilled by the issue of iteration k + 1
+  }
+  // general tiles by ticket, exactly as march_kernel.  When they are few next to the blocks
+  // (one annulus beside a large background), a ticket is a quarter tile (8 rows, one point
+  // per thread): their points' memory round trips then run in parallel blocks instead of
+  // one after another in the same threads (measured +17% on the disk workload in FP32; with
+  // many general tiles whole tiles are better).
+  const int gsplit = ngen * kPY <= 2 * nb ? kPY : 1;
+  while (true) {
+    if (tid == 0) s_next = atomicAdd(&ctl[1], 1);
+    __syncthreads();
+    const int g = s_next;
+    __syncthreads();
+    if (g >= gsplit * ngen) break;
+    const Tile t = gtiles[g / gsplit];
+    const int m0 = gsplit == 1 ? 0 : g % gsplit, m1 = gsplit == 1 ? kPY : m0 + 1;
+    const DevGrid &G = grids[t.grid];
+    const InstDev &I = inst[G.inst];
+    const int i = t.i0 + (int)threadIdx.x;
+    if (I.active && n < I.M && i < G.n0) {
+      const T fc = step_fc<T>(I, n, fs, FIRST);
+      const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
+      for (int m = m0; m < m1; ++m) {
+        const int j = t.j0 + (int)threadIdx.y + m * kTileY;
+        if (j < G.n1)
+          march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wout, Wout, F, Wt, V, fc, wf_new,
+                                       wf_cur);
+      }
+    }
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[2], 1) == nb - 1) {  // last block out: reset the tickets
+      atomicExch(&ctl[1], 0);
+      atomicExch(&ctl[2], 0);
     }
   }
 }
@@ -513,7 +791,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       }
       __syncthreads();
       if (s_fail) return;  // block-uniform after the barrier
-      const double fc = n == 0 ? 0.5 * A.fs * I.dt2 : A.fs * I.fc[n];
+      const T fc = step_fc<T>(I, n, A.fs, n == 0);
       const double fcos = A.fs * I.cosn[n];
       const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
       // stage W^n (tile + halo; wrapped on periodic axes, clamped into the extended array)
@@ -552,14 +830,14 @@ __global__ void __launch_bounds__(kTileX *kTileY)
           if (mk != 1) continue;
           T a;
           if (G.stencil == kConstCross) {
-            const T c0 = (T)G.cw[0], x1 = (T)G.cw[1], y1 = (T)G.cw[3];
+            const T c0 = grid_w<T>(G, 0), x1 = grid_w<T>(G, 1), y1 = grid_w<T>(G, 3);
             a = n == 0 ? c0 * wc : fma(c0, wc, -oth[p]);
             a = fma(x1, sw[r + R][threadIdx.x + R - 1], a);
             a = fma(x1, sw[r + R][threadIdx.x + R + 1], a);
             a = fma(y1, sw[r + R - 1][threadIdx.x + R], a);
             a = fma(y1, sw[r + R + 1][threadIdx.x + R], a);
             if (ORDER == 4) {
-              const T x2 = (T)G.cw[2], y2 = (T)G.cw[4];
+              const T x2 = grid_w<T>(G, 2), y2 = grid_w<T>(G, 4);
               a = fma(x2, sw[r + R][threadIdx.x + R - 2], a);
               a = fma(x2, sw[r + R][threadIdx.x + R + 2], a);
               a = fma(y2, sw[r + R - 2][threadIdx.x + R], a);
@@ -592,7 +870,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                         sw[r + R + bb][threadIdx.x + R + aa], a);
           }
           if (n == 0) a *= (T)0.5;
-          a = fma((T)(-fc), F[p], a);
+          a = fma(-fc, F[p], a);
           oth[p] = a;
           A.V[p] = fma(wf_new, to_f64(a), A.V[p]);
         }
@@ -1110,6 +1388,68 @@ void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cud
     else            { if (first) WH_MARCH(double, 2, true); else WH_MARCH(double, 2, false); }
   }
 #undef WH_MARCH
+}
+
+size_t march_tma_smem(bool fp32, int order) {
+  if (fp32) return order == 4 ? TmaStage<float, 4>::kSmem : TmaStage<float, 2>::kSmem;
+  return order == 4 ? TmaStage<double, 4>::kSmem : TmaStage<double, 2>::kSmem;
+}
+
+template <typename T, int O, bool FI>
+static void tma_attr() {
+  cudaFuncSetAttribute(march_tma_kernel<T, O, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaStage<T, O>::kSmem);
+}
+
+int march_tma_blocks_per_sm(bool fp32, int order) {
+  const int threads = kTileX * kTileY;
+  int nb = 0;
+  if (fp32) {
+    if (order == 4) {
+      tma_attr<float, 4, false>();
+      tma_attr<float, 4, true>();
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_tma_kernel<float, 4, false>,
+                                                    threads, TmaStage<float, 4>::kSmem);
+    } else {
+      tma_attr<float, 2, false>();
+      tma_attr<float, 2, true>();
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_tma_kernel<float, 2, false>,
+                                                    threads, TmaStage<float, 2>::kSmem);
+    }
+  } else {
+    if (order == 4) {
+      tma_attr<double, 4, false>();
+      tma_attr<double, 4, true>();
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_tma_kernel<double, 4, false>,
+                                                    threads, TmaStage<double, 4>::kSmem);
+    } else {
+      tma_attr<double, 2, false>();
+      tma_attr<double, 2, true>();
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, march_tma_kernel<double, 2, false>,
+                                                    threads, TmaStage<double, 2>::kSmem);
+    }
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+void launch_march_tma(bool fp32, int order, bool first, int nblocks, cudaStream_t s,
+                      const DevGrid *grids, const Tile *ftiles, int nfast, const CUtensorMap *maps,
+                      const Tile *gtiles, int ngen, const int8_t *mask, void *Wa, void *Wb,
+                      const void *F, const void *Wt, double *V, const InstDev *inst, int n,
+                      double fs, int *ctl, unsigned long long spin_limit) {
+  const dim3 tb(kTileX, kTileY);
+#define WH_TMA(T, O, FI)                                                                       \
+  march_tma_kernel<T, O, FI><<<nblocks, tb, TmaStage<T, O>::kSmem, s>>>(                       \
+      grids, ftiles, nfast, maps, gtiles, ngen, mask, (T *)Wa, (T *)Wb, (const T *)F,          \
+      (const T *)Wt, V, inst, n, fs, ctl, spin_limit)
+  if (fp32) {
+    if (order == 4) { if (first) WH_TMA(float, 4, true); else WH_TMA(float, 4, false); }
+    else            { if (first) WH_TMA(float, 2, true); else WH_TMA(float, 2, false); }
+  } else {
+    if (order == 4) { if (first) WH_TMA(double, 4, true); else WH_TMA(double, 4, false); }
+    else            { if (first) WH_TMA(double, 2, true); else WH_TMA(double, 2, false); }
+  }
+#undef WH_TMA
 }
 
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,

@@ -78,3 +78,20 @@ def test_fp32_refinement_reaches_1e6(torch, W, name, make):
     assert st.products_fp32 > st.products_fp64 > 0
     err = np.max(np.abs(u.cpu().numpy() - U)[act]) / np.max(np.abs(U)[act])
     assert err <= SOLVE_BOUND, err
+
+
+@pytest.mark.parametrize("n,order", [(64, 2), (45, 4), (100, 4)])
+def test_fp32_graph_equals_persistent_bitwise(torch, W, n, order):
+    """Without interpolation points both launch paths do the same FP32 arithmetic in the
+    same order: the graph path's TMA-staged march (shared-memory boxes, zero-filled edges,
+    ragged tiles) must reproduce the persistent kernel's result bit for bit."""
+    prob = G.unit_square_problem(n, order, 10.0, seed=3)
+    out = []
+    for mode in (W.GRAPH, W.PERSISTENT):
+        s = W.Solver(prob, precision=W.FP32, launch_mode=mode)
+        s.prepare()
+        v = torch.from_numpy(G.random_state(prob, 4)).cuda()
+        o = torch.empty_like(v)
+        s.iterate(v, o, True)
+        out.append(o.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
