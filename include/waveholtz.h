@@ -208,19 +208,21 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, doub
  * classical Gram-Schmidt applied twice, Sec. 4.3).  u: DEVICE compact vector, the
  * initial guess on entry and the solution on exit.  history (host, may be NULL)
  * receives up to history_cap relative residuals.  max_it bounds the wave solves.
- * On a WH_FP32 context, WH_GMRES is mixed-precision iterative refinement: b and every
- * outer residual b - A u use the FP64 march; each correction A d = r is one GMRES(restart)
- * cycle with the FP32 march (to 1e-4 relative); the orthogonalisation, the updates and
- * all reductions are FP64.  WH_FPI iterates with the context's march.  Returns
+ * On a WH_FP32 context, WH_GMRES runs in two phases: b uses the FP64 march; GMRES(restart)
+ * cycles whose wave solves use the FP32 march take the residual to max(tol, 1e-4) (or
+ * until a cycle no longer halves it), then FP64-march cycles continue from that iterate to
+ * tol, confirmed by a true FP64 residual.  The orthogonalisation, the updates and all
+ * reductions are FP64 throughout.  WH_FPI iterates with the context's march.  Returns
  * WH_ERR_NOT_CONVERGED (u holds the last iterate) when max_it is reached,
- * WH_ERR_DIVERGED on NaN/Inf or a growing refinement residual. */
+ * WH_ERR_DIVERGED on NaN/Inf. */
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
                    double *u, wh_stats *stats, double *history, int32_t history_cap);
 
 /* Batched solve: one GMRES per instance (restart cycles of the same length), all advancing
  * in lockstep around one batched wave solve per Arnoldi step; an instance that reaches
  * ||b_k - A_k u_k|| <= tol ||b_k|| (checked with the FP64 march) is switched off in the
- * kernels.  FP32 contexts refine each instance as wh_solve does.  u: DEVICE compact vector
+ * kernels.  FP32 contexts run the two phases of wh_solve per instance (FP32 wave solves to
+ * max(tol, 1e-4), then FP64 ones).  u: DEVICE compact vector
  * of all instances (initial guess in, solutions out); stats: host array of one entry per
  * instance (seconds is the whole batch's).  max_it bounds the batched wave solves. */
 wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,

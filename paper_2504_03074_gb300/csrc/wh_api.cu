@@ -1000,6 +1000,10 @@ wh_status apply_A(wh_ctx *ctx, const double *x, double *y, double *w0, SolveLog 
 // applied twice, Givens rotations; stops early when the residual estimate drops to
 // tol_abs or the product budget runs out.  scale converts residual norms into the
 // relative values written to the log.
+// FP32 contexts: relative residual at which a solve switches from FP32 to FP64 wave solves
+// (an FP32 product is accurate to a few 1e-5 relative on the tested problems)
+constexpr double kFp32Split = 1e-4;
+
 wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero, int m,
                       double tol_abs, int budget, double scale, SolveLog &L, double *res_out,
                       bool *finite) {
@@ -1933,69 +1937,59 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     return finish(WH_OK);
   }
   double *b = w2;
-  if (default_set(ctx) == 0) {
-    // FP64 GMRES(m): restart cycles, each starting from the true residual
+  if (default_set(ctx) == 1) {
+    // FP32 march: the first digits with FP32 wave solves, the rest with FP64 ones.  Phase 1:
+    // GMRES(m) cycles whose products use the FP32 march (orthogonalisation, rotations and
+    // the iterate stay FP64) down to max(tol, kFp32Split), or until a cycle no longer
+    // halves the residual; phase 2 below: FP64 GMRES(m) from that iterate to tol, ended by a
+    // true FP64 residual.  Each Krylov space is built once; refinement, which rebuilds one
+    // per correction, measured ~1.9x the wave solves of FP64 GMRES on the solve benchmark.
+    const double tol1 = std::max(tol, kFp32Split);
+    double prev = 1e300;
+    use_set(ctx, 1);
     while (true) {
       double res;
       bool fin;
       const int budget = max_it - (L.products[0] + L.products[1]);
-      if ((st = gmres_cycle(ctx, b, u, false, m, tol * bnorm, budget, 1.0 / bnorm, L, &res, &fin)))
+      if ((st = gmres_cycle(ctx, b, u, false, m, tol1 * bnorm, budget, 1.0 / bnorm, L, &res,
+                            &fin)))
         return finish(st);
-      S.residual = res / bnorm;
       if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual is not finite"));
-      if (res <= tol * bnorm) {
-        // the cycle's last value may be the Givens estimate: confirm with a true residual
-        double *rr = ctx->d_work + n;
-        if ((st = apply_A(ctx, u, rr, w0, L))) return finish(st);
-        launch_axpby(grid1d(n), s, 1.0, b, -1.0, rr, n);
-        double r2;
-        if ((st = multidot(ctx, rr, 0, 1, rr, n, &r2))) return finish(st);
-        S.residual = std::sqrt(r2) / bnorm;
-        L.add(S.residual);
-        if (S.residual <= tol) {
-          S.converged = 1;
-          return finish(WH_OK);
-        }
-      }
+      S.residual = res / bnorm;
+      if (res <= tol1 * bnorm || res > 0.5 * prev) break;
+      prev = res;
       if (L.products[0] + L.products[1] >= max_it)
         return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
                            S.residual));
     }
-  }
-  // FP32 march: iterative refinement.  Outer residual r = b - A u with the FP64 march;
-  // the correction A d = r by one GMRES cycle with the FP32 march (to 1e-4 relative or
-  // the cycle's end); u += d.
-  double *r = ctx->d_work + 3 * n, *d = ctx->d_work + 4 * n;
-  double prev = 1e300;
-  while (true) {
     use_set(ctx, 0);
-    if ((st = apply_A(ctx, u, r, w0, L))) return finish(st);
-    launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);  // r = b - A u
-    double r2;
-    if ((st = multidot(ctx, r, 0, 1, r, n, &r2))) return finish(st);
-    const double rn = std::sqrt(r2);
-    S.residual = rn / bnorm;
-    L.add(S.residual);
-    if (!std::isfinite(rn) || rn > 10.0 * prev)
-      return finish(fail(ctx, WH_ERR_DIVERGED, "refinement residual %g", S.residual));
-    if (S.residual <= tol) {
-      S.converged = 1;
-      return finish(WH_OK);
-    }
-    if (L.products[0] + L.products[1] >= max_it)
-      return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "refinement: %d products, residual %g",
-                         max_it, S.residual));
-    prev = rn;
-    use_set(ctx, 1);
-    CK(cudaMemsetAsync(d, 0, n * sizeof(double), s));
+  }
+  // FP64 GMRES(m): restart cycles, each starting from the true residual
+  while (true) {
     double res;
     bool fin;
-    const int left = max_it - (L.products[0] + L.products[1]);
-    if ((st = gmres_cycle(ctx, r, d, true, m, std::max(1e-4 * rn, 0.5 * tol * bnorm), left,
-                          1.0 / bnorm, L, &res, &fin)))
+    const int budget = max_it - (L.products[0] + L.products[1]);
+    if ((st = gmres_cycle(ctx, b, u, false, m, tol * bnorm, budget, 1.0 / bnorm, L, &res, &fin)))
       return finish(st);
-    if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "inner GMRES residual is not finite"));
-    launch_axpby(grid1d(n), s, 1.0, d, 1.0, u, n);  // u += d
+    S.residual = res / bnorm;
+    if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual is not finite"));
+    if (res <= tol * bnorm) {
+      // the cycle's last value may be the Givens estimate: confirm with a true residual
+      double *rr = ctx->d_work + n;
+      if ((st = apply_A(ctx, u, rr, w0, L))) return finish(st);
+      launch_axpby(grid1d(n), s, 1.0, b, -1.0, rr, n);
+      double r2;
+      if ((st = multidot(ctx, rr, 0, 1, rr, n, &r2))) return finish(st);
+      S.residual = std::sqrt(r2) / bnorm;
+      L.add(S.residual);
+      if (S.residual <= tol) {
+        S.converged = 1;
+        return finish(WH_OK);
+      }
+    }
+    if (L.products[0] + L.products[1] >= max_it)
+      return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
+                         S.residual));
   }
 }
 
@@ -2021,8 +2015,7 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
     I[k].off = ctx->icstart[k];
     I[k].len = ctx->icend[k] - ctx->icstart[k];
   }
-  double *w0 = ctx->d_work, *b = ctx->d_work + 2 * n, *r = ctx->d_work + 3 * n,
-         *d = ctx->d_work + 4 * n;
+  double *w0 = ctx->d_work, *b = ctx->d_work + 2 * n, *r = ctx->d_work + 3 * n;
   std::vector<int8_t> all(K, 1);
   auto finish = [&](wh_status code) {
     std::vector<int8_t> on(K, 1);
@@ -2062,61 +2055,55 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
       if (!G.converged) return false;
     return true;
   };
-  if (default_set(ctx) == 0) {
-    while (!all_done() && budget > 0) {
-      for (auto &G : I) {
-        G.in_cycle = !G.converged;
-        G.tol_abs = tol * G.bnorm;
+  if (default_set(ctx) == 1) {
+    // FP32 march, phase 1 (as in wh_solve): FP32 wave solves down to max(tol, kFp32Split)
+    // per instance, or until an instance's cycle no longer halves its residual
+    const double tol1 = std::max(tol, kFp32Split);
+    std::vector<int8_t> p1(K, 0);
+    std::vector<double> prev(K, 1e300);
+    for (int k = 0; k < K; ++k) p1[k] = !I[k].converged;
+    use_set(ctx, 1);
+    auto any = [&]() {
+      for (int8_t x : p1)
+        if (x) return true;
+      return false;
+    };
+    while (any() && budget > 0) {
+      for (int k = 0; k < K; ++k) {
+        I[k].in_cycle = p1[k] != 0;
+        I[k].tol_abs = tol1 * I[k].bnorm;
       }
       if ((st = gmres_cycle_batch(ctx, b, u, false, m, budget, I))) return finish(st);
-      for (auto &G : I)
-        if (!G.finite) return finish(fail(ctx, WH_ERR_DIVERGED, "batched GMRES: non-finite"));
-      // confirm with true residuals at the start of the next cycle; here a separate check
-      std::vector<int8_t> act(K, 0);
-      for (int k = 0; k < K; ++k) act[k] = !I[k].converged;
-      if ((st = apply_A_batch(ctx, u, r, w0, I, act))) return finish(st);
-      --budget;
-      launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);
       for (int k = 0; k < K; ++k) {
-        if (!act[k]) continue;
-        double rr;
-        if ((st = multidot(ctx, r + I[k].off, 0, 1, r + I[k].off, I[k].len, &rr)))
-          return finish(st);
-        I[k].res = std::sqrt(rr);
-        if (I[k].res <= tol * I[k].bnorm) I[k].converged = true;
+        if (!p1[k]) continue;
+        if (!I[k].finite) return finish(fail(ctx, WH_ERR_DIVERGED, "batched GMRES: non-finite"));
+        if (I[k].res <= tol1 * I[k].bnorm || I[k].res > 0.5 * prev[k]) p1[k] = 0;
+        prev[k] = I[k].res;
       }
     }
-  } else {
-    // FP32 march: per-instance iterative refinement, lockstep
-    while (budget > 0) {
-      use_set(ctx, 0);
-      std::vector<int8_t> act(K, 0);
-      for (int k = 0; k < K; ++k) act[k] = !I[k].converged;
-      if ((st = apply_A_batch(ctx, u, r, w0, I, act))) return finish(st);
-      --budget;
-      launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);
-      for (int k = 0; k < K; ++k) {
-        if (!act[k]) continue;
-        double rr;
-        if ((st = multidot(ctx, r + I[k].off, 0, 1, r + I[k].off, I[k].len, &rr)))
-          return finish(st);
-        I[k].res = std::sqrt(rr);
-        if (!std::isfinite(I[k].res))
-          return finish(fail(ctx, WH_ERR_DIVERGED, "batched refinement: non-finite"));
-        if (I[k].res <= tol * I[k].bnorm) I[k].converged = true;
-      }
-      if (all_done() || budget <= 0) break;
-      use_set(ctx, 1);
-      CK(cudaMemsetAsync(d, 0, n * sizeof(double), s));
-      for (auto &G : I) {
-        G.in_cycle = !G.converged;
-        G.tol_abs = std::max(1e-4 * G.res, 0.5 * tol * G.bnorm);
-      }
-      const double *rc = r;
-      if ((st = gmres_cycle_batch(ctx, rc, d, true, m, budget, I))) return finish(st);
-      for (int k = 0; k < K; ++k)
-        if (!I[k].converged)
-          launch_axpby(grid1d(I[k].len), s, 1.0, d + I[k].off, 1.0, u + I[k].off, I[k].len);
+    use_set(ctx, 0);
+  }
+  // FP64 GMRES(m) cycles to tol, each instance confirmed by a true FP64 residual
+  while (!all_done() && budget > 0) {
+    for (auto &G : I) {
+      G.in_cycle = !G.converged;
+      G.tol_abs = tol * G.bnorm;
+    }
+    if ((st = gmres_cycle_batch(ctx, b, u, false, m, budget, I))) return finish(st);
+    for (auto &G : I)
+      if (!G.finite) return finish(fail(ctx, WH_ERR_DIVERGED, "batched GMRES: non-finite"));
+    std::vector<int8_t> act(K, 0);
+    for (int k = 0; k < K; ++k) act[k] = !I[k].converged;
+    if ((st = apply_A_batch(ctx, u, r, w0, I, act))) return finish(st);
+    --budget;
+    launch_axpby(grid1d(n), s, 1.0, b, -1.0, r, n);
+    for (int k = 0; k < K; ++k) {
+      if (!act[k]) continue;
+      double rr;
+      if ((st = multidot(ctx, r + I[k].off, 0, 1, r + I[k].off, I[k].len, &rr)))
+        return finish(st);
+      I[k].res = std::sqrt(rr);
+      if (I[k].res <= tol * I[k].bnorm) I[k].converged = true;
     }
   }
   if (all_done()) return finish(WH_OK);
