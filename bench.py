@@ -192,9 +192,6 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
     sa = WH.Solver(prob, stream=stream)
     ta = sa.prepare()
     n = prob.n_total
-    x = torch.randn(n, dtype=torch.float64, device="cuda")
-    y = torch.empty_like(x)
-    zero = torch.zeros_like(x)
 
     def timed(fn, reps, warm=2):
         with torch.cuda.stream(stream):
@@ -212,16 +209,31 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
                 tot += e0.elapsed_time(e1) / 1e3
         return tot / reps
 
-    tf = time_iterations(WH, torch, sa, n, stream, flush, 5)
-    tt = timed(lambda: sa.apply_adjoint(x, y), 5)
-    tg = timed(lambda: sa.adjoint(x, zero, 1e-8, 10, 10), 3)
-    out["adjoint"] = {"transpose_apply": {"value": ta.n_active * ta.M / tt / 1e9,
-                                          "unit": "GLUP/s", "ms": tt * 1e3,
-                                          "vs_forward_iteration": tt / tf},
-                      "gradient_sweep": {"ms": tg * 1e3, "vs_forward_iteration": tg / tf},
-                      "workload": "same disk-in-square workload, FP64"}
+    def adjoint_costs(sa, ta, n):
+        x = torch.randn(n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        zero = torch.zeros_like(x)
+        tf = time_iterations(WH, torch, sa, n, stream, flush, 5)
+        tt = timed(lambda: sa.apply_adjoint(x, y), 5)
+        tg = timed(lambda: sa.adjoint(x, zero, 1e-8, 10, 10), 3)
+        return {"transpose_apply": {"value": ta.n_active * ta.M / tt / 1e9, "unit": "GLUP/s",
+                                    "ms": tt * 1e3, "vs_forward_iteration": tt / tf},
+                "gradient_sweep": {"ms": tg * 1e3, "vs_forward_iteration": tg / tf},
+                "forward_iteration_ms": tf * 1e3}
+
+    out["adjoint"] = adjoint_costs(sa, ta, n)
+    out["adjoint"]["workload"] = "same disk-in-square workload, FP64"
     sa.close()
-    del x, y, zero
+    # the sound-speed inversion geometry: 512^2 background + 1024x32 annulus, omega 20,
+    # c = 1 + 0.2 sum of 8 Gaussian bumps (every grid on per-point weights)
+    mp = G.misfit_problem(nb=512, omega=20.0, seed=0)
+    sm = WH.Solver(mp, stream=stream)
+    tm = sm.prepare()
+    out["adjoint_misfit_512"] = adjoint_costs(sm, tm, mp.n_total)
+    out["adjoint_misfit_512"]["workload"] = (
+        "disk-in-square 512^2 + 1024x32, order 4, omega 20, c = 1 + 0.2 sum of 8 Gaussian "
+        "bumps (width 0.2), FP64; M = %d" % tm.M)
+    sm.close()
     # batch: 256 disk-in-square instances, N ~ U{256..1024}, annulus 2N x N/16,
     # omega ~ U[10, 50], 1-4 sources
     t0 = time.perf_counter()

@@ -457,6 +457,42 @@ def batch_disk_problem(n_inst=256, seed=0, nb_range=(256, 1024), omega_range=(10
     return batch_problems(probs), probs
 
 
+def receiver_matrix(problem, n=64, radius=1.5):
+    """Receivers of a misfit: bilinear sampling of the background grid (grid 0, Cartesian) at
+    n points (k + 1/2) 2 pi / n on a circle, as a scipy CSR matrix acting on compact vectors
+    (n x n_total)."""
+    import scipy.sparse as sp
+    g = problem.grids[0]
+    th = 2 * np.pi * (np.arange(n) + 0.5) / n
+    rows, cols, vals = [], [], []
+    for k, t in enumerate(th):
+        fi = (radius * np.cos(t) - g.origin[0]) / g.h[0]
+        fj = (radius * np.sin(t) - g.origin[1]) / g.h[1]
+        i0, j0 = int(np.floor(fi)), int(np.floor(fj))
+        a, b = fi - i0, fj - j0
+        for di, dj, w in ((0, 0, (1 - a) * (1 - b)), (1, 0, a * (1 - b)), (0, 1, (1 - a) * b),
+                          (1, 1, a * b)):
+            rows.append(k)
+            cols.append((j0 + dj) * g.n[0] + (i0 + di))
+            vals.append(w)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, problem.n_total))
+
+
+def misfit_problem(nb=512, omega=20.0, order=4, seed=0, width=0.3, r_cut=0.65):
+    """The sound-speed inversion workload: disk-in-square at nb^2 (annulus 2nb x nb/16),
+    c = 1 + 0.2 sum of 8 seeded Gaussian bumps of width 0.2, one seeded source."""
+    return disk_problem(nb=nb, nth=2 * nb, nr=max(nb // 16, 8 + order), order=order,
+                        omega=omega, seed=seed, c_bumps=8, width=width, r_cut=r_cut)
+
+
+def perturbed_c2(problem, amp=0.05, center=(0.9, -0.4), width2=0.3):
+    """c^2 of the "true" medium that makes a misfit's data: the problem's c^2 scaled by
+    1 + amp exp(-|x - center|^2 / width2), per grid."""
+    return [c * (1 + amp * np.exp(-((g.xy[0] - center[0]) ** 2 + (g.xy[1] - center[1]) ** 2)
+                                  / width2))
+            for c, g in zip(problem.c2, problem.grids)]
+
+
 def random_state(problem, seed):
     """A seeded random vector on the active points (zero on unused points)."""
     rng = np.random.default_rng(seed)
