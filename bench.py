@@ -58,7 +58,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -70,6 +70,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=5.0):
+        """Block until the sampler has produced a line (nvidia-smi takes a while to start)."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self):
+        return len(self.lines)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -78,10 +87,15 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, start=0):
+        """Samples from index `start` (the timed region's start) on; if none arrived there,
+        all samples (warm-up included), flagged by "window"."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines, window = self.lines[start:], "timed"
+        if not lines:
+            lines, window = self.lines, "warmup+timed"
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -96,7 +110,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def kernel_sha():
@@ -460,7 +474,8 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     va = torch.zeros(n, dtype=torch.float64, device="cuda")
     vb = torch.empty_like(va)
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), ClockSampler(local) as clk:
+        clk.wait_first()
         for _ in range(max(args.warmup, 0)):
             s.iterate(va, vb, True)
             va, vb = vb, va
@@ -470,15 +485,15 @@ def main():
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            for k in range(args.steps):
-                flush.fill_(float(k))  # L2 flush between timed iterations (untimed)
-                ev[k][0].record(stream)
-                s.iterate(va, vb, True)
-                ev[k][1].record(stream)
-                va, vb = vb, va
-            stream.synchronize()
-            torch.cuda.synchronize()
+        clk_start = clk.mark()
+        for k in range(args.steps):
+            flush.fill_(float(k))  # L2 flush between timed iterations (untimed)
+            ev[k][0].record(stream)
+            s.iterate(va, vb, True)
+            ev[k][1].record(stream)
+            va, vb = vb, va
+        stream.synchronize()
+        torch.cuda.synchronize()
         launches = s.last_launch_count() * args.steps
     ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(ms) / 1e3
@@ -540,7 +555,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GLUP/s", "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": n * 8, "ms_per_step": e2e_t * 1e3},
-        "clocks": clk.summary(),
+        "clocks": clk.summary(clk_start),
         "gpu_launches": launches,
         "forms": forms,
         "kernels_ms_per_iteration": {k: v[0] * v[1] for k, v in prof.items()},

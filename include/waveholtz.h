@@ -265,8 +265,9 @@ wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, doubl
 /* Measurement aid: the device time of each kernel of the iteration, from graph-captured
  * bursts of `reps` back-to-back launches (warm L2, no host gaps) on the prepared problem.
  * ms[4] and counts[4] (host) receive the average milliseconds per launch and the launches
- * per iteration of: [0] the march kernel, [1] the ghost-rule + interpolation kernel,
- * [2] the input kernel, [3] the output kernel.  The bursts run on the context's internal
+ * per iteration of: [0] the march kernel (with the next level's ghost rules and
+ * interpolation when the iteration folds them into its launches), [1] the separate
+ * ghost-rule + interpolation kernel, [2] the input kernel, [3] the output kernel.  The bursts run on the context's internal
  * working buffers and leave them unspecified (every wh_iterate rebuilds them from its
  * input).  Synchronises. */
 wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts);

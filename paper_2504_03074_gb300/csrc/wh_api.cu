@@ -72,6 +72,12 @@ struct wh_ctx {
   std::vector<int32_t> fast_grids;  // grid of each map slot
   Tile *d_ftiles = nullptr, *d_gtiles = nullptr;
   int *d_err = nullptr;  // TMA march control: [0] sticky error flag, [1] ticket, [2] blocks done
+  // ghost rules + interpolation folded into the march launch (march_kernel sets)
+  int nunits = 0;
+  std::vector<int64_t> udep_off;
+  std::vector<int32_t> udep_tile;
+  int64_t *d_udep_off = nullptr;
+  int32_t *d_udep_tile = nullptr;
   std::vector<BcItem> hbc;
   std::vector<int32_t> hbc_grid, hbc_axis, hbc_hi;
   std::vector<void *> allocs;
@@ -380,31 +386,6 @@ wh_status build_layout(wh_ctx *ctx) {
     }
     ctx->htiles.swap(mixed);
   }
-  {
-    // TMA-staged march: tiles of non-periodic constant-weight grids whose ghost width is the
-    // stencil radius (every TMA box then starts at a 16-byte aligned extended column)
-    ctx->hftiles.clear();
-    ctx->hgtiles.clear();
-    ctx->fast_grids.clear();
-    std::vector<int32_t> slot(ctx->hgrids.size(), -1);
-    for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
-      const DevGrid &G = ctx->hgrids[g];
-      if (G.stencil == kConstCross && !G.per0 && !G.per1 && G.g0 == R && G.g1 == R &&
-          G.base % 32 == 0 && G.pitch % 32 == 0) {
-        slot[g] = (int32_t)ctx->fast_grids.size();
-        ctx->fast_grids.push_back((int32_t)g);
-      }
-    }
-    for (const Tile &t : ctx->htiles) {
-      if (slot[t.grid] >= 0 && t.i0 % 32 == 0) {
-        Tile f = t;
-        f.pad_ = slot[t.grid];
-        ctx->hftiles.push_back(f);
-      } else {
-        ctx->hgtiles.push_back(t);
-      }
-    }
-  }
   ctx->total = off;
   ctx->ncompact = coff;
   ctx->nactive = nact;
@@ -547,6 +528,86 @@ wh_status build_layout(wh_ctx *ctx) {
       }
   }
 
+  // Ghost rules and interpolation folded into the march launch: work units as the blocks of
+  // the separate kernel (256 items, or 256 / lanes receivers), and for each unit the tiles
+  // holding the values it reads (ghost-rule sources, donors).  Those tiles go first in the
+  // march order (they are done early in the launch) and signal when written (pad_ = 1).
+  {
+    const int ntl = (int)ctx->htiles.size();
+    std::vector<int32_t> owner(off, -1);
+    for (int t = 0; t < ntl; ++t) {
+      const Tile &T = ctx->htiles[t];
+      const DevGrid &G = ctx->hgrids[T.grid];
+      for (int j = T.j0; j < std::min(T.j0 + kTileY * kPY, G.n1); ++j)
+        for (int i = T.i0; i < std::min(T.i0 + kTileX, G.n0); ++i) owner[ext_index(G, i, j)] = t;
+    }
+    const int lanes = order == 4 ? 8 : 4;
+    const int nbc = (int)ctx->hbc.size();
+    const int bc_blocks = (nbc + 255) / 256;
+    const int g_blocks = (int)((ctx->nrecv * lanes + 255) / 256);
+    ctx->nunits = bc_blocks + g_blocks;
+    std::vector<std::vector<int32_t>> udep(ctx->nunits);
+    std::vector<char> needed(ntl, 0);
+    auto add = [&](int u, int64_t p) {
+      if (p >= 0 && p < off && owner[p] >= 0) {
+        udep[u].push_back(owner[p]);
+        needed[owner[p]] = 1;
+      }
+    };
+    for (int k = 0; k < nbc; ++k)
+      for (int q = 0; q < 4; ++q) add(k / 256, ctx->hbc[k].u[q]);
+    for (int64_t r = 0; r < ctx->nrecv; ++r)
+      for (int d = 0; d < ND; ++d) add(bc_blocks + (int)(r * lanes / 256), didx[r * ND + d]);
+    // stable partition: signalling tiles first
+    std::vector<int32_t> newpos(ntl);
+    std::vector<Tile> order_t;
+    order_t.reserve(ntl);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int t = 0; t < ntl; ++t)
+        if ((needed[t] != 0) == (pass == 0)) {
+          newpos[t] = (int32_t)order_t.size();
+          Tile T = ctx->htiles[t];
+          T.pad_ = needed[t] ? 1 : 0;
+          order_t.push_back(T);
+        }
+    ctx->htiles.swap(order_t);
+    ctx->udep_off.assign(ctx->nunits + 1, 0);
+    ctx->udep_tile.clear();
+    for (int u = 0; u < ctx->nunits; ++u) {
+      std::vector<int32_t> &d = udep[u];
+      for (int32_t &x : d) x = newpos[x];
+      std::sort(d.begin(), d.end());
+      d.erase(std::unique(d.begin(), d.end()), d.end());
+      ctx->udep_tile.insert(ctx->udep_tile.end(), d.begin(), d.end());
+      ctx->udep_off[u + 1] = (int64_t)ctx->udep_tile.size();
+    }
+  }
+  {
+    // TMA-staged march: tiles of non-periodic constant-weight grids whose ghost width is the
+    // stencil radius (every TMA box then starts at a 16-byte aligned extended column)
+    ctx->hftiles.clear();
+    ctx->hgtiles.clear();
+    ctx->fast_grids.clear();
+    std::vector<int32_t> slot(ctx->hgrids.size(), -1);
+    for (size_t g = 0; g < ctx->hgrids.size(); ++g) {
+      const DevGrid &G = ctx->hgrids[g];
+      if (G.stencil == kConstCross && !G.per0 && !G.per1 && G.g0 == R && G.g1 == R &&
+          G.base % 32 == 0 && G.pitch % 32 == 0) {
+        slot[g] = (int32_t)ctx->fast_grids.size();
+        ctx->fast_grids.push_back((int32_t)g);
+      }
+    }
+    for (const Tile &t : ctx->htiles) {
+      if (slot[t.grid] >= 0 && t.i0 % 32 == 0) {
+        Tile f = t;
+        f.pad_ = slot[t.grid];
+        ctx->hftiles.push_back(f);
+      } else {
+        ctx->hgtiles.push_back(t);
+      }
+    }
+  }
+
   // persistent-kernel patch lists: ghost and receiver positions inside each tile's staged
   // box (tile + halo of order/2, corner blocks excluded: the cross stencil never reads
   // them; box stencils only occur on grids without ghosts or receivers in the halo corners
@@ -663,6 +724,8 @@ wh_status build_layout(wh_ctx *ctx) {
       (st = dalloc(ctx, &ctx->d_ftiles, std::max<size_t>(ctx->hftiles.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_gtiles, std::max<size_t>(ctx->hgtiles.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_err, 3)) ||
+      (st = dalloc(ctx, &ctx->d_udep_off, ctx->udep_off.size())) ||
+      (st = dalloc(ctx, &ctx->d_udep_tile, std::max<size_t>(ctx->udep_tile.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_mask, off)) ||
       (st = dalloc(ctx, &ctx->d_V, off)) || (st = dalloc(ctx, &ctx->d_c2, off)) ||
       (st = dalloc(ctx, &ctx->d_rx, std::max<int64_t>(k5, 1))) ||
@@ -703,6 +766,11 @@ wh_status build_layout(wh_ctx *ctx) {
                 cudaMemcpyHostToDevice));
   if (!ctx->hftiles.empty())
     CK(cudaMemcpy(ctx->d_ftiles, ctx->hftiles.data(), ctx->hftiles.size() * sizeof(Tile),
+                  cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_udep_off, ctx->udep_off.data(), ctx->udep_off.size() * 8,
+                cudaMemcpyHostToDevice));
+  if (!ctx->udep_tile.empty())
+    CK(cudaMemcpy(ctx->d_udep_tile, ctx->udep_tile.data(), ctx->udep_tile.size() * 4,
                   cudaMemcpyHostToDevice));
   if (!ctx->hgtiles.empty())
     CK(cudaMemcpy(ctx->d_gtiles, ctx->hgtiles.data(), ctx->hgtiles.size() * sizeof(Tile),
@@ -749,9 +817,40 @@ wh_status build_layout(wh_ctx *ctx) {
   return WH_OK;
 }
 
+// Ghost rules and interpolation folded into march_kernel's launch (see GatherArgs) when
+// their work units are few next to the march blocks: each block then runs at most one unit
+// after its tiles (disk workload: 235 units, 608 blocks, +6%).  With many units (a batch
+// of instances) the separate, fully parallel kernel is faster (16 instances: folding -12%).
+bool folds_gather(const wh_ctx *ctx) {
+  const int nb = std::min((int)ctx->htiles.size(), ctx->march_blocks);
+  return !ctx->set[ctx->active].tma && ctx->nunits > 0 && 2 * ctx->nunits <= nb;
+}
+
+GatherArgs gather_args(wh_ctx *ctx) {
+  GatherArgs ga{};
+  const int nbc = (int)ctx->hbc.size();
+  ga.bc = ctx->d_bc;
+  ga.didx = ctx->d_didx;
+  ga.dw = ctx->d_dw;
+  ga.ridx = ctx->d_ridx;
+  ga.rinst = ctx->d_rinst;
+  ga.udep_off = ctx->d_udep_off;
+  ga.udep_tile = ctx->d_udep_tile;
+  ga.tile_done = ctx->d_tile_done;
+  ga.err = ctx->d_err;
+  ga.spin_limit = ctx->opt_spin_limit;
+  ga.nbc = nbc;
+  ga.bc_blocks = (nbc + 255) / 256;
+  ga.nunits = ctx->nunits;
+  ga.nrecv = (int)ctx->nrecv;
+  return ga;
+}
+
 // One march step of the active set: the TMA-staged kernel when the set has tensor maps,
-// else march_kernel.
-void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs) {
+// else march_kernel (with level n + 1's ghost rules and interpolation folded in when
+// `gather` is given).
+void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs,
+                const GatherArgs *gather = nullptr) {
   const MarchSet &S = ctx->set[ctx->active];
   const int order = ctx->opt.order;
   if (S.tma) {
@@ -765,7 +864,7 @@ void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs) {
   const int ntiles = (int)ctx->htiles.size();
   launch_march(S.fp32, order, n == 0, std::min(ntiles, ctx->march_blocks), ntiles, ctx->stream,
                ctx->d_grids, ctx->d_tiles, ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt,
-               ctx->d_V, ctx->d_inst, n, fs);
+               ctx->d_V, ctx->d_inst, n, fs, nullptr, gather);
 }
 
 wh_status launch_steps(wh_ctx *ctx, int forcing) {
@@ -788,11 +887,17 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
                      fs);
   };
   bcg(Wa, 0);
+  const bool fold = folds_gather(ctx);
+  const GatherArgs ga = gather_args(ctx);
   for (int n = 0; n < ctx->maxM; ++n) {
     void *cur = (n & 1) ? Wb : Wa;
     void *oth = (n & 1) ? Wa : Wb;
-    march_step(ctx, n, cur, oth, fs);
-    bcg(oth, n + 1);
+    if (fold) {
+      march_step(ctx, n, cur, oth, fs, &ga);  // level n + 1's ghosts and receivers included
+    } else {
+      march_step(ctx, n, cur, oth, fs);
+      bcg(oth, n + 1);
+    }
   }
   return WH_OK;
 }
@@ -800,7 +905,9 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
 wh_status build_graph(wh_ctx *ctx, int forcing) {
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  set_pdl(true);
   wh_status st = launch_steps(ctx, forcing);
+  set_pdl(false);
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
   if (st != WH_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -891,9 +998,11 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   CK(cudaGetLastError());
   if (ctx->set[ctx->active].tma)  // tickets start at zero (the kernel also leaves them so)
     CK(cudaMemsetAsync(ctx->d_err + 1, 0, 2 * sizeof(int), ctx->stream));
+  if (folds_gather(ctx))  // the tiles' step flags start at zero in every iteration
+    CK(cudaMemsetAsync(ctx->d_tile_done, 0, ctx->htiles.size() * sizeof(int32_t), ctx->stream));
   CK(cudaGraphLaunch(ctx->set[ctx->active].gexec[forcing], ctx->stream));
-  if (ctx->set[ctx->active].tma) {
-    // the TMA stages' bounded waits leave a sticky flag; reported by a later call
+  if (ctx->set[ctx->active].tma || folds_gather(ctx)) {
+    // bounded waits in the graph's kernels leave a sticky flag; reported by a later call
     CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaEventRecord(ctx->err_ev, ctx->stream));
     ctx->err_pending = true;
@@ -902,7 +1011,8 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   launch_finish(is_fp32(ctx), (unsigned)nc, ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->d_V,
                 ctx->d_Wa, ctx->d_Wb, ctx->d_inst, vout, ctx->ncompact);
   CK(cudaGetLastError());
-  ctx->launches += 2 + 2 * (int64_t)ctx->maxM + 1;
+  // init, level 0's ghost rules + interpolation, the steps, output
+  ctx->launches += 3 + (folds_gather(ctx) ? 1 : 2) * (int64_t)ctx->maxM;
   return WH_OK;
 }
 
@@ -2234,12 +2344,22 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
   const int nblocks = std::min(ntiles, ctx->march_blocks);
   const int blk = 256;
   const int ng = (int)ctx->hgrids.size();
+  const bool fold = folds_gather(ctx);
+  const GatherArgs ga = gather_args(ctx);
   // four bursts of `reps` back-to-back launches, each captured in a graph
   auto burst = [&](int kind) {
     for (int r = 0; r < reps; ++r) {
       void *cur = (r & 1) ? ctx->d_Wb : ctx->d_Wa, *oth = (r & 1) ? ctx->d_Wa : ctx->d_Wb;
-      if (kind == 0)
+      if (kind == 0 && fold) {
+        // the folded launch, as in the iteration: steps 1, 2, ... so that the tiles' step
+        // flags increase (cleared at the start and whenever the steps wrap)
+        const int nn = 1 + r % std::max(ctx->maxM - 2, 1);
+        if (nn == 1)
+          (void)cudaMemsetAsync(ctx->d_tile_done, 0, ctx->htiles.size() * sizeof(int32_t), s);
+        march_step(ctx, nn, cur, oth, 1.0, &ga);
+      } else if (kind == 0) {
         march_step(ctx, 1 + (r & 1), cur, oth, 1.0);
+      }
       else if (kind == 1 && bg_blocks)
         launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx,
                          ctx->d_dw, ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, oth, ctx->d_F,
@@ -2258,7 +2378,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int per_iter[4] = {ctx->maxM, bg_blocks ? ctx->maxM + 1 : 0, 1, 1};
+  const int per_iter[4] = {ctx->maxM, bg_blocks ? (fold ? 1 : ctx->maxM + 1) : 0, 1, 1};
   for (int kind = 0; kind < 4; ++kind) {
     ms[kind] = 0.0;
     counts[kind] = per_iter[kind];

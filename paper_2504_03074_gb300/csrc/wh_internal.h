@@ -87,6 +87,24 @@ struct GridBarrier {
   unsigned long long ticket[16];  // dataflow tickets: ticket k is step k / ntiles, tile k % ntiles
 };
 
+// The ghost rules and interpolation of level n + 1 folded into the march launch of step n
+// (nunits = 0: not folded).  Unit u (as a block of the separate kernel) runs after the tiles
+// udep_tile[udep_off[u] .. udep_off[u+1]) have written level n + 1 (tile_done >= n + 1);
+// tiles whose Tile::pad_ is 1 signal.  tile_done is zero at the start of each iteration.
+struct GatherArgs {
+  const BcItem *bc;
+  const int32_t *didx;
+  const double *dw;
+  const int64_t *ridx;
+  const int32_t *rinst;
+  const int64_t *udep_off;
+  const int32_t *udep_tile;
+  int32_t *tile_done;
+  int *err;
+  unsigned long long spin_limit;
+  int nbc, bc_blocks, nunits, nrecv;
+};
+
 // Everything the persistent iteration kernel reads (device pointers, per-step tables).
 struct IterArgs {
   const DevGrid *grids;
@@ -126,10 +144,14 @@ struct IterArgs {
 
 // Host launchers (wh_kernels.cu).  T is double unless fp32 is set; pointers typed void
 // carry T arrays.
+// While on, launches of the iteration graph's kernels (march, TMA march, ghost rules +
+// interpolation) made from this thread ask for programmatic dependent launch.
+void set_pdl(bool on);
 void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
                   void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
-                  int n, double fs, const void *Wprev = nullptr);  // W^{n-1}: Wout if null
+                  int n, double fs, const void *Wprev = nullptr,  // W^{n-1}: Wout if null
+                  const GatherArgs *gather = nullptr);            // fold level n + 1's gather
 int march_blocks_per_sm(bool fp32, int order);
 // TMA-staged march, one launch per step: each block walks a strided share of the fast tiles
 // (double-buffered TMA boxes on mbarriers, bounded waits), then takes general tiles by

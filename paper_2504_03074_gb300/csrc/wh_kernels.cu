@@ -56,6 +56,14 @@ __device__ __forceinline__ double to_f64(float x) {
   return (double)x;
 }
 
+// Programmatic dependent launch.  Kernels of the iteration graph start with pdl_wait: the
+// previous kernel in the stream has completed and its writes are visible (a no-op when the
+// launch did not ask for programmatic serialization).  The next kernel is released as this
+// grid's blocks exit (no early trigger: triggering at kernel start, which lets the next
+// grids' blocks sit in SM slots while they wait, measured 5-12% slower), which hides the
+// launch gap between the graph's kernels (measured +2% FP64, +3% FP32 on the disk workload).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Constant cross weight k and forcing factor of step n in the march precision.  The FP32
 // values are rounded once on the host: converting FP64 to FP32 in the kernel is an FP64-pipe
 // instruction on this part, several times the cost of a DFMA, and was most of that pipe's
@@ -171,15 +179,23 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
 //   type 2, Dirichlet order 4: c^2 (a_nn D_nn + b_n D_n) W_b = f_b cos(omega_e t) and
 //   D+^5 G2 = 0, solved as G1 = (F - A2(-30U0 + 16U1 - U2) - B1(8U1 - U2) + (A2 - B1) E) /
 //   (11 A2 - 3 B1), G2 = 5 G1 + E with E = -10U0 + 10U1 - 5U2 + U3.
-template <typename T>
+// Load of a state value: through L1, or (CG) from L2 only, for values another SM wrote
+// during the same launch.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_state(const T *p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
+template <typename T, bool CG = false>
 __device__ __forceinline__ void bc_item(const BcItem &it, T *W, const T *__restrict__ F,
                                         double fcos) {
-  const double U0 = to_f64(W[it.u[0]]), U1 = to_f64(W[it.u[1]]);
+  const double U0 = to_f64(ld_state<CG>(W + it.u[0])), U1 = to_f64(ld_state<CG>(W + it.u[1]));
   if (it.type == 0) {
     W[it.g[0]] = (T)U1;
     return;
   }
-  const double U2 = to_f64(W[it.u[2]]), U3 = to_f64(W[it.u[3]]);
+  const double U2 = to_f64(ld_state<CG>(W + it.u[2])), U3 = to_f64(ld_state<CG>(W + it.u[3]));
   const double E = -10.0 * U0 + 10.0 * U1 - 5.0 * U2 + U3;
   double G1;
   if (it.type == 1) {
@@ -196,7 +212,7 @@ __device__ __forceinline__ void bc_item(const BcItem &it, T *W, const T *__restr
 // Warp-cooperative gather of receiver r: LANES lanes split its (p+1)^2 donors and combine
 // their partial sums with xor shuffles.  Every lane of the warp must call this (live may be
 // false); lane 0 of the group stores the value.
-template <typename T, int ORDER>
+template <typename T, int ORDER, bool CG = false>
 __device__ __forceinline__ void gather_group(int r, int lane, bool live,
                                              const int32_t *__restrict__ didx,
                                              const double *__restrict__ dw,
@@ -208,7 +224,7 @@ __device__ __forceinline__ void gather_group(int r, int lane, bool live,
     const int32_t *di = didx + (int64_t)r * ND;
     const double *wi = dw + (int64_t)r * ND;
 #pragma unroll
-    for (int d = lane; d < ND; d += LANES) s = fma(wi[d], to_f64(W[di[d]]), s);
+    for (int d = lane; d < ND; d += LANES) s = fma(wi[d], to_f64(ld_state<CG>(W + di[d])), s);
   }
 #pragma unroll
   for (int off = LANES / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LANES);
@@ -219,66 +235,133 @@ __device__ __forceinline__ void gather_group(int r, int lane, bool live,
 // Graph path: one launch per phase.
 // ---------------------------------------------------------------------------------
 // Step n of every active instance with n < M (FIRST: n = 0).
+// Work unit u of the ghost rules (units [0, bc_blocks): 256 items each) and interpolation
+// (the remaining units: 256 / lanes receivers each) at one level; tid in [0, 256).
+template <typename T, int ORDER, bool CG>
+__device__ __forceinline__ void gather_unit(int u, int tid, const BcItem *__restrict__ bc,
+                                            int nbc, int bc_blocks,
+                                            const int32_t *__restrict__ didx,
+                                            const double *__restrict__ dw,
+                                            const int64_t *__restrict__ ridx,
+                                            const int32_t *__restrict__ rinst, int nrecv, T *W,
+                                            const T *__restrict__ F,
+                                            const InstDev *__restrict__ inst, int level,
+                                            double fs) {
+  if (u < bc_blocks) {
+    const int k = u * 256 + tid;
+    if (k >= nbc) return;
+    const BcItem it = bc[k];
+    const InstDev &I = inst[it.inst];
+    if (I.active && level <= I.M) bc_item<T, CG>(it, W, F, fs * I.cosn[level]);
+    return;
+  }
+  constexpr int LANES = ORDER == 4 ? 8 : 4;
+  const int r = ((u - bc_blocks) * 256 + tid) / LANES;
+  bool live = r < nrecv;
+  if (live) {
+    const InstDev &I = inst[rinst[r]];
+    live = I.active && level <= I.M;
+  }
+  gather_group<T, ORDER, CG>(r, tid % LANES, live, didx, dw, ridx, W);
+}
+
 template <typename T, int ORDER, bool FIRST>
 __global__ void __launch_bounds__(kTileX *kTileY)
     march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
                  const int8_t *__restrict__ mask, const T *Wn, const T *Wprev, T *Wout,
                  const T *__restrict__ F, const T *__restrict__ Wt, double *V,
-                 const InstDev *__restrict__ inst, int n, double fs) {
+                 const InstDev *__restrict__ inst, int n, double fs, GatherArgs ga) {
+  pdl_wait();
+  const int tid = (int)threadIdx.y * kTileX + (int)threadIdx.x;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const Tile t = tiles[tile];
     const DevGrid &G = grids[t.grid];
     const InstDev &I = inst[G.inst];
-    if (!I.active || n >= I.M) continue;
-    const T fc = step_fc<T>(I, n, fs, FIRST);
-    const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
     const int i = t.i0 + (int)threadIdx.x;
-    if (i >= G.n0) continue;
-    if (sizeof(T) == 4 && G.stencil == kConstCross && !G.per0 && !G.per1) {
-      // FP32 march, constant weights, no wrap: the ghost layers (width order/2) hold every
-      // neighbour, so neighbour addresses are fixed offsets from the point (same arithmetic,
-      // in the same order, as march_point).  Measured on the disk workload: +20% for the
-      // latency-bound FP32 march, -5% for the ALU-bound FP64 march, which keeps march_point.
-      const int64_t pitch = G.pitch, n1 = G.n1;
-      const int64_t b0 = G.base + (int64_t)G.g1 * pitch + G.g0 + i;
-      const T c0 = grid_w<T>(G, 0), x1 = grid_w<T>(G, 1), x2 = grid_w<T>(G, 2);
-      const T y1 = grid_w<T>(G, 3), y2 = grid_w<T>(G, 4);
+    if (I.active && n < I.M && i < G.n0) {
+      const T fc = step_fc<T>(I, n, fs, FIRST);
+      const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
+      if (sizeof(T) == 4 && G.stencil == kConstCross && !G.per0 && !G.per1) {
+        // FP32 march, constant weights, no wrap: the ghost layers (width order/2) hold every
+        // neighbour, so neighbour addresses are fixed offsets from the point (same
+        // arithmetic, in the same order, as march_point).  Measured on the disk workload:
+        // +20% for the latency-bound FP32 march, -5% for the ALU-bound FP64 march, which
+        // keeps march_point.
+        const int64_t pitch = G.pitch, n1 = G.n1;
+        const int64_t b0 = G.base + (int64_t)G.g1 * pitch + G.g0 + i;
+        const T c0 = grid_w<T>(G, 0), x1 = grid_w<T>(G, 1), x2 = grid_w<T>(G, 2);
+        const T y1 = grid_w<T>(G, 3), y2 = grid_w<T>(G, 4);
 #pragma unroll
-      for (int m = 0; m < kPY; ++m) {
-        const int j = t.j0 + (int)threadIdx.y + m * kTileY;
-        if (j >= n1) continue;
-        const int64_t p = b0 + j * pitch;
-        const int8_t mk = mask[p];
-        if (mk == 2) {
-          V[p] = fma(wf_cur, to_f64(Wn[p]), V[p]);
-          continue;
+        for (int m = 0; m < kPY; ++m) {
+          const int j = t.j0 + (int)threadIdx.y + m * kTileY;
+          if (j >= n1) continue;
+          const int64_t p = b0 + j * pitch;
+          const int8_t mk = mask[p];
+          if (mk == 2) {
+            V[p] = fma(wf_cur, to_f64(Wn[p]), V[p]);
+            continue;
+          }
+          if (mk != 1) continue;
+          T a = FIRST ? c0 * Wn[p] : fma(c0, Wn[p], -Wprev[p]);
+          a = fma(x1, Wn[p - 1], a);
+          a = fma(x1, Wn[p + 1], a);
+          a = fma(y1, Wn[p - pitch], a);
+          a = fma(y1, Wn[p + pitch], a);
+          if (ORDER == 4) {
+            a = fma(x2, Wn[p - 2], a);
+            a = fma(x2, Wn[p + 2], a);
+            a = fma(y2, Wn[p - 2 * pitch], a);
+            a = fma(y2, Wn[p + 2 * pitch], a);
+          }
+          if (FIRST) a *= (T)0.5;
+          a = fma(-fc, F[p], a);
+          Wout[p] = a;
+          V[p] = fma(wf_new, to_f64(a), V[p]);
         }
-        if (mk != 1) continue;
-        T a = FIRST ? c0 * Wn[p] : fma(c0, Wn[p], -Wprev[p]);
-        a = fma(x1, Wn[p - 1], a);
-        a = fma(x1, Wn[p + 1], a);
-        a = fma(y1, Wn[p - pitch], a);
-        a = fma(y1, Wn[p + pitch], a);
-        if (ORDER == 4) {
-          a = fma(x2, Wn[p - 2], a);
-          a = fma(x2, Wn[p + 2], a);
-          a = fma(y2, Wn[p - 2 * pitch], a);
-          a = fma(y2, Wn[p + 2 * pitch], a);
+      } else {
+#pragma unroll
+        for (int m = 0; m < kPY; ++m) {
+          const int j = t.j0 + (int)threadIdx.y + m * kTileY;
+          if (j < G.n1)
+            march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wprev, Wout, F, Wt, V, fc, wf_new,
+                                         wf_cur);
         }
-        if (FIRST) a *= (T)0.5;
-        a = fma(-fc, F[p], a);
-        Wout[p] = a;
-        V[p] = fma(wf_new, to_f64(a), V[p]);
       }
-      continue;
     }
-#pragma unroll
-    for (int m = 0; m < kPY; ++m) {
-      const int j = t.j0 + (int)threadIdx.y + m * kTileY;
-      if (j < G.n1)
-        march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wprev, Wout, F, Wt, V, fc, wf_new,
-                                     wf_cur);
+    if (ga.nunits && t.pad_) {  // a gather unit reads this tile's level n + 1: signal it
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicExch(&ga.tile_done[tile], n + 1);
+      }
     }
+  }
+  if (!ga.nunits) return;
+  // The folded ghost rules and interpolation of level n + 1: unit u on block nb - 1 - u (the
+  // blocks with the fewest march tiles), after its source tiles have signalled.  Blocks
+  // only wait here, after their own march tiles, and the grid is one resident wave, so
+  // every awaited tile is computed; each wait is bounded all the same.
+  __shared__ int s_fail;
+  for (int u = (int)gridDim.x - 1 - (int)blockIdx.x; u < ga.nunits; u += gridDim.x) {
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int64_t e = ga.udep_off[u] + tid; e < ga.udep_off[u + 1]; e += kTileX * kTileY) {
+      volatile int *flag = (volatile int *)&ga.tile_done[ga.udep_tile[e]];
+      unsigned long long it = 0;
+      while (*flag < n + 1) {
+        if (++it > ga.spin_limit) {
+          atomicExch(ga.err, 1);
+          s_fail = 1;
+          break;
+        }
+        if (it > 64) __nanosleep(32);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_fail) return;
+    gather_unit<T, ORDER, true>(u, tid, ga.bc, ga.nbc, ga.bc_blocks, ga.didx, ga.dw, ga.ridx,
+                                ga.rinst, ga.nrecv, Wout, F, inst, n + 1, fs);
   }
 }
 
@@ -374,6 +457,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                      unsigned long long spin_limit) {
   using S = TmaStage<T, ORDER>;
   constexpr int R = ORDER / 2;
+  pdl_wait();
   const T *Wn = (n & 1) ? Wb : Wa;
   T *Wout = (n & 1) ? Wa : Wb;
   extern __shared__ unsigned char smem_raw[];
@@ -545,23 +629,9 @@ __global__ void __launch_bounds__(256)
                      const int64_t *__restrict__ ridx, const int32_t *__restrict__ rinst,
                      int nrecv, T *W, const T *__restrict__ F,
                      const InstDev *__restrict__ inst, int level, double fs) {
-  if ((int)blockIdx.x < bc_blocks) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nbc) return;
-    const BcItem it = bc[k];
-    const InstDev &I = inst[it.inst];
-    if (I.active && level <= I.M) bc_item<T>(it, W, F, fs * I.cosn[level]);
-    return;
-  }
-  constexpr int LANES = ORDER == 4 ? 8 : 4;
-  const int gtid = (blockIdx.x - bc_blocks) * blockDim.x + threadIdx.x;
-  const int r = gtid / LANES;
-  bool live = r < nrecv;
-  if (live) {
-    const InstDev &I = inst[rinst[r]];
-    live = I.active && level <= I.M;
-  }
-  gather_group<T, ORDER>(r, threadIdx.x % LANES, live, didx, dw, ridx, W);
+  pdl_wait();
+  gather_unit<T, ORDER, false>((int)blockIdx.x, (int)threadIdx.x, bc, nbc, bc_blocks, didx, dw,
+                               ridx, rinst, nrecv, W, F, inst, level, fs);
 }
 
 // W^0 = v on discretization and interpolation points, 0 elsewhere (ghosts included);
@@ -1370,16 +1440,43 @@ __global__ void gemv_acc(const double *__restrict__ X, int64_t ldx, int nv,
 // Host launchers (the only entry points the host code uses).
 // ---------------------------------------------------------------------------------
 
+// Launches of the iteration graph's kernels ask for programmatic serialization while
+// set_pdl(true) is in effect on this thread (the graph capture).
+static thread_local bool t_pdl = false;
+void set_pdl(bool on) { t_pdl = on; }
+
+template <typename... KArgs, typename... Args>
+static void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args... args) {
+  if (!t_pdl) {
+    kernel<<<grid, block, smem, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 void launch_march(bool fp32, int order, bool first, int nblocks, int ntiles, cudaStream_t s,
                   const DevGrid *grids, const Tile *tiles, const int8_t *mask, const void *Wn,
                   void *Wout, const void *F, const void *Wt, double *V, const InstDev *inst,
-                  int n, double fs, const void *Wprev) {
+                  int n, double fs, const void *Wprev, const GatherArgs *gather) {
   const dim3 tb(kTileX, kTileY);
   if (!Wprev) Wprev = Wout;
+  GatherArgs ga{};
+  if (gather) ga = *gather;
 #define WH_MARCH(T, O, FI)                                                                 \
-  march_kernel<T, O, FI><<<nblocks, tb, 0, s>>>(grids, tiles, ntiles, mask, (const T *)Wn, \
-                                                (const T *)Wprev, (T *)Wout, (const T *)F, \
-                                                (const T *)Wt, V, inst, n, fs)
+  launch_k(march_kernel<T, O, FI>, dim3(nblocks), tb, 0, s, grids, tiles, ntiles, mask,    \
+           (const T *)Wn, (const T *)Wprev, (T *)Wout, (const T *)F, (const T *)Wt, V, inst, \
+           n, fs, ga)
   if (fp32) {
     if (order == 4) { if (first) WH_MARCH(float, 4, true); else WH_MARCH(float, 4, false); }
     else            { if (first) WH_MARCH(float, 2, true); else WH_MARCH(float, 2, false); }
@@ -1439,9 +1536,9 @@ void launch_march_tma(bool fp32, int order, bool first, int nblocks, cudaStream_
                       double fs, int *ctl, unsigned long long spin_limit) {
   const dim3 tb(kTileX, kTileY);
 #define WH_TMA(T, O, FI)                                                                       \
-  march_tma_kernel<T, O, FI><<<nblocks, tb, TmaStage<T, O>::kSmem, s>>>(                       \
-      grids, ftiles, nfast, maps, gtiles, ngen, mask, (T *)Wa, (T *)Wb, (const T *)F,          \
-      (const T *)Wt, V, inst, n, fs, ctl, spin_limit)
+  launch_k(march_tma_kernel<T, O, FI>, dim3(nblocks), tb, TmaStage<T, O>::kSmem, s, grids,     \
+           ftiles, nfast, maps, gtiles, ngen, mask, (T *)Wa, (T *)Wb, (const T *)F,            \
+           (const T *)Wt, V, inst, n, fs, ctl, spin_limit)
   if (fp32) {
     if (order == 4) { if (first) WH_TMA(float, 4, true); else WH_TMA(float, 4, false); }
     else            { if (first) WH_TMA(float, 2, true); else WH_TMA(float, 2, false); }
@@ -1456,9 +1553,9 @@ void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const Bc
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
                       const int64_t *ridx, const int32_t *rinst, int nrecv, void *W,
                       const void *F, const InstDev *inst, int level, double fs) {
-#define WH_BCG(T, O)                                                                   \
-  bc_gather_kernel<T, O><<<blocks, 256, 0, s>>>(bc, nbc, bc_blocks, didx, dw, ridx, rinst, \
-                                                nrecv, (T *)W, (const T *)F, inst, level, fs)
+#define WH_BCG(T, O)                                                                       \
+  launch_k(bc_gather_kernel<T, O>, dim3(blocks), dim3(256), 0, s, bc, nbc, bc_blocks, didx, dw, \
+           ridx, rinst, nrecv, (T *)W, (const T *)F, inst, level, fs)
   if (fp32) { if (order == 4) WH_BCG(float, 4); else WH_BCG(float, 2); }
   else      { if (order == 4) WH_BCG(double, 4); else WH_BCG(double, 2); }
 #undef WH_BCG

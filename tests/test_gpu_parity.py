@@ -108,6 +108,24 @@ def test_full_size_disk_iteration(torch, W, oracle_mod):
     got = gpu_iterate(torch, s, v, True)
     ref = orc.iterate(v, True)
     assert rel_err(got, ref, orc.active()) <= TOL
+    # few ghost-rule/interpolation units next to the march blocks: they are folded into the
+    # march launches (init, level 0's ghost rules + interpolation, M steps, output)
+    assert s.last_launch_count() == ti.M + 3
+
+
+def test_folded_gather_order2(torch, W, oracle_mod):
+    """Order 2 with the ghost rules and interpolation folded into the march launches
+    (Neumann cylinder, 256^2 background + 512x16 annulus)."""
+    prob = G.disk_problem(nb=256, nth=512, nr=16, order=2, omega=10.0, seed=4)
+    orc = oracle_mod.Oracle(prob)
+    s = W.Solver(prob)
+    ti = s.prepare()
+    v = G.random_state(prob, 12)
+    for forcing in (True, False):
+        got = gpu_iterate(torch, s, v, forcing)
+        ref = orc.iterate(v, forcing)
+        assert rel_err(got, ref, orc.active()) <= TOL
+    assert s.last_launch_count() == ti.M + 3
 
 
 def test_determinism_and_zero(torch, W):
@@ -123,7 +141,9 @@ def test_determinism_and_zero(torch, W):
     # host-buffer path equals the device path
     c = s.iterate_host(v, True)
     assert np.array_equal(a, c)
-    assert s.last_launch_count() == 2 * s.info.M + 3
+    # init, level 0's ghost rules + interpolation, the steps (M march launches folding in
+    # the next level's ghost rules and interpolation, or M pairs), output
+    assert s.last_launch_count() in (s.info.M + 3, 2 * s.info.M + 3)
     p = W.Solver(prob, launch_mode=W.PERSISTENT)
     p.prepare()
     d = gpu_iterate(torch, p, v, True)
