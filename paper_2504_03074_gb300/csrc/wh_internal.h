@@ -101,6 +101,9 @@ struct GatherArgs {
   const int32_t *udep_tile;
   int32_t *tile_done;
   int *err;
+  // march tiles by ticket (non-null: ctl[1] next ticket, ctl[2] blocks done; the last
+  // block out resets both) instead of the fixed grid stride
+  int *ctl;
   unsigned long long spin_limit;
   int nbc, bc_blocks, nunits, nrecv;
 };

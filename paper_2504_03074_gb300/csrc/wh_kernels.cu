@@ -273,7 +273,15 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                  const InstDev *__restrict__ inst, int n, double fs, GatherArgs ga) {
   pdl_wait();
   const int tid = (int)threadIdx.y * kTileX + (int)threadIdx.x;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // tiles by ticket when ga.ctl is set (the next ticket is fetched while a tile is computed,
+  // and blocks that finish early take more tiles), else by grid stride
+  __shared__ int s_tile;
+  if (ga.ctl && tid == 0) s_tile = atomicAdd(&ga.ctl[1], 1);
+  __syncthreads();
+  int tile = ga.ctl ? s_tile : (int)blockIdx.x;
+  __syncthreads();
+  while (tile < ntiles) {
+    if (ga.ctl && tid == 0) s_tile = atomicAdd(&ga.ctl[1], 1);
     const Tile t = tiles[tile];
     const DevGrid &G = grids[t.grid];
     const InstDev &I = inst[G.inst];
@@ -335,6 +343,17 @@ __global__ void __launch_bounds__(kTileX *kTileY)
         atomicExch(&ga.tile_done[tile], n + 1);
       }
     }
+    if (ga.ctl) {
+      __syncthreads();
+      tile = s_tile;
+      __syncthreads();
+    } else {
+      tile += gridDim.x;
+    }
+  }
+  if (ga.ctl && tid == 0 && atomicAdd(&ga.ctl[2], 1) == (int)gridDim.x - 1) {
+    atomicExch(&ga.ctl[1], 0);  // last block out: tickets start at zero in the next launch
+    atomicExch(&ga.ctl[2], 0);
   }
   if (!ga.nunits) return;
   // The folded ghost rules and interpolation of level n + 1: unit u on block nb - 1 - u (the
