@@ -259,9 +259,10 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
         sb = WH.Solver(bp, stream=stream, precision=prec)
         infos = sb.prepare()
         lups = sum(t.n_active * t.M for t in infos)
+        tuned = sb.autotune(reps=1)  # launch layout picked by timing each candidate (untimed)
         tb = time_iterations(WH, torch, sb, bp.n_total, stream, flush, 2, warm=1)
         res[f"batched_{name}"] = {"value": lups / tb / 1e9, "unit": "GLUP/s",
-                                  "s_per_iteration": tb}
+                                  "s_per_iteration": tb, "layout": tuned}
         sb.close()
         del sb
     # plain FP64, one instance at a time, on 8 seeded instances (GLUP/s by LUP count)

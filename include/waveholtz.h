@@ -257,6 +257,43 @@ wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, 
  * wh_prepare. */
 wh_status wh_set_coefficient(wh_ctx *ctx, int32_t grid_id, const double *c2);
 
+/* How an iteration is laid out in launches (none of it changes the results beyond rounding
+ * order; every configuration is tested against the oracle).  -1 in a field: the library's
+ * own choice, which depends on the problem (see each field).
+ *   launch_mode   WH_LAUNCH_GRAPH or WH_LAUNCH_PERSISTENT.
+ *   fold_gather   graph path: 1 = each march launch also does the next level's ghost rules
+ *                 and interpolation (library: when their work units are at most half the
+ *                 march blocks); 0 = a separate kernel after each march launch.
+ *   tile_tickets  graph path without folding: 1 = march tiles by atomic ticket (library),
+ *                 0 = by fixed grid stride.
+ *   tma           FP32 march sets: 1 = TMA-staged march for constant-weight grids (library,
+ *                 when such grids exist), 0 = the plain march kernel.
+ *   pdl           graph path: 1 = the graph's kernels use programmatic dependent launch
+ *                 (library), 0 = plain stream order.
+ *   ms_per_iteration, candidates: filled by wh_autotune. */
+typedef struct {
+  int32_t launch_mode;
+  int32_t fold_gather;
+  int32_t tile_tickets;
+  int32_t tma;
+  int32_t pdl;
+  double ms_per_iteration;
+  int32_t candidates;
+} wh_tuning;
+
+/* Fix the launch layout (fields of -1 leave the library's choice; launch_mode -1 keeps the
+ * current mode).  Takes effect at the next iteration. */
+wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *tuning);
+
+/* Autotuner: after wh_prepare, times `reps` forced WaveHoltz iterations (after one untimed)
+ * of every valid launch layout on the prepared problem — persistent; graph with the gather
+ * folded; graph with a separate gather and tiles by ticket or by stride; for FP32 contexts
+ * also with and without the TMA-staged march; each graph layout with and without
+ * programmatic dependent launch — keeps the fastest, and reports it (resolved
+ * to 0/1 values) with its time and the number of layouts timed in *out (host, may be NULL).
+ * Uses the context's working vectors only.  Synchronises. */
+wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out);
+
 /* FP64 inner product <x, y> over n entries of two DEVICE vectors (the GMRES reduction:
  * warp-shuffle partial sums, then one deterministic pass).  *out is a host scalar.  n = 0
  * gives 0 (x, y may then be NULL). */

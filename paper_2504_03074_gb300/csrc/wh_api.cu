@@ -72,6 +72,8 @@ struct wh_ctx {
   std::vector<int32_t> fast_grids;  // grid of each map slot
   Tile *d_ftiles = nullptr, *d_gtiles = nullptr;
   int *d_err = nullptr;  // TMA march control: [0] sticky error flag, [1] ticket, [2] blocks done
+  // launch layout fixed by wh_set_tuning / wh_autotune (-1: the library's choice)
+  int tune_fold = -1, tune_tickets = -1, tune_tma = -1, tune_pdl = -1;
   // ghost rules + interpolation folded into the march launch (march_kernel sets)
   int nunits = 0;
   std::vector<int64_t> udep_off;
@@ -386,6 +388,8 @@ wh_status build_layout(wh_ctx *ctx) {
     }
     ctx->htiles.swap(mixed);
   }
+  // the TMA-staged march keeps this interleaved order (grids mixed tile by tile)
+  const std::vector<Tile> mixed_tiles = ctx->htiles;
   ctx->total = off;
   ctx->ncompact = coff;
   ctx->nactive = nact;
@@ -597,7 +601,7 @@ wh_status build_layout(wh_ctx *ctx) {
         ctx->fast_grids.push_back((int32_t)g);
       }
     }
-    for (const Tile &t : ctx->htiles) {
+    for (const Tile &t : mixed_tiles) {
       if (slot[t.grid] >= 0 && t.i0 % 32 == 0) {
         Tile f = t;
         f.pad_ = slot[t.grid];
@@ -821,10 +825,16 @@ wh_status build_layout(wh_ctx *ctx) {
 // their work units are few next to the march blocks: each block then runs at most one unit
 // after its tiles (disk workload: 235 units, 608 blocks, +6%).  With many units (a batch
 // of instances) the separate, fully parallel kernel is faster (16 instances: folding -12%).
+bool uses_tma(const wh_ctx *ctx) { return ctx->set[ctx->active].tma && ctx->tune_tma != 0; }
+
 bool folds_gather(const wh_ctx *ctx) {
+  if (uses_tma(ctx) || ctx->nunits == 0) return false;
+  if (ctx->tune_fold >= 0) return ctx->tune_fold != 0;
   const int nb = std::min((int)ctx->htiles.size(), ctx->march_blocks);
-  return !ctx->set[ctx->active].tma && ctx->nunits > 0 && 2 * ctx->nunits <= nb;
+  return 2 * ctx->nunits <= nb;
 }
+
+bool tile_tickets(const wh_ctx *ctx) { return ctx->tune_tickets != 0; }
 
 GatherArgs gather_args(wh_ctx *ctx) {
   GatherArgs ga{};
@@ -856,7 +866,7 @@ void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs,
                 const GatherArgs *gather = nullptr) {
   const MarchSet &S = ctx->set[ctx->active];
   const int order = ctx->opt.order;
-  if (S.tma) {
+  if (uses_tma(ctx)) {
     const int nf = (int)ctx->hftiles.size(), ngn = (int)ctx->hgtiles.size();
     launch_march_tma(S.fp32, order, n == 0, std::min(S.tma_blocks, nf + ngn), ctx->stream,
                      ctx->d_grids, ctx->d_ftiles, nf, S.maps, ctx->d_gtiles, ngn, ctx->d_mask,
@@ -900,7 +910,7 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
     if (fold) {
       march_step(ctx, n, cur, oth, fs, &ga);  // level n + 1's ghosts and receivers included
     } else {
-      march_step(ctx, n, cur, oth, fs, &ga_tiles);
+      march_step(ctx, n, cur, oth, fs, tile_tickets(ctx) ? &ga_tiles : nullptr);
       bcg(oth, n + 1);
     }
   }
@@ -910,7 +920,7 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
 wh_status build_graph(wh_ctx *ctx, int forcing) {
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  set_pdl(true);
+  set_pdl(ctx->tune_pdl != 0);
   wh_status st = launch_steps(ctx, forcing);
   set_pdl(false);
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
@@ -1006,7 +1016,7 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   if (folds_gather(ctx))  // the tiles' step flags start at zero in every iteration
     CK(cudaMemsetAsync(ctx->d_tile_done, 0, ctx->htiles.size() * sizeof(int32_t), ctx->stream));
   CK(cudaGraphLaunch(ctx->set[ctx->active].gexec[forcing], ctx->stream));
-  if (ctx->set[ctx->active].tma || folds_gather(ctx)) {
+  if (uses_tma(ctx) || folds_gather(ctx)) {
     // bounded waits in the graph's kernels leave a sticky flag; reported by a later call
     CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaEventRecord(ctx->err_ev, ctx->stream));
@@ -2334,6 +2344,106 @@ wh_status wh_set_coefficient(wh_ctx *ctx, int32_t gid, const double *c2) {
   return WH_OK;
 }
 
+wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *t) {
+  if (!ctx || !t) return fail(ctx, WH_ERR_ARG, "bad wh_set_tuning arguments");
+  auto tri = [](int32_t v) { return v >= -1 && v <= 1; };
+  if (!tri(t->fold_gather) || !tri(t->tile_tickets) || !tri(t->tma) || !tri(t->pdl) ||
+      (t->launch_mode != -1 && t->launch_mode != WH_LAUNCH_GRAPH &&
+       t->launch_mode != WH_LAUNCH_PERSISTENT))
+    return fail(ctx, WH_ERR_ARG, "tuning fields must be -1, 0 or 1 (launch_mode: -1 or a mode)");
+  if (t->launch_mode == WH_LAUNCH_PERSISTENT && ctx->prepared && ctx->iter_blocks < 1)
+    return fail(ctx, WH_ERR_CUDA, "the persistent kernel cannot be resident on this device");
+  ctx->tune_fold = t->fold_gather;
+  ctx->tune_tickets = t->tile_tickets;
+  ctx->tune_tma = t->tma;
+  ctx->tune_pdl = t->pdl;
+  if (t->launch_mode != -1) ctx->persistent = t->launch_mode == WH_LAUNCH_PERSISTENT;
+  drop_graphs(ctx);
+  return WH_OK;
+}
+
+wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out) {
+  if (!ctx || reps < 1 || reps > 1000) return fail(ctx, WH_ERR_ARG, "bad wh_autotune arguments");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  wh_status st;
+  const int64_t n = ctx->ncompact;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
+  double *vin = ctx->d_work, *vout = ctx->d_work + n;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(vin, 0, n * sizeof(double), s));
+  struct Cand {
+    bool persistent;
+    int fold, tickets, tma, pdl;
+  };
+  std::vector<Cand> cands;
+  const bool has_tma = ctx->set[ctx->active].tma;
+  for (int pdl = 1; pdl >= 0; --pdl)
+    for (int tma = has_tma ? 1 : 0; tma >= 0; --tma) {
+      if (tma) {
+        cands.push_back({false, 0, 0, 1, pdl});
+        continue;
+      }
+      if (ctx->nunits > 0) cands.push_back({false, 1, 0, 0, pdl});
+      cands.push_back({false, 0, 1, 0, pdl});
+      cands.push_back({false, 0, 0, 0, pdl});
+    }
+  if (ctx->iter_blocks >= 1) cands.push_back({true, 0, 0, has_tma ? 1 : 0, 0});
+  const int sf = ctx->tune_fold, stk = ctx->tune_tickets, stm = ctx->tune_tma;
+  const int spd = ctx->tune_pdl;
+  const bool sp = ctx->persistent;
+  auto apply = [&](const Cand &c) {
+    ctx->tune_fold = c.fold;
+    ctx->tune_tickets = c.tickets;
+    ctx->tune_tma = c.tma;
+    ctx->tune_pdl = c.pdl;
+    ctx->persistent = c.persistent;
+    drop_graphs(ctx);
+  };
+  auto restore = [&](wh_status code) {
+    ctx->tune_fold = sf;
+    ctx->tune_tickets = stk;
+    ctx->tune_tma = stm;
+    ctx->tune_pdl = spd;
+    ctx->persistent = sp;
+    drop_graphs(ctx);
+    return code;
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int ib = -1;
+  for (size_t k = 0; k < cands.size(); ++k) {
+    apply(cands[k]);
+    if ((st = iterate_device(ctx, 1, vin, vout))) break;  // untimed (builds the graph)
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps && !st; ++r) st = iterate_device(ctx, 1, vin, vout);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    if (st || (st = check_timeout(ctx, true))) break;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / reps < best) {
+      best = ms / reps;
+      ib = (int)k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st || ib < 0) return restore(st ? st : fail(ctx, WH_ERR_CUDA, "no layout could be timed"));
+  apply(cands[ib]);
+  if (out) {
+    out->launch_mode = cands[ib].persistent ? WH_LAUNCH_PERSISTENT : WH_LAUNCH_GRAPH;
+    out->fold_gather = cands[ib].fold;
+    out->tile_tickets = cands[ib].tickets;
+    out->tma = cands[ib].tma;
+    out->pdl = cands[ib].pdl;
+    out->ms_per_iteration = best;
+    out->candidates = (int32_t)cands.size();
+  }
+  return WH_OK;
+}
+
 wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts) {
   if (!ctx || !ms || !counts || reps < 1 || reps > 10000)
     return fail(ctx, WH_ERR_ARG, "bad wh_profile_kernels arguments");
@@ -2365,7 +2475,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
           (void)cudaMemsetAsync(ctx->d_tile_done, 0, ctx->htiles.size() * sizeof(int32_t), s);
         march_step(ctx, nn, cur, oth, 1.0, &ga);
       } else if (kind == 0) {
-        march_step(ctx, 1 + (r & 1), cur, oth, 1.0, &ga_tiles);
+        march_step(ctx, 1 + (r & 1), cur, oth, 1.0, tile_tickets(ctx) ? &ga_tiles : nullptr);
       }
       else if (kind == 1 && bg_blocks)
         launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx,

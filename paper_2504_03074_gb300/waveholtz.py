@@ -61,6 +61,15 @@ class TimeInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("launch_mode", C.c_int32), ("fold_gather", C.c_int32),
+                ("tile_tickets", C.c_int32), ("tma", C.c_int32), ("pdl", C.c_int32),
+                ("ms_per_iteration", C.c_double), ("candidates", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("residual", C.c_double),
                 ("seconds", C.c_double), ("n_history", C.c_int32), ("products_fp64", C.c_int32),
@@ -71,7 +80,7 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
-           "wh_set_coefficient"]
+           "wh_set_coefficient", "wh_set_tuning", "wh_autotune"]
 
 
 def lib_path():
@@ -110,6 +119,8 @@ def lib():
     L.wh_adjoint.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32, vp, vp, vp,
                              C.POINTER(Stats)]
     L.wh_set_coefficient.argtypes = [vp, C.c_int32, vp]
+    L.wh_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.wh_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -315,6 +326,22 @@ class Solver:
         self._enter()
         self._check(self.L.wh_dot(self.h, _ptr(x), _ptr(y), x.numel(), C.byref(out)))
         return out.value
+
+    def set_tuning(self, launch_mode=-1, fold_gather=-1, tile_tickets=-1, tma=-1, pdl=-1):
+        """Fix the launch layout (-1: the library's choice); see wh_tuning."""
+        t = Tuning(launch_mode, fold_gather, tile_tickets, tma, pdl, 0.0, 0)
+        self._check(self.L.wh_set_tuning(self.h, C.byref(t)))
+
+    def autotune(self, reps=3):
+        """Time every valid launch layout on the prepared problem and keep the fastest;
+        returns it as a dict (launch_mode, fold_gather, tile_tickets, tma, pdl,
+        ms_per_iteration, candidates)."""
+        t = Tuning()
+        self._enter()
+        status = self.L.wh_autotune(self.h, reps, C.byref(t))
+        self._leave()
+        self._check(status)
+        return t.as_dict()
 
     def profile_kernels(self, reps=50):
         """Average device ms per launch and launches per iteration of each kernel:

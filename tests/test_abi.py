@@ -76,6 +76,26 @@ def test_options_and_create(W):
     L.wh_destroy(None)
 
 
+def test_tuning_validation_on_host(W):
+    """wh_set_tuning checks its fields without touching the device; wh_autotune needs a
+    prepared context."""
+    L = W.lib()
+    opt = W.Options()
+    L.wh_options_default(C.byref(opt))
+    h = C.c_void_p()
+    assert L.wh_create(C.byref(opt), C.byref(h)) == 0
+    ok = W.Tuning(-1, 1, 0, -1, 1, 0.0, 0)
+    assert L.wh_set_tuning(h, C.byref(ok)) == 0
+    for bad in (W.Tuning(-1, 2, 0, 0, 0, 0.0, 0), W.Tuning(-1, 0, -2, 0, 0, 0.0, 0),
+                W.Tuning(7, 0, 0, 0, 0, 0.0, 0), W.Tuning(-1, 0, 0, 0, 3, 0.0, 0)):
+        assert L.wh_set_tuning(h, C.byref(bad)) == -1
+    assert L.wh_set_tuning(h, None) == -1
+    out = W.Tuning()
+    assert L.wh_autotune(h, 3, C.byref(out)) == -3  # WH_ERR_STATE before wh_prepare
+    assert L.wh_autotune(h, 0, C.byref(out)) == -1
+    L.wh_destroy(h)
+
+
 def test_grid_validation_on_host(W):
     L = W.lib()
     h = _ctx(W)

@@ -220,3 +220,30 @@ def test_errors_on_device(torch, W):
     with pytest.raises(W.WHError) as e:
         s.prepare()
     assert e.value.status == -7
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_launch_layout_and_autotune(torch, W, oracle_mod, prec):
+    """Every launch layout (persistent; graph with the gather folded; separate gather with
+    tiles by ticket or by stride; TMA-staged or plain FP32 march) gives the oracle's
+    iteration, and so does the layout the autotuner keeps."""
+    prob = G.disk_problem(nb=256, nth=512, nr=16, order=4, omega=10.0, seed=6)
+    orc = oracle_mod.Oracle(prob)
+    act = orc.active()
+    v = G.random_state(prob, 13)
+    ref = orc.iterate(v, True)
+    tol = TOL if prec == "fp64" else 1e-4
+    s = W.Solver(prob, precision=W.FP64 if prec == "fp64" else W.FP32)
+    s.prepare()
+    layouts = [(W.PERSISTENT, -1, -1, -1, -1), (W.GRAPH, 1, -1, 0, 1), (W.GRAPH, 0, 1, 0, 1),
+               (W.GRAPH, 0, 0, 0, 0), (W.GRAPH, 1, -1, 0, 0)]
+    if prec == "fp32":
+        layouts += [(W.GRAPH, -1, -1, 1, 1), (W.GRAPH, -1, -1, 1, 0)]
+    for lay in layouts:
+        s.set_tuning(*lay)
+        got = gpu_iterate(torch, s, v, True)
+        assert rel_err(got, ref, act) <= tol, lay
+    t = s.autotune(reps=2)
+    assert t["candidates"] >= 7 and t["ms_per_iteration"] > 0
+    got = gpu_iterate(torch, s, v, True)
+    assert rel_err(got, ref, act) <= tol, t
