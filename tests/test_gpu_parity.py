@@ -111,6 +111,12 @@ def test_full_size_disk_iteration(torch, W, oracle_mod):
     # few ghost-rule/interpolation units next to the march blocks: they are folded into the
     # march launches (init, level 0's ghost rules + interpolation, M steps, output)
     assert s.last_launch_count() == ti.M + 3
+    # the FP32-march form at full size (TMA-staged background, annulus by ticket) against the
+    # same oracle iteration, within the form's stated bound
+    s32 = W.Solver(prob, precision=W.FP32)
+    s32.prepare()
+    got32 = gpu_iterate(torch, s32, v, True)
+    assert rel_err(got32, ref, orc.active()) <= 1e-4
 
 
 def test_folded_gather_order2(torch, W, oracle_mod):
