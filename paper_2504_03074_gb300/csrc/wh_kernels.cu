@@ -265,8 +265,11 @@ __device__ __forceinline__ void gather_unit(int u, int tid, const BcItem *__rest
   gather_group<T, ORDER, CG>(r, tid % LANES, live, didx, dw, ridx, W);
 }
 
+// Five resident blocks per SM (registers capped at 48, a few spilled): the FP64 march is
+// FP64-pipe bound but stalls on memory latency, and the fifth block hides more of it than
+// the spills cost (disk workload +7%; six blocks measured slower there).
 template <typename T, int ORDER, bool FIRST>
-__global__ void __launch_bounds__(kTileX *kTileY)
+__global__ void __launch_bounds__(kTileX *kTileY, 5)
     march_kernel(const DevGrid *__restrict__ grids, const Tile *__restrict__ tiles, int ntiles,
                  const int8_t *__restrict__ mask, const T *Wn, const T *Wprev, T *Wout,
                  const T *__restrict__ F, const T *__restrict__ Wt, double *V,
