@@ -345,6 +345,30 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
         bs["plain_fp64"]["solves_per_s"]
     out["batch_solve"] = bs
     del sb_p, sb_probs, uref
+    # roofline probe: one Cartesian grid of 16384^2 points (HBM resident), no interpolation,
+    # orders 2 and 4, FP64 and FP32; the march kernel's device time per launch from a
+    # graph-captured burst (an iteration would be ~11,600 steps here).  Effective bandwidth
+    # counts the compulsory bytes of one update (48 B FP64, 32 B FP32 state + FP64 filter).
+    hbm = float(measured_peaks().get("hbm_gbs", 6793.0))
+    probe = {"workload": "unit square 16384^2, Dirichlet, omega 10, no interpolation",
+             "hbm_peak_gbs": hbm}
+    for order in (2, 4):
+        pp = G.unit_square_problem(16384, order, 10.0, seed=0)
+        for name, prec, bpl in (("fp64", WH.FP64, 48.0), ("fp32", WH.FP32, 32.0)):
+            sp = WH.Solver(pp, stream=stream, precision=prec)
+            tp = sp.prepare()
+            ms = sp.profile_kernels(reps=10)["march"][0]
+            glups = tp.n_active / (ms * 1e-3) / 1e9
+            rec = {"march_us": ms * 1e3, "value": glups, "unit": "GLUP/s",
+                   "effective_gbs": glups * bpl, "hbm_frac": glups * bpl / hbm}
+            if prec == WH.FP64:
+                flop = 12.0 if order == 2 else 18.0
+                rec["fp64_frac"] = glups * flop / 1e3 / FP64_PEAK_TFLOPS
+            probe[f"order{order}_{name}"] = rec
+            sp.close()
+            del sp
+        del pp
+    out["roofline_probe_16384"] = probe
     # time to 1e-6 relative error, 64^2 unit square, order 2, omega 10
     sq = G.unit_square_problem(64, 2, 10.0, seed=0)
     ref = WH.Solver(sq, stream=stream)
@@ -414,8 +438,17 @@ def run_profile_case(case):
     from paper_2504_03074_gb300 import build as B
     B.build()
     from paper_2504_03074_gb300 import grids as G, waveholtz as WH
+    prec = WH.FP32 if case.startswith("fp32") else WH.FP64
+    if case.endswith("square8192"):
+        sq = G.unit_square_problem(8192, 4, 10.0, seed=0)
+        s = WH.Solver(sq, precision=prec)
+        s.prepare()
+        s.profile_kernels(reps=5)  # march launches only (the first step of an iteration)
+        torch.cuda.synchronize()
+        print(f"profile case {case}: {sq.n_total} points, 5 march launches")
+        return 0
     bp, _ = G.batch_disk_problem(16, seed=100)
-    s = WH.Solver(bp, precision=WH.FP32 if case.startswith("fp32") else WH.FP64)
+    s = WH.Solver(bp, precision=prec)
     s.prepare()
     a = torch.zeros(bp.n_total, dtype=torch.float64, device="cuda")
     b = torch.empty_like(a)
@@ -437,10 +470,12 @@ def main():
     ap.add_argument("--small", action="store_true", help="small workload (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32 / batched / solve-time measurements")
-    ap.add_argument("--profile-case", choices=["fp32_batch16", "fp64_batch16"],
-                    help="profiling aid: run 3 iterations of a 16-instance disk-in-square "
-                         "batch (8.4 M points, HBM resident) in one precision and exit "
-                         "without a bench line")
+    ap.add_argument("--profile-case",
+                    choices=["fp32_batch16", "fp64_batch16", "fp32_square8192",
+                             "fp64_square8192"],
+                    help="profiling aid: a 16-instance disk-in-square batch (8.4 M points, "
+                         "3 iterations) or one 8192^2 order-4 Cartesian grid (67 M points, "
+                         "5 march launches), HBM resident, in one precision; no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
