@@ -261,9 +261,10 @@ wh_status wh_set_coefficient(wh_ctx *ctx, int32_t grid_id, const double *c2);
  * order; every configuration is tested against the oracle).  -1 in a field: the library's
  * own choice, which depends on the problem (see each field).
  *   launch_mode   WH_LAUNCH_GRAPH or WH_LAUNCH_PERSISTENT.
- *   fold_gather   graph path: 1 = each march launch also does the next level's ghost rules
- *                 and interpolation (library: when their work units are at most half the
- *                 march blocks); 0 = a separate kernel after each march launch.
+ *   fold_gather   graph path: 1 = each march launch (plain or TMA-staged) also does the
+ *                 next level's ghost rules and interpolation (library: for the plain march
+ *                 when their work units are at most half the march blocks); 0 = a separate
+ *                 kernel after each march launch.
  *   tile_tickets  graph path without folding: 1 = march tiles by atomic ticket (library),
  *                 0 = by fixed grid stride.
  *   tma           FP32 march sets: 1 = TMA-staged march for constant-weight grids (library,

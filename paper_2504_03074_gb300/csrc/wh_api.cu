@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -80,6 +82,9 @@ struct wh_ctx {
   std::vector<int32_t> udep_tile;
   int64_t *d_udep_off = nullptr;
   int32_t *d_udep_tile = nullptr;
+  // the same dependencies numbered as the TMA-staged march's tiles (fast, then general)
+  std::vector<int32_t> udep_tile_tma;
+  int32_t *d_udep_tile_tma = nullptr;
   std::vector<BcItem> hbc;
   std::vector<int32_t> hbc_grid, hbc_axis, hbc_hi;
   std::vector<void *> allocs;
@@ -611,6 +616,23 @@ wh_status build_layout(wh_ctx *ctx) {
       }
     }
   }
+  {
+    // the folded gather's dependencies in the TMA march's numbering (fast tiles, then general)
+    std::map<std::tuple<int, int, int>, int32_t> tma_index;
+    for (size_t k = 0; k < ctx->hftiles.size(); ++k) {
+      const Tile &t = ctx->hftiles[k];
+      tma_index[std::make_tuple(t.grid, t.i0, t.j0)] = (int32_t)k;
+    }
+    for (size_t k = 0; k < ctx->hgtiles.size(); ++k) {
+      const Tile &t = ctx->hgtiles[k];
+      tma_index[std::make_tuple(t.grid, t.i0, t.j0)] = (int32_t)(ctx->hftiles.size() + k);
+    }
+    ctx->udep_tile_tma.resize(ctx->udep_tile.size());
+    for (size_t e = 0; e < ctx->udep_tile.size(); ++e) {
+      const Tile &t = ctx->htiles[ctx->udep_tile[e]];
+      ctx->udep_tile_tma[e] = tma_index.at(std::make_tuple(t.grid, t.i0, t.j0));
+    }
+  }
 
   // persistent-kernel patch lists: ghost and receiver positions inside each tile's staged
   // box (tile + halo of order/2, corner blocks excluded: the cross stencil never reads
@@ -730,6 +752,7 @@ wh_status build_layout(wh_ctx *ctx) {
       (st = dalloc(ctx, &ctx->d_err, 3)) ||
       (st = dalloc(ctx, &ctx->d_udep_off, ctx->udep_off.size())) ||
       (st = dalloc(ctx, &ctx->d_udep_tile, std::max<size_t>(ctx->udep_tile.size(), 1))) ||
+      (st = dalloc(ctx, &ctx->d_udep_tile_tma, std::max<size_t>(ctx->udep_tile.size(), 1))) ||
       (st = dalloc(ctx, &ctx->d_mask, off)) ||
       (st = dalloc(ctx, &ctx->d_V, off)) || (st = dalloc(ctx, &ctx->d_c2, off)) ||
       (st = dalloc(ctx, &ctx->d_rx, std::max<int64_t>(k5, 1))) ||
@@ -773,9 +796,12 @@ wh_status build_layout(wh_ctx *ctx) {
                   cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_udep_off, ctx->udep_off.data(), ctx->udep_off.size() * 8,
                 cudaMemcpyHostToDevice));
-  if (!ctx->udep_tile.empty())
+  if (!ctx->udep_tile.empty()) {
     CK(cudaMemcpy(ctx->d_udep_tile, ctx->udep_tile.data(), ctx->udep_tile.size() * 4,
                   cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_udep_tile_tma, ctx->udep_tile_tma.data(),
+                  ctx->udep_tile_tma.size() * 4, cudaMemcpyHostToDevice));
+  }
   if (!ctx->hgtiles.empty())
     CK(cudaMemcpy(ctx->d_gtiles, ctx->hgtiles.data(), ctx->hgtiles.size() * sizeof(Tile),
                   cudaMemcpyHostToDevice));
@@ -828,8 +854,11 @@ wh_status build_layout(wh_ctx *ctx) {
 bool uses_tma(const wh_ctx *ctx) { return ctx->set[ctx->active].tma && ctx->tune_tma != 0; }
 
 bool folds_gather(const wh_ctx *ctx) {
-  if (uses_tma(ctx) || ctx->nunits == 0) return false;
+  if (ctx->nunits == 0) return false;
   if (ctx->tune_fold >= 0) return ctx->tune_fold != 0;
+  // the TMA march's units would start after its ticketed general tiles run out (a tail:
+  // folding measured -6% on the FP32 disk workload), so it folds only when tuned to
+  if (uses_tma(ctx)) return false;
   const int nb = std::min((int)ctx->htiles.size(), ctx->march_blocks);
   return 2 * ctx->nunits <= nb;
 }
@@ -845,7 +874,7 @@ GatherArgs gather_args(wh_ctx *ctx) {
   ga.ridx = ctx->d_ridx;
   ga.rinst = ctx->d_rinst;
   ga.udep_off = ctx->d_udep_off;
-  ga.udep_tile = ctx->d_udep_tile;
+  ga.udep_tile = uses_tma(ctx) ? ctx->d_udep_tile_tma : ctx->d_udep_tile;
   ga.tile_done = ctx->d_tile_done;
   ga.err = ctx->d_err;
   // tiles by fixed stride: blocks with fewer tiles reach their gather unit early (tickets,
@@ -871,7 +900,7 @@ void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs,
     launch_march_tma(S.fp32, order, n == 0, std::min(S.tma_blocks, nf + ngn), ctx->stream,
                      ctx->d_grids, ctx->d_ftiles, nf, S.maps, ctx->d_gtiles, ngn, ctx->d_mask,
                      S.Wa, S.Wb, S.F, S.Wt, ctx->d_V, ctx->d_inst, n, fs, ctx->d_err,
-                     ctx->opt_spin_limit);
+                     ctx->opt_spin_limit, gather && gather->nunits ? gather : nullptr);
     return;
   }
   const int ntiles = (int)ctx->htiles.size();
@@ -2380,6 +2409,7 @@ wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out) {
   for (int pdl = 1; pdl >= 0; --pdl)
     for (int tma = has_tma ? 1 : 0; tma >= 0; --tma) {
       if (tma) {
+        if (ctx->nunits > 0) cands.push_back({false, 1, 0, 1, pdl});
         cands.push_back({false, 0, 0, 1, pdl});
         continue;
       }

@@ -166,7 +166,8 @@ void launch_march_tma(bool fp32, int order, bool first, int nblocks, cudaStream_
                       const DevGrid *grids, const Tile *ftiles, int nfast, const CUtensorMap *maps,
                       const Tile *gtiles, int ngen, const int8_t *mask, void *Wa, void *Wb,
                       const void *F, const void *Wt, double *V, const InstDev *inst, int n,
-                      double fs, int *ctl, unsigned long long spin_limit);
+                      double fs, int *ctl, unsigned long long spin_limit,
+                      const GatherArgs *gather = nullptr);  // fold level n + 1's gather
 void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const BcItem *bc,
                       int nbc, int bc_blocks, const int32_t *didx, const double *dw,
                       const int64_t *ridx, const int32_t *rinst, int nrecv, void *W,

@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                      const Tile *__restrict__ gtiles, int ngen, const int8_t *__restrict__ mask,
                      T *Wa, T *Wb, const T *__restrict__ F, const T *__restrict__ Wt, double *V,
                      const InstDev *__restrict__ inst, int n, double fs, int *ctl,
-                     unsigned long long spin_limit) {
+                     unsigned long long spin_limit, GatherArgs ga) {
   using S = TmaStage<T, ORDER>;
   constexpr int R = ORDER / 2;
   pdl_wait();
@@ -602,6 +602,10 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       }
     }
     __syncthreads();  // this stage is read; it is refilled by the issue of iteration k + 1
+    if (ga.nunits && tid == 0) {  // fast tile blockIdx + k nb has written level n + 1
+      __threadfence();
+      atomicAdd(&ga.tile_done[blockIdx.x + k * nb], 1);
+    }
   }
   // general tiles by ticket, exactly as march_kernel.  When they are few next to the blocks
   // (one annulus beside a large background), a ticket is a quarter tile (8 rows, one point
@@ -630,6 +634,13 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                                        wf_cur);
       }
     }
+    if (ga.nunits) {  // one of the general tile's gsplit parts has written level n + 1
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(&ga.tile_done[nfast + g / gsplit], 1);
+      }
+    }
   }
   if (tid == 0) {
     __threadfence();
@@ -637,6 +648,34 @@ __global__ void __launch_bounds__(kTileX *kTileY)
       atomicExch(&ctl[1], 0);
       atomicExch(&ctl[2], 0);
     }
+  }
+  if (!ga.nunits) return;
+  // Level n + 1's ghost rules and interpolation folded in, as in march_kernel: unit u on
+  // block nb - 1 - u after its tiles.  Tile flags count the parts written in this iteration
+  // (one per step for a fast tile, gsplit per step for a general one), so a source tile t
+  // has written level n + 1 once its flag reaches parts(t) (n + 1).
+  for (int u = nb - 1 - (int)blockIdx.x; u < ga.nunits; u += nb) {
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int64_t e = ga.udep_off[u] + tid; e < ga.udep_off[u + 1]; e += kTileX * kTileY) {
+      const int dt = ga.udep_tile[e];
+      const int need = (dt < nfast ? 1 : gsplit) * (n + 1);
+      volatile int *flag = (volatile int *)&ga.tile_done[dt];
+      unsigned long long it = 0;
+      while (*flag < need) {
+        if (++it > ga.spin_limit) {
+          atomicExch(ga.err, 1);
+          s_fail = 1;
+          break;
+        }
+        if (it > 64) __nanosleep(32);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_fail) return;
+    gather_unit<T, ORDER, true>(u, tid, ga.bc, ga.nbc, ga.bc_blocks, ga.didx, ga.dw, ga.ridx,
+                                ga.rinst, ga.nrecv, Wout, F, inst, n + 1, fs);
   }
 }
 
@@ -1555,12 +1594,15 @@ void launch_march_tma(bool fp32, int order, bool first, int nblocks, cudaStream_
                       const DevGrid *grids, const Tile *ftiles, int nfast, const CUtensorMap *maps,
                       const Tile *gtiles, int ngen, const int8_t *mask, void *Wa, void *Wb,
                       const void *F, const void *Wt, double *V, const InstDev *inst, int n,
-                      double fs, int *ctl, unsigned long long spin_limit) {
+                      double fs, int *ctl, unsigned long long spin_limit,
+                      const GatherArgs *gather) {
   const dim3 tb(kTileX, kTileY);
+  GatherArgs ga{};
+  if (gather) ga = *gather;
 #define WH_TMA(T, O, FI)                                                                       \
   launch_k(march_tma_kernel<T, O, FI>, dim3(nblocks), tb, TmaStage<T, O>::kSmem, s, grids,     \
            ftiles, nfast, maps, gtiles, ngen, mask, (T *)Wa, (T *)Wb, (const T *)F,            \
-           (const T *)Wt, V, inst, n, fs, ctl, spin_limit)
+           (const T *)Wt, V, inst, n, fs, ctl, spin_limit, ga)
   if (fp32) {
     if (order == 4) { if (first) WH_TMA(float, 4, true); else WH_TMA(float, 4, false); }
     else            { if (first) WH_TMA(float, 2, true); else WH_TMA(float, 2, false); }
