@@ -127,6 +127,8 @@ struct wh_ctx {
   double *d_adj = nullptr;   // lam, Y, Z x3, gc2, gf (extended)
   double *d_ckpt = nullptr;  // checkpoints and segment states
   int64_t ckpt_cap = 0;
+  cudaGraphExec_t adj_graph = nullptr;  // the S^T sweep (lam -> Z^0), captured once
+  double *adj_z0 = nullptr;              // where that graph leaves Z^0
   double *d_traj = nullptr;  // the whole forward trajectory X^0 .. X^M (when it fits)
   int64_t traj_cap = 0;
 
@@ -207,6 +209,10 @@ void drop_graphs(wh_ctx *ctx) {
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
+  if (ctx->adj_graph) {
+    cudaGraphExecDestroy(ctx->adj_graph);
+    ctx->adj_graph = nullptr;
+  }
 }
 
 void free_device(wh_ctx *ctx) {
@@ -1622,16 +1628,35 @@ wh_status adj_sweep(wh_ctx *ctx, const double *lam, double **z0_out, const doubl
   return WH_OK;
 }
 
-// y = S^T x for compact x, y (the zero-forcing map's transpose)
+// y = S^T x for compact x, y (the zero-forcing map's transpose).  The sweep between the
+// fixed buffers lam and Z^0 is captured once per preparation as a CUDA graph (its kernels
+// with programmatic dependent launch, as the forward iteration's) and replayed.
 wh_status apply_adjoint(wh_ctx *ctx, const double *x, double *y) {
   wh_status st = adj_setup(ctx);
   if (st) return st;
   const int ng = (int)ctx->hgrids.size();
   double *lam = ctx->d_adj;
+  if (!ctx->adj_graph) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    set_pdl(ctx->tune_pdl != 0);
+    st = adj_sweep(ctx, lam, &ctx->adj_z0, nullptr, nullptr, nullptr);
+    set_pdl(false);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(ctx, WH_ERR_CUDA, "adjoint capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->adj_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+      return fail(ctx, WH_ERR_CUDA, "adjoint graph: %s", cudaGetErrorString(e));
+  }
   launch_compact_to_ext(ctx->stream, ctx->d_grids, ng, ctx->d_mask, x, lam, ctx->total);
-  double *z0;
-  if ((st = adj_sweep(ctx, lam, &z0, nullptr, nullptr, nullptr))) return st;
-  launch_ext_to_compact(ctx->stream, ctx->d_grids, ng, ctx->d_mask, z0, y, ctx->ncompact, 1);
+  CK(cudaGraphLaunch(ctx->adj_graph, ctx->stream));
+  launch_ext_to_compact(ctx->stream, ctx->d_grids, ng, ctx->d_mask, ctx->adj_z0, y,
+                        ctx->ncompact, 1);
   CK(cudaGetLastError());
   return WH_OK;
 }
@@ -1962,6 +1987,10 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   CK(cudaStreamSynchronize(s));
   ctx->prepared = true;
   ctx->adj_ready = false;
+  if (ctx->adj_graph) {  // it holds this preparation's step weights and constraint lists
+    cudaGraphExecDestroy(ctx->adj_graph);
+    ctx->adj_graph = nullptr;
+  }
   return WH_OK;
 }
 

@@ -1099,6 +1099,7 @@ __global__ void adj_step_kernel(const DevGrid *__restrict__ grids, int ngrids,
                                 const double *__restrict__ Xnext, const double *__restrict__ F,
                                 double fc, double *gc2, double *gf) {
   constexpr int R = ORDER / 2;
+  pdl_wait();
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= total) return;
   int g, i, j;
@@ -1192,6 +1193,7 @@ __global__ void adj_post_kernel(const int64_t *__restrict__ fq, const int64_t *_
                                 const BcItem *__restrict__ bc, int nbc,
                                 const double *__restrict__ F, double fcos, double *gc2,
                                 double *gf) {
+  pdl_wait();
   if ((int)blockIdx.x < fix_blocks) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t k = t / kFixLanes;
@@ -1716,11 +1718,11 @@ void launch_adj_step(int order, cudaStream_t s, const DevGrid *grids, int ngrids
                      const double *F, double fc, double *gc2, double *gf) {
   const unsigned nb = (unsigned)((total + 255) / 256);
   if (order == 4)
-    adj_step_kernel<4><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, Znew,
-                                          total, Xprev, Xn, Xnext, F, fc, gc2, gf);
+    launch_k(adj_step_kernel<4>, dim3(nb), dim3(256), 0, s, grids, ngrids, mask, Wt, lam, wn, sc,
+             Z1, Z2, Y, Znew, total, Xprev, Xn, Xnext, F, fc, gc2, gf);
   else
-    adj_step_kernel<2><<<nb, 256, 0, s>>>(grids, ngrids, mask, Wt, lam, wn, sc, Z1, Z2, Y, Znew,
-                                          total, Xprev, Xn, Xnext, F, fc, gc2, gf);
+    launch_k(adj_step_kernel<2>, dim3(nb), dim3(256), 0, s, grids, ngrids, mask, Wt, lam, wn, sc,
+             Z1, Z2, Y, Znew, total, Xprev, Xn, Xnext, F, fc, gc2, gf);
 }
 
 void launch_adj_post(cudaStream_t s, const int64_t *fq, const int64_t *foff, const int64_t *rpos,
@@ -1730,9 +1732,8 @@ void launch_adj_post(cudaStream_t s, const int64_t *fq, const int64_t *foff, con
   const int fix_blocks = (int)((nfix * kFixLanes + 255) / 256);
   const int bc_blocks = gc2 ? (nbc + 255) / 256 : 0;
   if (fix_blocks + bc_blocks)
-    adj_post_kernel<<<fix_blocks + bc_blocks, 256, 0, s>>>(fq, foff, rpos, rcoef, Y, Z, nfix,
-                                                            fix_blocks, bc, gc2 ? nbc : 0, F, fcos,
-                                                            gc2, gf);
+    launch_k(adj_post_kernel, dim3(fix_blocks + bc_blocks), dim3(256), 0, s, fq, foff, rpos,
+             rcoef, Y, Z, nfix, fix_blocks, bc, gc2 ? nbc : 0, F, fcos, gc2, gf);
 }
 
 void launch_compact_to_ext(cudaStream_t s, const DevGrid *grids, int ngrids, const int8_t *mask,
