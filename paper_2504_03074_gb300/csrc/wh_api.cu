@@ -73,7 +73,8 @@ struct wh_ctx {
   std::vector<Tile> hftiles, hgtiles;
   std::vector<int32_t> fast_grids;  // grid of each map slot
   Tile *d_ftiles = nullptr, *d_gtiles = nullptr;
-  int *d_err = nullptr;  // TMA march control: [0] sticky error flag, [1] ticket, [2] blocks done
+  // march control: [0] sticky error flag, [1] tile ticket, [2] blocks done
+  int *d_err = nullptr;
   // launch layout fixed by wh_set_tuning / wh_autotune (-1: the library's choice)
   int tune_fold = -1, tune_tickets = -1, tune_tma = -1, tune_pdl = -1;
   // ghost rules + interpolation folded into the march launch (march_kernel sets)

@@ -358,11 +358,11 @@ __global__ void __launch_bounds__(kTileX *kTileY, 5)
     atomicExch(&ga.ctl[1], 0);  // last block out: tickets start at zero in the next launch
     atomicExch(&ga.ctl[2], 0);
   }
-  if (!ga.nunits) return;
-  // The folded ghost rules and interpolation of level n + 1: unit u on block nb - 1 - u (the
-  // blocks with the fewest march tiles), after its source tiles have signalled.  Blocks
-  // only wait here, after their own march tiles, and the grid is one resident wave, so
-  // every awaited tile is computed; each wait is bounded all the same.
+  // The folded ghost rules and interpolation of level n + 1 (the graph path passes no tile
+  // tickets with them): unit u on block nb - 1 - u (the blocks with the fewest march
+  // tiles), after its source tiles have signalled.  Blocks only wait here, after their own
+  // march tiles, and the grid is one resident wave, so every awaited tile is computed; each
+  // wait is bounded all the same.  (Tiles and units both by ticket measured -25%.)
   __shared__ int s_fail;
   for (int u = (int)gridDim.x - 1 - (int)blockIdx.x; u < ga.nunits; u += gridDim.x) {
     if (tid == 0) s_fail = 0;
