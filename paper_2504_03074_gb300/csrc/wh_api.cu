@@ -982,9 +982,15 @@ wh_status check_timeout(wh_ctx *ctx, bool wait) {
     return WH_OK;
   }
   ctx->err_pending = false;
-  if (*ctx->h_err)
+  if (*ctx->h_err) {
+    *ctx->h_err = 0;
+    // the graph path's flag is sticky on the device: clear it once reported, so that the
+    // context stays usable (the persistent path clears its own at every launch)
+    if (ctx->d_err) CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     return fail(ctx, WH_ERR_TIMEOUT,
-                "a bounded wait timed out (persistent grid barrier or TMA stage of the march)");
+                "a bounded wait timed out (grid barrier, step flag or TMA stage of an "
+                "iteration)");
+  }
   return WH_OK;
 }
 

@@ -546,14 +546,16 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     }
     __syncthreads();
     if (s_fail) {
-      // give the copies still in flight a bounded time to land, then report and leave
+      // let the copies still in flight land before the block (and its shared memory) goes:
+      // this drain is bounded on its own scale (about a second), not by the caller's spin
+      // limit, which may be set tiny to provoke the timeout; then report and leave
       if (tid == 0) {
         atomicExch(&ctl[0], 1);
         for (int q = k; q < k + kTmaStages && q < nmy; ++q) {
           unsigned long long w = 0;
           while (!mbar_try_wait(&bar[q % kTmaStages], (uint32_t)((q / kTmaStages) & 1)) &&
-                 ++w < spin_limit) {
-          }
+                 ++w < (1ull << 22))
+            __nanosleep(256);
         }
       }
       return;

@@ -174,6 +174,35 @@ def test_barrier_timeout_is_reported(torch, W):
     assert float(torch.ones(4, device="cuda").sum()) == 4.0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_path_wait_timeout_is_reported(torch, W, oracle_mod, prec):
+    """The graph path's bounded waits (folded gather's step flags in FP64, TMA stages in
+    FP32; copies in flight are drained first) with a spin limit of 1: an iteration either
+    completes or reports WH_ERR_TIMEOUT (each poll of an mbarrier may itself wait a while,
+    so whether a limit of 1 runs out is up to the hardware), the context stays usable, and
+    a solver with the normal limit still gives the oracle's iteration."""
+    prob = G.disk_problem(nb=256, nth=512, nr=16, order=4, omega=10.0, seed=6)
+    pr = W.FP64 if prec == "fp64" else W.FP32
+    s = W.Solver(prob, precision=pr, barrier_spin_limit=1)
+    s.prepare()
+    v = G.random_state(prob, 13)
+    reported = 0
+    for _ in range(3):
+        try:
+            out = s.iterate_host(v, True)
+            assert np.all(np.isfinite(out))
+        except W.WHError as e:
+            assert e.status == -5
+            reported += 1
+    ok = W.Solver(prob, precision=pr)
+    ok.prepare()
+    ref = oracle_mod.Oracle(prob).iterate(v, True)
+    got = ok.iterate_host(v, True)
+    act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
+    assert rel_err(got, ref, act) <= (TOL if prec == "fp64" else 1e-4)
+    assert float(torch.ones(4, device="cuda").sum()) == 4.0
+
+
 def test_gmres_reaches_direct_solution(torch, W):
     import dhs
     prob = G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, width=0.8, r_cut=0.75)
