@@ -1,0 +1,468 @@
+/*
+ * waveholtz_oracle3.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
+ *
+ * A plain, slow, single-threaded FP64 CPU implementation of one WaveHoltz iteration on a
+ * three-dimensional overset grid at second order, written from the paper (Appelo, Banks,
+ * Henshaw, Schwendeman, "An optimal O(N) Helmholtz solver for complex geometry using
+ * WaveHoltz and overset grids").  Only tests/, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header or table with the CUDA library
+ * nor with the two-dimensional oracle.
+ *
+ * What it computes (each step cites the passage it follows):
+ *   - time-step setup: the explicit CFL bound c dt sqrt(sum_k a_kk / dr_k^2 +
+ *     2 sum_{k<l} |a_kl| / (dr_k dr_l)) <= 1 (Eq. dtForCartesian, Sec. 3.2, C = 1 at second
+ *     order, frozen coefficients on curvilinear grids), then Recipe OmegaTildeExplicit
+ *     (dt = (2/omega) sin(pi/Nt), omega_e = 2 pi/(Nt dt)) and alpha_d (Eq. alphad, Sec. 4.2);
+ *   - the mapped Laplacian in three dimensions (Sec. 3.1, mapping method):
+ *       L u = sum_k a_kk u_{r_k r_k} + 2 sum_{k<l} a_kl u_{r_k r_l} + sum_k b_k u_{r_k},
+ *       a_kl = sum_m dr_k/dx_m dr_l/dx_m,  b_k = sum_m sum_l dr_l/dx_m d/dr_l(dr_k/dx_m),
+ *     discretised with D+D- for the second derivatives, D0 for first derivatives and
+ *     D0 D0 for mixed ones (Sec. 3.2, order 2); b_k from D0 differences of the metrics;
+ *   - the explicit scheme D+tD-t W = c^2 L_h W - f cos(omega_e t) with the first step
+ *     W^1 = W^0 + dt^2/2 (c^2 L_h W^0 - f) (Eq. WaveSchemeexplicit, Sec. 4.2);
+ *   - Algorithm 2 per step: advance every grid, apply boundary conditions, interpolate;
+ *   - tensor-product Lagrange interpolation from 3 x 3 x 3 donor stencils (Sec. 3.1);
+ *   - the trapezoid-rule filter (Eq. updateDiscreteExplicit, Sec. 4.2), T-bar = Np Nt dt.
+ *
+ * Ghost rules at second order (the paper defers them to its reference on overset wave
+ * solvers); boundary data g = 0:
+ *   Dirichlet: W_b = 0; ghosts are never read.
+ *   Neumann:   centred normal derivative D0 W = 0 along the boundary's normal grid axis,
+ *              i.e. W_{-1} = W_{+1}.  This is the normal derivative when the normal grid
+ *              axis is orthogonal to the two tangential axes, which is required.
+ * Grid lines of a pair of axes declared orthogonal drop the mixed term (a_kl = 0).
+ */
+#include <math.h>
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { O3_UNUSED = 0, O3_DISC = 1, O3_INTERP = 2, O3_DIRICHLET = 3 };
+enum { O3_BC_NONE = 0, O3_BC_DIRICHLET = 1, O3_BC_NEUMANN = 2, O3_BC_PERIODIC = 3 };
+enum { O3_CARTESIAN = 0, O3_CURVILINEAR = 1 };
+#define O3_MAX_GRIDS 64
+
+/* Coefficient arrays (c^2 folded in), in this order. */
+enum { C_A00 = 0, C_A11, C_A22, C_A01, C_A02, C_A12, C_B0, C_B1, C_B2, C_N };
+
+typedef struct {
+  int n[3], g[3], e[3];
+  int kind;
+  int ortho;       /* bit 0: axes (0,1) orthogonal, bit 1: (0,2), bit 2: (1,2) */
+  int bc[6];       /* [axis0 lo, axis0 hi, axis1 lo, axis1 hi, axis2 lo, axis2 hi] */
+  double h[3];
+  signed char *mask; /* extended */
+  double *rx;      /* curvilinear: 9 extended arrays, rx[(3 k + m) E + q] = dr_k / dx_m */
+  double *c2, *f;  /* extended */
+  double *coef;    /* curvilinear: C_N extended arrays */
+  long offset;
+} o3_grid;
+
+typedef struct {
+  int ngrids;
+  o3_grid G[O3_MAX_GRIDS];
+  long nrecv;
+  int *rg, *ri, *rj, *rk, *dg, *di, *dj, *dk;
+  double *wx, *wy, *wz;
+  double omega, dt, omega_e, alpha, cfl;
+  int Nt, Np, M, prepared;
+  char err[256];
+} o3_problem;
+
+/* pair index of axes a < b: (0,1) -> 0, (0,2) -> 1, (1,2) -> 2 */
+static int pair_of(int a, int b) { return a + b - 1; }
+
+static long ext_size(const o3_grid *G) { return (long)G->e[0] * G->e[1] * G->e[2]; }
+
+static long at(const o3_grid *G, int i, int j, int k) {
+  int ix[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (G->bc[2 * a] == O3_BC_PERIODIC) ix[a] = ((ix[a] % G->n[a]) + G->n[a]) % G->n[a];
+    if (ix[a] < -G->g[a] || ix[a] >= G->n[a] + G->g[a]) {
+      fprintf(stderr, "oracle3: index (%d,%d,%d) outside grid\n", i, j, k);
+      abort();
+    }
+  }
+  return ((long)(ix[2] + G->g[2]) * G->e[1] + (ix[1] + G->g[1])) * G->e[0] + (ix[0] + G->g[0]);
+}
+
+/* Value of W at (i, j, k) + d. */
+static double val(const o3_grid *G, const double *W, int i, int j, int k, const int *d) {
+  return W[at(G, i + d[0], j + d[1], k + d[2])];
+}
+
+/* D+D- W along axis a (divided). */
+static double d2(const o3_grid *G, const double *W, int i, int j, int k, int a) {
+  int p[3] = {0, 0, 0}, m[3] = {0, 0, 0}, z[3] = {0, 0, 0};
+  p[a] = 1; m[a] = -1;
+  return (val(G, W, i, j, k, p) - 2.0 * val(G, W, i, j, k, z) + val(G, W, i, j, k, m)) /
+         (G->h[a] * G->h[a]);
+}
+
+/* D0 W along axis a. */
+static double d1(const o3_grid *G, const double *W, int i, int j, int k, int a) {
+  int p[3] = {0, 0, 0}, m[3] = {0, 0, 0};
+  p[a] = 1; m[a] = -1;
+  return (val(G, W, i, j, k, p) - val(G, W, i, j, k, m)) / (2.0 * G->h[a]);
+}
+
+/* D0_a D0_b W, a != b. */
+static double d11(const o3_grid *G, const double *W, int i, int j, int k, int a, int b) {
+  int pp[3] = {0, 0, 0}, pm[3] = {0, 0, 0}, mp[3] = {0, 0, 0}, mm[3] = {0, 0, 0};
+  pp[a] = 1; pp[b] = 1;
+  pm[a] = 1; pm[b] = -1;
+  mp[a] = -1; mp[b] = 1;
+  mm[a] = -1; mm[b] = -1;
+  return (val(G, W, i, j, k, pp) - val(G, W, i, j, k, pm) - val(G, W, i, j, k, mp) +
+          val(G, W, i, j, k, mm)) / (4.0 * G->h[a] * G->h[b]);
+}
+
+/* c^2 L_h W at (i, j, k) (Sec. 3.1 mapping method; Cartesian: c^2 sum D+D-). */
+static double lap(const o3_grid *G, const double *W, int i, int j, int k) {
+  long q = at(G, i, j, k);
+  if (G->kind == O3_CARTESIAN)
+    return G->c2[q] * (d2(G, W, i, j, k, 0) + d2(G, W, i, j, k, 1) + d2(G, W, i, j, k, 2));
+  long E = ext_size(G);
+  const double *c = G->coef;
+  double L = 0.0;
+  for (int a = 0; a < 3; ++a) L += c[(C_A00 + a) * E + q] * d2(G, W, i, j, k, a);
+  const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+  for (int p = 0; p < 3; ++p)
+    if (!(G->ortho >> p & 1)) L += 2.0 * c[(C_A01 + p) * E + q] * d11(G, W, i, j, k, pa[p], pb[p]);
+  for (int a = 0; a < 3; ++a) L += c[(C_B0 + a) * E + q] * d1(G, W, i, j, k, a);
+  return L;
+}
+
+/* a_kl, b_k (c^2 folded in) at discretization and Dirichlet points. */
+static void precompute_coeffs(o3_grid *G) {
+  long E = ext_size(G);
+  free(G->coef);
+  G->coef = (double *)calloc(C_N * E, sizeof(double));
+  const double *rx = G->rx;
+  for (int k = 0; k < G->n[2]; ++k)
+    for (int j = 0; j < G->n[1]; ++j)
+      for (int i = 0; i < G->n[0]; ++i) {
+        long q = at(G, i, j, k);
+        signed char m = G->mask[q];
+        if (m != O3_DISC && m != O3_DIRICHLET) continue;
+        double a[3][3], b[3];
+        for (int r = 0; r < 3; ++r)
+          for (int s = 0; s < 3; ++s) {
+            a[r][s] = 0.0;
+            for (int mm = 0; mm < 3; ++mm) a[r][s] += rx[(3 * r + mm) * E + q] * rx[(3 * s + mm) * E + q];
+          }
+        for (int r = 0; r < 3; ++r) {
+          b[r] = 0.0;
+          for (int mm = 0; mm < 3; ++mm)
+            for (int l = 0; l < 3; ++l)
+              b[r] += rx[(3 * l + mm) * E + q] * d1(G, rx + (3 * r + mm) * E, i, j, k, l);
+        }
+        double c2 = G->c2[q];
+        G->coef[C_A00 * E + q] = c2 * a[0][0];
+        G->coef[C_A11 * E + q] = c2 * a[1][1];
+        G->coef[C_A22 * E + q] = c2 * a[2][2];
+        G->coef[C_A01 * E + q] = (G->ortho & 1) ? 0.0 : c2 * a[0][1];
+        G->coef[C_A02 * E + q] = (G->ortho & 2) ? 0.0 : c2 * a[0][2];
+        G->coef[C_A12 * E + q] = (G->ortho & 4) ? 0.0 : c2 * a[1][2];
+        for (int r = 0; r < 3; ++r) G->coef[(C_B0 + r) * E + q] = c2 * b[r];
+      }
+}
+
+/* Largest stable dt at second order, frozen coefficients (Eq. dtForCartesian). */
+static double dt_bound(const o3_problem *P) {
+  double smax = 0.0;
+  for (int g = 0; g < P->ngrids; ++g) {
+    const o3_grid *G = &P->G[g];
+    long E = ext_size(G);
+    for (int k = 0; k < G->n[2]; ++k)
+      for (int j = 0; j < G->n[1]; ++j)
+        for (int i = 0; i < G->n[0]; ++i) {
+          long q = at(G, i, j, k);
+          if (G->mask[q] != O3_DISC) continue;
+          double s = 0.0;
+          if (G->kind == O3_CARTESIAN) {
+            for (int a = 0; a < 3; ++a) s += 1.0 / (G->h[a] * G->h[a]);
+            s *= G->c2[q];
+          } else {
+            for (int a = 0; a < 3; ++a) s += G->coef[(C_A00 + a) * E + q] / (G->h[a] * G->h[a]);
+            const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+            for (int p = 0; p < 3; ++p)
+              s += 2.0 * fabs(G->coef[(C_A01 + p) * E + q]) / (G->h[pa[p]] * G->h[pb[p]]);
+          }
+          if (s > smax) smax = s;
+        }
+  }
+  return 1.0 / sqrt(smax);
+}
+
+/* Ghost points of every Neumann side: W_{-1} = W_{+1} next to discretization points. */
+static void apply_bc(const o3_problem *P, int gidx, double *W) {
+  const o3_grid *G = &P->G[gidx];
+  for (int s = 0; s < 6; ++s) {
+    if (G->bc[s] != O3_BC_NEUMANN) continue;
+    int a = s / 2, hi = s % 2, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    for (int v = 0; v < G->n[t2]; ++v)
+      for (int u = 0; u < G->n[t1]; ++u) {
+        int ib[3], ig[3], in[3];
+        ib[t1] = ig[t1] = in[t1] = u;
+        ib[t2] = ig[t2] = in[t2] = v;
+        ib[a] = hi ? G->n[a] - 1 : 0;
+        ig[a] = hi ? G->n[a] : -1;
+        in[a] = hi ? G->n[a] - 2 : 1;
+        if (G->mask[at(G, ib[0], ib[1], ib[2])] != O3_DISC) continue;
+        W[at(G, ig[0], ig[1], ig[2])] = W[at(G, in[0], in[1], in[2])];
+      }
+  }
+}
+
+/* Every receiver from its 3 x 3 x 3 donor stencil (Sec. 3.1). */
+static void interpolate(const o3_problem *P, double **W) {
+  for (long r = 0; r < P->nrecv; ++r) {
+    const o3_grid *D = &P->G[P->dg[r]];
+    double s = 0.0;
+    for (int c = 0; c < 3; ++c)
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a)
+          s += P->wx[r * 3 + a] * P->wy[r * 3 + b] * P->wz[r * 3 + c] *
+               W[P->dg[r]][at(D, P->di[r] + a, P->dj[r] + b, P->dk[r] + c)];
+    W[P->rg[r]][at(&P->G[P->rg[r]], P->ri[r], P->rj[r], P->rk[r])] = s;
+  }
+}
+
+/* ------------------------------------------------------------ public API */
+
+o3_problem *o3_new(void) { return (o3_problem *)calloc(1, sizeof(o3_problem)); }
+
+const char *o3_error(const o3_problem *P) { return P->err; }
+
+/* mask, c2 are compact (n2 x n1 x n0, axis 0 fastest); rx covers the extended extent. */
+int o3_add_grid(o3_problem *P, int n0, int n1, int n2, int kind, const int *bc, int ortho,
+                double h0, double h1, double h2, const signed char *mask, const double *rx,
+                const double *c2) {
+  if (P->ngrids >= O3_MAX_GRIDS) return -1;
+  for (int a = 0; a < 3; ++a)
+    if ((bc[2 * a] == O3_BC_PERIODIC) != (bc[2 * a + 1] == O3_BC_PERIODIC)) {
+      snprintf(P->err, sizeof P->err, "periodic must pair");
+      return -1;
+    }
+  for (int s = 0; s < 6; ++s) {
+    if (bc[s] != O3_BC_NEUMANN) continue;
+    int a = s / 2;
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) continue;
+      int p = pair_of(a < b ? a : b, a < b ? b : a);
+      if (kind == O3_CURVILINEAR && !(ortho >> p & 1)) {
+        snprintf(P->err, sizeof P->err, "Neumann axis not orthogonal to the tangential axes");
+        return -1;
+      }
+    }
+  }
+  o3_grid *G = &P->G[P->ngrids];
+  memset(G, 0, sizeof *G);
+  G->n[0] = n0; G->n[1] = n1; G->n[2] = n2;
+  for (int s = 0; s < 6; ++s) G->bc[s] = bc[s];
+  for (int a = 0; a < 3; ++a) {
+    G->g[a] = bc[2 * a] == O3_BC_PERIODIC ? 0 : 1;
+    G->e[a] = G->n[a] + 2 * G->g[a];
+  }
+  G->kind = kind; G->ortho = kind == O3_CARTESIAN ? 7 : ortho;
+  G->h[0] = h0; G->h[1] = h1; G->h[2] = h2;
+  long E = ext_size(G);
+  G->mask = (signed char *)calloc(E, 1);
+  G->c2 = (double *)malloc(E * sizeof(double));
+  G->f = (double *)calloc(E, sizeof(double));
+  for (long q = 0; q < E; ++q) G->c2[q] = 1.0;
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n0; ++i) {
+        long q = at(G, i, j, k), c = ((long)k * n1 + j) * n0 + i;
+        G->mask[q] = mask[c];
+        if (c2) G->c2[q] = c2[c];
+      }
+  if (kind == O3_CURVILINEAR) {
+    G->rx = (double *)malloc(9 * E * sizeof(double));
+    memcpy(G->rx, rx, 9 * E * sizeof(double));
+  }
+  long off = 0;
+  for (int g = 0; g < P->ngrids; ++g) off += (long)P->G[g].n[0] * P->G[g].n[1] * P->G[g].n[2];
+  G->offset = off;
+  P->prepared = 0;
+  return P->ngrids++;
+}
+
+int o3_set_forcing(o3_problem *P, int gidx, const double *f) {
+  o3_grid *G = &P->G[gidx];
+  for (int k = 0; k < G->n[2]; ++k)
+    for (int j = 0; j < G->n[1]; ++j)
+      for (int i = 0; i < G->n[0]; ++i)
+        G->f[at(G, i, j, k)] = f[((long)k * G->n[1] + j) * G->n[0] + i];
+  return 0;
+}
+
+int o3_set_interp(o3_problem *P, long n, const int *rg, const int *ri, const int *rj,
+                  const int *rk, const int *dg, const int *di, const int *dj, const int *dk,
+                  const double *wx, const double *wy, const double *wz) {
+  P->nrecv = n;
+  int **dst[8] = {&P->rg, &P->ri, &P->rj, &P->rk, &P->dg, &P->di, &P->dj, &P->dk};
+  const int *src[8] = {rg, ri, rj, rk, dg, di, dj, dk};
+  for (int q = 0; q < 8; ++q) {
+    free(*dst[q]);
+    *dst[q] = (int *)malloc((n ? n : 1) * sizeof(int));
+    if (n) memcpy(*dst[q], src[q], n * sizeof(int));
+  }
+  double **wd[3] = {&P->wx, &P->wy, &P->wz};
+  const double *ws[3] = {wx, wy, wz};
+  for (int q = 0; q < 3; ++q) {
+    free(*wd[q]);
+    *wd[q] = (double *)malloc((n ? n : 1) * 3 * sizeof(double));
+    if (n) memcpy(*wd[q], ws[q], n * 3 * sizeof(double));
+  }
+  return 0;
+}
+
+/* Time setup (Recipe OmegaTildeExplicit; Eq. alphad).
+ * out[0..6] = dt, omega_e, alpha, Nt, M, dt_max, Tbar. */
+int o3_prepare(o3_problem *P, double omega, double cfl, int Np, int alpha_mode, double *out) {
+  for (int g = 0; g < P->ngrids; ++g)
+    if (P->G[g].kind == O3_CURVILINEAR) precompute_coeffs(&P->G[g]);
+  double dtmax = cfl * dt_bound(P);
+  int Nt = (int)ceil(2.0 * M_PI / (omega * dtmax));
+  if (Nt < 2) Nt = 2;
+  double dt = 2.0 / omega * sin(M_PI / Nt);
+  while (dt > dtmax) { ++Nt; dt = 2.0 / omega * sin(M_PI / Nt); }
+  P->omega = omega; P->cfl = cfl; P->Nt = Nt; P->Np = Np; P->M = Np * Nt; P->dt = dt;
+  P->omega_e = 2.0 * M_PI / (Nt * dt);
+  P->alpha = alpha_mode ? 0.5 : tan(P->omega_e * dt / 2.0) / tan(P->omega_e * dt);
+  P->prepared = 1;
+  if (out) {
+    out[0] = dt; out[1] = P->omega_e; out[2] = P->alpha; out[3] = Nt; out[4] = P->M;
+    out[5] = dtmax; out[6] = P->M * dt;
+  }
+  return 0;
+}
+
+/* One WaveHoltz iteration v_out = W_h(v_in, f) (forcing = 1) or W_h(v_in, 0). */
+int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
+  if (!P->prepared) return -1;
+  int ng = P->ngrids, M = P->M;
+  double dt = P->dt, we = P->omega_e, fs = forcing ? 1.0 : 0.0;
+  double *Wm[O3_MAX_GRIDS], *W0[O3_MAX_GRIDS], *Wp[O3_MAX_GRIDS], *V[O3_MAX_GRIDS];
+  for (int g = 0; g < ng; ++g) {
+    long E = ext_size(&P->G[g]);
+    Wm[g] = (double *)calloc(E, sizeof(double));
+    W0[g] = (double *)calloc(E, sizeof(double));
+    Wp[g] = (double *)calloc(E, sizeof(double));
+    V[g] = (double *)calloc(E, sizeof(double));
+  }
+  /* filter weight of level n: (2/Tbar) sigma_n dt (cos(omega_e t^n) - alpha/2) */
+#define FILTER_W(n) ((2.0 / (M * dt)) * (((n) == 0 || (n) == M) ? 0.5 : 1.0) * dt * \
+                     (cos(we * (n) * dt) - P->alpha / 2.0))
+  for (int g = 0; g < ng; ++g) {
+    o3_grid *G = &P->G[g];
+    for (int k = 0; k < G->n[2]; ++k)
+      for (int j = 0; j < G->n[1]; ++j)
+        for (int i = 0; i < G->n[0]; ++i) {
+          long q = at(G, i, j, k);
+          signed char m = G->mask[q];
+          double v = v_in[G->offset + ((long)k * G->n[1] + j) * G->n[0] + i];
+          W0[g][q] = (m == O3_DISC || m == O3_INTERP) ? v : 0.0;
+        }
+    apply_bc(P, g, W0[g]);
+  }
+  interpolate(P, W0);
+  for (int n = 0; n < M; ++n) {
+    double tn = n * dt, wn = FILTER_W(n);
+    for (int g = 0; g < ng; ++g) {
+      o3_grid *G = &P->G[g];
+      long E = ext_size(G);
+      for (long q = 0; q < E; ++q)
+        if (G->mask[q] != O3_UNUSED) V[g][q] += wn * W0[g][q];
+    }
+    for (int g = 0; g < ng; ++g) {
+      o3_grid *G = &P->G[g];
+      memset(Wp[g], 0, ext_size(G) * sizeof(double));
+      for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+          for (int i = 0; i < G->n[0]; ++i) {
+            long q = at(G, i, j, k);
+            if (G->mask[q] != O3_DISC) continue;
+            double L = lap(G, W0[g], i, j, k);
+            if (n == 0)
+              Wp[g][q] = W0[g][q] + 0.5 * dt * dt * (L - fs * G->f[q]);
+            else
+              Wp[g][q] = 2.0 * W0[g][q] - Wm[g][q] + dt * dt * (L - fs * G->f[q] * cos(we * tn));
+          }
+      apply_bc(P, g, Wp[g]);
+    }
+    interpolate(P, Wp);
+    for (int g = 0; g < ng; ++g) {
+      double *t = Wm[g]; Wm[g] = W0[g]; W0[g] = Wp[g]; Wp[g] = t;
+    }
+  }
+  {
+    double wn = FILTER_W(M);
+    for (int g = 0; g < ng; ++g) {
+      o3_grid *G = &P->G[g];
+      long E = ext_size(G);
+      for (long q = 0; q < E; ++q)
+        if (G->mask[q] != O3_UNUSED) V[g][q] += wn * W0[g][q];
+    }
+  }
+#undef FILTER_W
+  for (int g = 0; g < ng; ++g) {
+    o3_grid *G = &P->G[g];
+    for (int k = 0; k < G->n[2]; ++k)
+      for (int j = 0; j < G->n[1]; ++j)
+        for (int i = 0; i < G->n[0]; ++i)
+          v_out[G->offset + ((long)k * G->n[1] + j) * G->n[0] + i] = V[g][at(G, i, j, k)];
+    free(Wm[g]); free(W0[g]); free(Wp[g]); free(V[g]);
+  }
+  return 0;
+}
+
+/* ---- pieces exposed for the tests ---- */
+
+/* c^2 L_h of an extended array of grid g at discretization and Dirichlet points. */
+int o3_apply_lap(o3_problem *P, int gidx, const double *u, double *out) {
+  o3_grid *G = &P->G[gidx];
+  for (int k = 0; k < G->n[2]; ++k)
+    for (int j = 0; j < G->n[1]; ++j)
+      for (int i = 0; i < G->n[0]; ++i) {
+        long q = at(G, i, j, k);
+        if (G->mask[q] == O3_DISC || G->mask[q] == O3_DIRICHLET) out[q] = lap(G, u, i, j, k);
+      }
+  return 0;
+}
+
+int o3_apply_bc(o3_problem *P, int gidx, double *u) {
+  apply_bc(P, gidx, u);
+  return 0;
+}
+
+int o3_get_coef(o3_problem *P, int gidx, int which, double *out) {
+  o3_grid *G = &P->G[gidx];
+  if (!G->coef || which < 0 || which >= C_N) return -1;
+  memcpy(out, G->coef + which * ext_size(G), ext_size(G) * sizeof(double));
+  return 0;
+}
+
+int o3_interpolate(o3_problem *P, double **u) {
+  interpolate(P, u);
+  return 0;
+}
+
+void o3_free(o3_problem *P) {
+  if (!P) return;
+  for (int g = 0; g < P->ngrids; ++g) {
+    o3_grid *G = &P->G[g];
+    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->coef);
+  }
+  free(P->rg); free(P->ri); free(P->rj); free(P->rk);
+  free(P->dg); free(P->di); free(P->dj); free(P->dk);
+  free(P->wx); free(P->wy); free(P->wz);
+  free(P);
+}

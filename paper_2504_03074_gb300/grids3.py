@@ -1,0 +1,531 @@
+"""Seeded synthetic three-dimensional overset grids (second order): the stand-in for the
+paper's grid generator (Ogen, Sec. 3.1) in 3D.
+
+It builds component grids from analytic mappings x = G_g(r) -- an axis-aligned Cartesian
+box, a spherical shell (periodic in azimuth, a polar band), and orthographic pole patches
+-- cuts the hole of the background, classifies points as discretization / interpolation /
+unused, finds 3 x 3 x 3 donor stencils (explicit interpolation: donors are discretization
+or Dirichlet points only) and their tensor-product Lagrange weights (Sec. 3.1), and
+evaluates Gaussian sources (Eq. gaussianSource).  Like ``grids`` it holds none of the
+WaveHoltz arithmetic: its outputs are the input data that both the CUDA library and the
+CPU oracle consume.
+
+Array conventions:
+
+* a grid has ``n = (n0, n1, n2)`` points along parameter axes 0, 1, 2 (boundary points
+  included, ghosts excluded; a periodic axis lists each point once);
+* compact per-grid arrays have shape ``(n2, n1, n0)`` in C order (axis 0 fastest);
+* the ghost width is 1 on non-periodic axes and 0 on periodic ones; extended arrays
+  (metrics) have shape ``(n2 + 2 g2, n1 + 2 g1, n0 + 2 g0)``;
+* sides are ``[axis0-lo, axis0-hi, axis1-lo, axis1-hi, axis2-lo, axis2-hi]``;
+* ``ortho`` is a bit mask of orthogonal axis pairs: bit 0 = (0, 1), bit 1 = (0, 2),
+  bit 2 = (1, 2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .grids import (BC_DIRICHLET, BC_NEUMANN, BC_NONE, BC_PERIODIC, CARTESIAN, CURVILINEAR,
+                    DIRICHLET, DISC, INTERP, UNUSED, lagrange_weights)
+
+ORDER = 2  # the three-dimensional path is second order
+_EPS = 1e-9  # index-space tolerance of "inside a grid" (points on a shared boundary)
+
+
+@dataclass
+class Grid3:
+    """One component grid of a three-dimensional overset grid (Sec. 3.1)."""
+
+    name: str
+    kind: int
+    n: tuple                      # (n0, n1, n2)
+    bc: list                      # 6 side codes
+    h: tuple                      # Cartesian: physical spacing; curvilinear: parameter spacing
+    mask: np.ndarray              # int8 (n2, n1, n0)
+    ortho: int = 7                # orthogonal axis pairs (bit mask)
+    rx: np.ndarray | None = None  # float64 (9, e2, e1, e0): rx[3k + m] = dr_k / dx_m
+    origin: tuple = (0.0, 0.0, 0.0)
+    mapping: dict = field(default_factory=dict)
+
+    def ghosts(self, order=ORDER):
+        return tuple(0 if self.bc[2 * a] == BC_PERIODIC else order // 2 for a in range(3))
+
+    @property
+    def npts(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def coords(self, k=None):
+        """Physical coordinates (3, n2, n1, n0), or of the plane k only (3, n1, n0)."""
+        ks = np.arange(self.n[2]) if k is None else np.array([k])
+        t = [np.arange(self.n[0]) * self.h[0], np.arange(self.n[1]) * self.h[1],
+             ks * self.h[2]]
+        T0, T1, T2 = np.meshgrid(t[0], t[1], t[2], indexing="ij")
+        T0, T1, T2 = (np.ascontiguousarray(np.transpose(a, (2, 1, 0))) for a in (T0, T1, T2))
+        out = self.mapping["map"](T0, T1, T2)
+        return out if k is None else out[:, 0]
+
+    def param(self, x, y, z):
+        """Fractional point indices (fi, fj, fk) of physical points, and a mask of the
+        points the mapping covers."""
+        return self.mapping["inverse"](x, y, z)
+
+
+@dataclass
+class Interp3:
+    """Receiver k of grid recv_grid at (recv_i, recv_j, recv_k) takes
+    sum_{a,b,c} wx[k,a] wy[k,b] wz[k,c] u_donor(i0 + a, j0 + b, k0 + c)."""
+
+    recv_grid: np.ndarray
+    recv_i: np.ndarray
+    recv_j: np.ndarray
+    recv_k: np.ndarray
+    donor_grid: np.ndarray
+    donor_i0: np.ndarray
+    donor_j0: np.ndarray
+    donor_k0: np.ndarray
+    wx: np.ndarray
+    wy: np.ndarray
+    wz: np.ndarray
+
+    @property
+    def n(self):
+        return int(self.recv_grid.shape[0])
+
+    @staticmethod
+    def empty():
+        z = np.zeros(0, np.int32)
+        w = np.zeros((0, 3))
+        return Interp3(z, z, z, z, z, z, z, z, w, w, w)
+
+
+@dataclass
+class Problem3:
+    """c^2 Lap u + omega^2 u = f on a three-dimensional overset grid (Eq. HelmholtzBVP)."""
+
+    grids: list
+    interp: Interp3
+    omega: float
+    f: list                       # per-grid compact forcing (n2, n1, n0)
+    c2: list | None = None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+    order: int = ORDER
+    dim: int = 3
+
+    @property
+    def n_active(self):
+        return int(sum(int(np.count_nonzero(g.mask != UNUSED)) for g in self.grids))
+
+    @property
+    def n_total(self):
+        return int(sum(g.npts for g in self.grids))
+
+    def split(self, vec):
+        out, o = [], 0
+        for g in self.grids:
+            out.append(vec[o:o + g.npts].reshape(g.n[2], g.n[1], g.n[0]))
+            o += g.npts
+        return out
+
+
+# ----------------------------------------------------------------------------------
+# Component grids
+# ----------------------------------------------------------------------------------
+
+def cartesian_grid3(name, n, lo, hi, bc):
+    """Axis-aligned box [lo, hi] with n[a] points per axis; Dirichlet sides marked."""
+    h = tuple((hi[a] - lo[a]) / (n[a] - 1) for a in range(3))
+    mask = np.full((n[2], n[1], n[0]), DISC, np.int8)
+    sl = [np.s_[:, :, 0], np.s_[:, :, -1], np.s_[:, 0, :], np.s_[:, -1, :],
+          np.s_[0, :, :], np.s_[-1, :, :]]
+    for s, code in enumerate(bc):
+        if code == BC_DIRICHLET:
+            mask[sl[s]] = DIRICHLET
+    lo = tuple(float(v) for v in lo)
+
+    def fmap(t0, t1, t2):
+        return np.stack([lo[0] + t0, lo[1] + t1, lo[2] + t2])
+
+    def inv(x, y, z):
+        fi, fj, fk = (x - lo[0]) / h[0], (y - lo[1]) / h[1], (z - lo[2]) / h[2]
+        ok = ((fi >= -_EPS) & (fi <= n[0] - 1 + _EPS) & (fj >= -_EPS) &
+              (fj <= n[1] - 1 + _EPS) & (fk >= -_EPS) & (fk <= n[2] - 1 + _EPS))
+        return fi, fj, fk, ok
+
+    # Cartesian parameters are physical offsets: coords() maps t -> lo + t
+    g = Grid3(name, CARTESIAN, tuple(n), list(bc), h, mask, 7, None, lo)
+    g.mapping = dict(map=fmap, inverse=inv)
+    return g
+
+
+def shell_grid(name, nphi, nth, nr, r_in, width, th_lo_deg, th_hi_deg):
+    """Spherical shell x = r (sin th cos phi, sin th sin phi, cos th).
+
+    Axis 0: phi = 2 pi t0 (periodic, nphi points), axis 1: th = th_lo + (th_hi - th_lo) t1
+    (nth points), axis 2: r = r_in + width t2 (nr points).  Side axis2-lo is the sphere
+    (Neumann); the polar edges and the outer shell are interpolation points.  All three
+    pairs of grid lines are orthogonal.  Metrics are analytic and also evaluated on the
+    ghost lines.
+    """
+    th0, th1 = math.radians(th_lo_deg), math.radians(th_hi_deg)
+    d0, d1, d2 = 1.0 / nphi, 1.0 / (nth - 1), 1.0 / (nr - 1)
+    dth = th1 - th0
+
+    def fmap(t0, t1, t2):
+        ph, th, r = 2 * np.pi * t0, th0 + dth * t1, r_in + width * t2
+        return np.stack([r * np.sin(th) * np.cos(ph), r * np.sin(th) * np.sin(ph),
+                         r * np.cos(th)])
+
+    def inv(x, y, z):
+        r = np.sqrt(x * x + y * y + z * z)
+        ph = np.mod(np.arctan2(y, x), 2 * np.pi)
+        th = np.arccos(np.clip(z / np.maximum(r, 1e-300), -1.0, 1.0))
+        fi = ph / (2 * np.pi) * nphi
+        fj = (th - th0) / dth * (nth - 1)
+        fk = (r - r_in) / width * (nr - 1)
+        ok = (fj >= -_EPS) & (fj <= nth - 1 + _EPS) & (fk >= -_EPS) & (fk <= nr - 1 + _EPS)
+        return fi, fj, fk, ok
+
+    # inverse metrics on the extended extent (no ghosts on the periodic axis 0)
+    t0 = np.arange(nphi) * d0
+    t1 = np.arange(-1, nth + 1) * d1
+    t2 = np.arange(-1, nr + 1) * d2
+    T2, T1, T0 = np.meshgrid(t2, t1, t0, indexing="ij")
+    ph, th, r = 2 * np.pi * T0, th0 + dth * T1, r_in + width * T2
+    sp, cp, st, ct = np.sin(ph), np.cos(ph), np.sin(th), np.cos(th)
+    rx = np.empty((9,) + T0.shape)
+    # grad phi = (-sin phi, cos phi, 0) / (r sin th);  t0 = phi / (2 pi)
+    rx[0], rx[1], rx[2] = -sp / (r * st) / (2 * np.pi), cp / (r * st) / (2 * np.pi), 0.0
+    # grad th = (cos th cos phi, cos th sin phi, -sin th) / r;  t1 = (th - th0) / dth
+    rx[3], rx[4], rx[5] = ct * cp / r / dth, ct * sp / r / dth, -st / r / dth
+    # grad r = (sin th cos phi, sin th sin phi, cos th);  t2 = (r - r_in) / width
+    rx[6], rx[7], rx[8] = st * cp / width, st * sp / width, ct / width
+    mask = np.full((nr, nth, nphi), DISC, np.int8)
+    mask[:, 0, :] = INTERP
+    mask[:, -1, :] = INTERP
+    mask[-1, :, :] = INTERP
+    bc = [BC_PERIODIC, BC_PERIODIC, BC_NONE, BC_NONE, BC_NEUMANN, BC_NONE]
+    g = Grid3(name, CURVILINEAR, (nphi, nth, nr), bc, (d0, d1, d2), mask, 7, rx)
+    g.mapping = dict(map=fmap, inverse=inv, r_in=r_in, width=width, th=(th0, th1))
+    return g
+
+
+def pole_patch_grid(name, na, nr, A, r_in, width, sign):
+    """Orthographic pole patch x = r (a, b, sign sqrt(1 - a^2 - b^2)), a, b in [-A, A].
+
+    Axes 0, 1: a, b (na points each), axis 2: r = r_in + width t2 (nr points).  Side
+    axis2-lo is the sphere (Neumann); the four (a, b) edges and the outer layer are
+    interpolation points.  The radial lines are orthogonal to the (a, b) surfaces (pairs
+    (0, 2) and (1, 2)); a and b lines are not (the mixed a-b term is present).
+    """
+    d0 = d1 = 1.0 / (na - 1)
+    d2 = 1.0 / (nr - 1)
+
+    def fmap(t0, t1, t2):
+        a, b, r = -A + 2 * A * t0, -A + 2 * A * t1, r_in + width * t2
+        return np.stack([r * a, r * b, sign * r * np.sqrt(1.0 - a * a - b * b)])
+
+    def inv(x, y, z):
+        r = np.sqrt(x * x + y * y + z * z)
+        rs = np.maximum(r, 1e-300)
+        a, b = x / rs, y / rs
+        fi = (a + A) / (2 * A) * (na - 1)
+        fj = (b + A) / (2 * A) * (na - 1)
+        fk = (r - r_in) / width * (nr - 1)
+        ok = ((sign * z > 0) & (fi >= -_EPS) & (fi <= na - 1 + _EPS) & (fj >= -_EPS) &
+              (fj <= na - 1 + _EPS) & (fk >= -_EPS) & (fk <= nr - 1 + _EPS))
+        return fi, fj, fk, ok
+
+    t = np.arange(-1, na + 1) * d0
+    t2 = np.arange(-1, nr + 1) * d2
+    T2, T1, T0 = np.meshgrid(t2, t, t, indexing="ij")
+    a, b, r = -A + 2 * A * T0, -A + 2 * A * T1, r_in + width * T2
+    c = sign * np.sqrt(1.0 - a * a - b * b)  # unit vector s = (a, b, c)
+    rx = np.empty((9,) + T0.shape)
+    # grad a = (e_x - a s) / r, grad b = (e_y - b s) / r, grad r = s
+    rx[0], rx[1], rx[2] = (1 - a * a) / r, -a * b / r, -a * c / r
+    rx[3], rx[4], rx[5] = -a * b / r, (1 - b * b) / r, -b * c / r
+    rx[0:3] /= 2 * A
+    rx[3:6] /= 2 * A
+    rx[6], rx[7], rx[8] = a / width, b / width, c / width
+    mask = np.full((nr, na, na), DISC, np.int8)
+    mask[:, :, 0] = INTERP
+    mask[:, :, -1] = INTERP
+    mask[:, 0, :] = INTERP
+    mask[:, -1, :] = INTERP
+    mask[-1, :, :] = INTERP
+    bc = [BC_NONE, BC_NONE, BC_NONE, BC_NONE, BC_NEUMANN, BC_NONE]
+    g = Grid3(name, CURVILINEAR, (na, na, nr), bc, (d0, d1, d2), mask, 6, rx)
+    g.mapping = dict(map=fmap, inverse=inv, A=A, sign=sign, r_in=r_in, width=width)
+    return g
+
+
+# ----------------------------------------------------------------------------------
+# Donor search (explicit interpolation)
+# ----------------------------------------------------------------------------------
+
+def _stencil(g, fi, fj, fk):
+    """Lower corners of the 3-point stencils nearest (fi, fj, fk), shifted inside."""
+    f = [fi, fj, fk]
+    c = []
+    for a in range(3):
+        i0 = np.rint(f[a]).astype(np.int64) - 1
+        if g.bc[2 * a] == BC_PERIODIC:
+            i0 = np.mod(i0, g.n[a])
+        else:
+            i0 = np.clip(i0, 0, g.n[a] - 3)
+        c.append(i0)
+    return c
+
+
+def _valid(g, c):
+    """True where all 27 stencil points are discretization or Dirichlet points."""
+    ok = np.ones(c[0].shape, bool)
+    for dc in range(3):
+        for db in range(3):
+            for da in range(3):
+                ii = [c[0] + da, c[1] + db, c[2] + dc]
+                for a in range(3):
+                    if g.bc[2 * a] == BC_PERIODIC:
+                        ii[a] = np.mod(ii[a], g.n[a])
+                m = g.mask[ii[2], ii[1], ii[0]]
+                ok &= (m == DISC) | (m == DIRICHLET)
+    return ok
+
+
+def find_donors(grids, recv_gid, pts, order_of_donors):
+    """Donor stencils for receivers of grid ``recv_gid`` at physical points pts (3, N),
+    trying donor grids in the given order; raises if a receiver has no valid stencil."""
+    N = pts.shape[1]
+    out_g = np.full(N, -1, np.int32)
+    out_c = np.zeros((3, N), np.int64)
+    out_f = np.zeros((3, N))
+    for dgid in order_of_donors:
+        todo = np.nonzero(out_g < 0)[0]
+        if todo.size == 0:
+            break
+        g = grids[dgid]
+        fi, fj, fk, ok = g.param(pts[0, todo], pts[1, todo], pts[2, todo])
+        sel = np.nonzero(ok)[0]
+        if sel.size == 0:
+            continue
+        c = _stencil(g, fi[sel], fj[sel], fk[sel])
+        v = _valid(g, c)
+        take = todo[sel[v]]
+        out_g[take] = dgid
+        for a, fa in enumerate((fi, fj, fk)):
+            out_c[a, take] = c[a][v]
+            frac = fa[sel[v]] - c[a][v]
+            if g.bc[2 * a] == BC_PERIODIC:  # distance along the periodic axis from i0
+                frac = np.mod(frac + 1.0, g.n[a]) - 1.0
+            out_f[a, take] = frac
+    if np.any(out_g < 0):
+        k = int(np.nonzero(out_g < 0)[0][0])
+        raise ValueError(f"receiver {k} of grid {recv_gid} at {pts[:, k]} has no donor")
+    return out_g, out_c, out_f
+
+
+def check_explicit_interp3(grids, it):
+    """Every donor is a discretization or Dirichlet point; receivers are INTERP points."""
+    rg = it.recv_grid
+    for gid, g in enumerate(grids):
+        sel = rg == gid
+        m = g.mask[it.recv_k[sel], it.recv_j[sel], it.recv_i[sel]]
+        if not np.all(m == INTERP):
+            raise ValueError(f"grid {gid}: a receiver is not an interpolation point")
+        if int(np.count_nonzero(g.mask == INTERP)) != int(np.count_nonzero(sel)):
+            raise ValueError(f"grid {gid}: interpolation points and receivers differ")
+    for gid, g in enumerate(grids):
+        sel = it.donor_grid == gid
+        if not np.any(sel):
+            continue
+        c = [it.donor_i0[sel].astype(np.int64), it.donor_j0[sel].astype(np.int64),
+             it.donor_k0[sel].astype(np.int64)]
+        for a in range(3):
+            if g.bc[2 * a] != BC_PERIODIC and (c[a].min() < 0 or c[a].max() > g.n[a] - 3):
+                raise ValueError(f"donor stencil outside grid {gid}")
+        if not np.all(_valid(g, c)):
+            raise ValueError(f"grid {gid}: a donor stencil touches a non-discretization point")
+
+
+def _assemble(grids, parts):
+    """Concatenate (recv_gid, ijk (3, N), donor g (N), corner (3, N), frac (3, N))."""
+    cols = [[] for _ in range(11)]
+    for rgid, ijk, dg, c, f in parts:
+        n = ijk.shape[1]
+        cols[0].append(np.full(n, rgid, np.int32))
+        for a in range(3):
+            cols[1 + a].append(ijk[a].astype(np.int32))
+        cols[4].append(dg.astype(np.int32))
+        for a in range(3):
+            cols[5 + a].append(c[a].astype(np.int32))
+        for a in range(3):
+            cols[8 + a].append(lagrange_weights(f[a], 3))
+    arrs = [np.concatenate(c) for c in cols]
+    return Interp3(*arrs)
+
+
+def _interp_points(g):
+    k, j, i = np.nonzero(g.mask == INTERP)
+    return np.stack([i, j, k])
+
+
+def _points_of(g, ijk):
+    """Physical coordinates of the listed points of g."""
+    t = [ijk[a] * g.h[a] for a in range(3)]
+    return g.mapping["map"](t[0].astype(np.float64), t[1].astype(np.float64),
+                            t[2].astype(np.float64))
+
+
+# ----------------------------------------------------------------------------------
+# Overset grids
+# ----------------------------------------------------------------------------------
+
+def sphere_in_box(nb=320, nphi=256, nth=128, nr=24, npatch=96, box=2.0, r_in=0.5,
+                  width=0.3, band=(15.0, 165.0), patch_deg=24.0, r_hole=0.65):
+    """Cartesian background [-box, box]^3 (nb^3 points, Dirichlet) + spherical shell
+    (nphi x nth x nr, polar band) + two orthographic pole patches (npatch^2 x nr).
+
+    Background points with |x| < r_hole are cut out; the cut points that are 7-point
+    stencil neighbours of a background discretization point become interpolation points.
+    Donors: background receivers from the shell, else a patch; shell receivers from a
+    patch, else the background; patch receivers from the shell, else the background.
+    Returns (grids, interp).
+    """
+    B = cartesian_grid3("background", (nb, nb, nb), (-box,) * 3, (box,) * 3,
+                        [BC_DIRICHLET] * 6)
+    S = shell_grid("shell", nphi, nth, nr, r_in, width, band[0], band[1])
+    A = math.sin(math.radians(patch_deg))
+    PN = pole_patch_grid("north", npatch, nr, A, r_in, width, 1.0)
+    PS = pole_patch_grid("south", npatch, nr, A, r_in, width, -1.0)
+    # hole cutting, plane by plane
+    x = -box + B.h[0] * np.arange(nb)
+    inside = np.zeros((nb, nb, nb), bool)
+    X2 = x[None, :] ** 2 + x[:, None] ** 2
+    for k in range(nb):
+        inside[k] = X2 + x[k] ** 2 < r_hole * r_hole
+    active = ~inside
+    near = np.zeros_like(active)
+    near[1:] |= active[:-1]
+    near[:-1] |= active[1:]
+    near[:, 1:] |= active[:, :-1]
+    near[:, :-1] |= active[:, 1:]
+    near[:, :, 1:] |= active[:, :, :-1]
+    near[:, :, :-1] |= active[:, :, 1:]
+    B.mask[inside & near] = INTERP
+    B.mask[inside & ~near] = UNUSED
+    del inside, active, near
+    grids = [B, S, PN, PS]
+    parts = []
+    for rgid, order in ((0, (1, 2, 3)), (1, (2, 3, 0)), (2, (1, 0)), (3, (1, 0))):
+        g = grids[rgid]
+        ijk = _interp_points(g)
+        pts = _points_of(g, ijk)
+        dg, c, f = find_donors(grids, rgid, pts, order)
+        parts.append((rgid, ijk, dg, c, f))
+    interp = _assemble(grids, parts)
+    check_explicit_interp3(grids, interp)
+    return grids, interp
+
+
+def box_in_box(nb=12, ni=10, box=1.0, inner=0.45, hole=0.25):
+    """Two Cartesian grids: background [-box, box]^3 (Dirichlet, nb^3) with a cubic hole
+    |x|_inf < hole, and an inner box [-inner, inner]^3 (ni^3) whose faces are
+    interpolation points.  A small overset grid for brute-force checks."""
+    B = cartesian_grid3("background", (nb,) * 3, (-box,) * 3, (box,) * 3, [BC_DIRICHLET] * 6)
+    I = cartesian_grid3("inner", (ni,) * 3, (-inner,) * 3, (inner,) * 3, [BC_NONE] * 6)
+    x = -box + B.h[0] * np.arange(nb)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    inside = np.maximum(np.maximum(abs(X), abs(Y)), abs(Z)) < hole
+    active = ~inside
+    near = np.zeros_like(active)
+    near[1:] |= active[:-1]
+    near[:-1] |= active[1:]
+    near[:, 1:] |= active[:, :-1]
+    near[:, :-1] |= active[:, 1:]
+    near[:, :, 1:] |= active[:, :, :-1]
+    near[:, :, :-1] |= active[:, :, 1:]
+    B.mask[inside & near] = INTERP
+    B.mask[inside & ~near] = UNUSED
+    I.mask[:, :, 0] = I.mask[:, :, -1] = INTERP
+    I.mask[:, 0, :] = I.mask[:, -1, :] = INTERP
+    I.mask[0, :, :] = I.mask[-1, :, :] = INTERP
+    grids = [B, I]
+    parts = []
+    for rgid, order in ((0, (1,)), (1, (0,))):
+        g = grids[rgid]
+        ijk = _interp_points(g)
+        pts = _points_of(g, ijk)
+        dg, c, f = find_donors(grids, rgid, pts, order)
+        parts.append((rgid, ijk, dg, c, f))
+    interp = _assemble(grids, parts)
+    check_explicit_interp3(grids, interp)
+    return grids, interp
+
+
+# ----------------------------------------------------------------------------------
+# Sources and problems
+# ----------------------------------------------------------------------------------
+
+def gaussian3(g, x0, amp=1.0, b=200.0):
+    """f(x) = amp exp(-b |x - x0|^2) on the points of g (compact (n2, n1, n0))."""
+    out = np.empty((g.n[2], g.n[1], g.n[0]))
+    for k in range(g.n[2]):
+        X = g.coords(k)
+        out[k] = amp * np.exp(-b * ((X[0] - x0[0]) ** 2 + (X[1] - x0[1]) ** 2 +
+                                    (X[2] - x0[2]) ** 2))
+    return out
+
+
+def _seeded_point(rng, lo, hi, rmin):
+    while True:
+        p = rng.uniform(lo, hi, size=3)
+        if np.linalg.norm(p) >= rmin:
+            return p
+
+
+def sphere_problem(nb=320, nphi=256, nth=128, nr=24, npatch=96, omega=30.0, seed=0,
+                   width=0.3, r_hole=0.65, patch_deg=24.0, b=200.0):
+    """Sphere-in-box: Gaussian point source seeded in the background away from the
+    sphere.  Coarse test grids need a wider shell and a larger hole radius so that every
+    receiver still has a full donor stencil."""
+    rng = np.random.default_rng(seed)
+    grids, interp = sphere_in_box(nb, nphi, nth, nr, npatch, width=width, r_hole=r_hole,
+                                  patch_deg=patch_deg)
+    x0 = _seeded_point(rng, -1.5, 1.5, 1.0)
+    f = [gaussian3(g, x0, 1.0, b) for g in grids]
+    return Problem3(grids, interp, omega, f,
+                    name=f"sphere-in-box-{nb}^3+{nphi}x{nth}x{nr}+2x{npatch}^2x{nr}-o2",
+                    meta=dict(source=x0.tolist(), seed=seed))
+
+
+def unit_cube_problem(n=24, omega=10.0, seed=0, bc=BC_DIRICHLET, b=200.0):
+    """One Cartesian grid on [0, 1]^3 with n^3 points, Gaussian at x0 ~ U[0.3, 0.7]^3."""
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(0.3, 0.7, size=3)
+    g = cartesian_grid3("cube", (n, n, n), (0.0,) * 3, (1.0,) * 3, [bc] * 6)
+    return Problem3([g], Interp3.empty(), omega, [gaussian3(g, x0, 1.0, b)],
+                    name=f"unit-cube-{n}^3", meta=dict(source=x0.tolist(), seed=seed))
+
+
+def box_in_box_problem(nb=12, ni=10, omega=6.0, seed=0, b=20.0):
+    rng = np.random.default_rng(seed)
+    grids, interp = box_in_box(nb, ni)
+    x0 = _seeded_point(rng, -0.7, 0.7, 0.5)
+    f = [gaussian3(g, x0, 1.0, b) for g in grids]
+    return Problem3(grids, interp, omega, f, name=f"box-in-box-{nb}^3+{ni}^3",
+                    meta=dict(source=x0.tolist(), seed=seed))
+
+
+def random_state3(problem, seed):
+    """A seeded random vector on the active points (zero on unused points)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for g in problem.grids:
+        v = rng.standard_normal(g.mask.shape)
+        v[g.mask == UNUSED] = 0.0
+        out.append(v.ravel())
+    return np.concatenate(out)
