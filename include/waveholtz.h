@@ -127,6 +127,58 @@ typedef struct {
   const double *wx, *wy;
 } wh_interp_desc;
 
+/* Three-dimensional grids (second order, Sec. 3 in three space dimensions).  A context
+ * takes either two-dimensional grids (wh_add_grid / wh_set_interp) or three-dimensional ones
+ * (wh_add_grid3 / wh_set_interp3), fixed by the first grid added; 3D contexts need
+ * opt.order = 2 and hold one instance.  Compact 3D vectors hold n0*n1*n2 values per grid
+ * with axis 0 fastest (index (k*n1 + j)*n0 + i); the ghost width is 1 on non-periodic axes
+ * and 0 on periodic ones, and extended arrays cover [-g_a, n_a + g_a) per axis in the same
+ * order.  Sides are [axis0-lo, axis0-hi, axis1-lo, axis1-hi, axis2-lo, axis2-hi].
+ *   n[3]    points per axis (boundary points included; a periodic axis lists each point
+ *           once); n >= 5 on non-periodic axes, >= 3 on periodic ones.
+ *   kind    WH_CARTESIAN (h physical) or WH_CURVILINEAR (h the parameter spacing).
+ *   bc[6]   per-side WH_BC_*; periodic sides come in pairs.  Discretization points may lie
+ *           on a non-periodic side only if it is a Neumann side, and their inward neighbour
+ *           must be a discretization or Dirichlet point.
+ *   ortho   bit mask of axis pairs whose grid lines are orthogonal: bit 0 (0,1), bit 1
+ *           (0,2), bit 2 (1,2).  The mixed term 2 a_kl u_{r_k r_l} of such a pair is dropped
+ *           (a_kl = 0).  The normal axis of a Neumann side must be orthogonal to the other
+ *           two (the centred rule W_{-1} = W_{+1} is then the normal derivative).  Ignored
+ *           on Cartesian grids.
+ *   mask    n0*n1*n2 int8 point classes (WH_UNUSED ... WH_DIRICHLET).  A discretization
+ *           point's stencil (the 7-point cross and the edge points of non-orthogonal pairs)
+ *           must read no unused point.
+ *   rx      curvilinear: 9 extended arrays, array 3k+m = dr_k/dx_m.
+ *   c2      n0*n1*n2 values of c(x)^2 > 0, or NULL for c = 1.
+ * Host pointers, copied during the call.  Errors: WH_ERR_ARG (bad sizes, codes, spacing,
+ * orthogonality of a Neumann axis), WH_ERR_GRID (stencils reading unused points, Neumann
+ * inward neighbours), WH_ERR_STATE (a two-dimensional context). */
+typedef struct {
+  int32_t n[3];
+  int32_t kind;
+  int32_t bc[6];
+  int32_t ortho;
+  int32_t instance;  /* must be 0 */
+  double h[3];
+  const int8_t *mask;
+  const double *rx;
+  const double *c2;
+} wh_grid3_desc;
+
+/* Three-dimensional interpolation data (Sec. 3.1): receiver k of grid recv_grid[k] at
+ * (recv_i, recv_j, recv_k) takes sum_{a,b,c} wx[k][a] wy[k][b] wz[k][c]
+ * u_donor(i0 + a, j0 + b, k0 + c), a, b, c = 0..2, from grid donor_grid[k] with lower corner
+ * (donor_i0, donor_j0, donor_k0), wrapping on periodic axes.  Every donor must be a
+ * WH_DISC or WH_DIRICHLET point (explicit interpolation), every receiver a WH_INTERP point,
+ * and each WH_INTERP point listed exactly once (else WH_ERR_GRID).  Host pointers; wx, wy,
+ * wz are [n][3] FP64. */
+typedef struct {
+  int64_t n;
+  const int32_t *recv_grid, *recv_i, *recv_j, *recv_k;
+  const int32_t *donor_grid, *donor_i0, *donor_j0, *donor_k0;
+  const double *wx, *wy, *wz;
+} wh_interp3_desc;
+
 /* Time setup of one frequency (Recipe OmegaTildeExplicit, Eq. alphad). */
 typedef struct {
   double omega;      /* requested frequency */
@@ -175,6 +227,15 @@ wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *grid, int32_t *grid_id);
 /* Set the interpolation data for all receivers (replaces earlier data).  Validated
  * against the masks: WH_ERR_GRID on any violation. */
 wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *interp);
+/* Add a three-dimensional grid / set three-dimensional interpolation data (see
+ * wh_grid3_desc, wh_interp3_desc).  wh_set_forcing, wh_prepare, wh_iterate,
+ * wh_iterate_host, wh_solve, wh_dot, wh_profile_kernels and wh_get_time_info work on 3D
+ * contexts unchanged; batches, differentiation, wh_set_coefficient and the launch tuning
+ * calls return WH_ERR_STATE there.  One 3D iteration is an input kernel, a CUDA graph of
+ * 2M + 1 kernels (level-0 ghost rules and interpolation, then per step the march and the
+ * next level's ghost rules and interpolation) and an output kernel. */
+wh_status wh_add_grid3(wh_ctx *ctx, const wh_grid3_desc *grid, int32_t *grid_id);
+wh_status wh_set_interp3(wh_ctx *ctx, const wh_interp3_desc *interp);
 
 /* Forcing f(x) of grid grid_id (host, n0*n1): the right-hand side of
  * c^2 Lap u + omega^2 u = f; the scheme applies -f cos(omega_e t). */

@@ -1,4 +1,4 @@
-"""Build libwaveholtz.so in-tree for sm_103a (GB300) with nvcc, two units in parallel."""
+"""Build libwaveholtz.so in-tree for sm_103a (GB300) with nvcc, the units in parallel."""
 from __future__ import annotations
 
 import os
@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwaveholtz.so")
-SOURCES = ["wh_kernels.cu", "wh_api.cu", "wh_noalloc.cu"]
+SOURCES = ["wh_kernels.cu", "wh_api.cu", "wh_noalloc.cu", "wh_kernels3.cu", "wh_api3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

@@ -1,0 +1,106 @@
+// wh3_internal.h -- the three-dimensional (second-order) path of libwaveholtz: device data
+// structures, kernel launchers and the host context (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/waveholtz.h"
+
+namespace wh3 {
+
+// Stencil storage of a 3D grid in the march kernel.
+enum Stencil3 : int32_t {
+  kConst7 = 0,   // Cartesian grid, c = 1: four constant weights in Grid3Dev::cw
+  kPoint7 = 1,   // per-point weights on the 7-point cross (all axis pairs orthogonal, or c(x))
+  kPoint19 = 2   // per-point weights on the 19-point box (a non-orthogonal axis pair)
+};
+// Per-point weight planes, in this order: centre (with the "2"), then the face neighbours
+// -x +x -y +y -z +z, then (kPoint19) the edge neighbours of pairs (x,y), (x,z), (y,z), each
+// as (-,-) (+,-) (-,+) (+,+).
+constexpr int kNw7 = 7, kNw19 = 19;
+// Coefficient planes of curvilinear grids (c^2 folded in).
+enum { kA00 = 0, kA11, kA22, kA01, kA02, kA12, kB0, kB1, kB2, kNcoef };
+
+// March block: 32 x 8 threads, each marching kTZ points along axis 2.
+constexpr int kTX = 32, kTY = 8, kTZ = 8;
+
+// One component grid in device memory.  Extended arrays (ghosts included, ghost width 1 on
+// non-periodic axes) are stored with axis 0 fastest: (i, j, k) is at
+// base + ((k + g2) * e1 + (j + g1)) * e0 + (i + g0).
+struct Grid3Dev {
+  int32_t n0, n1, n2;
+  int32_t g0, g1, g2;
+  int32_t e0, e1, e2;
+  int32_t per;      // bit a: axis a periodic
+  int32_t stencil;  // Stencil3
+  int32_t nw;       // weight planes (point stencils)
+  int32_t kind;     // WH_CARTESIAN / WH_CURVILINEAR
+  int32_t ortho;    // orthogonal axis pairs: bit 0 (0,1), bit 1 (0,2), bit 2 (1,2)
+  int64_t base;     // offset of the extended array in the state arrays
+  int64_t ext;      // e0 * e1 * e2
+  int64_t cbase;    // offset in compact vectors
+  int64_t wbase;    // offset of weight plane 0 (plane stride ext)
+  int64_t kbase;    // offset of coefficient plane 0 (plane stride ext), curvilinear only
+  int64_t rbase;    // offset of metric plane 0 (9 planes, stride ext), curvilinear only
+  double h[3];
+  double cw[4];     // kConst7: centre, axis-0, axis-1, axis-2 neighbour weights (dt^2 folded)
+  float cwf[4];     // the same rounded to FP32
+};
+
+// One march tile: 32 x 8 points of the (axis 0, axis 1) plane, kTZ planes deep.
+struct Tile3 {
+  int32_t grid, i0, j0, k0;
+};
+
+// Per-step tables of the prepared frequency.
+struct Tab3 {
+  const double *fc;  // dt^2 cos(omega_e t^n), n = 0..M
+  const double *wf;  // filter weights of level n
+  const float *fcf;  // fc rounded to FP32
+  double dt2h;       // dt^2 / 2
+  float dt2hf;
+};
+
+// Launchers (wh_kernels3.cu).  T is double unless fp32; void pointers carry T arrays.
+void launch_coef3(cudaStream_t s, const Grid3Dev *grids, int gidx, const Grid3Dev &G,
+                  const int8_t *mask, const double *rx, const double *c2, double *coef,
+                  unsigned long long *smax);
+void launch_weight3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int gidx,
+                    const Grid3Dev &G, const int8_t *mask, const double *coef, const double *c2,
+                    void *Wt, double dt2);
+void launch_init3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int ngrids,
+                  int64_t max_ext, const int8_t *mask, const double *v, void *W0, double *V,
+                  const double *wf);
+void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
+                   const Tile3 *tiles, const int8_t *mask, const void *Wn, void *Wout,
+                   const void *F, const void *Wt, double *V, Tab3 tab, int n, double fs);
+void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
+                    const int64_t *ridx, const int32_t *didx, const double *dw,
+                    const int32_t *gdst, const int32_t *gsrc, void *W, double *V,
+                    const double *wf, int level);
+void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
+                    const double *V, double *vout);
+void launch_to_precision(bool fp32, cudaStream_t s, const double *src, void *dst, int64_t n);
+
+// Host context of a three-dimensional problem (wh_api3.cu).
+struct Ctx3;
+Ctx3 *create();
+void destroy(Ctx3 *c);
+wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std::string &err);
+wh_status set_interp(Ctx3 *c, const wh_interp3_desc *d, std::string &err);
+wh_status set_forcing(Ctx3 *c, int32_t gid, const double *f, std::string &err);
+// Prepare one frequency: upload (first time), coefficients, CFL bound, time tables, stencil
+// weights; with fp32 also the FP32 march arrays.  Returns the time setup and sizes.
+wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
+                  wh_time_info *ti, int64_t *ncompact, int64_t *nactive, std::string &err);
+// v_out = W_h(v_in, f or 0) on the device with the FP64 or the FP32 march.
+wh_status iterate(Ctx3 *c, bool fp32, int forcing, const double *vin, double *vout,
+                  cudaStream_t s, int64_t *launches, std::string &err);
+int ngrids(const Ctx3 *c);
+// Per-kernel device time of one iteration (march, gather, init + finish), milliseconds.
+wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int32_t *counts,
+                  std::string &err);
+
+}  // namespace wh3

@@ -22,6 +22,7 @@
 
 #include "../../include/waveholtz.h"
 #include "wh_internal.h"
+#include "wh3_internal.h"
 
 using namespace wh;
 
@@ -51,6 +52,9 @@ struct MarchSet {
 
 struct wh_ctx {
   wh_options opt{};
+  // 0 until the first grid is added, then 2 or 3; three-dimensional problems live in c3
+  int dim = 0;
+  wh3::Ctx3 *c3 = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   std::string err;
@@ -1041,6 +1045,9 @@ wh_status iterate_persistent(wh_ctx *ctx, int forcing, const double *vin, double
 
 wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vout) {
   forcing = forcing ? 1 : 0;
+  if (ctx->dim == 3)
+    return wh3::iterate(ctx->c3, ctx->active == 1, forcing, vin, vout, ctx->stream,
+                        &ctx->launches, ctx->err);
   if (ctx->persistent) return iterate_persistent(ctx, forcing, vin, vout);
   if (wh_status st = check_timeout(ctx, false)) return st;
   if (!ctx->set[ctx->active].gexec[forcing]) {
@@ -1717,6 +1724,7 @@ void wh_destroy(wh_ctx *ctx) {
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   if (ctx->err_ev) cudaEventDestroy(ctx->err_ev);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  wh3::destroy(ctx->c3);
   delete ctx;
 }
 
@@ -1736,6 +1744,7 @@ wh_status wh_set_stream(wh_ctx *ctx, void *stream) {
 
 wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *gd, int32_t *grid_id) {
   if (!ctx || !gd || !gd->mask) return fail(ctx, WH_ERR_ARG, "null grid description");
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "the context holds three-dimensional grids");
   const int order = ctx->opt.order;
   const int *bc = gd->bc;
   for (int s = 0; s < 4; ++s)
@@ -1794,14 +1803,37 @@ wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *gd, int32_t *grid_id) {
       if (!(v > 0) || !std::isfinite(v)) return fail(ctx, WH_ERR_ARG, "c^2 must be positive");
   }
   ctx->grids.push_back(std::move(H));
+  ctx->dim = 2;
   ctx->dirty = true;
   ctx->prepared = false;
   if (grid_id) *grid_id = (int32_t)ctx->grids.size() - 1;
   return WH_OK;
 }
 
+wh_status wh_add_grid3(wh_ctx *ctx, const wh_grid3_desc *gd, int32_t *grid_id) {
+  if (!ctx) return WH_ERR_ARG;
+  if (ctx->dim == 2) return fail(ctx, WH_ERR_STATE, "the context holds two-dimensional grids");
+  if (!ctx->c3 && !(ctx->c3 = wh3::create())) return fail(ctx, WH_ERR_NOMEM, "out of memory");
+  wh_status st = wh3::add_grid(ctx->c3, gd, ctx->opt.order, grid_id, ctx->err);
+  if (st) return st;
+  ctx->dim = 3;
+  ctx->prepared = false;
+  return WH_OK;
+}
+
+wh_status wh_set_interp3(wh_ctx *ctx, const wh_interp3_desc *it) {
+  if (!ctx) return WH_ERR_ARG;
+  if (ctx->dim != 3 || !ctx->c3)
+    return fail(ctx, WH_ERR_STATE, "add three-dimensional grids first");
+  wh_status st = wh3::set_interp(ctx->c3, it, ctx->err);
+  if (st) return st;
+  ctx->prepared = false;
+  return WH_OK;
+}
+
 wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *it) {
   if (!ctx || !it || it->n < 0) return fail(ctx, WH_ERR_ARG, "null interpolation data");
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "use wh_set_interp3 on a 3D context");
   const int w = ctx->opt.order + 1;
   const int64_t n = it->n;
   if (n > 0 && (!it->recv_grid || !it->recv_i || !it->recv_j || !it->donor_grid ||
@@ -1832,6 +1864,11 @@ wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *it) {
 }
 
 wh_status wh_set_forcing(wh_ctx *ctx, int32_t gid, const double *f) {
+  if (ctx && ctx->dim == 3) {
+    if (!f) return fail(ctx, WH_ERR_ARG, "null forcing");
+    ctx->prepared = false;
+    return wh3::set_forcing(ctx->c3, gid, f, ctx->err);
+  }
   if (!ctx || !f || gid < 0 || gid >= (int)ctx->grids.size())
     return fail(ctx, WH_ERR_ARG, "bad forcing arguments");
   HostGrid &H = ctx->grids[gid];
@@ -2001,9 +2038,42 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   return WH_OK;
 }
 
+// A three-dimensional context: everything below the solvers lives in wh3.
+static wh_status prepare3(wh_ctx *ctx, double omega) {
+  wh_status st;
+  if ((st = ensure_stream(ctx))) return st;
+  drop_graphs(ctx);
+  ctx->prepared = false;
+  wh_time_info ti{};
+  int64_t nc = 0, na = 0;
+  if ((st = wh3::prepare(ctx->c3, ctx->opt, omega, ctx->stream, &ti, &nc, &na, ctx->err)))
+    return st;
+  if (ctx->ncompact != nc) {  // solver workspace is sized by the compact length
+    dfree(ctx, &ctx->d_work);
+    dfree(ctx, &ctx->d_q);
+    ctx->q_cap = 0;
+  }
+  ctx->ncompact = nc;
+  ctx->nactive = na;
+  ctx->ti = ti;
+  ctx->iti.assign(1, ti);
+  ctx->ninst = 1;
+  ctx->maxM = ti.M;
+  ctx->err_pending = false;
+  ctx->prepared = true;
+  use_set(ctx, default_set(ctx));
+  return WH_OK;
+}
+
 wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
   if (!ctx) return WH_ERR_ARG;
   if (!(omega > 0) || !std::isfinite(omega)) return fail(ctx, WH_ERR_ARG, "omega must be > 0");
+  if (ctx->dim == 3) {
+    wh_status st = prepare3(ctx, omega);
+    if (st) return st;
+    if (info) *info = ctx->ti;
+    return WH_OK;
+  }
   if (ctx->grids.empty()) return fail(ctx, WH_ERR_STATE, "no grids");
   const int K = ctx->grids.back().d.instance + 1;
   std::vector<double> om(K, omega);
@@ -2015,6 +2085,7 @@ wh_status wh_prepare(wh_ctx *ctx, double omega, wh_time_info *info) {
 
 wh_status wh_prepare_batch(wh_ctx *ctx, const double *omegas, wh_time_info *infos) {
   if (!ctx || !omegas) return fail(ctx, WH_ERR_ARG, "null omegas");
+  if (ctx->dim == 3) return wh_prepare(ctx, omegas[0], infos);
   if (ctx->grids.empty()) return fail(ctx, WH_ERR_STATE, "no grids");
   wh_status st = prepare_instances(ctx, omegas);
   if (st) return st;
@@ -2187,6 +2258,7 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
                          wh_stats *stats) {
   if (!ctx || !u || !(tol > 0) || max_it < 1 || restart < 1 || restart > 4000)
     return fail(ctx, WH_ERR_ARG, "bad wh_solve_batch arguments");
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "3D contexts hold one instance: wh_solve");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = ctx->ncompact;
@@ -2302,6 +2374,8 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
 }
 
 static wh_status adj_check(wh_ctx *ctx) {
+  if (ctx->dim == 3)
+    return fail(ctx, WH_ERR_STATE, "differentiation is not available on 3D contexts");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   if (ctx->ninst != 1) return fail(ctx, WH_ERR_ARG, "differentiation needs a single instance");
   return WH_OK;
@@ -2393,6 +2467,8 @@ wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, 
 }
 
 wh_status wh_set_coefficient(wh_ctx *ctx, int32_t gid, const double *c2) {
+  if (ctx && ctx->dim == 3)
+    return fail(ctx, WH_ERR_STATE, "3D contexts take c(x)^2 in wh_add_grid3");
   if (!ctx || gid < 0 || gid >= (int)ctx->grids.size())
     return fail(ctx, WH_ERR_ARG, "bad wh_set_coefficient arguments");
   HostGrid &H = ctx->grids[gid];
@@ -2411,6 +2487,7 @@ wh_status wh_set_coefficient(wh_ctx *ctx, int32_t gid, const double *c2) {
 
 wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *t) {
   if (!ctx || !t) return fail(ctx, WH_ERR_ARG, "bad wh_set_tuning arguments");
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "3D contexts have one launch layout");
   auto tri = [](int32_t v) { return v >= -1 && v <= 1; };
   if (!tri(t->fold_gather) || !tri(t->tile_tickets) || !tri(t->tma) || !tri(t->pdl) ||
       (t->launch_mode != -1 && t->launch_mode != WH_LAUNCH_GRAPH &&
@@ -2429,6 +2506,7 @@ wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *t) {
 
 wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out) {
   if (!ctx || reps < 1 || reps > 1000) return fail(ctx, WH_ERR_ARG, "bad wh_autotune arguments");
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "3D contexts have one launch layout");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   wh_status st;
   const int64_t n = ctx->ncompact;
@@ -2514,6 +2592,13 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
   if (!ctx || !ms || !counts || reps < 1 || reps > 10000)
     return fail(ctx, WH_ERR_ARG, "bad wh_profile_kernels arguments");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  if (ctx->dim == 3) {
+    for (int k = 0; k < 4; ++k) {
+      ms[k] = 0.0;
+      counts[k] = k < 2 ? 0 : 1;
+    }
+    return wh3::profile(ctx->c3, ctx->active == 1, ctx->stream, reps, ms, counts, ctx->err);
+  }
   const int order = ctx->opt.order;
   const bool f32 = is_fp32(ctx);
   cudaStream_t s = ctx->stream;

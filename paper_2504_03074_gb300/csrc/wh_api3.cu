@@ -1,0 +1,728 @@
+// wh_api3.cu -- host side of the three-dimensional, second-order path of libwaveholtz.
+//
+// Validates and uploads a 3D overset grid description (component grids with masks, metrics
+// and c(x)^2; explicit 3 x 3 x 3 interpolation), prepares one frequency (coefficients and
+// the CFL bound on the device, Recipe OmegaTildeExplicit, alpha_d of Eq. alphad, stencil
+// weights, per-step tables) and issues one WaveHoltz iteration as init + a CUDA graph of
+// 2M + 1 kernels + output.  The solvers of wh_api.cu (fixed-point iteration, GMRES, the
+// two-phase FP32 solve) drive it through iterate().
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "wh3_internal.h"
+
+namespace wh3 {
+namespace {
+
+struct HostGrid3 {
+  wh_grid3_desc d{};
+  std::vector<int8_t> mask;  // compact (n2, n1, n0)
+  std::vector<double> rx;    // 9 extended planes
+  std::vector<double> c2;    // compact, empty for c = 1
+  std::vector<double> f;     // compact
+  int g[3] = {1, 1, 1};
+  int e[3] = {0, 0, 0};
+};
+
+}  // namespace
+
+struct Ctx3 {
+  std::vector<HostGrid3> grids;
+  int64_t nrecv = 0;
+  std::vector<int32_t> rg, ri, rj, rk, dg, di, dj, dk;
+  std::vector<double> wx, wy, wz;
+  bool dirty = true, f_dirty = true, fp32_ready = false;
+  std::vector<Grid3Dev> hg;
+  std::vector<Tile3> tiles;
+  int64_t total = 0, ncompact = 0, nactive = 0, max_ext = 0, max_compact = 0, nghost = 0;
+  int64_t w_total = 0, coef_total = 0;
+  std::vector<void *> allocs;
+  Grid3Dev *d_grids = nullptr;
+  Tile3 *d_tiles = nullptr;
+  int8_t *d_mask = nullptr;
+  double *d_Wa = nullptr, *d_Wb = nullptr, *d_F = nullptr, *d_V = nullptr, *d_c2 = nullptr;
+  double *d_rx = nullptr, *d_coef = nullptr, *d_Wt = nullptr;
+  float *d_Wa32 = nullptr, *d_Wb32 = nullptr, *d_F32 = nullptr, *d_Wt32 = nullptr;
+  int64_t *d_ridx = nullptr;
+  int32_t *d_didx = nullptr, *d_gdst = nullptr, *d_gsrc = nullptr;
+  double *d_dw = nullptr;
+  double *d_tabs = nullptr;
+  float *d_ftabs = nullptr;
+  int64_t tabs_cap = 0;
+  unsigned long long *d_smax = nullptr;
+  int M = 0;
+  double dt2 = 0.0;
+  Tab3 tab{};
+  cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [fp32][forcing]
+};
+
+namespace {
+
+wh_status fail3(std::string &err, wh_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  err = buf;
+  return s;
+}
+
+#define CK3(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail3(err, WH_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+template <typename T>
+wh_status alloc3(Ctx3 *c, T **p, size_t n, std::string &err) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess)
+    return fail3(err, WH_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T),
+                 cudaGetErrorString(e));
+  c->allocs.push_back((void *)*p);
+  e = cudaMemset(*p, 0, n * sizeof(T));
+  if (e != cudaSuccess) return fail3(err, WH_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return WH_OK;
+}
+
+void drop_graphs3(Ctx3 *c) {
+  for (auto &row : c->gexec)
+    for (auto &g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+void free_all(Ctx3 *c) {
+  drop_graphs3(c);
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->d_grids = nullptr;
+  c->d_tiles = nullptr;
+  c->d_mask = nullptr;
+  c->d_Wa = c->d_Wb = c->d_F = c->d_V = c->d_c2 = c->d_rx = c->d_coef = c->d_Wt = nullptr;
+  c->d_Wa32 = c->d_Wb32 = c->d_F32 = c->d_Wt32 = nullptr;
+  c->d_ridx = nullptr;
+  c->d_didx = c->d_gdst = c->d_gsrc = nullptr;
+  c->d_dw = nullptr;
+  c->d_tabs = nullptr;
+  c->d_ftabs = nullptr;
+  c->tabs_cap = 0;
+  c->d_smax = nullptr;
+  c->fp32_ready = false;
+}
+
+inline bool periodic(const HostGrid3 &G, int a) { return G.d.bc[2 * a] == WH_BC_PERIODIC; }
+
+// compact index of (i, j, k)
+inline int64_t cidx(const HostGrid3 &G, int i, int j, int k) {
+  return ((int64_t)k * G.d.n[1] + j) * G.d.n[0] + i;
+}
+
+// extended index (relative to the grid's base) of (i, j, k), wrapping periodic axes;
+// -1 outside the extended range
+inline int64_t eidx(const HostGrid3 &G, int i, int j, int k) {
+  int ix[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (periodic(G, a)) ix[a] = ((ix[a] % G.d.n[a]) + G.d.n[a]) % G.d.n[a];
+    if (ix[a] < -G.g[a] || ix[a] >= G.d.n[a] + G.g[a]) return -1;
+  }
+  return ((int64_t)(ix[2] + G.g[2]) * G.e[1] + (ix[1] + G.g[1])) * G.e[0] + (ix[0] + G.g[0]);
+}
+
+// mask at (i, j, k) with wrap; -1 outside the grid's points (ghosts included)
+inline int mask_at(const HostGrid3 &G, int i, int j, int k) {
+  int ix[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (periodic(G, a)) ix[a] = ((ix[a] % G.d.n[a]) + G.d.n[a]) % G.d.n[a];
+    if (ix[a] < 0 || ix[a] >= G.d.n[a]) return -1;
+  }
+  return G.mask[cidx(G, ix[0], ix[1], ix[2])];
+}
+
+int pair_bit(int a, int b) { return 1 << (std::min(a, b) + std::max(a, b) - 1); }
+
+// Structural checks of one grid's discretization points: a point on a non-periodic side
+// must lie on a Neumann side, with a discretization or Dirichlet point inward; every grid
+// point its stencil reads (the 7-point cross, plus the edges of non-orthogonal pairs) must
+// be in use.
+wh_status check_grid(const HostGrid3 &G, std::string &err) {
+  const int n0 = G.d.n[0], n1 = G.d.n[1], n2 = G.d.n[2];
+  const bool curv = G.d.kind == WH_CURVILINEAR;
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n0; ++i) {
+        if (G.mask[cidx(G, i, j, k)] != WH_DISC) continue;
+        const int ix[3] = {i, j, k};
+        for (int a = 0; a < 3; ++a) {
+          if (periodic(G, a)) continue;
+          for (int hi = 0; hi < 2; ++hi) {
+            if (ix[a] != (hi ? G.d.n[a] - 1 : 0)) continue;
+            if (G.d.bc[2 * a + hi] != WH_BC_NEUMANN)
+              return fail3(err, WH_ERR_GRID,
+                           "discretization point (%d,%d,%d) lies on a side without a Neumann "
+                           "condition", i, j, k);
+            int in[3] = {i, j, k};
+            in[a] += hi ? -1 : 1;
+            const int m = mask_at(G, in[0], in[1], in[2]);
+            if (m != WH_DISC && m != WH_DIRICHLET)
+              return fail3(err, WH_ERR_GRID,
+                           "the inward neighbour of Neumann boundary point (%d,%d,%d) is not a "
+                           "discretization or Dirichlet point", i, j, k);
+          }
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int s = -1; s <= 1; s += 2) {
+            int d[3] = {0, 0, 0};
+            d[a] = s;
+            const int m = mask_at(G, i + d[0], j + d[1], k + d[2]);
+            if (m == WH_UNUSED)
+              return fail3(err, WH_ERR_GRID,
+                           "the stencil of discretization point (%d,%d,%d) reads an unused point",
+                           i, j, k);
+          }
+        if (curv)
+          for (int a = 0; a < 3; ++a)
+            for (int b = a + 1; b < 3; ++b) {
+              if (G.d.ortho & pair_bit(a, b)) continue;
+              for (int sa = -1; sa <= 1; sa += 2)
+                for (int sb = -1; sb <= 1; sb += 2) {
+                  int d[3] = {0, 0, 0};
+                  d[a] = sa;
+                  d[b] = sb;
+                  const int m = mask_at(G, i + d[0], j + d[1], k + d[2]);
+                  if (m == WH_UNUSED)
+                    return fail3(err, WH_ERR_GRID,
+                                 "the stencil of discretization point (%d,%d,%d) reads an "
+                                 "unused point", i, j, k);
+                }
+            }
+      }
+  return WH_OK;
+}
+
+// Device layout: extended arrays of all grids in one state array (each starting on a
+// 32-element boundary), tiles, masks, metrics, c^2, forcing, interpolation lists, Neumann
+// ghost lists.
+wh_status build_layout(Ctx3 *c, std::string &err) {
+  free_all(c);
+  const int ng = (int)c->grids.size();
+  c->hg.assign(ng, Grid3Dev{});
+  c->tiles.clear();
+  int64_t base = 0, cbase = 0, wbase = 0, kbase = 0;
+  c->nactive = 0;
+  c->max_ext = c->max_compact = 0;
+  for (int g = 0; g < ng; ++g) {
+    HostGrid3 &H = c->grids[g];
+    Grid3Dev &D = c->hg[g];
+    D.n0 = H.d.n[0];
+    D.n1 = H.d.n[1];
+    D.n2 = H.d.n[2];
+    D.g0 = H.g[0];
+    D.g1 = H.g[1];
+    D.g2 = H.g[2];
+    D.e0 = H.e[0];
+    D.e1 = H.e[1];
+    D.e2 = H.e[2];
+    D.per = (periodic(H, 0) ? 1 : 0) | (periodic(H, 1) ? 2 : 0) | (periodic(H, 2) ? 4 : 0);
+    D.kind = H.d.kind;
+    D.ortho = H.d.kind == WH_CARTESIAN ? 7 : H.d.ortho;
+    if (H.d.kind == WH_CARTESIAN && H.c2.empty()) {
+      D.stencil = kConst7;
+      D.nw = 0;
+    } else if (D.ortho == 7) {
+      D.stencil = kPoint7;
+      D.nw = kNw7;
+    } else {
+      D.stencil = kPoint19;
+      D.nw = kNw19;
+    }
+    D.ext = (int64_t)D.e0 * D.e1 * D.e2;
+    D.base = base;
+    D.cbase = cbase;
+    D.wbase = wbase;
+    D.kbase = H.d.kind == WH_CURVILINEAR ? kbase : -1;
+    D.rbase = D.kbase;  // metrics use the same layout as the coefficients (9 planes)
+    for (int a = 0; a < 3; ++a) D.h[a] = H.d.h[a];
+    base += (D.ext + 31) / 32 * 32;
+    const int64_t np = (int64_t)D.n0 * D.n1 * D.n2;
+    cbase += np;
+    wbase += (int64_t)D.nw * D.ext;
+    if (H.d.kind == WH_CURVILINEAR) kbase += (int64_t)kNcoef * D.ext;
+    c->max_ext = std::max(c->max_ext, D.ext);
+    c->max_compact = std::max(c->max_compact, np);
+    for (int8_t m : H.mask) c->nactive += m != WH_UNUSED;
+    for (int k0 = 0; k0 < D.n2; k0 += kTZ)
+      for (int j0 = 0; j0 < D.n1; j0 += kTY)
+        for (int i0 = 0; i0 < D.n0; i0 += kTX) c->tiles.push_back(Tile3{g, i0, j0, k0});
+  }
+  c->total = base;
+  c->ncompact = cbase;
+  c->w_total = wbase;
+  c->coef_total = kbase;
+  if (c->total >= (int64_t)INT32_MAX)
+    return fail3(err, WH_ERR_GRID, "%lld extended points exceed 32-bit donor indices",
+                 (long long)c->total);
+  wh_status st;
+  if ((st = alloc3(c, &c->d_grids, ng, err)) || (st = alloc3(c, &c->d_tiles, c->tiles.size(), err)) ||
+      (st = alloc3(c, &c->d_mask, c->total, err)) || (st = alloc3(c, &c->d_Wa, c->total, err)) ||
+      (st = alloc3(c, &c->d_Wb, c->total, err)) || (st = alloc3(c, &c->d_F, c->total, err)) ||
+      (st = alloc3(c, &c->d_V, c->total, err)) || (st = alloc3(c, &c->d_c2, c->total, err)) ||
+      (st = alloc3(c, &c->d_rx, c->coef_total, err)) ||
+      (st = alloc3(c, &c->d_coef, c->coef_total, err)) ||
+      (st = alloc3(c, &c->d_Wt, c->w_total, err)) || (st = alloc3(c, &c->d_smax, 1, err)))
+    return st;
+  CK3(cudaMemcpy(c->d_tiles, c->tiles.data(), c->tiles.size() * sizeof(Tile3),
+                 cudaMemcpyHostToDevice));
+  // per grid: mask and c^2 over the extended extent, metrics
+  for (int g = 0; g < ng; ++g) {
+    const HostGrid3 &H = c->grids[g];
+    const Grid3Dev &D = c->hg[g];
+    std::vector<int8_t> m(D.ext, (int8_t)WH_UNUSED);
+    std::vector<double> c2(D.ext, 1.0);
+    for (int k = 0; k < D.n2; ++k)
+      for (int j = 0; j < D.n1; ++j)
+        for (int i = 0; i < D.n0; ++i) {
+          const int64_t q = eidx(H, i, j, k), p = cidx(H, i, j, k);
+          m[q] = H.mask[p];
+          if (!H.c2.empty()) c2[q] = H.c2[p];
+        }
+    CK3(cudaMemcpy(c->d_mask + D.base, m.data(), D.ext, cudaMemcpyHostToDevice));
+    CK3(cudaMemcpy(c->d_c2 + D.base, c2.data(), D.ext * sizeof(double), cudaMemcpyHostToDevice));
+    if (H.d.kind == WH_CURVILINEAR)
+      CK3(cudaMemcpy(c->d_rx + D.rbase, H.rx.data(), 9 * D.ext * sizeof(double),
+                     cudaMemcpyHostToDevice));
+  }
+  // interpolation: receiver index, 27 donor indices and weight products
+  const int64_t R = c->nrecv;
+  std::vector<int64_t> ridx(R > 0 ? R : 1);
+  std::vector<int32_t> didx(R > 0 ? R * 27 : 1);
+  std::vector<double> dw(R > 0 ? R * 27 : 1);
+  for (int64_t r = 0; r < R; ++r) {
+    const HostGrid3 &RG = c->grids[c->rg[r]];
+    ridx[r] = c->hg[c->rg[r]].base + eidx(RG, c->ri[r], c->rj[r], c->rk[r]);
+    const HostGrid3 &DG = c->grids[c->dg[r]];
+    const int64_t db = c->hg[c->dg[r]].base;
+    for (int cc = 0; cc < 3; ++cc)
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          const int u = cc * 9 + b * 3 + a;
+          didx[r * 27 + u] =
+              (int32_t)(db + eidx(DG, c->di[r] + a, c->dj[r] + b, c->dk[r] + cc));
+          dw[r * 27 + u] = c->wx[r * 3 + a] * c->wy[r * 3 + b] * c->wz[r * 3 + cc];
+        }
+  }
+  // Neumann ghosts next to discretization points
+  std::vector<int32_t> gdst, gsrc;
+  for (int g = 0; g < ng; ++g) {
+    const HostGrid3 &H = c->grids[g];
+    const int64_t b0 = c->hg[g].base;
+    for (int s = 0; s < 6; ++s) {
+      if (H.d.bc[s] != WH_BC_NEUMANN) continue;
+      const int a = s / 2, hi = s % 2, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+      for (int v = 0; v < H.d.n[t2]; ++v)
+        for (int u = 0; u < H.d.n[t1]; ++u) {
+          int ib[3], ig[3], in[3];
+          ib[t1] = ig[t1] = in[t1] = u;
+          ib[t2] = ig[t2] = in[t2] = v;
+          ib[a] = hi ? H.d.n[a] - 1 : 0;
+          ig[a] = hi ? H.d.n[a] : -1;
+          in[a] = hi ? H.d.n[a] - 2 : 1;
+          if (H.mask[cidx(H, ib[0], ib[1], ib[2])] != WH_DISC) continue;
+          gdst.push_back((int32_t)(b0 + eidx(H, ig[0], ig[1], ig[2])));
+          gsrc.push_back((int32_t)(b0 + eidx(H, in[0], in[1], in[2])));
+        }
+    }
+  }
+  c->nghost = (int64_t)gdst.size();
+  if (gdst.empty()) {
+    gdst.push_back(0);
+    gsrc.push_back(0);
+  }
+  if ((st = alloc3(c, &c->d_ridx, ridx.size(), err)) ||
+      (st = alloc3(c, &c->d_didx, didx.size(), err)) || (st = alloc3(c, &c->d_dw, dw.size(), err)) ||
+      (st = alloc3(c, &c->d_gdst, gdst.size(), err)) ||
+      (st = alloc3(c, &c->d_gsrc, gsrc.size(), err)))
+    return st;
+  CK3(cudaMemcpy(c->d_ridx, ridx.data(), ridx.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_didx, didx.data(), didx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_dw, dw.data(), dw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_gdst, gdst.data(), gdst.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_gsrc, gsrc.data(), gsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  c->dirty = false;
+  c->f_dirty = true;
+  return WH_OK;
+}
+
+wh_status upload_forcing(Ctx3 *c, std::string &err) {
+  for (size_t g = 0; g < c->grids.size(); ++g) {
+    const HostGrid3 &H = c->grids[g];
+    const Grid3Dev &D = c->hg[g];
+    std::vector<double> f(D.ext, 0.0);
+    if (!H.f.empty())
+      for (int k = 0; k < D.n2; ++k)
+        for (int j = 0; j < D.n1; ++j)
+          for (int i = 0; i < D.n0; ++i) f[eidx(H, i, j, k)] = H.f[cidx(H, i, j, k)];
+    CK3(cudaMemcpy(c->d_F + D.base, f.data(), D.ext * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  c->f_dirty = false;
+  c->fp32_ready = false;
+  return WH_OK;
+}
+
+// The body of one iteration after init: level-0 ghost rules + interpolation, then M steps.
+void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
+  void *Wa = fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa;
+  void *Wb = fp32 ? (void *)c->d_Wb32 : (void *)c->d_Wb;
+  const void *F = fp32 ? (const void *)c->d_F32 : (const void *)c->d_F;
+  const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
+  const double fs = forcing ? 1.0 : 0.0;
+  auto gather = [&](void *W, int level) {
+    launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_didx, c->d_dw, c->d_gdst,
+                   c->d_gsrc, W, c->d_V, c->tab.wf, level);
+  };
+  gather(Wa, 0);
+  for (int n = 0; n < c->M; ++n) {
+    void *cur = (n & 1) ? Wb : Wa;
+    void *oth = (n & 1) ? Wa : Wb;
+    launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth, F,
+                  Wt, c->d_V, c->tab, n, fs);
+    gather(oth, n + 1);
+  }
+}
+
+wh_status build_graph3(Ctx3 *c, bool fp32, int forcing, cudaStream_t s, std::string &err) {
+  cudaGraph_t graph = nullptr;
+  CK3(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  launch_steps(c, fp32, forcing, s);
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess) return fail3(err, WH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->gexec[fp32][forcing], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return fail3(err, WH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return WH_OK;
+}
+
+}  // namespace
+
+Ctx3 *create() { return new (std::nothrow) Ctx3(); }
+
+void destroy(Ctx3 *c) {
+  if (!c) return;
+  free_all(c);
+  delete c;
+}
+
+int ngrids(const Ctx3 *c) { return c ? (int)c->grids.size() : 0; }
+
+wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std::string &err) {
+  if (!d || !d->mask) return fail3(err, WH_ERR_ARG, "null grid description or mask");
+  if (order != 2) return fail3(err, WH_ERR_ARG, "three-dimensional grids need order 2");
+  if (d->instance != 0)
+    return fail3(err, WH_ERR_ARG, "three-dimensional contexts hold one instance");
+  if (d->kind != WH_CARTESIAN && d->kind != WH_CURVILINEAR)
+    return fail3(err, WH_ERR_ARG, "bad grid kind %d", d->kind);
+  if (d->kind == WH_CURVILINEAR && !d->rx)
+    return fail3(err, WH_ERR_ARG, "curvilinear grid without metrics");
+  if (d->ortho < 0 || d->ortho > 7) return fail3(err, WH_ERR_ARG, "ortho must be in [0, 7]");
+  if (c->grids.size() >= 64) return fail3(err, WH_ERR_ARG, "at most 64 grids");
+  for (int s = 0; s < 6; ++s)
+    if (d->bc[s] < WH_BC_NONE || d->bc[s] > WH_BC_PERIODIC)
+      return fail3(err, WH_ERR_ARG, "bad boundary code on side %d", s);
+  HostGrid3 H;
+  H.d = *d;
+  for (int a = 0; a < 3; ++a) {
+    const bool p0 = d->bc[2 * a] == WH_BC_PERIODIC, p1 = d->bc[2 * a + 1] == WH_BC_PERIODIC;
+    if (p0 != p1) return fail3(err, WH_ERR_ARG, "periodic sides must come in pairs");
+    if (d->n[a] < (p0 ? 3 : 5))
+      return fail3(err, WH_ERR_ARG, "axis %d: %d points (need >= %d)", a, d->n[a], p0 ? 3 : 5);
+    if (!(d->h[a] > 0) || !std::isfinite(d->h[a]))
+      return fail3(err, WH_ERR_ARG, "spacing of axis %d must be > 0", a);
+    H.g[a] = p0 ? 0 : 1;
+    H.e[a] = d->n[a] + 2 * H.g[a];
+  }
+  if (d->kind == WH_CURVILINEAR)
+    for (int s = 0; s < 6; ++s) {
+      if (d->bc[s] != WH_BC_NEUMANN) continue;
+      const int a = s / 2;
+      for (int b = 0; b < 3; ++b)
+        if (b != a && !(d->ortho & pair_bit(a, b)))
+          return fail3(err, WH_ERR_ARG,
+                       "a Neumann side's normal axis must be orthogonal to the other two");
+    }
+  const int64_t np = (int64_t)d->n[0] * d->n[1] * d->n[2];
+  const int64_t ext = (int64_t)H.e[0] * H.e[1] * H.e[2];
+  H.mask.assign(d->mask, d->mask + np);
+  for (int8_t m : H.mask)
+    if (m < WH_UNUSED || m > WH_DIRICHLET) return fail3(err, WH_ERR_ARG, "bad mask value %d", m);
+  if (d->kind == WH_CURVILINEAR) H.rx.assign(d->rx, d->rx + 9 * ext);
+  if (d->c2) {
+    H.c2.assign(d->c2, d->c2 + np);
+    for (double v : H.c2)
+      if (!(v > 0) || !std::isfinite(v)) return fail3(err, WH_ERR_ARG, "c^2 must be > 0");
+  }
+  wh_status st = check_grid(H, err);
+  if (st) return st;
+  c->grids.push_back(std::move(H));
+  c->dirty = true;
+  if (id) *id = (int32_t)c->grids.size() - 1;
+  return WH_OK;
+}
+
+wh_status set_interp(Ctx3 *c, const wh_interp3_desc *d, std::string &err) {
+  if (!d || d->n < 0) return fail3(err, WH_ERR_ARG, "bad interpolation description");
+  const int64_t n = d->n;
+  if (n > 0 && (!d->recv_grid || !d->recv_i || !d->recv_j || !d->recv_k || !d->donor_grid ||
+                !d->donor_i0 || !d->donor_j0 || !d->donor_k0 || !d->wx || !d->wy || !d->wz))
+    return fail3(err, WH_ERR_ARG, "null interpolation array");
+  const int ng = (int)c->grids.size();
+  std::vector<std::vector<int8_t>> seen(ng);
+  for (int g = 0; g < ng; ++g) seen[g].assign(c->grids[g].mask.size(), 0);
+  for (int64_t r = 0; r < n; ++r) {
+    const int g = d->recv_grid[r], dgid = d->donor_grid[r];
+    if (g < 0 || g >= ng || dgid < 0 || dgid >= ng)
+      return fail3(err, WH_ERR_GRID, "receiver %lld: bad grid index", (long long)r);
+    const HostGrid3 &RG = c->grids[g];
+    const int i = d->recv_i[r], j = d->recv_j[r], k = d->recv_k[r];
+    if (i < 0 || i >= RG.d.n[0] || j < 0 || j >= RG.d.n[1] || k < 0 || k >= RG.d.n[2])
+      return fail3(err, WH_ERR_GRID, "receiver %lld outside its grid", (long long)r);
+    const int64_t p = cidx(RG, i, j, k);
+    if (RG.mask[p] != WH_INTERP)
+      return fail3(err, WH_ERR_GRID, "receiver %lld is not an interpolation point", (long long)r);
+    if (seen[g][p]++)
+      return fail3(err, WH_ERR_GRID, "receiver %lld listed twice", (long long)r);
+    const HostGrid3 &DG = c->grids[dgid];
+    const int c0[3] = {d->donor_i0[r], d->donor_j0[r], d->donor_k0[r]};
+    for (int a = 0; a < 3; ++a)
+      if (!periodic(DG, a) && (c0[a] < 0 || c0[a] + 2 >= DG.d.n[a]))
+        return fail3(err, WH_ERR_GRID, "receiver %lld: donor stencil outside its grid",
+                     (long long)r);
+    for (int cc = 0; cc < 3; ++cc)
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          const int m = mask_at(DG, c0[0] + a, c0[1] + b, c0[2] + cc);
+          if (m != WH_DISC && m != WH_DIRICHLET)
+            return fail3(err, WH_ERR_GRID,
+                         "receiver %lld: a donor is not a discretization or Dirichlet point "
+                         "(explicit interpolation)", (long long)r);
+        }
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(d->wx[r * 3 + a]) || !std::isfinite(d->wy[r * 3 + a]) ||
+          !std::isfinite(d->wz[r * 3 + a]))
+        return fail3(err, WH_ERR_ARG, "receiver %lld: weight not finite", (long long)r);
+  }
+  for (int g = 0; g < ng; ++g)
+    for (size_t p = 0; p < seen[g].size(); ++p)
+      if (c->grids[g].mask[p] == WH_INTERP && !seen[g][p])
+        return fail3(err, WH_ERR_GRID, "grid %d: an interpolation point has no donor stencil", g);
+  auto cp = [n](std::vector<int32_t> &v, const int32_t *s) { v.assign(s, s + n); };
+  cp(c->rg, d->recv_grid);
+  cp(c->ri, d->recv_i);
+  cp(c->rj, d->recv_j);
+  cp(c->rk, d->recv_k);
+  cp(c->dg, d->donor_grid);
+  cp(c->di, d->donor_i0);
+  cp(c->dj, d->donor_j0);
+  cp(c->dk, d->donor_k0);
+  c->wx.assign(d->wx, d->wx + 3 * n);
+  c->wy.assign(d->wy, d->wy + 3 * n);
+  c->wz.assign(d->wz, d->wz + 3 * n);
+  c->nrecv = n;
+  c->dirty = true;
+  return WH_OK;
+}
+
+wh_status set_forcing(Ctx3 *c, int32_t gid, const double *f, std::string &err) {
+  if (gid < 0 || gid >= (int)c->grids.size() || !f)
+    return fail3(err, WH_ERR_ARG, "bad grid index or null forcing");
+  HostGrid3 &H = c->grids[gid];
+  H.f.assign(f, f + H.mask.size());
+  c->f_dirty = true;
+  return WH_OK;
+}
+
+wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
+                  wh_time_info *ti, int64_t *ncompact, int64_t *nactive, std::string &err) {
+  if (c->grids.empty()) return fail3(err, WH_ERR_STATE, "no grids");
+  for (const auto &H : c->grids)
+    for (int8_t m : H.mask)
+      if (m == WH_INTERP && c->nrecv == 0)
+        return fail3(err, WH_ERR_GRID, "interpolation points but no interpolation data");
+  // earlier iterations on the stream may still read the arrays rewritten below
+  CK3(cudaStreamSynchronize(s));
+  wh_status st;
+  if (c->dirty && (st = build_layout(c, err))) return st;
+  if (c->f_dirty && (st = upload_forcing(c, err))) return st;
+  drop_graphs3(c);
+  const int ng = (int)c->grids.size();
+  CK3(cudaMemcpy(c->d_grids, c->hg.data(), ng * sizeof(Grid3Dev), cudaMemcpyHostToDevice));
+  CK3(cudaMemsetAsync(c->d_smax, 0, sizeof(unsigned long long), s));
+  for (int g = 0; g < ng; ++g)
+    launch_coef3(s, c->d_grids, g, c->hg[g], c->d_mask, c->d_rx, c->d_c2, c->d_coef, c->d_smax);
+  CK3(cudaGetLastError());
+  unsigned long long bits = 0;
+  CK3(cudaMemcpyAsync(&bits, c->d_smax, sizeof bits, cudaMemcpyDeviceToHost, s));
+  CK3(cudaStreamSynchronize(s));
+  double smax;
+  std::memcpy(&smax, &bits, sizeof smax);
+  if (!(smax > 0) || !std::isfinite(smax))
+    return fail3(err, WH_ERR_GRID, "no discretization point");
+  // Eq. dtForCartesian at second order (C = 1), Recipe OmegaTildeExplicit, Eq. alphad
+  const double dtmax = opt.cfl / std::sqrt(smax);
+  int Nt = (int)std::ceil(2.0 * M_PI / (omega * dtmax));
+  if (Nt < 2) Nt = 2;
+  double dt = 2.0 / omega * std::sin(M_PI / Nt);
+  while (dt > dtmax) {
+    ++Nt;
+    dt = 2.0 / omega * std::sin(M_PI / Nt);
+  }
+  wh_time_info T{};
+  T.omega = omega;
+  T.dt = dt;
+  T.Nt = Nt;
+  T.M = opt.periods * Nt;
+  T.omega_e = 2.0 * M_PI / (Nt * dt);
+  T.alpha = opt.alpha_mode ? 0.5 : std::tan(T.omega_e * dt / 2) / std::tan(T.omega_e * dt);
+  T.dt_max = dtmax;
+  T.Tbar = T.M * dt;
+  T.n_active = c->nactive;
+  T.n_total = c->ncompact;
+  const int M = T.M;
+  c->M = M;
+  c->dt2 = dt * dt;
+  // tables: fc[0..M], wf[0..M]; fc rounded to FP32
+  const int64_t len = 2 * (int64_t)(M + 1);
+  if (c->tabs_cap < len) {
+    if ((st = alloc3(c, &c->d_tabs, len, err)) || (st = alloc3(c, &c->d_ftabs, M + 1, err)))
+      return st;
+    c->tabs_cap = len;
+  }
+  std::vector<double> tab(len);
+  std::vector<float> ftab(M + 1);
+  for (int n = 0; n <= M; ++n) {
+    const double cn = std::cos(T.omega_e * n * dt);
+    const double sig = (n == 0 || n == M) ? 0.5 : 1.0;
+    tab[n] = dt * dt * cn;
+    tab[(M + 1) + n] = (2.0 / M) * sig * (cn - T.alpha / 2.0);
+    ftab[n] = (float)tab[n];
+  }
+  CK3(cudaMemcpy(c->d_tabs, tab.data(), len * sizeof(double), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_ftabs, ftab.data(), (M + 1) * sizeof(float), cudaMemcpyHostToDevice));
+  c->tab.fc = c->d_tabs;
+  c->tab.wf = c->d_tabs + (M + 1);
+  c->tab.fcf = c->d_ftabs;
+  c->tab.dt2h = 0.5 * dt * dt;
+  c->tab.dt2hf = (float)(0.5 * dt * dt);
+  // constant weights (Cartesian, c = 1): centre 2 - 2 dt^2 sum 1/h^2, neighbours dt^2/h^2
+  for (auto &D : c->hg) {
+    if (D.stencil != kConst7) continue;
+    double x[3];
+    for (int a = 0; a < 3; ++a) x[a] = c->dt2 / (D.h[a] * D.h[a]);
+    D.cw[0] = 2.0 - 2.0 * (x[0] + x[1] + x[2]);
+    for (int a = 0; a < 3; ++a) D.cw[1 + a] = x[a];
+    for (int a = 0; a < 4; ++a) D.cwf[a] = (float)D.cw[a];
+  }
+  CK3(cudaMemcpy(c->d_grids, c->hg.data(), ng * sizeof(Grid3Dev), cudaMemcpyHostToDevice));
+  const bool fp32 = opt.precision == WH_FP32;
+  if (fp32 && !c->d_Wa32) {
+    if ((st = alloc3(c, &c->d_Wa32, c->total, err)) || (st = alloc3(c, &c->d_Wb32, c->total, err)) ||
+        (st = alloc3(c, &c->d_F32, c->total, err)) || (st = alloc3(c, &c->d_Wt32, c->w_total, err)))
+      return st;
+  }
+  for (int g = 0; g < ng; ++g) {
+    if (c->hg[g].stencil == kConst7) continue;
+    launch_weight3(false, s, c->d_grids, g, c->hg[g], c->d_mask, c->d_coef, c->d_c2, c->d_Wt,
+                   c->dt2);
+    if (fp32)
+      launch_weight3(true, s, c->d_grids, g, c->hg[g], c->d_mask, c->d_coef, c->d_c2,
+                     c->d_Wt32, c->dt2);
+  }
+  if (fp32 && !c->fp32_ready) {
+    launch_to_precision(true, s, c->d_F, c->d_F32, c->total);
+    c->fp32_ready = true;
+  }
+  CK3(cudaGetLastError());
+  CK3(cudaStreamSynchronize(s));
+  if (ti) *ti = T;
+  if (ncompact) *ncompact = c->ncompact;
+  if (nactive) *nactive = c->nactive;
+  return WH_OK;
+}
+
+wh_status iterate(Ctx3 *c, bool fp32, int forcing, const double *vin, double *vout,
+                  cudaStream_t s, int64_t *launches, std::string &err) {
+  forcing = forcing ? 1 : 0;
+  if (fp32 && !c->d_Wa32)
+    return fail3(err, WH_ERR_STATE, "the FP32 march was not prepared");
+  if (!c->gexec[fp32][forcing]) {
+    wh_status st = build_graph3(c, fp32, forcing, s, err);
+    if (st) return st;
+  }
+  const int ng = (int)c->grids.size();
+  launch_init3(fp32, s, c->d_grids, ng, c->max_ext, c->d_mask, vin,
+               fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa, c->d_V, c->tab.wf);
+  CK3(cudaGetLastError());
+  CK3(cudaGraphLaunch(c->gexec[fp32][forcing], s));
+  launch_finish3(s, c->d_grids, ng, c->max_compact, c->d_V, vout);
+  CK3(cudaGetLastError());
+  if (launches) *launches += 3 + 2 * (int64_t)c->M;
+  return WH_OK;
+}
+
+wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int32_t *counts,
+                  std::string &err) {
+  if (reps < 1) reps = 1;
+  if (fp32 && !c->d_Wa32) return fail3(err, WH_ERR_STATE, "the FP32 march was not prepared");
+  cudaEvent_t ev[6];
+  for (auto &e : ev) CK3(cudaEventCreate(&e));
+  void *Wa = fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa;
+  void *Wb = fp32 ? (void *)c->d_Wb32 : (void *)c->d_Wb;
+  const void *F = fp32 ? (const void *)c->d_F32 : (const void *)c->d_F;
+  const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
+  double t_march = 0, t_gather = 0;
+  float t;
+  for (int r = 0; r < reps; ++r) {
+    for (int n = 0; n < c->M; ++n) {
+      void *cur = (n & 1) ? Wb : Wa;
+      void *oth = (n & 1) ? Wa : Wb;
+      CK3(cudaEventRecord(ev[0], s));
+      launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth,
+                    F, Wt, c->d_V, c->tab, n, 0.0);
+      CK3(cudaEventRecord(ev[1], s));
+      launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_didx, c->d_dw, c->d_gdst,
+                     c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
+      CK3(cudaEventRecord(ev[2], s));
+      CK3(cudaEventSynchronize(ev[2]));
+      CK3(cudaEventElapsedTime(&t, ev[0], ev[1]));
+      t_march += t;
+      CK3(cudaEventElapsedTime(&t, ev[1], ev[2]));
+      t_gather += t;
+    }
+  }
+  CK3(cudaGetLastError());
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (ms) {
+    ms[0] = t_march / reps;
+    ms[1] = t_gather / reps;
+  }
+  if (counts) {
+    counts[0] = c->M;
+    counts[1] = c->M;
+  }
+  return WH_OK;
+}
+
+}  // namespace wh3

@@ -1,0 +1,426 @@
+// wh_kernels3.cu -- CUDA kernels of the three-dimensional, second-order WaveHoltz path
+// (sm_103a).
+//
+// One WaveHoltz iteration (Algorithm 1) on a 3D overset grid is
+//   init3 -> gather3(level 0) -> [march3(n) -> gather3(level n + 1)] for n < M -> finish3:
+//   - march3: the explicit scheme of Eq. WaveSchemeexplicit (Sec. 4.2) at every
+//     discretization point of every grid, the stencil of the mapped Laplacian (Sec. 3.1,
+//     second order: D+D-, D0, D0 D0) with dt^2 c^2 folded into per-point or constant
+//     weights, the forcing term, and the filter accumulation of Eq. updateDiscreteExplicit
+//     fused into the write of W^{n+1}.  W^{n+1} overwrites W^{n-1} in place.
+//   - gather3: the ghost rules (Neumann: centred normal derivative, a copy of the inward
+//     value) and the explicit interpolation of every receiver from its 3 x 3 x 3 donor
+//     stencil (Sec. 3.1, Algorithm 2: boundary conditions and interpolation after every
+//     grid has advanced), warp-cooperative: one warp per receiver, one lane per donor, a
+//     shuffle reduction.  Receivers add their filter term too.
+// Setup kernels compute the mapped-Laplacian coefficients a_kl, b_k from the metrics with
+// the CFL bound (Eq. dtForCartesian), and the stencil weights for one dt.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "wh3_internal.h"
+
+namespace wh3 {
+namespace {
+
+constexpr int8_t kDisc = WH_DISC, kInterpPt = WH_INTERP, kDirichlet = WH_DIRICHLET;
+
+__device__ __forceinline__ int wrap(int i, int n, int per) {
+  if (!per) return i;
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+__device__ __forceinline__ int64_t at3(const Grid3Dev &G, int i, int j, int k) {
+  return G.base + ((int64_t)(k + G.g2) * G.e1 + (j + G.g1)) * G.e0 + (i + G.g0);
+}
+
+// Index of (i + di, j + dj, k + dk), wrapping periodic axes.
+__device__ __forceinline__ int64_t nb3(const Grid3Dev &G, int i, int j, int k, int di, int dj,
+                                       int dk) {
+  return at3(G, wrap(i + di, G.n0, G.per & 1), wrap(j + dj, G.n1, G.per & 2),
+             wrap(k + dk, G.n2, G.per & 4));
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
+  // positive doubles order like their bit patterns
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------- setup kernels
+
+// Coefficients c^2 a_kl, c^2 b_k at discretization and Dirichlet points of a curvilinear
+// grid (Sec. 3.1: a_kl = sum_m dr_k/dx_m dr_l/dx_m, b_k = sum_m sum_l dr_l/dx_m
+// D0_l(dr_k/dx_m)); mixed coefficients of pairs declared orthogonal are 0.  At
+// discretization points of every grid, the frozen-coefficient CFL quantity
+// sum_k a_kk / h_k^2 + 2 sum_{k<l} |a_kl| / (h_k h_l) goes into smax.
+__global__ void coef3_kernel(const Grid3Dev *grids, int gidx, const int8_t *mask,
+                             const double *rx, const double *c2, double *coef,
+                             unsigned long long *smax) {
+  const Grid3Dev G = grids[gidx];
+  const int64_t npts = (int64_t)G.n0 * G.n1 * G.n2;
+  const int64_t E = G.ext;
+  double local = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % G.n0), j = (int)((t / G.n0) % G.n1), k = (int)(t / ((int64_t)G.n0 * G.n1));
+    const int64_t q = at3(G, i, j, k), ql = q - G.base;
+    const int8_t m = mask[q];
+    if (m != kDisc && m != kDirichlet) continue;
+    const double c2q = c2[q];
+    if (G.kind == WH_CARTESIAN) {
+      if (m == kDisc) {
+        double s = 1.0 / (G.h[0] * G.h[0]) + 1.0 / (G.h[1] * G.h[1]) + 1.0 / (G.h[2] * G.h[2]);
+        local = fmax(local, c2q * s);
+      }
+      continue;
+    }
+    const double *R = rx + G.rbase;
+    double r[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) r[p] = R[p * E + ql];
+    double a[3][3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) a[u][v] = r[3 * u] * r[3 * v] + r[3 * u + 1] * r[3 * v + 1] +
+                                            r[3 * u + 2] * r[3 * v + 2];
+    // neighbour offsets (relative to the grid's base) along each parameter axis
+    int64_t qp[3], qm[3];
+    qp[0] = nb3(G, i, j, k, 1, 0, 0) - G.base;
+    qm[0] = nb3(G, i, j, k, -1, 0, 0) - G.base;
+    qp[1] = nb3(G, i, j, k, 0, 1, 0) - G.base;
+    qm[1] = nb3(G, i, j, k, 0, -1, 0) - G.base;
+    qp[2] = nb3(G, i, j, k, 0, 0, 1) - G.base;
+    qm[2] = nb3(G, i, j, k, 0, 0, -1) - G.base;
+    double b[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      double s = 0.0;
+#pragma unroll
+      for (int mm = 0; mm < 3; ++mm) {
+        const double *P = R + (3 * u + mm) * E;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) s += r[3 * l + mm] * ((P[qp[l]] - P[qm[l]]) / (2.0 * G.h[l]));
+      }
+      b[u] = s;
+    }
+    double *C = coef + G.kbase;
+    const double A01 = (G.ortho & 1) ? 0.0 : c2q * a[0][1];
+    const double A02 = (G.ortho & 2) ? 0.0 : c2q * a[0][2];
+    const double A12 = (G.ortho & 4) ? 0.0 : c2q * a[1][2];
+    C[kA00 * E + ql] = c2q * a[0][0];
+    C[kA11 * E + ql] = c2q * a[1][1];
+    C[kA22 * E + ql] = c2q * a[2][2];
+    C[kA01 * E + ql] = A01;
+    C[kA02 * E + ql] = A02;
+    C[kA12 * E + ql] = A12;
+    C[kB0 * E + ql] = c2q * b[0];
+    C[kB1 * E + ql] = c2q * b[1];
+    C[kB2 * E + ql] = c2q * b[2];
+    if (m == kDisc) {
+      double s = c2q * a[0][0] / (G.h[0] * G.h[0]) + c2q * a[1][1] / (G.h[1] * G.h[1]) +
+                 c2q * a[2][2] / (G.h[2] * G.h[2]);
+      s += 2.0 * fabs(A01) / (G.h[0] * G.h[1]) + 2.0 * fabs(A02) / (G.h[0] * G.h[2]) +
+           2.0 * fabs(A12) / (G.h[1] * G.h[2]);
+      local = fmax(local, s);
+    }
+  }
+  if (local > 0.0) atomic_max_pos(smax, local);
+}
+
+// Per-point stencil weights with dt^2 folded in (the centre carries the "2" of the
+// leapfrog): centre 2 - 2 dt^2 sum_k a_kk/h_k^2; face -+k: dt^2 (a_kk/h_k^2 -+ b_k/(2 h_k));
+// edge (k,l): +-dt^2 a_kl / (2 h_k h_l) (from 2 a_kl D0_k D0_l).  Cartesian grids with c(x)
+// use a_kk = c^2, b = 0.
+template <typename T>
+__global__ void weight3_kernel(const Grid3Dev *grids, int gidx, const int8_t *mask,
+                               const double *coef, const double *c2, T *Wt, double dt2) {
+  const Grid3Dev G = grids[gidx];
+  const int64_t npts = (int64_t)G.n0 * G.n1 * G.n2;
+  const int64_t E = G.ext;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % G.n0), j = (int)((t / G.n0) % G.n1), k = (int)(t / ((int64_t)G.n0 * G.n1));
+    const int64_t q = at3(G, i, j, k), ql = q - G.base;
+    if (mask[q] != kDisc) continue;
+    double A[3], B[3], Mx[3] = {0.0, 0.0, 0.0};
+    if (G.kind == WH_CARTESIAN) {
+      A[0] = A[1] = A[2] = c2[q];
+      B[0] = B[1] = B[2] = 0.0;
+    } else {
+      const double *C = coef + G.kbase;
+      A[0] = C[kA00 * E + ql];
+      A[1] = C[kA11 * E + ql];
+      A[2] = C[kA22 * E + ql];
+      B[0] = C[kB0 * E + ql];
+      B[1] = C[kB1 * E + ql];
+      B[2] = C[kB2 * E + ql];
+      Mx[0] = C[kA01 * E + ql];
+      Mx[1] = C[kA02 * E + ql];
+      Mx[2] = C[kA12 * E + ql];
+    }
+    T *W = Wt + G.wbase + ql;
+    double xs[3], ys[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xs[a] = dt2 * A[a] / (G.h[a] * G.h[a]);
+      ys[a] = dt2 * B[a] / (2.0 * G.h[a]);
+    }
+    W[0] = (T)(2.0 - 2.0 * (xs[0] + xs[1] + xs[2]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      W[(1 + 2 * a) * E] = (T)(xs[a] - ys[a]);
+      W[(2 + 2 * a) * E] = (T)(xs[a] + ys[a]);
+    }
+    if (G.stencil == kPoint19) {
+      const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const double z = dt2 * Mx[p] / (2.0 * G.h[pa[p]] * G.h[pb[p]]);
+        W[(7 + 4 * p) * E] = (T)z;       // (-,-)
+        W[(8 + 4 * p) * E] = (T)(-z);    // (+,-)
+        W[(9 + 4 * p) * E] = (T)(-z);    // (-,+)
+        W[(10 + 4 * p) * E] = (T)z;      // (+,+)
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- iteration kernels
+
+// W^0 = v at discretization and interpolation points, 0 elsewhere (ghosts included);
+// V = w_0 W^0 at discretization points, 0 elsewhere (receivers add theirs after the
+// level-0 interpolation).  blockIdx.y = grid.
+template <typename T>
+__global__ void init3_kernel(const Grid3Dev *grids, const int8_t *mask, const double *vin,
+                             T *W0, double *V, const double *wf) {
+  const Grid3Dev G = grids[blockIdx.y];
+  const double w0 = wf[0];
+  const int64_t pl = (int64_t)G.e0 * G.e1;
+  for (int64_t ql = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ql < G.ext;
+       ql += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(ql % G.e0) - G.g0, j = (int)((ql / G.e0) % G.e1) - G.g1,
+              k = (int)(ql / pl) - G.g2;
+    const int64_t q = G.base + ql;
+    const int8_t m = mask[q];
+    double v = 0.0;
+    if ((m == kDisc || m == kInterpPt) && i >= 0 && i < G.n0 && j >= 0 && j < G.n1 && k >= 0 &&
+        k < G.n2)
+      v = vin[G.cbase + ((int64_t)k * G.n1 + j) * G.n0 + i];
+    const T w = (T)v;
+    W0[q] = w;
+    V[q] = m == kDisc ? w0 * (double)w : 0.0;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T fsel(double d, float f);
+template <>
+__device__ __forceinline__ double fsel<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float fsel<float>(double, float f) { return f; }
+
+// One time step n -> n + 1 of every grid (Eq. WaveSchemeexplicit) with the fused filter
+// term of level n + 1.  Block = one Tile3; each thread marches kTZ points along axis 2.
+template <typename T>
+__global__ void __launch_bounds__(kTX *kTY) march3_kernel(
+    const Grid3Dev *__restrict__ grids, const Tile3 *__restrict__ tiles,
+    const int8_t *__restrict__ mask, const T *__restrict__ Wn, T *__restrict__ Wout,
+    const T *__restrict__ F, const T *__restrict__ Wt, double *__restrict__ V, Tab3 tab, int n,
+    double fs) {
+  const Tile3 tl = tiles[blockIdx.x];
+  const Grid3Dev &Gg = grids[tl.grid];
+  const int n0 = Gg.n0, n1 = Gg.n1, n2 = Gg.n2;
+  const int i = tl.i0 + threadIdx.x, j = tl.j0 + threadIdx.y;
+  if (i >= n0 || j >= n1) return;
+  const bool first = n == 0;
+  const double wfn = tab.wf[n + 1];
+  const T fcn = first ? fsel<T>(tab.dt2h, tab.dt2hf) : fsel<T>(tab.fc[n], tab.fcf[n]);
+  const T fsT = (T)fs;
+  const int kend = min(tl.k0 + kTZ, n2);
+  const int stencil = Gg.stencil, per = Gg.per;
+  const int64_t e0 = Gg.e0, pl = (int64_t)Gg.e0 * Gg.e1;
+  if (stencil == kConst7 && per == 0) {
+    // constant weights, no wrap: a register queue of W^n along axis 2
+    const T c0 = fsel<T>(Gg.cw[0], Gg.cwf[0]), c1 = fsel<T>(Gg.cw[1], Gg.cwf[1]),
+            c2 = fsel<T>(Gg.cw[2], Gg.cwf[2]), c3 = fsel<T>(Gg.cw[3], Gg.cwf[3]);
+    int64_t q = at3(Gg, i, j, tl.k0);
+    T wm = Wn[q - pl], wc = Wn[q];
+    for (int k = tl.k0; k < kend; ++k, q += pl) {
+      const T wp = Wn[q + pl];
+      if (mask[q] == kDisc) {
+        const T S = c0 * wc + c1 * (Wn[q - 1] + Wn[q + 1]) + c2 * (Wn[q - e0] + Wn[q + e0]) +
+                    c3 * (wm + wp);
+        const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wout[q] - fcn * fsT * F[q];
+        Wout[q] = out;
+        V[q] += wfn * (double)out;
+      }
+      wm = wc;
+      wc = wp;
+    }
+    return;
+  }
+  const Grid3Dev G = Gg;
+  const int64_t E = G.ext;
+  for (int k = tl.k0; k < kend; ++k) {
+    const int64_t q = at3(G, i, j, k);
+    if (mask[q] != kDisc) continue;
+    const int64_t xm = nb3(G, i, j, k, -1, 0, 0), xp = nb3(G, i, j, k, 1, 0, 0);
+    const int64_t ym = nb3(G, i, j, k, 0, -1, 0), yp = nb3(G, i, j, k, 0, 1, 0);
+    const int64_t zm = nb3(G, i, j, k, 0, 0, -1), zp = nb3(G, i, j, k, 0, 0, 1);
+    T S;
+    if (stencil == kConst7) {
+      S = fsel<T>(G.cw[0], G.cwf[0]) * Wn[q] + fsel<T>(G.cw[1], G.cwf[1]) * (Wn[xm] + Wn[xp]) +
+          fsel<T>(G.cw[2], G.cwf[2]) * (Wn[ym] + Wn[yp]) +
+          fsel<T>(G.cw[3], G.cwf[3]) * (Wn[zm] + Wn[zp]);
+    } else {
+      const T *w = Wt + G.wbase + (q - G.base);
+      S = w[0] * Wn[q] + w[E] * Wn[xm] + w[2 * E] * Wn[xp] + w[3 * E] * Wn[ym] +
+          w[4 * E] * Wn[yp] + w[5 * E] * Wn[zm] + w[6 * E] * Wn[zp];
+      if (stencil == kPoint19) {
+        // edges of pairs (x,y), (x,z), (y,z): (-,-) (+,-) (-,+) (+,+)
+        S += w[7 * E] * Wn[nb3(G, i, j, k, -1, -1, 0)] + w[8 * E] * Wn[nb3(G, i, j, k, 1, -1, 0)] +
+             w[9 * E] * Wn[nb3(G, i, j, k, -1, 1, 0)] + w[10 * E] * Wn[nb3(G, i, j, k, 1, 1, 0)];
+        S += w[11 * E] * Wn[nb3(G, i, j, k, -1, 0, -1)] + w[12 * E] * Wn[nb3(G, i, j, k, 1, 0, -1)] +
+             w[13 * E] * Wn[nb3(G, i, j, k, -1, 0, 1)] + w[14 * E] * Wn[nb3(G, i, j, k, 1, 0, 1)];
+        S += w[15 * E] * Wn[nb3(G, i, j, k, 0, -1, -1)] + w[16 * E] * Wn[nb3(G, i, j, k, 0, 1, -1)] +
+             w[17 * E] * Wn[nb3(G, i, j, k, 0, -1, 1)] + w[18 * E] * Wn[nb3(G, i, j, k, 0, 1, 1)];
+      }
+    }
+    const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wout[q] - fcn * fsT * F[q];
+    Wout[q] = out;
+    V[q] += wfn * (double)out;
+  }
+}
+
+// Ghost rules and interpolation of one time level.  Warp w handles receivers w, w + W, ...:
+// lane u < 27 loads donor u (weights wx wy wz multiplied out), a shuffle tree sums them,
+// lane 0 writes the receiver and its filter term.  Every thread then copies Neumann ghosts
+// (gdst <- gsrc).  Donors and ghost sources are discretization or Dirichlet points, so
+// the two parts read nothing the other writes.
+template <typename T>
+__global__ void gather3_kernel(int64_t nrecv, int64_t nghost, const int64_t *__restrict__ ridx,
+                               const int32_t *__restrict__ didx, const double *__restrict__ dw,
+                               const int32_t *__restrict__ gdst, const int32_t *__restrict__ gsrc,
+                               T *W, double *V, const double *__restrict__ wf, int level) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double wl = wf[level];
+  for (int64_t r = warp; r < nrecv; r += nwarps) {
+    double s = 0.0;
+    if (lane < 27) s = dw[r * 27 + lane] * (double)W[didx[r * 27 + lane]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const T v = (T)s;
+      const int64_t q = ridx[r];
+      W[q] = v;
+      V[q] += wl * (double)v;
+    }
+  }
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nghost;
+       g += (int64_t)gridDim.x * blockDim.x)
+    W[gdst[g]] = W[gsrc[g]];
+}
+
+// v_out (compact) = V at every point of every grid; blockIdx.y = grid.
+__global__ void finish3_kernel(const Grid3Dev *grids, const double *V, double *vout) {
+  const Grid3Dev G = grids[blockIdx.y];
+  const int64_t npts = (int64_t)G.n0 * G.n1 * G.n2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % G.n0), j = (int)((t / G.n0) % G.n1), k = (int)(t / ((int64_t)G.n0 * G.n1));
+    vout[G.cbase + t] = V[at3(G, i, j, k)];
+  }
+}
+
+template <typename T>
+__global__ void convert_kernel(const double *src, T *dst, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = (T)src[t];
+}
+
+unsigned blocks_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+void launch_coef3(cudaStream_t s, const Grid3Dev *grids, int gidx, const Grid3Dev &G,
+                  const int8_t *mask, const double *rx, const double *c2, double *coef,
+                  unsigned long long *smax) {
+  const int64_t n = (int64_t)G.n0 * G.n1 * G.n2;
+  coef3_kernel<<<blocks_for(n, 256), 256, 0, s>>>(grids, gidx, mask, rx, c2, coef, smax);
+}
+
+void launch_weight3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int gidx,
+                    const Grid3Dev &G, const int8_t *mask, const double *coef, const double *c2,
+                    void *Wt, double dt2) {
+  const int64_t n = (int64_t)G.n0 * G.n1 * G.n2;
+  if (fp32)
+    weight3_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(grids, gidx, mask, coef, c2,
+                                                             (float *)Wt, dt2);
+  else
+    weight3_kernel<double><<<blocks_for(n, 256), 256, 0, s>>>(grids, gidx, mask, coef, c2,
+                                                              (double *)Wt, dt2);
+}
+
+void launch_init3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int ngrids,
+                  int64_t max_ext, const int8_t *mask, const double *v, void *W0, double *V,
+                  const double *wf) {
+  dim3 gb(blocks_for(max_ext, 256), ngrids);
+  if (fp32)
+    init3_kernel<float><<<gb, 256, 0, s>>>(grids, mask, v, (float *)W0, V, wf);
+  else
+    init3_kernel<double><<<gb, 256, 0, s>>>(grids, mask, v, (double *)W0, V, wf);
+}
+
+void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
+                   const Tile3 *tiles, const int8_t *mask, const void *Wn, void *Wout,
+                   const void *F, const void *Wt, double *V, Tab3 tab, int n, double fs) {
+  dim3 tb(kTX, kTY);
+  if (fp32)
+    march3_kernel<float><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const float *)Wn,
+                                               (float *)Wout, (const float *)F,
+                                               (const float *)Wt, V, tab, n, fs);
+  else
+    march3_kernel<double><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const double *)Wn,
+                                                (double *)Wout, (const double *)F,
+                                                (const double *)Wt, V, tab, n, fs);
+}
+
+void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
+                    const int64_t *ridx, const int32_t *didx, const double *dw,
+                    const int32_t *gdst, const int32_t *gsrc, void *W, double *V,
+                    const double *wf, int level) {
+  const int threads = 256;
+  int64_t need = nrecv * 32 > nghost ? nrecv * 32 : nghost;
+  if (need < 1) need = 1;
+  const unsigned nb = blocks_for(need, threads);
+  if (fp32)
+    gather3_kernel<float><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, didx, dw, gdst, gsrc,
+                                                 (float *)W, V, wf, level);
+  else
+    gather3_kernel<double><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, didx, dw, gdst, gsrc,
+                                                  (double *)W, V, wf, level);
+}
+
+void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
+                    const double *V, double *vout) {
+  dim3 gb(blocks_for(max_compact, 256), ngrids);
+  finish3_kernel<<<gb, 256, 0, s>>>(grids, V, vout);
+}
+
+void launch_to_precision(bool fp32, cudaStream_t s, const double *src, void *dst, int64_t n) {
+  if (fp32)
+    convert_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(src, (float *)dst, n);
+  else
+    convert_kernel<double><<<blocks_for(n, 256), 256, 0, s>>>(src, (double *)dst, n);
+}
+
+}  // namespace wh3

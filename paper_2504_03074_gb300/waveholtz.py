@@ -51,6 +51,18 @@ class InterpDesc(C.Structure):
                                       "donor_j0", "wx", "wy")]
 
 
+class Grid3Desc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("kind", C.c_int32), ("bc", C.c_int32 * 6),
+                ("ortho", C.c_int32), ("instance", C.c_int32), ("h", C.c_double * 3),
+                ("mask", C.c_void_p), ("rx", C.c_void_p), ("c2", C.c_void_p)]
+
+
+class Interp3Desc(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in
+                                     ("recv_grid", "recv_i", "recv_j", "recv_k", "donor_grid",
+                                      "donor_i0", "donor_j0", "donor_k0", "wx", "wy", "wz")]
+
+
 class TimeInfo(C.Structure):
     _fields_ = [("omega", C.c_double), ("dt", C.c_double), ("omega_e", C.c_double),
                 ("alpha", C.c_double), ("dt_max", C.c_double), ("Tbar", C.c_double),
@@ -80,7 +92,8 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
-           "wh_set_coefficient", "wh_set_tuning", "wh_autotune"]
+           "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
+           "wh_set_interp3"]
 
 
 def lib_path():
@@ -106,6 +119,8 @@ def lib():
     L.wh_set_stream.argtypes = [vp, vp]
     L.wh_add_grid.argtypes = [vp, C.POINTER(GridDesc), C.POINTER(C.c_int32)]
     L.wh_set_interp.argtypes = [vp, C.POINTER(InterpDesc)]
+    L.wh_add_grid3.argtypes = [vp, C.POINTER(Grid3Desc), C.POINTER(C.c_int32)]
+    L.wh_set_interp3.argtypes = [vp, C.POINTER(Interp3Desc)]
     L.wh_set_forcing.argtypes = [vp, C.c_int32, vp]
     L.wh_prepare.argtypes = [vp, C.c_double, C.POINTER(TimeInfo)]
     L.wh_prepare_batch.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(TimeInfo)]
@@ -165,6 +180,10 @@ class Solver:
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.set_stream(self.stream)
+        if getattr(problem, "dim", 2) == 3:
+            self._add_3d(problem)
+            self.info = None
+            return
         for gi, g in enumerate(problem.grids):
             mask = np.ascontiguousarray(g.mask, np.int8)
             rx = None if g.rx is None else np.ascontiguousarray(g.rx, np.float64)
@@ -189,6 +208,32 @@ class Solver:
         d = InterpDesc(it.n, *[_ptr(a) for a in arrs + ws])
         self._check(self.L.wh_set_interp(self.h, C.byref(d)))
         self.info = None
+
+    def _add_3d(self, problem):
+        """Three-dimensional grids and interpolation (``grids3.Problem3``)."""
+        for gi, g in enumerate(problem.grids):
+            mask = np.ascontiguousarray(g.mask, np.int8)
+            rx = None if g.rx is None else np.ascontiguousarray(g.rx, np.float64)
+            c2 = None if problem.c2 is None else np.ascontiguousarray(problem.c2[gi], np.float64)
+            d = Grid3Desc()
+            for a in range(3):
+                d.n[a] = g.n[a]
+                d.h[a] = g.h[a]
+            for s in range(6):
+                d.bc[s] = g.bc[s]
+            d.kind, d.ortho, d.instance = g.kind, int(g.ortho), 0
+            d.mask, d.rx, d.c2 = _ptr(mask), _ptr(rx), _ptr(c2)
+            gid = C.c_int32()
+            self._check(self.L.wh_add_grid3(self.h, C.byref(d), C.byref(gid)))
+            f = np.ascontiguousarray(problem.f[gi], np.float64)
+            self._check(self.L.wh_set_forcing(self.h, gid.value, _ptr(f)))
+        it = problem.interp
+        arrs = [np.ascontiguousarray(a, np.int32) for a in
+                (it.recv_grid, it.recv_i, it.recv_j, it.recv_k, it.donor_grid, it.donor_i0,
+                 it.donor_j0, it.donor_k0)]
+        ws = [np.ascontiguousarray(a, np.float64) for a in (it.wx, it.wy, it.wz)]
+        d = Interp3Desc(it.n, *[_ptr(a) for a in arrs + ws])
+        self._check(self.L.wh_set_interp3(self.h, C.byref(d)))
 
     def _check(self, status, h=0):
         if status != WH_OK:

@@ -148,3 +148,107 @@ def test_grid_validation_on_host(W):
     ti = W.TimeInfo()
     assert L.wh_get_time_info(h, C.byref(ti)) == -3
     L.wh_destroy(h)
+
+
+def _desc3(W, g):
+    d = W.Grid3Desc()
+    for a in range(3):
+        d.n[a] = g.n[a]
+        d.h[a] = g.h[a]
+    for s in range(6):
+        d.bc[s] = g.bc[s]
+    d.kind, d.ortho, d.instance = g.kind, int(g.ortho), 0
+    keep = [np.ascontiguousarray(g.mask, np.int8)]
+    d.mask = keep[0].ctypes.data
+    if g.rx is not None:
+        keep.append(np.ascontiguousarray(g.rx))
+        d.rx = keep[-1].ctypes.data
+    return d, keep
+
+
+def _interp3(W, it, **override):
+    cols = {k: np.ascontiguousarray(getattr(it, k), np.int32).copy() for k in
+            ("recv_grid", "recv_i", "recv_j", "recv_k", "donor_grid", "donor_i0", "donor_j0",
+             "donor_k0")}
+    cols.update(override)
+    ws = [np.ascontiguousarray(getattr(it, k)) for k in ("wx", "wy", "wz")]
+    keep = list(cols.values()) + ws
+    return W.Interp3Desc(it.n, *[a.ctypes.data for a in keep]), keep
+
+
+def test_grid3_validation_on_host(W):
+    """Three-dimensional grids: order 2 only, no mixing with 2D grids, Neumann axes must be
+    orthogonal, discretization points may not sit on non-Neumann sides or read unused
+    points, and interpolation data must be explicit and complete."""
+    from paper_2504_03074_gb300 import grids3 as G3
+    L = W.lib()
+    gid = C.c_int32()
+    cube = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
+    # order 4 context: rejected
+    h = _ctx(W, order=4)
+    d, keep = _desc3(W, cube)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -1
+    L.wh_destroy(h)
+    # 2D and 3D grids do not mix
+    h = _ctx(W, order=2)
+    g2 = G.cartesian_grid("c", 16, 16, 0, 1, 0, 1, [1, 1, 1, 1], 2)
+    d2, keep2 = _desc(W, g2)
+    assert L.wh_add_grid(h, C.byref(d2), C.byref(gid)) == 0
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -3
+    L.wh_destroy(h)
+    h = _ctx(W, order=2)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0
+    assert L.wh_add_grid(h, C.byref(d2), C.byref(gid)) == -3
+    L.wh_destroy(h)
+    # a discretization point on a Dirichlet side
+    h = _ctx(W, order=2)
+    bad = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
+    bad.mask[0, 4, 4] = G.DISC
+    d, keep = _desc3(W, bad)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -7
+    # a stencil reading an unused point
+    bad = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
+    bad.mask[4, 4, 4] = G.UNUSED
+    d, keep = _desc3(W, bad)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -7
+    # a Neumann side whose normal axis is not orthogonal to the others
+    patch = G3.pole_patch_grid("p", 9, 6, 0.5, 0.5, 0.3, 1.0)
+    patch.ortho = 4
+    d, keep = _desc3(W, patch)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -1
+    # unpaired periodic sides, too few points
+    bad = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [3, 1, 1, 1, 1, 1])
+    d, keep = _desc3(W, bad)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -1
+    bad = G3.cartesian_grid3("c", (4, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
+    d, keep = _desc3(W, bad)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -1
+    L.wh_destroy(h)
+    # a valid sphere-in-box grid, then interpolation errors
+    prob = G3.sphere_problem(nb=48, nphi=64, nth=32, nr=10, npatch=20, width=0.5,
+                             r_hole=0.75, patch_deg=30.0, omega=6.0)
+    h = _ctx(W, order=2)
+    keeps = []
+    for g in prob.grids:
+        d, keep = _desc3(W, g)
+        keeps.append(keep)
+        assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0, L.wh_last_error(h)
+    it = prob.interp
+    ok, keep = _interp3(W, it)
+    assert L.wh_set_interp3(h, C.byref(ok)) == 0, L.wh_last_error(h)
+    rg = np.ascontiguousarray(it.recv_grid, np.int32).copy()
+    rg[0] = 9
+    desc, keep = _interp3(W, it, recv_grid=rg)
+    assert L.wh_set_interp3(h, C.byref(desc)) == -7
+    di = np.ascontiguousarray(it.donor_i0, np.int32).copy()
+    sel = np.nonzero(it.donor_grid == 0)[0][0]
+    di[sel] = prob.grids[0].n[0] - 2  # stencil leaves the background
+    desc, keep = _interp3(W, it, donor_i0=di)
+    assert L.wh_set_interp3(h, C.byref(desc)) == -7
+    short = W.Interp3Desc(it.n - 1, *[a.ctypes.data for a in _interp3(W, it)[1]])
+    assert L.wh_set_interp3(h, C.byref(short)) == -7  # an interpolation point left out
+    # 3D contexts: batch, differentiation and tuning calls are state errors
+    out = W.Tuning()
+    assert L.wh_set_tuning(h, C.byref(W.Tuning(-1, 1, 0, -1, 1, 0.0, 0))) == -3
+    assert L.wh_set_coefficient(h, 0, None) == -3
+    L.wh_destroy(h)
