@@ -393,7 +393,42 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
     solve["workload"] = ("64^2 unit square, order 2, omega 10, residual 1e-7; reference: FP64 "
                          "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
     out["solve_unit_square"] = solve
+    out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush)
     return out
+
+
+def measure_sphere(WH, torch, stream, flush):
+    """The three-dimensional workload: sphere-in-box, 320^3 Cartesian background on
+    [-2, 2]^3 + spherical shell 256 x 128 x 24 (polar band 15-165 degrees, width 0.3) + two
+    orthographic pole patches 96^2 x 24, second order, Neumann sphere, Dirichlet box,
+    omega 30, one seeded Gaussian source: one WaveHoltz iteration with the FP64 and with the
+    FP32 march (GLUP/s, L2 flushed between iterations) and the device time per launch of
+    the march and of the ghost-rule + interpolation kernel."""
+    from paper_2504_03074_gb300 import grids3 as G3
+    t0 = time.perf_counter()
+    prob = G3.sphere_problem()
+    res = {"workload": "sphere-in-box 320^3 + 256x128x24 + 2x96^2x24, order 2, omega 30",
+           "points": prob.n_total, "active_points": prob.n_active,
+           "receivers": prob.interp.n, "generate_s": time.perf_counter() - t0}
+    for name, prec in (("fp64", WH.FP64), ("fp32", WH.FP32)):
+        sp = WH.Solver(prob, stream=stream, precision=prec)
+        tp = sp.prepare()
+        t = time_iterations(WH, torch, sp, prob.n_total, stream, flush, 3)
+        prof = sp.profile_kernels(reps=1)
+        march_glups = tp.n_active / (prof["march"][0] * 1e-3) / 1e9
+        rec = {"value": tp.n_active * tp.M / t / 1e9, "unit": "GLUP/s",
+               "ms_per_iteration": t * 1e3, "M": tp.M,
+               "march_ms_per_launch": prof["march"][0],
+               "gather_ms_per_launch": prof["bc_gather"][0], "march_glups": march_glups}
+        if prec == WH.FP64:  # 15 FP64 FLOP per 7-point update (stencil 10, forcing 3, filter 2)
+            rec["march_fp64_frac"] = march_glups * 15.0 / 1e3 / FP64_PEAK_TFLOPS
+        else:  # 33 compulsory bytes per update (W^n, W^{n-1} r/w, F, V r/w, mask)
+            rec["march_hbm_frac"] = march_glups * 33.0 / float(measured_peaks().get("hbm_gbs", 6793.0))
+        res[name] = rec
+        sp.close()
+        del sp
+    res["speedup_fp32_vs_fp64"] = res["fp32"]["value"] / res["fp64"]["value"]
+    return res
 
 
 def run_reference(args):
@@ -439,6 +474,17 @@ def run_profile_case(case):
     B.build()
     from paper_2504_03074_gb300 import grids as G, waveholtz as WH
     prec = WH.FP32 if case.startswith("fp32") else WH.FP64
+    if case.endswith("sphere320"):
+        from paper_2504_03074_gb300 import grids3 as G3
+        sp = G3.sphere_problem()
+        s = WH.Solver(sp, precision=prec)
+        ti = s.prepare()
+        a = torch.zeros(sp.n_total, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        s.iterate(a, b, True)
+        torch.cuda.synchronize()
+        print(f"profile case {case}: {sp.n_total} points, 1 iteration ({ti.M} march launches)")
+        return 0
     if case.endswith("square8192"):
         sq = G.unit_square_problem(8192, 4, 10.0, seed=0)
         s = WH.Solver(sq, precision=prec)
@@ -472,10 +518,11 @@ def main():
                     help="skip the FP32 / batched / solve-time measurements")
     ap.add_argument("--profile-case",
                     choices=["fp32_batch16", "fp64_batch16", "fp32_square8192",
-                             "fp64_square8192"],
+                             "fp64_square8192", "fp32_sphere320", "fp64_sphere320"],
                     help="profiling aid: a 16-instance disk-in-square batch (8.4 M points, "
-                         "3 iterations) or one 8192^2 order-4 Cartesian grid (67 M points, "
-                         "5 march launches), HBM resident, in one precision; no bench line")
+                         "3 iterations), one 8192^2 order-4 Cartesian grid (67 M points, "
+                         "5 march launches) or the 3D sphere-in-box (34 M points, one "
+                         "iteration), HBM resident, in one precision; no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

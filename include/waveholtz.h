@@ -368,7 +368,9 @@ wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, doubl
  * interpolation when the iteration folds them into its launches), [1] the separate
  * ghost-rule + interpolation kernel, [2] the input kernel, [3] the output kernel.  The bursts run on the context's internal
  * working buffers and leave them unspecified (every wh_iterate rebuilds them from its
- * input).  Synchronises. */
+ * input).  On three-dimensional contexts [0] and [1] are the march and the ghost-rule +
+ * interpolation kernel, each launch timed on its own with events over `reps` iterations'
+ * steps, and [2], [3] are 0.  Synchronises. */
 wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts);
 
 /* Allocation-free inner products.  The paper has no counterpart: this serves callers that

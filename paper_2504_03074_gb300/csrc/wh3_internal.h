@@ -76,10 +76,12 @@ void launch_init3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int ngrids,
 void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
                    const Tile3 *tiles, const int8_t *mask, const void *Wn, void *Wout,
                    const void *F, const void *Wt, double *V, Tab3 tab, int n, double fs);
+// Receiver r: donor (i0 + a, j0 + b, k0 + c) at gbase[r] + goff[9r + a] + goff[9r + 3 + b] +
+// goff[9r + 6 + c] with weight gw[9r + a] gw[9r + 3 + b] gw[9r + 6 + c] (wx, wy, wz).
 void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
-                    const int64_t *ridx, const int32_t *didx, const double *dw,
-                    const int32_t *gdst, const int32_t *gsrc, void *W, double *V,
-                    const double *wf, int level);
+                    const int64_t *ridx, const int32_t *gbase, const int32_t *goff,
+                    const double *gw, const int32_t *gdst, const int32_t *gsrc, void *W,
+                    double *V, const double *wf, int level);
 void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
                     const double *V, double *vout);
 void launch_to_precision(bool fp32, cudaStream_t s, const double *src, void *dst, int64_t n);
@@ -99,7 +101,8 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
 wh_status iterate(Ctx3 *c, bool fp32, int forcing, const double *vin, double *vout,
                   cudaStream_t s, int64_t *launches, std::string &err);
 int ngrids(const Ctx3 *c);
-// Per-kernel device time of one iteration (march, gather, init + finish), milliseconds.
+// Device time per launch (ms) of the march and of the ghost-rule + interpolation kernel, each
+// launch timed on its own with events (reps iterations' worth of steps); counts = M each.
 wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int32_t *counts,
                   std::string &err);
 

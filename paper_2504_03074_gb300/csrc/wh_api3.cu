@@ -52,8 +52,8 @@ struct Ctx3 {
   double *d_rx = nullptr, *d_coef = nullptr, *d_Wt = nullptr;
   float *d_Wa32 = nullptr, *d_Wb32 = nullptr, *d_F32 = nullptr, *d_Wt32 = nullptr;
   int64_t *d_ridx = nullptr;
-  int32_t *d_didx = nullptr, *d_gdst = nullptr, *d_gsrc = nullptr;
-  double *d_dw = nullptr;
+  int32_t *d_gbase = nullptr, *d_goff = nullptr, *d_gdst = nullptr, *d_gsrc = nullptr;
+  double *d_gw = nullptr;
   double *d_tabs = nullptr;
   float *d_ftabs = nullptr;
   int64_t tabs_cap = 0;
@@ -115,8 +115,8 @@ void free_all(Ctx3 *c) {
   c->d_Wa = c->d_Wb = c->d_F = c->d_V = c->d_c2 = c->d_rx = c->d_coef = c->d_Wt = nullptr;
   c->d_Wa32 = c->d_Wb32 = c->d_F32 = c->d_Wt32 = nullptr;
   c->d_ridx = nullptr;
-  c->d_didx = c->d_gdst = c->d_gsrc = nullptr;
-  c->d_dw = nullptr;
+  c->d_gbase = c->d_goff = c->d_gdst = c->d_gsrc = nullptr;
+  c->d_gw = nullptr;
   c->d_tabs = nullptr;
   c->d_ftabs = nullptr;
   c->tabs_cap = 0;
@@ -305,24 +305,31 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
       CK3(cudaMemcpy(c->d_rx + D.rbase, H.rx.data(), 9 * D.ext * sizeof(double),
                      cudaMemcpyHostToDevice));
   }
-  // interpolation: receiver index, 27 donor indices and weight products
+  // interpolation: receiver index; donor corner index, per-axis offsets (wrapped on
+  // periodic axes) and per-axis weights
   const int64_t R = c->nrecv;
   std::vector<int64_t> ridx(R > 0 ? R : 1);
-  std::vector<int32_t> didx(R > 0 ? R * 27 : 1);
-  std::vector<double> dw(R > 0 ? R * 27 : 1);
+  std::vector<int32_t> gbase(R > 0 ? R : 1), goff(R > 0 ? R * 9 : 1);
+  std::vector<double> gw(R > 0 ? R * 9 : 1);
   for (int64_t r = 0; r < R; ++r) {
     const HostGrid3 &RG = c->grids[c->rg[r]];
     ridx[r] = c->hg[c->rg[r]].base + eidx(RG, c->ri[r], c->rj[r], c->rk[r]);
     const HostGrid3 &DG = c->grids[c->dg[r]];
     const int64_t db = c->hg[c->dg[r]].base;
-    for (int cc = 0; cc < 3; ++cc)
-      for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) {
-          const int u = cc * 9 + b * 3 + a;
-          didx[r * 27 + u] =
-              (int32_t)(db + eidx(DG, c->di[r] + a, c->dj[r] + b, c->dk[r] + cc));
-          dw[r * 27 + u] = c->wx[r * 3 + a] * c->wy[r * 3 + b] * c->wz[r * 3 + cc];
-        }
+    const int c0[3] = {c->di[r], c->dj[r], c->dk[r]};
+    const int64_t corner = eidx(DG, c0[0], c0[1], c0[2]);
+    gbase[r] = (int32_t)(db + corner);
+    for (int a = 0; a < 3; ++a)
+      for (int t = 0; t < 3; ++t) {
+        int d[3] = {c0[0], c0[1], c0[2]};
+        d[a] += t;
+        goff[r * 9 + 3 * a + t] = (int32_t)(eidx(DG, d[0], d[1], d[2]) - corner);
+      }
+    for (int t = 0; t < 3; ++t) {
+      gw[r * 9 + t] = c->wx[r * 3 + t];
+      gw[r * 9 + 3 + t] = c->wy[r * 3 + t];
+      gw[r * 9 + 6 + t] = c->wz[r * 3 + t];
+    }
   }
   // Neumann ghosts next to discretization points
   std::vector<int32_t> gdst, gsrc;
@@ -352,13 +359,16 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
     gsrc.push_back(0);
   }
   if ((st = alloc3(c, &c->d_ridx, ridx.size(), err)) ||
-      (st = alloc3(c, &c->d_didx, didx.size(), err)) || (st = alloc3(c, &c->d_dw, dw.size(), err)) ||
+      (st = alloc3(c, &c->d_gbase, gbase.size(), err)) ||
+      (st = alloc3(c, &c->d_goff, goff.size(), err)) || (st = alloc3(c, &c->d_gw, gw.size(), err)) ||
       (st = alloc3(c, &c->d_gdst, gdst.size(), err)) ||
       (st = alloc3(c, &c->d_gsrc, gsrc.size(), err)))
     return st;
   CK3(cudaMemcpy(c->d_ridx, ridx.data(), ridx.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-  CK3(cudaMemcpy(c->d_didx, didx.data(), didx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  CK3(cudaMemcpy(c->d_dw, dw.data(), dw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_gbase, gbase.data(), gbase.size() * sizeof(int32_t),
+                 cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_goff, goff.data(), goff.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK3(cudaMemcpy(c->d_gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK3(cudaMemcpy(c->d_gdst, gdst.data(), gdst.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK3(cudaMemcpy(c->d_gsrc, gsrc.data(), gsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   c->dirty = false;
@@ -390,8 +400,8 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
   const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
   const double fs = forcing ? 1.0 : 0.0;
   auto gather = [&](void *W, int level) {
-    launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_didx, c->d_dw, c->d_gdst,
-                   c->d_gsrc, W, c->d_V, c->tab.wf, level);
+    launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
+                   c->d_gdst, c->d_gsrc, W, c->d_V, c->tab.wf, level);
   };
   gather(Wa, 0);
   for (int n = 0; n < c->M; ++n) {
@@ -702,8 +712,8 @@ wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int3
       launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth,
                     F, Wt, c->d_V, c->tab, n, 0.0);
       CK3(cudaEventRecord(ev[1], s));
-      launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_didx, c->d_dw, c->d_gdst,
-                     c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
+      launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
+                     c->d_gdst, c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
       CK3(cudaEventRecord(ev[2], s));
       CK3(cudaEventSynchronize(ev[2]));
       CK3(cudaEventElapsedTime(&t, ev[0], ev[1]));
@@ -714,9 +724,9 @@ wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int3
   }
   CK3(cudaGetLastError());
   for (auto &e : ev) cudaEventDestroy(e);
-  if (ms) {
-    ms[0] = t_march / reps;
-    ms[1] = t_gather / reps;
+  if (ms) {  // per launch
+    ms[0] = t_march / ((double)reps * c->M);
+    ms[1] = t_gather / ((double)reps * c->M);
   }
   if (counts) {
     counts[0] = c->M;

@@ -242,22 +242,40 @@ __global__ void __launch_bounds__(kTX *kTY) march3_kernel(
   const int stencil = Gg.stencil, per = Gg.per;
   const int64_t e0 = Gg.e0, pl = (int64_t)Gg.e0 * Gg.e1;
   if (stencil == kConst7 && per == 0) {
-    // constant weights, no wrap: a register queue of W^n along axis 2
+    // constant weights, no wrap: a register queue of W^n along axis 2, and the next plane's
+    // loads issued before this plane's arithmetic (more bytes in flight per warp)
     const T c0 = fsel<T>(Gg.cw[0], Gg.cwf[0]), c1 = fsel<T>(Gg.cw[1], Gg.cwf[1]),
             c2 = fsel<T>(Gg.cw[2], Gg.cwf[2]), c3 = fsel<T>(Gg.cw[3], Gg.cwf[3]);
     int64_t q = at3(Gg, i, j, tl.k0);
-    T wm = Wn[q - pl], wc = Wn[q];
+    T wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl];
+    int8_t mk = mask[q];
+    T fq = F[q], wo = first ? (T)0 : Wout[q];
+    double vq = V[q];
     for (int k = tl.k0; k < kend; ++k, q += pl) {
-      const T wp = Wn[q + pl];
-      if (mask[q] == kDisc) {
+      T wp2 = (T)0, fq2 = (T)0, wo2 = (T)0;
+      int8_t mk2 = 0;
+      double vq2 = 0.0;
+      if (k + 1 < kend) {  // plane k + 2 is at most the ghost plane n2
+        wp2 = Wn[q + 2 * pl];
+        mk2 = mask[q + pl];
+        fq2 = F[q + pl];
+        if (!first) wo2 = Wout[q + pl];
+        vq2 = V[q + pl];
+      }
+      if (mk == kDisc) {
         const T S = c0 * wc + c1 * (Wn[q - 1] + Wn[q + 1]) + c2 * (Wn[q - e0] + Wn[q + e0]) +
                     c3 * (wm + wp);
-        const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wout[q] - fcn * fsT * F[q];
+        const T out = first ? (T)0.5 * S - fcn * fsT * fq : S - wo - fcn * fsT * fq;
         Wout[q] = out;
-        V[q] += wfn * (double)out;
+        V[q] = vq + wfn * (double)out;
       }
       wm = wc;
       wc = wp;
+      wp = wp2;
+      mk = mk2;
+      fq = fq2;
+      wo = wo2;
+      vq = vq2;
     }
     return;
   }
@@ -295,22 +313,30 @@ __global__ void __launch_bounds__(kTX *kTY) march3_kernel(
 }
 
 // Ghost rules and interpolation of one time level.  Warp w handles receivers w, w + W, ...:
-// lane u < 27 loads donor u (weights wx wy wz multiplied out), a shuffle tree sums them,
-// lane 0 writes the receiver and its filter term.  Every thread then copies Neumann ghosts
-// (gdst <- gsrc).  Donors and ghost sources are discretization or Dirichlet points, so
-// the two parts read nothing the other writes.
+// lane u = 9c + 3b + a (< 27) reads donor (i0 + a, j0 + b, k0 + c) at gbase + ox[a] + oy[b] +
+// oz[c] (per-axis offsets, wrapped on periodic axes) with weight wx[a] wy[b] wz[c], a
+// shuffle tree sums the 27 terms, lane 0 writes the receiver and its filter term.  Every
+// thread then copies Neumann ghosts (gdst <- gsrc).  Donors and ghost sources are
+// discretization or Dirichlet points, so the two parts read nothing the other writes.
 template <typename T>
 __global__ void gather3_kernel(int64_t nrecv, int64_t nghost, const int64_t *__restrict__ ridx,
-                               const int32_t *__restrict__ didx, const double *__restrict__ dw,
-                               const int32_t *__restrict__ gdst, const int32_t *__restrict__ gsrc,
-                               T *W, double *V, const double *__restrict__ wf, int level) {
+                               const int32_t *__restrict__ gbase, const int32_t *__restrict__ goff,
+                               const double *__restrict__ gw, const int32_t *__restrict__ gdst,
+                               const int32_t *__restrict__ gsrc, T *W, double *V,
+                               const double *__restrict__ wf, int level) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const double wl = wf[level];
+  const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
   for (int64_t r = warp; r < nrecv; r += nwarps) {
     double s = 0.0;
-    if (lane < 27) s = dw[r * 27 + lane] * (double)W[didx[r * 27 + lane]];
+    if (lane < 27) {
+      const int32_t *o = goff + r * 9;
+      const double *w = gw + r * 9;
+      const int64_t q = (int64_t)gbase[r] + o[a] + o[3 + b] + o[6 + c];
+      s = w[a] * w[3 + b] * w[6 + c] * (double)W[q];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) {
@@ -395,19 +421,19 @@ void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
 }
 
 void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
-                    const int64_t *ridx, const int32_t *didx, const double *dw,
-                    const int32_t *gdst, const int32_t *gsrc, void *W, double *V,
-                    const double *wf, int level) {
+                    const int64_t *ridx, const int32_t *gbase, const int32_t *goff,
+                    const double *gw, const int32_t *gdst, const int32_t *gsrc, void *W,
+                    double *V, const double *wf, int level) {
   const int threads = 256;
   int64_t need = nrecv * 32 > nghost ? nrecv * 32 : nghost;
   if (need < 1) need = 1;
   const unsigned nb = blocks_for(need, threads);
   if (fp32)
-    gather3_kernel<float><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, didx, dw, gdst, gsrc,
-                                                 (float *)W, V, wf, level);
+    gather3_kernel<float><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, gbase, goff, gw, gdst,
+                                                 gsrc, (float *)W, V, wf, level);
   else
-    gather3_kernel<double><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, didx, dw, gdst, gsrc,
-                                                  (double *)W, V, wf, level);
+    gather3_kernel<double><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, gbase, goff, gw, gdst,
+                                                  gsrc, (double *)W, V, wf, level);
 }
 
 void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
