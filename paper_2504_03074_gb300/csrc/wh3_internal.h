@@ -76,8 +76,9 @@ void launch_init3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int ngrids,
 void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
                    const Tile3 *tiles, const int8_t *mask, const void *Wn, void *Wout,
                    const void *F, const void *Wt, double *V, Tab3 tab, int n, double fs);
-// Receiver r: donor (i0 + a, j0 + b, k0 + c) at gbase[r] + goff[9r + a] + goff[9r + 3 + b] +
-// goff[9r + 6 + c] with weight gw[9r + a] gw[9r + 3 + b] gw[9r + 6 + c] (wx, wy, wz).
+// Receiver r of R: donor (i0 + a, j0 + b, k0 + c) at gbase[r] + goff[a R + r] +
+// goff[(3 + b) R + r] + goff[(6 + c) R + r] with weight gw[a R + r] gw[(3 + b) R + r]
+// gw[(6 + c) R + r] (planes of wx, wy, wz).
 void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
                     const int64_t *ridx, const int32_t *gbase, const int32_t *goff,
                     const double *gw, const int32_t *gdst, const int32_t *gsrc, void *W,

@@ -306,7 +306,7 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
                      cudaMemcpyHostToDevice));
   }
   // interpolation: receiver index; donor corner index, per-axis offsets (wrapped on
-  // periodic axes) and per-axis weights
+  // periodic axes) and per-axis weights, as planes of R entries
   const int64_t R = c->nrecv;
   std::vector<int64_t> ridx(R > 0 ? R : 1);
   std::vector<int32_t> gbase(R > 0 ? R : 1), goff(R > 0 ? R * 9 : 1);
@@ -323,12 +323,12 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
       for (int t = 0; t < 3; ++t) {
         int d[3] = {c0[0], c0[1], c0[2]};
         d[a] += t;
-        goff[r * 9 + 3 * a + t] = (int32_t)(eidx(DG, d[0], d[1], d[2]) - corner);
+        goff[(3 * a + t) * R + r] = (int32_t)(eidx(DG, d[0], d[1], d[2]) - corner);
       }
     for (int t = 0; t < 3; ++t) {
-      gw[r * 9 + t] = c->wx[r * 3 + t];
-      gw[r * 9 + 3 + t] = c->wy[r * 3 + t];
-      gw[r * 9 + 6 + t] = c->wz[r * 3 + t];
+      gw[t * R + r] = c->wx[r * 3 + t];
+      gw[(3 + t) * R + r] = c->wy[r * 3 + t];
+      gw[(6 + t) * R + r] = c->wz[r * 3 + t];
     }
   }
   // Neumann ghosts next to discretization points

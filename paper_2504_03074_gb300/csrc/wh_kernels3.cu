@@ -11,8 +11,9 @@
 //   - gather3: the ghost rules (Neumann: centred normal derivative, a copy of the inward
 //     value) and the explicit interpolation of every receiver from its 3 x 3 x 3 donor
 //     stencil (Sec. 3.1, Algorithm 2: boundary conditions and interpolation after every
-//     grid has advanced), warp-cooperative: one warp per receiver, one lane per donor, a
-//     shuffle reduction.  Receivers add their filter term too.
+//     grid has advanced), one thread per receiver evaluating the tensor product axis by
+//     axis (the FP64 pipe, not memory, bounds a lane-per-donor form on GB300).  Receivers
+//     add their filter term too.
 // Setup kernels compute the mapped-Laplacian coefficients a_kl, b_k from the metrics with
 // the CFL bound (Eq. dtForCartesian), and the stencil weights for one dt.
 #include <cuda_runtime.h>
@@ -223,8 +224,9 @@ __device__ __forceinline__ float fsel<float>(double, float f) { return f; }
 
 // One time step n -> n + 1 of every grid (Eq. WaveSchemeexplicit) with the fused filter
 // term of level n + 1.  Block = one Tile3; each thread marches kTZ points along axis 2.
+// Register caps for occupancy: FP32 48 (5 blocks per SM), FP64 64 (4), neither spills.
 template <typename T>
-__global__ void __launch_bounds__(kTX *kTY) march3_kernel(
+__global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kernel(
     const Grid3Dev *__restrict__ grids, const Tile3 *__restrict__ tiles,
     const int8_t *__restrict__ mask, const T *__restrict__ Wn, T *__restrict__ Wout,
     const T *__restrict__ F, const T *__restrict__ Wt, double *__restrict__ V, Tab3 tab, int n,
@@ -312,42 +314,68 @@ __global__ void __launch_bounds__(kTX *kTY) march3_kernel(
   }
 }
 
-// Ghost rules and interpolation of one time level.  Warp w handles receivers w, w + W, ...:
-// lane u = 9c + 3b + a (< 27) reads donor (i0 + a, j0 + b, k0 + c) at gbase + ox[a] + oy[b] +
-// oz[c] (per-axis offsets, wrapped on periodic axes) with weight wx[a] wy[b] wz[c], a
-// shuffle tree sums the 27 terms, lane 0 writes the receiver and its filter term.  Every
-// thread then copies Neumann ghosts (gdst <- gsrc).  Donors and ghost sources are
+// FP32 -> FP64 widening with integer operations (binary32 -> binary64: same sign, exponent
+// + 896, fraction followed by 29 zeros); zero, subnormal, inf and NaN take the hardware
+// conversion.  The hardware conversion is an FP64-pipe instruction, and GB300 has few.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// Ghost rules and interpolation of one time level, one thread per receiver: the 27 donors
+// (i0 + a, j0 + b, k0 + c) at gbase + ox[a] + oy[b] + oz[c] (per-axis offsets, periodic wrap
+// resolved at set-up) are all loaded first, then the tensor product is evaluated as rows
+// sum_a wx[a] u, columns sum_b wy[b] row_b, and sum_c wz[c] col_c: 39 FP64 operations per
+// receiver.  Metadata are planes of nrecv entries (goff[t * nrecv + r], gw[t * nrecv + r],
+// t = 0..8: x, y, z), read coalesced.  The receiver's filter term is added as it is written.
+// Every thread then copies Neumann ghosts (gdst <- gsrc).  Donors and ghost sources are
 // discretization or Dirichlet points, so the two parts read nothing the other writes.
 template <typename T>
-__global__ void gather3_kernel(int64_t nrecv, int64_t nghost, const int64_t *__restrict__ ridx,
-                               const int32_t *__restrict__ gbase, const int32_t *__restrict__ goff,
-                               const double *__restrict__ gw, const int32_t *__restrict__ gdst,
-                               const int32_t *__restrict__ gsrc, T *W, double *V,
-                               const double *__restrict__ wf, int level) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+__global__ void __launch_bounds__(256) gather3_kernel(
+    int64_t nrecv, int64_t nghost, const int64_t *__restrict__ ridx,
+    const int32_t *__restrict__ gbase, const int32_t *__restrict__ goff,
+    const double *__restrict__ gw, const int32_t *__restrict__ gdst,
+    const int32_t *__restrict__ gsrc, T *W, double *V, const double *__restrict__ wf,
+    int level) {
   const double wl = wf[level];
-  const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
-  for (int64_t r = warp; r < nrecv; r += nwarps) {
-    double s = 0.0;
-    if (lane < 27) {
-      const int32_t *o = goff + r * 9;
-      const double *w = gw + r * 9;
-      const int64_t q = (int64_t)gbase[r] + o[a] + o[3 + b] + o[6 + c];
-      s = w[a] * w[3 + b] * w[6 + c] * (double)W[q];
-    }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrecv; r += stride) {
+    int32_t o[9];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      const T v = (T)s;
-      const int64_t q = ridx[r];
-      W[q] = v;
-      V[q] += wl * (double)v;
+    for (int t = 0; t < 9; ++t) o[t] = goff[t * nrecv + r];
+    const int64_t b0 = gbase[r];
+    T u[27];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[9 * c + 3 * b + a] = W[b0 + o[a] + o[3 + b] + o[6 + c]];
+    double w[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) w[t] = gw[t * nrecv + r];
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double col = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T *x = u + 9 * c + 3 * b;
+        const double row = w[0] * widen(x[0]) + w[1] * widen(x[1]) + w[2] * widen(x[2]);
+        col = fma(w[3 + b], row, col);
+      }
+      s = fma(w[6 + c], col, s);
     }
+    const T v = (T)s;
+    const int64_t q = ridx[r];
+    W[q] = v;
+    V[q] += wl * widen(v);
   }
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nghost;
-       g += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nghost; g += stride)
     W[gdst[g]] = W[gsrc[g]];
 }
 
@@ -425,7 +453,7 @@ void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
                     const double *gw, const int32_t *gdst, const int32_t *gsrc, void *W,
                     double *V, const double *wf, int level) {
   const int threads = 256;
-  int64_t need = nrecv * 32 > nghost ? nrecv * 32 : nghost;
+  int64_t need = nrecv > nghost ? nrecv : nghost;
   if (need < 1) need = 1;
   const unsigned nb = blocks_for(need, threads);
   if (fp32)
