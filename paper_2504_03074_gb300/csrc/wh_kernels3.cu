@@ -248,36 +248,80 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
     // loads issued before this plane's arithmetic (more bytes in flight per warp)
     const T c0 = fsel<T>(Gg.cw[0], Gg.cwf[0]), c1 = fsel<T>(Gg.cw[1], Gg.cwf[1]),
             c2 = fsel<T>(Gg.cw[2], Gg.cwf[2]), c3 = fsel<T>(Gg.cw[3], Gg.cwf[3]);
-    int64_t q = at3(Gg, i, j, tl.k0);
-    T wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl];
-    int8_t mk = mask[q];
-    T fq = F[q], wo = first ? (T)0 : Wout[q];
-    double vq = V[q];
-    for (int k = tl.k0; k < kend; ++k, q += pl) {
-      T wp2 = (T)0, fq2 = (T)0, wo2 = (T)0;
-      int8_t mk2 = 0;
-      double vq2 = 0.0;
-      if (k + 1 < kend) {  // plane k + 2 is at most the ghost plane n2
-        wp2 = Wn[q + 2 * pl];
-        mk2 = mask[q + pl];
-        fq2 = F[q + pl];
-        if (!first) wo2 = Wout[q + pl];
-        vq2 = V[q + pl];
+    if constexpr (sizeof(T) == 4) {
+      // FP32 (latency-bound): the next plane's x/y neighbours are prefetched too
+      int64_t q = at3(Gg, i, j, tl.k0);
+      T wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl];
+      T sx = Wn[q - 1] + Wn[q + 1], sy = Wn[q - e0] + Wn[q + e0];
+      int8_t mk = mask[q];
+      T fq = F[q], wo = first ? (T)0 : Wout[q];
+      double vq = V[q];
+      for (int k = tl.k0; k < kend; ++k, q += pl) {
+        T wp2 = (T)0, fq2 = (T)0, wo2 = (T)0, xm2 = (T)0, xp2 = (T)0, ym2 = (T)0, yp2 = (T)0;
+        int8_t mk2 = 0;
+        double vq2 = 0.0;
+        if (k + 1 < kend) {  // plane k + 2 is at most the ghost plane n2
+          const int64_t q1 = q + pl;
+          wp2 = Wn[q1 + pl];
+          xm2 = Wn[q1 - 1];
+          xp2 = Wn[q1 + 1];
+          ym2 = Wn[q1 - e0];
+          yp2 = Wn[q1 + e0];
+          mk2 = mask[q1];
+          fq2 = F[q1];
+          if (!first) wo2 = Wout[q1];
+          vq2 = V[q1];
+        }
+        if (mk == kDisc) {
+          const T S = c0 * wc + c1 * sx + c2 * sy + c3 * (wm + wp);
+          const T out = first ? (T)0.5 * S - fcn * fsT * fq : S - wo - fcn * fsT * fq;
+          Wout[q] = out;
+          V[q] = vq + wfn * (double)out;
+        }
+        wm = wc;
+        wc = wp;
+        wp = wp2;
+        sx = xm2 + xp2;
+        sy = ym2 + yp2;
+        mk = mk2;
+        fq = fq2;
+        wo = wo2;
+        vq = vq2;
       }
-      if (mk == kDisc) {
-        const T S = c0 * wc + c1 * (Wn[q - 1] + Wn[q + 1]) + c2 * (Wn[q - e0] + Wn[q + e0]) +
-                    c3 * (wm + wp);
-        const T out = first ? (T)0.5 * S - fcn * fsT * fq : S - wo - fcn * fsT * fq;
-        Wout[q] = out;
-        V[q] = vq + wfn * (double)out;
+    } else {
+      // FP64 (FP64-pipe bound): neighbours loaded in place (the extra registers of
+      // their prefetch measured 1.6% slower here, 10% faster in FP32)
+      int64_t q = at3(Gg, i, j, tl.k0);
+      T wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl];
+      int8_t mk = mask[q];
+      T fq = F[q], wo = first ? (T)0 : Wout[q];
+      double vq = V[q];
+      for (int k = tl.k0; k < kend; ++k, q += pl) {
+        T wp2 = (T)0, fq2 = (T)0, wo2 = (T)0;
+        int8_t mk2 = 0;
+        double vq2 = 0.0;
+        if (k + 1 < kend) {  // plane k + 2 is at most the ghost plane n2
+          wp2 = Wn[q + 2 * pl];
+          mk2 = mask[q + pl];
+          fq2 = F[q + pl];
+          if (!first) wo2 = Wout[q + pl];
+          vq2 = V[q + pl];
+        }
+        if (mk == kDisc) {
+          const T S = c0 * wc + c1 * (Wn[q - 1] + Wn[q + 1]) + c2 * (Wn[q - e0] + Wn[q + e0]) +
+                      c3 * (wm + wp);
+          const T out = first ? (T)0.5 * S - fcn * fsT * fq : S - wo - fcn * fsT * fq;
+          Wout[q] = out;
+          V[q] = vq + wfn * (double)out;
+        }
+        wm = wc;
+        wc = wp;
+        wp = wp2;
+        mk = mk2;
+        fq = fq2;
+        wo = wo2;
+        vq = vq2;
       }
-      wm = wc;
-      wc = wp;
-      wp = wp2;
-      mk = mk2;
-      fq = fq2;
-      wo = wo2;
-      vq = vq2;
     }
     return;
   }
