@@ -394,7 +394,34 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
                          "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
     out["solve_unit_square"] = solve
     out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush)
+    out["roofline_probe_3d_512"] = measure_cube_probe(WH, torch, stream)
     return out
+
+
+def measure_cube_probe(WH, torch, stream):
+    """The 3D half of the roofline probe: one Cartesian 512^3 grid on [0, 1]^3 (Dirichlet,
+    omega 10, no interpolation, HBM resident), second order, FP64 and FP32: the march
+    kernel's device time per launch over one iteration's steps; effective bandwidth counts
+    the compulsory bytes of one update (49 B FP64, 33 B FP32: state, forcing, FP64 filter
+    read and write, mask)."""
+    from paper_2504_03074_gb300 import grids3 as G3
+    hbm = float(measured_peaks().get("hbm_gbs", 6793.0))
+    cube = G3.unit_cube_problem(512, omega=10.0)
+    probe = {"workload": "unit cube 512^3, Dirichlet, omega 10, order 2, no interpolation",
+             "hbm_peak_gbs": hbm}
+    for name, prec, bpl in (("fp64", WH.FP64, 49.0), ("fp32", WH.FP32, 33.0)):
+        sp = WH.Solver(cube, stream=stream, precision=prec)
+        tp = sp.prepare()
+        ms = sp.profile_kernels(reps=1)["march"][0]
+        glups = tp.n_active / (ms * 1e-3) / 1e9
+        rec = {"march_us": ms * 1e3, "value": glups, "unit": "GLUP/s", "M": tp.M,
+               "effective_gbs": glups * bpl, "hbm_frac": glups * bpl / hbm}
+        if prec == WH.FP64:
+            rec["fp64_frac"] = glups * 15.0 / 1e3 / FP64_PEAK_TFLOPS
+        probe[name] = rec
+        sp.close()
+        del sp
+    return probe
 
 
 def measure_sphere(WH, torch, stream, flush):
