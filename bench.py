@@ -35,6 +35,22 @@ WORKLOAD = ("disk-in-square overset: background [-2,2]^2 1024^2 + annulus 2048x6
 L2_BYTES = 129 * 1024 * 1024
 
 
+def whole_job(lups_local, t_local, world):
+    """Whole-job throughput of `world` replicas: the point updates of all ranks divided by
+    the slowest rank's time (max over ranks).  Returns (GLUP/s, t_max in s)."""
+    import torch
+    if world <= 1:
+        return lups_local / t_local / 1e9, t_local
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    n = torch.tensor([float(lups_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return float(n.item()) / t_max / 1e9, t_max
+
+
 def rank_info():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -625,11 +641,7 @@ def main():
         launches = s.last_launch_count() * args.steps
     ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = lups * args.steps * world / t_max / 1e9
+    value, t_max = whole_job(lups * args.steps, t_local, world)
 
     # end-to-end through the public API with host buffers (pinned), copies inside
     hin = torch.zeros(n, dtype=torch.float64).pin_memory()
