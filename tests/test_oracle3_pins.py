@@ -93,6 +93,25 @@ def test_mapped_laplacian_second_order(o3, kind):
     assert 1.8 < rate < 2.3, (errs, rate)
 
 
+def test_mapped_laplacian_with_sound_speed(o3):
+    """With c(x) on a curvilinear grid the operator is c(x)^2 times the mapped Laplacian
+    (Eq. HelmholtzBVP, c^2 folded into every a_kl and b_k): second order against
+    c^2 Lap u on the spherical shell."""
+    errs = []
+    for s in (1, 2):
+        g = G3.shell_grid("shell", 32 * s, 16 * s + 1 - s, 8 * s + 1 - s, 0.5, 0.3, 40.0, 140.0)
+        X = g.coords()
+        c2 = (1.0 + 0.3 * np.sin(3.0 * X[0]) * np.cos(2.0 * X[2])) ** 2
+        prob = _single(g)
+        prob.c2 = [c2]
+        orc = o3.Oracle3(prob)
+        Xe = _ext_coords(g)
+        out = _interior(g, orc.apply_lap(0, _smooth(Xe)))
+        ref = c2 * _interior(g, _smooth_lap(Xe))
+        errs.append(np.max(np.abs(out - ref)[g.mask == G.DISC]))
+    assert 1.8 < math.log2(errs[0] / errs[1]) < 2.3, errs
+
+
 def test_shell_coefficients_analytic(o3):
     """Spherical coordinates: Lap u = u_rr + (2/r) u_r + u_thth / r^2 + cot(th) u_th / r^2
     + u_phph / (r sin th)^2, so in the shell's parameters a00 = 1/(2 pi r sin th)^2,
