@@ -34,6 +34,19 @@ def _cube_c2(n=13):
     return prob
 
 
+def _sphere_c2():
+    # c(x) = 1 + 0.2 exp(-|x - x1|^2 / 0.2^2) on every grid (per-point weights on the
+    # background, c^2 folded into the shell's and patches' coefficients)
+    prob = _small_sphere()
+    c2 = []
+    for g in prob.grids:
+        X = g.coords()
+        c = 1.0 + 0.2 * np.exp(-((X[0] - 0.55) ** 2 + (X[1] + 0.3) ** 2 + (X[2] - 0.4) ** 2) / 0.04)
+        c2.append(c * c)
+    prob.c2 = c2
+    return prob
+
+
 CASES = [
     ("sphere-in-box-48", _small_sphere),
     ("box-in-box", lambda: G3.box_in_box_problem()),
@@ -41,6 +54,7 @@ CASES = [
     ("neumann-cube-21", lambda: G3.unit_cube_problem(21, omega=7.0, bc=G.BC_NEUMANN, b=20.0)),
     ("periodic-cube-17", lambda: G3.unit_cube_problem(17, omega=5.0, bc=G.BC_PERIODIC, b=20.0)),
     ("cube-c(x)-13", _cube_c2),
+    ("sphere-in-box-48-c(x)", _sphere_c2),
 ]
 
 
