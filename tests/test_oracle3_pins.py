@@ -279,3 +279,47 @@ def test_rejects_neumann_on_non_orthogonal_axis(o3):
     g.ortho = 4  # declare (0, 2) non-orthogonal: the Neumann axis 2 then is not normal
     with pytest.raises(ValueError):
         o3.Oracle3(_single(g))
+
+
+# ------------------------------------------------------- solution accuracy
+
+@pytest.mark.parametrize("bc", [G.BC_DIRICHLET, G.BC_NEUMANN])
+def test_eigenfunction_solution_second_order_3d(o3, bc):
+    """Helmholtz solution phi = sin(pi x) sin(pi y) sin(pi z) on the Dirichlet cube and
+    phi = cos(pi x) cos(pi y) cos(pi z) on the Neumann cube, with f = (omega^2 - 3 pi^2) phi:
+    the WaveHoltz fixed point reached by the oracle's GMRES (Sec. 4.3) converges to phi at
+    second order."""
+    from oracle.oracle import gmres
+    om = 3.0
+    fn = np.sin if bc == G.BC_DIRICHLET else np.cos
+    errs = []
+    for n in (9, 17):
+        prob = G3.unit_cube_problem(n, omega=om, bc=bc)
+        X = prob.grids[0].coords()
+        phi = fn(np.pi * X[0]) * fn(np.pi * X[1]) * fn(np.pi * X[2])
+        prob.f = [(om ** 2 - 3 * np.pi ** 2) * phi]
+        v, its, hist = gmres(o3.Oracle3(prob), tol=1e-12, restart=100, max_it=400)
+        errs.append(np.max(np.abs(v.reshape(n, n, n) - phi)))
+    assert 1.8 < math.log2(errs[0] / errs[1]) < 2.3, errs
+
+
+def test_overset_solution_second_order_3d(o3):
+    """On the box-in-box overset grid the solution of the Dirichlet problem with
+    phi = prod sin(pi (x_m + 1) / 2) and f = (omega^2 - 3 pi^2 / 4) phi converges at second
+    order (second-order march, third-order interpolation) under refinement of both grids."""
+    from oracle.oracle import gmres
+    om = 3.0
+    errs = []
+    for nb, ni in ((12, 10), (23, 19)):
+        prob = G3.box_in_box_problem(nb=nb, ni=ni, omega=om)
+
+        def phi(X):
+            return (np.sin(np.pi * (X[0] + 1) / 2) * np.sin(np.pi * (X[1] + 1) / 2) *
+                    np.sin(np.pi * (X[2] + 1) / 2))
+
+        prob.f = [(om ** 2 - 3 * np.pi ** 2 / 4) * phi(g.coords()) for g in prob.grids]
+        orc = o3.Oracle3(prob)
+        v, its, hist = gmres(orc, tol=1e-12, restart=200, max_it=600)
+        ref = np.concatenate([phi(g.coords()).ravel() for g in prob.grids])
+        errs.append(np.max(np.abs(v - ref)[orc.active()]))
+    assert 1.8 < math.log2(errs[0] / errs[1]) < 2.4, errs
