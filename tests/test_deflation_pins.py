@@ -1,0 +1,101 @@
+"""Pins for WaveHoltz with deflation (Algorithm 3) on the oracle (CPU only): on the unit
+square the discrete eigenmodes are DST-I modes with known eigenvalues, so every deflated
+iterate has a closed form."""
+import math
+
+import numpy as np
+import pytest
+import scipy.fft as sfft
+
+from paper_2504_03074_gb300 import grids as G
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _square_modes(prob, ts):
+    """DST-I data of the 64^2 unit square: f_hat, lambda_h^2 and beta_d(lambda~) per mode
+    (Eqs. betad, discreteExplicitLambdaTilde; eigenvalues of D+D- with Dirichlet data)."""
+    from oracle.oracle import beta_d_sum, lambda_tilde
+    n = prob.grids[0].n[0]
+    h = prob.grids[0].h[0]
+    fh = sfft.dstn(prob.f[0][1:-1, 1:-1], type=1, norm="ortho")
+    m = np.arange(1, n - 1)
+    sx = np.sin(m * np.pi * h / 2) ** 2
+    lam2 = (4 / h ** 2) * (sx[None, :] + sx[:, None])
+    lt = lambda_tilde(np.sqrt(lam2).ravel(), ts.dt)
+    bd = beta_d_sum(lt, ts.omega_e, ts.dt, ts.Nt, ts.alpha).reshape(lam2.shape)
+    return fh, lam2, bd
+
+
+def _mode_vector(n, my, mx):
+    """Orthonormal (Euclidean, compact n x n vector) DST-I mode (my, mx), zero on the
+    boundary."""
+    phi = np.zeros((n, n))
+    z = np.zeros((n - 2, n - 2))
+    z[my - 1, mx - 1] = 1.0
+    phi[1:-1, 1:-1] = sfft.idstn(z, type=1, norm="ortho")
+    return phi.ravel()
+
+
+@pytest.mark.parametrize("K", [1, 8])
+def test_deflated_iterates_match_closed_form(oracle_mod, K):
+    """Deflating the K modes with |beta_d| closest to 1: the k-th deflated iterate from
+    v = 0 is sum over kept modes (1 - beta_m^k) U_m Phi_m (the deflated components stay 0),
+    the inflated iterate adds U_m Phi_m for the deflated modes, with
+    U_m = f_m / (omega^2 - lambda_m^2) (Algorithm 3; c2 reading: omega-hat = omega)."""
+    from oracle import deflation as D
+    prob = G.unit_square_problem(64, 2, 10.0, seed=0)
+    orc = oracle_mod.Oracle(prob)
+    ts = orc.time
+    fh, lam2, bd = _square_modes(prob, ts)
+    order = np.argsort(-np.abs(bd).ravel())[:K]
+    dmask = np.zeros(bd.size, bool)
+    dmask[order] = True
+    dmask = dmask.reshape(bd.shape)
+    n = 64
+    Phi = np.array([_mode_vector(n, i + 1, j + 1) for i, j in zip(*np.nonzero(dmask))])
+    lam2_d = lam2[dmask]
+    f = prob.f[0].ravel()
+    U = fh / (prob.omega ** 2 - lam2)
+    iters = 12
+    u, hist, res = D.deflated_fpi(orc, Phi, lam2_d, f, prob.omega, iters)
+    for k in (1, 5, iters):
+        kept = np.where(dmask, 0.0, (1 - bd ** k) * U)
+        ref = np.zeros((n, n))
+        ref[1:-1, 1:-1] = sfft.idstn(kept, type=1, norm="ortho")
+        got = hist[k].reshape(n, n)
+        assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref)), k
+    # inflation adds the deflated modes' Helmholtz components exactly
+    full = np.where(dmask, U, (1 - bd ** iters) * U)
+    ref = np.zeros((n, n))
+    ref[1:-1, 1:-1] = sfft.idstn(full, type=1, norm="ortho")
+    assert np.max(np.abs(u.reshape(n, n) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_deflated_rate_is_largest_kept_beta(oracle_mod):
+    """Theorem (WaveHoltz FPI convergence with deflation): the deflated zero-forcing map
+    P S (P the projector off the deflated modes) sends a kept mode to beta_d times itself
+    and a deflated mode to 0, so its spectral radius is the largest |beta_d| kept; deflating
+    the 8 modes nearest omega lowers it from 0.99965 here."""
+    from oracle import deflation as D
+    prob = G.unit_square_problem(64, 2, 10.0, seed=0)
+    orc = oracle_mod.Oracle(prob)
+    fh, lam2, bd = _square_modes(prob, orc.time)
+    order = np.argsort(-np.abs(bd).ravel())
+    K = 8
+    idx = [np.unravel_index(q, bd.shape) for q in order]
+    Phi = np.array([_mode_vector(64, i + 1, j + 1) for i, j in idx[:K]])
+    for i, j in idx[:K + 3]:
+        phi = _mode_vector(64, i + 1, j + 1)
+        out = D.deflate(orc.iterate(phi, False), Phi)
+        expect = 0.0 if (i, j) in idx[:K] else bd[i, j]
+        assert np.max(np.abs(out - expect * phi)) < 1e-13
+    mu = np.abs(bd.ravel()[order[K]])
+    assert np.abs(bd).max() == pytest.approx(0.99965, abs=1e-5)
+    assert mu < np.abs(bd).max()
+    # the rate: error after k deflated iterations decays like mu^k along the slowest kept mode
+    iters = 30
+    u, hist, res = D.deflated_fpi(orc, Phi, lam2[tuple(np.array(idx[:K]).T)],
+                                  prob.f[0].ravel(), prob.omega, iters)
+    ratios = [res[k + 1] / res[k] for k in range(iters - 6, iters - 1)]
+    assert max(ratios) <= mu + 1e-9
