@@ -273,7 +273,10 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, doub
  * cycles whose wave solves use the FP32 march take the residual to max(tol, 1e-4) (or
  * until a cycle no longer halves it), then FP64-march cycles continue from that iterate to
  * tol, confirmed by a true FP64 residual.  The orthogonalisation, the updates and all
- * reductions are FP64 throughout.  WH_FPI iterates with the context's march.  Returns
+ * reductions are FP64 throughout.  WH_FPI iterates with the context's march; with a
+ * deflation set (wh_set_deflation) it removes the set's components after every iteration
+ * and, on return (converged or not), adds back the Helmholtz solution's components along
+ * the set (Algorithm 3); its residuals are those of the deflated iterates.  Returns
  * WH_ERR_NOT_CONVERGED (u holds the last iterate) when max_it is reached,
  * WH_ERR_DIVERGED on NaN/Inf. */
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
@@ -286,6 +289,21 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
  * max(tol, 1e-4), then FP64 ones).  u: DEVICE compact vector
  * of all instances (initial guess in, solutions out); stats: host array of one entry per
  * instance (seconds is the whole batch's).  max_it bounds the batched wave solves. */
+/* Deflation set for WH_FPI (Algorithm 3, Sec. 4.4): k discrete eigenpairs (phi_m,
+ * lambda_m^2) of the spatial operator (c^2 L_h phi = -lambda^2 phi with the boundary and
+ * interpolation constraints).  After every WaveHoltz iteration of wh_solve(WH_FPI) the
+ * iterate loses its components along the set, v <- v - sum_m (v, phi_m) phi_m; on return
+ * the solution gains u = v + sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m.  Inner products
+ * are plain sums over the compact vector, so the rows must be orthonormal in it (exact for
+ * self-adjoint discretizations; an approximation on overset grids).  phi: DEVICE pointer to
+ * k compact vectors, row m at phi + m * n_total; the context keeps the pointer (not a copy):
+ * the caller owns the memory and keeps it alive and unchanged while the set is in use.
+ * lambda2: HOST array of k values, copied.  k = 0 removes the set.  Two-dimensional
+ * single-instance contexts only.  Errors: WH_ERR_ARG (k < 0 or > 4000, null pointers,
+ * non-finite lambda2; at solve time omega^2 equal to a lambda_m^2), WH_ERR_STATE (a 3D
+ * context; at solve time a batch). */
+wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2);
+
 wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,
                          wh_stats *stats);
 

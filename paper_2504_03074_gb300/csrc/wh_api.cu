@@ -54,6 +54,12 @@ struct wh_ctx {
   wh_options opt{};
   // 0 until the first grid is added, then 2 or 3; three-dimensional problems live in c3
   int dim = 0;
+  // deflation set of wh_solve(WH_FPI): caller-owned device eigenvectors, host eigenvalues,
+  // and the compact forcing for the final inflation
+  int defl_k = 0;
+  const double *defl_phi = nullptr;
+  std::vector<double> defl_lam2;
+  double *d_fcompact = nullptr;
   wh3::Ctx3 *c3 = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -2157,10 +2163,46 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     if (stats) *stats = S;
     return code;
   };
-  if (method == WH_FPI) {  // Algorithm 1 with the context's march precision
+  if (method == WH_FPI) {  // Algorithm 1 (Algorithm 3 with a deflation set)
+    const int K = ctx->defl_k;
+    if (K > 0) {
+      if (ctx->ninst != 1) return finish(fail(ctx, WH_ERR_STATE, "deflation needs one instance"));
+      for (double l2 : ctx->defl_lam2)
+        if (l2 == ctx->ti.omega * ctx->ti.omega)
+          return finish(fail(ctx, WH_ERR_ARG, "omega^2 equals a deflated eigenvalue"));
+      if ((st = ensure_red(ctx, K))) return finish(st);
+      if (!ctx->d_fcompact && (st = dalloc(ctx, &ctx->d_fcompact, (size_t)n))) return finish(st);
+      std::vector<double> fc((size_t)n, 0.0);
+      int64_t o = 0;
+      for (const auto &H : ctx->grids) {
+        const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
+        if (!H.f.empty()) std::copy(H.f.begin(), H.f.end(), fc.begin() + o);
+        o += np;
+      }
+      CK(cudaMemcpy(ctx->d_fcompact, fc.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // on every return: add the Helmholtz solution's components along the deflation set,
+    // u += sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m
+    auto inflate = [&]() -> wh_status {
+      if (K == 0) return WH_OK;
+      std::vector<double> c((size_t)K);
+      wh_status e = multidot(ctx, ctx->defl_phi, n, K, ctx->d_fcompact, n, c.data());
+      if (e) return e;
+      const double om2 = ctx->ti.omega * ctx->ti.omega;
+      for (int m = 0; m < K; ++m) c[m] /= om2 - ctx->defl_lam2[m];
+      CK(cudaMemcpyAsync(ctx->d_red, c.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_gemv_acc(grid1d(n), s, ctx->defl_phi, n, K, ctx->d_red, u, n);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(s));  // c is read by the copy above
+      return WH_OK;
+    };
     for (int k = 0; k < max_it; ++k) {
       if ((st = iterate_device(ctx, 1, u, w0))) return finish(st);
       L.products[ctx->active] += 1;
+      if (K > 0) {  // deflate: w0 -= sum_m (w0, phi_m) phi_m
+        if ((st = multidot(ctx, ctx->defl_phi, n, K, w0, n, nullptr))) return finish(st);
+        launch_multi_axpy(grid1d(n), s, ctx->defl_phi, n, K, ctx->d_red, w0, n);
+      }
       launch_sub(grid1d(n), s, w0, u, w1, n);
       CK(cudaMemcpyAsync(u, w0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       double d[2];
@@ -2172,9 +2214,10 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
       if (!std::isfinite(r)) return finish(fail(ctx, WH_ERR_DIVERGED, "FPI residual is %g", r));
       if (r <= tol) {
         S.converged = 1;
-        return finish(WH_OK);
+        return finish(inflate());
       }
     }
+    if ((st = inflate())) return finish(st);
     return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "FPI: %d iterations, residual %g", max_it,
                        S.residual));
   }
@@ -2252,6 +2295,19 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
       return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
                          S.residual));
   }
+}
+
+wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2) {
+  if (!ctx) return WH_ERR_ARG;
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "deflation is not available on 3D contexts");
+  if (k < 0 || k > 4000) return fail(ctx, WH_ERR_ARG, "deflation set size must be in [0, 4000]");
+  if (k > 0 && (!phi || !lambda2)) return fail(ctx, WH_ERR_ARG, "null deflation arrays");
+  for (int m = 0; m < k; ++m)
+    if (!std::isfinite(lambda2[m])) return fail(ctx, WH_ERR_ARG, "non-finite eigenvalue");
+  ctx->defl_k = k;
+  ctx->defl_phi = k > 0 ? phi : nullptr;
+  ctx->defl_lam2.assign(lambda2 ? lambda2 : nullptr, lambda2 ? lambda2 + k : nullptr);
+  return WH_OK;
 }
 
 wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,

@@ -93,7 +93,7 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
-           "wh_set_interp3"]
+           "wh_set_interp3", "wh_set_deflation"]
 
 
 def lib_path():
@@ -121,6 +121,7 @@ def lib():
     L.wh_set_interp.argtypes = [vp, C.POINTER(InterpDesc)]
     L.wh_add_grid3.argtypes = [vp, C.POINTER(Grid3Desc), C.POINTER(C.c_int32)]
     L.wh_set_interp3.argtypes = [vp, C.POINTER(Interp3Desc)]
+    L.wh_set_deflation.argtypes = [vp, C.c_int32, vp, vp]
     L.wh_set_forcing.argtypes = [vp, C.c_int32, vp]
     L.wh_prepare.argtypes = [vp, C.c_double, C.POINTER(TimeInfo)]
     L.wh_prepare_batch.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(TimeInfo)]
@@ -315,6 +316,19 @@ class Solver:
         st.history = hist[:st.n_history].copy()
         st.status = STATUS.get(status, status)
         return st
+
+    def set_deflation(self, phi=None, lam2=None):
+        """Deflation set of FPI solves (Algorithm 3): phi a contiguous float64 CUDA tensor of
+        shape (k, n_total) with orthonormal rows (kept by reference: keep it alive and
+        unchanged), lam2 the k eigenvalues lambda_m^2; None removes the set."""
+        if phi is None:
+            self._check(self.L.wh_set_deflation(self.h, 0, None, None))
+            self._defl = None
+            return
+        lam = np.ascontiguousarray(lam2, np.float64)
+        assert phi.is_cuda and phi.is_contiguous() and phi.shape[0] == lam.size
+        self._check(self.L.wh_set_deflation(self.h, int(lam.size), _ptr(phi), _ptr(lam)))
+        self._defl = (phi, lam)
 
     def solve_batch(self, u, tol=1e-8, max_it=500, restart=50):
         """Batched solve of every instance in place on device tensor u; list of Stats."""

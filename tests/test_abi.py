@@ -252,3 +252,27 @@ def test_grid3_validation_on_host(W):
     assert L.wh_set_tuning(h, C.byref(W.Tuning(-1, 1, 0, -1, 1, 0.0, 0))) == -3
     assert L.wh_set_coefficient(h, 0, None) == -3
     L.wh_destroy(h)
+
+
+def test_deflation_validation_on_host(W):
+    """wh_set_deflation checks its arguments without touching the device; 3D contexts
+    refuse it."""
+    L = W.lib()
+    h = _ctx(W, order=2)
+    lam = (C.c_double * 2)(1.0, 2.0)
+    assert L.wh_set_deflation(h, -1, None, None) == -1
+    assert L.wh_set_deflation(h, 2, None, lam) == -1
+    assert L.wh_set_deflation(h, 2, C.c_void_p(64), None) == -1
+    bad = (C.c_double * 1)(float("nan"))
+    assert L.wh_set_deflation(h, 1, C.c_void_p(64), bad) == -1
+    assert L.wh_set_deflation(h, 2, C.c_void_p(64), lam) == 0
+    assert L.wh_set_deflation(h, 0, None, None) == 0
+    L.wh_destroy(h)
+    from paper_2504_03074_gb300 import grids3 as G3
+    h = _ctx(W, order=2)
+    cube = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
+    d, keep = _desc3(W, cube)
+    gid = C.c_int32()
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0
+    assert L.wh_set_deflation(h, 2, C.c_void_p(64), lam) == -3
+    L.wh_destroy(h)
