@@ -176,7 +176,21 @@ def cpu_baseline(problem, sample):
     dt = time.perf_counter() - t0
     lups = problem.n_active * orc.time.M
     return {"value": lups / dt / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-            "sample": sample, "seconds": dt}
+            "sample": sample, "seconds": dt, "host": host_cpu()}
+
+
+def host_cpu():
+    """CPU model and logical core count of this host (the oracle uses one core)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        model = None
+    return {"model": model, "logical_cores": os.cpu_count()}
 
 
 def time_iterations(WH, torch, solver, n_total, stream, flush, reps, warm=2):
@@ -521,7 +535,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": val,
-                         "unit": "GLUP/s"},
+                         "unit": "GLUP/s", "host": host_cpu()},
         "e2e": {"value": val, "unit": "GLUP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }))
