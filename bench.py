@@ -215,7 +215,7 @@ def time_iterations(WH, torch, solver, n_total, stream, flush, reps, warm=2):
     return tot / reps
 
 
-def measure_forms(WH, G, torch, prob, stream, flush, rank):
+def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
     """The FP32-march form on the same workload, the differentiation form (S^T and one
     gradient sweep), the 256-instance batch (batched FP32 and FP64 iterations vs plain
     per-instance FP64 iterations on a sample of instances), Helmholtz solves/s to 1e-6
@@ -423,7 +423,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank):
     solve["workload"] = ("64^2 unit square, order 2, omega 10, residual 1e-7; reference: FP64 "
                          "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
     out["solve_unit_square"] = solve
-    out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush)
+    out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush, cpu)
     out["roofline_probe_3d_512"] = measure_cube_probe(WH, torch, stream)
     return out
 
@@ -454,7 +454,7 @@ def measure_cube_probe(WH, torch, stream):
     return probe
 
 
-def measure_sphere(WH, torch, stream, flush):
+def measure_sphere(WH, torch, stream, flush, cpu=False):
     """The three-dimensional workload: sphere-in-box, 320^3 Cartesian background on
     [-2, 2]^3 + spherical shell 256 x 128 x 24 (polar band 15-165 degrees, width 0.3) + two
     orthographic pole patches 96^2 x 24, second order, Neumann sphere, Dirichlet box,
@@ -503,6 +503,19 @@ def measure_sphere(WH, torch, stream, flush):
         del sp, u
     solve["speedup_fp32_vs_fp64"] = solve["fp64"]["seconds"] / solve["fp32_then_fp64"]["seconds"]
     res["solve_to_1e-3"] = solve
+    if cpu:  # the 3D oracle, single thread, on the half-resolution sample of the same recipe
+        from oracle import oracle3 as O3
+        half = G3.sphere_problem(nb=160, nphi=128, nth=64, nr=12, npatch=48)
+        orc = O3.Oracle3(half)
+        v = G3.random_state3(half, 1)
+        t0 = time.perf_counter()
+        orc.iterate(v, True)
+        el = time.perf_counter() - t0
+        res["cpu_baseline"] = {
+            "value": half.n_active * orc.time.M / el / 1e9, "unit": "GLUP/s", "cores": 1,
+            "kind": "oracle", "seconds": el, "host": host_cpu(),
+            "sample": "one oracle WaveHoltz iteration of the half-resolution sample "
+                      "(160^3 + 128x64x12 + 2x48^2x12, M=%d)" % orc.time.M}
     return res
 
 
@@ -690,7 +703,8 @@ def main():
 
     forms = None
     if not args.no_forms and not args.small:
-        forms = measure_forms(WH, G, torch, prob, stream, flush, rank)
+        forms = measure_forms(WH, G, torch, prob, stream, flush, rank,
+                              cpu=rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.small:
