@@ -48,3 +48,50 @@ def deflated_fpi(orc, Phi, lam2, f, omega, iters, v0=None):
         v = vn
         hist.append(v.copy())
     return inflate(v, Phi, lam2, f, omega), hist, res
+
+
+def wave_eigenpairs(orc, k, tol=1e-12, seed=0):
+    """The k eigenpairs of the zero-forcing WaveHoltz map S = W_h(., 0) of largest |beta|
+    (the modes the fixed-point iteration reduces most slowly), by ARPACK (implicitly
+    restarted Arnoldi, scipy) on S as a linear operator, each with its eigenvalue lambda^2
+    of the constrained spatial operator from the Rayleigh quotient -(phi, c^2 L_h phi) /
+    (phi, phi) over the discretization points (ghosts filled by the boundary rules first).
+
+    An eigenvector of S is an eigenvector of the discrete spatial operator with its boundary
+    and interpolation constraints (S is a polynomial of the one-step map), so the quotient is
+    exact up to the eigensolver's accuracy.  Returns (Phi, lam2, beta): Phi (k, n) with
+    orthonormal rows (a QR of the eigenvectors: exact eigenvectors for a self-adjoint
+    discretization, a basis of their span otherwise), lam2 (k,), beta (k,)."""
+    import scipy.sparse.linalg as spla
+    n = orc.problem.n_total
+    act = orc.active()
+    op = spla.LinearOperator((n, n), matvec=lambda x: orc.iterate(np.real(x), False),
+                             dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    v0 = rng.standard_normal(n) * act
+    vals, vecs = spla.eigs(op, k=k, which="LM", v0=v0, tol=tol)
+    order = np.argsort(-np.abs(vals))
+    vals, vecs = np.real(vals[order]), np.real(vecs[:, order])
+    Q, _ = np.linalg.qr(vecs)
+    Phi = Q.T.copy()
+    lam2 = np.array([_rayleigh_lam2(orc, vecs[:, m]) for m in range(k)])
+    return Phi, lam2, vals
+
+
+def _rayleigh_lam2(orc, phi):
+    """-(phi, c^2 L_h phi) / (phi, phi) over discretization points, phi a compact vector."""
+    prob = orc.problem
+    num = den = 0.0
+    parts = prob.split(phi)
+    for gi, g in enumerate(prob.grids):
+        shape = orc.ext_shape(gi)
+        u = np.zeros(shape)
+        gh = [(shape[a] - p) // 2 for a, p in enumerate(parts[gi].shape)]
+        sl = tuple(slice(gh[a], gh[a] + parts[gi].shape[a]) for a in range(len(shape)))
+        u[sl] = parts[gi]
+        u = orc.apply_bc(gi, u, 0.0) if getattr(prob, "dim", 2) == 2 else orc.apply_bc(gi, u)
+        lu = orc.apply_lap(gi, u)[sl]
+        disc = g.mask == 1
+        num += float(np.sum(parts[gi][disc] * lu[disc]))
+        den += float(np.sum(parts[gi][disc] ** 2))
+    return -num / den

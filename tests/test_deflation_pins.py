@@ -99,3 +99,42 @@ def test_deflated_rate_is_largest_kept_beta(oracle_mod):
                                   prob.f[0].ravel(), prob.omega, iters)
     ratios = [res[k + 1] / res[k] for k in range(iters - 6, iters - 1)]
     assert max(ratios) <= mu + 1e-9
+
+
+def test_wave_eigenpairs_match_closed_form(oracle_mod):
+    """The oracle's eigenpairs of S on the 32^2 unit square: the six of largest |beta| carry
+    beta_d(lambda~) and lambda_h^2 of the DST-I modes nearest omega, in closed form."""
+    from oracle import deflation as D
+    prob = G.unit_square_problem(32, 2, 10.0, seed=0)
+    orc = oracle_mod.Oracle(prob)
+    fh, lam2, bd = _square_modes(prob, orc.time)
+    order = np.argsort(-np.abs(bd).ravel())[:6]
+    Phi, l2, beta = D.wave_eigenpairs(orc, 6)
+    assert np.allclose(np.sort(beta), np.sort(bd.ravel()[order]), rtol=0, atol=1e-10)
+    assert np.allclose(np.sort(l2), np.sort(lam2.ravel()[order]), rtol=1e-10)
+    assert np.allclose(Phi @ Phi.T, np.eye(6), atol=1e-12)
+
+
+def test_wave_eigenpairs_match_discrete_pencil_on_overset_grid(oracle_mod):
+    """On an overset disk-in-square (order 2) the eigenvalues lambda^2 of the six slowest
+    modes of S are eigenvalues of the discrete pencil A(omega) x = (omega^2 - lambda^2) B x,
+    assembled independently from textbook stencils (tests/dhs.py; B = 1 on discretization
+    rows, 0 on the boundary and interpolation rows: the constrained eigenproblem of the
+    deflation set, Sec. 4.4)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import dhs
+    from oracle import deflation as D
+    dp = G.disk_problem(nb=48, nth=96, nr=10, order=2, omega=8.0, width=0.8, r_cut=0.75)
+    orc = oracle_mod.Oracle(dp)
+    Phi, l2, beta = D.wave_eigenpairs(orc, 6)
+    A, rhs, lay = dhs.assemble(dp, dp.omega)
+    Bd = np.zeros(lay.N)
+    for gi, g in enumerate(dp.grids):
+        for j, i in zip(*np.nonzero(g.mask == G.DISC)):
+            Bd[lay.idx(gi, int(i), int(j))] = 1.0
+    mu, _ = spla.eigs(A.tocsc(), k=12, M=sp.diags(Bd).tocsc(), sigma=0.0)
+    lam_pencil = np.real(dp.omega ** 2 - mu)
+    for x in l2:
+        assert np.min(np.abs(lam_pencil - x)) < 1e-7 * x, (x, np.sort(lam_pencil))
+    assert np.all(np.abs(beta) > 0.99)  # the modes nearest omega: |beta| close to 1
