@@ -702,9 +702,9 @@ def main():
                 "peak_source": "GB300 FP64 1.25 TFLOP/s (pool figure; FMA=2)"}
 
     forms = None
-    if not args.no_forms and not args.small:
+    if not args.no_forms and not args.small and rank == 0:  # only rank 0 prints them
         forms = measure_forms(WH, G, torch, prob, stream, flush, rank,
-                              cpu=rank == 0 and world == 1 and not args.no_cpu_baseline)
+                              cpu=world == 1 and not args.no_cpu_baseline)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.small:
