@@ -56,6 +56,8 @@ def test_deflated_fpi_matches_oracle(K):
     assert st.status == "WH_ERR_NOT_CONVERGED" and st.iterations == 12
     got = u.cpu().numpy()
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # residuals ||v_{k+1} - v_k|| / ||v_{k+1}|| fall to 2e-4 here, so rounding differences of
+    # ~1e-14 in the iterates show up at ~1e-10 in them
     assert np.allclose(st.history[:12], [r / max(np.linalg.norm(hist[k + 1]), 1e-300)
-                                          for k, r in enumerate(res)], rtol=1e-10)
+                                          for k, r in enumerate(res)], rtol=1e-8)
     s.set_deflation(None)
