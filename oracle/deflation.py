@@ -50,28 +50,49 @@ def deflated_fpi(orc, Phi, lam2, f, omega, iters, v0=None):
     return inflate(v, Phi, lam2, f, omega), hist, res
 
 
-def wave_eigenpairs(orc, k, tol=1e-12, seed=0):
+def wave_eigenpairs(orc, k, tol=1e-12, seed=0, passes=2):
     """The k eigenpairs of the zero-forcing WaveHoltz map S = W_h(., 0) of largest |beta|
     (the modes the fixed-point iteration reduces most slowly), by ARPACK (implicitly
     restarted Arnoldi, scipy) on S as a linear operator, each with its eigenvalue lambda^2
     of the constrained spatial operator from the Rayleigh quotient -(phi, c^2 L_h phi) /
     (phi, phi) over the discretization points (ghosts filled by the boundary rules first).
 
-    An eigenvector of S is an eigenvector of the discrete spatial operator with its boundary
-    and interpolation constraints (S is a polynomial of the one-step map), so the quotient is
-    exact up to the eigensolver's accuracy.  Returns (Phi, lam2, beta): Phi (k, n) with
-    orthonormal rows (a QR of the eigenvectors: exact eigenvectors for a self-adjoint
-    discretization, a basis of their span otherwise), lam2 (k,), beta (k,)."""
+    A single-vector Krylov method finds repeated eigenvalues (symmetric geometries) only
+    through rounding, so each further pass runs ARPACK again on (I - Q Q^T) S (I - Q Q^T),
+    Q an orthonormal basis of the eigenvectors found so far, and the k pairs of largest
+    |beta| of the union are kept.  An eigenvector of S is an eigenvector of the discrete
+    spatial operator with its boundary and interpolation constraints (S is a polynomial of
+    the one-step map), so the quotient is exact up to the eigensolver's accuracy.  Returns
+    (Phi, lam2, beta): Phi (k, n) with orthonormal rows (a QR of the eigenvectors: exact
+    eigenvectors for a self-adjoint discretization, a basis of their span otherwise), lam2
+    (k,), beta (k,)."""
     import scipy.sparse.linalg as spla
     n = orc.problem.n_total
     act = orc.active()
-    op = spla.LinearOperator((n, n), matvec=lambda x: orc.iterate(np.real(x), False),
-                             dtype=np.float64)
     rng = np.random.default_rng(seed)
-    v0 = rng.standard_normal(n) * act
-    vals, vecs = spla.eigs(op, k=k, which="LM", v0=v0, tol=tol)
-    order = np.argsort(-np.abs(vals))
-    vals, vecs = np.real(vals[order]), np.real(vecs[:, order])
+    vals_all, vecs_all = [], []
+    Q = np.zeros((n, 0))
+    for _ in range(max(1, passes)):
+        def matvec(x, Q=Q):
+            x = np.real(x)
+            if Q.shape[1]:
+                x = x - Q @ (Q.T @ x)
+            y = orc.iterate(x, False)
+            if Q.shape[1]:
+                y = y - Q @ (Q.T @ y)
+            return y
+        op = spla.LinearOperator((n, n), matvec=matvec, dtype=np.float64)
+        v0 = rng.standard_normal(n) * act
+        if Q.shape[1]:
+            v0 = v0 - Q @ (Q.T @ v0)
+        vals, vecs = spla.eigs(op, k=k, which="LM", v0=v0, tol=tol)
+        vals_all.append(np.real(vals))
+        vecs_all.append(np.real(vecs))
+        Q, _ = np.linalg.qr(np.concatenate(vecs_all, axis=1))
+    vals = np.concatenate(vals_all)
+    vecs = np.concatenate(vecs_all, axis=1)
+    order = np.argsort(-np.abs(vals))[:k]
+    vals, vecs = vals[order], vecs[:, order]
     Q, _ = np.linalg.qr(vecs)
     Phi = Q.T.copy()
     lam2 = np.array([_rayleigh_lam2(orc, vecs[:, m]) for m in range(k)])

@@ -138,3 +138,51 @@ def test_wave_eigenpairs_match_discrete_pencil_on_overset_grid(oracle_mod):
     for x in l2:
         assert np.min(np.abs(lam_pencil - x)) < 1e-7 * x, (x, np.sort(lam_pencil))
     assert np.all(np.abs(beta) > 0.99)  # the modes nearest omega: |beta| close to 1
+
+
+def test_wave_eigenpairs_3d_cube_closed_form():
+    """3D: on the 11^3 Dirichlet cube the six modes of S with largest |beta| are two
+    triply degenerate groups of sine modes; beta_d(lambda~) and lambda_h^2 in closed form,
+    each eigenspace complete (the second ARPACK pass on the projected map finds the copies
+    a single Krylov sequence misses)."""
+    from oracle import deflation as D
+    from oracle import oracle3 as O3
+    from oracle.oracle import beta_d_sum, lambda_tilde
+    from paper_2504_03074_gb300 import grids3 as G3
+    n = 11
+    prob = G3.unit_cube_problem(n, omega=9.0)
+    orc = O3.Oracle3(prob)
+    ts = orc.time
+    h = 1.0 / (n - 1)
+    s2 = (4 / h ** 2) * np.sin(np.arange(1, n - 1) * np.pi * h / 2) ** 2
+    L2 = (s2[:, None, None] + s2[None, :, None] + s2[None, None, :]).ravel()
+    bd = beta_d_sum(lambda_tilde(np.sqrt(L2), ts.dt), ts.omega_e, ts.dt, ts.Nt, ts.alpha)
+    top = np.argsort(-np.abs(bd))[:6]
+    Phi, l2, beta = D.wave_eigenpairs(orc, 6)
+    assert np.allclose(np.sort(beta), np.sort(bd[top]), rtol=0, atol=1e-10)
+    assert np.allclose(np.sort(l2), np.sort(L2[top]), rtol=1e-10)
+    assert np.allclose(Phi @ Phi.T, np.eye(6), atol=1e-10)
+
+
+def test_wave_eigenpairs_3d_overset_match_pencil_with_multiplicity():
+    """3D overset (box-in-box, cubic symmetry): the six slowest modes of S are two triply
+    degenerate eigenvalues of the discrete pencil A(omega) x = (omega^2 - lambda^2) B x,
+    assembled independently (tests/dhs3.py), with the full multiplicity."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import dhs3
+    from oracle import deflation as D
+    from oracle import oracle3 as O3
+    from paper_2504_03074_gb300 import grids3 as G3
+    bp = G3.box_in_box_problem(omega=6.0)
+    Phi, l2, beta = D.wave_eigenpairs(O3.Oracle3(bp), 6)
+    A, rhs, lay = dhs3.assemble(bp)
+    Bd = np.zeros(lay.N)
+    for gi, g in enumerate(bp.grids):
+        for k, j, i in zip(*np.nonzero(g.mask == G.DISC)):
+            Bd[lay.idx(gi, int(i), int(j), int(k))] = 1.0
+    mu, _ = spla.eigs(A.tocsc(), k=12, M=sp.diags(Bd).tocsc(), sigma=0.0)
+    lp = np.real(bp.omega ** 2 - mu)
+    for x in l2:
+        close = lambda arr: int(np.sum(np.abs(arr - x) < 1e-9 * x))
+        assert close(lp) >= 1 and close(l2) == close(lp), (x, np.sort(lp), np.sort(l2))
