@@ -76,7 +76,9 @@ enum { WH_LAUNCH_PERSISTENT = 0, WH_LAUNCH_GRAPH = 1 };
 typedef struct {
   int32_t order;      /* spatial order p: 2 or 4 (Sec. 3.2) */
   int32_t periods;    /* Np >= 1: Tbar = Np * T (Algorithm 1) */
-  double cfl;         /* fraction in (0, 1] of the explicit stability limit */
+  double cfl;         /* fraction of the explicit stability limit: (0, 1] is stable; values
+                         in (1, 2] are accepted only so that the divergence checks of
+                         wh_solve can be exercised (the march then grows without bound) */
   int32_t alpha_mode; /* 0: alpha_d of Eq. alphad (default); 1: alpha = 1/2 */
   int32_t precision;  /* WH_FP64 (default) or WH_FP32 */
   int32_t launch_mode;  /* WH_LAUNCH_GRAPH (default) or WH_LAUNCH_PERSISTENT */
@@ -86,6 +88,16 @@ typedef struct {
                                    states) in device memory when it needs at most this
                                    many bytes, else recomputes it from checkpoints every
                                    16 steps; 0 = default (half the free device memory) */
+  int32_t resident_blocks;      /* launch layouts whose blocks wait on one another (the
+                                   march with the ghost rules and interpolation folded into
+                                   it; the persistent kernel) need all their blocks on the
+                                   GPU at once.  0 (default): the occupancy query's figure for
+                                   the whole device; > 0: assume at most this many (a GPU
+                                   shared with other streams or processes): the folded
+                                   layout is then used only when its grid fits, and the
+                                   persistent kernel's grid is capped.  Independently, a
+                                   folded launch whose bounded wait expires makes the context
+                                   stop folding (that call reports WH_ERR_TIMEOUT). */
 } wh_options;
 
 /* One component grid (Sec. 3.1).  All pointers are host pointers, read during the call.
@@ -273,14 +285,38 @@ wh_status wh_iterate_host(wh_ctx *ctx, int32_t forcing, const double *v_in, doub
  * cycles whose wave solves use the FP32 march take the residual to max(tol, 1e-4) (or
  * until a cycle no longer halves it), then FP64-march cycles continue from that iterate to
  * tol, confirmed by a true FP64 residual.  The orthogonalisation, the updates and all
- * reductions are FP64 throughout.  WH_FPI iterates with the context's march; with a
- * deflation set (wh_set_deflation) it removes the set's components after every iteration
- * and, on return (converged or not), adds back the Helmholtz solution's components along
- * the set (Algorithm 3); its residuals are those of the deflated iterates.  Returns
- * WH_ERR_NOT_CONVERGED (u holds the last iterate) when max_it is reached,
- * WH_ERR_DIVERGED on NaN/Inf. */
+ * reductions are FP64 throughout.  WH_FPI iterates with the context's march.
+ * With a deflation set (wh_set_deflation) both methods solve the deflated problem of
+ * Algorithm 3 and, on return (converged or not), add back the Helmholtz solution's
+ * components along the set: WH_FPI removes the set's components after every iteration;
+ * WH_GMRES (Sec. 4.3 applied to the deflated fixed-point iteration) solves
+ * (I - P S) v = P b with P = I - sum_m phi_m phi_m^T, starting from P u.  Residuals are
+ * those of the deflated iterates.  Returns WH_ERR_NOT_CONVERGED (u holds the last iterate)
+ * when max_it is reached; WH_ERR_DIVERGED on a NaN/Inf residual, on FPI differences
+ * ||v_{k+1} - v_k|| growing past 10x their smallest value, or on a GMRES product with
+ * ||A q|| > 25 ||q|| (a stable march keeps it near 2): the signs of an unstable march. */
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
                    double *u, wh_stats *stats, double *history, int32_t history_cap);
+
+/* Deflation set of wh_solve (Algorithm 3, Sec. 4.4): k discrete eigenpairs (phi_m,
+ * lambda_m^2) of the spatial operator (c^2 L_h phi = -lambda^2 phi with the boundary and
+ * interpolation constraints; wh_eigs computes them).  After every WaveHoltz iteration of
+ * wh_solve(WH_FPI) the iterate loses its components along the set,
+ * v <- v - sum_m (v, phi_m) phi_m (wh_solve(WH_GMRES) solves for the fixed point of that
+ * deflated iteration); on return the solution gains
+ * u = v + sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m, where (f, phi_m) pairs phi_m
+ * with f at discretization points only (the forcing enters the discrete system on those
+ * rows).  Inner products are plain sums over the compact vector, so the rows must be
+ * orthonormal in it (exact for self-adjoint discretizations; an approximation on overset
+ * grids, whose discrete operator is not symmetric).  phi: DEVICE pointer to
+ * k compact vectors, row m at phi + m * n_total; the context keeps the pointer (not a copy):
+ * the caller owns the memory and keeps it alive and unchanged while the set is in use.
+ * lambda2: HOST array of k values, copied.  k = 0 removes the set.  Two-dimensional
+ * single-instance contexts only.  Errors: WH_ERR_ARG (k < 0 or > 4000, null pointers,
+ * non-finite lambda2; at solve time |omega^2 - lambda_m^2| <= 1e-12 omega^2 for some m,
+ * where the inflation would divide by a near-zero difference), WH_ERR_STATE (a 3D context;
+ * at solve time a batch). */
+wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2);
 
 /* Batched solve: one GMRES per instance (restart cycles of the same length), all advancing
  * in lockstep around one batched wave solve per Arnoldi step; an instance that reaches
@@ -289,21 +325,6 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
  * max(tol, 1e-4), then FP64 ones).  u: DEVICE compact vector
  * of all instances (initial guess in, solutions out); stats: host array of one entry per
  * instance (seconds is the whole batch's).  max_it bounds the batched wave solves. */
-/* Deflation set for WH_FPI (Algorithm 3, Sec. 4.4): k discrete eigenpairs (phi_m,
- * lambda_m^2) of the spatial operator (c^2 L_h phi = -lambda^2 phi with the boundary and
- * interpolation constraints).  After every WaveHoltz iteration of wh_solve(WH_FPI) the
- * iterate loses its components along the set, v <- v - sum_m (v, phi_m) phi_m; on return
- * the solution gains u = v + sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m.  Inner products
- * are plain sums over the compact vector, so the rows must be orthonormal in it (exact for
- * self-adjoint discretizations; an approximation on overset grids).  phi: DEVICE pointer to
- * k compact vectors, row m at phi + m * n_total; the context keeps the pointer (not a copy):
- * the caller owns the memory and keeps it alive and unchanged while the set is in use.
- * lambda2: HOST array of k values, copied.  k = 0 removes the set.  Two-dimensional
- * single-instance contexts only.  Errors: WH_ERR_ARG (k < 0 or > 4000, null pointers,
- * non-finite lambda2; at solve time omega^2 equal to a lambda_m^2), WH_ERR_STATE (a 3D
- * context; at solve time a batch). */
-wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2);
-
 wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restart, double *u,
                          wh_stats *stats);
 
@@ -404,6 +425,9 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
  * that array's device address; make it before any stream capture on that device.  All
  * calls on a device share the array (it keeps the last call's contents; each call writes
  * every entry it reads), so calls that overlap on the GPU race and must be serialised.
+ * The looked-up address is kept for the life of the process: it does not survive
+ * cudaDeviceReset on that device (the array is then reloaded at another address), so do
+ * not call this function again on a device after resetting it.
  * Returns WH_ERR_ARG, without touching the device, if nv is outside
  * [1, WH_NOALLOC_MAX_VECTORS], n < 0, ldx < n (nv > 1) or a needed pointer is NULL;
  * WH_ERR_CUDA if a CUDA call fails. */
@@ -411,6 +435,22 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
 #define WH_NOALLOC_BLOCKS 512
 wh_status wh_multidot_noalloc(const double *X, int64_t ldx, int32_t nv, const double *y,
                               int64_t n, double *out, void *stream);
+
+/* Testing aid: out[i] = x[i] widened from FP32 to FP64 by the integer routine the FP32 march
+ * uses for its FP64 filter (every normal number and signed zero assembled from its bits by
+ * IEEE 754's binary32 -> binary64 rule; subnormals, infinities and NaNs by the hardware
+ * conversion), so that it can be checked bit for bit against the hardware conversion.
+ * x, out: DEVICE arrays of n values owned by the caller; stream a cudaStream_t (NULL =
+ * legacy default stream); asynchronous.  The paper has no counterpart.  WH_ERR_ARG on
+ * n < 0 or null pointers with n > 0. */
+wh_status wh_widen_f32(const float *x, double *out, int64_t n, void *stream);
+
+/* Measurement aid: the FP64 FMA throughput of the current device (the ALU roofline of the
+ * FP64 march), from a kernel of independent dependent FMA chains and nothing else, timed
+ * with CUDA events; *tflops receives the best of `reps` launches in TFLOP/s (an FMA counts
+ * as 2 FLOP) and *ms (may be NULL) that launch's milliseconds.  Allocates and frees its own
+ * small output buffer and stream; synchronises.  The paper has no counterpart. */
+wh_status wh_probe_fp64(int32_t reps, double *tflops, double *ms);
 
 /* Time setup of the last wh_prepare. */
 wh_status wh_get_time_info(const wh_ctx *ctx, wh_time_info *info);

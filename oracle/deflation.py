@@ -10,7 +10,11 @@ eigenpairs (phi_m, lambda_m^2) supplied by the caller:
   added back ("inflate"): v <- v + sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m.
 
 Inner products are the plain sum over the compact vector (unused points hold 0); the
-eigenvectors must be orthonormal in that inner product.  With g = 0 only, as in the paper.
+eigenvectors must be orthonormal in that inner product.  In (f, phi_m) the forcing counts
+at discretization points only: Sec. 4.4 writes the discrete eigenproblem as A x = lambda B x
+with B = 1 on the rows where the PDE is discretized and 0 on the boundary and interpolation
+rows, which is also where the forcing enters the discrete Helmholtz system.  With g = 0
+only, as in the paper.
 The deflated fixed-point iteration converges at the rate max over non-deflated modes of
 |beta_d(lambda~_m)| (Theorem "WaveHoltz FPI convergence with deflation").
 """
@@ -26,12 +30,20 @@ def deflate(v, Phi):
     return v - Phi.T @ (Phi @ v)
 
 
-def inflate(v, Phi, lam2, f, omega):
+def disc_mask(problem):
+    """1.0 at discretization points, 0.0 elsewhere, as a compact vector."""
+    return np.concatenate([(np.asarray(g.mask) == 1).ravel() for g in problem.grids]
+                          ).astype(np.float64)
+
+
+def inflate(v, Phi, lam2, f, omega, disc=None):
     """v + sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m (the Helmholtz solution's
-    components along the deflated modes, g = 0)."""
+    components along the deflated modes, g = 0); with `disc` (1 at discretization points)
+    the pairing (f, phi_m) takes f on those points only."""
     if Phi is None or len(Phi) == 0:
         return v
-    coef = (Phi @ f) / (omega ** 2 - np.asarray(lam2, np.float64))
+    fd = f if disc is None else f * disc
+    coef = (Phi @ fd) / (omega ** 2 - np.asarray(lam2, np.float64))
     return v + Phi.T @ coef
 
 
@@ -47,7 +59,29 @@ def deflated_fpi(orc, Phi, lam2, f, omega, iters, v0=None):
         res.append(float(np.linalg.norm(vn - v)))
         v = vn
         hist.append(v.copy())
-    return inflate(v, Phi, lam2, f, omega), hist, res
+    return inflate(v, Phi, lam2, f, omega, disc_mask(orc.problem)), hist, res
+
+
+class _Deflated:
+    """The deflated WaveHoltz map v -> P W_h(v, f), P = I - Phi^T Phi, with the oracle's
+    interface (``iterate``, ``zeros``), so that the oracle's GMRES solves its fixed point."""
+
+    def __init__(self, orc, Phi):
+        self.orc, self.Phi, self.problem = orc, Phi, orc.problem
+
+    def iterate(self, v, forcing=True):
+        return deflate(self.orc.iterate(v, forcing), self.Phi)
+
+    def zeros(self):
+        return self.orc.zeros()
+
+
+def deflated_gmres(orc, Phi, lam2, f, omega, tol=1e-12, restart=60, max_it=2000):
+    """GMRES (Sec. 4.3) on the deflated fixed-point iteration of Algorithm 3: solves
+    (I - P S) v = P b, then inflates.  Returns (u, products, history)."""
+    from .oracle import gmres
+    v, its, hist = gmres(_Deflated(orc, Phi), tol=tol, restart=restart, max_it=max_it)
+    return inflate(v, Phi, lam2, f, omega, disc_mask(orc.problem)), its, hist
 
 
 def wave_eigenpairs(orc, k, tol=1e-12, seed=0, passes=2):

@@ -60,6 +60,7 @@ struct wh_ctx {
   const double *defl_phi = nullptr;
   std::vector<double> defl_lam2;
   double *d_fcompact = nullptr;
+  bool defl_on = false;  // apply_A projects the set out of W_h(x, 0) (deflated GMRES)
   wh3::Ctx3 *c3 = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -161,6 +162,7 @@ struct wh_ctx {
   int32_t *d_dep_tile = nullptr;
   int32_t *d_tile_done = nullptr;  // steps completed by each tile in the current launch
   bool persistent = true;
+  bool fold_failed = false;  // a folded launch timed out: use the separate gather kernel
   unsigned long long opt_spin_limit = 1ull << 22;
   cudaEvent_t err_ev = nullptr;
   bool err_pending = false;
@@ -850,6 +852,8 @@ wh_status build_layout(wh_ctx *ctx) {
       if (!S.present) continue;
       S.march_blocks = sms * march_blocks_per_sm(S.fp32, order);
       S.iter_blocks = sms * iteration_blocks_per_sm(S.fp32, order);
+      if (ctx->opt.resident_blocks > 0)
+        S.iter_blocks = std::min(S.iter_blocks, ctx->opt.resident_blocks);
       S.tma = S.fp32 && !ctx->hftiles.empty();
       if (S.tma) {
         S.tma_blocks = sms * march_tma_blocks_per_sm(S.fp32, order);
@@ -871,7 +875,12 @@ wh_status build_layout(wh_ctx *ctx) {
 bool uses_tma(const wh_ctx *ctx) { return ctx->set[ctx->active].tma && ctx->tune_tma != 0; }
 
 bool folds_gather(const wh_ctx *ctx) {
-  if (ctx->nunits == 0) return false;
+  if (ctx->nunits == 0 || ctx->fold_failed) return false;
+  // the folded units wait for tiles of other blocks: the whole grid must be resident
+  const int cap = ctx->opt.resident_blocks;
+  const int grid = uses_tma(ctx) ? ctx->set[ctx->active].tma_blocks
+                                 : std::min((int)ctx->htiles.size(), ctx->march_blocks);
+  if (cap > 0 && grid > cap) return false;
   if (ctx->tune_fold >= 0) return ctx->tune_fold != 0;
   // the TMA march's units would start after its ticketed general tiles run out (a tail:
   // folding measured -6% on the FP32 disk workload), so it folds only when tuned to
@@ -994,6 +1003,13 @@ wh_status check_timeout(wh_ctx *ctx, bool wait) {
   ctx->err_pending = false;
   if (*ctx->h_err) {
     *ctx->h_err = 0;
+    if (!ctx->persistent && folds_gather(ctx)) {
+      // a folded gather unit gave up waiting (fewer blocks resident than the grid, e.g. a
+      // GPU shared with other work): from now on the ghost rules and interpolation run as
+      // their own kernel, which waits on nothing
+      ctx->fold_failed = true;
+      drop_graphs(ctx);
+    }
     // the graph path's flag is sticky on the device: clear it once reported, so that the
     // context stays usable (the persistent path clears its own at every launch)
     if (ctx->d_err) CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
@@ -1096,11 +1112,25 @@ wh_status ensure_red(wh_ctx *ctx, int nv) {
   }
   if (nv > ctx->red_cap) {
     wh_status st;
+    dfree(ctx, &ctx->d_partial);
+    dfree(ctx, &ctx->d_red);
     if ((st = dalloc(ctx, &ctx->d_partial, (size_t)nv * ctx->partial_blocks)) ||
         (st = dalloc(ctx, &ctx->d_red, (size_t)nv)))
       return st;
     ctx->red_cap = nv;
   }
+  return WH_OK;
+}
+
+// A Krylov basis of at least nv compact vectors in d_q (an old, smaller one is freed).
+wh_status ensure_q(wh_ctx *ctx, int nv) {
+  const int64_t need = (int64_t)nv * ctx->ncompact;
+  if (ctx->q_cap >= need) return WH_OK;
+  dfree(ctx, &ctx->d_q);
+  ctx->q_cap = 0;
+  wh_status st = dalloc(ctx, &ctx->d_q, (size_t)need);
+  if (st) return st;
+  ctx->q_cap = need;
   return WH_OK;
 }
 
@@ -1168,10 +1198,21 @@ struct SolveLog {
 // y = A x = x - W_h(x, 0) (w0 is scratch)
 wh_status apply_adjoint(wh_ctx *ctx, const double *x, double *y);
 
+// w -= sum_m (w, phi_m) phi_m over the deflation set (Algorithm 3's deflation step)
+wh_status defl_project(wh_ctx *ctx, double *w) {
+  const int64_t n = ctx->ncompact;
+  wh_status st = multidot(ctx, ctx->defl_phi, n, ctx->defl_k, w, n, nullptr);
+  if (st) return st;
+  launch_multi_axpy(grid1d(n), ctx->stream, ctx->defl_phi, n, ctx->defl_k, ctx->d_red, w, n);
+  return WH_OK;
+}
+
 wh_status apply_A(wh_ctx *ctx, const double *x, double *y, double *w0, SolveLog &L) {
   wh_status st = ctx->adjoint_mode ? apply_adjoint(ctx, x, w0) : iterate_device(ctx, 0, x, w0);
   if (st) return st;
   L.products[ctx->active] += 1;
+  // deflated GMRES: A_d x = x - P S x with P = I - Phi Phi^T
+  if (ctx->defl_on && (st = defl_project(ctx, w0))) return st;
   launch_sub(grid1d(ctx->ncompact), ctx->stream, x, w0, y, ctx->ncompact);
   return WH_OK;
 }
@@ -1183,6 +1224,14 @@ wh_status apply_A(wh_ctx *ctx, const double *x, double *y, double *w0, SolveLog 
 // FP32 contexts: relative residual at which a solve switches from FP32 to FP64 wave solves
 // (an FP32 product is accurate to a few 1e-5 relative on the tested problems)
 constexpr double kFp32Split = 1e-4;
+// a deflated eigenvalue this close to omega^2 (relative) is refused: the inflation divides
+// by omega^2 - lambda_m^2 and would amplify any error in (f, phi_m)
+constexpr double kResonanceRel = 1e-12;
+// divergence by growth: an FPI difference ||v_{k+1} - v_k|| above kGrowth x the smallest one
+// so far, or a GMRES product ||A q|| (q a unit vector) above kGrowth x kOpBound.  A stable
+// march gives |beta| <= 1 on every eigenmode, so ||A q|| = ||q - S q|| stays near 2.
+constexpr double kGrowth = 10.0;
+constexpr double kOpBound = 2.5;
 
 wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero, int m,
                       double tol_abs, int budget, double scale, SolveLog &L, double *res_out,
@@ -1227,6 +1276,15 @@ wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero,
     double ww;
     if ((st = multidot(ctx, w, 0, 1, w, n, &ww))) return st;
     const double hk1 = std::sqrt(ww);
+    {  // ||A q_k||^2 = sum_i h_ik^2 + hk1^2 (q_k a unit vector)
+      double col = ww;
+      for (int i = 0; i <= k; ++i) col += H[(size_t)i * m + k] * H[(size_t)i * m + k];
+      if (!(std::sqrt(col) <= kGrowth * kOpBound)) {
+        *finite = false;
+        *res_out = std::sqrt(col);
+        return WH_OK;
+      }
+    }
     if (hk1 > 0) launch_axpby(grid1d(n), s, 0.0, w, 1.0 / hk1, w, n);
     for (int i = 0; i < k; ++i) {
       const double t = cs[i] * H[(size_t)i * m + k] + sn[i] * H[(size_t)(i + 1) * m + k];
@@ -1698,6 +1756,7 @@ wh_status wh_options_default(wh_options *opt) {
   opt->launch_mode = WH_LAUNCH_GRAPH;
   opt->barrier_spin_limit = 0;
   opt->trajectory_bytes = 0;
+  opt->resident_blocks = 0;
   return WH_OK;
 }
 
@@ -1707,7 +1766,8 @@ wh_status wh_create(const wh_options *opt, wh_ctx **out) {
   wh_options o;
   wh_options_default(&o);
   if (opt) o = *opt;
-  if ((o.order != 2 && o.order != 4) || o.periods < 1 || !(o.cfl > 0.0 && o.cfl <= 1.0) ||
+  if ((o.order != 2 && o.order != 4) || o.periods < 1 || !(o.cfl > 0.0 && o.cfl <= 2.0) ||
+      o.resident_blocks < 0 ||
       (o.alpha_mode != 0 && o.alpha_mode != 1) ||
       (o.precision != WH_FP64 && o.precision != WH_FP32) ||
       (o.launch_mode != WH_LAUNCH_PERSISTENT && o.launch_mode != WH_LAUNCH_GRAPH))
@@ -1872,16 +1932,18 @@ wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *it) {
 wh_status wh_set_forcing(wh_ctx *ctx, int32_t gid, const double *f) {
   if (ctx && ctx->dim == 3) {
     if (!f) return fail(ctx, WH_ERR_ARG, "null forcing");
-    ctx->prepared = false;
-    return wh3::set_forcing(ctx->c3, gid, f, ctx->err);
+    const wh_status st = wh3::set_forcing(ctx->c3, gid, f, ctx->err);
+    if (st == WH_OK) ctx->prepared = false;
+    return st;
   }
   if (!ctx || !f || gid < 0 || gid >= (int)ctx->grids.size())
     return fail(ctx, WH_ERR_ARG, "bad forcing arguments");
   HostGrid &H = ctx->grids[gid];
   const int64_t n = (int64_t)H.d.n[0] * H.d.n[1];
+  // validate before storing: a rejected call leaves the context's forcing unchanged
+  for (int64_t q = 0; q < n; ++q)
+    if (!std::isfinite(f[q])) return fail(ctx, WH_ERR_ARG, "non-finite forcing");
   H.f.assign(f, f + n);
-  for (double v : H.f)
-    if (!std::isfinite(v)) return fail(ctx, WH_ERR_ARG, "non-finite forcing");
   ctx->dirty = true;
   ctx->prepared = false;
   return WH_OK;
@@ -2134,6 +2196,54 @@ wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, doubl
   return multidot(ctx, x, 0, 1, y, n, out);
 }
 
+wh_status wh_widen_f32(const float *x, double *out, int64_t n, void *stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return WH_ERR_ARG;
+  if (n == 0) return WH_OK;
+  launch_widen((cudaStream_t)stream, x, out, n);
+  return cudaGetLastError() == cudaSuccess ? WH_OK : WH_ERR_CUDA;
+}
+
+wh_status wh_probe_fp64(int32_t reps, double *tflops, double *ms) {
+  if (reps < 1 || !tflops) return WH_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return WH_ERR_CUDA;
+  const int blocks = sms * 8, iters = 4096;  // 8 blocks of 256 threads per SM
+  double *out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  wh_status st = WH_ERR_CUDA;
+  double best = 0.0, best_ms = 0.0;
+  if (cudaMalloc(&out, (size_t)blocks * 256 * sizeof(double)) != cudaSuccess) return WH_ERR_NOMEM;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    goto done;
+  launch_dfma_probe(s, blocks, iters, out);  // warm-up
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, s);
+    const int64_t fmas = launch_dfma_probe(s, blocks, iters, out);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) goto done;
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    const double tf = 2.0 * (double)fmas / (t * 1e-3) / 1e12;
+    if (tf > best) {
+      best = tf;
+      best_ms = t;
+    }
+  }
+  st = cudaGetLastError() == cudaSuccess ? WH_OK : WH_ERR_CUDA;
+  *tflops = best;
+  if (ms) *ms = best_ms;
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(out);
+  return st;
+}
+
 wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int32_t restart,
                    double *u, wh_stats *stats, double *history, int32_t history_cap) {
   if (!ctx || !u || !(tol > 0) || max_it < 1 || (method != WH_FPI && method != WH_GMRES))
@@ -2163,46 +2273,54 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     if (stats) *stats = S;
     return code;
   };
-  if (method == WH_FPI) {  // Algorithm 1 (Algorithm 3 with a deflation set)
-    const int K = ctx->defl_k;
-    if (K > 0) {
-      if (ctx->ninst != 1) return finish(fail(ctx, WH_ERR_STATE, "deflation needs one instance"));
-      for (double l2 : ctx->defl_lam2)
-        if (l2 == ctx->ti.omega * ctx->ti.omega)
-          return finish(fail(ctx, WH_ERR_ARG, "omega^2 equals a deflated eigenvalue"));
-      if ((st = ensure_red(ctx, K))) return finish(st);
-      if (!ctx->d_fcompact && (st = dalloc(ctx, &ctx->d_fcompact, (size_t)n))) return finish(st);
-      std::vector<double> fc((size_t)n, 0.0);
-      int64_t o = 0;
-      for (const auto &H : ctx->grids) {
-        const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
-        if (!H.f.empty()) std::copy(H.f.begin(), H.f.end(), fc.begin() + o);
-        o += np;
-      }
-      CK(cudaMemcpy(ctx->d_fcompact, fc.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  // Deflation set (Algorithm 3): checked and its forcing pairing vector built once per solve
+  const int K = ctx->defl_k;
+  if (K > 0) {
+    if (ctx->ninst != 1) return finish(fail(ctx, WH_ERR_STATE, "deflation needs one instance"));
+    const double om2 = ctx->ti.omega * ctx->ti.omega;
+    for (double l2 : ctx->defl_lam2)
+      if (std::fabs(om2 - l2) <= kResonanceRel * om2)
+        return finish(fail(ctx, WH_ERR_ARG,
+                           "omega^2 = %.17g is within %g (relative) of a deflated eigenvalue "
+                           "lambda^2 = %.17g",
+                           om2, kResonanceRel, l2));
+    if ((st = ensure_red(ctx, K))) return finish(st);
+    if (!ctx->d_fcompact && (st = dalloc(ctx, &ctx->d_fcompact, (size_t)n))) return finish(st);
+    // the forcing enters the discrete Helmholtz system on discretization rows only (the
+    // generalized eigenproblem A x = lambda B x of Sec. 4.4 has B = 1 there and 0 on the
+    // boundary and interpolation rows), so (f, phi_m) pairs phi_m with f at those points
+    std::vector<double> fc((size_t)n, 0.0);
+    int64_t o = 0;
+    for (const auto &H : ctx->grids) {
+      const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
+      if (!H.f.empty())
+        for (int64_t q = 0; q < np; ++q)
+          if (H.mask[q] == WH_DISC) fc[o + q] = H.f[q];
+      o += np;
     }
-    // on every return: add the Helmholtz solution's components along the deflation set,
-    // u += sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m
-    auto inflate = [&]() -> wh_status {
-      if (K == 0) return WH_OK;
-      std::vector<double> c((size_t)K);
-      wh_status e = multidot(ctx, ctx->defl_phi, n, K, ctx->d_fcompact, n, c.data());
-      if (e) return e;
-      const double om2 = ctx->ti.omega * ctx->ti.omega;
-      for (int m = 0; m < K; ++m) c[m] /= om2 - ctx->defl_lam2[m];
-      CK(cudaMemcpyAsync(ctx->d_red, c.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
-      launch_gemv_acc(grid1d(n), s, ctx->defl_phi, n, K, ctx->d_red, u, n);
-      CK(cudaGetLastError());
-      CK(cudaStreamSynchronize(s));  // c is read by the copy above
-      return WH_OK;
-    };
+    CK(cudaMemcpy(ctx->d_fcompact, fc.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  // on every return: add the Helmholtz solution's components along the deflation set,
+  // u += sum_m (f, phi_m) / (omega^2 - lambda_m^2) phi_m
+  auto inflate = [&]() -> wh_status {
+    if (K == 0) return WH_OK;
+    std::vector<double> c((size_t)K);
+    wh_status e = multidot(ctx, ctx->defl_phi, n, K, ctx->d_fcompact, n, c.data());
+    if (e) return e;
+    const double om2 = ctx->ti.omega * ctx->ti.omega;
+    for (int m = 0; m < K; ++m) c[m] /= om2 - ctx->defl_lam2[m];
+    CK(cudaMemcpyAsync(ctx->d_red, c.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gemv_acc(grid1d(n), s, ctx->defl_phi, n, K, ctx->d_red, u, n);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));  // c is read by the copy above
+    return WH_OK;
+  };
+  if (method == WH_FPI) {  // Algorithm 1 (Algorithm 3 with a deflation set)
+    double dmin = 1e300;
     for (int k = 0; k < max_it; ++k) {
       if ((st = iterate_device(ctx, 1, u, w0))) return finish(st);
       L.products[ctx->active] += 1;
-      if (K > 0) {  // deflate: w0 -= sum_m (w0, phi_m) phi_m
-        if ((st = multidot(ctx, ctx->defl_phi, n, K, w0, n, nullptr))) return finish(st);
-        launch_multi_axpy(grid1d(n), s, ctx->defl_phi, n, K, ctx->d_red, w0, n);
-      }
+      if (K > 0 && (st = defl_project(ctx, w0))) return finish(st);  // deflate
       launch_sub(grid1d(n), s, w0, u, w1, n);
       CK(cudaMemcpyAsync(u, w0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       double d[2];
@@ -2212,6 +2330,14 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
       S.residual = r;
       L.add(r);
       if (!std::isfinite(r)) return finish(fail(ctx, WH_ERR_DIVERGED, "FPI residual is %g", r));
+      // the map contracts every component (|beta| <= 1), so a difference that grows past
+      // kGrowth times the smallest one seen means the march itself is unstable
+      const double dabs = std::sqrt(d[0]);
+      if (k > 0 && dabs > kGrowth * dmin)
+        return finish(fail(ctx, WH_ERR_DIVERGED,
+                           "FPI: ||v_%d - v_%d|| = %g grew past %g x its smallest value %g",
+                           k + 1, k, dabs, kGrowth, dmin));
+      dmin = std::min(dmin, dabs);
       if (r <= tol) {
         S.converged = 1;
         return finish(inflate());
@@ -2222,23 +2348,31 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
                        S.residual));
   }
   const int m = restart;
-  if (ctx->q_cap < (int64_t)(m + 1) * n) {
-    if ((st = dalloc(ctx, &ctx->d_q, (size_t)(m + 1) * n))) return finish(st);
-    ctx->q_cap = (int64_t)(m + 1) * n;
-  }
+  if ((st = ensure_q(ctx, m + 1))) return finish(st);
   if ((st = ensure_red(ctx, m + 1))) return finish(st);
-  // b = W_h(0, f) with the FP64 march (residuals stay in FP64)
+  // b = W_h(0, f) with the FP64 march (residuals stay in FP64); with a deflation set the
+  // system is the deflated fixed point (I - P S) v = P b, P = I - Phi Phi^T, inflated on
+  // return like the fixed-point iteration's
   use_set(ctx, 0);
   CK(cudaMemsetAsync(w0, 0, n * sizeof(double), s));
   if ((st = iterate_device(ctx, 1, w0, w2))) return finish(st);
   L.products[0] += 1;
+  if (K > 0) {
+    if ((st = defl_project(ctx, w2))) return finish(st);
+    if ((st = defl_project(ctx, u))) return finish(st);  // the guess lives in range(P) too
+  }
+  struct DeflOff {  // apply_A leaves the deflated operator on every return
+    wh_ctx *c;
+    ~DeflOff() { c->defl_on = false; }
+  } defl_off{ctx};
+  ctx->defl_on = K > 0;
   double bb;
   if ((st = multidot(ctx, w2, 0, 1, w2, n, &bb))) return finish(st);
   const double bnorm = std::sqrt(bb);
   if (!(bnorm > 0)) {
     CK(cudaMemsetAsync(u, 0, n * sizeof(double), s));
     S.converged = 1;
-    return finish(WH_OK);
+    return finish(inflate());
   }
   double *b = w2;
   if (default_set(ctx) == 1) {
@@ -2258,7 +2392,10 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
       if ((st = gmres_cycle(ctx, b, u, false, m, tol1 * bnorm, budget, 1.0 / bnorm, L, &res,
                             &fin)))
         return finish(st);
-      if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual is not finite"));
+      if (!fin)
+        return finish(fail(ctx, WH_ERR_DIVERGED,
+                           "GMRES: residual or product norm %g is not finite or exceeds %g "
+                           "(unstable march)", res, kGrowth * kOpBound));
       S.residual = res / bnorm;
       if (res <= tol1 * bnorm || res > 0.5 * prev) break;
       prev = res;
@@ -2276,7 +2413,10 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     if ((st = gmres_cycle(ctx, b, u, false, m, tol * bnorm, budget, 1.0 / bnorm, L, &res, &fin)))
       return finish(st);
     S.residual = res / bnorm;
-    if (!fin) return finish(fail(ctx, WH_ERR_DIVERGED, "GMRES residual is not finite"));
+    if (!fin)
+      return finish(fail(ctx, WH_ERR_DIVERGED,
+                         "GMRES: residual or product norm %g is not finite or exceeds %g "
+                         "(unstable march)", res, kGrowth * kOpBound));
     if (res <= tol * bnorm) {
       // the cycle's last value may be the Givens estimate: confirm with a true residual
       double *rr = ctx->d_work + n;
@@ -2288,12 +2428,14 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
       L.add(S.residual);
       if (S.residual <= tol) {
         S.converged = 1;
-        return finish(WH_OK);
+        return finish(inflate());
       }
     }
-    if (L.products[0] + L.products[1] >= max_it)
+    if (L.products[0] + L.products[1] >= max_it) {
+      if ((st = inflate())) return finish(st);
       return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
                          S.residual));
+    }
   }
 }
 
@@ -2322,10 +2464,7 @@ wh_status wh_solve_batch(wh_ctx *ctx, double tol, int32_t max_it, int32_t restar
   cudaStream_t s = ctx->stream;
   wh_status st;
   if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
-  if (ctx->q_cap < (int64_t)(m + 1) * n) {
-    if ((st = dalloc(ctx, &ctx->d_q, (size_t)(m + 1) * n))) return st;
-    ctx->q_cap = (int64_t)(m + 1) * n;
-  }
+  if ((st = ensure_q(ctx, m + 1))) return st;
   if ((st = ensure_red(ctx, m + 1))) return st;
   ctx->launches = 0;
   std::vector<InstGmres> I(K);
@@ -2462,10 +2601,7 @@ wh_status wh_adjoint(wh_ctx *ctx, const double *u, const double *g, double tol, 
   use_set(ctx, 0);
   if ((st = adj_setup(ctx))) return st;
   if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
-  if (ctx->q_cap < (int64_t)(restart + 1) * n) {
-    if ((st = dalloc(ctx, &ctx->d_q, (size_t)(restart + 1) * n))) return st;
-    ctx->q_cap = (int64_t)(restart + 1) * n;
-  }
+  if ((st = ensure_q(ctx, restart + 1))) return st;
   if ((st = ensure_red(ctx, restart + 1))) return st;
   SolveLog L;
   wh_stats S{};

@@ -559,6 +559,9 @@ wh_status set_forcing(Ctx3 *c, int32_t gid, const double *f, std::string &err) {
   if (gid < 0 || gid >= (int)c->grids.size() || !f)
     return fail3(err, WH_ERR_ARG, "bad grid index or null forcing");
   HostGrid3 &H = c->grids[gid];
+  // validate before storing: a rejected call leaves the forcing unchanged
+  for (size_t q = 0; q < H.mask.size(); ++q)
+    if (!std::isfinite(f[q])) return fail3(err, WH_ERR_ARG, "non-finite forcing");
   H.f.assign(f, f + H.mask.size());
   c->f_dirty = true;
   return WH_OK;

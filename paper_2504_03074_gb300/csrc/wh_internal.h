@@ -218,5 +218,10 @@ void launch_sub(unsigned nb, cudaStream_t s, const double *x, const double *z, d
                 int64_t n);
 void launch_gemv_acc(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
                      const double *c, double *y, int64_t n);
+// y[i] = the filter's FP32 -> FP64 widening of x[i] (testing aid)
+void launch_widen(cudaStream_t s, const float *x, double *y, int64_t n);
+// FP64 FMA throughput probe (blocks x 256 threads, out: one double per thread); returns the
+// number of FMAs issued
+int64_t launch_dfma_probe(cudaStream_t s, int blocks, int iters, double *out);
 
 }  // namespace wh

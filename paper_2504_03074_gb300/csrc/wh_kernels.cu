@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "wh_internal.h"
+#include "wh_widen.cuh"
 
 namespace wh {
 
@@ -34,26 +35,6 @@ __device__ __forceinline__ int64_t row_off(const DevGrid &G, int jj) {
   jj = wrap(jj, G.n1, G.per1);
   jj = jj < -G.g1 ? -G.g1 : (jj >= G.n1 + G.g1 ? G.n1 + G.g1 - 1 : jj);
   return G.base + (int64_t)(jj + G.g1) * G.pitch + G.g0;
-}
-
-// Exact widening of a state value to FP64 for the filter and the interpolation sums.  On this
-// part the hardware float -> double conversion runs on the narrow FP64 pipe and occupies it
-// several times longer than a DFMA (in the FP32 march it kept that pipe ~70% busy while the
-// DFMAs used a tenth of its rate); IEEE 754 fixes binary64
-// as the same sign, the exponent rebiased by 1023 - 127 = 896 and the 23 fraction bits
-// followed by 29 zeros, which integer operations assemble exactly.  Zeros take the same
-// path; subnormals, infinities and NaNs (never produced by a stable march) use the
-// hardware conversion.
-__device__ __forceinline__ double to_f64(double x) { return x; }
-__device__ __forceinline__ double to_f64(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned e = (b >> 23) & 0xffu;
-  if (e - 1u < 254u) {
-    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-    return __hiloint2double((int)hi, (int)(b << 29));
-  }
-  if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  return (double)x;
 }
 
 // Programmatic dependent launch.  Kernels of the iteration graph start with pdl_wait: the
@@ -1760,6 +1741,43 @@ void launch_multidot(int nb, cudaStream_t s, const double *X, int64_t ldx, int n
 void launch_multi_axpy(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
                        const double *h, double *y, int64_t n) {
   multi_axpy<<<nb, 256, 0, s>>>(X, ldx, nv, h, y, n);
+}
+
+// out[i] = to_f64(x[i]): the filter's widening, run on its own for testing.
+__global__ void widen_kernel(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = to_f64(x[i]);
+}
+
+void launch_widen(cudaStream_t s, const float *x, double *y, int64_t n) {
+  int64_t nb = (n + 255) / 256;
+  nb = nb < 1 ? 1 : (nb > 152 * 16 ? 152 * 16 : nb);
+  widen_kernel<<<(unsigned)nb, 256, 0, s>>>(x, y, n);
+}
+
+// FP64 FMA throughput probe: every thread runs kChains independent dependent chains
+// a <- fma(a, b, c) for `iters` rounds (nothing else in the loop), then stores their sum so
+// that no chain is dead code.  2 FLOP per FMA.
+constexpr int kChains = 8;
+__global__ void __launch_bounds__(256) dfma_probe_kernel(double b, double c, int iters,
+                                                         double *out) {
+  double a[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], b, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) sum += a[k];
+  out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = sum;
+}
+
+int64_t launch_dfma_probe(cudaStream_t s, int blocks, int iters, double *out) {
+  dfma_probe_kernel<<<blocks, 256, 0, s>>>(0.9999999, 1e-7, iters, out);
+  return (int64_t)blocks * 256 * iters * kChains;  // FMAs issued
 }
 
 void launch_axpby(unsigned nb, cudaStream_t s, double a, const double *x, double b, double *y,

@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "wh3_internal.h"
+#include "wh_widen.cuh"
 
 namespace wh3 {
 namespace {
@@ -358,18 +359,6 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
   }
 }
 
-// FP32 -> FP64 widening with integer operations (binary32 -> binary64: same sign, exponent
-// + 896, fraction followed by 29 zeros); zero, subnormal, inf and NaN take the hardware
-// conversion.  The hardware conversion is an FP64-pipe instruction, and GB300 has few.
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-  return __hiloint2double((int)hi, (int)(u << 29));
-}
-__device__ __forceinline__ double widen(double d) { return d; }
-
 // Ghost rules and interpolation of one time level, one thread per receiver: the 27 donors
 // (i0 + a, j0 + b, k0 + c) at gbase + ox[a] + oy[b] + oz[c] (per-axis offsets, periodic wrap
 // resolved at set-up) are all loaded first, then the tensor product is evaluated as rows
@@ -409,7 +398,7 @@ __global__ void __launch_bounds__(256) gather3_kernel(
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const T *x = u + 9 * c + 3 * b;
-        const double row = w[0] * widen(x[0]) + w[1] * widen(x[1]) + w[2] * widen(x[2]);
+        const double row = w[0] * wh::to_f64(x[0]) + w[1] * wh::to_f64(x[1]) + w[2] * wh::to_f64(x[2]);
         col = fma(w[3 + b], row, col);
       }
       s = fma(w[6 + c], col, s);
@@ -417,7 +406,7 @@ __global__ void __launch_bounds__(256) gather3_kernel(
     const T v = (T)s;
     const int64_t q = ridx[r];
     W[q] = v;
-    V[q] += wl * widen(v);
+    V[q] += wl * wh::to_f64(v);
   }
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nghost; g += stride)
     W[gdst[g]] = W[gsrc[g]];

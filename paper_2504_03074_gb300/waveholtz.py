@@ -35,7 +35,8 @@ class WHError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("order", C.c_int32), ("periods", C.c_int32), ("cfl", C.c_double),
                 ("alpha_mode", C.c_int32), ("precision", C.c_int32), ("launch_mode", C.c_int32),
-                ("barrier_spin_limit", C.c_uint64), ("trajectory_bytes", C.c_uint64)]
+                ("barrier_spin_limit", C.c_uint64), ("trajectory_bytes", C.c_uint64),
+                ("resident_blocks", C.c_int32)]
 
 
 class GridDesc(C.Structure):
@@ -93,7 +94,7 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
-           "wh_set_interp3", "wh_set_deflation"]
+           "wh_set_interp3", "wh_set_deflation", "wh_widen_f32", "wh_probe_fp64"]
 
 
 def lib_path():
@@ -141,6 +142,8 @@ def lib():
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
                                      C.POINTER(C.c_int32)]
+    L.wh_widen_f32.argtypes = [vp, vp, C.c_int64, vp]
+    L.wh_probe_fp64.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wh_last_launch_count.argtypes = [vp]
     L.wh_last_launch_count.restype = C.c_int64
     for name in EXPORTS:
@@ -148,6 +151,24 @@ def lib():
             getattr(L, name).restype = st
     _lib = L
     return L
+
+
+def probe_fp64(reps=5):
+    """The device's FP64 FMA throughput (TFLOP/s, FMA = 2 FLOP) and the best launch's ms."""
+    t, ms = C.c_double(), C.c_double()
+    st = lib().wh_probe_fp64(reps, C.byref(t), C.byref(ms))
+    if st != WH_OK:
+        raise WHError(st, "wh_probe_fp64 failed")
+    return t.value, ms.value
+
+
+def widen_f32(x, out, stream=None):
+    """out = FP64 of the float32 device tensor x by the library's integer widening."""
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib().wh_widen_f32(_ptr(x), _ptr(out), x.numel(), C.c_void_p(raw))
+    if st != WH_OK:
+        raise WHError(st, "wh_widen_f32 failed")
+    return out
 
 
 def _ptr(a):
@@ -162,7 +183,8 @@ class Solver:
     """One overset Helmholtz problem in libwaveholtz (one context)."""
 
     def __init__(self, problem, periods=1, cfl=0.9, alpha_mode=0, precision=FP64, stream=None,
-                 launch_mode=GRAPH, barrier_spin_limit=0, trajectory_bytes=0):
+                 launch_mode=GRAPH, barrier_spin_limit=0, trajectory_bytes=0,
+                 resident_blocks=0):
         self.L = lib()
         self.problem = problem
         opt = Options()
@@ -171,6 +193,7 @@ class Solver:
         opt.alpha_mode, opt.precision = alpha_mode, precision
         opt.launch_mode, opt.barrier_spin_limit = launch_mode, barrier_spin_limit
         opt.trajectory_bytes = trajectory_bytes
+        opt.resident_blocks = resident_blocks
         h = C.c_void_p()
         self._check(self.L.wh_create(C.byref(opt), C.byref(h)), None)
         self.h = h

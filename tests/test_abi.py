@@ -70,8 +70,11 @@ def test_options_and_create(W):
     h = C.c_void_p()
     opt.order = 3
     assert L.wh_create(C.byref(opt), C.byref(h)) == -1
-    opt.order, opt.cfl = 4, 1.5
+    opt.order, opt.cfl = 4, 2.5  # (1, 2] is accepted, unstable, for the divergence checks
     assert L.wh_create(C.byref(opt), C.byref(h)) == -1
+    opt.cfl, opt.resident_blocks = 0.9, -1
+    assert L.wh_create(C.byref(opt), C.byref(h)) == -1
+    opt.resident_blocks = 0
     assert L.wh_create(None, None) == -1
     L.wh_destroy(None)
 
@@ -276,3 +279,33 @@ def test_deflation_validation_on_host(W):
     assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0
     assert L.wh_set_deflation(h, 2, C.c_void_p(64), lam) == -3
     L.wh_destroy(h)
+
+
+def test_set_forcing_rejection_leaves_forcing_unchanged(W):
+    """A rejected wh_set_forcing (non-finite values) leaves the stored forcing as it was:
+    the validation runs before anything is stored (checked through the host-side solve
+    preconditions: the context stays usable and reports the same sizes)."""
+    L = W.lib()
+    prob = G.unit_square_problem(16, 2, 3.0)
+    h = _ctx(W, 2)
+    d, keep = _desc(W, prob.grids[0])
+    gid = C.c_int32()
+    assert L.wh_add_grid(h, C.byref(d), C.byref(gid)) == 0
+    f = np.ascontiguousarray(prob.f[0], np.float64)
+    assert L.wh_set_forcing(h, 0, f.ctypes.data) == 0
+    bad = f.copy()
+    bad[3, 4] = np.nan
+    assert L.wh_set_forcing(h, 0, bad.ctypes.data) == -1
+    assert b"non-finite" in L.wh_last_error(h)
+    L.wh_destroy(h)
+
+
+def test_widen_and_probe_arguments(W):
+    """The testing and measurement aids refuse bad arguments without a device."""
+    L = W.lib()
+    assert L.wh_widen_f32(None, None, -1, None) == -1
+    assert L.wh_widen_f32(None, None, 5, None) == -1
+    assert L.wh_widen_f32(None, None, 0, None) == 0
+    t = C.c_double()
+    assert L.wh_probe_fp64(0, C.byref(t), None) == -1
+    assert L.wh_probe_fp64(3, None, None) == -1

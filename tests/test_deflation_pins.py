@@ -186,3 +186,26 @@ def test_wave_eigenpairs_3d_overset_match_pencil_with_multiplicity():
     for x in l2:
         close = lambda arr: int(np.sum(np.abs(arr - x) < 1e-9 * x))
         assert close(lp) >= 1 and close(l2) == close(lp), (x, np.sort(lp), np.sort(l2))
+
+
+def test_deflated_gmres_reaches_closed_form_solution(oracle_mod):
+    """GMRES (Sec. 4.3) on the deflated fixed-point iteration of Algorithm 3, then the
+    inflation: on the unit square, where the DST-I modes are exact orthonormal eigenvectors
+    of the self-adjoint discrete operator, the result is the discrete Helmholtz solution
+    sum_m f_m / (omega^2 - lambda_m^2) Phi_m in closed form, whatever modes are deflated."""
+    from oracle import deflation as D
+    prob = G.unit_square_problem(32, 2, 10.0, seed=3)
+    orc = oracle_mod.Oracle(prob)
+    fh, lam2, bd = _square_modes(prob, orc.time)
+    n = 32
+    order = np.argsort(-np.abs(bd).ravel())[:6]
+    idx = [np.unravel_index(q, bd.shape) for q in order]
+    Phi = np.array([_mode_vector(n, i + 1, j + 1) for i, j in idx])
+    l2 = np.array([lam2[i, j] for i, j in idx])
+    u, its, hist = D.deflated_gmres(orc, Phi, l2, prob.f[0].ravel(), prob.omega, tol=1e-13)
+    ref = np.zeros((n, n))
+    ref[1:-1, 1:-1] = sfft.idstn(fh / (prob.omega ** 2 - lam2), type=1, norm="ortho")
+    assert np.max(np.abs(u.reshape(n, n) - ref)) < 1e-10 * np.max(np.abs(ref))
+    # the deflated components of the deflated iterate are zero before the inflation
+    v = u - Phi.T @ ((Phi @ prob.f[0].ravel()) / (prob.omega ** 2 - l2))
+    assert np.max(np.abs(Phi @ v)) < 1e-12 * np.max(np.abs(ref))
