@@ -371,7 +371,20 @@ wh_status wh_set_coefficient(wh_ctx *ctx, int32_t grid_id, const double *c2);
  *                 when such grids exist), 0 = the plain march kernel.
  *   pdl           graph path: 1 = the graph's kernels use programmatic dependent launch
  *                 (library), 0 = plain stream order.
- *   ms_per_iteration, candidates: filled by wh_autotune. */
+ *   temporal_depth  three-dimensional FP32 march: time steps per launch of the temporally
+ *                 blocked march, 1..4 (1 = one step per launch); library: 4.  Blocks of
+ *                 kTX x 16 x unit_depth points whose box widened by depth - 1 points holds no
+ *                 receiver and no Neumann ghost advance that many steps per launch from
+ *                 shared memory and registers (recomputing a halo of depth points); the
+ *                 rest (the overset coupling region) advances one step at a time with the
+ *                 ghost rules and interpolation after each.  Results are bit-identical to
+ *                 depth 1.  Ignored by the FP64 march and by two-dimensional contexts (-1 or
+ *                 1 there).
+ *   unit_depth    planes along axis 2 of a blocked unit: a multiple of 8 in [8, 256];
+ *                 library: 64.
+ *   ms_per_iteration, candidates: filled by wh_autotune; blocked_points (points that
+ *                 advance temporal_depth steps per launch): filled by wh_autotune and
+ *                 wh_get_tuning. */
 typedef struct {
   int32_t launch_mode;
   int32_t fold_gather;
@@ -380,17 +393,26 @@ typedef struct {
   int32_t pdl;
   double ms_per_iteration;
   int32_t candidates;
+  int32_t temporal_depth;
+  int32_t unit_depth;
+  int64_t blocked_points;
 } wh_tuning;
 
 /* Fix the launch layout (fields of -1 leave the library's choice; launch_mode -1 keeps the
- * current mode).  Takes effect at the next iteration. */
+ * current mode).  Takes effect at the next iteration.  On three-dimensional contexts only
+ * temporal_depth and unit_depth apply and the other layout fields must be -1. */
 wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *tuning);
+
+/* The launch layout in use, resolved to the values the library applies (after wh_prepare;
+ * ms_per_iteration and candidates are 0). */
+wh_status wh_get_tuning(const wh_ctx *ctx, wh_tuning *out);
 
 /* Autotuner: after wh_prepare, times `reps` forced WaveHoltz iterations (after one untimed)
  * of every valid launch layout on the prepared problem — persistent; graph with the gather
  * folded; graph with a separate gather and tiles by ticket or by stride; for FP32 contexts
  * also with and without the TMA-staged march; each graph layout with and without
- * programmatic dependent launch — keeps the fastest, and reports it (resolved
+ * programmatic dependent launch; on three-dimensional FP32 contexts the temporal depth
+ * 1..4 with unit depths 32, 64 and 128 — keeps the fastest, and reports it (resolved
  * to 0/1 values) with its time and the number of layouts timed in *out (host, may be NULL).
  * Uses the context's working vectors only.  Synchronises. */
 wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out);
@@ -407,9 +429,10 @@ wh_status wh_dot(wh_ctx *ctx, const double *x, const double *y, int64_t n, doubl
  * interpolation when the iteration folds them into its launches), [1] the separate
  * ghost-rule + interpolation kernel, [2] the input kernel, [3] the output kernel.  The bursts run on the context's internal
  * working buffers and leave them unspecified (every wh_iterate rebuilds them from its
- * input).  On three-dimensional contexts [0] and [1] are the march and the ghost-rule +
- * interpolation kernel, each launch timed on its own with events over `reps` iterations'
- * steps, and [2], [3] are 0.  Synchronises. */
+ * input).  On three-dimensional contexts [0] is the single-step march, [1] the ghost-rule +
+ * interpolation kernel and [2] the temporally blocked march (0 launches when blocking is
+ * off), each launch timed on its own with events over `reps` iterations, and [3] is 0.
+ * Synchronises. */
 wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *counts);
 
 /* Allocation-free inner products.  The paper has no counterpart: this serves callers that

@@ -54,6 +54,18 @@ struct Tile3 {
   int32_t grid, i0, j0, k0;
 };
 
+// Temporal blocking of the FP32 march (constant-weight, non-periodic grids): a unit is a
+// box of kTX x kUY points of the (axis 0, axis 1) plane and up to `depth` planes along axis 2
+// (a union of march tiles) that advances K time steps in one launch from the two levels
+// before them, recomputing a K-point halo (overlapped tiling).  Its (K-1)-dilated box holds
+// no receiver and no ghost that a rule rewrites, so every point the K steps read is either
+// marched or constant.  flags bit 0: write every intermediate level (a coupled tile or a
+// donor reads them), else only the last two.
+constexpr int kUY = 16;
+struct Unit3 {
+  int32_t grid, i0, j0, k0, nz, flags;
+};
+
 // Per-step tables of the prepared frequency.
 struct Tab3 {
   const double *fc;  // dt^2 cos(omega_e t^n), n = 0..M
@@ -73,9 +85,20 @@ void launch_weight3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int gidx,
 void launch_init3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int ngrids,
                   int64_t max_ext, const int8_t *mask, const double *v, void *W0, double *V,
                   const double *wf);
+// One step n -> n + 1 over `tiles`: W^{n+1} -> Wout from W^n (Wn) and W^{n-1} (Wprev, which
+// may be Wout itself: the two-level in-place layout).
 void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
-                   const Tile3 *tiles, const int8_t *mask, const void *Wn, void *Wout,
-                   const void *F, const void *Wt, double *V, Tab3 tab, int n, double fs);
+                   const Tile3 *tiles, const int8_t *mask, const void *Wn, const void *Wprev,
+                   void *Wout, const void *F, const void *Wt, double *V, Tab3 tab, int n,
+                   double fs);
+// K steps n -> n + K (K = 2, 3 or 4) of the FP32 march over `nunits` units.  ring holds L
+// levels of the FP32 state, level l at ring + (l % L) * stride; levels n - 1 and n are read,
+// levels n + 1 .. n + K written (only n + K - 1 and n + K for units without the export
+// flag).  Same arithmetic, in the same order, as launch_march3's.
+void launch_march3_block(int K, cudaStream_t s, int nunits, const Grid3Dev *grids,
+                         const Unit3 *units, const int8_t *mask, float *ring, int64_t stride,
+                         int L, const float *F, double *V, Tab3 tab, int n, double fs);
+size_t march3_block_threads(int K);
 // Receiver r of R: donor (i0 + a, j0 + b, k0 + c) at gbase[r] + goff[a R + r] +
 // goff[(3 + b) R + r] + goff[(6 + c) R + r] with weight gw[a R + r] gw[(3 + b) R + r]
 // gw[(6 + c) R + r] (planes of wx, wy, wz).
@@ -102,8 +125,15 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
 wh_status iterate(Ctx3 *c, bool fp32, int forcing, const double *vin, double *vout,
                   cudaStream_t s, int64_t *launches, std::string &err);
 int ngrids(const Ctx3 *c);
-// Device time per launch (ms) of the march and of the ghost-rule + interpolation kernel, each
-// launch timed on its own with events (reps iterations' worth of steps); counts = M each.
+// Temporal blocking of the FP32 march: depth K in [1, 4] (1 = single steps) and unit depth
+// (planes, a multiple of 8 in [8, 256]); -1 = the library's choice.  Takes effect at once
+// when the FP32 march is prepared, else at the next prepare.
+wh_status set_blocking(Ctx3 *c, int K, int uz, std::string &err);
+// The plan in use: depth, unit depth, points and units that advance K steps per launch.
+void blocking(const Ctx3 *c, int *K, int *uz, int64_t *points, int64_t *units);
+// Device time per launch (ms) and launches per iteration of [0] the single-step march, [1]
+// the ghost-rule + interpolation kernel and [2] the K-step blocked march, each launch timed
+// on its own with events over reps iterations.
 wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int32_t *counts,
                   std::string &err);
 

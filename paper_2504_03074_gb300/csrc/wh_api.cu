@@ -2679,7 +2679,15 @@ wh_status wh_set_coefficient(wh_ctx *ctx, int32_t gid, const double *c2) {
 
 wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *t) {
   if (!ctx || !t) return fail(ctx, WH_ERR_ARG, "bad wh_set_tuning arguments");
-  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "3D contexts have one launch layout");
+  if (ctx->dim == 3) {
+    if (t->launch_mode != -1 || t->fold_gather != -1 || t->tile_tickets != -1 ||
+        t->tma != -1 || t->pdl != -1)
+      return fail(ctx, WH_ERR_STATE,
+                  "3D contexts take only temporal_depth and unit_depth (other fields -1)");
+    return wh3::set_blocking(ctx->c3, t->temporal_depth, t->unit_depth, ctx->err);
+  }
+  if (t->temporal_depth < -1 || t->temporal_depth > 1 || t->unit_depth < -1)
+    return fail(ctx, WH_ERR_ARG, "temporal blocking is a three-dimensional FP32 form");
   auto tri = [](int32_t v) { return v >= -1 && v <= 1; };
   if (!tri(t->fold_gather) || !tri(t->tile_tickets) || !tri(t->tma) || !tri(t->pdl) ||
       (t->launch_mode != -1 && t->launch_mode != WH_LAUNCH_GRAPH &&
@@ -2696,10 +2704,85 @@ wh_status wh_set_tuning(wh_ctx *ctx, const wh_tuning *t) {
   return WH_OK;
 }
 
+wh_status wh_get_tuning(const wh_ctx *ctx, wh_tuning *out) {
+  if (!ctx || !out) return WH_ERR_ARG;
+  *out = wh_tuning{};
+  out->launch_mode = out->fold_gather = out->tile_tickets = out->tma = out->pdl = -1;
+  out->temporal_depth = 1;
+  out->unit_depth = 0;
+  if (!ctx->prepared) return WH_ERR_STATE;
+  if (ctx->dim == 3) {
+    int K = 1, uz = 0;
+    int64_t pts = 0, nu = 0;
+    wh3::blocking(ctx->c3, &K, &uz, &pts, &nu);
+    out->temporal_depth = ctx->opt.precision == WH_FP32 ? K : 1;
+    out->unit_depth = uz;
+    out->blocked_points = ctx->opt.precision == WH_FP32 && K > 1 ? pts : 0;
+    return WH_OK;
+  }
+  out->launch_mode = ctx->persistent ? WH_LAUNCH_PERSISTENT : WH_LAUNCH_GRAPH;
+  out->fold_gather = folds_gather(ctx) ? 1 : 0;
+  out->tile_tickets = tile_tickets(ctx) ? 1 : 0;
+  out->tma = uses_tma(ctx) ? 1 : 0;
+  out->pdl = ctx->tune_pdl != 0 ? 1 : 0;
+  return WH_OK;
+}
+
+// Three-dimensional autotuner: the FP32 march's temporal depth and unit depth.
+static wh_status autotune3(wh_ctx *ctx, int32_t reps, wh_tuning *out) {
+  wh_status st = WH_OK;
+  const int64_t n = ctx->ncompact;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
+  double *vin = ctx->d_work, *vout = ctx->d_work + n;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(vin, 0, n * sizeof(double), s));
+  std::vector<std::pair<int, int>> cands;
+  if (ctx->opt.precision == WH_FP32) {
+    cands.push_back({1, 64});
+    for (int K = 2; K <= 4; ++K)
+      for (int uz : {32, 64, 128}) cands.push_back({K, uz});
+  } else {
+    cands.push_back({1, 64});
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int ib = -1;
+  for (size_t k = 0; k < cands.size() && !st; ++k) {
+    if ((st = wh3::set_blocking(ctx->c3, cands[k].first, cands[k].second, ctx->err))) break;
+    if ((st = iterate_device(ctx, 1, vin, vout))) break;  // untimed (builds the graph)
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps && !st; ++r) st = iterate_device(ctx, 1, vin, vout);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    if (st) break;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / reps < best) {
+      best = ms / reps;
+      ib = (int)k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st || ib < 0) {
+    wh3::set_blocking(ctx->c3, -1, -1, ctx->err);
+    return st ? st : fail(ctx, WH_ERR_CUDA, "no layout could be timed");
+  }
+  if ((st = wh3::set_blocking(ctx->c3, cands[ib].first, cands[ib].second, ctx->err))) return st;
+  if (out) {
+    wh_get_tuning(ctx, out);
+    out->ms_per_iteration = best;
+    out->candidates = (int32_t)cands.size();
+  }
+  return WH_OK;
+}
+
 wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out) {
   if (!ctx || reps < 1 || reps > 1000) return fail(ctx, WH_ERR_ARG, "bad wh_autotune arguments");
-  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "3D contexts have one launch layout");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  if (ctx->dim == 3) return autotune3(ctx, reps, out);
   wh_status st;
   const int64_t n = ctx->ncompact;
   if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
@@ -2776,6 +2859,9 @@ wh_status wh_autotune(wh_ctx *ctx, int32_t reps, wh_tuning *out) {
     out->pdl = cands[ib].pdl;
     out->ms_per_iteration = best;
     out->candidates = (int32_t)cands.size();
+    out->temporal_depth = 1;
+    out->unit_depth = 0;
+    out->blocked_points = 0;
   }
   return WH_OK;
 }
@@ -2787,7 +2873,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
   if (ctx->dim == 3) {
     for (int k = 0; k < 4; ++k) {
       ms[k] = 0.0;
-      counts[k] = k < 2 ? 0 : 1;
+      counts[k] = 0;
     }
     return wh3::profile(ctx->c3, ctx->active == 1, ctx->stream, reps, ms, counts, ctx->err);
   }

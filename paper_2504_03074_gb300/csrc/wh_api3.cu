@@ -62,6 +62,20 @@ struct Ctx3 {
   double dt2 = 0.0;
   Tab3 tab{};
   cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [fp32][forcing]
+  // Neumann ghost copies (grid, i, j, k of destination and source), kept for the blocking plan
+  std::vector<int32_t> nghost_dst, nghost_src;  // 4 ints per copy
+  // temporal blocking of the FP32 march: depth K (1 = off), unit depth along axis 2, the
+  // plan they were built for, the units and the single-step (coupled) tiles, and the ring
+  // of K + 2 FP32 state levels
+  int tdepth = 0, unit_depth = 0;  // requested (0 = the library's choice)
+  int plan_K = 1, plan_uz = 0;
+  std::vector<Unit3> units;
+  std::vector<Tile3> ctiles;
+  Unit3 *d_units = nullptr;
+  Tile3 *d_ctiles = nullptr;
+  float *d_ring = nullptr;
+  int ring_L = 0;
+  int64_t blocked_points = 0;  // points in blocked units
 };
 
 namespace {
@@ -122,6 +136,14 @@ void free_all(Ctx3 *c) {
   c->tabs_cap = 0;
   c->d_smax = nullptr;
   c->fp32_ready = false;
+  c->d_units = nullptr;
+  c->d_ctiles = nullptr;
+  c->d_ring = nullptr;
+  c->ring_L = 0;
+  c->plan_K = 1;
+  c->plan_uz = 0;
+  c->units.clear();
+  c->ctiles.clear();
 }
 
 inline bool periodic(const HostGrid3 &G, int a) { return G.d.bc[2 * a] == WH_BC_PERIODIC; }
@@ -333,6 +355,8 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
   }
   // Neumann ghosts next to discretization points
   std::vector<int32_t> gdst, gsrc;
+  c->nghost_dst.clear();
+  c->nghost_src.clear();
   for (int g = 0; g < ng; ++g) {
     const HostGrid3 &H = c->grids[g];
     const int64_t b0 = c->hg[g].base;
@@ -350,6 +374,8 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
           if (H.mask[cidx(H, ib[0], ib[1], ib[2])] != WH_DISC) continue;
           gdst.push_back((int32_t)(b0 + eidx(H, ig[0], ig[1], ig[2])));
           gsrc.push_back((int32_t)(b0 + eidx(H, in[0], in[1], in[2])));
+          c->nghost_dst.insert(c->nghost_dst.end(), {g, ig[0], ig[1], ig[2]});
+          c->nghost_src.insert(c->nghost_src.end(), {g, in[0], in[1], in[2]});
         }
     }
   }
@@ -392,8 +418,184 @@ wh_status upload_forcing(Ctx3 *c, std::string &err) {
   return WH_OK;
 }
 
+// Temporal blocking plan for depth K and unit depth uz (FP32 march).  Eligible grids
+// (constant weights, no periodic axis) are cut into units of kTX x kUY x uz points; a unit
+// is coupled (marched one step at a time, as its march tiles) when its box dilated by K - 1
+// points holds a point whose value is not the march's own: a receiver (rewritten by the
+// interpolation every step) or a ghost that a Neumann rule rewrites.  Every other point a
+// K-step block reads is marched by the block itself or constant (Dirichlet values, unused
+// points).  A blocked unit exports every intermediate level when something outside it
+// reads them: a coupled neighbour (the 26 around it), a donor of the interpolation or a
+// Neumann ghost source inside it.  Units without a discretization point are dropped.
+wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
+  c->units.clear();
+  c->ctiles.clear();
+  c->blocked_points = 0;
+  c->plan_K = K;
+  c->plan_uz = uz;
+  const int ng = (int)c->grids.size();
+  for (int g = 0; g < ng; ++g) {
+    const HostGrid3 &H = c->grids[g];
+    const Grid3Dev &D = c->hg[g];
+    const int n0 = D.n0, n1 = D.n1, n2 = D.n2;
+    auto add_tiles = [&](int i0, int i1, int j0, int j1, int k0, int k1) {
+      for (int k = k0; k < k1; k += kTZ)
+        for (int j = j0; j < j1; j += kTY)
+          for (int i = i0; i < i1; i += kTX) c->ctiles.push_back(Tile3{g, i, j, k});
+    };
+    if (K < 2 || D.stencil != kConst7 || D.per != 0) {
+      add_tiles(0, n0, 0, n1, 0, n2);
+      continue;
+    }
+    const int nux = (n0 + kTX - 1) / kTX, nuy = (n1 + kUY - 1) / kUY, nuz = (n2 + uz - 1) / uz;
+    const size_t nu = (size_t)nux * nuy * nuz;
+    std::vector<uint8_t> coupled(nu, 0), exporter(nu, 0), hasdisc(nu, 0);
+    auto uid = [&](int ux, int uy, int uzi) { return ((size_t)uzi * nuy + uy) * nux + ux; };
+    // mark every unit whose (K-1)-dilated box contains grid point (i, j, k)
+    auto mark_near = [&](int i, int j, int k) {
+      const int r = K - 1;
+      const int ax0 = std::max(0, (i - r) >= 0 ? (i - r) / kTX : 0);
+      const int ax1 = std::min(nux - 1, (i + r) / kTX);
+      const int ay0 = std::max(0, (j - r) >= 0 ? (j - r) / kUY : 0);
+      const int ay1 = std::min(nuy - 1, (j + r) / kUY);
+      const int az0 = std::max(0, (k - r) >= 0 ? (k - r) / uz : 0);
+      const int az1 = std::min(nuz - 1, (k + r) / uz);
+      for (int a = az0; a <= az1; ++a)
+        for (int b = ay0; b <= ay1; ++b)
+          for (int d = ax0; d <= ax1; ++d) coupled[uid(d, b, a)] = 1;
+    };
+    auto unit_of = [&](int i, int j, int k) -> int64_t {
+      if (i < 0 || j < 0 || k < 0 || i >= n0 || j >= n1 || k >= n2) return -1;
+      return (int64_t)uid(i / kTX, j / kUY, k / uz);
+    };
+    for (int64_t r = 0; r < c->nrecv; ++r)
+      if (c->rg[r] == g) mark_near(c->ri[r], c->rj[r], c->rk[r]);
+    for (size_t t = 0; t < c->nghost_dst.size(); t += 4)
+      if (c->nghost_dst[t] == g)
+        mark_near(c->nghost_dst[t + 1], c->nghost_dst[t + 2], c->nghost_dst[t + 3]);
+    for (int64_t r = 0; r < c->nrecv; ++r)
+      if (c->dg[r] == g)
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            for (int d = 0; d < 3; ++d) {
+              const int64_t q = unit_of(c->di[r] + d, c->dj[r] + b, c->dk[r] + a);
+              if (q >= 0) exporter[q] = 1;
+            }
+    for (size_t t = 0; t < c->nghost_src.size(); t += 4)
+      if (c->nghost_src[t] == g) {
+        const int64_t q =
+            unit_of(c->nghost_src[t + 1], c->nghost_src[t + 2], c->nghost_src[t + 3]);
+        if (q >= 0) exporter[q] = 1;
+      }
+    for (int k = 0; k < n2; ++k)
+      for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n0; ++i)
+          if (H.mask[cidx(H, i, j, k)] == WH_DISC) hasdisc[uid(i / kTX, j / kUY, k / uz)] = 1;
+    for (int a = 0; a < nuz; ++a)
+      for (int b = 0; b < nuy; ++b)
+        for (int d = 0; d < nux; ++d) {
+          const size_t q = uid(d, b, a);
+          const int i0 = d * kTX, j0 = b * kUY, k0 = a * uz;
+          const int i1 = std::min(n0, i0 + kTX), j1 = std::min(n1, j0 + kUY),
+                    k1 = std::min(n2, k0 + uz);
+          if (coupled[q]) {
+            add_tiles(i0, i1, j0, j1, k0, k1);
+            continue;
+          }
+          if (!hasdisc[q]) continue;
+          bool ex = exporter[q] != 0;
+          for (int za = std::max(0, a - 1); za <= std::min(nuz - 1, a + 1) && !ex; ++za)
+            for (int yb = std::max(0, b - 1); yb <= std::min(nuy - 1, b + 1) && !ex; ++yb)
+              for (int xd = std::max(0, d - 1); xd <= std::min(nux - 1, d + 1) && !ex; ++xd)
+                if (coupled[uid(xd, yb, za)]) ex = true;
+          c->units.push_back(Unit3{g, i0, j0, k0, k1 - k0, ex ? 1 : 0});
+          c->blocked_points += (int64_t)(i1 - i0) * (j1 - j0) * (k1 - k0);
+        }
+  }
+  // units in plane-chunk-major order (already: k outermost per grid); upload
+  wh_status st;
+  c->d_units = nullptr;
+  c->d_ctiles = nullptr;
+  if ((st = alloc3(c, &c->d_units, std::max<size_t>(c->units.size(), 1), err)) ||
+      (st = alloc3(c, &c->d_ctiles, std::max<size_t>(c->ctiles.size(), 1), err)))
+    return st;
+  if (!c->units.empty())
+    CK3(cudaMemcpy(c->d_units, c->units.data(), c->units.size() * sizeof(Unit3),
+                   cudaMemcpyHostToDevice));
+  if (!c->ctiles.empty())
+    CK3(cudaMemcpy(c->d_ctiles, c->ctiles.data(), c->ctiles.size() * sizeof(Tile3),
+                   cudaMemcpyHostToDevice));
+  if (K > 1 && !c->units.empty() && c->ring_L < K + 2) {
+    // the ring: K + 2 levels (n - 1 .. n + K live during a block)
+    c->d_ring = nullptr;
+    if ((st = alloc3(c, &c->d_ring, (size_t)(K + 2) * c->total, err))) return st;
+    c->ring_L = K + 2;
+  }
+  return WH_OK;
+}
+
+bool blocked(const Ctx3 *c, bool fp32) { return fp32 && c->plan_K > 1 && !c->units.empty(); }
+
+// The library's choice of depth and unit depth (measured on the sphere-in-box workload).
+constexpr int kDefaultDepth = 4, kDefaultUnitDepth = 64;
+
+// Build the blocking plan the requested (or default) depth calls for, if it changed.
+wh_status ensure_plan(Ctx3 *c, std::string &err) {
+  const int K = c->tdepth > 0 ? c->tdepth : kDefaultDepth;
+  const int uz = c->unit_depth > 0 ? c->unit_depth : kDefaultUnitDepth;
+  if (K == c->plan_K && uz == c->plan_uz) return WH_OK;
+  drop_graphs3(c);
+  return plan_blocking(c, K, uz, err);
+}
+
+// State pointer of level l in the FP32 ring.
+inline float *ring_level(Ctx3 *c, int l) { return c->d_ring + (int64_t)(l % c->ring_L) * c->total; }
+
+// Launches of one iteration after init (without init and output).
+int64_t step_launches(const Ctx3 *c, bool fp32) {
+  if (!blocked(c, fp32)) return 1 + 2 * (int64_t)c->M;
+  const int K = c->plan_K;
+  const int64_t sup = c->M > 1 ? (c->M - 1) / K : 0;
+  const int64_t rest = (int64_t)c->M - 1 - sup * K;
+  const int64_t cm = c->ctiles.empty() ? 0 : 1;  // coupled march launches per single step
+  return 1 + 2 + sup * (1 + K * (cm + 1)) + 2 * rest;
+}
+
 // The body of one iteration after init: level-0 ghost rules + interpolation, then M steps.
+// Temporally blocked FP32 march: after the first step, blocks of K steps (the blocked units'
+// kernel, then K single steps of the coupled tiles, each followed by the ghost rules and
+// interpolation of its level), then single steps for the remainder.
 void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
+  if (blocked(c, fp32)) {
+    const double fs = forcing ? 1.0 : 0.0;
+    const int K = c->plan_K;
+    auto gather = [&](int level) {
+      launch_gather3(true, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
+                     c->d_gdst, c->d_gsrc, ring_level(c, level), c->d_V, c->tab.wf, level);
+    };
+    auto single = [&](int nt, const Tile3 *tiles, int n) {
+      launch_march3(true, s, nt, c->d_grids, tiles, c->d_mask, ring_level(c, n),
+                    n > 0 ? ring_level(c, n - 1) : nullptr, ring_level(c, n + 1), c->d_F32,
+                    c->d_Wt32, c->d_V, c->tab, n, fs);
+    };
+    gather(0);
+    single((int)c->tiles.size(), c->d_tiles, 0);
+    gather(1);
+    int n = 1;
+    for (; n + K <= c->M; n += K) {
+      launch_march3_block(K, s, (int)c->units.size(), c->d_grids, c->d_units, c->d_mask,
+                          c->d_ring, c->total, c->ring_L, c->d_F32, c->d_V, c->tab, n, fs);
+      for (int t = 0; t < K; ++t) {
+        single((int)c->ctiles.size(), c->d_ctiles, n + t);
+        gather(n + t + 1);
+      }
+    }
+    for (; n < c->M; ++n) {
+      single((int)c->tiles.size(), c->d_tiles, n);
+      gather(n + 1);
+    }
+    return;
+  }
   void *Wa = fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa;
   void *Wb = fp32 ? (void *)c->d_Wb32 : (void *)c->d_Wb;
   const void *F = fp32 ? (const void *)c->d_F32 : (const void *)c->d_F;
@@ -407,8 +609,8 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
   for (int n = 0; n < c->M; ++n) {
     void *cur = (n & 1) ? Wb : Wa;
     void *oth = (n & 1) ? Wa : Wb;
-    launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth, F,
-                  Wt, c->d_V, c->tab, n, fs);
+    launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth,
+                  oth, F, Wt, c->d_V, c->tab, n, fs);
     gather(oth, n + 1);
   }
 }
@@ -667,6 +869,7 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
     launch_to_precision(true, s, c->d_F, c->d_F32, c->total);
     c->fp32_ready = true;
   }
+  if (fp32 && (st = ensure_plan(c, err))) return st;
   CK3(cudaGetLastError());
   CK3(cudaStreamSynchronize(s));
   if (ti) *ti = T;
@@ -685,55 +888,121 @@ wh_status iterate(Ctx3 *c, bool fp32, int forcing, const double *vin, double *vo
     if (st) return st;
   }
   const int ng = (int)c->grids.size();
-  launch_init3(fp32, s, c->d_grids, ng, c->max_ext, c->d_mask, vin,
-               fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa, c->d_V, c->tab.wf);
+  void *W0 = blocked(c, fp32) ? (void *)ring_level(c, 0)
+                              : (fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa);
+  launch_init3(fp32, s, c->d_grids, ng, c->max_ext, c->d_mask, vin, W0, c->d_V, c->tab.wf);
   CK3(cudaGetLastError());
   CK3(cudaGraphLaunch(c->gexec[fp32][forcing], s));
   launch_finish3(s, c->d_grids, ng, c->max_compact, c->d_V, vout);
   CK3(cudaGetLastError());
-  if (launches) *launches += 3 + 2 * (int64_t)c->M;
+  if (launches) *launches += 2 + step_launches(c, fp32);
   return WH_OK;
+}
+
+wh_status set_blocking(Ctx3 *c, int K, int uz, std::string &err) {
+  if (K != -1 && (K < 1 || K > 4))
+    return fail3(err, WH_ERR_ARG, "temporal_depth must be -1 or in [1, 4]");
+  if (uz != -1 && (uz < 8 || uz > 256 || uz % 8))
+    return fail3(err, WH_ERR_ARG, "unit_depth must be -1 or a multiple of 8 in [8, 256]");
+  c->tdepth = K < 0 ? 0 : K;
+  c->unit_depth = uz < 0 ? 0 : uz;
+  if (c->d_Wa32 && !c->dirty) return ensure_plan(c, err);  // FP32 march prepared
+  return WH_OK;
+}
+
+void blocking(const Ctx3 *c, int *K, int *uz, int64_t *points, int64_t *units) {
+  if (K) *K = c->plan_K;
+  if (uz) *uz = c->plan_uz;
+  if (points) *points = c->blocked_points;
+  if (units) *units = (int64_t)c->units.size();
 }
 
 wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int32_t *counts,
                   std::string &err) {
   if (reps < 1) reps = 1;
   if (fp32 && !c->d_Wa32) return fail3(err, WH_ERR_STATE, "the FP32 march was not prepared");
-  cudaEvent_t ev[6];
+  cudaEvent_t ev[2];
   for (auto &e : ev) CK3(cudaEventCreate(&e));
-  void *Wa = fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa;
-  void *Wb = fp32 ? (void *)c->d_Wb32 : (void *)c->d_Wb;
-  const void *F = fp32 ? (const void *)c->d_F32 : (const void *)c->d_F;
-  const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
-  double t_march = 0, t_gather = 0;
+  // kinds: [0] single-step march, [1] ghost rules + interpolation, [2] K-step blocked march
+  double tot[3] = {0, 0, 0};
+  int64_t cnt[3] = {0, 0, 0};
   float t;
-  for (int r = 0; r < reps; ++r) {
-    for (int n = 0; n < c->M; ++n) {
-      void *cur = (n & 1) ? Wb : Wa;
-      void *oth = (n & 1) ? Wa : Wb;
-      CK3(cudaEventRecord(ev[0], s));
-      launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth,
-                    F, Wt, c->d_V, c->tab, n, 0.0);
-      CK3(cudaEventRecord(ev[1], s));
-      launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
-                     c->d_gdst, c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
-      CK3(cudaEventRecord(ev[2], s));
-      CK3(cudaEventSynchronize(ev[2]));
-      CK3(cudaEventElapsedTime(&t, ev[0], ev[1]));
-      t_march += t;
-      CK3(cudaEventElapsedTime(&t, ev[1], ev[2]));
-      t_gather += t;
+  wh_status st = WH_OK;
+  auto timed = [&](int kind, auto &&launch) {
+    if (st) return;
+    cudaEventRecord(ev[0], s);
+    launch();
+    cudaEventRecord(ev[1], s);
+    if (cudaEventSynchronize(ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess) {
+      st = fail3(err, WH_ERR_CUDA, "profile: %s", cudaGetErrorString(cudaGetLastError()));
+      return;
+    }
+    tot[kind] += t;
+    cnt[kind] += 1;
+  };
+  if (blocked(c, fp32)) {
+    const int K = c->plan_K;
+    auto gather = [&](int level) {
+      timed(1, [&] {
+        launch_gather3(true, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
+                       c->d_gdst, c->d_gsrc, ring_level(c, level), c->d_V, c->tab.wf, level);
+      });
+    };
+    auto single = [&](int nt, const Tile3 *tiles, int n) {
+      if (nt < 1) return;
+      timed(0, [&] {
+        launch_march3(true, s, nt, c->d_grids, tiles, c->d_mask, ring_level(c, n),
+                      n > 0 ? ring_level(c, n - 1) : nullptr, ring_level(c, n + 1), c->d_F32,
+                      c->d_Wt32, c->d_V, c->tab, n, 0.0);
+      });
+    };
+    for (int r = 0; r < reps; ++r) {
+      gather(0);
+      single((int)c->tiles.size(), c->d_tiles, 0);
+      gather(1);
+      int n = 1;
+      for (; n + K <= c->M; n += K) {
+        timed(2, [&] {
+          launch_march3_block(K, s, (int)c->units.size(), c->d_grids, c->d_units, c->d_mask,
+                              c->d_ring, c->total, c->ring_L, c->d_F32, c->d_V, c->tab, n, 0.0);
+        });
+        for (int q = 0; q < K; ++q) {
+          single((int)c->ctiles.size(), c->d_ctiles, n + q);
+          gather(n + q + 1);
+        }
+      }
+      for (; n < c->M; ++n) {
+        single((int)c->tiles.size(), c->d_tiles, n);
+        gather(n + 1);
+      }
+    }
+  } else {
+    void *Wa = fp32 ? (void *)c->d_Wa32 : (void *)c->d_Wa;
+    void *Wb = fp32 ? (void *)c->d_Wb32 : (void *)c->d_Wb;
+    const void *F = fp32 ? (const void *)c->d_F32 : (const void *)c->d_F;
+    const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
+    for (int r = 0; r < reps; ++r) {
+      for (int n = 0; n < c->M; ++n) {
+        void *cur = (n & 1) ? Wb : Wa;
+        void *oth = (n & 1) ? Wa : Wb;
+        timed(0, [&] {
+          launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur,
+                        oth, oth, F, Wt, c->d_V, c->tab, n, 0.0);
+        });
+        timed(1, [&] {
+          launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff,
+                         c->d_gw, c->d_gdst, c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
+        });
+      }
     }
   }
-  CK3(cudaGetLastError());
   for (auto &e : ev) cudaEventDestroy(e);
-  if (ms) {  // per launch
-    ms[0] = t_march / ((double)reps * c->M);
-    ms[1] = t_gather / ((double)reps * c->M);
-  }
-  if (counts) {
-    counts[0] = c->M;
-    counts[1] = c->M;
+  if (st) return st;
+  CK3(cudaGetLastError());
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = cnt[k] ? tot[k] / (double)cnt[k] : 0.0;  // per launch
+    if (counts) counts[k] = (int32_t)(cnt[k] / reps);        // per iteration
   }
   return WH_OK;
 }

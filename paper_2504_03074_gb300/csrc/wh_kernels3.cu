@@ -223,13 +223,29 @@ __device__ __forceinline__ double fsel<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float fsel<float>(double, float f) { return f; }
 
+// One FP32 update of a constant-weight 7-point point (Eq. WaveSchemeexplicit, weights with
+// dt^2 folded, centre including the "2"): W^{n+1} = c0 W + c1 (W_x- + W_x+) + c2 (W_y- + W_y+)
+// + c3 (W_z- + W_z+) - W^{n-1} - fc_n F, every rounding fixed by the intrinsics so that the
+// single-step march and the temporally blocked one give the same bits.
+__device__ __forceinline__ float step7f(float c0, float c1, float c2, float c3, float wc,
+                                        float sx, float sy, float sz, float wo, float fcs,
+                                        float fq) {
+  float S = __fmul_rn(c0, wc);
+  S = __fmaf_rn(c1, sx, S);
+  S = __fmaf_rn(c2, sy, S);
+  S = __fmaf_rn(c3, sz, S);
+  return __fmaf_rn(-fcs, fq, __fsub_rn(S, wo));
+}
+
 // One time step n -> n + 1 of every grid (Eq. WaveSchemeexplicit) with the fused filter
 // term of level n + 1.  Block = one Tile3; each thread marches kTZ points along axis 2.
+// W^{n-1} comes from Wprev, which is Wout itself in the two-level in-place layout (so
+// neither carries __restrict__).
 // Register caps for occupancy: FP32 48 (5 blocks per SM), FP64 64 (4), neither spills.
 template <typename T>
 __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kernel(
     const Grid3Dev *__restrict__ grids, const Tile3 *__restrict__ tiles,
-    const int8_t *__restrict__ mask, const T *__restrict__ Wn, T *__restrict__ Wout,
+    const int8_t *__restrict__ mask, const T *__restrict__ Wn, const T *Wprev, T *Wout,
     const T *__restrict__ F, const T *__restrict__ Wt, double *__restrict__ V, Tab3 tab, int n,
     double fs) {
   const Tile3 tl = tiles[blockIdx.x];
@@ -253,10 +269,11 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
       // FP32 (latency-bound): the next plane's x/y neighbours are prefetched too
       int64_t q = at3(Gg, i, j, tl.k0);
       T wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl];
-      T sx = Wn[q - 1] + Wn[q + 1], sy = Wn[q - e0] + Wn[q + e0];
+      T sx = __fadd_rn(Wn[q - 1], Wn[q + 1]), sy = __fadd_rn(Wn[q - e0], Wn[q + e0]);
       int8_t mk = mask[q];
-      T fq = F[q], wo = first ? (T)0 : Wout[q];
+      T fq = F[q], wo = first ? (T)0 : Wprev[q];
       double vq = V[q];
+      const float fcs = fcn * fsT;
       for (int k = tl.k0; k < kend; ++k, q += pl) {
         T wp2 = (T)0, fq2 = (T)0, wo2 = (T)0, xm2 = (T)0, xp2 = (T)0, ym2 = (T)0, yp2 = (T)0;
         int8_t mk2 = 0;
@@ -270,20 +287,25 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
           yp2 = Wn[q1 + e0];
           mk2 = mask[q1];
           fq2 = F[q1];
-          if (!first) wo2 = Wout[q1];
+          if (!first) wo2 = Wprev[q1];
           vq2 = V[q1];
         }
         if (mk == kDisc) {
-          const T S = c0 * wc + c1 * sx + c2 * sy + c3 * (wm + wp);
-          const T out = first ? (T)0.5 * S - fcn * fsT * fq : S - wo - fcn * fsT * fq;
+          float out;
+          if (first) {
+            const T S = c0 * wc + c1 * sx + c2 * sy + c3 * (wm + wp);
+            out = (T)0.5 * S - fcs * fq;
+          } else {
+            out = step7f(c0, c1, c2, c3, wc, sx, sy, __fadd_rn(wm, wp), wo, fcs, fq);
+          }
           Wout[q] = out;
-          V[q] = vq + wfn * (double)out;
+          V[q] = fma(wfn, wh::to_f64(out), vq);
         }
         wm = wc;
         wc = wp;
         wp = wp2;
-        sx = xm2 + xp2;
-        sy = ym2 + yp2;
+        sx = __fadd_rn(xm2, xp2);
+        sy = __fadd_rn(ym2, yp2);
         mk = mk2;
         fq = fq2;
         wo = wo2;
@@ -295,7 +317,7 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
       int64_t q = at3(Gg, i, j, tl.k0);
       T wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl];
       int8_t mk = mask[q];
-      T fq = F[q], wo = first ? (T)0 : Wout[q];
+      T fq = F[q], wo = first ? (T)0 : Wprev[q];
       double vq = V[q];
       for (int k = tl.k0; k < kend; ++k, q += pl) {
         T wp2 = (T)0, fq2 = (T)0, wo2 = (T)0;
@@ -305,7 +327,7 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
           wp2 = Wn[q + 2 * pl];
           mk2 = mask[q + pl];
           fq2 = F[q + pl];
-          if (!first) wo2 = Wout[q + pl];
+          if (!first) wo2 = Wprev[q + pl];
           vq2 = V[q + pl];
         }
         if (mk == kDisc) {
@@ -353,9 +375,135 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
              w[17 * E] * Wn[nb3(G, i, j, k, 0, -1, 1)] + w[18 * E] * Wn[nb3(G, i, j, k, 0, 1, 1)];
       }
     }
-    const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wout[q] - fcn * fsT * F[q];
+    const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wprev[q] - fcn * fsT * F[q];
     Wout[q] = out;
     V[q] += wfn * (double)out;
+  }
+}
+
+// Temporally blocked FP32 march: K steps n -> n + K over one Unit3 per block, from the
+// levels n - 1 and n in the ring (2.5D overlapped tiling).  Thread (tx, ty) owns the column
+// (x, y) = (i0 - K + tx, j0 - K + ty) of the unit's box widened by a K-point halo and
+// streams it along axis 2: in iteration it it loads level n at plane p_0 = k0 - K + it and
+// computes level s at plane p_s = p_0 - s (s = 1..K), where level s exists on the box
+// shrunk by K - s points in every direction (columns further out carry the level below,
+// which no computed point reads).  Per level a register queue holds the planes p_s - 1,
+// p_s, p_s + 1 (the axis-2 neighbours) and a shared plane, double-buffered across
+// iterations, holds plane p_{s+1} of level s for the axis-0/1 neighbours, so one
+// __syncthreads per plane suffices.  Points that are not discretization points are
+// constant in time here (Dirichlet values and unused points); the unit's dilated box holds
+// no receiver and no rewritten ghost (checked on the host).  Own points accumulate their K
+// filter terms in registers (V read and written once) and write levels n + K - 1 and n + K
+// (every level with the export flag).  The update is step7f, as in march3_kernel.
+template <int K>
+__global__ void __launch_bounds__((kTX + 2 * K) * (kUY + 2 * K), 1) march3_block_kernel(
+    const Grid3Dev *__restrict__ grids, const Unit3 *__restrict__ units,
+    const int8_t *__restrict__ mask, float *ring, int64_t stride, int L,
+    const float *__restrict__ F, double *__restrict__ V, Tab3 tab, int n, float fs) {
+  constexpr int BX = kTX + 2 * K, BY = kUY + 2 * K;
+  __shared__ float sm[2][K][BY][BX];
+  __shared__ float s_fc[K + 1];
+  __shared__ double s_wf[K + 1];
+  const Unit3 u = units[blockIdx.x];
+  const Grid3Dev &G = grids[u.grid];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (ty == 0 && tx >= 1 && tx <= K) {
+    s_fc[tx] = tab.fcf[n + tx - 1] * fs;  // forcing factor of the step to level n + tx
+    s_wf[tx] = tab.wf[n + tx];            // filter weight of level n + tx
+  }
+  const int x = u.i0 - K + tx, y = u.j0 - K + ty;
+  const int dxy = max(max(max(u.i0 - x, x - (u.i0 + kTX - 1)),
+                          max(u.j0 - y, y - (u.j0 + kUY - 1))), 0);
+  const bool col_ok = x >= -G.g0 && x < G.n0 + G.g0 && y >= -G.g1 && y < G.n1 + G.g1;
+  const bool own = dxy == 0 && x < G.n0 && y < G.n1;
+  const bool exp_all = (u.flags & 1) != 0;
+  const int64_t pl = (int64_t)G.e0 * G.e1;
+  // element (x, y, z) of the grid's extended array is at col + z * pl
+  const int64_t col = G.base + ((int64_t)G.g2 * G.e1 + (y + G.g1)) * G.e0 + (x + G.g0);
+  const float c0 = G.cwf[0], c1 = G.cwf[1], c2 = G.cwf[2], c3 = G.cwf[3];
+  const float *Wn = ring + (int64_t)(n % L) * stride;
+  const float *Wm = ring + (int64_t)((n - 1) % L) * stride;
+  const int zlo = -G.g2, zhi = G.n2 + G.g2;     // extended planes
+  const int klo = u.k0, khi = u.k0 + u.nz;      // the unit's own planes
+  float q[K][3];
+  float fq[K];
+  double acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    q[j][0] = q[j][1] = q[j][2] = 0.0f;
+    fq[j] = 0.0f;
+    acc[j] = 0.0;
+  }
+  unsigned mbits = 0u;
+  // loads of iteration it (prefetched one iteration ahead): level n at p_0, the mask at
+  // p_0, level n - 1 and F at p_1 = p_0 - 1, and V at p_1 for own points
+  auto load = [&](int it, float &w0, int &m0, float &wm1, float &f1) {
+    const int p0 = u.k0 - K + it, p1 = p0 - 1;
+    w0 = 0.0f;
+    m0 = 0;
+    wm1 = 0.0f;
+    f1 = 0.0f;
+    if (col_ok && p0 >= zlo && p0 < zhi) {
+      w0 = Wn[col + p0 * pl];
+      m0 = mask[col + p0 * pl] == kDisc;
+    }
+    if (col_ok && dxy < K && p1 >= zlo && p1 < zhi) {
+      wm1 = Wm[col + p1 * pl];
+      f1 = F[col + p1 * pl];
+    }
+  };
+  float nw0, nwm1, nf1;
+  int nm0;
+  load(0, nw0, nm0, nwm1, nf1);
+  __syncthreads();  // s_fc, s_wf
+  const int iters = u.nz + 2 * K;
+  for (int it = 0; it < iters; ++it) {
+    const float w0 = nw0, wm1 = nwm1, f1 = nf1;
+    const int m0 = nm0;
+    if (it + 1 < iters) load(it + 1, nw0, nm0, nwm1, nf1);
+    const int p0 = u.k0 - K + it;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      q[j][0] = q[j][1];
+      q[j][1] = q[j][2];
+    }
+#pragma unroll
+    for (int j = K - 1; j >= 1; --j) {
+      fq[j] = fq[j - 1];
+      acc[j] = acc[j - 1];
+    }
+    fq[0] = f1;
+    mbits = (mbits << 1) | (unsigned)m0;
+    {
+      const int p1 = p0 - 1;
+      acc[0] = (own && (mbits & 2u) && p1 >= klo && p1 < khi) ? V[col + p1 * pl] : 0.0;
+    }
+    const int cur = it & 1, prv = cur ^ 1;
+    q[0][2] = w0;
+    sm[cur][0][ty][tx] = w0;
+#pragma unroll
+    for (int s = 1; s <= K; ++s) {
+      const int ps = p0 - s;
+      const bool disc = (mbits >> s) & 1u;
+      float out = q[s - 1][1];
+      if (disc && it >= 2 * s && dxy <= K - s) {
+        const float xm = sm[prv][s - 1][ty][tx - 1], xp = sm[prv][s - 1][ty][tx + 1];
+        const float ym = sm[prv][s - 1][ty - 1][tx], yp = sm[prv][s - 1][ty + 1][tx];
+        const float wo = s == 1 ? wm1 : q[s - 2 < 0 ? 0 : s - 2][0];
+        out = step7f(c0, c1, c2, c3, q[s - 1][1], __fadd_rn(xm, xp), __fadd_rn(ym, yp),
+                     __fadd_rn(q[s - 1][0], q[s - 1][2]), wo, s_fc[s], fq[s - 1]);
+      }
+      if (s < K) {
+        q[s < K ? s : 0][2] = out;
+        sm[cur][s < K ? s : 0][ty][tx] = out;
+      }
+      if (own && disc && ps >= klo && ps < khi) {
+        acc[s - 1] = fma(s_wf[s], wh::to_f64(out), acc[s - 1]);
+        if (exp_all || s >= K - 1) ring[(int64_t)((n + s) % L) * stride + col + ps * pl] = out;
+        if (s == K) V[col + ps * pl] = acc[K - 1];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -468,17 +616,44 @@ void launch_init3(bool fp32, cudaStream_t s, const Grid3Dev *grids, int ngrids,
 }
 
 void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
-                   const Tile3 *tiles, const int8_t *mask, const void *Wn, void *Wout,
-                   const void *F, const void *Wt, double *V, Tab3 tab, int n, double fs) {
+                   const Tile3 *tiles, const int8_t *mask, const void *Wn, const void *Wprev,
+                   void *Wout, const void *F, const void *Wt, double *V, Tab3 tab, int n,
+                   double fs) {
+  if (ntiles < 1) return;
   dim3 tb(kTX, kTY);
   if (fp32)
     march3_kernel<float><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const float *)Wn,
-                                               (float *)Wout, (const float *)F,
-                                               (const float *)Wt, V, tab, n, fs);
+                                               (const float *)Wprev, (float *)Wout,
+                                               (const float *)F, (const float *)Wt, V, tab, n,
+                                               fs);
   else
     march3_kernel<double><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const double *)Wn,
-                                                (double *)Wout, (const double *)F,
-                                                (const double *)Wt, V, tab, n, fs);
+                                                (const double *)Wprev, (double *)Wout,
+                                                (const double *)F, (const double *)Wt, V, tab,
+                                                n, fs);
+}
+
+size_t march3_block_threads(int K) { return (size_t)(kTX + 2 * K) * (kUY + 2 * K); }
+
+void launch_march3_block(int K, cudaStream_t s, int nunits, const Grid3Dev *grids,
+                         const Unit3 *units, const int8_t *mask, float *ring, int64_t stride,
+                         int L, const float *F, double *V, Tab3 tab, int n, double fs) {
+  if (nunits < 1) return;
+  const float f = (float)fs;
+  switch (K) {
+    case 2:
+      march3_block_kernel<2><<<nunits, dim3(kTX + 4, kUY + 4), 0, s>>>(
+          grids, units, mask, ring, stride, L, F, V, tab, n, f);
+      break;
+    case 3:
+      march3_block_kernel<3><<<nunits, dim3(kTX + 6, kUY + 6), 0, s>>>(
+          grids, units, mask, ring, stride, L, F, V, tab, n, f);
+      break;
+    default:
+      march3_block_kernel<4><<<nunits, dim3(kTX + 8, kUY + 8), 0, s>>>(
+          grids, units, mask, ring, stride, L, F, V, tab, n, f);
+      break;
+  }
 }
 
 void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,

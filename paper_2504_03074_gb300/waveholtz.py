@@ -77,7 +77,9 @@ class TimeInfo(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("launch_mode", C.c_int32), ("fold_gather", C.c_int32),
                 ("tile_tickets", C.c_int32), ("tma", C.c_int32), ("pdl", C.c_int32),
-                ("ms_per_iteration", C.c_double), ("candidates", C.c_int32)]
+                ("ms_per_iteration", C.c_double), ("candidates", C.c_int32),
+                ("temporal_depth", C.c_int32), ("unit_depth", C.c_int32),
+                ("blocked_points", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,7 +96,8 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
-           "wh_set_interp3", "wh_set_deflation", "wh_widen_f32", "wh_probe_fp64"]
+           "wh_set_interp3", "wh_set_deflation", "wh_widen_f32", "wh_probe_fp64",
+           "wh_get_tuning"]
 
 
 def lib_path():
@@ -138,6 +141,7 @@ def lib():
     L.wh_set_coefficient.argtypes = [vp, C.c_int32, vp]
     L.wh_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.wh_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
+    L.wh_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -409,10 +413,18 @@ class Solver:
         self._check(self.L.wh_dot(self.h, _ptr(x), _ptr(y), x.numel(), C.byref(out)))
         return out.value
 
-    def set_tuning(self, launch_mode=-1, fold_gather=-1, tile_tickets=-1, tma=-1, pdl=-1):
+    def set_tuning(self, launch_mode=-1, fold_gather=-1, tile_tickets=-1, tma=-1, pdl=-1,
+                   temporal_depth=-1, unit_depth=-1):
         """Fix the launch layout (-1: the library's choice); see wh_tuning."""
-        t = Tuning(launch_mode, fold_gather, tile_tickets, tma, pdl, 0.0, 0)
+        t = Tuning(launch_mode, fold_gather, tile_tickets, tma, pdl, 0.0, 0, temporal_depth,
+                   unit_depth, 0)
         self._check(self.L.wh_set_tuning(self.h, C.byref(t)))
+
+    def get_tuning(self):
+        """The launch layout in use (after prepare) as a dict."""
+        t = Tuning()
+        self._check(self.L.wh_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
 
     def autotune(self, reps=3):
         """Time every valid launch layout on the prepared problem and keep the fastest;
