@@ -94,10 +94,13 @@ void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
 // K steps n -> n + K (K = 2, 3 or 4) of the FP32 march over `nunits` units.  ring holds L
 // levels of the FP32 state, level l at ring + (l % L) * stride; levels n - 1 and n are read,
 // levels n + 1 .. n + K written (only n + K - 1 and n + K for units without the export
-// flag).  Same arithmetic, in the same order, as launch_march3's.
+// flag).  FM: the FP32 forcing at discretization points, NaN elsewhere
+// (launch_forcing_mask).  Same arithmetic, in the same order, as launch_march3's.
 void launch_march3_block(int K, cudaStream_t s, int nunits, const Grid3Dev *grids,
-                         const Unit3 *units, const int8_t *mask, float *ring, int64_t stride,
-                         int L, const float *F, double *V, Tab3 tab, int n, double fs);
+                         const Unit3 *units, const float *FM, float *ring, int64_t stride,
+                         int L, double *V, Tab3 tab, int n, double fs);
+void launch_forcing_mask(cudaStream_t s, const float *F, const int8_t *mask, float *FM,
+                         int64_t n);
 size_t march3_block_threads(int K);
 // Receiver r of R: donor (i0 + a, j0 + b, k0 + c) at gbase[r] + goff[a R + r] +
 // goff[(3 + b) R + r] + goff[(6 + c) R + r] with weight gw[a R + r] gw[(3 + b) R + r]

@@ -74,6 +74,7 @@ struct Ctx3 {
   Unit3 *d_units = nullptr;
   Tile3 *d_ctiles = nullptr;
   float *d_ring = nullptr;
+  float *d_FM32 = nullptr;  // FP32 forcing at discretization points, NaN elsewhere
   int ring_L = 0;
   int64_t blocked_points = 0;  // points in blocked units
 };
@@ -139,6 +140,7 @@ void free_all(Ctx3 *c) {
   c->d_units = nullptr;
   c->d_ctiles = nullptr;
   c->d_ring = nullptr;
+  c->d_FM32 = nullptr;
   c->ring_L = 0;
   c->plan_K = 1;
   c->plan_uz = 0;
@@ -443,7 +445,9 @@ wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
         for (int j = j0; j < j1; j += kTY)
           for (int i = i0; i < i1; i += kTX) c->ctiles.push_back(Tile3{g, i, j, k});
     };
-    if (K < 2 || D.stencil != kConst7 || D.per != 0) {
+    // the blocked kernel indexes the ring with 32-bit integers
+    const bool fits = (int64_t)(K + 2) * c->total < (int64_t)INT32_MAX;
+    if (K < 2 || !fits || D.stencil != kConst7 || D.per != 0) {
       add_tiles(0, n0, 0, n1, 0, n2);
       continue;
     }
@@ -531,13 +535,23 @@ wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
     if ((st = alloc3(c, &c->d_ring, (size_t)(K + 2) * c->total, err))) return st;
     c->ring_L = K + 2;
   }
+  if (K > 1 && !c->units.empty() && !c->d_FM32) {
+    if ((st = alloc3(c, &c->d_FM32, c->total, err))) return st;
+    launch_forcing_mask(nullptr, c->d_F32, c->d_mask, c->d_FM32, c->total);
+    CK3(cudaDeviceSynchronize());
+  }
   return WH_OK;
 }
 
 bool blocked(const Ctx3 *c, bool fp32) { return fp32 && c->plan_K > 1 && !c->units.empty(); }
 
-// The library's choice of depth and unit depth (measured on the sphere-in-box workload).
-constexpr int kDefaultDepth = 4, kDefaultUnitDepth = 64;
+// The library's choice: depth 3 with 64-plane units when at least kAutoBlockedShare of the
+// points advance in blocked units, else single steps.  Measured: on a 512^3 cube (all
+// points blocked) depth 3 runs 1.27x the single-step march; on the sphere-in-box, where 86%
+// are blocked, the coupled region's single steps (the curvilinear shell and patches, the
+// background around the hole) cost more than blocking saves.
+constexpr int kDefaultDepth = 3, kDefaultUnitDepth = 64;
+constexpr double kAutoBlockedShare = 0.95;
 
 // Build the blocking plan the requested (or default) depth calls for, if it changed.
 wh_status ensure_plan(Ctx3 *c, std::string &err) {
@@ -545,7 +559,11 @@ wh_status ensure_plan(Ctx3 *c, std::string &err) {
   const int uz = c->unit_depth > 0 ? c->unit_depth : kDefaultUnitDepth;
   if (K == c->plan_K && uz == c->plan_uz) return WH_OK;
   drop_graphs3(c);
-  return plan_blocking(c, K, uz, err);
+  wh_status st = plan_blocking(c, K, uz, err);
+  if (st || c->tdepth > 0) return st;
+  if ((double)c->blocked_points < kAutoBlockedShare * (double)c->ncompact)
+    st = plan_blocking(c, 1, uz, err);
+  return st;
 }
 
 // State pointer of level l in the FP32 ring.
@@ -583,8 +601,8 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
     gather(1);
     int n = 1;
     for (; n + K <= c->M; n += K) {
-      launch_march3_block(K, s, (int)c->units.size(), c->d_grids, c->d_units, c->d_mask,
-                          c->d_ring, c->total, c->ring_L, c->d_F32, c->d_V, c->tab, n, fs);
+      launch_march3_block(K, s, (int)c->units.size(), c->d_grids, c->d_units, c->d_FM32,
+                          c->d_ring, c->total, c->ring_L, c->d_V, c->tab, n, fs);
       for (int t = 0; t < K; ++t) {
         single((int)c->ctiles.size(), c->d_ctiles, n + t);
         gather(n + t + 1);
@@ -867,6 +885,7 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
   }
   if (fp32 && !c->fp32_ready) {
     launch_to_precision(true, s, c->d_F, c->d_F32, c->total);
+    if (c->d_FM32) launch_forcing_mask(s, c->d_F32, c->d_mask, c->d_FM32, c->total);
     c->fp32_ready = true;
   }
   if (fp32 && (st = ensure_plan(c, err))) return st;
@@ -964,8 +983,8 @@ wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int3
       int n = 1;
       for (; n + K <= c->M; n += K) {
         timed(2, [&] {
-          launch_march3_block(K, s, (int)c->units.size(), c->d_grids, c->d_units, c->d_mask,
-                              c->d_ring, c->total, c->ring_L, c->d_F32, c->d_V, c->tab, n, 0.0);
+          launch_march3_block(K, s, (int)c->units.size(), c->d_grids, c->d_units, c->d_FM32,
+                              c->d_ring, c->total, c->ring_L, c->d_V, c->tab, n, 0.0);
         });
         for (int q = 0; q < K; ++q) {
           single((int)c->ctiles.size(), c->d_ctiles, n + q);

@@ -350,12 +350,21 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
   }
   const Grid3Dev G = Gg;
   const int64_t E = G.ext;
+  // neighbour offsets of this column: wraps on periodic axes 0 and 1 are fixed per column,
+  // on a periodic axis 2 they depend on the plane (at3 is linear in each index, so the
+  // offset of a diagonal neighbour is the sum of its axis offsets)
+  const int64_t oxm = (per & 1) && i == 0 ? (int64_t)(n0 - 1) : -1;
+  const int64_t oxp = (per & 1) && i == n0 - 1 ? -(int64_t)(n0 - 1) : 1;
+  const int64_t oym = (per & 2) && j == 0 ? (int64_t)(n1 - 1) * e0 : -e0;
+  const int64_t oyp = (per & 2) && j == n1 - 1 ? -(int64_t)(n1 - 1) * e0 : e0;
+  const int64_t q0 = at3(G, i, j, tl.k0);
   for (int k = tl.k0; k < kend; ++k) {
-    const int64_t q = at3(G, i, j, k);
+    const int64_t q = q0 + (int64_t)(k - tl.k0) * pl;
     if (mask[q] != kDisc) continue;
-    const int64_t xm = nb3(G, i, j, k, -1, 0, 0), xp = nb3(G, i, j, k, 1, 0, 0);
-    const int64_t ym = nb3(G, i, j, k, 0, -1, 0), yp = nb3(G, i, j, k, 0, 1, 0);
-    const int64_t zm = nb3(G, i, j, k, 0, 0, -1), zp = nb3(G, i, j, k, 0, 0, 1);
+    const int64_t ozm = (per & 4) && k == 0 ? (int64_t)(n2 - 1) * pl : -pl;
+    const int64_t ozp = (per & 4) && k == n2 - 1 ? -(int64_t)(n2 - 1) * pl : pl;
+    const int64_t xm = q + oxm, xp = q + oxp, ym = q + oym, yp = q + oyp, zm = q + ozm,
+                  zp = q + ozp;
     T S;
     if (stencil == kConst7) {
       S = fsel<T>(G.cw[0], G.cwf[0]) * Wn[q] + fsel<T>(G.cw[1], G.cwf[1]) * (Wn[xm] + Wn[xp]) +
@@ -367,12 +376,12 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
           w[4 * E] * Wn[yp] + w[5 * E] * Wn[zm] + w[6 * E] * Wn[zp];
       if (stencil == kPoint19) {
         // edges of pairs (x,y), (x,z), (y,z): (-,-) (+,-) (-,+) (+,+)
-        S += w[7 * E] * Wn[nb3(G, i, j, k, -1, -1, 0)] + w[8 * E] * Wn[nb3(G, i, j, k, 1, -1, 0)] +
-             w[9 * E] * Wn[nb3(G, i, j, k, -1, 1, 0)] + w[10 * E] * Wn[nb3(G, i, j, k, 1, 1, 0)];
-        S += w[11 * E] * Wn[nb3(G, i, j, k, -1, 0, -1)] + w[12 * E] * Wn[nb3(G, i, j, k, 1, 0, -1)] +
-             w[13 * E] * Wn[nb3(G, i, j, k, -1, 0, 1)] + w[14 * E] * Wn[nb3(G, i, j, k, 1, 0, 1)];
-        S += w[15 * E] * Wn[nb3(G, i, j, k, 0, -1, -1)] + w[16 * E] * Wn[nb3(G, i, j, k, 0, 1, -1)] +
-             w[17 * E] * Wn[nb3(G, i, j, k, 0, -1, 1)] + w[18 * E] * Wn[nb3(G, i, j, k, 0, 1, 1)];
+        S += w[7 * E] * Wn[q + oxm + oym] + w[8 * E] * Wn[q + oxp + oym] +
+             w[9 * E] * Wn[q + oxm + oyp] + w[10 * E] * Wn[q + oxp + oyp];
+        S += w[11 * E] * Wn[q + oxm + ozm] + w[12 * E] * Wn[q + oxp + ozm] +
+             w[13 * E] * Wn[q + oxm + ozp] + w[14 * E] * Wn[q + oxp + ozp];
+        S += w[15 * E] * Wn[q + oym + ozm] + w[16 * E] * Wn[q + oyp + ozm] +
+             w[17 * E] * Wn[q + oym + ozp] + w[18 * E] * Wn[q + oyp + ozp];
       }
     }
     const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wprev[q] - fcn * fsT * F[q];
@@ -381,35 +390,80 @@ __global__ void __launch_bounds__(kTX *kTY, sizeof(T) == 4 ? 5 : 4) march3_kerne
   }
 }
 
+// cp.async (the asynchronous global -> shared copy): `bytes` (4 or 8) from src to the shared
+// address dst, or zeros when src_bytes is 0 (src is then not read); groups committed per
+// pipeline stage and awaited with wait_group.
+__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Temporally blocked FP32 march: K steps n -> n + K over one Unit3 per block, from the
 // levels n - 1 and n in the ring (2.5D overlapped tiling).  Thread (tx, ty) owns the column
 // (x, y) = (i0 - K + tx, j0 - K + ty) of the unit's box widened by a K-point halo and
-// streams it along axis 2: in iteration it it loads level n at plane p_0 = k0 - K + it and
+// streams it along axis 2: in iteration it it takes level n at plane p_0 = k0 - K + it and
 // computes level s at plane p_s = p_0 - s (s = 1..K), where level s exists on the box
 // shrunk by K - s points in every direction (columns further out carry the level below,
-// which no computed point reads).  Per level a register queue holds the planes p_s - 1,
-// p_s, p_s + 1 (the axis-2 neighbours) and a shared plane, double-buffered across
-// iterations, holds plane p_{s+1} of level s for the axis-0/1 neighbours, so one
-// __syncthreads per plane suffices.  Points that are not discretization points are
-// constant in time here (Dirichlet values and unused points); the unit's dilated box holds
-// no receiver and no rewritten ghost (checked on the host).  Own points accumulate their K
-// filter terms in registers (V read and written once) and write levels n + K - 1 and n + K
-// (every level with the export flag).  The update is step7f, as in march3_kernel.
+// which no computed point reads).
+//   Inputs arrive through a ring of kStages shared-memory planes filled by cp.async
+// kAhead iterations early: level n and FM at p_0, level n - 1 and (own columns) V at p_1.
+// FM is the FP32 forcing at discretization points and NaN elsewhere, so one array gives
+// both the forcing and the point class.  Level 0's axis-0/1 neighbours are read from the
+// previous stage's plane; levels 1..K-1 keep a double-buffered shared plane each, written
+// in one iteration and read in the next, so one __syncthreads per plane suffices.  Per
+// level a register queue holds the planes p - 1, p, p + 1 (the axis-2 neighbours).
+//   Points that are not discretization points are constant in time here (Dirichlet
+// values, unused points); the unit's dilated box holds no receiver and no rewritten ghost
+// (checked on the host).  Own points accumulate their K filter terms in registers (V read
+// and written once) and write levels n + K - 1 and n + K (every level with the export
+// flag).  The update is step7f, as in march3_kernel, so the results are the same bits.
+constexpr int kAhead = 2, kStages = kAhead + 2;
+template <int K>
+struct BlockSmem {
+  static constexpr int BX = kTX + 2 * K, BY = kUY + 2 * K, P = BX * BY;
+  float wn[kStages][P];   // level n at p_0 of the stage
+  float fm[kStages][P];   // FM at p_0
+  float wm[kStages][P];   // level n - 1 at p_1
+  double v[kStages][P];   // V at p_1 (own columns)
+  float lev[2][K > 1 ? K - 1 : 1][P];  // levels 1..K-1, double-buffered
+  float fc[K + 1];
+  double wf[K + 1];
+  int roff[K + 1];        // ring offset of level n + s (the ring has < 2^31 elements)
+};
+
+template <int K>
+size_t block_smem_bytes() { return sizeof(BlockSmem<K>); }
+
 template <int K>
 __global__ void __launch_bounds__((kTX + 2 * K) * (kUY + 2 * K), 1) march3_block_kernel(
-    const Grid3Dev *__restrict__ grids, const Unit3 *__restrict__ units,
-    const int8_t *__restrict__ mask, float *ring, int64_t stride, int L,
-    const float *__restrict__ F, double *__restrict__ V, Tab3 tab, int n, float fs) {
-  constexpr int BX = kTX + 2 * K, BY = kUY + 2 * K;
-  __shared__ float sm[2][K][BY][BX];
-  __shared__ float s_fc[K + 1];
-  __shared__ double s_wf[K + 1];
+    const Grid3Dev *__restrict__ grids, const Unit3 *__restrict__ units, float *ring,
+    int64_t stride, int L, const float *__restrict__ FM, double *__restrict__ V, Tab3 tab,
+    int n, float fs) {
+  using SM = BlockSmem<K>;
+  constexpr int BX = SM::BX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &S = *reinterpret_cast<SM *>(smem_raw);
   const Unit3 u = units[blockIdx.x];
   const Grid3Dev &G = grids[u.grid];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, to = ty * BX + tx;
   if (ty == 0 && tx >= 1 && tx <= K) {
-    s_fc[tx] = tab.fcf[n + tx - 1] * fs;  // forcing factor of the step to level n + tx
-    s_wf[tx] = tab.wf[n + tx];            // filter weight of level n + tx
+    S.fc[tx] = tab.fcf[n + tx - 1] * fs;  // forcing factor of the step to level n + tx
+    S.wf[tx] = tab.wf[n + tx];            // filter weight of level n + tx
+    S.roff[tx] = (int)(((n + tx) % L) * stride);
   }
   const int x = u.i0 - K + tx, y = u.j0 - K + ty;
   const int dxy = max(max(max(u.i0 - x, x - (u.i0 + kTX - 1)),
@@ -417,94 +471,114 @@ __global__ void __launch_bounds__((kTX + 2 * K) * (kUY + 2 * K), 1) march3_block
   const bool col_ok = x >= -G.g0 && x < G.n0 + G.g0 && y >= -G.g1 && y < G.n1 + G.g1;
   const bool own = dxy == 0 && x < G.n0 && y < G.n1;
   const bool exp_all = (u.flags & 1) != 0;
-  const int64_t pl = (int64_t)G.e0 * G.e1;
+  // bit s: level s exists in this column (the box shrunk by K - s points)
+  unsigned actb = 0u;
+#pragma unroll
+  for (int s = 1; s <= K; ++s) actb |= (dxy <= K - s ? 1u : 0u) << s;
+  // 32-bit element indices: the host enables blocking only when the whole ring has fewer
+  // than 2^31 elements
+  const int pl = G.e0 * G.e1;
   // element (x, y, z) of the grid's extended array is at col + z * pl
-  const int64_t col = G.base + ((int64_t)G.g2 * G.e1 + (y + G.g1)) * G.e0 + (x + G.g0);
+  const int col = (int)G.base + (G.g2 * G.e1 + (y + G.g1)) * G.e0 + (x + G.g0);
+  const int gbase = (int)G.base;
   const float c0 = G.cwf[0], c1 = G.cwf[1], c2 = G.cwf[2], c3 = G.cwf[3];
   const float *Wn = ring + (int64_t)(n % L) * stride;
   const float *Wm = ring + (int64_t)((n - 1) % L) * stride;
-  const int zlo = -G.g2, zhi = G.n2 + G.g2;     // extended planes
-  const int klo = u.k0, khi = u.k0 + u.nz;      // the unit's own planes
+  const int zlo = -G.g2, zhi = G.n2 + G.g2;  // extended planes
+  const int nz = u.nz, iters = nz + 2 * K;
+  // stage `it`: level n and FM at p_0, level n - 1 and V at p_1 (zeros outside the array)
+  int isl = 0;                                   // stage slot of the next issue
+  int iq0 = col + (u.k0 - K) * pl;  // element at the next issue's p_0
+  int ip0 = u.k0 - K;
+  auto issue = [&]() {
+    const int p0 = ip0, p1 = p0 - 1;
+    const bool z0 = col_ok && p0 >= zlo && p0 < zhi;
+    const bool z1 = col_ok && dxy < K && p1 >= zlo && p1 < zhi;
+    const int q0 = z0 ? iq0 : gbase, q1 = z1 ? iq0 - pl : gbase;
+    cp_async(&S.wn[isl][to], Wn + q0, 4, z0 ? 4 : 0);
+    cp_async(&S.fm[isl][to], FM + q0, 4, z0 ? 4 : 0);
+    cp_async(&S.wm[isl][to], Wm + q1, 4, z1 ? 4 : 0);
+    const bool v1 = own && p1 >= u.k0 && p1 < u.k0 + nz;
+    cp_async(&S.v[isl][to], V + (v1 ? q1 : gbase), 8, v1 ? 8 : 0);
+    isl = isl + 1 == kStages ? 0 : isl + 1;
+    iq0 += pl;
+    ++ip0;
+  };
+#pragma unroll
+  for (int a = 0; a < kAhead; ++a) {
+    if (a < iters) issue();
+    cp_async_commit();
+  }
   float q[K][3];
-  float fq[K];
+  float fq[K + 1];
   double acc[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     q[j][0] = q[j][1] = q[j][2] = 0.0f;
-    fq[j] = 0.0f;
     acc[j] = 0.0;
   }
+#pragma unroll
+  for (int j = 0; j <= K; ++j) fq[j] = 0.0f;
   unsigned mbits = 0u;
-  // loads of iteration it (prefetched one iteration ahead): level n at p_0, the mask at
-  // p_0, level n - 1 and F at p_1 = p_0 - 1, and V at p_1 for own points
-  auto load = [&](int it, float &w0, int &m0, float &wm1, float &f1) {
-    const int p0 = u.k0 - K + it, p1 = p0 - 1;
-    w0 = 0.0f;
-    m0 = 0;
-    wm1 = 0.0f;
-    f1 = 0.0f;
-    if (col_ok && p0 >= zlo && p0 < zhi) {
-      w0 = Wn[col + p0 * pl];
-      m0 = mask[col + p0 * pl] == kDisc;
-    }
-    if (col_ok && dxy < K && p1 >= zlo && p1 < zhi) {
-      wm1 = Wm[col + p1 * pl];
-      f1 = F[col + p1 * pl];
-    }
-  };
-  float nw0, nwm1, nf1;
-  int nm0;
-  load(0, nw0, nm0, nwm1, nf1);
-  __syncthreads();  // s_fc, s_wf
-  const int iters = u.nz + 2 * K;
+  int sl = 0, sp = kStages - 1;  // stage slots of this iteration and the previous one
+  int cur = 0;                   // level buffer written this iteration
+  int qz = col + (u.k0 - K) * pl;  // element at p_0
+  int p0 = u.k0 - K;
   for (int it = 0; it < iters; ++it) {
-    const float w0 = nw0, wm1 = nwm1, f1 = nf1;
-    const int m0 = nm0;
-    if (it + 1 < iters) load(it + 1, nw0, nm0, nwm1, nf1);
-    const int p0 = u.k0 - K + it;
+    cp_async_wait<kAhead - 1>();  // this thread's copies of stage it have landed
+    __syncthreads();              // everyone's; and last iteration's shared reads are done
+    if (it + kAhead < iters) issue();
+    cp_async_commit();
+    const bool z0 = col_ok && p0 >= zlo && p0 < zhi;
+    const float w0 = S.wn[sl][to], fm = S.fm[sl][to];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       q[j][0] = q[j][1];
       q[j][1] = q[j][2];
     }
 #pragma unroll
-    for (int j = K - 1; j >= 1; --j) {
-      fq[j] = fq[j - 1];
-      acc[j] = acc[j - 1];
-    }
-    fq[0] = f1;
-    mbits = (mbits << 1) | (unsigned)m0;
-    {
-      const int p1 = p0 - 1;
-      acc[0] = (own && (mbits & 2u) && p1 >= klo && p1 < khi) ? V[col + p1 * pl] : 0.0;
-    }
-    const int cur = it & 1, prv = cur ^ 1;
+    for (int j = K; j >= 1; --j) fq[j] = fq[j - 1];
+#pragma unroll
+    for (int j = K - 1; j >= 1; --j) acc[j] = acc[j - 1];
+    fq[0] = fm;
+    mbits = (mbits << 1) | ((z0 && !isnan(fm)) ? 1u : 0u);
+    // own planes: level s is at plane p_0 - s, own when it - K - s is in [0, nz)
+    acc[0] = (own && (mbits & 2u) && (unsigned)(it - K - 1) < (unsigned)nz) ? S.v[sl][to] : 0.0;
     q[0][2] = w0;
-    sm[cur][0][ty][tx] = w0;
+    const unsigned lv = mbits & actb;
+    const float *lprv = &S.lev[cur ^ 1][0][0];
+    float *lcur = &S.lev[cur][0][0];
 #pragma unroll
     for (int s = 1; s <= K; ++s) {
-      const int ps = p0 - s;
-      const bool disc = (mbits >> s) & 1u;
       float out = q[s - 1][1];
-      if (disc && it >= 2 * s && dxy <= K - s) {
-        const float xm = sm[prv][s - 1][ty][tx - 1], xp = sm[prv][s - 1][ty][tx + 1];
-        const float ym = sm[prv][s - 1][ty - 1][tx], yp = sm[prv][s - 1][ty + 1][tx];
-        const float wo = s == 1 ? wm1 : q[s - 2 < 0 ? 0 : s - 2][0];
+      if ((lv >> s) & 1u) {
+        // neighbours along axes 0 and 1 of level s - 1 at plane p_s: level 0 from the
+        // previous stage's plane, higher levels from last iteration's level buffer
+        const float *pl_prev = s == 1 ? &S.wn[sp][0] : lprv + (s >= 2 ? s - 2 : 0) * SM::P;
+        const float xm = pl_prev[to - 1], xp = pl_prev[to + 1];
+        const float ym = pl_prev[to - BX], yp = pl_prev[to + BX];
+        const float wo = s == 1 ? S.wm[sl][to] : q[s >= 2 ? s - 2 : 0][0];
         out = step7f(c0, c1, c2, c3, q[s - 1][1], __fadd_rn(xm, xp), __fadd_rn(ym, yp),
-                     __fadd_rn(q[s - 1][0], q[s - 1][2]), wo, s_fc[s], fq[s - 1]);
+                     __fadd_rn(q[s - 1][0], q[s - 1][2]), wo, S.fc[s], fq[s]);
+        if (own && (unsigned)(it - K - s) < (unsigned)nz) {
+          const int qs = qz - s * pl;
+          acc[s - 1] = fma(S.wf[s], wh::to_f64(out), acc[s - 1]);
+          if (exp_all || s >= K - 1) ring[S.roff[s] + qs] = out;
+          if (s == K) V[qs] = acc[K - 1];
+        }
       }
       if (s < K) {
         q[s < K ? s : 0][2] = out;
-        sm[cur][s < K ? s : 0][ty][tx] = out;
-      }
-      if (own && disc && ps >= klo && ps < khi) {
-        acc[s - 1] = fma(s_wf[s], wh::to_f64(out), acc[s - 1]);
-        if (exp_all || s >= K - 1) ring[(int64_t)((n + s) % L) * stride + col + ps * pl] = out;
-        if (s == K) V[col + ps * pl] = acc[K - 1];
+        lcur[(s >= 1 && s < K ? s - 1 : 0) * SM::P + to] = out;
       }
     }
-    __syncthreads();
+    sp = sl;
+    sl = sl + 1 == kStages ? 0 : sl + 1;
+    cur ^= 1;
+    qz += pl;
+    ++p0;
   }
+  cp_async_wait<0>();
 }
 
 // Ghost rules and interpolation of one time level, one thread per receiver: the 27 donors
@@ -635,25 +709,44 @@ void launch_march3(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
 
 size_t march3_block_threads(int K) { return (size_t)(kTX + 2 * K) * (kUY + 2 * K); }
 
+template <int K>
+void launch_block_k(cudaStream_t s, int nunits, const Grid3Dev *grids, const Unit3 *units,
+                    float *ring, int64_t stride, int L, const float *FM, double *V, Tab3 tab,
+                    int n, float fs) {
+  static bool attr = false;  // opt in to more than 48 KiB of dynamic shared memory once
+  const size_t bytes = block_smem_bytes<K>();
+  if (!attr) {
+    cudaFuncSetAttribute(march3_block_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
+    attr = true;
+  }
+  march3_block_kernel<K><<<nunits, dim3(kTX + 2 * K, kUY + 2 * K), bytes, s>>>(
+      grids, units, ring, stride, L, FM, V, tab, n, fs);
+}
+
 void launch_march3_block(int K, cudaStream_t s, int nunits, const Grid3Dev *grids,
-                         const Unit3 *units, const int8_t *mask, float *ring, int64_t stride,
-                         int L, const float *F, double *V, Tab3 tab, int n, double fs) {
+                         const Unit3 *units, const float *FM, float *ring, int64_t stride,
+                         int L, double *V, Tab3 tab, int n, double fs) {
   if (nunits < 1) return;
   const float f = (float)fs;
   switch (K) {
-    case 2:
-      march3_block_kernel<2><<<nunits, dim3(kTX + 4, kUY + 4), 0, s>>>(
-          grids, units, mask, ring, stride, L, F, V, tab, n, f);
-      break;
-    case 3:
-      march3_block_kernel<3><<<nunits, dim3(kTX + 6, kUY + 6), 0, s>>>(
-          grids, units, mask, ring, stride, L, F, V, tab, n, f);
-      break;
-    default:
-      march3_block_kernel<4><<<nunits, dim3(kTX + 8, kUY + 8), 0, s>>>(
-          grids, units, mask, ring, stride, L, F, V, tab, n, f);
-      break;
+    case 2: launch_block_k<2>(s, nunits, grids, units, ring, stride, L, FM, V, tab, n, f); break;
+    case 3: launch_block_k<3>(s, nunits, grids, units, ring, stride, L, FM, V, tab, n, f); break;
+    default: launch_block_k<4>(s, nunits, grids, units, ring, stride, L, FM, V, tab, n, f); break;
   }
+}
+
+// FM = the FP32 forcing at discretization points, NaN elsewhere (the blocked march's input).
+__global__ void forcing_mask_kernel(const float *__restrict__ F, const int8_t *__restrict__ mask,
+                                    float *__restrict__ FM, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    FM[t] = mask[t] == kDisc ? F[t] : __int_as_float(0x7fc00000);
+}
+
+void launch_forcing_mask(cudaStream_t s, const float *F, const int8_t *mask, float *FM,
+                         int64_t n) {
+  forcing_mask_kernel<<<blocks_for(n, 256), 256, 0, s>>>(F, mask, FM, n);
 }
 
 void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
