@@ -318,6 +318,58 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
  * at solve time a batch). */
 wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2);
 
+/* Deflation set as an orthonormal basis Q of an S-invariant subspace (S = W_h(., 0)) with
+ * its Rayleigh matrix T = Q^T S Q, as wh_eigs returns them.  wh_solve then deflates with
+ * P = I - Q Q^T like wh_set_deflation's set and inflates exactly: the Helmholtz solution is
+ * U = v + Q c with (I - T) c = Q^T W_h(v, f) (from U = S U + b, Sec. 4.3, projected on Q;
+ * one extra FP64 wave solve).  Algorithm 3's inflation with (f, phi_m) / (omega^2 -
+ * lambda_m^2) is exact only for self-adjoint discretizations; this one also holds on
+ * overset grids, where interpolation makes the discrete operator non-symmetric (on a
+ * nearly resonant overset disk: 8e-11 against the direct solve, where the printed formula
+ * was off by 42%).  The paper has no counterpart of this form.  Q: DEVICE, k compact
+ * vectors (row m at Q + m * n_total), kept by pointer like wh_set_deflation's; T: HOST,
+ * k x k row-major, copied.  Errors: WH_ERR_ARG (k outside [1, 4000], null or non-finite
+ * input; at solve time I - T singular), WH_ERR_STATE (3D context).  wh_set_deflation with
+ * k = 0 removes either kind of set. */
+wh_status wh_set_deflation_basis(wh_ctx *ctx, int32_t k, const double *Q, const double *T);
+
+/* Eigenpairs for the deflation set on the GPU (Sec. 4.4; the paper calls SLEPc's
+ * Krylov-Schur method on the spatial pencil and notes that WaveHoltz itself can provide
+ * them): a Krylov-Schur-style iteration (Arnoldi with classical Gram-Schmidt twice, thick
+ * restarts that keep the Schur-like basis of the wanted Ritz values) on the zero-forcing map
+ * S with the FP64 march.  S has the eigenvectors of the constrained spatial operator with
+ * eigenvalues beta_d(lambda~) (Theorem FullyDiscreteExplicitWaveHoltzConvergenceRate), so
+ * its k eigenvalues of largest modulus are the k modes the fixed-point iteration reduces
+ * most slowly.  With passes = 2 a second run on (I - Q1 Q1^T) S (I - Q1 Q1^T) from another
+ * start vector finds the copies of repeated eigenvalues that one Krylov sequence misses
+ * (symmetric geometries), and the k largest of the union are kept (k more products for the
+ * coupling block Q1^T S Q2).
+ *   k      eigenpairs wanted; m: basis size (0 = max(2k + 10, k + 20), at most 2048);
+ *   tol    relative residual ||S y - beta y|| <= tol |beta| of every wanted Ritz pair;
+ *   max_products  wave solves allowed (all passes);  seed: start vectors (splitmix64).
+ * Outputs: Q (DEVICE, k compact vectors, row i at Q + i * n_total): an orthonormal basis of
+ * the invariant subspace of the k eigenvalues, in decreasing |beta| (for a self-adjoint
+ * discretization, the eigenvectors themselves); T (HOST k x k row-major, may be NULL):
+ * Q^T S Q (for wh_set_deflation_basis); beta (HOST k): the eigenvalues, decreasing modulus;
+ * lambda2 (HOST k, may be NULL): lambda^2 = -(y, c^2 L_h y) / (y, y) over discretization
+ * points for each eigenvector y (ghost rules applied first; c^2 L_h y from one first step
+ * of the march), for wh_set_deflation.  stats (may be NULL): products, converged, the
+ * largest relative residual, seconds.  Two-dimensional single-instance contexts after
+ * wh_prepare.  Allocates its basis ((m + 1) + max(m, 2k) + 3k vectors) for the call.
+ * Errors: WH_ERR_ARG, WH_ERR_STATE; WH_ERR_NOT_CONVERGED when the products run out first
+ * (the outputs then hold the current approximations). */
+wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_products,
+                  int32_t passes, uint64_t seed, double *Q, double *T, double *beta,
+                  double *lambda2, wh_stats *stats);
+
+/* Testing aid for the host side of wh_eigs: eigenvalues w (2m: re, im) and unit
+ * eigenvectors V (may be NULL; 2 m^2: element (r, i), i the eigenvalue's index, at
+ * V[2 (r m + i)] re, +1 im) of the real m x m row-major matrix A, by Householder reduction
+ * to Hessenberg form and the shifted QR algorithm in complex arithmetic.  No device work.
+ * WH_ERR_ARG for m outside [1, 4096] or null pointers; WH_ERR_NOT_CONVERGED if the QR
+ * algorithm does not converge.  The paper has no counterpart. */
+wh_status wh_dense_eig(int32_t m, const double *A, double *w, double *V);
+
 /* Batched solve: one GMRES per instance (restart cycles of the same length), all advancing
  * in lockstep around one batched wave solve per Arnoldi step; an instance that reaches
  * ||b_k - A_k u_k|| <= tol ||b_k|| (checked with the FP64 march) is switched off in the

@@ -84,6 +84,32 @@ def deflated_gmres(orc, Phi, lam2, f, omega, tol=1e-12, restart=60, max_it=2000)
     return inflate(v, Phi, lam2, f, omega, disc_mask(orc.problem)), its, hist
 
 
+def rayleigh_matrix(orc, Q):
+    """T = Q S Q^T (T[i, j] = (q_i, S q_j)) for the rows q_i of Q, by one zero-forcing
+    WaveHoltz iteration per row."""
+    SQ = np.array([orc.iterate(q, False) for q in Q])
+    return Q @ SQ.T
+
+
+def schur_inflate(orc, v, Q, T):
+    """The Helmholtz solution from the deflated fixed point v, exactly, when the rows of Q
+    are an orthonormal basis of an S-invariant subspace with S Q^T = Q^T T: writing
+    U = v + Q^T c and U = S U + b (Sec. 4.3) and projecting on the rows of Q gives
+    (I - T) c = Q W_h(v, f).  On a self-adjoint discretization, with Q eigenvectors, this
+    equals Algorithm 3's inflation; on overset grids it does not need left eigenvectors."""
+    w = orc.iterate(v, True)
+    c = np.linalg.solve(np.eye(len(Q)) - T, Q @ w)
+    return v + Q.T @ c
+
+
+def deflated_gmres_schur(orc, Q, T, tol=1e-12, restart=60, max_it=3000):
+    """GMRES on the deflated fixed-point iteration (projector I - Q^T Q), then the exact
+    inflation of schur_inflate.  Returns (u, products, history)."""
+    from .oracle import gmres
+    v, its, hist = gmres(_Deflated(orc, Q), tol=tol, restart=restart, max_it=max_it)
+    return schur_inflate(orc, v, Q, T), its, hist
+
+
 def wave_eigenpairs(orc, k, tol=1e-12, seed=0, passes=2):
     """The k eigenpairs of the zero-forcing WaveHoltz map S = W_h(., 0) of largest |beta|
     (the modes the fixed-point iteration reduces most slowly), by ARPACK (implicitly

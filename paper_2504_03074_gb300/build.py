@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwaveholtz.so")
-SOURCES = ["wh_kernels.cu", "wh_api.cu", "wh_noalloc.cu", "wh_kernels3.cu", "wh_api3.cu"]
+SOURCES = ["wh_kernels.cu", "wh_api.cu", "wh_noalloc.cu", "wh_kernels3.cu", "wh_api3.cu",
+           "wh_dense.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]
@@ -41,7 +42,7 @@ def build(force=False, verbose=False):
     tag = f"{os.getpid()}"
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}.o"))
+        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + f".{tag}.o")
         cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

@@ -61,6 +61,10 @@ struct wh_ctx {
   std::vector<double> defl_lam2;
   double *d_fcompact = nullptr;
   bool defl_on = false;  // apply_A projects the set out of W_h(x, 0) (deflated GMRES)
+  // the set as an S-invariant basis with its Rayleigh matrix T = Q^T S Q (row-major k x k):
+  // the inflation is then exact, u = v + Q (I - T)^{-1} Q^T W_h(v, f)
+  bool defl_basis = false;
+  std::vector<double> defl_T;
   wh3::Ctx3 *c3 = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -1744,6 +1748,299 @@ wh_status apply_adjoint(wh_ctx *ctx, const double *x, double *y) {
 // =====================================================================================
 // C ABI
 // =====================================================================================
+namespace {
+
+// ---- eigenpairs of S for deflation (Sec. 4.4, Algorithm 3's deflation set) ----
+//
+// The paper computes the deflation set with a Krylov-Schur method (SLEPc) on the spatial
+// pencil and notes that WaveHoltz itself can yield the eigenpairs.  Here a Krylov-Schur-
+// style Arnoldi iteration runs on the zero-forcing map S = W_h(., 0) on the GPU: its
+// eigenvectors are those of the constrained spatial operator (S is a polynomial of the
+// one-step map) and its largest |beta| are exactly the slowest modes of the fixed-point
+// iteration.  Products are library iterations; the basis lives in device memory; only the
+// small projected matrices are on the host.
+
+// splitmix64 (Steele, Lea and Flood, 2014): a counter-based generator for the start vectors.
+uint64_t splitmix64(uint64_t &x) {
+  x += 0x9E3779B97F4A7C15ull;
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Orthonormalise the p columns of the column-major m x p matrix Z (modified Gram-Schmidt,
+// twice); columns that vanish are dropped.  Returns the number kept.
+int orthonormalize(int m, int p, std::vector<double> &Z) {
+  int kept = 0;
+  for (int c = 0; c < p; ++c) {
+    double *z = &Z[(size_t)c * m];
+    double n0 = 0.0;
+    for (int r = 0; r < m; ++r) n0 += z[r] * z[r];
+    n0 = std::sqrt(n0);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int d = 0; d < kept; ++d) {
+        const double *q = &Z[(size_t)d * m];
+        double h = 0.0;
+        for (int r = 0; r < m; ++r) h += q[r] * z[r];
+        for (int r = 0; r < m; ++r) z[r] -= h * q[r];
+      }
+    double nn = 0.0;
+    for (int r = 0; r < m; ++r) nn += z[r] * z[r];
+    nn = std::sqrt(nn);
+    if (!(nn > 1e-10 * n0) || !(nn > 0)) continue;
+    double *dst = &Z[(size_t)kept * m];
+    for (int r = 0; r < m; ++r) dst[r] = z[r] / nn;
+    ++kept;
+  }
+  return kept;
+}
+
+// The real basis of the `want` eigenvalues of largest modulus of the m x m matrix A
+// (row-major): their eigenvectors (real parts; a complex conjugate pair contributes its real
+// and imaginary parts), in decreasing modulus, as columns of Z (column-major m x p).  order,
+// w, Y receive the full eigen-decomposition.  Returns p (want, or want + 1 when the cut
+// falls inside a complex pair), or -1 if the QR algorithm failed.
+struct SmallEig {
+  std::vector<std::complex<double>> w, Y;
+  std::vector<int> order;
+};
+int real_basis(int m, const std::vector<double> &A, int want, SmallEig &E, std::vector<double> &Z,
+               bool split_pairs) {
+  if (!dense_eig(m, A.data(), E.w, E.Y)) return -1;
+  E.order.resize(m);
+  for (int i = 0; i < m; ++i) E.order[i] = i;
+  std::stable_sort(E.order.begin(), E.order.end(),
+                   [&](int a, int b) { return std::abs(E.w[a]) > std::abs(E.w[b]); });
+  Z.assign((size_t)m * (want + 1), 0.0);
+  int p = 0;
+  for (int t = 0; t < m && p < want; ++t) {
+    const int i = E.order[t];
+    const std::complex<double> th = E.w[i];
+    const bool cplx = std::fabs(th.imag()) > 1e-8 * std::abs(th);
+    if (cplx && th.imag() < 0) continue;  // the pair is taken at its + member
+    // rotate the eigenvector so that its largest entry is real and positive
+    int rmax = 0;
+    for (int r = 1; r < m; ++r)
+      if (std::abs(E.Y[(size_t)r * m + i]) > std::abs(E.Y[(size_t)rmax * m + i])) rmax = r;
+    const std::complex<double> ph = std::abs(E.Y[(size_t)rmax * m + i]) > 0
+                                        ? std::conj(E.Y[(size_t)rmax * m + i]) /
+                                              std::abs(E.Y[(size_t)rmax * m + i])
+                                        : 1.0;
+    for (int r = 0; r < m; ++r) Z[(size_t)p * m + r] = (E.Y[(size_t)r * m + i] * ph).real();
+    ++p;
+    if (cplx && (p < want || !split_pairs)) {
+      for (int r = 0; r < m; ++r) Z[(size_t)p * m + r] = (E.Y[(size_t)r * m + i] * ph).imag();
+      ++p;
+    }
+  }
+  return p;
+}
+
+// T = Z^T A Z (A row-major m x m, Z column-major m x p, T row-major p x p).
+std::vector<double> project(int m, const std::vector<double> &A, int p, const std::vector<double> &Z) {
+  std::vector<double> AZ((size_t)m * p, 0.0), T((size_t)p * p, 0.0);
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < p; ++c) {
+      double t = 0.0;
+      for (int l = 0; l < m; ++l) t += A[(size_t)r * m + l] * Z[(size_t)c * m + l];
+      AZ[(size_t)c * m + r] = t;
+    }
+  for (int a = 0; a < p; ++a)
+    for (int c = 0; c < p; ++c) {
+      double t = 0.0;
+      for (int r = 0; r < m; ++r) t += Z[(size_t)a * m + r] * AZ[(size_t)c * m + r];
+      T[(size_t)a * p + c] = t;
+    }
+  return T;
+}
+
+// y = P x (P = I - L L^T over the nl locked vectors L, orthonormal), in place
+wh_status eig_project(wh_ctx *ctx, const double *Lk, int nl, double *x) {
+  if (nl == 0) return WH_OK;
+  const int64_t n = ctx->ncompact;
+  wh_status st = multidot(ctx, Lk, n, nl, x, n, nullptr);
+  if (st) return st;
+  launch_multi_axpy(grid1d(n), ctx->stream, Lk, n, nl, ctx->d_red, x, n);
+  return WH_OK;
+}
+
+struct EigPass {
+  int k = 0;                // Schur vectors delivered
+  std::vector<double> T;    // k x k row-major, T = Q^T S Q
+  std::vector<std::complex<double>> theta;  // eigenvalues of T (the Ritz values)
+  double maxres = 0.0;      // largest relative residual of the wanted Ritz pairs
+  bool converged = false;
+};
+
+// One Krylov-Schur run on P S P (P = I - L L^T, or S alone when nl = 0): the orthonormal
+// basis Q (k vectors into Qout, stride n) of the invariant subspace of the k eigenvalues of
+// largest modulus, and T = Q^T S Q.  V: m + 1 basis vectors; W: m scratch vectors.
+wh_status eig_pass(wh_ctx *ctx, int k, int m, double tol, int budget, uint64_t seed,
+                   const double *Lk, int nl, double *V, double *W, double *Qout, EigPass &R,
+                   int &products) {
+  const int64_t n = ctx->ncompact;
+  cudaStream_t s = ctx->stream;
+  wh_status st;
+  if ((st = ensure_red(ctx, std::max(m + 1, nl)))) return st;
+  // start: uniform in (-1, 1) at discretization points (S ignores the others' values)
+  {
+    std::vector<double> v0((size_t)n, 0.0);
+    uint64_t x = seed;
+    int64_t o = 0;
+    for (const auto &H : ctx->grids) {
+      const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
+      for (int64_t q = 0; q < np; ++q) {
+        const double r = (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0);
+        if (H.mask[q] == WH_DISC) v0[o + q] = 2.0 * r - 1.0;
+      }
+      o += np;
+    }
+    CK(cudaMemcpy(V, v0.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if ((st = eig_project(ctx, Lk, nl, V))) return st;
+  double nn;
+  if ((st = multidot(ctx, V, 0, 1, V, n, &nn))) return st;
+  if (!(nn > 0)) return fail(ctx, WH_ERR_STATE, "wh_eigs: no discretization point to start from");
+  launch_axpby(grid1d(n), s, 0.0, V, 1.0 / std::sqrt(nn), V, n);
+  // H: (m + 1) x m, row-major with row stride m
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), h(m + 1);
+  int p = 0;
+  SmallEig E;
+  std::vector<double> Z, Hm((size_t)m * m), Zd;
+  double *dZ = nullptr;
+  if ((st = dalloc(ctx, &dZ, (size_t)m * m))) return st;
+  struct FreeZ {
+    wh_ctx *c;
+    double **p;
+    ~FreeZ() { dfree(c, p); }
+  } free_z{ctx, &dZ};
+  int mm = m;  // basis size reached (smaller after an invariant-subspace breakdown)
+  while (true) {
+    mm = m;
+    for (int j = p; j < m; ++j) {
+      double *vj = V + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
+      if (budget - products <= 0) {
+        mm = j;
+        break;
+      }
+      if ((st = iterate_device(ctx, 0, vj, w))) return st;
+      ++products;
+      if ((st = eig_project(ctx, Lk, nl, w))) return st;
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((st = multidot(ctx, V, n, j + 1, w, n, h.data()))) return st;
+        launch_multi_axpy(grid1d(n), s, V, n, j + 1, ctx->d_red, w, n);
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
+      }
+      double ww;
+      if ((st = multidot(ctx, w, 0, 1, w, n, &ww))) return st;
+      const double hn = std::sqrt(ww);
+      if (!std::isfinite(hn)) return fail(ctx, WH_ERR_DIVERGED, "wh_eigs: product not finite");
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn <= 1e-14) {  // invariant subspace: the basis cannot grow
+        mm = j + 1;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        break;
+      }
+      launch_axpby(grid1d(n), s, 0.0, w, 1.0 / hn, w, n);
+    }
+    if (mm < std::min(k, m)) return fail(ctx, WH_ERR_NOT_CONVERGED, "wh_eigs: product budget too small for the basis");
+    // the projected matrix and its eigenvalues
+    Hm.assign((size_t)mm * mm, 0.0);
+    for (int r = 0; r < mm; ++r)
+      for (int c = 0; c < mm; ++c) Hm[(size_t)r * mm + c] = H[(size_t)r * m + c];
+    const double hlast = mm < m + 1 && mm > 0 ? H[(size_t)mm * m + (mm - 1)] : 0.0;
+    const int keep_final = std::min(k, mm);
+    int pk = real_basis(mm, Hm, keep_final, E, Z, true);
+    if (pk < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
+    // residuals ||S y - theta y|| = |h_{m,m-1}| |y_{m-1}| of the wanted Ritz pairs
+    R.maxres = 0.0;
+    for (int t = 0; t < keep_final; ++t) {
+      const int i = E.order[t];
+      const double r = std::fabs(hlast) * std::abs(E.Y[(size_t)(mm - 1) * mm + i]);
+      R.maxres = std::max(R.maxres, r / std::max(std::abs(E.w[i]), 1e-300));
+    }
+    R.converged = R.maxres <= tol;
+    const bool out_of_budget = budget - products <= 0 || mm < m;
+    if (R.converged || out_of_budget) {
+      // deliver: orthonormal basis of the wanted eigenvectors' span, Q = V Z, T = Z^T H Z
+      pk = orthonormalize(mm, pk, Z);
+      Zd.assign((size_t)mm * pk, 0.0);
+      for (int c = 0; c < pk; ++c)
+        for (int r = 0; r < mm; ++r) Zd[(size_t)c * mm + r] = Z[(size_t)c * mm + r];
+      CK(cudaMemcpyAsync(dZ, Zd.data(), Zd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_gemm_tall(s, V, n, mm, dZ, pk, Qout, n, n);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(s));
+      R.k = pk;
+      R.T = project(mm, Hm, pk, Z);
+      std::vector<std::complex<double>> tw, tY;
+      dense_eig(pk, R.T.data(), tw, tY);
+      R.theta = tw;
+      return WH_OK;
+    }
+    // thick restart: keep the Schur-like basis of the pk2 Ritz values of largest modulus
+    const int pk2 = real_basis(mm, Hm, std::min(mm - 1, k + std::max(1, (m - k) / 2)), E, Z, false);
+    if (pk2 < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
+    const int pnew = orthonormalize(mm, pk2, Z);
+    std::vector<double> T = project(mm, Hm, pnew, Z);
+    Zd.assign((size_t)mm * pnew, 0.0);
+    for (int c = 0; c < pnew; ++c)
+      for (int r = 0; r < mm; ++r) Zd[(size_t)c * mm + r] = Z[(size_t)c * mm + r];
+    CK(cudaMemcpyAsync(dZ, Zd.data(), Zd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gemm_tall(s, V, n, mm, dZ, pnew, W, n, n);
+    CK(cudaMemcpyAsync(V, W, (size_t)pnew * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(V + (int64_t)pnew * n, V + (int64_t)mm * n, n * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    std::fill(H.begin(), H.end(), 0.0);
+    for (int r = 0; r < pnew; ++r)
+      for (int c = 0; c < pnew; ++c) H[(size_t)r * m + c] = T[(size_t)r * pnew + c];
+    for (int c = 0; c < pnew; ++c) H[(size_t)pnew * m + c] = hlast * Z[(size_t)c * mm + (mm - 1)];
+    p = pnew;
+    CK(cudaStreamSynchronize(s));  // Zd is reused
+  }
+}
+
+// lambda^2 of the eigenvector y (compact, device): -(y, c^2 L_h y) / (y, y) over
+// discretization points, with the ghost rules applied to y first (no interpolation).
+// c^2 L_h y comes from one first step of the FP64 march with zero forcing:
+// W^1 = y + dt^2/2 c^2 L_h y at discretization points.  Uses the FP64 set's two state
+// levels and the work vectors w0, w1.
+wh_status rayleigh_lam2(wh_ctx *ctx, const double *y, double *w0, double *w1, double *lam2) {
+  const int64_t n = ctx->ncompact;
+  cudaStream_t s = ctx->stream;
+  MarchSet &S0 = ctx->set[0];
+  const int order = ctx->opt.order;
+  const int ng = (int)ctx->hgrids.size();
+  const int64_t nb = (ctx->total + 255) / 256;
+  launch_init(false, (unsigned)nb, s, ctx->d_grids, ng, ctx->d_mask, y, S0.Wa, ctx->d_V,
+              ctx->total, ctx->d_inst);
+  const int nbc = (int)ctx->hbc.size();
+  if (nbc > 0) {
+    const int bcb = (nbc + 255) / 256;
+    launch_bc_gather(false, order, bcb, s, ctx->d_bc, nbc, bcb, ctx->d_didx, ctx->d_dw,
+                     ctx->d_ridx, ctx->d_rinst, 0, S0.Wa, S0.F, ctx->d_inst, 0, 0.0);
+  }
+  const int ntiles = (int)ctx->htiles.size();
+  launch_march(false, order, true, std::min(ntiles, S0.march_blocks), ntiles, s, ctx->d_grids,
+               ctx->d_tiles, ctx->d_mask, S0.Wa, S0.Wb, S0.F, S0.Wt, ctx->d_V, ctx->d_inst, 0,
+               0.0);
+  launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, (const double *)S0.Wa, w0, n, 1);
+  launch_ext_to_compact(s, ctx->d_grids, ng, ctx->d_mask, (const double *)S0.Wb, w1, n, 1);
+  launch_axpby(grid1d(n), s, -1.0, w0, 1.0, w1, n);  // w1 = W^1 - y at discretization points
+  CK(cudaGetLastError());
+  double d[2];
+  wh_status st = multidot(ctx, w0, n, 2, w0, n, d);  // (y, y), (W^1 - y, y)
+  if (st) return st;
+  const double dt = ctx->ti.dt;
+  *lam2 = -(2.0 / (dt * dt)) * d[1] / d[0];
+  return WH_OK;
+}
+
+}  // namespace
+
+
 extern "C" {
 
 wh_status wh_options_default(wh_options *opt) {
@@ -2279,7 +2576,7 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     if (ctx->ninst != 1) return finish(fail(ctx, WH_ERR_STATE, "deflation needs one instance"));
     const double om2 = ctx->ti.omega * ctx->ti.omega;
     for (double l2 : ctx->defl_lam2)
-      if (std::fabs(om2 - l2) <= kResonanceRel * om2)
+      if (!ctx->defl_basis && std::fabs(om2 - l2) <= kResonanceRel * om2)
         return finish(fail(ctx, WH_ERR_ARG,
                            "omega^2 = %.17g is within %g (relative) of a deflated eigenvalue "
                            "lambda^2 = %.17g",
@@ -2305,7 +2602,48 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
   auto inflate = [&]() -> wh_status {
     if (K == 0) return WH_OK;
     std::vector<double> c((size_t)K);
-    wh_status e = multidot(ctx, ctx->defl_phi, n, K, ctx->d_fcompact, n, c.data());
+    wh_status e;
+    if (ctx->defl_basis) {
+      // exact inflation: U = v + Q c with (I - T) c = Q^T W_h(v, f) (FP64 march)
+      const int keep = ctx->active;
+      use_set(ctx, 0);
+      e = iterate_device(ctx, 1, u, w0);
+      use_set(ctx, keep);
+      if (e) return e;
+      L.products[0] += 1;
+      if ((e = multidot(ctx, ctx->defl_phi, n, K, w0, n, c.data()))) return e;
+      std::vector<double> A((size_t)K * K);
+      for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) A[(size_t)i * K + j] = (i == j) - ctx->defl_T[(size_t)i * K + j];
+      // Gaussian elimination with partial pivoting on the small system
+      for (int col = 0; col < K; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < K; ++r)
+          if (std::fabs(A[(size_t)r * K + col]) > std::fabs(A[(size_t)piv * K + col])) piv = r;
+        if (!(std::fabs(A[(size_t)piv * K + col]) > 0))
+          return fail(ctx, WH_ERR_ARG, "deflation basis: I - T is singular (an eigenvalue 1)");
+        if (piv != col) {
+          for (int j = 0; j < K; ++j) std::swap(A[(size_t)col * K + j], A[(size_t)piv * K + j]);
+          std::swap(c[col], c[piv]);
+        }
+        for (int r = col + 1; r < K; ++r) {
+          const double f = A[(size_t)r * K + col] / A[(size_t)col * K + col];
+          for (int j = col; j < K; ++j) A[(size_t)r * K + j] -= f * A[(size_t)col * K + j];
+          c[r] -= f * c[col];
+        }
+      }
+      for (int r = K - 1; r >= 0; --r) {
+        double t = c[r];
+        for (int j = r + 1; j < K; ++j) t -= A[(size_t)r * K + j] * c[j];
+        c[r] = t / A[(size_t)r * K + r];
+      }
+      CK(cudaMemcpyAsync(ctx->d_red, c.data(), K * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_gemv_acc(grid1d(n), s, ctx->defl_phi, n, K, ctx->d_red, u, n);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(s));
+      return WH_OK;
+    }
+    e = multidot(ctx, ctx->defl_phi, n, K, ctx->d_fcompact, n, c.data());
     if (e) return e;
     const double om2 = ctx->ti.omega * ctx->ti.omega;
     for (int m = 0; m < K; ++m) c[m] /= om2 - ctx->defl_lam2[m];
@@ -2449,6 +2787,172 @@ wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const doub
   ctx->defl_k = k;
   ctx->defl_phi = k > 0 ? phi : nullptr;
   ctx->defl_lam2.assign(lambda2 ? lambda2 : nullptr, lambda2 ? lambda2 + k : nullptr);
+  ctx->defl_basis = false;
+  ctx->defl_T.clear();
+  return WH_OK;
+}
+
+wh_status wh_set_deflation_basis(wh_ctx *ctx, int32_t k, const double *Q, const double *T) {
+  if (!ctx) return WH_ERR_ARG;
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "deflation is not available on 3D contexts");
+  if (k < 1 || k > 4000) return fail(ctx, WH_ERR_ARG, "deflation basis size must be in [1, 4000]");
+  if (!Q || !T) return fail(ctx, WH_ERR_ARG, "null deflation arrays");
+  std::vector<double> A((size_t)k * k);
+  for (int64_t i = 0; i < (int64_t)k * k; ++i) {
+    if (!std::isfinite(T[i])) return fail(ctx, WH_ERR_ARG, "non-finite Rayleigh matrix");
+    A[i] = T[i];
+  }
+  ctx->defl_k = k;
+  ctx->defl_phi = Q;
+  ctx->defl_lam2.assign((size_t)k, 0.0);
+  ctx->defl_basis = true;
+  ctx->defl_T = std::move(A);
+  return WH_OK;
+}
+
+wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_products,
+                  int32_t passes, uint64_t seed, double *Q, double *T, double *beta,
+                  double *lambda2, wh_stats *stats) {
+  if (!ctx || !Q || !beta || k < 1 || !(tol > 0) || max_products < 1 || passes < 1 ||
+      passes > 2 || m < 0 || m > 2048)
+    return fail(ctx, WH_ERR_ARG, "bad wh_eigs arguments");
+  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "wh_eigs is available on 2D contexts");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  if (ctx->ninst != 1) return fail(ctx, WH_ERR_STATE, "wh_eigs needs one instance");
+  if (m == 0) m = std::min(2048, std::max(2 * k + 10, k + 20));
+  if (m < k + 2) return fail(ctx, WH_ERR_ARG, "basis size m must be at least k + 2");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = ctx->ncompact;
+  cudaStream_t s = ctx->stream;
+  ctx->launches = 0;
+  wh_status st;
+  // the FP64 march throughout; the deflation set is ignored while computing a new one
+  const int keep_set = ctx->active;
+  use_set(ctx, 0);
+  struct Restore {
+    wh_ctx *c;
+    int set;
+    ~Restore() { use_set(c, set); }
+  } restore{ctx, keep_set};
+  // workspace: basis V (m + 1), scratch W (max(m, 2k)), locked/merged L (2k), eigvecs Y (k)
+  const int nw = std::max(m, 2 * k);
+  double *V = nullptr, *Wk = nullptr, *Lk = nullptr, *Y = nullptr;
+  struct Bufs {
+    wh_ctx *c;
+    double **a, **b, **d, **e;
+    ~Bufs() { dfree(c, a); dfree(c, b); dfree(c, d); dfree(c, e); }
+  } bufs{ctx, &V, &Wk, &Lk, &Y};
+  if ((st = dalloc(ctx, &V, (size_t)(m + 1) * n)) || (st = dalloc(ctx, &Wk, (size_t)nw * n)) ||
+      (st = dalloc(ctx, &Lk, (size_t)2 * k * n)) || (st = dalloc(ctx, &Y, (size_t)k * n)))
+    return st;
+  if (!ctx->d_work && (st = dalloc(ctx, &ctx->d_work, kWorkVectors * (size_t)n))) return st;
+  int products = 0;
+  EigPass P1, P2;
+  if ((st = eig_pass(ctx, k, m, tol, max_products, seed, nullptr, 0, V, Wk, Lk, P1, products)))
+    return st;
+  int kb = P1.k;  // basis vectors in Lk: Schur vectors of pass 1, then pass 2
+  std::vector<double> TB = P1.T;
+  bool conv = P1.converged;
+  double maxres = P1.maxres;
+  if (passes == 2 && products < max_products) {
+    // a second Krylov sequence on P S P finds the copies of repeated eigenvalues the first
+    // one only meets through rounding; the union stays invariant (S Q2 = Q2 T2 + Q1 X)
+    if ((st = eig_pass(ctx, k, m, tol, max_products, seed ^ 0x5DEECE66Dull, Lk, kb, V, Wk,
+                       Lk + (int64_t)kb * n, P2, products)))
+      return st;
+    const int k2 = P2.k, kt = kb + k2;
+    // X = Q1^T S Q2 (k2 products)
+    std::vector<double> X((size_t)kb * k2), col((size_t)kb);
+    for (int j = 0; j < k2; ++j) {
+      if ((st = iterate_device(ctx, 0, Lk + (int64_t)(kb + j) * n, Wk))) return st;
+      ++products;
+      if ((st = multidot(ctx, Lk, n, kb, Wk, n, col.data()))) return st;
+      for (int i = 0; i < kb; ++i) X[(size_t)i * k2 + j] = col[i];
+    }
+    std::vector<double> TT((size_t)kt * kt, 0.0);
+    for (int i = 0; i < kb; ++i)
+      for (int j = 0; j < kb; ++j) TT[(size_t)i * kt + j] = P1.T[(size_t)i * kb + j];
+    for (int i = 0; i < kb; ++i)
+      for (int j = 0; j < k2; ++j) TT[(size_t)i * kt + kb + j] = X[(size_t)i * k2 + j];
+    for (int i = 0; i < k2; ++i)
+      for (int j = 0; j < k2; ++j) TT[(size_t)(kb + i) * kt + kb + j] = P2.T[(size_t)i * k2 + j];
+    TB = TT;
+    kb = kt;
+    conv = conv && P2.converged;
+    maxres = std::max(maxres, P2.maxres);
+  }
+  // the k eigenvalues of largest modulus of T_B, their eigenvectors in the basis, and an
+  // orthonormal basis of their span (Q) with its Rayleigh matrix
+  SmallEig E;
+  std::vector<double> Z;
+  const int kk = std::min(k, kb);
+  int pk = real_basis(kb, TB, kk, E, Z, true);
+  if (pk < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
+  std::vector<double> Zy(Z.begin(), Z.begin() + (size_t)kb * pk);  // eigenvectors (lambda^2)
+  const int pq = orthonormalize(kb, pk, Z);
+  std::vector<double> Tout = project(kb, TB, pq, Z);
+  double *dZ = nullptr;
+  struct FreeZ {
+    wh_ctx *c;
+    double **p;
+    ~FreeZ() { dfree(c, p); }
+  } fz{ctx, &dZ};
+  if ((st = dalloc(ctx, &dZ, (size_t)kb * std::max(pq, pk)))) return st;
+  CK(cudaMemcpy(dZ, Z.data(), (size_t)kb * pq * sizeof(double), cudaMemcpyHostToDevice));
+  launch_gemm_tall(s, Lk, n, kb, dZ, pq, Q, n, n);
+  CK(cudaMemcpy(dZ, Zy.data(), (size_t)kb * pk * sizeof(double), cudaMemcpyHostToDevice));
+  launch_gemm_tall(s, Lk, n, kb, dZ, pk, Y, n, n);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  // outputs (k entries; missing ones, when the basis came out smaller, are zero)
+  for (int i = 0; i < k; ++i) beta[i] = 0.0;
+  int t = 0;
+  for (int q = 0; q < kb && t < kk; ++q) {
+    const std::complex<double> th = E.w[E.order[q]];
+    if (std::fabs(th.imag()) > 1e-8 * std::abs(th) && th.imag() < 0) continue;
+    beta[t++] = th.real();
+    if (t < kk && std::fabs(th.imag()) > 1e-8 * std::abs(th)) beta[t++] = th.real();
+  }
+  if (T) {
+    for (int64_t i = 0; i < (int64_t)k * k; ++i) T[i] = 0.0;
+    for (int i = 0; i < pq && i < k; ++i)
+      for (int j = 0; j < pq && j < k; ++j) T[(size_t)i * k + j] = Tout[(size_t)i * pq + j];
+  }
+  if (lambda2) {
+    double *w0 = ctx->d_work, *w1 = ctx->d_work + n;
+    for (int i = 0; i < k; ++i) lambda2[i] = 0.0;
+    for (int i = 0; i < pk && i < k; ++i)
+      if ((st = rayleigh_lam2(ctx, Y + (int64_t)i * n, w0, w1, &lambda2[i]))) return st;
+  }
+  if (stats) {
+    wh_stats S{};
+    S.iterations = products;
+    S.products_fp64 = products;
+    S.converged = conv ? 1 : 0;
+    S.residual = maxres;
+    S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *stats = S;
+  }
+  if (pq < k) return fail(ctx, WH_ERR_NOT_CONVERGED, "wh_eigs: only %d basis vectors", pq);
+  if (!conv)
+    return fail(ctx, WH_ERR_NOT_CONVERGED, "wh_eigs: %d products, largest residual %g",
+                products, maxres);
+  return WH_OK;
+}
+
+wh_status wh_dense_eig(int32_t m, const double *A, double *w, double *V) {
+  if (m < 1 || m > 4096 || !A || !w) return WH_ERR_ARG;
+  std::vector<std::complex<double>> ew, EV;
+  if (!dense_eig(m, A, ew, EV)) return WH_ERR_NOT_CONVERGED;
+  for (int i = 0; i < m; ++i) {
+    w[2 * i] = ew[i].real();
+    w[2 * i + 1] = ew[i].imag();
+  }
+  if (V)
+    for (int64_t q = 0; q < (int64_t)m * m; ++q) {
+      V[2 * q] = EV[q].real();
+      V[2 * q + 1] = EV[q].imag();
+    }
   return WH_OK;
 }
 

@@ -4,6 +4,9 @@
 #include <cuda.h>  // CUtensorMap (type only; maps are encoded through the runtime entry point)
 #include <cuda_runtime.h>
 
+#include <complex>
+#include <vector>
+
 namespace wh {
 
 constexpr int kMaxOrder = 4;
@@ -218,6 +221,15 @@ void launch_sub(unsigned nb, cudaStream_t s, const double *x, const double *z, d
                 int64_t n);
 void launch_gemv_acc(unsigned nb, cudaStream_t s, const double *X, int64_t ldx, int nv,
                      const double *c, double *y, int64_t n);
+// Y_c = sum_{j < m} X_j Z[j + c m], c < p (tall basis times a small column-major matrix on
+// the device; m <= 2048; Y may not alias X)
+void launch_gemm_tall(cudaStream_t s, const double *X, int64_t ldx, int m, const double *Z,
+                      int p, double *Y, int64_t ldy, int64_t n);
+// Eigenvalues w (complex) and unit eigenvectors V (complex, column i for w[i], row-major
+// m x m) of the real m x m row-major matrix A (host, wh_dense.cpp); false if the QR
+// algorithm does not converge.
+bool dense_eig(int m, const double *A, std::vector<std::complex<double>> &w,
+               std::vector<std::complex<double>> &V);
 // y[i] = the filter's FP32 -> FP64 widening of x[i] (testing aid)
 void launch_widen(cudaStream_t s, const float *x, double *y, int64_t n);
 // FP64 FMA throughput probe (blocks x 256 threads, out: one double per thread); returns the

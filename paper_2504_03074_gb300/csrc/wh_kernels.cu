@@ -1743,6 +1743,53 @@ void launch_multi_axpy(unsigned nb, cudaStream_t s, const double *X, int64_t ldx
   multi_axpy<<<nb, 256, 0, s>>>(X, ldx, nv, h, y, n);
 }
 
+// Y_c = sum_j X_j Z[j + c m] for c < p: a tall basis (m vectors of n values, X_j at X + j ldx)
+// times a small m x p matrix (column-major, device).  One thread per row i, kGemmCols output
+// columns per block row (blockIdx.y picks the column chunk), that chunk of Z in shared
+// memory; X is read once per chunk, coalesced.  Y may not alias X.
+constexpr int kGemmCols = 8;
+__global__ void __launch_bounds__(256) gemm_tall_kernel(const double *__restrict__ X, int64_t ldx,
+                                                         int m, const double *__restrict__ Z,
+                                                         int p, double *__restrict__ Y,
+                                                         int64_t ldy, int64_t n) {
+  extern __shared__ double sz[];  // m x kGemmCols, row j = Z[j, c0 .. c0 + 7]
+  const int c0 = blockIdx.y * kGemmCols;
+  for (int t = threadIdx.x; t < m * kGemmCols; t += blockDim.x) {
+    const int j = t / kGemmCols, c = t % kGemmCols;
+    sz[t] = c0 + c < p ? Z[j + (int64_t)(c0 + c) * m] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc[kGemmCols];
+#pragma unroll
+    for (int c = 0; c < kGemmCols; ++c) acc[c] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double x = X[j * ldx + i];
+#pragma unroll
+      for (int c = 0; c < kGemmCols; ++c) acc[c] = fma(x, sz[j * kGemmCols + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kGemmCols; ++c)
+      if (c0 + c < p) Y[(c0 + c) * ldy + i] = acc[c];
+  }
+}
+
+void launch_gemm_tall(cudaStream_t s, const double *X, int64_t ldx, int m, const double *Z,
+                      int p, double *Y, int64_t ldy, int64_t n) {
+  if (m < 1 || p < 1 || n < 1) return;
+  static int attr_bytes = 0;
+  const int bytes = m * kGemmCols * (int)sizeof(double);
+  if (bytes > 48 * 1024 && bytes > attr_bytes) {
+    cudaFuncSetAttribute(gemm_tall_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr_bytes = bytes;
+  }
+  int64_t nb = (n + 255) / 256;
+  nb = nb > 152 * 8 ? 152 * 8 : nb;
+  const dim3 grid((unsigned)nb, (unsigned)((p + kGemmCols - 1) / kGemmCols));
+  gemm_tall_kernel<<<grid, 256, bytes, s>>>(X, ldx, m, Z, p, Y, ldy, n);
+}
+
 // out[i] = to_f64(x[i]): the filter's widening, run on its own for testing.
 __global__ void widen_kernel(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

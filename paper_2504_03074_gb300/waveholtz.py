@@ -97,7 +97,7 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
            "wh_set_interp3", "wh_set_deflation", "wh_widen_f32", "wh_probe_fp64",
-           "wh_get_tuning"]
+           "wh_get_tuning", "wh_set_deflation_basis", "wh_eigs", "wh_dense_eig"]
 
 
 def lib_path():
@@ -142,6 +142,10 @@ def lib():
     L.wh_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.wh_autotune.argtypes = [vp, C.c_int32, C.POINTER(Tuning)]
     L.wh_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.wh_set_deflation_basis.argtypes = [vp, C.c_int32, vp, vp]
+    L.wh_eigs.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                          C.c_uint64, vp, vp, vp, vp, C.POINTER(Stats)]
+    L.wh_dense_eig.argtypes = [C.c_int32, vp, vp, vp]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -173,6 +177,19 @@ def widen_f32(x, out, stream=None):
     if st != WH_OK:
         raise WHError(st, "wh_widen_f32 failed")
     return out
+
+
+def dense_eig(A):
+    """Eigenvalues and unit eigenvectors (columns) of a small real matrix by the library's
+    host routine (the one wh_eigs uses): (w, V) complex numpy arrays."""
+    A = np.ascontiguousarray(A, np.float64)
+    m = A.shape[0]
+    w = np.zeros(2 * m)
+    V = np.zeros(2 * m * m)
+    st = lib().wh_dense_eig(m, _ptr(A), _ptr(w), _ptr(V))
+    if st != WH_OK:
+        raise WHError(st, "wh_dense_eig failed")
+    return w[0::2] + 1j * w[1::2], (V[0::2] + 1j * V[1::2]).reshape(m, m)
 
 
 def _ptr(a):
@@ -356,6 +373,34 @@ class Solver:
         assert phi.is_cuda and phi.is_contiguous() and phi.shape[0] == lam.size
         self._check(self.L.wh_set_deflation(self.h, int(lam.size), _ptr(phi), _ptr(lam)))
         self._defl = (phi, lam)
+
+    def set_deflation_basis(self, Q, T):
+        """Deflation with an S-invariant orthonormal basis Q (contiguous float64 CUDA tensor
+        (k, n_total), kept by reference) and its Rayleigh matrix T = Q S Q^T (k x k host
+        array): the exact inflation of wh_set_deflation_basis."""
+        Tm = np.ascontiguousarray(T, np.float64)
+        assert Q.is_cuda and Q.is_contiguous() and Q.shape[0] == Tm.shape[0] == Tm.shape[1]
+        self._check(self.L.wh_set_deflation_basis(self.h, int(Q.shape[0]), _ptr(Q), _ptr(Tm)))
+        self._defl = (Q, Tm)
+
+    def eigs(self, k, m=0, tol=1e-10, max_products=5000, passes=2, seed=0):
+        """Deflation eigenpairs on the GPU (wh_eigs): returns (Q, T, beta, lambda2, stats);
+        Q a (k, n_total) CUDA tensor.  A run that ends at max_products returns with
+        stats.converged == 0 instead of raising."""
+        torch = self._torch
+        Q = torch.zeros((k, self.problem.n_total), dtype=torch.float64, device="cuda")
+        T = np.zeros((k, k))
+        beta = np.zeros(k)
+        lam2 = np.zeros(k)
+        st = Stats()
+        self._enter()
+        status = self.L.wh_eigs(self.h, k, m, tol, max_products, passes, seed, _ptr(Q), _ptr(T),
+                                _ptr(beta), _ptr(lam2), C.byref(st))
+        self._leave()
+        if status not in (WH_OK, -6):
+            self._check(status)
+        st.status = STATUS.get(status, status)
+        return Q, T, beta, lam2, st
 
     def solve_batch(self, u, tol=1e-8, max_it=500, restart=50):
         """Batched solve of every instance in place on device tensor u; list of Stats."""

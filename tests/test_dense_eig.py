@@ -1,0 +1,74 @@
+"""The host side of the GPU eigensolver (wh_eigs): the small dense eigenproblems of its
+projected matrices, by Householder reduction to Hessenberg form and the shifted QR
+algorithm, against numpy's LAPACK routine and the definition A v = w v (CPU only)."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2504_03074_gb300 import build
+    build.build()
+    from paper_2504_03074_gb300 import waveholtz
+    return waveholtz
+
+
+def _match(w, ref):
+    """Every computed eigenvalue matched to a distinct reference one (greedy)."""
+    ref = list(ref)
+    err = 0.0
+    for x in sorted(w, key=lambda z: (z.real, z.imag)):
+        j = int(np.argmin([abs(x - r) for r in ref]))
+        err = max(err, abs(x - ref[j]))
+        ref.pop(j)
+    return err
+
+
+@pytest.mark.parametrize("kind", ["general", "symmetric", "hessenberg", "rotation",
+                                  "repeated", "defective", "zero", "one"])
+def test_dense_eig_against_lapack_and_definition(W, kind):
+    rng = np.random.default_rng(3)
+    m = 40
+    if kind == "general":
+        A = rng.standard_normal((m, m))
+    elif kind == "symmetric":
+        B = rng.standard_normal((m, m))
+        A = B + B.T
+    elif kind == "hessenberg":  # the shape Arnoldi produces: decaying subdiagonal
+        A = np.triu(rng.standard_normal((m, m)), -1)
+        A[np.arange(1, m), np.arange(m - 1)] *= np.logspace(0, -6, m - 1)
+    elif kind == "rotation":  # complex pairs only
+        A = np.zeros((m, m))
+        for b in range(0, m, 2):
+            t = 0.1 * (b + 1)
+            A[b:b + 2, b:b + 2] = [[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]]
+        Qr, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        A = Qr @ A @ Qr.T
+    elif kind == "repeated":  # eigenvalue 2 four times, diagonalisable
+        d = np.concatenate([np.full(4, 2.0), rng.standard_normal(m - 4)])
+        Qr, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        A = Qr @ np.diag(d) @ Qr.T
+    elif kind == "defective":  # a Jordan block: eigenvalues converge only to sqrt(eps)
+        m = 6
+        A = np.eye(m) * 0.5 + np.diag(np.ones(m - 1), 1)
+    elif kind == "zero":
+        A = np.zeros((m, m))
+    else:
+        m = 1
+        A = np.array([[3.5]])
+    w, V = W.dense_eig(A)
+    ref = np.linalg.eigvals(A)
+    scale = max(1.0, np.max(np.abs(ref)))
+    tol = 1e-6 if kind == "defective" else 1e-10
+    assert _match(w, ref) <= tol * scale
+    res = np.abs(A @ V - V * w[None, :]).max()
+    assert res <= 1e-10 * scale
+    assert np.allclose(np.linalg.norm(V, axis=0), 1.0, atol=1e-12)
+
+
+def test_dense_eig_rejects_bad_arguments(W):
+    import ctypes as C
+    L = W.lib()
+    assert L.wh_dense_eig(0, None, None, None) == -1
+    A = np.eye(2)
+    assert L.wh_dense_eig(2, A.ctypes.data, None, None) == -1
