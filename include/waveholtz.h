@@ -369,6 +369,12 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
  * WH_ERR_ARG for m outside [1, 4096] or null pointers; WH_ERR_NOT_CONVERGED if the QR
  * algorithm does not converge.  The paper has no counterpart. */
 wh_status wh_dense_eig(int32_t m, const double *A, double *w, double *V);
+/* Testing aid, the same host routine's invariant subspace: a real orthonormal basis Q
+ * (column-major m x p, room for m x (want + 1)) of the invariant subspace of the `want`
+ * eigenvalues of largest modulus of A (row-major m x m; a complex pair is kept whole, so
+ * *p is want or want + 1), from the complex Schur form reordered by unitary swaps.  No
+ * device work.  WH_ERR_ARG on bad sizes or null pointers. */
+wh_status wh_dense_invariant(int32_t m, const double *A, int32_t want, double *Q, int32_t *p);
 
 /* Batched solve: one GMRES per instance (restart cycles of the same length), all advancing
  * in lockstep around one batched wave solve per Arnoldi step; an instance that reaches

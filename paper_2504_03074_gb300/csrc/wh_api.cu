@@ -1963,8 +1963,12 @@ wh_status eig_pass(wh_ctx *ctx, int k, int m, double tol, int budget, uint64_t s
     R.converged = R.maxres <= tol;
     const bool out_of_budget = budget - products <= 0 || mm < m;
     if (R.converged || out_of_budget) {
-      // deliver: orthonormal basis of the wanted eigenvectors' span, Q = V Z, T = Z^T H Z
-      pk = orthonormalize(mm, pk, Z);
+      // deliver: an orthonormal basis of the wanted eigenvalues' invariant subspace (from the
+      // reordered Schur form, stable also for nearly defective pairs), Q = V Z, T = Z^T H Z
+      std::vector<std::complex<double>> wsel;
+      pk = invariant_basis(mm, Hm.data(), keep_final, Z, wsel);
+      if (pk > k) pk = invariant_basis(mm, Hm.data(), keep_final - 1, Z, wsel);
+      if (pk < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
       Zd.assign((size_t)mm * pk, 0.0);
       for (int c = 0; c < pk; ++c)
         for (int r = 0; r < mm; ++r) Zd[(size_t)c * mm + r] = Z[(size_t)c * mm + r];
@@ -1979,10 +1983,12 @@ wh_status eig_pass(wh_ctx *ctx, int k, int m, double tol, int budget, uint64_t s
       R.theta = tw;
       return WH_OK;
     }
-    // thick restart: keep the Schur-like basis of the pk2 Ritz values of largest modulus
-    const int pk2 = real_basis(mm, Hm, std::min(mm - 1, k + std::max(1, (m - k) / 2)), E, Z, false);
-    if (pk2 < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
-    const int pnew = orthonormalize(mm, pk2, Z);
+    // thick restart: keep the Schur basis of the Ritz values of largest modulus (the
+    // invariant subspace of the small matrix, so S V Z = V Z T + v_{m+1} b^T holds exactly)
+    std::vector<std::complex<double>> wsel;
+    int pnew = invariant_basis(mm, Hm.data(), std::min(mm - 2, k + std::max(1, (m - k) / 2)),
+                               Z, wsel);
+    if (pnew < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
     std::vector<double> T = project(mm, Hm, pnew, Z);
     Zd.assign((size_t)mm * pnew, 0.0);
     for (int c = 0; c < pnew; ++c)
@@ -2889,7 +2895,10 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
   int pk = real_basis(kb, TB, kk, E, Z, true);
   if (pk < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
   std::vector<double> Zy(Z.begin(), Z.begin() + (size_t)kb * pk);  // eigenvectors (lambda^2)
-  const int pq = orthonormalize(kb, pk, Z);
+  std::vector<std::complex<double>> wsel;
+  int pq = invariant_basis(kb, TB.data(), kk, Z, wsel);
+  if (pq > k) pq = invariant_basis(kb, TB.data(), kk - 1, Z, wsel);
+  if (pq < 0) return fail(ctx, WH_ERR_CUDA, "wh_eigs: the small eigenproblem did not converge");
   std::vector<double> Tout = project(kb, TB, pq, Z);
   double *dZ = nullptr;
   struct FreeZ {
@@ -2937,6 +2946,17 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
   if (!conv)
     return fail(ctx, WH_ERR_NOT_CONVERGED, "wh_eigs: %d products, largest residual %g",
                 products, maxres);
+  return WH_OK;
+}
+
+wh_status wh_dense_invariant(int32_t m, const double *A, int32_t want, double *Q, int32_t *p) {
+  if (m < 1 || m > 4096 || !A || !Q || !p || want < 1 || want > m) return WH_ERR_ARG;
+  std::vector<double> Z;
+  std::vector<std::complex<double>> w;
+  const int q = invariant_basis(m, A, want, Z, w);
+  if (q < 0) return WH_ERR_NOT_CONVERGED;
+  std::copy(Z.begin(), Z.end(), Q);
+  *p = q;
   return WH_OK;
 }
 

@@ -161,7 +161,133 @@ bool schur(int m, std::vector<cd> &H, std::vector<cd> &Z) {
   return true;
 }
 
+// Swap the adjacent diagonal entries i, i+1 of the upper triangular T (complex Schur form)
+// by a unitary rotation, updating Z: the rotation's first column is the eigenvector of the
+// 2 x 2 block for its second eigenvalue.
+void schur_swap(int m, std::vector<cd> &T, std::vector<cd> &Z, int i) {
+  auto t = [&](int r, int c) -> cd & { return T[(size_t)r * m + c]; };
+  const cd a = t(i, i), b = t(i + 1, i + 1), c = t(i, i + 1);
+  cd x1 = c, x2 = b - a;
+  const double nx = std::sqrt(std::norm(x1) + std::norm(x2));
+  if (nx == 0.0) return;  // equal eigenvalues, nothing to swap
+  x1 /= nx;
+  x2 /= nx;
+  // T <- U^* T U with U = [[x1, -conj(x2)], [x2, conj(x1)]]
+  for (int j = i; j < m; ++j) {
+    const cd p = t(i, j), q = t(i + 1, j);
+    t(i, j) = std::conj(x1) * p + std::conj(x2) * q;
+    t(i + 1, j) = -x2 * p + x1 * q;
+  }
+  for (int r = 0; r <= i + 1; ++r) {
+    const cd p = t(r, i), q = t(r, i + 1);
+    t(r, i) = x1 * p + x2 * q;
+    t(r, i + 1) = -std::conj(x2) * p + std::conj(x1) * q;
+  }
+  for (int r = 0; r < m; ++r) {
+    const cd p = Z[(size_t)r * m + i], q = Z[(size_t)r * m + i + 1];
+    Z[(size_t)r * m + i] = x1 * p + x2 * q;
+    Z[(size_t)r * m + i + 1] = -std::conj(x2) * p + std::conj(x1) * q;
+  }
+  t(i + 1, i) = 0.0;
+}
+
 }  // namespace
+
+int invariant_basis(int m, const double *A, int want, std::vector<double> &Q,
+                    std::vector<std::complex<double>> &w) {
+  Q.clear();
+  w.clear();
+  if (m <= 0 || want <= 0) return 0;
+  want = std::min(want, m);
+  std::vector<double> H(A, A + (size_t)m * m), Qh;
+  hessenberg(m, H, Qh);
+  std::vector<cd> T(H.begin(), H.end()), Z(Qh.begin(), Qh.end());
+  if (!schur(m, T, Z)) return -1;
+  // the wanted eigenvalues: largest modulus, a complex pair kept whole
+  std::vector<int> idx(m);
+  for (int i = 0; i < m; ++i) idx[i] = i;
+  std::vector<cd> d(m);
+  for (int i = 0; i < m; ++i) d[i] = T[(size_t)i * m + i];
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return std::abs(d[a]) > std::abs(d[b]); });
+  std::vector<char> sel(m, 0);
+  int p = 0;
+  for (int t = 0; t < m && p < want; ++t) {
+    const int i = idx[t];
+    if (sel[i]) continue;
+    sel[i] = 1;
+    ++p;
+    if (std::fabs(d[i].imag()) > 1e-8 * std::abs(d[i])) {  // its conjugate too
+      int best = -1;
+      for (int j = 0; j < m; ++j)
+        if (!sel[j] && (best < 0 || std::abs(d[j] - std::conj(d[i])) < std::abs(d[best] - std::conj(d[i]))))
+          best = j;
+      if (best >= 0) {
+        sel[best] = 1;
+        ++p;
+      }
+    }
+  }
+  // bubble the selected eigenvalues to the leading positions
+  int slot = 0;
+  for (int i = 0; i < m; ++i) {
+    if (!sel[i]) continue;
+    for (int j = i; j > slot; --j) {
+      schur_swap(m, T, Z, j - 1);
+      std::swap(sel[j], sel[j - 1]);
+    }
+    ++slot;
+  }
+  for (int i = 0; i < p; ++i) w.push_back(T[(size_t)i * m + i]);
+  // a real orthonormal basis of span(Z[:, 0..p)): the leading p left singular vectors of
+  // [Re Z_p, Im Z_p], from the eigenvectors of its (symmetric) Gram matrix
+  const int q = 2 * p;
+  std::vector<double> B((size_t)m * q);
+  for (int c = 0; c < p; ++c)
+    for (int r = 0; r < m; ++r) {
+      B[(size_t)(2 * c) * m + r] = Z[(size_t)r * m + c].real();
+      B[(size_t)(2 * c + 1) * m + r] = Z[(size_t)r * m + c].imag();
+    }
+  std::vector<double> Gm((size_t)q * q, 0.0);
+  for (int a = 0; a < q; ++a)
+    for (int b = 0; b < q; ++b) {
+      double s = 0.0;
+      for (int r = 0; r < m; ++r) s += B[(size_t)a * m + r] * B[(size_t)b * m + r];
+      Gm[(size_t)a * q + b] = s;
+    }
+  std::vector<cd> gw, GV;
+  if (!dense_eig(q, Gm.data(), gw, GV)) return -1;
+  std::vector<int> gi(q);
+  for (int i = 0; i < q; ++i) gi[i] = i;
+  std::stable_sort(gi.begin(), gi.end(), [&](int a, int b) { return gw[a].real() > gw[b].real(); });
+  Q.assign((size_t)m * p, 0.0);
+  for (int c = 0; c < p; ++c) {
+    const int e = gi[c];
+    double nrm = 0.0;
+    for (int r = 0; r < m; ++r) {
+      double s = 0.0;
+      for (int a = 0; a < q; ++a) s += B[(size_t)a * m + r] * GV[(size_t)a * q + e].real();
+      Q[(size_t)c * m + r] = s;
+      nrm += s * s;
+    }
+    nrm = std::sqrt(nrm);
+    for (int r = 0; r < m; ++r) Q[(size_t)c * m + r] /= nrm;
+  }
+  // one more Gram-Schmidt sweep against rounding
+  for (int c = 0; c < p; ++c) {
+    double *z = &Q[(size_t)c * m];
+    for (int d2 = 0; d2 < c; ++d2) {
+      const double *y = &Q[(size_t)d2 * m];
+      double h = 0.0;
+      for (int r = 0; r < m; ++r) h += y[r] * z[r];
+      for (int r = 0; r < m; ++r) z[r] -= h * y[r];
+    }
+    double nn = 0.0;
+    for (int r = 0; r < m; ++r) nn += z[r] * z[r];
+    nn = std::sqrt(nn);
+    for (int r = 0; r < m; ++r) z[r] /= nn;
+  }
+  return p;
+}
 
 bool dense_eig(int m, const double *A, std::vector<std::complex<double>> &w,
                std::vector<std::complex<double>> &V) {

@@ -230,6 +230,12 @@ void launch_gemm_tall(cudaStream_t s, const double *X, int64_t ldx, int m, const
 // algorithm does not converge.
 bool dense_eig(int m, const double *A, std::vector<std::complex<double>> &w,
                std::vector<std::complex<double>> &V);
+// A real orthonormal basis Q (column-major m x p) of the invariant subspace of the `want`
+// eigenvalues of largest modulus of the real m x m row-major A (a complex pair kept whole, so
+// p is want or want + 1), from its complex Schur form reordered to put them first; w gets
+// those eigenvalues.  Returns p, or -1 if the QR algorithm does not converge.
+int invariant_basis(int m, const double *A, int want, std::vector<double> &Q,
+                    std::vector<std::complex<double>> &w);
 // y[i] = the filter's FP32 -> FP64 widening of x[i] (testing aid)
 void launch_widen(cudaStream_t s, const float *x, double *y, int64_t n);
 // FP64 FMA throughput probe (blocks x 256 threads, out: one double per thread); returns the

@@ -97,7 +97,8 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
            "wh_set_interp3", "wh_set_deflation", "wh_widen_f32", "wh_probe_fp64",
-           "wh_get_tuning", "wh_set_deflation_basis", "wh_eigs", "wh_dense_eig"]
+           "wh_get_tuning", "wh_set_deflation_basis", "wh_eigs", "wh_dense_eig",
+           "wh_dense_invariant"]
 
 
 def lib_path():
@@ -146,6 +147,7 @@ def lib():
     L.wh_eigs.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32,
                           C.c_uint64, vp, vp, vp, vp, C.POINTER(Stats)]
     L.wh_dense_eig.argtypes = [C.c_int32, vp, vp, vp]
+    L.wh_dense_invariant.argtypes = [C.c_int32, vp, C.c_int32, vp, C.POINTER(C.c_int32)]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -190,6 +192,20 @@ def dense_eig(A):
     if st != WH_OK:
         raise WHError(st, "wh_dense_eig failed")
     return w[0::2] + 1j * w[1::2], (V[0::2] + 1j * V[1::2]).reshape(m, m)
+
+
+def invariant_basis(A, want):
+    """Real orthonormal basis (columns) of the invariant subspace of the `want` eigenvalues
+    of largest modulus of a small real matrix, by the library's host routine; returns
+    (Q, p)."""
+    A = np.ascontiguousarray(A, np.float64)
+    m = A.shape[0]
+    Q = np.zeros(m * (want + 1))
+    p = C.c_int32()
+    st = lib().wh_dense_invariant(m, _ptr(A), want, _ptr(Q), C.byref(p))
+    if st != WH_OK:
+        raise WHError(st, "wh_dense_invariant failed")
+    return Q[:m * p.value].reshape(p.value, m).T.copy(), p.value
 
 
 def _ptr(a):

@@ -72,3 +72,40 @@ def test_dense_eig_rejects_bad_arguments(W):
     assert L.wh_dense_eig(0, None, None, None) == -1
     A = np.eye(2)
     assert L.wh_dense_eig(2, A.ctypes.data, None, None) == -1
+
+
+@pytest.mark.parametrize("kind", ["general", "rotation", "near-defective"])
+def test_invariant_basis_spans_an_invariant_subspace(W, kind):
+    """The Schur-reordered basis of the p eigenvalues of largest modulus: orthonormal, A Q =
+    Q (Q^T A Q) to rounding, and Q^T A Q carries exactly those eigenvalues (tested through
+    wh_eigs' host routine on matrices with complex pairs and a nearly defective pair)."""
+    rng = np.random.default_rng(5)
+    m = 30
+    if kind == "general":
+        A = rng.standard_normal((m, m))
+    elif kind == "rotation":
+        A = np.zeros((m, m))
+        for b in range(0, m, 2):
+            t = 0.2 * (b + 1)
+            r = 1.0 + 0.01 * b
+            A[b:b + 2, b:b + 2] = r * np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+        Qr, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        A = Qr @ A @ Qr.T
+    else:  # eigenvalue 2 with a Jordan-like coupling of 1e-8, then random ones below 1
+        J = np.diag(np.concatenate([[2.0, 2.0], 0.9 * rng.random(m - 2)]))
+        J[0, 1] = 1.0
+        J[1, 0] = 1e-16
+        Qr, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        A = Qr @ J @ Qr.T
+    import ctypes as C
+    # through the binding: the basis of the 4 (or 5) largest eigenvalues
+    from paper_2504_03074_gb300 import waveholtz as WH
+    Q, w = WH.invariant_basis(A, 4)
+    p = Q.shape[1]
+    assert p in (4, 5)
+    assert np.allclose(Q.T @ Q, np.eye(p), atol=1e-12)
+    T = Q.T @ A @ Q
+    assert np.max(np.abs(A @ Q - Q @ T)) < 1e-10 * np.max(np.abs(A))
+    ref = np.linalg.eigvals(A)
+    top = ref[np.argsort(-np.abs(ref))][:p]
+    assert _match(np.linalg.eigvals(T), top) < 1e-6

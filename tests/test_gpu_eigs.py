@@ -32,14 +32,15 @@ def _square_closed_form(prob, ts, k):
 
 def _subspace_gap(A, B):
     """Largest sine of the principal angles between the row spaces of A and B (orthonormal
-    rows)."""
-    s = np.linalg.svd(A @ B.T, compute_uv=False)
-    return float(np.sqrt(max(0.0, 1.0 - np.min(s) ** 2)))
+    rows, same count): the spectral norm of A's rows minus their projection on B's span
+    (computed directly; sqrt(1 - cos^2) would lose half the digits)."""
+    R = A - (A @ B.T) @ B
+    return float(np.linalg.norm(R, 2))
 
 
 def test_eigs_unit_square_closed_form_and_oracle(env, oracle_mod):
-    """32^2 unit square: the six modes of S with largest |beta| (degenerate pairs complete)
-    carry beta_d(lambda~) and lambda_h^2 in closed form (1e-10), their span equals the
+    """32^2 unit square: the five modes of S with largest |beta| (two degenerate pairs
+    complete; the sixth would split a pair) carry beta_d(lambda~) and lambda_h^2 in closed form (1e-10), their span equals the
     oracle's ARPACK span, and the basis is orthonormal with T = Q S Q^T."""
     torch, W = env
     from oracle import deflation as D
@@ -47,47 +48,54 @@ def test_eigs_unit_square_closed_form_and_oracle(env, oracle_mod):
     s = W.Solver(prob)
     ti = s.prepare()
     orc = oracle_mod.Oracle(prob)
-    bref, lref, nxt = _square_closed_form(prob, orc.time, 6)
+    bref, lref, nxt = _square_closed_form(prob, orc.time, 5)
     assert nxt < np.min(np.abs(bref)) - 1e-6  # a gap after the sixth
-    Q, T, beta, lam2, st = s.eigs(6, tol=1e-11, max_products=3000)
+    Q, T, beta, lam2, st = s.eigs(5, tol=1e-11, max_products=3000)
     assert st.converged == 1, (st.status, st.residual, st.iterations)
     assert np.allclose(np.sort(beta), np.sort(bref), rtol=0, atol=1e-10)
     assert np.allclose(np.sort(lam2), np.sort(lref), rtol=1e-10)
     Qh = Q.cpu().numpy()
-    assert np.allclose(Qh @ Qh.T, np.eye(6), atol=1e-12)
-    Phi, l2, b2 = D.wave_eigenpairs(orc, 6)
+    assert np.allclose(Qh @ Qh.T, np.eye(5), atol=1e-12)
+    Phi, l2, b2 = D.wave_eigenpairs(orc, 5)
     assert _subspace_gap(Qh, Phi) < 1e-8
     # T is the Rayleigh matrix: T = Q S Q^T, checked with the oracle's map
     assert np.allclose(T, D.rayleigh_matrix(orc, Qh), atol=1e-11)
 
 
 def test_eigs_overset_disk_match_pencil_and_deflated_solve(env, oracle_mod):
-    """Overset disk-in-square (order 2, non-self-adjoint): the GPU eigenpairs' lambda^2 are
-    eigenvalues of the independently assembled pencil A(omega) x = (omega^2 - lambda^2) B x
-    (B = 1 on discretization rows), their beta agree with the oracle's ARPACK run, and GMRES
-    on the deflated iteration with the exact inflation reaches the direct solution with
-    fewer wave solves than plain GMRES."""
+    """Overset disk-in-square (order 2, non-self-adjoint): the GPU eigenpairs are those of
+    the independently assembled pencil A(omega) x = (omega^2 - lambda^2) B x (B = 1 on
+    discretization rows, the constrained eigenproblem of Sec. 4.4): the six pencil
+    eigenvalues of largest |beta_d(lambda~)| (the filter's transfer function, Eq. betad)
+    give the GPU's beta (to 5e-8, see below) and its lambda^2 (1e-7 relative); GMRES on the deflated
+    iteration with the exact inflation reaches the direct solution with fewer wave solves
+    than plain GMRES."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
     import dhs
+    from oracle.oracle import beta_d_sum, lambda_tilde
     torch, W = env
-    from oracle import deflation as D
     dp = G.disk_problem(nb=48, nth=96, nr=10, order=2, omega=8.0, width=0.8, r_cut=0.75)
     s = W.Solver(dp)
-    s.prepare()
+    ti = s.prepare()
     Q, T, beta, lam2, st = s.eigs(6, tol=1e-11, max_products=4000)
     assert st.converged == 1, (st.status, st.residual, st.iterations)
-    Phi, l2o, bo = D.wave_eigenpairs(oracle_mod.Oracle(dp), 6)
-    assert np.allclose(np.sort(beta), np.sort(bo), rtol=0, atol=1e-9)
     A, rhs, lay = dhs.assemble(dp, dp.omega)
     Bd = np.zeros(lay.N)
     for gi, g in enumerate(dp.grids):
         for j, i in zip(*np.nonzero(g.mask == G.DISC)):
             Bd[lay.idx(gi, int(i), int(j))] = 1.0
-    mu, _ = spla.eigs(A.tocsc(), k=12, M=sp.diags(Bd).tocsc(), sigma=0.0)
+    mu, _ = spla.eigs(A.tocsc(), k=16, M=sp.diags(Bd).tocsc(), sigma=0.0)
     lp = np.real(dp.omega ** 2 - mu)
-    for x in lam2:
-        assert np.min(np.abs(lp - x)) < 1e-7 * x, (x, np.sort(lp))
+    orc = oracle_mod.Oracle(dp)
+    ts = orc.time
+    bp = beta_d_sum(lambda_tilde(np.sqrt(lp), ts.dt), ts.omega_e, ts.dt, ts.Nt, ts.alpha)
+    top = np.argsort(-np.abs(bp))[:6]
+    # 5e-8: the third and fourth modes are a nearly defective pair (the pencil returns them
+    # as a complex pair with imaginary part 1.2e-8), whose eigenvalues move by about the
+    # square root of a perturbation; the others agree to rounding
+    assert np.allclose(np.sort(beta), np.sort(bp[top]), rtol=0, atol=5e-8)
+    assert np.allclose(np.sort(lam2), np.sort(lp[top]), rtol=1e-7)
     U = dhs.solve(dp)
     s.set_deflation_basis(Q, T)
     u = torch.zeros(dp.n_total, dtype=torch.float64, device="cuda")
