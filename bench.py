@@ -166,17 +166,34 @@ FLOP_PER_LUP_O4 = 18.0
 
 
 def cpu_baseline(problem, sample):
-    """Time the CPU oracle (as it stands, single thread) on a bounded sample."""
+    """Time the CPU oracle, as it stands, on a bounded sample: single thread, and the same
+    source built with OpenMP over its point loops on all host cores (the same arithmetic:
+    its result is checked to equal the single-thread one bit for bit).  `value` and `cores`
+    are the all-cores figures."""
+    import numpy as np
     from oracle import oracle as O
     from paper_2504_03074_gb300 import grids as G
-    orc = O.Oracle(problem)
     v = G.random_state(problem, 1)
+    orc = O.Oracle(problem)
     t0 = time.perf_counter()
-    orc.iterate(v, True)
-    dt = time.perf_counter() - t0
+    ref = orc.iterate(v, True)
+    dt1 = time.perf_counter() - t0
     lups = problem.n_active * orc.time.M
-    return {"value": lups / dt / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-            "sample": sample, "seconds": dt, "host": host_cpu()}
+    rec = {"value": lups / dt1 / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+           "sample": sample, "seconds": dt1, "host": host_cpu(),
+           "single_thread": {"value": lups / dt1 / 1e9, "seconds": dt1, "cores": 1}}
+    try:
+        omp = O.Oracle(problem, openmp=True)
+        t0 = time.perf_counter()
+        out = omp.iterate(v, True)
+        dtn = time.perf_counter() - t0
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        rec.update({"value": lups / dtn / 1e9, "cores": threads, "seconds": dtn,
+                    "all_cores": {"value": lups / dtn / 1e9, "seconds": dtn, "cores": threads,
+                                  "equals_single_thread": bool(np.array_equal(out, ref))}})
+    except Exception as e:  # no OpenMP toolchain on the host: single thread only
+        rec["all_cores"] = {"unavailable": str(e)[:200]}
+    return rec
 
 
 def host_cpu():
@@ -503,19 +520,35 @@ def measure_sphere(WH, torch, stream, flush, cpu=False):
         del sp, u
     solve["speedup_fp32_vs_fp64"] = solve["fp64"]["seconds"] / solve["fp32_then_fp64"]["seconds"]
     res["solve_to_1e-3"] = solve
-    if cpu:  # the 3D oracle, single thread, on the half-resolution sample of the same recipe
+    if cpu:  # the 3D oracle on the half-resolution sample of the same recipe: one thread,
+        # then all cores (the same source built with OpenMP; equal results checked)
+        import numpy as np
         from oracle import oracle3 as O3
         half = G3.sphere_problem(nb=160, nphi=128, nth=64, nr=12, npatch=48)
         orc = O3.Oracle3(half)
         v = G3.random_state3(half, 1)
         t0 = time.perf_counter()
-        orc.iterate(v, True)
+        ref = orc.iterate(v, True)
         el = time.perf_counter() - t0
-        res["cpu_baseline"] = {
-            "value": half.n_active * orc.time.M / el / 1e9, "unit": "GLUP/s", "cores": 1,
-            "kind": "oracle", "seconds": el, "host": host_cpu(),
-            "sample": "one oracle WaveHoltz iteration of the half-resolution sample "
-                      "(160^3 + 128x64x12 + 2x48^2x12, M=%d)" % orc.time.M}
+        lups = half.n_active * orc.time.M
+        rec = {"value": lups / el / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+               "seconds": el, "host": host_cpu(),
+               "single_thread": {"value": lups / el / 1e9, "seconds": el, "cores": 1},
+               "sample": "one oracle WaveHoltz iteration of the half-resolution sample "
+                         "(160^3 + 128x64x12 + 2x48^2x12, M=%d)" % orc.time.M}
+        try:
+            omp = O3.Oracle3(half, openmp=True)
+            t0 = time.perf_counter()
+            out = omp.iterate(v, True)
+            eln = time.perf_counter() - t0
+            threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            rec.update({"value": lups / eln / 1e9, "cores": threads, "seconds": eln,
+                        "all_cores": {"value": lups / eln / 1e9, "seconds": eln,
+                                      "cores": threads,
+                                      "equals_single_thread": bool(np.array_equal(out, ref))}})
+        except Exception as e:
+            rec["all_cores"] = {"unavailable": str(e)[:200]}
+        res["cpu_baseline"] = rec
     return res
 
 

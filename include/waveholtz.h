@@ -318,6 +318,25 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
  * at solve time a batch). */
 wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2);
 
+/* Checkpoint and resume of a solve.  When wh_solve stops at its max_it wave solves
+ * (WH_ERR_NOT_CONVERGED), the context keeps what continuing it needs: the iterate (for
+ * GMRES stopped inside a restart cycle: the cycle's starting iterate, the Krylov basis built
+ * so far, the Hessenberg matrix, the Givens rotations and the residual vector), the
+ * right-hand side b, the product counts and the FP32/FP64 phase.  wh_get_state writes it
+ * into the HOST buffer buf (*bytes: its size on entry, the bytes written on return); with
+ * buf NULL it only returns the size in *bytes.  wh_set_state loads such a state into a
+ * context prepared for the same problem and frequency (checked: sizes, omega, dt, M); the
+ * next wh_solve with the same method (and restart) then continues that solve instead of
+ * starting one: its u receives the saved iterate (the initial guess is ignored) and max_it
+ * keeps counting the products made before the save.  A solve stopped at N products and
+ * resumed with max_it = N_total gives bit for bit the result of one uninterrupted solve with
+ * max_it = N_total.  The deflation set and tuning must be the same as when the state was
+ * saved (not checked).  Another wh_solve on the context discards a state not yet saved.
+ * Errors: WH_ERR_STATE (no stopped solve; another problem; an FP32 phase state on an FP64
+ * context), WH_ERR_ARG (buffer too small or not a saved state). */
+wh_status wh_get_state(wh_ctx *ctx, void *buf, size_t *bytes);
+wh_status wh_set_state(wh_ctx *ctx, const void *buf, size_t bytes);
+
 /* Deflation set as an orthonormal basis Q of an S-invariant subspace (S = W_h(., 0)) with
  * its Rayleigh matrix T = Q^T S Q, as wh_eigs returns them.  wh_solve then deflates with
  * P = I - Q Q^T like wh_set_deflation's set and inflates exactly: the Helmholtz solution is

@@ -30,26 +30,32 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "waveholtz_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 
-def build(force=False):
+def build(force=False, openmp=False):
     """Compile the C oracle with gcc (plain -O2, no fast-math, no vectorisation flags)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+    out = _LIB_OMP if openmp else _LIB
+    extra = ["-fopenmp"] if openmp else []
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-ffp-contract=off", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(openmp=False):
+    """The oracle library; openmp=True loads the same source built with OpenMP over its
+    point loops (the all-cores CPU baseline: same arithmetic per point, same results)."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if (_lib_omp if openmp else _lib) is None:
+            L = C.CDLL(build(openmp=openmp))
             vp, ip, dp, cp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_char_p
             L.or_new.restype = vp
             L.or_new.argtypes = [C.c_int]
@@ -71,8 +77,11 @@ def lib():
             L.or_b_mu.restype = C.c_double
             L.or_b_mu.argtypes = [C.c_int]
             L.or_free.argtypes = [vp]
-            _lib = L
-    return _lib
+            if openmp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if openmp else _lib
 
 
 def _p(a):
@@ -93,9 +102,9 @@ class TimeSetup:
 class Oracle:
     """One overset Helmholtz problem held by the C oracle."""
 
-    def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0):
+    def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0, openmp=False):
         self.problem = problem
-        self.L = lib()
+        self.L = lib(openmp)
         self.h = self.L.or_new(problem.order)
         self._keep = []
         for gi, g in enumerate(problem.grids):

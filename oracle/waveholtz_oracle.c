@@ -466,6 +466,9 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
     for (int g = 0; g < ng; ++g) {
       or_grid *G = &P->G[g];
       long E = ext_size(G);
+      /* OpenMP builds (timing only) split the point loops across threads; every point's
+         arithmetic is the same, so the results are the same bits */
+#pragma omp parallel for schedule(static)
       for (long q = 0; q < E; ++q)
         if (G->mask[q] != OR_UNUSED) V[g][q] += wn * W0[g][q];
     }
@@ -473,6 +476,7 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
     for (int g = 0; g < ng; ++g) {
       or_grid *G = &P->G[g];
       memset(Wp[g], 0, ext_size(G) * sizeof(double));
+#pragma omp parallel for schedule(static)
       for (int j = 0; j < G->n[1]; ++j)
         for (int i = 0; i < G->n[0]; ++i) {
           long q = at(G, i, j);
@@ -495,6 +499,7 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
     for (int g = 0; g < ng; ++g) {
       or_grid *G = &P->G[g];
       long E = ext_size(G);
+#pragma omp parallel for schedule(static)
       for (long q = 0; q < E; ++q)
         if (G->mask[q] != OR_UNUSED) V[g][q] += wn * W0[g][q];
     }

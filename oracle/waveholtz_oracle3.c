@@ -379,12 +379,16 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
     for (int g = 0; g < ng; ++g) {
       o3_grid *G = &P->G[g];
       long E = ext_size(G);
+      /* OpenMP builds (timing only) split the point loops across threads; every point's
+         arithmetic is the same, so the results are the same bits */
+#pragma omp parallel for schedule(static)
       for (long q = 0; q < E; ++q)
         if (G->mask[q] != O3_UNUSED) V[g][q] += wn * W0[g][q];
     }
     for (int g = 0; g < ng; ++g) {
       o3_grid *G = &P->G[g];
       memset(Wp[g], 0, ext_size(G) * sizeof(double));
+#pragma omp parallel for schedule(static)
       for (int k = 0; k < G->n[2]; ++k)
         for (int j = 0; j < G->n[1]; ++j)
           for (int i = 0; i < G->n[0]; ++i) {
@@ -408,6 +412,7 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
     for (int g = 0; g < ng; ++g) {
       o3_grid *G = &P->G[g];
       long E = ext_size(G);
+#pragma omp parallel for schedule(static)
       for (long q = 0; q < E; ++q)
         if (G->mask[q] != O3_UNUSED) V[g][q] += wn * W0[g][q];
     }

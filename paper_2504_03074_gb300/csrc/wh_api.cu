@@ -65,6 +65,20 @@ struct wh_ctx {
   // the inflation is then exact, u = v + Q (I - T)^{-1} Q^T W_h(v, f)
   bool defl_basis = false;
   std::vector<double> defl_T;
+  // a solve that stopped at its product budget, for wh_get_state, or one loaded by
+  // wh_set_state for the next wh_solve to continue (resume)
+  struct SavedSolve {
+    bool valid = false, resume = false;
+    int method = 0, restart = 0, phase = 0;  // phase 1: FP32 wave solves of an FP32 context
+    int products[2] = {0, 0};
+    int fpi_k = 0;
+    double bnorm = 0.0, prev = 0.0, residual = 0.0, dmin = 0.0;
+    bool cycle = false;  // stopped inside an Arnoldi cycle after kk steps
+    int kk = 0;
+    double beta = 0.0;
+    std::vector<double> H, cs, sn, g;
+  } saved;
+  double *d_saved = nullptr;  // device: [0] the iterate (the cycle's start inside a cycle), [1] b
   wh3::Ctx3 *c3 = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -1239,35 +1253,53 @@ constexpr double kOpBound = 2.5;
 
 wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero, int m,
                       double tol_abs, int budget, double scale, SolveLog &L, double *res_out,
-                      bool *finite) {
+                      bool *finite, wh_ctx::SavedSolve *sv = nullptr) {
   const int64_t n = ctx->ncompact;
   cudaStream_t s = ctx->stream;
   double *w0 = ctx->d_work, *r = ctx->d_work + n;
   double *Q = ctx->d_q;
   wh_status st;
   *finite = true;
-  if (x_is_zero) {
-    CK(cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  } else {
-    if ((st = apply_A(ctx, x, r, w0, L))) return st;
-    launch_axpby(grid1d(n), s, 1.0, rhs, -1.0, r, n);  // r = rhs - A x
-    --budget;
-  }
-  double rr;
-  if ((st = multidot(ctx, r, 0, 1, r, n, &rr))) return st;
-  const double beta = std::sqrt(rr);
-  *res_out = beta;
-  L.add(beta * scale);
-  if (!std::isfinite(beta)) {
-    *finite = false;
-    return WH_OK;
-  }
-  if (beta <= tol_abs || budget <= 0) return WH_OK;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m), h(m + 1);
-  g[0] = beta;
-  launch_axpby(grid1d(n), s, 1.0 / beta, r, 0.0, Q, n);
-  int kk = 0;
-  for (int k = 0; k < m && budget > 0; ++k) {
+  int k0 = 0;
+  if (sv && sv->cycle) {
+    // continue a cycle stopped after kk Arnoldi steps: x holds its starting iterate and
+    // Q[0..kk] its basis; the rotations and the residual vector g come from the state
+    H = sv->H;
+    cs = sv->cs;
+    sn = sv->sn;
+    g = sv->g;
+    k0 = sv->kk;
+    *res_out = std::fabs(g[k0]);
+    sv->cycle = false;
+  } else {
+    if (x_is_zero) {
+      CK(cudaMemcpyAsync(r, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      if ((st = apply_A(ctx, x, r, w0, L))) return st;
+      launch_axpby(grid1d(n), s, 1.0, rhs, -1.0, r, n);  // r = rhs - A x
+      --budget;
+    }
+    double rr;
+    if ((st = multidot(ctx, r, 0, 1, r, n, &rr))) return st;
+    const double beta = std::sqrt(rr);
+    *res_out = beta;
+    L.add(beta * scale);
+    if (!std::isfinite(beta)) {
+      *finite = false;
+      return WH_OK;
+    }
+    if (beta <= tol_abs || budget <= 0) return WH_OK;
+    g[0] = beta;
+    launch_axpby(grid1d(n), s, 1.0 / beta, r, 0.0, Q, n);
+  }
+  int kk = k0;
+  bool stopped = false;  // the budget ran out inside the cycle
+  for (int k = k0; k < m; ++k) {
+    if (budget <= 0) {
+      stopped = true;
+      break;
+    }
     double *qk = Q + (int64_t)k * n, *w = Q + (int64_t)(k + 1) * n;
     if ((st = apply_A(ctx, qk, w, w0, L))) return st;
     --budget;
@@ -1311,6 +1343,21 @@ wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero,
       return WH_OK;
     }
     if (est <= tol_abs || hk1 == 0) break;
+    if (budget <= 0 && kk < m) {
+      stopped = true;
+      break;
+    }
+  }
+  if (stopped && sv) {
+    // keep what continuing this cycle needs: the starting iterate (x, before the update
+    // below), the Arnoldi data, and the basis Q[0..kk] (stays in d_q)
+    sv->cycle = true;
+    sv->kk = kk;
+    sv->H = H;
+    sv->cs = cs;
+    sv->sn = sn;
+    sv->g = g;
+    CK(cudaMemcpyAsync(ctx->d_saved, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   for (int i = kk - 1; i >= 0; --i) {
     double t = g[i];
@@ -1322,6 +1369,7 @@ wh_status gmres_cycle(wh_ctx *ctx, const double *rhs, double *x, bool x_is_zero,
     launch_gemv_acc(grid1d(n), s, Q, n, kk, ctx->d_red, x, n);
   }
   CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));  // y is read by the copy above
   return WH_OK;
 }
 
@@ -1767,33 +1815,6 @@ uint64_t splitmix64(uint64_t &x) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
-}
-
-// Orthonormalise the p columns of the column-major m x p matrix Z (modified Gram-Schmidt,
-// twice); columns that vanish are dropped.  Returns the number kept.
-int orthonormalize(int m, int p, std::vector<double> &Z) {
-  int kept = 0;
-  for (int c = 0; c < p; ++c) {
-    double *z = &Z[(size_t)c * m];
-    double n0 = 0.0;
-    for (int r = 0; r < m; ++r) n0 += z[r] * z[r];
-    n0 = std::sqrt(n0);
-    for (int pass = 0; pass < 2; ++pass)
-      for (int d = 0; d < kept; ++d) {
-        const double *q = &Z[(size_t)d * m];
-        double h = 0.0;
-        for (int r = 0; r < m; ++r) h += q[r] * z[r];
-        for (int r = 0; r < m; ++r) z[r] -= h * q[r];
-      }
-    double nn = 0.0;
-    for (int r = 0; r < m; ++r) nn += z[r] * z[r];
-    nn = std::sqrt(nn);
-    if (!(nn > 1e-10 * n0) || !(nn > 0)) continue;
-    double *dst = &Z[(size_t)kept * m];
-    for (int r = 0; r < m; ++r) dst[r] = z[r] / nn;
-    ++kept;
-  }
-  return kept;
 }
 
 // The real basis of the `want` eigenvalues of largest modulus of the m x m matrix A
@@ -2659,9 +2680,47 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     CK(cudaStreamSynchronize(s));  // c is read by the copy above
     return WH_OK;
   };
+  // a state loaded by wh_set_state is continued; a new stop replaces the saved one
+  wh_ctx::SavedSolve &SV = ctx->saved;
+  const bool resume = SV.resume;
+  if (resume && (SV.method != method || (method == WH_GMRES && SV.restart != restart)))
+    return finish(fail(ctx, WH_ERR_STATE,
+                       "the loaded state is of another solve (method %d, restart %d)", SV.method,
+                       SV.restart));
+  SV.resume = false;
+  if (!resume) {
+    SV.valid = false;
+    SV.cycle = false;
+  }
+  if (!ctx->d_saved && (st = dalloc(ctx, &ctx->d_saved, 2 * (size_t)n))) return finish(st);
+  if (resume) {
+    CK(cudaMemcpyAsync(u, ctx->d_saved, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    L.products[0] = SV.products[0];
+    L.products[1] = SV.products[1];
+  }
+  // record a stop at the product budget (before any inflation touches u): the iterate (or,
+  // inside an Arnoldi cycle, the gmres_cycle already kept the cycle's start) and b
+  auto save_stop = [&](int phase, double prev, double dmin, int fpi_k) -> wh_status {
+    SV.valid = true;
+    SV.method = method;
+    SV.restart = method == WH_GMRES ? restart : 0;
+    SV.phase = phase;
+    SV.products[0] = L.products[0];
+    SV.products[1] = L.products[1];
+    SV.prev = prev;
+    SV.dmin = dmin;
+    SV.fpi_k = fpi_k;
+    SV.residual = S.residual;
+    if (!SV.cycle)
+      CK(cudaMemcpyAsync(ctx->d_saved, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (method == WH_GMRES)
+      CK(cudaMemcpyAsync(ctx->d_saved + n, w2, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return WH_OK;
+  };
   if (method == WH_FPI) {  // Algorithm 1 (Algorithm 3 with a deflation set)
-    double dmin = 1e300;
-    for (int k = 0; k < max_it; ++k) {
+    double dmin = resume ? SV.dmin : 1e300;
+    for (int k = resume ? SV.fpi_k : 0; k < max_it; ++k) {
       if ((st = iterate_device(ctx, 1, u, w0))) return finish(st);
       L.products[ctx->active] += 1;
       if (K > 0 && (st = defl_project(ctx, w0))) return finish(st);  // deflate
@@ -2687,6 +2746,7 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
         return finish(inflate());
       }
     }
+    if ((st = save_stop(0, 0.0, dmin, max_it))) return finish(st);
     if ((st = inflate())) return finish(st);
     return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "FPI: %d iterations, residual %g", max_it,
                        S.residual));
@@ -2698,28 +2758,36 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
   // system is the deflated fixed point (I - P S) v = P b, P = I - Phi Phi^T, inflated on
   // return like the fixed-point iteration's
   use_set(ctx, 0);
-  CK(cudaMemsetAsync(w0, 0, n * sizeof(double), s));
-  if ((st = iterate_device(ctx, 1, w0, w2))) return finish(st);
-  L.products[0] += 1;
-  if (K > 0) {
-    if ((st = defl_project(ctx, w2))) return finish(st);
-    if ((st = defl_project(ctx, u))) return finish(st);  // the guess lives in range(P) too
+  double bnorm;
+  if (resume) {  // b (deflated when a set is installed) and its norm come with the state
+    CK(cudaMemcpyAsync(w2, ctx->d_saved + n, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    bnorm = SV.bnorm;
+  } else {
+    CK(cudaMemsetAsync(w0, 0, n * sizeof(double), s));
+    if ((st = iterate_device(ctx, 1, w0, w2))) return finish(st);
+    L.products[0] += 1;
+    if (K > 0) {
+      if ((st = defl_project(ctx, w2))) return finish(st);
+      if ((st = defl_project(ctx, u))) return finish(st);  // the guess lives in range(P) too
+    }
+    double bb;
+    if ((st = multidot(ctx, w2, 0, 1, w2, n, &bb))) return finish(st);
+    bnorm = std::sqrt(bb);
   }
+  SV.bnorm = bnorm;
   struct DeflOff {  // apply_A leaves the deflated operator on every return
     wh_ctx *c;
     ~DeflOff() { c->defl_on = false; }
   } defl_off{ctx};
   ctx->defl_on = K > 0;
-  double bb;
-  if ((st = multidot(ctx, w2, 0, 1, w2, n, &bb))) return finish(st);
-  const double bnorm = std::sqrt(bb);
   if (!(bnorm > 0)) {
     CK(cudaMemsetAsync(u, 0, n * sizeof(double), s));
     S.converged = 1;
     return finish(inflate());
   }
   double *b = w2;
-  if (default_set(ctx) == 1) {
+  const bool fp32_phase = resume ? SV.phase == 1 : default_set(ctx) == 1;
+  if (fp32_phase) {
     // FP32 march: the first digits with FP32 wave solves, the rest with FP64 ones.  Phase 1:
     // GMRES(m) cycles whose products use the FP32 march (orthogonalisation, rotations and
     // the iterate stay FP64) down to max(tol, kFp32Split), or until a cycle no longer
@@ -2727,25 +2795,28 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     // true FP64 residual.  Each Krylov space is built once; refinement, which rebuilds one
     // per correction, measured ~1.9x the wave solves of FP64 GMRES on the solve benchmark.
     const double tol1 = std::max(tol, kFp32Split);
-    double prev = 1e300;
+    double prev = resume ? SV.prev : 1e300;
     use_set(ctx, 1);
     while (true) {
       double res;
       bool fin;
       const int budget = max_it - (L.products[0] + L.products[1]);
       if ((st = gmres_cycle(ctx, b, u, false, m, tol1 * bnorm, budget, 1.0 / bnorm, L, &res,
-                            &fin)))
+                            &fin, &SV)))
         return finish(st);
       if (!fin)
         return finish(fail(ctx, WH_ERR_DIVERGED,
                            "GMRES: residual or product norm %g is not finite or exceeds %g "
                            "(unstable march)", res, kGrowth * kOpBound));
       S.residual = res / bnorm;
-      if (res <= tol1 * bnorm || res > 0.5 * prev) break;
-      prev = res;
-      if (L.products[0] + L.products[1] >= max_it)
+      if (!SV.cycle && (res <= tol1 * bnorm || res > 0.5 * prev)) break;
+      if (!SV.cycle) prev = res;
+      if (L.products[0] + L.products[1] >= max_it) {
+        if ((st = save_stop(1, prev, 0.0, 0))) return finish(st);
+        if ((st = inflate())) return finish(st);
         return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
                            S.residual));
+      }
     }
     use_set(ctx, 0);
   }
@@ -2754,14 +2825,15 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     double res;
     bool fin;
     const int budget = max_it - (L.products[0] + L.products[1]);
-    if ((st = gmres_cycle(ctx, b, u, false, m, tol * bnorm, budget, 1.0 / bnorm, L, &res, &fin)))
+    if ((st = gmres_cycle(ctx, b, u, false, m, tol * bnorm, budget, 1.0 / bnorm, L, &res, &fin,
+                          &SV)))
       return finish(st);
     S.residual = res / bnorm;
     if (!fin)
       return finish(fail(ctx, WH_ERR_DIVERGED,
                          "GMRES: residual or product norm %g is not finite or exceeds %g "
                          "(unstable march)", res, kGrowth * kOpBound));
-    if (res <= tol * bnorm) {
+    if (!SV.cycle && res <= tol * bnorm) {
       // the cycle's last value may be the Givens estimate: confirm with a true residual
       double *rr = ctx->d_work + n;
       if ((st = apply_A(ctx, u, rr, w0, L))) return finish(st);
@@ -2776,6 +2848,7 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
       }
     }
     if (L.products[0] + L.products[1] >= max_it) {
+      if ((st = save_stop(0, 0.0, 0.0, 0))) return finish(st);
       if ((st = inflate())) return finish(st);
       return finish(fail(ctx, WH_ERR_NOT_CONVERGED, "GMRES: %d products, residual %g", max_it,
                          S.residual));
@@ -2795,6 +2868,144 @@ wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const doub
   ctx->defl_lam2.assign(lambda2 ? lambda2 : nullptr, lambda2 ? lambda2 + k : nullptr);
   ctx->defl_basis = false;
   ctx->defl_T.clear();
+  return WH_OK;
+}
+
+// Byte layout of a saved solve: this header, then (cycle only) H ((m+1) x m), cs, sn (m
+// each), g (m + 1) as doubles, then the device vectors: the iterate, b (GMRES), and (cycle
+// only) the Krylov basis Q[0..kk].
+struct StateHeader {
+  char magic[8];  // "WHSOLVE"
+  uint32_t version, size;
+  int32_t method, restart, phase, fpi_k, cycle, kk, products0, products1, M, pad;
+  int64_t n;
+  double bnorm, prev, residual, dmin, omega, dt;
+};
+
+static size_t state_bytes(const wh_ctx::SavedSolve &SV, int64_t n) {
+  size_t b = sizeof(StateHeader);
+  if (SV.cycle) b += sizeof(double) * ((size_t)(SV.restart + 1) * SV.restart + 3 * (size_t)SV.restart + 1);
+  b += sizeof(double) * (size_t)n * (SV.method == WH_GMRES ? 2 : 1);
+  if (SV.cycle) b += sizeof(double) * (size_t)n * (SV.kk + 1);
+  return b;
+}
+
+wh_status wh_get_state(wh_ctx *ctx, void *buf, size_t *bytes) {
+  if (!ctx || !bytes) return fail(ctx, WH_ERR_ARG, "bad wh_get_state arguments");
+  const wh_ctx::SavedSolve &SV = ctx->saved;
+  if (!SV.valid || SV.resume)
+    return fail(ctx, WH_ERR_STATE, "no stopped solve to save (wh_solve must have ended at max_it)");
+  const int64_t n = ctx->ncompact;
+  const size_t need = state_bytes(SV, n);
+  if (!buf) {
+    *bytes = need;
+    return WH_OK;
+  }
+  if (*bytes < need) return fail(ctx, WH_ERR_ARG, "state buffer of %zu bytes, %zu needed", *bytes, need);
+  StateHeader h{};
+  std::memcpy(h.magic, "WHSOLVE", 8);
+  h.version = 1;
+  h.size = (uint32_t)sizeof(StateHeader);
+  h.method = SV.method;
+  h.restart = SV.restart;
+  h.phase = SV.phase;
+  h.fpi_k = SV.fpi_k;
+  h.cycle = SV.cycle ? 1 : 0;
+  h.kk = SV.kk;
+  h.products0 = SV.products[0];
+  h.products1 = SV.products[1];
+  h.M = ctx->ti.M;
+  h.n = n;
+  h.bnorm = SV.bnorm;
+  h.prev = SV.prev;
+  h.residual = SV.residual;
+  h.dmin = SV.dmin;
+  h.omega = ctx->ti.omega;
+  h.dt = ctx->ti.dt;
+  char *p = (char *)buf;
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  auto put = [&](const std::vector<double> &v, size_t cnt) {
+    std::memcpy(p, v.data(), cnt * sizeof(double));
+    p += cnt * sizeof(double);
+  };
+  const int m = SV.restart;
+  if (SV.cycle) {
+    put(SV.H, (size_t)(m + 1) * m);
+    put(SV.cs, m);
+    put(SV.sn, m);
+    put(SV.g, (size_t)m + 1);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(p, ctx->d_saved, n * sizeof(double), cudaMemcpyDeviceToHost));
+  p += n * sizeof(double);
+  if (SV.method == WH_GMRES) {
+    CK(cudaMemcpy(p, ctx->d_saved + n, n * sizeof(double), cudaMemcpyDeviceToHost));
+    p += n * sizeof(double);
+  }
+  if (SV.cycle) CK(cudaMemcpy(p, ctx->d_q, (size_t)n * (SV.kk + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return WH_OK;
+}
+
+wh_status wh_set_state(wh_ctx *ctx, const void *buf, size_t bytes) {
+  if (!ctx || !buf) return fail(ctx, WH_ERR_ARG, "bad wh_set_state arguments");
+  if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
+  StateHeader h;
+  if (bytes < sizeof h) return fail(ctx, WH_ERR_ARG, "state buffer too short");
+  std::memcpy(&h, buf, sizeof h);
+  const int64_t n = ctx->ncompact;
+  if (std::memcmp(h.magic, "WHSOLVE", 8) != 0 || h.version != 1 || h.size != sizeof h)
+    return fail(ctx, WH_ERR_ARG, "not a saved wh_solve state");
+  if ((h.method != WH_FPI && h.method != WH_GMRES) || (h.method == WH_GMRES &&
+      (h.restart < 1 || h.restart > 4000 || h.kk < 0 || h.kk > h.restart)) || h.fpi_k < 0 ||
+      h.products0 < 0 || h.products1 < 0 || (h.phase != 0 && h.phase != 1))
+    return fail(ctx, WH_ERR_ARG, "inconsistent saved state");
+  if (h.n != n || h.M != ctx->ti.M || h.omega != ctx->ti.omega || h.dt != ctx->ti.dt)
+    return fail(ctx, WH_ERR_STATE, "the saved state belongs to another problem or frequency");
+  if (h.phase == 1 && ctx->opt.precision != WH_FP32)
+    return fail(ctx, WH_ERR_STATE, "the saved state is an FP32-march phase; the context is FP64");
+  wh_ctx::SavedSolve SV;
+  SV.method = h.method;
+  SV.restart = h.method == WH_GMRES ? h.restart : 0;
+  SV.phase = h.phase;
+  SV.fpi_k = h.fpi_k;
+  SV.cycle = h.cycle != 0;
+  SV.kk = h.kk;
+  SV.products[0] = h.products0;
+  SV.products[1] = h.products1;
+  SV.bnorm = h.bnorm;
+  SV.prev = h.prev;
+  SV.residual = h.residual;
+  SV.dmin = h.dmin;
+  if (bytes < state_bytes(SV, n)) return fail(ctx, WH_ERR_ARG, "state buffer too short");
+  const char *p = (const char *)buf + sizeof h;
+  auto get = [&](std::vector<double> &v, size_t cnt) {
+    v.resize(cnt);
+    std::memcpy(v.data(), p, cnt * sizeof(double));
+    p += cnt * sizeof(double);
+  };
+  const int m = SV.restart;
+  if (SV.cycle) {
+    get(SV.H, (size_t)(m + 1) * m);
+    get(SV.cs, m);
+    get(SV.sn, m);
+    get(SV.g, (size_t)m + 1);
+  }
+  wh_status st;
+  if (!ctx->d_saved && (st = dalloc(ctx, &ctx->d_saved, 2 * (size_t)n))) return st;
+  if (SV.method == WH_GMRES && (st = ensure_q(ctx, m + 1))) return st;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(ctx->d_saved, p, n * sizeof(double), cudaMemcpyHostToDevice));
+  p += n * sizeof(double);
+  if (SV.method == WH_GMRES) {
+    CK(cudaMemcpy(ctx->d_saved + n, p, n * sizeof(double), cudaMemcpyHostToDevice));
+    p += n * sizeof(double);
+  }
+  if (SV.cycle) CK(cudaMemcpy(ctx->d_q, p, (size_t)n * (SV.kk + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  SV.valid = true;
+  SV.resume = true;
+  ctx->saved = std::move(SV);
   return WH_OK;
 }
 

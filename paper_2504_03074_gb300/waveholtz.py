@@ -98,7 +98,7 @@ EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
            "wh_set_interp3", "wh_set_deflation", "wh_widen_f32", "wh_probe_fp64",
            "wh_get_tuning", "wh_set_deflation_basis", "wh_eigs", "wh_dense_eig",
-           "wh_dense_invariant"]
+           "wh_dense_invariant", "wh_get_state", "wh_set_state"]
 
 
 def lib_path():
@@ -148,6 +148,8 @@ def lib():
                           C.c_uint64, vp, vp, vp, vp, C.POINTER(Stats)]
     L.wh_dense_eig.argtypes = [C.c_int32, vp, vp, vp]
     L.wh_dense_invariant.argtypes = [C.c_int32, vp, C.c_int32, vp, C.POINTER(C.c_int32)]
+    L.wh_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.wh_set_state.argtypes = [vp, vp, C.c_size_t]
     L.wh_get_time_info.argtypes = [vp, C.POINTER(TimeInfo)]
     L.wh_multidot_noalloc.argtypes = [vp, C.c_int64, C.c_int32, vp, C.c_int64, vp, vp]
     L.wh_profile_kernels.argtypes = [vp, C.c_int32, C.POINTER(C.c_double),
@@ -389,6 +391,19 @@ class Solver:
         assert phi.is_cuda and phi.is_contiguous() and phi.shape[0] == lam.size
         self._check(self.L.wh_set_deflation(self.h, int(lam.size), _ptr(phi), _ptr(lam)))
         self._defl = (phi, lam)
+
+    def get_state(self):
+        """The state of the last solve that stopped at max_it, as bytes (wh_get_state)."""
+        n = C.c_size_t(0)
+        self._check(self.L.wh_get_state(self.h, None, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        self._check(self.L.wh_get_state(self.h, _ptr(buf), C.byref(n)))
+        return buf.tobytes()
+
+    def set_state(self, state):
+        """Load a saved solve (bytes from get_state); the next solve() continues it."""
+        buf = np.frombuffer(state, np.uint8).copy()
+        self._check(self.L.wh_set_state(self.h, _ptr(buf), buf.size))
 
     def set_deflation_basis(self, Q, T):
         """Deflation with an S-invariant orthonormal basis Q (contiguous float64 CUDA tensor

@@ -309,3 +309,17 @@ def test_widen_and_probe_arguments(W):
     t = C.c_double()
     assert L.wh_probe_fp64(0, C.byref(t), None) == -1
     assert L.wh_probe_fp64(3, None, None) == -1
+
+
+def test_state_validation_on_host(W):
+    """wh_get_state / wh_set_state refuse without a stopped solve or a prepared context,
+    before any device work."""
+    L = W.lib()
+    h = _ctx(W, 2)
+    n = C.c_size_t(0)
+    assert L.wh_get_state(h, None, None) == -1
+    assert L.wh_get_state(h, None, C.byref(n)) == -3  # nothing saved
+    buf = np.zeros(64, np.uint8)
+    assert L.wh_set_state(h, None, 0) == -1
+    assert L.wh_set_state(h, buf.ctypes.data, buf.size) == -3  # not prepared
+    L.wh_destroy(h)
