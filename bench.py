@@ -221,7 +221,8 @@ def time_iterations(WH, torch, solver, n_total, stream, flush, reps, warm=2):
             a, b = b, a
         tot = 0.0
         for k in range(reps):
-            flush.fill_(float(k))
+            if flush is not None:  # inputs larger than L2 need no flush
+                flush.fill_(float(k))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             solver.iterate(a, b, True)
@@ -440,8 +441,81 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
     solve["workload"] = ("64^2 unit square, order 2, omega 10, residual 1e-7; reference: FP64 "
                          "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
     out["solve_unit_square"] = solve
+    out["deflation_disk512_omega20"] = measure_deflation(WH, G, torch, stream)
     out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush, cpu)
     out["roofline_probe_3d_512"] = measure_cube_probe(WH, torch, stream)
+    return out
+
+
+def _solve_timed(WH, torch, s, n, tol, max_it, restart=300):
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = s.solve(u, WH.GMRES, tol=tol, max_it=max_it, restart=restart)
+    torch.cuda.synchronize()
+    return u, {"seconds": time.perf_counter() - t0, "wave_solves": st.iterations,
+               "wave_solves_fp32": st.products_fp32, "residual": st.residual,
+               "converged": st.converged}
+
+
+def measure_deflation(WH, G, torch, stream, nb=512, nth=1024, nr=32, omega=20.0, k=48,
+                      periods=(1, 2), eig_budget=4000, plain_budget=3000, extra_sources=3):
+    """Helmholtz solve time to 1e-6 relative error with deflation (Algorithm 3 through GMRES,
+    Sec. 4.3-4.4) on the overset disk-in-square (nb^2 background + nth x nr annulus, order 4,
+    c = 1), for N_p periods per iteration: k eigenpairs of S from the GPU eigensolver
+    (wh_eigs, once per frequency), then deflated GMRES(300) to a 1e-8 residual with the FP64
+    march and with FP32-then-FP64 wave solves, each checked against a deflated FP64 solve to
+    1e-12 (the reference); plain FP64 GMRES(300) with a fixed product budget for comparison;
+    and `extra_sources` further seeded sources solved with the same eigenpairs (the paper's
+    amortisation of the eigenpairs over several right-hand sides)."""
+    import numpy as np
+    prob = G.disk_problem(nb=nb, nth=nth, nr=nr, order=4, omega=omega, seed=0)
+    n = prob.n_total
+    out = {"workload": "disk-in-square %d^2 + %dx%d, order 4, omega %g, c = 1" % (nb, nth, nr, omega),
+           "k": k}
+    for Np in periods:
+        rec = {}
+        s = WH.Solver(prob, stream=stream, periods=Np)
+        ti = s.prepare()
+        rec["M"] = ti.M
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Q, T, beta, lam2, se = s.eigs(k, tol=1e-8, max_products=eig_budget, passes=1)
+        torch.cuda.synchronize()
+        rec["eigs"] = {"seconds": time.perf_counter() - t0, "wave_solves": se.iterations,
+                       "converged": se.converged, "residual": se.residual,
+                       "beta_max": float(np.max(beta)), "beta_k": float(np.min(np.abs(beta)))}
+        s.set_deflation_basis(Q, T)
+        uref, rec["reference_1e-12"] = _solve_timed(WH, torch, s, n, 1e-12, 4000)
+        nref = float(uref.abs().max())
+        u64, rec["deflated_fp64"] = _solve_timed(WH, torch, s, n, 1e-8, 4000)
+        rec["deflated_fp64"]["rel_err"] = float((u64 - uref).abs().max()) / nref
+        s32 = WH.Solver(prob, stream=stream, periods=Np, precision=WH.FP32)
+        s32.prepare()
+        s32.set_deflation_basis(Q, T)
+        u32, rec["deflated_fp32_then_fp64"] = _solve_timed(WH, torch, s32, n, 1e-8, 4000)
+        rec["deflated_fp32_then_fp64"]["rel_err"] = float((u32 - uref).abs().max()) / nref
+        s32.close()
+        s.set_deflation(None)
+        up, rec["plain_fp64"] = _solve_timed(WH, torch, s, n, 1e-8, plain_budget)
+        rec["plain_fp64"]["rel_err"] = float((up - uref).abs().max()) / nref
+        # more sources, same frequency: the eigenpairs are reused
+        s.set_deflation_basis(Q, T)
+        tot, prods = 0.0, 0
+        for seed in range(1, extra_sources + 1):
+            p2 = G.disk_problem(nb=nb, nth=nth, nr=nr, order=4, omega=omega, seed=seed)
+            for gi in range(len(p2.grids)):
+                s.set_forcing(gi, p2.f[gi])
+            s.prepare()
+            _, r = _solve_timed(WH, torch, s, n, 1e-8, 4000)
+            tot += r["seconds"]
+            prods += r["wave_solves"]
+        rec["more_sources"] = {"sources": extra_sources, "seconds": tot, "wave_solves": prods}
+        d = rec["deflated_fp64"]
+        rec["speedup_deflated_vs_plain_budget"] = rec["plain_fp64"]["seconds"] / d["seconds"]
+        s.close()
+        del Q, s
+        out["Np%d" % Np] = rec
     return out
 
 
@@ -459,6 +533,8 @@ def measure_cube_probe(WH, torch, stream):
     for name, prec, bpl in (("fp64", WH.FP64, 49.0), ("fp32", WH.FP32, 33.0)):
         sp = WH.Solver(cube, stream=stream, precision=prec)
         tp = sp.prepare()
+        if prec == WH.FP32:
+            sp.set_tuning(temporal_depth=1)  # the single-step march kernel on its own
         ms = sp.profile_kernels(reps=1)["march"][0]
         glups = tp.n_active / (ms * 1e-3) / 1e9
         rec = {"march_us": ms * 1e3, "value": glups, "unit": "GLUP/s", "M": tp.M,
@@ -466,6 +542,28 @@ def measure_cube_probe(WH, torch, stream):
         if prec == WH.FP64:
             rec["fp64_frac"] = glups * 15.0 / 1e3 / FP64_PEAK_TFLOPS
         probe[name] = rec
+        if prec == WH.FP32:
+            # temporal blocking: K steps per launch (the library's choice here), whole
+            # iterations timed; path-level effective bandwidth = GLUP/s x 33 B (the k = 1
+            # compulsory bytes); the blocked kernel's own algorithmic bytes per launch:
+            # per point W^n, W^{n-1}, F (NaN-marked) 4 B each, V read + write 16 B, two
+            # levels written 8 B = 36 B for K updates
+            sp.set_tuning()
+            t = sp.get_tuning()
+            it = time_iterations(WH, torch, sp, cube.n_total, stream, None, 2)
+            gl = tp.n_active * tp.M / it / 1e9
+            pk = sp.profile_kernels(reps=1)
+            bms, bn = pk["init"]  # [2] on three-dimensional contexts: the blocked march
+            bbytes = t["blocked_points"] * 36.0
+            probe["fp32_blocked"] = {
+                "temporal_depth": t["temporal_depth"], "unit_depth": t["unit_depth"],
+                "ms_per_iteration": it * 1e3, "value": gl, "unit": "GLUP/s",
+                "path_effective_gbs": gl * 33.0, "path_hbm_frac": gl * 33.0 / hbm,
+                "speedup_vs_single_step": gl / glups,
+                "blocked_kernel_ms_per_launch": bms, "blocked_launches": bn,
+                "blocked_kernel_gbs": bbytes / (bms * 1e-3) / 1e9,
+                "blocked_kernel_hbm_frac": bbytes / (bms * 1e-3) / 1e9 / hbm,
+                "blocked_bytes_per_update": 36.0 / t["temporal_depth"]}
         sp.close()
         del sp
     return probe
@@ -497,7 +595,20 @@ def measure_sphere(WH, torch, stream, flush, cpu=False):
         if prec == WH.FP64:  # 15 FP64 FLOP per 7-point update (stencil 10, forcing 3, filter 2)
             rec["march_fp64_frac"] = march_glups * 15.0 / 1e3 / FP64_PEAK_TFLOPS
         else:  # 33 compulsory bytes per update (W^n, W^{n-1} r/w, F, V r/w, mask)
-            rec["march_hbm_frac"] = march_glups * 33.0 / float(measured_peaks().get("hbm_gbs", 6793.0))
+            hbm = float(measured_peaks().get("hbm_gbs", 6793.0))
+            rec["march_hbm_frac"] = march_glups * 33.0 / hbm
+            rec["layout"] = sp.get_tuning()
+            # the autotuner over temporal depth 1..4 and unit depths (blocked march)
+            tune = sp.autotune(reps=1)
+            ta = time_iterations(WH, torch, sp, prob.n_total, stream, flush, 3)
+            pk = sp.profile_kernels(reps=1)
+            rec["autotuned"] = {
+                "temporal_depth": tune["temporal_depth"], "unit_depth": tune["unit_depth"],
+                "blocked_points": tune["blocked_points"], "candidates": tune["candidates"],
+                "value": tp.n_active * tp.M / ta / 1e9, "ms_per_iteration": ta * 1e3,
+                "path_hbm_frac": tp.n_active * tp.M / ta / 1e9 * 33.0 / hbm,
+                "single_step_march_ms": pk["march"], "gather_ms": pk["bc_gather"],
+                "blocked_march_ms": pk["init"]}
         res[name] = rec
         sp.close()
         del sp
@@ -606,6 +717,19 @@ def run_profile_case(case):
         torch.cuda.synchronize()
         print(f"profile case {case}: {sp.n_total} points, 1 iteration ({ti.M} march launches)")
         return 0
+    if case.startswith("fp32_cube320"):
+        from paper_2504_03074_gb300 import grids3 as G3
+        cp = G3.unit_cube_problem(320, omega=10.0)
+        s = WH.Solver(cp, precision=prec)
+        ti = s.prepare()
+        if case.endswith("single"):
+            s.set_tuning(temporal_depth=1)
+        a = torch.zeros(cp.n_total, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        s.iterate(a, b, True)
+        torch.cuda.synchronize()
+        print(f"profile case {case}: {cp.n_total} points, 1 iteration, layout {s.get_tuning()}")
+        return 0
     if case.endswith("square8192"):
         sq = G.unit_square_problem(8192, 4, 10.0, seed=0)
         s = WH.Solver(sq, precision=prec)
@@ -639,11 +763,13 @@ def main():
                     help="skip the FP32 / batched / solve-time measurements")
     ap.add_argument("--profile-case",
                     choices=["fp32_batch16", "fp64_batch16", "fp32_square8192",
-                             "fp64_square8192", "fp32_sphere320", "fp64_sphere320"],
+                             "fp64_square8192", "fp32_sphere320", "fp64_sphere320",
+                             "fp32_cube320_blocked", "fp32_cube320_single"],
                     help="profiling aid: a 16-instance disk-in-square batch (8.4 M points, "
                          "3 iterations), one 8192^2 order-4 Cartesian grid (67 M points, "
-                         "5 march launches) or the 3D sphere-in-box (34 M points, one "
-                         "iteration), HBM resident, in one precision; no bench line")
+                         "5 march launches), the 3D sphere-in-box (34 M points, one "
+                         "iteration) or a 320^3 cube with the blocked or the single-step "
+                         "FP32 march, HBM resident, in one precision; no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -726,13 +852,25 @@ def main():
     flops_per_launch = FLOP_PER_LUP_O4 * ti.n_active  # every launch updates all points
     achieved = flops_per_launch / avg_march_s / 1e12
     total_prof = sum(v[0] * v[1] for v in prof.values())
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+    # the FP64 roofline measured here, on this GPU, right after the timed region: a kernel
+    # of independent FMA chains and nothing else (wh_probe_fp64), best of 5 launches, with
+    # the clocks sampled during it
+    global FP64_PEAK_TFLOPS
+    with ClockSampler(local) as pclk:
+        pclk.wait_first()
+        pmark = pclk.mark()
+        peak_tf, peak_ms = WH.probe_fp64(5)
+    FP64_PEAK_TFLOPS = peak_tf
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf,
                 "traffic": recorded_traffic("march_kernel"),
                 "kernel": "march_kernel<double,4>", "avg_launch_us": avg_march_s * 1e6,
                 "flop_per_launch": flops_per_launch,
                 "share_of_iteration": march_ms * march_n / total_prof,
-                "peak_source": "GB300 FP64 1.25 TFLOP/s (pool figure; FMA=2)"}
+                "peak_source": "measured in this run: wh_probe_fp64 (independent DFMA chains, "
+                               "FMA = 2 FLOP, best of 5 launches of %.2f ms)" % peak_ms,
+                "peak_clocks": pclk.summary(pmark),
+                "nominal_fp64_tflops": 1.25}
 
     forms = None
     if not args.no_forms and not args.small and rank == 0:  # only rank 0 prints them
@@ -742,7 +880,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.small:
         cpu = cpu_baseline(prob, "one full oracle WaveHoltz iteration (M=%d steps) of the "
-                                 "same workload, single thread" % ti.M)
+                                 "same workload, single thread and all host cores" % ti.M)
     out = {
         "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

@@ -362,8 +362,9 @@ wh_status wh_set_deflation_basis(wh_ctx *ctx, int32_t k, const double *Q, const 
  * most slowly.  With passes = 2 a second run on (I - Q1 Q1^T) S (I - Q1 Q1^T) from another
  * start vector finds the copies of repeated eigenvalues that one Krylov sequence misses
  * (symmetric geometries), and the k largest of the union are kept (k more products for the
- * coupling block Q1^T S Q2).
- *   k      eigenpairs wanted; m: basis size (0 = max(2k + 10, k + 20), at most 2048);
+ * coupling block Q1^T S Q2); it runs only when the first pass converged and a whole basis
+ * of products remains, and its result is kept only if it converged too.
+ *   k      eigenpairs wanted; m: basis size (0 = max(3k, k + 60), at most 2048);
  *   tol    relative residual ||S y - beta y|| <= tol |beta| of every wanted Ritz pair;
  *   max_products  wave solves allowed (all passes);  seed: start vectors (splitmix64).
  * Outputs: Q (DEVICE, k compact vectors, row i at Q + i * n_total): an orthonormal basis of

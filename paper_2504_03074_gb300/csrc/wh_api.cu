@@ -3036,7 +3036,9 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
   if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "wh_eigs is available on 2D contexts");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   if (ctx->ninst != 1) return fail(ctx, WH_ERR_STATE, "wh_eigs needs one instance");
-  if (m == 0) m = std::min(2048, std::max(2 * k + 10, k + 20));
+  // default basis: wide enough for the clustered spectra of S near 1 (|beta| of many modes
+  // within 1e-4 of 1 at high frequency)
+  if (m == 0) m = std::min(2048, std::max(3 * k, k + 60));
   if (m < k + 2) return fail(ctx, WH_ERR_ARG, "basis size m must be at least k + 2");
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t n = ctx->ncompact;
@@ -3071,12 +3073,16 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
   std::vector<double> TB = P1.T;
   bool conv = P1.converged;
   double maxres = P1.maxres;
-  if (passes == 2 && products < max_products) {
+  // the second pass only when the first converged (its span is then S-invariant, which the
+  // block-triangular coupling below assumes) and a whole basis still fits in the budget
+  if (passes == 2 && P1.converged && max_products - products >= m) {
     // a second Krylov sequence on P S P finds the copies of repeated eigenvalues the first
     // one only meets through rounding; the union stays invariant (S Q2 = Q2 T2 + Q1 X)
     if ((st = eig_pass(ctx, k, m, tol, max_products, seed ^ 0x5DEECE66Dull, Lk, kb, V, Wk,
                        Lk + (int64_t)kb * n, P2, products)))
       return st;
+    if (!P2.converged) goto merged;  // keep the first pass's invariant subspace
+    {
     const int k2 = P2.k, kt = kb + k2;
     // X = Q1^T S Q2 (k2 products)
     std::vector<double> X((size_t)kb * k2), col((size_t)kb);
@@ -3095,9 +3101,10 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
       for (int j = 0; j < k2; ++j) TT[(size_t)(kb + i) * kt + kb + j] = P2.T[(size_t)i * k2 + j];
     TB = TT;
     kb = kt;
-    conv = conv && P2.converged;
     maxres = std::max(maxres, P2.maxres);
+    }
   }
+merged:
   // the k eigenvalues of largest modulus of T_B, their eigenvectors in the basis, and an
   // orthonormal basis of their span (Q) with its Rayleigh matrix
   SmallEig E;

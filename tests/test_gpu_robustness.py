@@ -168,3 +168,20 @@ def test_deflated_gmres_matches_oracle_and_direct_solve(torch, W, oracle_mod):
     u0 = torch.zeros_like(u)
     st0 = s.solve(u0, W.GMRES, tol=1e-12, max_it=4000, restart=100)
     assert st0.converged and st.iterations < st0.iterations
+
+
+def test_rejected_forcing_leaves_the_problem_unchanged(torch, W):
+    """A wh_set_forcing refused for non-finite values stores nothing: after it (and a new
+    prepare) an iteration gives the result it gave before the refused call, bit for bit."""
+    prob = G.disk_problem(nb=128, nth=256, nr=16, order=4, omega=10.0, seed=5)
+    s = W.Solver(prob)
+    s.prepare()
+    v = G.random_state(prob, 6)
+    before = s.iterate_host(v, True)
+    bad = np.array(prob.f[0], dtype=np.float64, copy=True)
+    bad.flat[17] = np.inf
+    with pytest.raises(W.WHError) as e:
+        s.set_forcing(0, bad)
+    assert e.value.status == -1
+    s.prepare()
+    assert np.array_equal(s.iterate_host(v, True), before)
