@@ -129,6 +129,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
+def stage(msg):
+    """Progress on stderr (the JSON line stays alone on stdout)."""
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def kernel_sha():
     p = os.path.join(ROOT, "paper_2504_03074_gb300", "csrc", "wh_kernels.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -243,6 +248,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
     s32 = WH.Solver(prob, stream=stream, precision=WH.FP32)
     ti = s32.prepare()
     t32 = time_iterations(WH, torch, s32, prob.n_total, stream, flush, 5)
+    stage("forms: fp32_march")
     out["fp32_march"] = {"value": ti.n_active * ti.M / t32 / 1e9, "unit": "GLUP/s",
                          "ms_per_iteration": t32 * 1e3,
                          "workload": "same disk-in-square workload, FP32 march, FP64 filter"}
@@ -283,6 +289,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
                 "gradient_sweep": {"ms": tg * 1e3, "vs_forward_iteration": tg / tf},
                 "forward_iteration_ms": tf * 1e3}
 
+    stage("forms: adjoint")
     out["adjoint"] = adjoint_costs(sa, ta, n)
     out["adjoint"]["workload"] = "same disk-in-square workload, FP64"
     sa.close()
@@ -291,6 +298,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
     mp = G.misfit_problem(nb=512, omega=20.0, seed=0)
     sm = WH.Solver(mp, stream=stream)
     tm = sm.prepare()
+    stage("forms: adjoint_misfit_512")
     out["adjoint_misfit_512"] = adjoint_costs(sm, tm, mp.n_total)
     out["adjoint_misfit_512"]["workload"] = (
         "disk-in-square 512^2 + 1024x32, order 4, omega 20, c = 1 + 0.2 sum of 8 Gaussian "
@@ -327,6 +335,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
                                       "sample": "8 seeded instances, one at a time"}
     res["speedup_batched_fp32_vs_plain_fp64"] = res["batched_fp32"]["value"] / \
         res["plain_fp64_per_instance"]["value"]
+    stage("forms: batch_256")
     out["batch_256"] = res
     del bp, probs
     # Helmholtz solves/s to 1e-6 relative error: batched FP32 (refined), batched FP64 and
@@ -391,6 +400,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
         bs["plain_fp64"]["solves_per_s"]
     bs["speedup_batched_fp64_vs_plain_fp64"] = bs["batched_fp64"]["solves_per_s"] / \
         bs["plain_fp64"]["solves_per_s"]
+    stage("forms: batch_solve")
     out["batch_solve"] = bs
     del sb_p, sb_probs, uref
     # roofline probe: one Cartesian grid of 16384^2 points (HBM resident), no interpolation,
@@ -416,6 +426,7 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
             sp.close()
             del sp
         del pp
+    stage("forms: roofline_probe_16384")
     out["roofline_probe_16384"] = probe
     # time to 1e-6 relative error, 64^2 unit square, order 2, omega 10
     sq = G.unit_square_problem(64, 2, 10.0, seed=0)
@@ -440,9 +451,16 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
                        "residual": st.residual}
     solve["workload"] = ("64^2 unit square, order 2, omega 10, residual 1e-7; reference: FP64 "
                          "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
+    stage("forms: solve_unit_square")
     out["solve_unit_square"] = solve
+    stage("forms: deflation")
+    stage("forms: deflation_disk512_omega20")
     out["deflation_disk512_omega20"] = measure_deflation(WH, G, torch, stream)
+    stage("forms: sphere-in-box")
+    stage("forms: sphere_in_box_320")
     out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush, cpu)
+    stage("forms: 3D roofline probe")
+    stage("forms: roofline_probe_3d_512")
     out["roofline_probe_3d_512"] = measure_cube_probe(WH, torch, stream)
     return out
 
@@ -868,6 +886,7 @@ def main():
     # of independent FMA chains and nothing else (wh_probe_fp64), best of 5 launches, with
     # the clocks sampled during it
     global FP64_PEAK_TFLOPS
+    stage("FP64 probe")
     with ClockSampler(local) as pclk:
         pclk.wait_first()
         pmark = pclk.mark()
@@ -884,13 +903,16 @@ def main():
                 "peak_clocks": pclk.summary(pmark),
                 "nominal_fp64_tflops": 1.25}
 
+    stage("main line done")
     forms = None
     if not args.no_forms and not args.small and rank == 0:  # only rank 0 prints them
         forms = measure_forms(WH, G, torch, prob, stream, flush, rank,
                               cpu=world == 1 and not args.no_cpu_baseline)
 
+    stage("forms done")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.small:
+        stage("cpu baseline")
         cpu = cpu_baseline(prob, "one full oracle WaveHoltz iteration (M=%d steps) of the "
                                  "same workload, single thread and all host cores" % ti.M)
     out = {

@@ -269,6 +269,11 @@ void free_device(wh_ctx *ctx) {
   ctx->d_rcoef = ctx->d_adj = ctx->d_ckpt = ctx->d_traj = nullptr;
   ctx->ckpt_cap = ctx->traj_cap = 0;
   ctx->d_bar = nullptr;
+  // buffers allocated on first use must be allocated again after a new layout
+  ctx->d_fcompact = nullptr;
+  ctx->d_saved = nullptr;
+  ctx->saved = wh_ctx::SavedSolve{};  // a stopped solve refers to the old layout
+  for (auto &S : ctx->set) S.maps = nullptr;
 }
 
 inline int64_t ext_index(const DevGrid &G, int i, int j) {
@@ -2444,6 +2449,8 @@ static wh_status prepare3(wh_ctx *ctx, double omega) {
     dfree(ctx, &ctx->d_work);
     dfree(ctx, &ctx->d_q);
     ctx->q_cap = 0;
+    dfree(ctx, &ctx->d_saved);
+    ctx->saved = wh_ctx::SavedSolve{};
   }
   ctx->ncompact = nc;
   ctx->nactive = na;

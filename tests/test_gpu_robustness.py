@@ -185,3 +185,30 @@ def test_rejected_forcing_leaves_the_problem_unchanged(torch, W):
     assert e.value.status == -1
     s.prepare()
     assert np.array_equal(s.iterate_host(v, True), before)
+
+
+def test_new_forcing_after_a_deflated_solve(torch, W, oracle_mod):
+    """A new forcing (which rebuilds the device layout at the next prepare) after solves that
+    allocated the deflation and checkpoint buffers: the next deflated GMRES solve runs on
+    fresh buffers and reaches the oracle's solution for the new source (the 48^2 unit
+    square, 8 DST modes)."""
+    import dhs
+    prob = G.unit_square_problem(48, 2, 10.0, seed=2)
+    s = W.Solver(prob)
+    orc = oracle_mod.Oracle(prob)
+    s.prepare()
+    Phi, l2 = _square_modes(prob, orc.time, 8)
+    phi = torch.from_numpy(Phi).cuda().contiguous()
+    s.set_deflation(phi, l2)
+    u = torch.zeros(prob.n_total, dtype=torch.float64, device="cuda")
+    s.solve(u, W.GMRES, tol=1e-12, max_it=30, restart=20)  # stops: a saved state exists
+    p2 = G.unit_square_problem(48, 2, 10.0, seed=7)
+    s.set_forcing(0, p2.f[0])
+    s.prepare()
+    u2 = torch.zeros_like(u)
+    st = s.solve(u2, W.GMRES, tol=1e-12, max_it=2000, restart=100)
+    assert st.converged
+    U = dhs.solve(p2)
+    assert _rel(u2.cpu().numpy(), U) <= 1e-9
+    with pytest.raises(W.WHError):
+        s.get_state()  # the stopped solve belonged to the old layout
