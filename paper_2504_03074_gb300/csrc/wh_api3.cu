@@ -106,9 +106,25 @@ wh_status alloc3(Ctx3 *c, T **p, size_t n, std::string &err) {
     return fail3(err, WH_ERR_NOMEM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T),
                  cudaGetErrorString(e));
   c->allocs.push_back((void *)*p);
+  // finish the legacy-stream zero fill before any launch on a non-blocking stream
   e = cudaMemset(*p, 0, n * sizeof(T));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   if (e != cudaSuccess) return fail3(err, WH_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
   return WH_OK;
+}
+
+// Release one buffer from alloc3 (after the device has finished with it).
+template <typename T>
+void free3(Ctx3 *c, T **p) {
+  if (!*p) return;
+  cudaDeviceSynchronize();
+  for (size_t k = 0; k < c->allocs.size(); ++k)
+    if (c->allocs[k] == (void *)*p) {
+      c->allocs.erase(c->allocs.begin() + k);
+      cudaFree((void *)*p);
+      break;
+    }
+  *p = nullptr;
 }
 
 void drop_graphs3(Ctx3 *c) {
@@ -518,8 +534,8 @@ wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
   }
   // units in plane-chunk-major order (already: k outermost per grid); upload
   wh_status st;
-  c->d_units = nullptr;
-  c->d_ctiles = nullptr;
+  free3(c, &c->d_units);  // the previous plan's lists
+  free3(c, &c->d_ctiles);
   if ((st = alloc3(c, &c->d_units, std::max<size_t>(c->units.size(), 1), err)) ||
       (st = alloc3(c, &c->d_ctiles, std::max<size_t>(c->ctiles.size(), 1), err)))
     return st;
@@ -531,15 +547,18 @@ wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
                    cudaMemcpyHostToDevice));
   if (K > 1 && !c->units.empty() && c->ring_L < K + 2) {
     // the ring: K + 2 levels (n - 1 .. n + K live during a block)
-    c->d_ring = nullptr;
+    free3(c, &c->d_ring);
+    c->ring_L = 0;
     if ((st = alloc3(c, &c->d_ring, (size_t)(K + 2) * c->total, err))) return st;
     c->ring_L = K + 2;
   }
   if (K > 1 && !c->units.empty() && !c->d_FM32) {
     if ((st = alloc3(c, &c->d_FM32, c->total, err))) return st;
     launch_forcing_mask(nullptr, c->d_F32, c->d_mask, c->d_FM32, c->total);
-    CK3(cudaDeviceSynchronize());
   }
+  // the unit and tile lists are plain copies from pageable memory: complete them (and the
+  // mask) before a launch on the context's non-blocking stream reads them
+  CK3(cudaDeviceSynchronize());
   return WH_OK;
 }
 
@@ -802,6 +821,9 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
   drop_graphs3(c);
   const int ng = (int)c->grids.size();
   CK3(cudaMemcpy(c->d_grids, c->hg.data(), ng * sizeof(Grid3Dev), cudaMemcpyHostToDevice));
+  // plain copies from pageable memory may still be in flight when they return, and the
+  // launches below go to a non-blocking stream: let the layout and forcing uploads land
+  CK3(cudaStreamSynchronize(cudaStreamLegacy));
   CK3(cudaMemsetAsync(c->d_smax, 0, sizeof(unsigned long long), s));
   for (int g = 0; g < ng; ++g)
     launch_coef3(s, c->d_grids, g, c->hg[g], c->d_mask, c->d_rx, c->d_c2, c->d_coef, c->d_smax);
@@ -869,6 +891,7 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
     for (int a = 0; a < 4; ++a) D.cwf[a] = (float)D.cw[a];
   }
   CK3(cudaMemcpy(c->d_grids, c->hg.data(), ng * sizeof(Grid3Dev), cudaMemcpyHostToDevice));
+  CK3(cudaStreamSynchronize(cudaStreamLegacy));
   const bool fp32 = opt.precision == WH_FP32;
   if (fp32 && !c->d_Wa32) {
     if ((st = alloc3(c, &c->d_Wa32, c->total, err)) || (st = alloc3(c, &c->d_Wb32, c->total, err)) ||

@@ -195,6 +195,8 @@ void schur_swap(int m, std::vector<cd> &T, std::vector<cd> &Z, int i) {
 
 int invariant_basis(int m, const double *A, int want, std::vector<double> &Q,
                     std::vector<std::complex<double>> &w) {
+  // the real basis may need one column per selected eigenvalue and, for members of split
+  // conjugate pairs, one more (see below); callers check the returned size
   Q.clear();
   w.clear();
   if (m <= 0 || want <= 0) return 0;
@@ -238,8 +240,13 @@ int invariant_basis(int m, const double *A, int want, std::vector<double> &Q,
     ++slot;
   }
   for (int i = 0; i < p; ++i) w.push_back(T[(size_t)i * m + i]);
-  // a real orthonormal basis of span(Z[:, 0..p)): the leading p left singular vectors of
-  // [Re Z_p, Im Z_p], from the eigenvectors of its (symmetric) Gram matrix
+  // A real orthonormal basis of span(Re Z_p, Im Z_p) — the real span of the selected complex
+  // subspace and of its conjugate, itself invariant since A is real — by Gram-Schmidt with
+  // column pivoting (the column with the largest remaining norm first, each orthogonalised
+  // twice), stopped when what remains is below 1e-6 of the largest column: rounding leaves
+  // ~1e-14 for a real eigenvalue's Schur vector, and a nearly real conjugate pair split by
+  // the selection keeps the extra dimension that its invariance needs.  (An eigensolve of
+  // the Gram matrix would not do: its nonzero eigenvalues are all near 1.)
   const int q = 2 * p;
   std::vector<double> B((size_t)m * q);
   for (int c = 0; c < p; ++c)
@@ -247,46 +254,53 @@ int invariant_basis(int m, const double *A, int want, std::vector<double> &Q,
       B[(size_t)(2 * c) * m + r] = Z[(size_t)r * m + c].real();
       B[(size_t)(2 * c + 1) * m + r] = Z[(size_t)r * m + c].imag();
     }
-  std::vector<double> Gm((size_t)q * q, 0.0);
-  for (int a = 0; a < q; ++a)
-    for (int b = 0; b < q; ++b) {
-      double s = 0.0;
-      for (int r = 0; r < m; ++r) s += B[(size_t)a * m + r] * B[(size_t)b * m + r];
-      Gm[(size_t)a * q + b] = s;
-    }
-  std::vector<cd> gw, GV;
-  if (!dense_eig(q, Gm.data(), gw, GV)) return -1;
-  std::vector<int> gi(q);
-  for (int i = 0; i < q; ++i) gi[i] = i;
-  std::stable_sort(gi.begin(), gi.end(), [&](int a, int b) { return gw[a].real() > gw[b].real(); });
-  Q.assign((size_t)m * p, 0.0);
-  for (int c = 0; c < p; ++c) {
-    const int e = gi[c];
-    double nrm = 0.0;
-    for (int r = 0; r < m; ++r) {
-      double s = 0.0;
-      for (int a = 0; a < q; ++a) s += B[(size_t)a * m + r] * GV[(size_t)a * q + e].real();
-      Q[(size_t)c * m + r] = s;
-      nrm += s * s;
-    }
-    nrm = std::sqrt(nrm);
-    for (int r = 0; r < m; ++r) Q[(size_t)c * m + r] /= nrm;
+  auto norm = [&](int c) {
+    double t = 0.0;
+    for (int r = 0; r < m; ++r) t += B[(size_t)c * m + r] * B[(size_t)c * m + r];
+    return std::sqrt(t);
+  };
+  double n0 = 0.0;
+  for (int c = 0; c < q; ++c) n0 = std::max(n0, norm(c));
+  std::vector<char> used(q, 0);
+  Q.clear();
+  int rank = 0;
+  while (rank < std::min(q, m)) {
+    int best = -1;
+    double bn = 0.0;
+    for (int c = 0; c < q; ++c)
+      if (!used[c]) {
+        const double t = norm(c);
+        if (t > bn) {
+          bn = t;
+          best = c;
+        }
+      }
+    if (best < 0 || !(bn > 1e-6 * n0)) break;
+    used[best] = 1;
+    std::vector<double> v(B.begin() + (size_t)best * m, B.begin() + (size_t)(best + 1) * m);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int d = 0; d < rank; ++d) {
+        const double *y = &Q[(size_t)d * m];
+        double h = 0.0;
+        for (int r = 0; r < m; ++r) h += y[r] * v[r];
+        for (int r = 0; r < m; ++r) v[r] -= h * y[r];
+      }
+    double nv = 0.0;
+    for (int r = 0; r < m; ++r) nv += v[r] * v[r];
+    nv = std::sqrt(nv);
+    for (int r = 0; r < m; ++r) v[r] /= nv;
+    Q.insert(Q.end(), v.begin(), v.end());
+    ++rank;
+    // remove the new direction from the columns still waiting
+    for (int c = 0; c < q; ++c)
+      if (!used[c]) {
+        double *b = &B[(size_t)c * m];
+        double h = 0.0;
+        for (int r = 0; r < m; ++r) h += v[r] * b[r];
+        for (int r = 0; r < m; ++r) b[r] -= h * v[r];
+      }
   }
-  // one more Gram-Schmidt sweep against rounding
-  for (int c = 0; c < p; ++c) {
-    double *z = &Q[(size_t)c * m];
-    for (int d2 = 0; d2 < c; ++d2) {
-      const double *y = &Q[(size_t)d2 * m];
-      double h = 0.0;
-      for (int r = 0; r < m; ++r) h += y[r] * z[r];
-      for (int r = 0; r < m; ++r) z[r] -= h * y[r];
-    }
-    double nn = 0.0;
-    for (int r = 0; r < m; ++r) nn += z[r] * z[r];
-    nn = std::sqrt(nn);
-    for (int r = 0; r < m; ++r) z[r] /= nn;
-  }
-  return p;
+  return rank;
 }
 
 bool dense_eig(int m, const double *A, std::vector<std::complex<double>> &w,

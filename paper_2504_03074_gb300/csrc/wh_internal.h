@@ -231,9 +231,11 @@ void launch_gemm_tall(cudaStream_t s, const double *X, int64_t ldx, int m, const
 bool dense_eig(int m, const double *A, std::vector<std::complex<double>> &w,
                std::vector<std::complex<double>> &V);
 // A real orthonormal basis Q (column-major m x p) of the invariant subspace of the `want`
-// eigenvalues of largest modulus of the real m x m row-major A (a complex pair kept whole, so
-// p is want or want + 1), from its complex Schur form reordered to put them first; w gets
-// those eigenvalues.  Returns p, or -1 if the QR algorithm does not converge.
+// eigenvalues of largest modulus of the real m x m row-major A (a complex pair kept whole),
+// from its complex Schur form reordered to put them first, widened to the real span of
+// that subspace and its conjugate (so p >= want: one more per nearly real conjugate pair
+// split by the selection); w gets the selected eigenvalues.  Returns p, or -1 if the QR
+// algorithm does not converge.
 int invariant_basis(int m, const double *A, int want, std::vector<double> &Q,
                     std::vector<std::complex<double>> &w);
 // y[i] = the filter's FP32 -> FP64 widening of x[i] (testing aid)

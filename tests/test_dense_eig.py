@@ -109,3 +109,35 @@ def test_invariant_basis_spans_an_invariant_subspace(W, kind):
     ref = np.linalg.eigvals(A)
     top = ref[np.argsort(-np.abs(ref))][:p]
     assert _match(np.linalg.eigvals(T), top) < 1e-6
+
+
+def test_invariant_basis_keeps_a_split_nearly_real_pair_whole(W):
+    """A conjugate pair whose imaginary part (1e-9) is below the pairing threshold, cut by
+    the selection: the returned real basis spans the pair's whole real invariant subspace
+    (one column more than asked), and A Q = Q (Q^T A Q) holds to rounding."""
+    from paper_2504_03074_gb300 import waveholtz as WH
+    rng = np.random.default_rng(11)
+    m = 20
+    J = np.diag(np.concatenate([[2.0, 1.5, 1.5], 0.5 * rng.random(m - 3)]))
+    J[1, 2], J[2, 1] = 1e-9, -1e-9  # 1.5 +- 1e-9 i
+    Qr, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    A = Qr @ J @ Qr.T
+    Q, p = WH.invariant_basis(A, 2)
+    assert p == 3
+    T = Q.T @ A @ Q
+    assert np.max(np.abs(A @ Q - Q @ T)) < 1e-12
+
+
+@pytest.mark.parametrize("m,want", [(48, 48), (144, 96), (96, 48)])
+def test_invariant_basis_large_selections(W, m, want):
+    """Selections covering most or all of the spectrum (the eigensolver's thick restarts and
+    its final k of a k-wide matrix): the basis stays orthonormal and invariant to rounding
+    (an earlier version built it from a degenerate Gram eigenproblem and lost both)."""
+    from paper_2504_03074_gb300 import waveholtz as WH
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, m)) / np.sqrt(m) + np.diag(np.linspace(1, 0.2, m))
+    Q, p = WH.invariant_basis(A, want)
+    assert want <= p <= want + 1
+    assert np.max(np.abs(Q.T @ Q - np.eye(p))) < 1e-13
+    T = Q.T @ A @ Q
+    assert np.max(np.abs(A @ Q - Q @ T)) < 1e-12
