@@ -126,3 +126,31 @@ def test_eigs_arguments_and_state(env):
     with pytest.raises(W.WHError) as e:
         c.eigs(2)
     assert e.value.status == -3
+
+
+def test_eigs_large_basis_invariant(env):
+    """A basis of 40 vectors (overset disk, order 4, four periods, where S has many modes
+    of |beta| near 1 in conjugate pairs and clusters): Q has orthonormal rows and spans an
+    S-invariant subspace, S Q^T = Q^T T, checked by applying the map to each row; T is
+    Q S Q^T.  Both coefficient sets of the final products are uploaded while the first
+    product may still run, so this also guards their ordering."""
+    torch, W = env
+    dp = G.disk_problem(nb=128, nth=256, nr=16, order=4, omega=12.0)
+    s = W.Solver(dp, periods=4)
+    s.prepare()
+    k = 40
+    Q, T, beta, lam2, st = s.eigs(k, tol=1e-12, max_products=4000)
+    assert st.converged == 1, (st.status, st.residual, st.iterations)
+    SQ = torch.empty_like(Q)
+    for i in range(k):
+        s.iterate(Q[i].contiguous(), SQ[i], False)
+    torch.cuda.synchronize()
+    Tt = torch.from_numpy(np.ascontiguousarray(T)).to(Q.device)
+    eye = torch.eye(k, dtype=Q.dtype, device=Q.device)
+    assert float((Q @ Q.T - eye).abs().max()) < 1e-12
+    assert float((SQ.T - Q.T @ Tt).abs().max()) < 1e-10
+    assert float((Q @ SQ.T - Tt).abs().max()) < 1e-12
+    # the reported beta are the eigenvalues of T (real parts, pairs repeated), descending
+    ev = np.linalg.eigvals(T)
+    assert np.allclose(np.sort(beta), np.sort(ev.real), atol=1e-10)
+    assert np.all(np.abs(beta) <= 1.0 + 1e-9) and np.all(np.isfinite(lam2))
