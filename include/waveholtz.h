@@ -241,9 +241,10 @@ wh_status wh_add_grid(wh_ctx *ctx, const wh_grid_desc *grid, int32_t *grid_id);
 wh_status wh_set_interp(wh_ctx *ctx, const wh_interp_desc *interp);
 /* Add a three-dimensional grid / set three-dimensional interpolation data (see
  * wh_grid3_desc, wh_interp3_desc).  wh_set_forcing, wh_prepare, wh_iterate,
- * wh_iterate_host, wh_solve, wh_dot, wh_profile_kernels and wh_get_time_info work on 3D
- * contexts unchanged; batches, differentiation, wh_set_coefficient and the launch tuning
- * calls return WH_ERR_STATE there.  One 3D iteration is an input kernel, a CUDA graph of
+ * wh_iterate_host, wh_solve, wh_dot, wh_eigs, the deflation calls, wh_get_state /
+ * wh_set_state, wh_profile_kernels and wh_get_time_info work on 3D contexts unchanged;
+ * batches, differentiation, wh_set_coefficient and the launch tuning calls return
+ * WH_ERR_STATE there.  One 3D iteration is an input kernel, a CUDA graph of
  * 2M + 1 kernels (level-0 ghost rules and interpolation, then per step the march and the
  * next level's ghost rules and interpolation) and an output kernel. */
 wh_status wh_add_grid3(wh_ctx *ctx, const wh_grid3_desc *grid, int32_t *grid_id);
@@ -311,11 +312,11 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
  * grids, whose discrete operator is not symmetric).  phi: DEVICE pointer to
  * k compact vectors, row m at phi + m * n_total; the context keeps the pointer (not a copy):
  * the caller owns the memory and keeps it alive and unchanged while the set is in use.
- * lambda2: HOST array of k values, copied.  k = 0 removes the set.  Two-dimensional
- * single-instance contexts only.  Errors: WH_ERR_ARG (k < 0 or > 4000, null pointers,
+ * lambda2: HOST array of k values, copied.  k = 0 removes the set.  Single-instance
+ * contexts (2D or 3D).  Errors: WH_ERR_ARG (k < 0 or > 4000, null pointers,
  * non-finite lambda2; at solve time |omega^2 - lambda_m^2| <= 1e-12 omega^2 for some m,
- * where the inflation would divide by a near-zero difference), WH_ERR_STATE (a 3D context;
- * at solve time a batch). */
+ * where the inflation would divide by a near-zero difference), WH_ERR_STATE (at solve time
+ * a batch). */
 wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2);
 
 /* Checkpoint and resume of a solve.  When wh_solve stops at its max_it wave solves
@@ -348,7 +349,7 @@ wh_status wh_set_state(wh_ctx *ctx, const void *buf, size_t bytes);
  * was off by 42%).  The paper has no counterpart of this form.  Q: DEVICE, k compact
  * vectors (row m at Q + m * n_total), kept by pointer like wh_set_deflation's; T: HOST,
  * k x k row-major, copied.  Errors: WH_ERR_ARG (k outside [1, 4000], null or non-finite
- * input; at solve time I - T singular), WH_ERR_STATE (3D context).  wh_set_deflation with
+ * input; at solve time I - T singular), WH_ERR_STATE (at solve time a batch).  wh_set_deflation with
  * k = 0 removes either kind of set. */
 wh_status wh_set_deflation_basis(wh_ctx *ctx, int32_t k, const double *Q, const double *T);
 
@@ -374,7 +375,7 @@ wh_status wh_set_deflation_basis(wh_ctx *ctx, int32_t k, const double *Q, const 
  * lambda2 (HOST k, may be NULL): lambda^2 = -(y, c^2 L_h y) / (y, y) over discretization
  * points for each eigenvector y (ghost rules applied first; c^2 L_h y from one first step
  * of the march), for wh_set_deflation.  stats (may be NULL): products, converged, the
- * largest relative residual, seconds.  Two-dimensional single-instance contexts after
+ * largest relative residual, seconds.  Single-instance contexts (2D or 3D) after
  * wh_prepare.  Allocates its basis ((m + 1) + max(m, 2k) + 3k vectors) for the call.
  * Errors: WH_ERR_ARG, WH_ERR_STATE; WH_ERR_NOT_CONVERGED when the products run out first
  * (the outputs then hold the current approximations). */

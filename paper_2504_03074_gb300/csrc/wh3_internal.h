@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -111,6 +112,9 @@ void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
                     double *V, const double *wf, int level);
 void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
                     const double *V, double *vout);
+// vout (compact) = W (extended, FP64) at discretization points, zero elsewhere.
+void launch_disc3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
+                  const int8_t *mask, const double *W, double *vout);
 void launch_to_precision(bool fp32, cudaStream_t s, const double *src, void *dst, int64_t n);
 
 // Host context of a three-dimensional problem (wh_api3.cu).
@@ -128,6 +132,16 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
 wh_status iterate(Ctx3 *c, bool fp32, int forcing, const double *vin, double *vout,
                   cudaStream_t s, int64_t *launches, std::string &err);
 int ngrids(const Ctx3 *c);
+// The masks (WH_DISC, ...) and the forcing (zero where none was set) of every grid in the
+// compact order (grids one after another, each (n2, n1, n0) row-major).
+void compact_mask(const Ctx3 *c, std::vector<int8_t> &m);
+void compact_forcing(const Ctx3 *c, std::vector<double> &f);
+// One first step of the FP64 march from y (compact) with zero forcing and the ghost rules
+// applied to y (no interpolation): wy = y and w1 = W^1 = y + dt^2/2 c^2 L_h y, both at
+// discretization points and zero elsewhere (compact).  Uses the FP64 state and filter
+// arrays as scratch.
+wh_status first_step(Ctx3 *c, const double *y, double *wy, double *w1, cudaStream_t s,
+                     std::string &err);
 // Temporal blocking of the FP32 march: depth K in [1, 4] (1 = single steps) and unit depth
 // (planes, a multiple of 8 in [8, 256]); -1 = the library's choice.  Takes effect at once
 // when the FP32 march is prepared, else at the next prepare.

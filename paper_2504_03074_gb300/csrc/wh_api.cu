@@ -1903,6 +1903,36 @@ wh_status eig_project(wh_ctx *ctx, const double *Lk, int nl, double *x) {
   return WH_OK;
 }
 
+// The masks and the forcing at discretization points (zero elsewhere) in the compact order,
+// for two- and three-dimensional contexts.
+void compact_disc(const wh_ctx *ctx, std::vector<int8_t> &m) {
+  if (ctx->dim == 3) {
+    wh3::compact_mask(ctx->c3, m);
+    return;
+  }
+  m.clear();
+  for (const auto &H : ctx->grids) m.insert(m.end(), H.mask.begin(), H.mask.end());
+}
+
+void compact_forcing_disc(const wh_ctx *ctx, std::vector<double> &f) {
+  std::vector<int8_t> m;
+  compact_disc(ctx, m);
+  if (ctx->dim == 3) {
+    wh3::compact_forcing(ctx->c3, f);
+  } else {
+    f.clear();
+    for (const auto &H : ctx->grids) {
+      const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
+      if (H.f.empty())
+        f.insert(f.end(), (size_t)np, 0.0);
+      else
+        f.insert(f.end(), H.f.begin(), H.f.begin() + np);
+    }
+  }
+  for (size_t q = 0; q < f.size(); ++q)
+    if (m[q] != WH_DISC) f[q] = 0.0;
+}
+
 struct EigPass {
   int k = 0;                // Schur vectors delivered
   std::vector<double> T;    // k x k row-major, T = Q^T S Q
@@ -1924,15 +1954,12 @@ wh_status eig_pass(wh_ctx *ctx, int k, int m, double tol, int budget, uint64_t s
   // start: uniform in (-1, 1) at discretization points (S ignores the others' values)
   {
     std::vector<double> v0((size_t)n, 0.0);
+    std::vector<int8_t> mk;
+    compact_disc(ctx, mk);
     uint64_t x = seed;
-    int64_t o = 0;
-    for (const auto &H : ctx->grids) {
-      const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
-      for (int64_t q = 0; q < np; ++q) {
-        const double r = (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0);
-        if (H.mask[q] == WH_DISC) v0[o + q] = 2.0 * r - 1.0;
-      }
-      o += np;
+    for (int64_t q = 0; q < n; ++q) {
+      const double r = (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0);
+      if (mk[q] == WH_DISC) v0[q] = 2.0 * r - 1.0;
     }
     if ((st = h2d(ctx, V, v0.data(), n * sizeof(double)))) return st;
   }
@@ -2055,6 +2082,15 @@ wh_status eig_pass(wh_ctx *ctx, int k, int m, double tol, int budget, uint64_t s
 wh_status rayleigh_lam2(wh_ctx *ctx, const double *y, double *w0, double *w1, double *lam2) {
   const int64_t n = ctx->ncompact;
   cudaStream_t s = ctx->stream;
+  if (ctx->dim == 3) {
+    if (wh_status e = wh3::first_step(ctx->c3, y, w0, w1, s, ctx->err)) return e;
+    launch_axpby(grid1d(n), s, -1.0, w0, 1.0, w1, n);
+    CK(cudaGetLastError());
+    double d[2];
+    if (wh_status e = multidot(ctx, w0, n, 2, w0, n, d)) return e;
+    *lam2 = -(2.0 / (ctx->ti.dt * ctx->ti.dt)) * d[1] / d[0];
+    return WH_OK;
+  }
   MarchSet &S0 = ctx->set[0];
   const int order = ctx->opt.order;
   const int ng = (int)ctx->hgrids.size();
@@ -2639,15 +2675,8 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
     // the forcing enters the discrete Helmholtz system on discretization rows only (the
     // generalized eigenproblem A x = lambda B x of Sec. 4.4 has B = 1 there and 0 on the
     // boundary and interpolation rows), so (f, phi_m) pairs phi_m with f at those points
-    std::vector<double> fc((size_t)n, 0.0);
-    int64_t o = 0;
-    for (const auto &H : ctx->grids) {
-      const int64_t np = (int64_t)H.d.n[0] * H.d.n[1];
-      if (!H.f.empty())
-        for (int64_t q = 0; q < np; ++q)
-          if (H.mask[q] == WH_DISC) fc[o + q] = H.f[q];
-      o += np;
-    }
+    std::vector<double> fc;
+    compact_forcing_disc(ctx, fc);
     if ((st = h2d(ctx, ctx->d_fcompact, fc.data(), n * sizeof(double)))) return st;
   }
   // on every return: add the Helmholtz solution's components along the deflation set,
@@ -2884,7 +2913,6 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
 
 wh_status wh_set_deflation(wh_ctx *ctx, int32_t k, const double *phi, const double *lambda2) {
   if (!ctx) return WH_ERR_ARG;
-  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "deflation is not available on 3D contexts");
   if (k < 0 || k > 4000) return fail(ctx, WH_ERR_ARG, "deflation set size must be in [0, 4000]");
   if (k > 0 && (!phi || !lambda2)) return fail(ctx, WH_ERR_ARG, "null deflation arrays");
   for (int m = 0; m < k; ++m)
@@ -3038,7 +3066,6 @@ wh_status wh_set_state(wh_ctx *ctx, const void *buf, size_t bytes) {
 
 wh_status wh_set_deflation_basis(wh_ctx *ctx, int32_t k, const double *Q, const double *T) {
   if (!ctx) return WH_ERR_ARG;
-  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "deflation is not available on 3D contexts");
   if (k < 1 || k > 4000) return fail(ctx, WH_ERR_ARG, "deflation basis size must be in [1, 4000]");
   if (!Q || !T) return fail(ctx, WH_ERR_ARG, "null deflation arrays");
   std::vector<double> A((size_t)k * k);
@@ -3060,7 +3087,6 @@ wh_status wh_eigs(wh_ctx *ctx, int32_t k, int32_t m, double tol, int32_t max_pro
   if (!ctx || !Q || !beta || k < 1 || !(tol > 0) || max_products < 1 || passes < 1 ||
       passes > 2 || m < 0 || m > 2048)
     return fail(ctx, WH_ERR_ARG, "bad wh_eigs arguments");
-  if (ctx->dim == 3) return fail(ctx, WH_ERR_STATE, "wh_eigs is available on 2D contexts");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   if (ctx->ninst != 1) return fail(ctx, WH_ERR_STATE, "wh_eigs needs one instance");
   // default basis: wide enough for the clustered spectra of S near 1 (|beta| of many modes

@@ -677,6 +677,37 @@ void destroy(Ctx3 *c) {
 
 int ngrids(const Ctx3 *c) { return c ? (int)c->grids.size() : 0; }
 
+void compact_mask(const Ctx3 *c, std::vector<int8_t> &m) {
+  m.clear();
+  for (const auto &H : c->grids) m.insert(m.end(), H.mask.begin(), H.mask.end());
+}
+
+void compact_forcing(const Ctx3 *c, std::vector<double> &f) {
+  f.clear();
+  for (const auto &H : c->grids) {
+    if (H.f.empty())
+      f.insert(f.end(), H.mask.size(), 0.0);
+    else
+      f.insert(f.end(), H.f.begin(), H.f.end());
+  }
+}
+
+wh_status first_step(Ctx3 *c, const double *y, double *wy, double *w1, cudaStream_t s,
+                     std::string &err) {
+  if (!c->d_Wa || c->dirty) return fail3(err, WH_ERR_STATE, "wh_prepare first");
+  const int ng = (int)c->grids.size();
+  launch_init3(false, s, c->d_grids, ng, c->max_ext, c->d_mask, y, c->d_Wa, c->d_V, c->tab.wf);
+  // the ghost rules of level 0 only (no receivers)
+  launch_gather3(false, s, 0, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw, c->d_gdst,
+                 c->d_gsrc, c->d_Wa, c->d_V, c->tab.wf, 0);
+  launch_march3(false, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, c->d_Wa,
+                c->d_Wb, c->d_Wb, c->d_F, c->d_Wt, c->d_V, c->tab, 0, 0.0);
+  launch_disc3(s, c->d_grids, ng, c->max_compact, c->d_mask, c->d_Wa, wy);
+  launch_disc3(s, c->d_grids, ng, c->max_compact, c->d_mask, c->d_Wb, w1);
+  CK3(cudaGetLastError());
+  return WH_OK;
+}
+
 wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std::string &err) {
   if (!d || !d->mask) return fail3(err, WH_ERR_ARG, "null grid description or mask");
   if (order != 2) return fail3(err, WH_ERR_ARG, "three-dimensional grids need order 2");

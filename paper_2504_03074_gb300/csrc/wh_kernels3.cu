@@ -634,14 +634,17 @@ __global__ void __launch_bounds__(256) gather3_kernel(
     W[gdst[g]] = W[gsrc[g]];
 }
 
-// v_out (compact) = V at every point of every grid; blockIdx.y = grid.
-__global__ void finish3_kernel(const Grid3Dev *grids, const double *V, double *vout) {
+// v_out (compact) = V at every point of every grid (with `mask`: at discretization points,
+// zero elsewhere); blockIdx.y = grid.
+__global__ void finish3_kernel(const Grid3Dev *grids, const int8_t *mask, const double *V,
+                               double *vout) {
   const Grid3Dev G = grids[blockIdx.y];
   const int64_t npts = (int64_t)G.n0 * G.n1 * G.n2;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % G.n0), j = (int)((t / G.n0) % G.n1), k = (int)(t / ((int64_t)G.n0 * G.n1));
-    vout[G.cbase + t] = V[at3(G, i, j, k)];
+    const int64_t q = at3(G, i, j, k);
+    vout[G.cbase + t] = (!mask || mask[q] == kDisc) ? V[q] : 0.0;
   }
 }
 
@@ -768,7 +771,13 @@ void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
 void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
                     const double *V, double *vout) {
   dim3 gb(blocks_for(max_compact, 256), ngrids);
-  finish3_kernel<<<gb, 256, 0, s>>>(grids, V, vout);
+  finish3_kernel<<<gb, 256, 0, s>>>(grids, nullptr, V, vout);
+}
+
+void launch_disc3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
+                  const int8_t *mask, const double *W, double *vout) {
+  dim3 gb(blocks_for(max_compact, 256), ngrids);
+  finish3_kernel<<<gb, 256, 0, s>>>(grids, mask, W, vout);
 }
 
 void launch_to_precision(bool fp32, cudaStream_t s, const double *src, void *dst, int64_t n) {

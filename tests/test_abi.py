@@ -258,8 +258,8 @@ def test_grid3_validation_on_host(W):
 
 
 def test_deflation_validation_on_host(W):
-    """wh_set_deflation checks its arguments without touching the device; 3D contexts
-    refuse it."""
+    """wh_set_deflation checks its arguments without touching the device, on 2D and 3D
+    contexts alike."""
     L = W.lib()
     h = _ctx(W, order=2)
     lam = (C.c_double * 2)(1.0, 2.0)
@@ -277,7 +277,9 @@ def test_deflation_validation_on_host(W):
     d, keep = _desc3(W, cube)
     gid = C.c_int32()
     assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0
-    assert L.wh_set_deflation(h, 2, C.c_void_p(64), lam) == -3
+    assert L.wh_set_deflation(h, 2, C.c_void_p(64), bad) == -1
+    assert L.wh_set_deflation(h, 2, C.c_void_p(64), lam) == 0
+    assert L.wh_set_deflation(h, 0, None, None) == 0
     L.wh_destroy(h)
 
 

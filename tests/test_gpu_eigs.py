@@ -122,10 +122,9 @@ def test_eigs_arguments_and_state(env):
         s.eigs(4, m=5)
     assert e.value.status == -1  # basis smaller than k + 2
     c = W.Solver(G3.unit_cube_problem(9, omega=4.0))
-    c.prepare()
     with pytest.raises(W.WHError) as e:
         c.eigs(2)
-    assert e.value.status == -3
+    assert e.value.status == -3  # a 3D context, before wh_prepare
 
 
 def test_eigs_large_basis_invariant(env):
