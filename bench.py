@@ -453,9 +453,15 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
                          "GMRES to 1e-13 (equal to the direct discrete solve in the tests)")
     stage("forms: solve_unit_square")
     out["solve_unit_square"] = solve
-    stage("forms: deflation")
     stage("forms: deflation_disk512_omega20")
-    out["deflation_disk512_omega20"] = measure_deflation(WH, G, torch, stream)
+    out["deflation_disk512_omega20"] = measure_deflation(WH, G, torch, stream, periods=(1,),
+                                                         tols=(1e-9, 1e-10))
+    stage("forms: deflation on the 1024^2 omega 40 disk")
+    # the headline workload solved to 1e-6 relative error: N_p = 4 (the paper runs 2-8),
+    # 64 eigenpairs; plain GMRES does not converge there within the budget
+    out["deflation_disk1024_omega40"] = measure_deflation(
+        WH, G, torch, stream, nb=1024, nth=2048, nr=64, omega=40.0, k=64, periods=(4,),
+        eig_budget=3000, plain_budget=600, extra_sources=2, tols=(1e-9, 1e-10))
     stage("forms: sphere-in-box")
     stage("forms: sphere_in_box_320")
     out["sphere_in_box_320"] = measure_sphere(WH, torch, stream, flush, cpu)
@@ -477,18 +483,21 @@ def _solve_timed(WH, torch, s, n, tol, max_it, restart=300):
 
 
 def measure_deflation(WH, G, torch, stream, nb=512, nth=1024, nr=32, omega=20.0, k=48,
-                      periods=(1, 4), eig_budget=4000, plain_budget=3000, extra_sources=3):
+                      periods=(1,), eig_budget=4000, plain_budget=3000, extra_sources=3,
+                      tols=(1e-8,)):
     """Helmholtz solve time to 1e-6 relative error with deflation (Algorithm 3 through GMRES,
     Sec. 4.3-4.4) on the overset disk-in-square (nb^2 background + nth x nr annulus, order 4,
     c = 1), for N_p periods per iteration: k eigenpairs of S from the GPU eigensolver
-    (wh_eigs, once per frequency), then deflated GMRES(300) to a 1e-8 residual with the FP64
-    march and with FP32-then-FP64 wave solves, each checked against a deflated FP64 solve to
-    1e-12 (the reference); plain FP64 GMRES(300) with a fixed product budget for comparison;
-    and `extra_sources` further seeded sources solved with the same eigenpairs (the paper's
-    amortisation of the eigenpairs over several right-hand sides).  The exact inflation's
-    error is the basis's invariance residual ||S Q - Q T|| amplified by ||(I - T)^{-1}||
-    (about 1 / (1 - beta_max)), so both are measured (k more products) and reported with
-    their product as the error bound."""
+    (wh_eigs, once per frequency), then deflated GMRES(300) to each residual tolerance in
+    `tols` with the FP64 march and with FP32-then-FP64 wave solves, each checked against a
+    deflated FP64 solve to 1e-12 (the reference); plain FP64 GMRES(300) with a fixed product
+    budget for comparison; and `extra_sources` further seeded sources solved with the same
+    eigenpairs (the paper's amortisation of the eigenpairs over several right-hand sides).
+    The exact inflation's error is the basis's invariance residual ||S Q - Q T|| amplified by
+    ||(I - T)^{-1}|| (about 1 / (1 - beta_max)), so both are measured (k more products) and
+    reported with their product as the bound on the reference's error.  time_to_1e-6 is the
+    eigensolve plus the first solve (loosest tolerance first) whose error against the
+    reference is at most 1e-6, per precision."""
     import numpy as np
     prob = G.disk_problem(nb=nb, nth=nth, nr=nr, order=4, omega=omega, seed=0)
     n = prob.n_total
@@ -518,17 +527,25 @@ def measure_deflation(WH, G, torch, stream, nb=512, nth=1024, nr=32, omega=20.0,
         s.set_deflation_basis(Q, T)
         uref, rec["reference_1e-12"] = _solve_timed(WH, torch, s, n, 1e-12, 4000)
         nref = float(uref.abs().max())
-        u64, rec["deflated_fp64"] = _solve_timed(WH, torch, s, n, 1e-8, 4000)
-        rec["deflated_fp64"]["rel_err"] = float((u64 - uref).abs().max()) / nref
         s32 = WH.Solver(prob, stream=stream, periods=Np, precision=WH.FP32)
         s32.prepare()
         s32.set_deflation_basis(Q, T)
-        u32, rec["deflated_fp32_then_fp64"] = _solve_timed(WH, torch, s32, n, 1e-8, 4000)
-        rec["deflated_fp32_then_fp64"]["rel_err"] = float((u32 - uref).abs().max()) / nref
+        tts = {}
+        for name, sv in (("fp64", s), ("fp32_then_fp64", s32)):
+            for tol in tols:
+                u, r = _solve_timed(WH, torch, sv, n, tol, 4000)
+                r["rel_err"] = float((u - uref).abs().max()) / nref
+                rec["deflated_%s_%g" % (name, tol)] = r
+                if name not in tts and r["converged"] and r["rel_err"] <= 1e-6:
+                    tts[name] = {"seconds": rec["eigs"]["seconds"] + r["seconds"], "tol": tol,
+                                 "wave_solves": se.iterations + r["wave_solves"]}
+                del u
+        rec["time_to_1e-6"] = tts
         s32.close()
         s.set_deflation(None)
-        up, rec["plain_fp64"] = _solve_timed(WH, torch, s, n, 1e-8, plain_budget)
+        up, rec["plain_fp64"] = _solve_timed(WH, torch, s, n, tols[0], plain_budget)
         rec["plain_fp64"]["rel_err"] = float((up - uref).abs().max()) / nref
+        del up
         # more sources, same frequency: the eigenpairs are reused
         s.set_deflation_basis(Q, T)
         tot, prods = 0.0, 0
@@ -537,14 +554,14 @@ def measure_deflation(WH, G, torch, stream, nb=512, nth=1024, nr=32, omega=20.0,
             for gi in range(len(p2.grids)):
                 s.set_forcing(gi, p2.f[gi])
             s.prepare()
-            _, r = _solve_timed(WH, torch, s, n, 1e-8, 4000)
+            _, r = _solve_timed(WH, torch, s, n, tts.get("fp64", {}).get("tol", tols[-1]), 4000)
             tot += r["seconds"]
             prods += r["wave_solves"]
         rec["more_sources"] = {"sources": extra_sources, "seconds": tot, "wave_solves": prods}
-        d = rec["deflated_fp64"]
+        d = rec["deflated_fp64_%g" % tols[0]]
         rec["speedup_deflated_vs_plain_budget"] = rec["plain_fp64"]["seconds"] / d["seconds"]
         s.close()
-        del Q, s
+        del Q, s, uref
         out["Np%d" % Np] = rec
     return out
 
