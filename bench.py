@@ -304,6 +304,37 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
         "disk-in-square 512^2 + 1024x32, order 4, omega 20, c = 1 + 0.2 sum of 8 Gaussian "
         "bumps (width 0.2), FP64; M = %d" % tm.M)
     sm.close()
+    # time to the gradient on that geometry: N_p = 4, the reverse march from checkpoints
+    # every 16 steps; forward GMRES to 1e-12, the receiver misfit against data from a
+    # medium 5% faster in a Gaussian patch, adjoint GMRES to 1e-12 and the gradient sweep
+    # (the gradients' agreement with central finite differences is a GPU test)
+    stage("forms: gradient_misfit_512_np4")
+    P = G.receiver_matrix(mp, n=64, radius=1.5)
+    sg = WH.Solver(mp, stream=stream, periods=4, trajectory_bytes=1)
+    for gi, c in enumerate(G.perturbed_c2(mp)):
+        sg.set_coefficient(gi, c)
+    sg.prepare()
+    ud, _ = _solve_timed(WH, torch, sg, mp.n_total, 1e-10, 3000, restart=400)
+    d = P @ ud.cpu().numpy()
+    for gi, c in enumerate(mp.c2):
+        sg.set_coefficient(gi, c)
+    tg = sg.prepare()
+    u, fw = _solve_timed(WH, torch, sg, mp.n_total, 1e-12, 3000, restart=400)
+    rr = P @ u.cpu().numpy() - d
+    g = torch.from_numpy(P.T @ rr).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, gc2, gf, sta = sg.adjoint(u, g, tol=1e-12, max_it=3000, restart=400)
+    torch.cuda.synchronize()
+    ta_s = time.perf_counter() - t0
+    out["gradient_misfit_512_np4"] = {
+        "M": tg.M, "misfit": 0.5 * float(rr @ rr), "forward": fw,
+        "adjoint": {"seconds": ta_s, "wave_solves": sta.iterations, "residual": sta.residual,
+                    "converged": sta.converged},
+        "time_to_gradient_s": fw["seconds"] + ta_s,
+        "grad_c2_norm": float(gc2.norm()), "grad_f_norm": float(gf.norm())}
+    sg.close()
+    del u, ud, gc2, gf, g
     # batch: 256 disk-in-square instances, N ~ U{256..1024}, annulus 2N x N/16,
     # omega ~ U[10, 50], 1-4 sources
     t0 = time.perf_counter()

@@ -176,3 +176,61 @@ def test_checkpointed_sweep_matches_whole_trajectory(torch, W, name, make):
         s.close()
     for a, b in zip(out[0], out[1]):
         assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a)), name
+
+
+def test_gradient_vs_finite_differences_inversion_geometry_512(torch, W):
+    """The sound-speed inversion workload at full size: disk-in-square 512^2 + 1024x32,
+    order 4, omega 20, c = 1 + 0.2 sum of 8 Gaussian bumps, 64 receivers on the circle of
+    radius 1.5, data from a medium 5% faster in a Gaussian patch; N_p = 4 periods per
+    iteration (forward and adjoint GMRES reach 1e-12 in about 330 wave solves; at N_p = 1
+    they need thousands) and the reverse march from checkpoints every 16 steps
+    (trajectory_bytes = 1).  Gradients w.r.t. c^2 and f against central finite differences
+    in ten random directions (six c^2, four f), 1e-6 relative."""
+    prob = G.misfit_problem(nb=512, omega=20.0, seed=0)
+    P = G.receiver_matrix(prob, n=64, radius=1.5)
+    n = prob.n_total
+
+    def solve(c2=None, f=None, tol=1e-12):
+        s = W.Solver(prob, periods=4, trajectory_bytes=1)
+        if c2 is not None:
+            for gi, c in enumerate(prob.split(c2)):
+                s.set_coefficient(gi, c)
+        if f is not None:
+            for gi, ff in enumerate(prob.split(f)):
+                s.set_forcing(gi, ff)
+        s.prepare()
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = s.solve(u, W.GMRES, tol=tol, max_it=3000, restart=400)
+        assert st.converged == 1, (st.status, st.residual, st.iterations)
+        return s, u
+
+    c2 = np.concatenate([c.ravel() for c in prob.c2])
+    f = np.concatenate([x.ravel() for x in prob.f])
+    _, up = solve(c2=np.concatenate([c.ravel() for c in G.perturbed_c2(prob)]), tol=1e-10)
+    d = P @ up.cpu().numpy()
+    s, u = solve()
+    r = P @ u.cpu().numpy() - d
+    g = torch.from_numpy(P.T @ r).cuda()
+    lam, gc2, gf, st = s.adjoint(u, g, tol=1e-12, max_it=3000, restart=400)
+    assert st.converged == 1
+    gc2 = gc2.cpu().numpy()
+    gf = gf.cpu().numpy()
+    rng = np.random.default_rng(2)
+
+    def J_of(c2v, fv):
+        _, u2 = solve(c2=c2v, f=fv)
+        rr = P @ u2.cpu().numpy() - d
+        return 0.5 * float(rr @ rr)
+
+    for kind in ("c2",) * 6 + ("f",) * 4:
+        dirn = rng.standard_normal(n)
+        if kind == "c2":
+            eps = 1e-5
+            jp, jm = J_of(c2 + eps * dirn * c2, f), J_of(c2 - eps * dirn * c2, f)
+            pred = float(gc2 @ (dirn * c2))
+        else:
+            eps = 1e-5 * np.max(np.abs(f))
+            jp, jm = J_of(c2, f + eps * dirn), J_of(c2, f - eps * dirn)
+            pred = float(gf @ dirn)
+        fd = (jp - jm) / (2 * eps)
+        assert abs(fd - pred) <= 1e-6 * max(abs(fd), abs(pred)), (kind, fd, pred)
