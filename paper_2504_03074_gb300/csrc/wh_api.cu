@@ -102,6 +102,13 @@ struct wh_ctx {
   std::vector<Tile> hftiles, hgtiles;
   std::vector<int32_t> fast_grids;  // grid of each map slot
   Tile *d_ftiles = nullptr, *d_gtiles = nullptr;
+  // batches: the same tile lists ordered by their instance's step count M (descending), so
+  // that the tiles of the instances still marching at step n form a prefix; mpre_*[n] is
+  // its length.  Used by the graph path when the gather is not folded (the folded gather
+  // numbers tiles in the original lists).
+  Tile *d_tiles_m = nullptr, *d_ftiles_m = nullptr, *d_gtiles_m = nullptr;
+  std::vector<int32_t> mpre_t, mpre_f, mpre_g;
+  bool msorted = false;
   // march control: [0] sticky error flag, [1] tile ticket, [2] blocks done
   int *d_err = nullptr;
   // launch layout fixed by wh_set_tuning / wh_autotune (-1: the library's choice)
@@ -280,6 +287,8 @@ void free_device(wh_ctx *ctx) {
   ctx->d_rcoef = ctx->d_adj = ctx->d_ckpt = ctx->d_traj = nullptr;
   ctx->ckpt_cap = ctx->traj_cap = 0;
   ctx->d_bar = nullptr;
+  ctx->d_tiles_m = ctx->d_ftiles_m = ctx->d_gtiles_m = nullptr;
+  ctx->msorted = false;
   // buffers allocated on first use must be allocated again after a new layout
   ctx->d_fcompact = nullptr;
   ctx->d_saved = nullptr;
@@ -955,18 +964,24 @@ void march_step(wh_ctx *ctx, int n, void *cur, void *oth, double fs,
                 const GatherArgs *gather = nullptr) {
   const MarchSet &S = ctx->set[ctx->active];
   const int order = ctx->opt.order;
+  // batches without the folded gather: only the prefix of instances still marching
+  const bool pre = ctx->msorted && !(gather && gather->nunits);
   if (uses_tma(ctx)) {
-    const int nf = (int)ctx->hftiles.size(), ngn = (int)ctx->hgtiles.size();
+    const int nf = pre ? ctx->mpre_f[n] : (int)ctx->hftiles.size();
+    const int ngn = pre ? ctx->mpre_g[n] : (int)ctx->hgtiles.size();
+    if (nf + ngn == 0) return;
     launch_march_tma(S.fp32, order, n == 0, std::min(S.tma_blocks, nf + ngn), ctx->stream,
-                     ctx->d_grids, ctx->d_ftiles, nf, S.maps, ctx->d_gtiles, ngn, ctx->d_mask,
-                     S.Wa, S.Wb, S.F, S.Wt, ctx->d_V, ctx->d_inst, n, fs, ctx->d_err,
-                     ctx->opt_spin_limit, gather && gather->nunits ? gather : nullptr);
+                     ctx->d_grids, pre ? ctx->d_ftiles_m : ctx->d_ftiles, nf, S.maps,
+                     pre ? ctx->d_gtiles_m : ctx->d_gtiles, ngn, ctx->d_mask, S.Wa, S.Wb, S.F,
+                     S.Wt, ctx->d_V, ctx->d_inst, n, fs, ctx->d_err, ctx->opt_spin_limit,
+                     gather && gather->nunits ? gather : nullptr);
     return;
   }
-  const int ntiles = (int)ctx->htiles.size();
+  const int ntiles = pre ? ctx->mpre_t[n] : (int)ctx->htiles.size();
+  if (ntiles == 0) return;
   launch_march(S.fp32, order, n == 0, std::min(ntiles, ctx->march_blocks), ntiles, ctx->stream,
-               ctx->d_grids, ctx->d_tiles, ctx->d_mask, cur, oth, ctx->d_F, ctx->d_Wt,
-               ctx->d_V, ctx->d_inst, n, fs, nullptr, gather);
+               ctx->d_grids, pre ? ctx->d_tiles_m : ctx->d_tiles, ctx->d_mask, cur, oth,
+               ctx->d_F, ctx->d_Wt, ctx->d_V, ctx->d_inst, n, fs, nullptr, gather);
 }
 
 wh_status launch_steps(wh_ctx *ctx, int forcing) {
@@ -2429,6 +2444,35 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
   CK(cudaMemcpy(ctx->d_tabs, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_ftabs, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_inst, ctx->hinst.data(), K * sizeof(InstDev), cudaMemcpyHostToDevice));
+  // batches: tile lists by descending M of their instance and the per-step prefix lengths
+  ctx->msorted = false;
+  if (K > 1) {
+    auto m_of = [&](const Tile &t) { return ctx->hinst[ctx->hgrids[t.grid].inst].M; };
+    auto order_by_m = [&](const std::vector<Tile> &src, Tile **dst,
+                          std::vector<int32_t> &pre) -> wh_status {
+      std::vector<Tile> v(src);
+      std::stable_sort(v.begin(), v.end(),
+                       [&](const Tile &a, const Tile &b) { return m_of(a) > m_of(b); });
+      std::vector<int64_t> hist((size_t)ctx->maxM + 1, 0);
+      for (const Tile &t : v) hist[(size_t)std::min(m_of(t), ctx->maxM)]++;
+      pre.assign((size_t)ctx->maxM, 0);
+      int64_t acc = 0;  // pre[n] = tiles whose instance has M > n
+      for (int n = ctx->maxM - 1; n >= 0; --n) {
+        acc += hist[(size_t)n + 1];
+        pre[(size_t)n] = (int32_t)acc;
+      }
+      if (v.empty()) return WH_OK;
+      wh_status e;
+      if (!*dst && (e = dalloc(ctx, dst, v.size()))) return e;
+      CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+      return WH_OK;
+    };
+    if ((st = order_by_m(ctx->htiles, &ctx->d_tiles_m, ctx->mpre_t)) ||
+        (st = order_by_m(ctx->hftiles, &ctx->d_ftiles_m, ctx->mpre_f)) ||
+        (st = order_by_m(ctx->hgtiles, &ctx->d_gtiles_m, ctx->mpre_g)))
+      return st;
+    ctx->msorted = true;
+  }
   // the plain copies above and those of the layout may still be in flight; the launches
   // below run on the context's non-blocking stream, which does not wait for them
   CK(cudaStreamSynchronize(cudaStreamLegacy));
