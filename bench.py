@@ -253,6 +253,20 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
                          "ms_per_iteration": t32 * 1e3,
                          "workload": "same disk-in-square workload, FP32 march, FP64 filter"}
     s32.close()
+    # several bodies: two ellipses (elliptic-coordinate grids) and a disk in a 1024^2
+    # background, order 4, omega 40: one iteration in FP64 and with the FP32 march
+    ep = G.ellipses_problem(nb=1024, omega=40.0, scale=2)
+    rec = {"workload": "two ellipses + a disk in [-2,2]^2: 1024^2 background + 3 body grids "
+                       "(%d points), order 4, omega 40" % ep.n_total}
+    for name, prec in (("fp64", WH.FP64), ("fp32", WH.FP32)):
+        se = WH.Solver(ep, stream=stream, precision=prec)
+        te = se.prepare()
+        tt = time_iterations(WH, torch, se, ep.n_total, stream, flush, 5)
+        rec[name] = {"value": te.n_active * te.M / tt / 1e9, "unit": "GLUP/s",
+                     "ms_per_iteration": tt * 1e3, "M": te.M}
+        se.close()
+    stage("forms: ellipses_1024")
+    out["ellipses_1024"] = rec
     # differentiation form: the transposed map S^T (the product of the adjoint GMRES) and
     # one gradient sweep (forward march from u kept whole in HBM, reverse sweep with the
     # c^2 and f gradients); g = 0 makes the adjoint GMRES return at once, so the call times

@@ -325,6 +325,183 @@ def check_explicit_interp(grids, interp, order):
 
 
 # ----------------------------------------------------------------------------------
+# Several bodies in a square: disks and ellipses, each wrapped in a body-fitted grid
+# ----------------------------------------------------------------------------------
+
+@dataclass
+class Body:
+    """A body in the background square: a disk (a == b) or an axis-aligned ellipse (a > b)
+    with semi-axes (a, b) centred at ``center``, wrapped in a body-fitted grid of nth x nr
+    points whose outer edge lies ``width`` further out along the x semi-axis (stretched
+    toward the body by ``beta``).  The background hole is the region whose radial grid
+    parameter is below ``cut`` (0: the body itself, 1: the grid's outer edge)."""
+
+    center: tuple
+    a: float
+    b: float
+    width: float
+    nth: int
+    nr: int
+    beta: float = 1.5
+    cut: float = 0.5
+    inner_bc: int = BC_NEUMANN
+
+
+class _BodyMap:
+    """The body grid's mapping x = G(t, s), t in [0, 1) around the body, s in [0, 1] out.
+
+    A disk uses polar coordinates, r(s) = a + width q(s); an ellipse uses elliptic
+    coordinates, x - c = f cosh(mu) cos(nu), y - c_y = f sinh(mu) sin(nu), f^2 = a^2 - b^2,
+    mu(s) = mu0 + (mu1 - mu0) q(s), nu = 2 pi t, with q(s) = (e^{beta s} - 1) / (e^beta - 1).
+    Both are orthogonal (the ellipse's conformal), as the Neumann ghost rule assumes."""
+
+    def __init__(self, body):
+        self.b = body
+        self.cx, self.cy = body.center
+        self.eb = math.exp(body.beta) - 1.0
+        if body.a < body.b:
+            raise ValueError("ellipses are taken with a >= b (x semi-axis the longer)")
+        self.polar = body.a == body.b
+        if self.polar:
+            self.r0, self.r1 = body.a, body.a + body.width
+        else:
+            self.f = math.sqrt(body.a ** 2 - body.b ** 2)
+            self.mu0 = math.atanh(body.b / body.a)
+            self.mu1 = math.acosh((body.a + body.width) / self.f)
+
+    def q(self, s):
+        return (np.exp(self.b.beta * s) - 1.0) / self.eb
+
+    def dq(self, s):
+        return self.b.beta * np.exp(self.b.beta * s) / self.eb
+
+    def lo_hi(self):
+        return (self.r0, self.r1) if self.polar else (self.mu0, self.mu1)
+
+    def xy(self, t, s):
+        lo, hi = self.lo_hi()
+        rho = lo + (hi - lo) * self.q(s)
+        th = 2.0 * np.pi * t
+        if self.polar:
+            return self.cx + rho * np.cos(th), self.cy + rho * np.sin(th)
+        return (self.cx + self.f * np.cosh(rho) * np.cos(th),
+                self.cy + self.f * np.sinh(rho) * np.sin(th))
+
+    def rx(self, t, s):
+        """dt/dx, dt/dy, ds/dx, ds/dy at parameter points (analytic)."""
+        lo, hi = self.lo_hi()
+        rho = lo + (hi - lo) * self.q(s)
+        drho_ds = (hi - lo) * self.dq(s)
+        th = 2.0 * np.pi * t
+        if self.polar:
+            c, sn = np.cos(th), np.sin(th)
+            return (-sn / (2.0 * np.pi * rho), c / (2.0 * np.pi * rho), c / drho_ds,
+                    sn / drho_ds)
+        # w = mu + i nu is analytic in z = x + i y with dw/dz = 1 / (f sinh w):
+        # mu_x = nu_y = Re w', nu_x = -mu_y = Im w'
+        w = rho + 1j * th
+        wp = 1.0 / (self.f * np.sinh(w))
+        mux, nux = wp.real, wp.imag
+        return nux / (2.0 * np.pi), mux / (2.0 * np.pi), mux / drho_ds, -nux / drho_ds
+
+    def param(self, x, y):
+        """Fractional (t n_th, s (n_r - 1)) indices of physical points, and the radial
+        parameter s itself (negative inside the body)."""
+        lo, hi = self.lo_hi()
+        if self.polar:
+            th = np.mod(np.arctan2(y - self.cy, x - self.cx), 2.0 * np.pi)
+            rho = np.hypot(x - self.cx, y - self.cy)
+        else:
+            # the principal branch has Re w >= 0 and Im w in (-pi, pi]
+            w = np.arccosh(((x - self.cx) + 1j * (y - self.cy)) / self.f)
+            rho, th = w.real, np.mod(w.imag, 2.0 * np.pi)
+        u = (rho - lo) / (hi - lo) * self.eb
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = np.where(u > -1.0, np.log1p(u) / self.b.beta, -np.inf)
+        return th / (2.0 * np.pi) * self.b.nth, s * (self.b.nr - 1), s
+
+
+def body_grid(name, body, order):
+    """The body-fitted grid of one Body: axis 0 periodic around the body (nth points),
+    axis 1 outward (nr points); the body is side axis1-lo, the outer order/2 lines are
+    interpolation points.  Inverse metrics analytic, on ghost lines too."""
+    m = _BodyMap(body)
+    g1 = order // 2
+    nth, nr = body.nth, body.nr
+    dt_, ds = 1.0 / nth, 1.0 / (nr - 1)
+    t = (np.arange(nth) * dt_)[None, :]
+    s_ext = (np.arange(-g1, nr + g1) * ds)[:, None]
+    rx = np.stack([np.broadcast_to(v, (nr + 2 * g1, nth)) for v in m.rx(t, s_ext)])
+    X, Y = m.xy(t, (np.arange(nr) * ds)[:, None])
+    X, Y = np.broadcast_to(X, (nr, nth)).copy(), np.broadcast_to(Y, (nr, nth)).copy()
+    mask = np.full((nr, nth), DISC, np.int8)
+    mask[nr - g1:, :] = INTERP
+    if body.inner_bc == BC_DIRICHLET:
+        mask[0, :] = DIRICHLET
+    bc = [BC_PERIODIC, BC_PERIODIC, body.inner_bc, BC_NONE]
+    g = Grid(name, CURVILINEAR, (nth, nr), bc, (dt_, ds), mask, np.stack([X, Y]), True,
+             np.ascontiguousarray(rx))
+    g.mapping = dict(body=body)
+    return g
+
+
+def bodies_in_square(nb, bodies, order, box=2.0):
+    """Cartesian background [-box, box]^2 (nb^2 points, Dirichlet) with holes cut for
+    several bodies, each wrapped in its body-fitted grid (Sec. 3.1's overset grid with
+    more than one curvilinear component).  Background points inside a body's cut become
+    interpolation points within order/2 index layers of a background discretization point
+    (donors on that body's grid), the rest unused; each body grid's outer order/2 lines
+    take donors on the background.  Donor stencils hold discretization points only
+    (explicit interpolation, checked).  Returns (grids, interp)."""
+    B = cartesian_grid("background", nb, nb, -box, box, -box, box, [BC_DIRICHLET] * 4, order)
+    maps = [_BodyMap(b) for b in bodies]
+    grids = [B] + [body_grid("body%d" % k, b, order) for k, b in enumerate(bodies)]
+    X, Y = B.xy
+    half = order // 2
+    # the body whose cut holds each background point (-1: none)
+    owner = np.full(X.shape, -1, np.int64)
+    for k, (m, b) in enumerate(zip(maps, bodies)):
+        _, _, s = m.param(X, Y)
+        inside = s < b.cut
+        if np.any(inside & (owner >= 0)):
+            raise ValueError("the cuts of two bodies overlap")
+        owner[inside] = k
+    active = owner < 0
+    near = np.zeros_like(active)
+    pad = np.pad(active, half)
+    for dj in range(-half, half + 1):
+        for di in range(-half, half + 1):
+            near |= pad[half + dj:half + dj + nb, half + di:half + di + nb]
+    B.mask[~active & near] = INTERP
+    B.mask[~active & ~near] = UNUSED
+    recv = []
+    for k, (m, b) in enumerate(zip(maps, bodies)):
+        A = grids[k + 1]
+        # background receivers in this body's cut <- body donors
+        jb, ib = np.nonzero((B.mask == INTERP) & (owner == k))
+        fi, fj, sr = m.param(X[jb, ib], Y[jb, ib])
+        if sr.size and not np.all(sr >= 0.0):
+            raise ValueError("body %d: background interpolation points lie inside the body "
+                             "(raise its cut or refine the background)" % k)
+        i0, j0, wx, wy = _donors(fi, fj, A, order, b.nr - 1 - half, True)
+        recv.append((0, ib, jb, k + 1, i0, j0, wx, wy))
+        # body receivers <- background donors
+        ja, ia = np.nonzero(A.mask == INTERP)
+        fi, fj = _cart_param(B, A.xy[0][ja, ia], A.xy[1][ja, ia])
+        i0, j0, wx, wy = _donors(fi, fj, B, order, nb - 1, False)
+        recv.append((k + 1, ia, ja, 0, i0, j0, wx, wy))
+    cols = list(zip(*recv))
+    interp = Interp(
+        np.concatenate([np.full(len(r[1]), r[0], np.int32) for r in recv]),
+        np.concatenate(cols[1]).astype(np.int32), np.concatenate(cols[2]).astype(np.int32),
+        np.concatenate([np.full(len(r[1]), r[3], np.int32) for r in recv]),
+        np.concatenate(cols[4]).astype(np.int32), np.concatenate(cols[5]).astype(np.int32),
+        np.concatenate(cols[6]), np.concatenate(cols[7]))
+    check_explicit_interp(grids, interp, order)
+    return grids, interp
+
+
+# ----------------------------------------------------------------------------------
 # Sources and coefficients
 # ----------------------------------------------------------------------------------
 
@@ -400,6 +577,53 @@ def disk_problem(nb=1024, nth=2048, nr=64, order=4, omega=40.0, seed=0, n_src=1,
                    name=f"disk-in-square-{nb}^2+{nth}x{nr}-o{order}",
                    meta=dict(sources=[s.tolist() for s in srcs], seed=seed,
                              bumps=[c.tolist() for c in centers]))
+
+
+def bodies_problem(nb, bodies, order=4, omega=10.0, seed=0, n_src=1, box=2.0, c_bumps=0,
+                   name="bodies-in-square"):
+    """Several bodies (disks, ellipses) in the square [-box, box]^2 with Gaussian source(s)
+    seeded in the background at least 0.3 from every body grid's outer edge."""
+    rng = np.random.default_rng(seed)
+    grids, interp = bodies_in_square(nb, bodies, order, box=box)
+    maps = [_BodyMap(b) for b in bodies]
+
+    def clear(p):
+        for m, b in zip(maps, bodies):
+            for dx, dy in ((0.3, 0), (-0.3, 0), (0, 0.3), (0, -0.3), (0, 0)):
+                if m.param(np.array([p[0] + dx]), np.array([p[1] + dy]))[2][0] <= 1.0:
+                    return False
+        return True
+
+    srcs = []
+    while len(srcs) < n_src:
+        p = rng.uniform(-0.8 * box, 0.8 * box, size=2)
+        if clear(p):
+            srcs.append(p)
+    f = []
+    for g in grids:
+        fg = np.zeros(g.mask.shape)
+        for x0 in srcs:
+            fg += gaussian(g.xy, x0, 1.0, 200.0)
+        f.append(fg)
+    c2 = None
+    if c_bumps:
+        centers = [rng.uniform(-0.9 * box, 0.9 * box, size=2) for _ in range(c_bumps)]
+        c2 = [bumps_c2(g.xy, centers) for g in grids]
+    return Problem(grids, interp, order, omega, f, c2,
+                   name=f"{name}-{nb}^2+{len(bodies)}-o{order}",
+                   meta=dict(sources=[q.tolist() for q in srcs], seed=seed))
+
+
+def ellipses_problem(nb=512, order=4, omega=20.0, seed=0, scale=1):
+    """Multi-object workload: two ellipses and a disk in [-2, 2]^2 with body-fitted grids
+    (``scale`` multiplies the body grids' resolution: at scale 1 they match a 512^2
+    background's spacing, at scale 2 a 1024^2 one's)."""
+    s = scale
+    bodies = [Body((-0.9, 0.55), 0.5, 0.25, 0.3, 320 * s, 24 * s),
+              Body((0.85, -0.6), 0.6, 0.35, 0.3, 384 * s, 24 * s),
+              Body((0.6, 1.05), 0.3, 0.3, 0.3, 256 * s, 24 * s)]
+    return bodies_problem(nb, bodies, order=order, omega=omega, seed=seed,
+                          name="ellipses-in-square")
 
 
 def sheared_torus_problem(n0=32, n1=28, order=4, omega=9.0, seed=0):

@@ -55,7 +55,18 @@ CASES = [
                                                            omega=7.0, n_src=2, width=0.6,
                                                            r_cut=0.7, seed=3),
      dict(periods=2, alpha_mode=1)),
+    # several bodies: two ellipses on elliptic-coordinate grids and a disk (4 grids)
+    ("ellipses-o4", lambda: G.ellipses_problem(nb=192, omega=12.0), {}),
+    ("ellipses-o4-Np3", lambda: G.ellipses_problem(nb=160, omega=8.0, seed=2),
+     dict(periods=3)),
 ]
+
+
+def _two_bodies(order):
+    """An ellipse (elliptic-coordinate grid) and a disk in a 64^2 background."""
+    bodies = [G.Body((-0.8, -0.3), 0.4, 0.22, 0.6, 64, 12, beta=1.0, cut=0.6),
+              G.Body((0.85, 0.45), 0.3, 0.3, 0.6, 56, 12, beta=1.0, cut=0.6)]
+    return G.bodies_problem(64, bodies, order=order, omega=4.0, seed=1)
 
 
 @pytest.mark.parametrize("mode", ["persistent", "graph"])
@@ -215,6 +226,22 @@ def test_gmres_reaches_direct_solution(torch, W):
     act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
     assert rel_err(u.cpu().numpy(), U, act) < 1e-9
     assert st.history[0] == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_gmres_reaches_direct_solution_two_bodies(torch, W, order):
+    """An ellipse and a disk in one background (three grids, two of them curvilinear):
+    GPU GMRES equals the direct solution of the discrete Helmholtz system."""
+    import dhs
+    prob = _two_bodies(order)
+    U = dhs.solve(prob)
+    s = W.Solver(prob)
+    s.prepare()
+    u = torch.zeros(prob.n_total, dtype=torch.float64, device="cuda")
+    st = s.solve(u, W.GMRES, tol=1e-12, max_it=400, restart=200)
+    assert st.converged == 1, (st.status, st.residual)
+    act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
+    assert rel_err(u.cpu().numpy(), U, act) < 1e-9
 
 
 def test_fpi_matches_oracle_iterates(torch, W, oracle_mod):

@@ -363,7 +363,16 @@ DHS_CASES = [
                                        r_cut=0.75), 1e-9),
     ("disk-o4", lambda: G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, width=0.8,
                                        r_cut=0.75), 1e-9),
+    ("ellipse-disk-o2", lambda: _two_bodies(2), 1e-9),
+    ("ellipse-disk-o4", lambda: _two_bodies(4), 1e-9),
 ]
+
+
+def _two_bodies(order):
+    """An ellipse (elliptic-coordinate grid) and a disk in a 64^2 background."""
+    bodies = [G.Body((-0.8, -0.3), 0.4, 0.22, 0.6, 64, 12, beta=1.0, cut=0.6),
+              G.Body((0.85, 0.45), 0.3, 0.3, 0.6, 56, 12, beta=1.0, cut=0.6)]
+    return G.bodies_problem(64, bodies, order=order, omega=4.0, seed=1)
 
 
 @pytest.mark.parametrize("name,make,tol", DHS_CASES, ids=[c[0] for c in DHS_CASES])
