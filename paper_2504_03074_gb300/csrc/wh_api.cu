@@ -109,6 +109,17 @@ struct wh_ctx {
   Tile *d_tiles_m = nullptr, *d_ftiles_m = nullptr, *d_gtiles_m = nullptr;
   std::vector<int32_t> mpre_t, mpre_f, mpre_g;
   bool msorted = false;
+  // the same for the separate ghost-rule + interpolation launch: items and receivers by
+  // descending M, prefix lengths per level (level L runs for instances with M >= L); the
+  // host copies of the receivers' donor lists that the ordering starts from
+  BcItem *d_bc_m = nullptr;
+  int32_t *d_didx_m = nullptr, *d_rinst_m = nullptr;
+  double *d_dw_m = nullptr;
+  int64_t *d_ridx_m = nullptr;
+  std::vector<int32_t> mpre_bc, mpre_r;
+  std::vector<int32_t> h_didx, h_rinst;
+  std::vector<double> h_dw;
+  std::vector<int64_t> h_ridx;
   // march control: [0] sticky error flag, [1] tile ticket, [2] blocks done
   int *d_err = nullptr;
   // launch layout fixed by wh_set_tuning / wh_autotune (-1: the library's choice)
@@ -288,6 +299,10 @@ void free_device(wh_ctx *ctx) {
   ctx->ckpt_cap = ctx->traj_cap = 0;
   ctx->d_bar = nullptr;
   ctx->d_tiles_m = ctx->d_ftiles_m = ctx->d_gtiles_m = nullptr;
+  ctx->d_bc_m = nullptr;
+  ctx->d_didx_m = ctx->d_rinst_m = nullptr;
+  ctx->d_dw_m = nullptr;
+  ctx->d_ridx_m = nullptr;
   ctx->msorted = false;
   // buffers allocated on first use must be allocated again after a new layout
   ctx->d_fcompact = nullptr;
@@ -850,7 +865,11 @@ wh_status build_layout(wh_ctx *ctx) {
     std::vector<int32_t> rinst(ridx.size(), 0);
     for (int64_t r = 0; r < ctx->nrecv; ++r) rinst[r] = ctx->hgrids[ctx->rg[r]].inst;
     CK(cudaMemcpy(ctx->d_rinst, rinst.data(), rinst.size() * 4, cudaMemcpyHostToDevice));
+    ctx->h_rinst = rinst;
   }
+  ctx->h_didx = didx;
+  ctx->h_dw = dw;
+  ctx->h_ridx = ridx;
   CK(cudaMemcpy(ctx->d_tiles, ctx->htiles.data(), ctx->htiles.size() * sizeof(Tile),
                 cudaMemcpyHostToDevice));
   if (!ctx->hftiles.empty())
@@ -999,6 +1018,15 @@ wh_status launch_steps(wh_ctx *ctx, int forcing) {
   void *Wa = ctx->d_Wa, *Wb = ctx->d_Wb;
   auto bcg = [&](void *W, int level) {
     if (bg_blocks == 0) return;
+    if (ctx->msorted) {  // batches: the items and receivers of instances still marching
+      const int nb_l = ctx->mpre_bc[(size_t)level], nr_l = ctx->mpre_r[(size_t)level];
+      const int bcb = (nb_l + 255) / 256, gb = (nr_l * lanes + 255) / 256;
+      if (bcb + gb == 0) return;
+      launch_bc_gather(f32, order, bcb + gb, s, ctx->d_bc_m, nb_l, bcb, ctx->d_didx_m,
+                       ctx->d_dw_m, ctx->d_ridx_m, ctx->d_rinst_m, nr_l, W, ctx->d_F,
+                       ctx->d_inst, level, fs);
+      return;
+    }
     launch_bc_gather(f32, order, bg_blocks, s, ctx->d_bc, nbc, bc_blocks, ctx->d_didx, ctx->d_dw,
                      ctx->d_ridx, ctx->d_rinst, (int)ctx->nrecv, W, ctx->d_F, ctx->d_inst, level,
                      fs);
@@ -2471,6 +2499,52 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
         (st = order_by_m(ctx->hftiles, &ctx->d_ftiles_m, ctx->mpre_f)) ||
         (st = order_by_m(ctx->hgtiles, &ctx->d_gtiles_m, ctx->mpre_g)))
       return st;
+    // ghost-rule items and receivers by descending M; pre[L] = entries with M >= L
+    auto prefix = [&](const std::vector<int> &ms, std::vector<int32_t> &pre) {
+      std::vector<int64_t> hist((size_t)ctx->maxM + 2, 0);
+      for (int m : ms) hist[(size_t)std::min(m, ctx->maxM)]++;
+      pre.assign((size_t)ctx->maxM + 1, 0);
+      int64_t acc = 0;
+      for (int L = ctx->maxM; L >= 0; --L) {
+        acc += hist[(size_t)L];
+        pre[(size_t)L] = (int32_t)acc;
+      }
+    };
+    {
+      const int64_t nr = ctx->nrecv;
+      const int ND = (order + 1) * (order + 1);
+      std::vector<int64_t> perm((size_t)nr);
+      for (int64_t r = 0; r < nr; ++r) perm[(size_t)r] = r;
+      auto mr = [&](int64_t r) { return ctx->hinst[ctx->h_rinst[(size_t)r]].M; };
+      std::stable_sort(perm.begin(), perm.end(),
+                       [&](int64_t a, int64_t b) { return mr(a) > mr(b); });
+      std::vector<int32_t> di((size_t)std::max<int64_t>(nr, 1) * ND, 0), ri((size_t)std::max<int64_t>(nr, 1), 0);
+      std::vector<double> dwv((size_t)std::max<int64_t>(nr, 1) * ND, 0.0);
+      std::vector<int64_t> rx((size_t)std::max<int64_t>(nr, 1), 0);
+      std::vector<int> ms((size_t)nr);
+      for (int64_t k = 0; k < nr; ++k) {
+        const int64_t r = perm[(size_t)k];
+        for (int d = 0; d < ND; ++d) {
+          di[(size_t)(k * ND + d)] = ctx->h_didx[(size_t)(r * ND + d)];
+          dwv[(size_t)(k * ND + d)] = ctx->h_dw[(size_t)(r * ND + d)];
+        }
+        rx[(size_t)k] = ctx->h_ridx[(size_t)r];
+        ri[(size_t)k] = ctx->h_rinst[(size_t)r];
+        ms[(size_t)k] = mr(r);
+      }
+      prefix(ms, ctx->mpre_r);
+      if (nr) {
+        if ((!ctx->d_didx_m && (st = dalloc(ctx, &ctx->d_didx_m, di.size()))) ||
+            (!ctx->d_dw_m && (st = dalloc(ctx, &ctx->d_dw_m, dwv.size()))) ||
+            (!ctx->d_ridx_m && (st = dalloc(ctx, &ctx->d_ridx_m, rx.size()))) ||
+            (!ctx->d_rinst_m && (st = dalloc(ctx, &ctx->d_rinst_m, ri.size()))))
+          return st;
+        CK(cudaMemcpy(ctx->d_didx_m, di.data(), di.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_dw_m, dwv.data(), dwv.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_ridx_m, rx.data(), rx.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_rinst_m, ri.data(), ri.size() * 4, cudaMemcpyHostToDevice));
+      }
+    }
     ctx->msorted = true;
   }
   // the plain copies above and those of the layout may still be in flight; the launches
@@ -2522,6 +2596,34 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
                    ctx->d_coef, ctx->d_c2);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  if (ctx->msorted && !ctx->hbc.empty()) {
+    // the ghost-rule items by descending M, taken from the device copy, whose Dirichlet
+    // coefficients bc_coef_kernel has just filled in
+    const size_t nbc = ctx->hbc.size();
+    std::vector<BcItem> dev(nbc);
+    CK(cudaMemcpy(dev.data(), ctx->d_bc, nbc * sizeof(BcItem), cudaMemcpyDeviceToHost));
+    std::vector<size_t> perm(nbc);
+    for (size_t k = 0; k < nbc; ++k) perm[k] = k;
+    auto mb = [&](size_t k) { return ctx->hinst[ctx->hbc[k].inst].M; };
+    std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) { return mb(a) > mb(b); });
+    std::vector<BcItem> v(nbc);
+    std::vector<int64_t> hist((size_t)ctx->maxM + 2, 0);
+    for (size_t k = 0; k < nbc; ++k) {
+      v[k] = dev[perm[k]];
+      hist[(size_t)std::min(mb(perm[k]), ctx->maxM)]++;
+    }
+    ctx->mpre_bc.assign((size_t)ctx->maxM + 1, 0);
+    int64_t acc = 0;  // items with M >= L
+    for (int L = ctx->maxM; L >= 0; --L) {
+      acc += hist[(size_t)L];
+      ctx->mpre_bc[(size_t)L] = (int32_t)acc;
+    }
+    if (!ctx->d_bc_m && (st = dalloc(ctx, &ctx->d_bc_m, nbc))) return st;
+    CK(cudaMemcpyAsync(ctx->d_bc_m, v.data(), nbc * sizeof(BcItem), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  } else if (ctx->msorted) {
+    ctx->mpre_bc.assign((size_t)ctx->maxM + 1, 0);
+  }
   ctx->prepared = true;
   ctx->adj_ready = false;
   if (ctx->adj_graph) {  // it holds this preparation's step weights and constraint lists
