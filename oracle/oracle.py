@@ -65,6 +65,7 @@ def lib(openmp=False):
             L.or_add_grid.argtypes = [vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, C.c_double,
                                       C.c_double, vp, vp, vp]
             L.or_set_forcing.argtypes = [vp, C.c_int, vp]
+            L.or_set_boundary.argtypes = [vp, C.c_int, vp]
             L.or_set_interp.argtypes = [vp, C.c_long] + [vp] * 8
             L.or_prepare.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
             L.or_iterate.restype = C.c_int
@@ -119,6 +120,11 @@ class Oracle:
                 raise ValueError(self.L.or_error(self.h).decode())
             f = np.ascontiguousarray(problem.f[gi], np.float64)
             self.L.or_set_forcing(self.h, gi, _p(f))
+            gb = getattr(problem, "g", None)
+            if gb is not None and gb[gi] is not None:
+                ga = np.ascontiguousarray(gb[gi], np.float64)
+                self._keep.append(ga)
+                self.L.or_set_boundary(self.h, gi, _p(ga))
         it = problem.interp
         arrs = [np.ascontiguousarray(a, np.int32) for a in
                 (it.recv_grid, it.recv_i, it.recv_j, it.donor_grid, it.donor_i0, it.donor_j0)]
@@ -129,7 +135,8 @@ class Oracle:
 
     def prepare(self, omega, cfl=0.9, periods=1, alpha_mode=0):
         out = (C.c_double * 7)()
-        self.L.or_prepare(self.h, omega, cfl, periods, alpha_mode, out)
+        if self.L.or_prepare(self.h, omega, cfl, periods, alpha_mode, out) != 0:
+            raise ValueError(self.L.or_error(self.h).decode())
         self.omega = omega
         self.time = TimeSetup(list(out))
         return self.time

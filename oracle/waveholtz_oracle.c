@@ -29,13 +29,21 @@
  * derivatives, frozen-coefficient CFL on curvilinear grids) are listed in the design
  * notes and restated at each function below.
  *
+ * Boundary data: Dirichlet sides carry W_b = g_b cos(omega_e t) with g given per boundary
+ * point (or_set_boundary; 0 when not given), switched off with the forcing (the map
+ * W_h(., 0) has g = 0).  The Helmholtz solution then takes the value g on those sides.
+ *
  * Ghost-point rules (the paper defers them to its reference on high-order overset wave
- * solvers); boundary data g = 0 throughout:
- *   order 2, Dirichlet: W_b = 0; ghosts are never read and stay 0.
+ * solvers):
+ *   order 2, Dirichlet: W_b = g_b cos(omega_e t); ghosts are never read and stay 0.
  *   order 2, Neumann:   centred normal derivative D0 W = 0  =>  W_{-1} = W_{+1}.
- *   order 4, Dirichlet: W_b = 0; ghosts G1, G2 from the compatibility condition
- *       c^2 (a_nn D_nn W + b_n D_n W)_b = f_b cos(omega_e t)
- *     (tangential terms vanish with g = 0) and the extrapolation D+^5 W_{-2} = 0.
+ *   order 4, Dirichlet: W_b = g_b cos(omega_e t); ghosts G1, G2 from the compatibility
+ *     condition (the scheme at the boundary point, where D+tD-t of g cos(omega_e t) is
+ *     -omega^2 g cos(omega_e t) exactly by the time-step recipe)
+ *       c^2 (a_nn D_nn W + b_n D_n W)_b = (f_b - omega^2 g_b - c^2 D_tt g_b) cos(omega_e t)
+ *     with D_tt the fourth-order second difference of g along the side (centred, wrapped
+ *     on a periodic side, one-sided with six points at the two ends: exact for quintics),
+ *     Cartesian grids only when g is given, and the extrapolation D+^5 W_{-2} = 0.
  *   order 4, Neumann: fourth-order centred normal derivative D_n W = 0 and the same
  *     extrapolation.
  * The boundary grid lines must be orthogonal to the boundary, and a Neumann side may
@@ -65,6 +73,8 @@ typedef struct {
   double *rx;    /* curvilinear: 4 extended arrays dr1/dx, dr1/dy, dr2/dx, dr2/dy */
   double *c2;    /* extended; c(x)^2 */
   double *f;     /* extended */
+  double *gb;    /* extended; Dirichlet boundary data g (used at Dirichlet points) */
+  int has_g;
   double *coef;  /* curvilinear: 5 extended arrays c^2 a11, c^2 a12, c^2 a22, c^2 b1, c^2 b2 */
   long offset;   /* offset of this grid in the concatenated compact vector */
 } or_grid;
@@ -236,8 +246,39 @@ static void side_point(const or_grid *G, int s, int t, int k, int *i, int *j) {
   if (a == 0) { *i = nrm; *j = t; } else { *i = t; *j = nrm; }
 }
 
+/* Fourth-order second difference of the boundary data along side s at tangential index t
+ * (undivided by h^2 * 12): centred where the five points exist (wrapping on a periodic
+ * side), else the six-point one-sided formulas exact for polynomials of degree 5. */
+static double side_d2_g(const or_grid *G, int s, int t) {
+  int ta = 1 - s / 2, n = G->n[ta];
+  int periodic = G->bc[2 * ta] == OR_BC_PERIODIC;
+  double v[6];
+  if (periodic || (t >= 2 && t <= n - 3)) {
+    static const double c[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
+    double acc = 0.0;
+    for (int k = -2; k <= 2; ++k) {
+      int i, j;
+      side_point(G, s, t + k, 0, &i, &j);
+      acc += c[k + 2] * G->gb[at(G, i, j)];
+    }
+    return acc;
+  }
+  static const double e0[6] = {45.0, -154.0, 214.0, -156.0, 61.0, -10.0};
+  static const double e1[6] = {10.0, -15.0, -4.0, 14.0, -6.0, 1.0};
+  const int lo = t < 2;
+  for (int k = 0; k < 6; ++k) {
+    int i, j;
+    side_point(G, s, lo ? k : n - 1 - k, 0, &i, &j);
+    v[k] = G->gb[at(G, i, j)];
+  }
+  const double *c = (lo ? t : n - 1 - t) == 0 ? e0 : e1;
+  double acc = 0.0;
+  for (int k = 0; k < 6; ++k) acc += c[k] * v[k];
+  return acc;
+}
+
 /* Fill the ghost points of every physical side at time t; fcos = cos(omega_e t) when the
- * forcing is on and 0 when it is off (the compatibility condition carries f). */
+ * forcing is on and 0 when it is off (the compatibility condition carries f and g). */
 static void apply_bc(const or_problem *P, int gidx, double *W, double fcos) {
   const or_grid *G = &P->G[gidx];
   long E = ext_size(G);
@@ -286,7 +327,13 @@ static void apply_bc(const or_problem *P, int gidx, double *W, double fcos) {
         /* D_nn: (-G2 + 16G1 - 30U0 + 16U1 - U2) / (12 h^2);
          * D_n : sgn (8(U1 - G1) - (U2 - G2)) / (12 h) */
         double A[2][2] = {{16.0 * A2 - 8.0 * B1, -A2 + B1}, {-5.0, 1.0}};
-        double r[2] = {G->f[qb] * fcos - A2 * (-30.0 * U[0] + 16.0 * U[1] - U[2]) -
+        double rhs_b = G->f[qb];
+        if (G->has_g) {
+          double ht = G->h[1 - a];
+          rhs_b -= P->omega * P->omega * G->gb[qb] +
+                   G->c2[qb] * side_d2_g(G, s, t) / (12.0 * ht * ht);
+        }
+        double r[2] = {rhs_b * fcos - A2 * (-30.0 * U[0] + 16.0 * U[1] - U[2]) -
                            B1 * (8.0 * U[1] - U[2]),
                        -(10.0 * U[0] - 10.0 * U[1] + 5.0 * U[2] - U[3])};
         double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
@@ -365,6 +412,7 @@ int or_add_grid(or_problem *P, int n0, int n1, int kind, const int *bc, int orth
   G->mask = (signed char *)calloc(E, 1);
   G->c2 = (double *)malloc(E * sizeof(double));
   G->f = (double *)calloc(E, sizeof(double));
+  G->gb = (double *)calloc(E, sizeof(double));
   for (long q = 0; q < E; ++q) G->c2[q] = 1.0;
   for (int j = 0; j < n1; ++j)
     for (int i = 0; i < n0; ++i) {
@@ -390,6 +438,15 @@ int or_set_forcing(or_problem *P, int gidx, const double *f) {
   return 0;
 }
 
+int or_set_boundary(or_problem *P, int gidx, const double *g) {
+  or_grid *G = &P->G[gidx];
+  for (int j = 0; j < G->n[1]; ++j)
+    for (int i = 0; i < G->n[0]; ++i) G->gb[at(G, i, j)] = g[(long)j * G->n[0] + i];
+  G->has_g = 1;
+  P->prepared = 0;
+  return 0;
+}
+
 int or_set_interp(or_problem *P, long n, const int *rg, const int *ri, const int *rj,
                   const int *dg, const int *di, const int *dj, const double *wx,
                   const double *wy) {
@@ -412,6 +469,21 @@ int or_set_interp(or_problem *P, long n, const int *rg, const int *ri, const int
 /* Time setup for frequency omega (Recipe OmegaTildeExplicit; Eq. alphad).
  * alpha_mode 0: alpha_d; 1: alpha = 1/2.  out[0..6] = dt, omega_e, alpha, Nt, M, dt_max, Tbar. */
 int or_prepare(or_problem *P, double omega, double cfl, int Np, int alpha_mode, double *out) {
+  for (int g = 0; g < P->ngrids; ++g) {
+    const or_grid *G = &P->G[g];
+    if (!G->has_g || P->order != 4) continue;
+    for (int s = 0; s < 4; ++s) {
+      if (G->bc[s] != OR_BC_DIRICHLET) continue;
+      if (G->kind != OR_CARTESIAN) {
+        snprintf(P->err, sizeof P->err, "boundary data on a curvilinear Dirichlet side (order 4)");
+        return -1;
+      }
+      if (G->n[1 - s / 2] < 6) {
+        snprintf(P->err, sizeof P->err, "a side with boundary data needs 6 points (order 4)");
+        return -1;
+      }
+    }
+  }
   for (int g = 0; g < P->ngrids; ++g)
     if (P->G[g].kind == OR_CURVILINEAR) precompute_coeffs(P, &P->G[g]);
   double dtmax = cfl * dt_bound(P);
@@ -455,7 +527,7 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
         long q = at(G, i, j);
         signed char m = G->mask[q];
         double v = v_in[G->offset + (long)j * G->n[0] + i];
-        W0[g][q] = (m == OR_DISC || m == OR_INTERP) ? v : 0.0;
+        W0[g][q] = (m == OR_DISC || m == OR_INTERP) ? v : (m == OR_DIRICHLET ? fs * G->gb[q] : 0.0);
       }
     apply_bc(P, g, W0[g], fs);
   }
@@ -486,6 +558,12 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
             Wp[g][q] = W0[g][q] + 0.5 * dt * dt * (L - fs * G->f[q]);
           else /* W^{n+1} = 2W^n - W^{n-1} + dt^2 (c^2 L W^n - f cos(omega_e t^n)) */
             Wp[g][q] = 2.0 * W0[g][q] - Wm[g][q] + dt * dt * (L - fs * G->f[q] * cos(we * tn));
+        }
+      /* Dirichlet points: the boundary data at t^{n+1} */
+      for (int j = 0; j < G->n[1]; ++j)
+        for (int i = 0; i < G->n[0]; ++i) {
+          long q = at(G, i, j);
+          if (G->mask[q] == OR_DIRICHLET) Wp[g][q] = fs * G->gb[q] * cos(we * (n + 1) * dt);
         }
       apply_bc(P, g, Wp[g], fs * cos(we * (n + 1) * dt));
     }
@@ -555,7 +633,7 @@ void or_free(or_problem *P) {
   if (!P) return;
   for (int g = 0; g < P->ngrids; ++g) {
     or_grid *G = &P->G[g];
-    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->coef);
+    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->gb); free(G->coef);
   }
   free(P->rg); free(P->ri); free(P->rj); free(P->dg); free(P->di); free(P->dj);
   free(P->wx); free(P->wy);

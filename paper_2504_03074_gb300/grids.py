@@ -100,6 +100,7 @@ class Problem:
     c2: list | None = None        # per-grid compact c(x)^2, or None for c = 1
     name: str = ""
     meta: dict = field(default_factory=dict)
+    g: list | None = None         # per-grid compact Dirichlet data (read at Dirichlet points)
 
     @property
     def n_active(self):
@@ -624,6 +625,16 @@ def ellipses_problem(nb=512, order=4, omega=20.0, seed=0, scale=1):
               Body((0.6, 1.05), 0.3, 0.3, 0.3, 256 * s, 24 * s)]
     return bodies_problem(nb, bodies, order=order, omega=omega, seed=seed,
                           name="ellipses-in-square")
+
+
+def with_boundary_data(problem, fn):
+    """The same problem with Dirichlet data g = fn(x, y) on every Dirichlet point (zero
+    elsewhere): the Helmholtz solution takes the value g there."""
+    import copy
+    p = copy.copy(problem)
+    p.g = [np.where(g.mask == DIRICHLET, fn(g.xy[0], g.xy[1]), 0.0) for g in problem.grids]
+    p.name = problem.name + "-g"
+    return p
 
 
 def sheared_torus_problem(n0=32, n1=28, order=4, omega=9.0, seed=0):

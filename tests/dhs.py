@@ -15,6 +15,10 @@ with a sparse LU.  Ghost rules (g = 0, orthogonal boundary lines):
 order 2 Neumann: U_{-1} - U_{+1} = 0;
 order 4 Neumann: 8(U_1 - G_1) - (U_2 - G_2) = 0 and D+^5 G_2 = 0;
 order 4 Dirichlet: c^2 (a_nn D_nn U + b_n D_n U)_b = f_b and D+^5 G_2 = 0.
+With Dirichlet data g (``problem.g``): U = g at Dirichlet points, and the order-4
+compatibility row's right side is f_b - omega^2 g_b - c^2 (D_tt g)_b (Cartesian grids),
+D_tt the fourth-order second difference along the side: centred, wrapped on a periodic
+side, one-sided six-point at the ends.
 """
 from __future__ import annotations
 
@@ -28,6 +32,19 @@ from paper_2504_03074_gb300 import grids as G
 D2W = {2: np.array([1.0, -2.0, 1.0]), 4: np.array([-1.0, 16.0, -30.0, 16.0, -1.0]) / 12.0}
 D1W = {2: np.array([-1.0, 0.0, 1.0]) / 2.0, 4: np.array([1.0, -8.0, 0.0, 8.0, -1.0]) / 12.0}
 EXTRAP5 = np.array([1.0, -5.0, 10.0, -10.0, 5.0, -1.0])   # D+^5 on G2, G1, U0, U1, U2, U3
+# fourth-order second differences (times 12 h^2) one-sided at the first and second point
+ONE_SIDED_D2 = {0: np.array([45.0, -154.0, 214.0, -156.0, 61.0, -10.0]),
+                1: np.array([10.0, -15.0, -4.0, 14.0, -6.0, 1.0])}
+
+
+def side_d2(line, t, periodic, h):
+    """Fourth-order second difference of the values `line` along a side at index t."""
+    n = len(line)
+    if periodic or 2 <= t <= n - 3:
+        return sum(D2W[4][k + 2] * line[(t + k) % n] for k in range(-2, 3)) / h ** 2
+    if t < 2:
+        return float(ONE_SIDED_D2[t] @ line[:6]) / (12.0 * h ** 2)
+    return float(ONE_SIDED_D2[n - 1 - t] @ line[::-1][:6]) / (12.0 * h ** 2)
 
 
 class Layout:
@@ -145,6 +162,9 @@ def assemble(problem, omega):
                     put(row, row, 1.0)
                 else:  # Dirichlet or unused
                     put(row, row, 1.0)
+                    gb = getattr(problem, "g", None)
+                    if m == G.DIRICHLET and gb is not None and gb[gi] is not None:
+                        rhs[row] = gb[gi][j, i]
         # ghost rules
         for s in range(4):
             code = g.bc[s]
@@ -189,6 +209,13 @@ def assemble(problem, omega):
                     for k, col in enumerate(seq):
                         put(gq[0], col, ann * D2W[4][k] / h ** 2 + bn * D1W[4][k] / h)
                     rhs[gq[0]] = problem.f[gi][bj, bi]
+                    gb = getattr(problem, "g", None)
+                    if gb is not None and gb[gi] is not None:
+                        assert g.kind == G.CARTESIAN
+                        line = gb[gi][:, bi] if a == 0 else gb[gi][bj, :]
+                        per = g.bc[2 * (1 - a)] == G.BC_PERIODIC
+                        rhs[gq[0]] -= omega ** 2 * gb[gi][bj, bi] + \
+                            c2[bj, bi] * side_d2(line, t, per, g.h[1 - a])
     # interpolation rows
     it = problem.interp
     w = order + 1
