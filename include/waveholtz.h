@@ -254,6 +254,22 @@ wh_status wh_set_interp3(wh_ctx *ctx, const wh_interp3_desc *interp);
  * c^2 Lap u + omega^2 u = f; the scheme applies -f cos(omega_e t). */
 wh_status wh_set_forcing(wh_ctx *ctx, int32_t grid_id, const double *f);
 
+/* Dirichlet boundary data g of grid grid_id (host, n0*n1 compact values, copied; read at
+ * the grid's WH_DIRICHLET points, ignored elsewhere; NULL removes them): the Helmholtz
+ * solution takes u = g there (the paper's problem statement with g != 0, which its
+ * experiments leave at g = 0).  The wave march holds W = g cos(omega_e t) at those points
+ * while the forcing is on (the map W_h(., 0) keeps g = 0, so GMRES and the eigensolver are
+ * unchanged); at order 4 the compatibility ghost rule's right side becomes
+ * f_b - omega^2 g_b - c^2 (D_tt g)_b with D_tt the fourth-order second difference along
+ * the side (centred; wrapped on a periodic side; six-point one-sided at the ends), since
+ * the scheme's second time difference of g cos(omega_e t) is exactly -omega^2 g cos.
+ * Takes effect at the next wh_prepare.  Two-dimensional contexts; differentiation and
+ * wh_set_deflation (Algorithm 3's inflation) then return WH_ERR_STATE, while
+ * wh_set_deflation_basis stays exact.  Errors: WH_ERR_ARG (bad grid, non-finite data),
+ * WH_ERR_GRID (order 4: a curvilinear grid with a Dirichlet side, or a Dirichlet side of
+ * fewer than 6 points), WH_ERR_STATE (3D context). */
+wh_status wh_set_boundary_data(wh_ctx *ctx, int32_t grid_id, const double *g);
+
 /* Prepare one frequency per instance (batching: several independent Helmholtz problems,
  * each with its own grids, omega, time step, Nt and alpha, advanced by the same kernel
  * launches; an instance stops after its own M steps).  omegas: host array of one value per

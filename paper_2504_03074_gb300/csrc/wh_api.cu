@@ -32,6 +32,7 @@ struct HostGrid {
   wh_grid_desc d;
   std::vector<int8_t> mask;
   std::vector<double> rx, c2, f;
+  std::vector<double> gdata;  // Dirichlet boundary data (compact), empty when none
   int g0 = 0, g1 = 0;
 };
 
@@ -113,6 +114,8 @@ struct wh_ctx {
   // descending M, prefix lengths per level (level L runs for instances with M >= L); the
   // host copies of the receivers' donor lists that the ordering starts from
   BcItem *d_bc_m = nullptr;
+  // Dirichlet boundary data of every grid in the state layout (null when no grid has any)
+  double *d_gb = nullptr;
   int32_t *d_didx_m = nullptr, *d_rinst_m = nullptr;
   double *d_dw_m = nullptr;
   int64_t *d_ridx_m = nullptr;
@@ -299,6 +302,7 @@ void free_device(wh_ctx *ctx) {
   ctx->ckpt_cap = ctx->traj_cap = 0;
   ctx->d_bar = nullptr;
   ctx->d_tiles_m = ctx->d_ftiles_m = ctx->d_gtiles_m = nullptr;
+  ctx->d_gb = nullptr;
   ctx->d_bc_m = nullptr;
   ctx->d_didx_m = ctx->d_rinst_m = nullptr;
   ctx->d_dw_m = nullptr;
@@ -904,6 +908,28 @@ wh_status build_layout(wh_ctx *ctx) {
   CK(cudaMemcpy(ctx->d_didx, didx.data(), didx.size() * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_dw, dw.data(), dw.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_ridx, ridx.data(), ridx.size() * 8, cudaMemcpyHostToDevice));
+  {
+    // Dirichlet boundary data: one FP64 array in the state layout, read at Dirichlet points
+    bool any = false;
+    for (const auto &H : ctx->grids) any |= !H.gdata.empty();
+    if (any) {
+      std::vector<double> gb((size_t)off, 0.0);
+      for (size_t g = 0; g < ctx->grids.size(); ++g) {
+        const HostGrid &H = ctx->grids[g];
+        if (H.gdata.empty()) continue;
+        const DevGrid &G = ctx->hgrids[g];
+        for (int j = 0; j < G.n1; ++j)
+          for (int i = 0; i < G.n0; ++i)
+            if (H.mask[(size_t)j * G.n0 + i] == WH_DIRICHLET)
+              gb[(size_t)ext_index(G, i, j)] = H.gdata[(size_t)j * G.n0 + i];
+      }
+      wh_status e;
+      if ((e = dalloc(ctx, &ctx->d_gb, (size_t)off))) return e;
+      CK(cudaMemcpy(ctx->d_gb, gb.data(), gb.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    for (size_t g = 0; g < ctx->grids.size(); ++g)
+      ctx->hgrids[g].gb = ctx->grids[g].gdata.empty() ? nullptr : ctx->d_gb;
+  }
   CK(cudaMemcpy(ctx->d_grids, ctx->hgrids.data(), ctx->hgrids.size() * sizeof(DevGrid),
                 cudaMemcpyHostToDevice));
   {
@@ -1157,7 +1183,7 @@ wh_status iterate_device(wh_ctx *ctx, int forcing, const double *vin, double *vo
   const int64_t nb = (ctx->total + blk - 1) / blk;
   const int ng = (int)ctx->hgrids.size();
   launch_init(is_fp32(ctx), (unsigned)nb, ctx->stream, ctx->d_grids, ng, ctx->d_mask, vin,
-              ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst);
+              ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst, forcing ? 1.0 : 0.0);
   CK(cudaGetLastError());
   // tickets start at zero (the kernels also leave them so)
   CK(cudaMemsetAsync(ctx->d_err + 1, 0, 2 * sizeof(int), ctx->stream));
@@ -1688,7 +1714,7 @@ void forward_start(wh_ctx *ctx, const double *u, double *W) {
   cudaStream_t s = ctx->stream;
   const int ng = (int)ctx->hgrids.size();
   launch_init(false, (unsigned)((ctx->total + 255) / 256), s, ctx->d_grids, ng, ctx->d_mask, u, W,
-              ctx->d_V, ctx->total, ctx->d_inst);
+              ctx->d_V, ctx->total, ctx->d_inst, 1.0);
   const int bc_blocks = ((int)ctx->hbc.size() + 255) / 256;
   const int bg_blocks = bc_blocks + (int)((ctx->nrecv * (order == 4 ? 8 : 4) + 255) / 256);
   if (bg_blocks)
@@ -2139,7 +2165,7 @@ wh_status rayleigh_lam2(wh_ctx *ctx, const double *y, double *w0, double *w1, do
   const int ng = (int)ctx->hgrids.size();
   const int64_t nb = (ctx->total + 255) / 256;
   launch_init(false, (unsigned)nb, s, ctx->d_grids, ng, ctx->d_mask, y, S0.Wa, ctx->d_V,
-              ctx->total, ctx->d_inst);
+              ctx->total, ctx->d_inst, 0.0);
   const int nbc = (int)ctx->hbc.size();
   if (nbc > 0) {
     const int bcb = (nbc + 255) / 256;
@@ -2370,6 +2396,35 @@ wh_status wh_set_forcing(wh_ctx *ctx, int32_t gid, const double *f) {
   return WH_OK;
 }
 
+wh_status wh_set_boundary_data(wh_ctx *ctx, int32_t gid, const double *g) {
+  if (!ctx) return WH_ERR_ARG;
+  if (ctx->dim == 3)
+    return fail(ctx, WH_ERR_STATE, "boundary data are available on 2D contexts");
+  if (gid < 0 || gid >= (int)ctx->grids.size())
+    return fail(ctx, WH_ERR_ARG, "bad boundary data arguments");
+  HostGrid &H = ctx->grids[gid];
+  const int64_t n = (int64_t)H.d.n[0] * H.d.n[1];
+  if (g)
+    for (int64_t q = 0; q < n; ++q)
+      if (!std::isfinite(g[q])) return fail(ctx, WH_ERR_ARG, "non-finite boundary data");
+  if (g && ctx->opt.order == 4 && H.d.kind != WH_CARTESIAN)
+    for (int sd = 0; sd < 4; ++sd)
+      if (H.d.bc[sd] == WH_BC_DIRICHLET)
+        return fail(ctx, WH_ERR_GRID,
+                    "boundary data on a curvilinear Dirichlet side at order 4 are not supported");
+  if (g && ctx->opt.order == 4)
+    for (int sd = 0; sd < 4; ++sd)
+      if (H.d.bc[sd] == WH_BC_DIRICHLET && H.d.n[1 - sd / 2] < 6)
+        return fail(ctx, WH_ERR_GRID, "a side with boundary data needs 6 points at order 4");
+  if (g)
+    H.gdata.assign(g, g + n);
+  else
+    H.gdata.clear();
+  ctx->dirty = true;
+  ctx->prepared = false;
+  return WH_OK;
+}
+
 // Prepare one frequency per instance: (a2) the operator coefficients and the per-instance
 // frozen-coefficient stability bounds on the device, (a1) the time setup of each instance
 // (Recipe OmegaTildeExplicit, alpha_d), the device step tables and the stencil weights.
@@ -2591,6 +2646,45 @@ static wh_status prepare_instances(wh_ctx *ctx, const double *omegas) {
                       ctx->d_c2, S.Wt, ctx->hinst[G.inst].dt2);
   }
   const int nbc = (int)ctx->hbc.size();
+  if (nbc && ctx->d_gb) {
+    // Dirichlet data on order-4 sides: the compatibility condition's extra right side
+    // -omega^2 g_b - c^2 (D_tt g)_b, D_tt the fourth-order second difference along the side
+    // (centred; wrapped on a periodic side; six-point one-sided at the two ends)
+    for (int k = 0; k < nbc; ++k) {
+      BcItem &it = ctx->hbc[(size_t)k];
+      it.fg = 0.0;
+      const HostGrid &H = ctx->grids[(size_t)ctx->hbc_grid[(size_t)k]];
+      if (it.type != 2 || H.gdata.empty()) continue;
+      const DevGrid &G = ctx->hgrids[(size_t)ctx->hbc_grid[(size_t)k]];
+      const int a = ctx->hbc_axis[(size_t)k], ta = 1 - a;
+      const int64_t o = it.u[0] - G.base;
+      const int j = (int)(o / G.pitch) - G.g1, i = (int)(o % G.pitch) - G.g0;
+      const int nt = ta == 0 ? G.n0 : G.n1, t = ta == 0 ? i : j;
+      const bool per = ta == 0 ? G.per0 : G.per1;
+      auto gline = [&](int q) {
+        q = per ? ((q % nt) + nt) % nt : q;
+        const int ii = ta == 0 ? q : i, jj = ta == 0 ? j : q;
+        return H.gdata[(size_t)jj * G.n0 + ii];
+      };
+      double d2 = 0.0;
+      if (per || (t >= 2 && t <= nt - 3)) {
+        d2 = -gline(t - 2) + 16.0 * gline(t - 1) - 30.0 * gline(t) + 16.0 * gline(t + 1) -
+             gline(t + 2);
+      } else {
+        static const double e0[6] = {45.0, -154.0, 214.0, -156.0, 61.0, -10.0};
+        static const double e1[6] = {10.0, -15.0, -4.0, 14.0, -6.0, 1.0};
+        const bool lo = t < 2;
+        const double *c = (lo ? t : nt - 1 - t) == 0 ? e0 : e1;
+        for (int q = 0; q < 6; ++q) d2 += c[q] * gline(lo ? q : nt - 1 - q);
+      }
+      const double ht = ta == 0 ? G.h0 : G.h1;
+      const double c2b = H.c2.empty() ? 1.0 : H.c2[(size_t)j * G.n0 + i];
+      const double om = omegas[G.inst];
+      it.fg = -om * om * H.gdata[(size_t)j * G.n0 + i] - c2b * d2 / (12.0 * ht * ht);
+    }
+    CK(cudaMemcpyAsync(ctx->d_bc, ctx->hbc.data(), (size_t)nbc * sizeof(BcItem),
+                       cudaMemcpyHostToDevice, s));
+  }
   if (nbc)
     launch_bc_coef(nbc, s, ctx->d_bc, ctx->d_bc_grid, ctx->d_bc_axis, ctx->d_bc_hi, ctx->d_grids,
                    ctx->d_coef, ctx->d_c2);
@@ -2809,6 +2903,10 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
   const int K = ctx->defl_k;
   if (K > 0) {
     if (ctx->ninst != 1) return finish(fail(ctx, WH_ERR_STATE, "deflation needs one instance"));
+    if (!ctx->defl_basis && ctx->d_gb)
+      return finish(fail(ctx, WH_ERR_STATE,
+                         "Algorithm 3's inflation takes g = 0; with Dirichlet data use "
+                         "wh_set_deflation_basis (exact for any data)"));
     const double om2 = ctx->ti.omega * ctx->ti.omega;
     for (double l2 : ctx->defl_lam2)
       if (!ctx->defl_basis && std::fabs(om2 - l2) <= kResonanceRel * om2)
@@ -3517,6 +3615,8 @@ static wh_status adj_check(wh_ctx *ctx) {
     return fail(ctx, WH_ERR_STATE, "differentiation is not available on 3D contexts");
   if (!ctx->prepared) return fail(ctx, WH_ERR_STATE, "wh_prepare first");
   if (ctx->ninst != 1) return fail(ctx, WH_ERR_ARG, "differentiation needs a single instance");
+  if (ctx->d_gb)
+    return fail(ctx, WH_ERR_STATE, "differentiation needs zero Dirichlet data (g = 0)");
   return WH_OK;
 }
 
@@ -3856,7 +3956,7 @@ wh_status wh_profile_kernels(wh_ctx *ctx, int32_t reps, double *ms, int32_t *cou
                          ctx->d_inst, 1, 1.0);
       else if (kind == 2)
         launch_init(f32, (unsigned)((ctx->total + blk - 1) / blk), s, ctx->d_grids, ng,
-                    ctx->d_mask, ctx->d_work, ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst);
+                    ctx->d_mask, ctx->d_work, ctx->d_Wa, ctx->d_V, ctx->total, ctx->d_inst, 1.0);
       else if (kind == 3)
         launch_finish(f32, (unsigned)((ctx->ncompact + blk - 1) / blk), s, ctx->d_grids, ng,
                       ctx->d_mask, ctx->d_V, ctx->d_Wa, ctx->d_Wb, ctx->d_inst,

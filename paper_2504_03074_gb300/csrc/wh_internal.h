@@ -43,6 +43,10 @@ struct DevGrid {
   // [centre, axis0 offset 1, axis0 offset 2, axis1 offset 1, axis1 offset 2]
   double cw[5];
   float cwf[5];  // the same weights rounded to FP32 (the FP32 march reads these)
+  // Dirichlet boundary data g (FP64, indexed by state index like the state arrays), or
+  // null when the grid has none: Dirichlet points then hold g cos(omega_e t) with the
+  // forcing on
+  const double *gb;
 };
 
 // One ghost-rule item: the ghost points next to one boundary point (Sec. 3.2 ghost
@@ -54,6 +58,8 @@ struct BcItem {
   int32_t inst;      // instance of the item's grid
   double A2, B1;     // Dirichlet order 4: a_nn/(12 h^2), +-b_n/(12 h) (c^2 folded)
   double inv;        // 1 / (11 A2 - 3 B1)
+  double fg;         // Dirichlet order 4 with boundary data: -omega^2 g_b - c^2 (D_tt g)_b,
+                     // added to f_b on the compatibility condition's right side (0 without)
 };
 
 // Time tables of one instance on the device (Recipe OmegaTildeExplicit per instance).
@@ -181,7 +187,7 @@ cudaError_t launch_iteration(bool fp32, int order, int nblocks, cudaStream_t s,
                              GridBarrier *bar);
 void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
                  const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
-                 const InstDev *inst);
+                 const InstDev *inst, double fs);
 void launch_finish(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
                    const int8_t *mask, const double *V, const void *Wa, const void *Wb,
                    const InstDev *inst, double *vout, int64_t ncompact);

@@ -75,6 +75,17 @@ __device__ __forceinline__ float step_fc<float>(const InstDev &I, int n, double 
 // Per-point arithmetic shared by the graph path and the persistent kernel.
 // ---------------------------------------------------------------------------------
 
+// A Dirichlet point with boundary data at step n -> n + 1: the filter takes its level-n
+// value (like an interpolation point's), and its level n + 1 is the data g cos(omega_e
+// t^{n+1}) (fcos1 = that cosine times the forcing switch).
+template <typename T>
+__device__ __forceinline__ void dirichlet_step(const DevGrid &G, int64_t p, const T *Wn,
+                                               T *Wout, double *V, double wf_cur,
+                                               double fcos1) {
+  V[p] = fma(wf_cur, to_f64(Wn[p]), V[p]);
+  Wout[p] = (T)(fcos1 * G.gb[p]);
+}
+
 // One time step at point (i, j) of grid G (Eq. WaveSchemeexplicit), fused with the filter:
 //   FIRST: W^1 = (sum_k w_k W^0_k)/2 - fc f            (fc = dt^2/2, or 0 without forcing)
 //   else : W^{n+1} = sum_k w_k W^n_k - W^{n-1} - fc f   (fc = dt^2 cos(omega_e t^n))
@@ -89,13 +100,18 @@ __device__ __forceinline__ void march_point(const DevGrid &G, int i, int j,
                                             const int8_t *__restrict__ mask,
                                             const T *Wn, const T *Wprev, T *Wout,
                                             const T *__restrict__ F, const T *__restrict__ Wt,
-                                            double *V, T fc, double wf_new, double wf_cur) {
+                                            double *V, T fc, double wf_new, double wf_cur,
+                                            double fcos1) {
   constexpr int R = ORDER / 2;
   const int64_t row = row_off(G, j);
   const int64_t p = row + i;
   const int8_t mk = mask[p];
   if (mk == 2) {
     V[p] = fma(wf_cur, to_f64(Wn[p]), V[p]);
+    return;
+  }
+  if (mk == 3) {
+    if (G.gb) dirichlet_step(G, p, Wn, Wout, V, wf_cur, fcos1);
     return;
   }
   if (mk != 1) return;
@@ -186,7 +202,7 @@ __device__ __forceinline__ void bc_item(const BcItem &it, T *W, const T *__restr
   if (it.type == 1) {
     G1 = (18.0 * U1 - 10.0 * U0 - 6.0 * U2 + U3) * (1.0 / 3.0);
   } else {
-    const double Fb = to_f64(F[it.u[0]]) * fcos;
+    const double Fb = (to_f64(F[it.u[0]]) + it.fg) * fcos;
     G1 = (Fb - it.A2 * (-30.0 * U0 + 16.0 * U1 - U2) - it.B1 * (8.0 * U1 - U2) +
           (it.A2 - it.B1) * E) * it.inv;
   }
@@ -277,6 +293,7 @@ __global__ void __launch_bounds__(kTileX *kTileY, 5)
     if (I.active && n < I.M && i < G.n0) {
       const T fc = step_fc<T>(I, n, fs, FIRST);
       const double wf_new = I.wf[n + 1], wf_cur = I.wf[n];
+      const double fcos1 = fs * I.cosn[n + 1];
       if (sizeof(T) == 4 && G.stencil == kConstCross && !G.per0 && !G.per1) {
         // FP32 march, constant weights, no wrap: the ghost layers (width order/2) hold every
         // neighbour, so neighbour addresses are fixed offsets from the point (same
@@ -295,6 +312,10 @@ __global__ void __launch_bounds__(kTileX *kTileY, 5)
           const int8_t mk = mask[p];
           if (mk == 2) {
             V[p] = fma(wf_cur, to_f64(Wn[p]), V[p]);
+            continue;
+          }
+          if (mk == 3) {
+            if (G.gb) dirichlet_step(G, p, Wn, Wout, V, wf_cur, fcos1);
             continue;
           }
           if (mk != 1) continue;
@@ -320,7 +341,7 @@ __global__ void __launch_bounds__(kTileX *kTileY, 5)
           const int j = t.j0 + (int)threadIdx.y + m * kTileY;
           if (j < G.n1)
             march_point<T, ORDER, FIRST, NOF>(G, i, j, mask, Wn, Wprev, Wout, F, Wt, V, fc,
-                                              wf_new, wf_cur);
+                                              wf_new, wf_cur, fcos1);
         }
       }
     }
@@ -447,6 +468,8 @@ struct TmaTileInfo {
   T fc, c0, x1, x2, y1, y2;
   int ni, nj;     // points of the tile inside the grid (ragged edges)
   int live;       // 0: the tile's instance is past its M or switched off
+  const double *gb;  // the grid's Dirichlet data (or null) and its factor at t^{n+1}
+  double fcos1;
 };
 
 // Every block first walks its strided share of the fast tiles (blockIdx.x, + gridDim.x, ...;
@@ -493,6 +516,8 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     f.wf_new = I.wf[n + 1];
     f.wf_cur = I.wf[n];
     f.fc = step_fc<T>(I, n, fs, FIRST);
+    f.gb = G.gb;
+    f.fcos1 = fs * I.cosn[n + 1];
     f.c0 = grid_w<T>(G, 0);
     f.x1 = grid_w<T>(G, 1);
     f.x2 = grid_w<T>(G, 2);
@@ -570,6 +595,13 @@ __global__ void __launch_bounds__(kTileX *kTileY)
           V[p] = fma(wf_cur, to_f64(w[0]), sV[q]);
           continue;
         }
+        if (mk == 3) {
+          if (f.gb) {
+            V[p] = fma(wf_cur, to_f64(w[0]), sV[q]);
+            Wout[p] = (T)(f.fcos1 * f.gb[p]);
+          }
+          continue;
+        }
         if (mk != 1) continue;
         T a = FIRST ? c0 * w[0] : fma(c0, w[0], -sWp[q]);
         a = fma(x1, w[-1], a);
@@ -618,7 +650,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
         const int j = t.j0 + (int)threadIdx.y + m * kTileY;
         if (j < G.n1)
           march_point<T, ORDER, FIRST>(G, i, j, mask, Wn, Wout, Wout, F, Wt, V, fc, wf_new,
-                                       wf_cur);
+                                       wf_cur, fs * I.cosn[n + 1]);
       }
     }
     if (ga.nunits) {  // one of the general tile's gsplit parts has written level n + 1
@@ -688,7 +720,8 @@ template <typename T>
 __device__ __forceinline__ void init_point(const DevGrid *__restrict__ grids, int ngrids,
                                            const int8_t *__restrict__ mask,
                                            const double *v, T *W0, double *V,
-                                           int64_t p, const InstDev *__restrict__ inst) {
+                                           int64_t p, const InstDev *__restrict__ inst,
+                                           double fs) {
   int g = 0;
   while (g + 1 < ngrids && p >= grids[g + 1].base) ++g;
   const DevGrid &G = grids[g];
@@ -702,6 +735,8 @@ __device__ __forceinline__ void init_point(const DevGrid *__restrict__ grids, in
   double val = 0.0;
   if ((m == 1 || m == 2) && i >= 0 && i < G.n0 && j >= 0 && j < G.n1)
     val = v[G.cbase + (int64_t)j * G.n0 + i];
+  else if (m == 3 && G.gb)  // Dirichlet data at t = 0
+    val = fs * G.gb[p];
   W0[p] = (T)val;
   V[p] = m == 1 ? w0 * (double)(T)val : 0.0;
 }
@@ -709,9 +744,10 @@ __device__ __forceinline__ void init_point(const DevGrid *__restrict__ grids, in
 template <typename T>
 __global__ void init_kernel(const DevGrid *__restrict__ grids, int ngrids,
                             const int8_t *__restrict__ mask, const double *__restrict__ v,
-                            T *W0, double *V, int64_t total, const InstDev *__restrict__ inst) {
+                            T *W0, double *V, int64_t total, const InstDev *__restrict__ inst,
+                            double fs) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < total) init_point<T>(grids, ngrids, mask, v, W0, V, p, inst);
+  if (p < total) init_point<T>(grids, ngrids, mask, v, W0, V, p, inst, fs);
 }
 
 // v_out (compact) = V at active points, 0 at unused points; interpolation points first
@@ -733,7 +769,8 @@ __device__ __forceinline__ void finish_point(const DevGrid *__restrict__ grids, 
   const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
   const int8_t m = mask[p];
   const T *WM = (I.M % 2 == 0) ? Wa : Wb;
-  vout[c] = m == 2 ? fma(I.wf[I.M], to_f64(WM[p]), V[p]) : (m != 0 ? V[p] : 0.0);
+  const bool last = m == 2 || (m == 3 && G.gb);  // their level M is not in V yet
+  vout[c] = last ? fma(I.wf[I.M], to_f64(WM[p]), V[p]) : (m != 0 ? V[p] : 0.0);
 }
 
 template <typename T>
@@ -803,7 +840,7 @@ __device__ __forceinline__ double bc_value(const BcItem &it, const T *W, const T
   if (it.type == 1) {
     G1 = (18.0 * U1 - 10.0 * U0 - 6.0 * U2 + U3) * (1.0 / 3.0);
   } else {
-    const double Fb = to_f64(F[it.u[0]]) * fcos;
+    const double Fb = (to_f64(F[it.u[0]]) + it.fg) * fcos;
     G1 = (Fb - it.A2 * (-30.0 * U0 + 16.0 * U1 - U2) - it.B1 * (8.0 * U1 - U2) +
           (it.A2 - it.B1) * E) * it.inv;
   }
@@ -849,7 +886,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
   // init: W^0 = v, V = w_0 W^0 (receivers' V accumulates from the first step on); no tile
   // has completed a step
   for (int64_t p = gtid; p < A.total; p += nthreads)
-    init_point<T>(A.grids, A.ngrids, A.mask, v_in, Wa, A.V, p, A.inst);
+    init_point<T>(A.grids, A.ngrids, A.mask, v_in, Wa, A.V, p, A.inst, A.fs);
   for (int64_t t = gtid; t < A.ntiles; t += nthreads) A.tile_done[t] = 0;
   if (!grid_sync(bar, nb, A.spin_limit)) return;
   // Dataflow over tickets k = n * ntiles + tile, handed out in increasing order.  Ticket
@@ -945,6 +982,13 @@ __global__ void __launch_bounds__(kTileX *kTileY)
             A.V[p] = fma(wf_cur, to_f64(wc), A.V[p]);
             continue;
           }
+          if (mk == 3) {
+            if (G.gb) {
+              A.V[p] = fma(wf_cur, to_f64(wc), A.V[p]);
+              oth[p] = (T)(A.fs * I.cosn[n + 1] * G.gb[p]);
+            }
+            continue;
+          }
           if (mk != 1) continue;
           T a;
           if (G.stencil == kConstCross) {
@@ -1016,7 +1060,9 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     const int64_t p = G.base + (int64_t)(j + G.g1) * G.pitch + (i + G.g0);
     const int8_t m = A.mask[p];
     double val = 0.0;
-    if (m == 1 || m == 3) val = A.V[p];
+    if (m == 1 || (m == 3 && !G.gb)) val = A.V[p];
+    else if (m == 3)  // Dirichlet data: the level-M contribution is not in V yet
+      val = fma(I.wf[I.M], to_f64(WM[p]), A.V[p]);
     else if (m == 2)
       val = fma(I.wf[I.M], recv_value<T, ORDER>(A.recv_of[p], A.didx, A.dw, WM), A.V[p]);
     v_out[c] = val;
@@ -1623,12 +1669,13 @@ void launch_bc_gather(bool fp32, int order, int blocks, cudaStream_t s, const Bc
 
 void launch_init(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,
                  const int8_t *mask, const double *v, void *W0, double *V, int64_t total,
-                 const InstDev *inst) {
+                 const InstDev *inst, double fs) {
   if (fp32)
-    init_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (float *)W0, V, total, inst);
+    init_kernel<float><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (float *)W0, V, total, inst,
+                                              fs);
   else
     init_kernel<double><<<blocks, 256, 0, s>>>(grids, ngrids, mask, v, (double *)W0, V, total,
-                                               inst);
+                                               inst, fs);
 }
 
 void launch_finish(bool fp32, unsigned blocks, cudaStream_t s, const DevGrid *grids, int ngrids,

@@ -652,8 +652,9 @@ def batch_problems(problems):
     keeps its data and gets instance i; the batch's omega is the list of omegas."""
     import copy
     order = problems[0].order
-    grids, f, c2, recv = [], [], [], []
+    grids, f, c2, recv, gb = [], [], [], [], []
     any_c2 = any(p.c2 is not None for p in problems)
+    any_g = any(getattr(p, "g", None) is not None for p in problems)
     goff = 0
     for k, p in enumerate(problems):
         assert p.order == order
@@ -663,6 +664,8 @@ def batch_problems(problems):
             grids.append(g2)
             f.append(p.f[gi])
             c2.append(p.c2[gi] if p.c2 is not None else np.ones(g.mask.shape))
+            pg = getattr(p, "g", None)
+            gb.append(pg[gi] if pg is not None else None)
         it = p.interp
         recv.append((it.recv_grid + goff, it.recv_i, it.recv_j, it.donor_grid + goff,
                      it.donor_i0, it.donor_j0, it.wx, it.wy))
@@ -673,7 +676,8 @@ def batch_problems(problems):
     return Problem(grids, interp, order, [p.omega for p in problems], f,
                    c2 if any_c2 else None, name=f"batch-{len(problems)}",
                    meta=dict(members=[p.name for p in problems],
-                             sizes=[p.n_total for p in problems]))
+                             sizes=[p.n_total for p in problems]),
+                   g=gb if any_g else None)
 
 
 def batch_disk_problem(n_inst=256, seed=0, nb_range=(256, 1024), omega_range=(10.0, 50.0),

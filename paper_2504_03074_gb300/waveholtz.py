@@ -92,7 +92,8 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["wh_options_default", "wh_create", "wh_destroy", "wh_last_error", "wh_set_stream",
-           "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_prepare", "wh_iterate",
+           "wh_add_grid", "wh_set_interp", "wh_set_forcing", "wh_set_boundary_data",
+           "wh_prepare", "wh_iterate",
            "wh_iterate_host", "wh_solve", "wh_dot", "wh_get_time_info", "wh_last_launch_count",
            "wh_profile_kernels", "wh_multidot_noalloc", "wh_prepare_batch", "wh_solve_batch", "wh_apply_adjoint", "wh_adjoint",
            "wh_set_coefficient", "wh_set_tuning", "wh_autotune", "wh_add_grid3",
@@ -128,6 +129,7 @@ def lib():
     L.wh_set_interp3.argtypes = [vp, C.POINTER(Interp3Desc)]
     L.wh_set_deflation.argtypes = [vp, C.c_int32, vp, vp]
     L.wh_set_forcing.argtypes = [vp, C.c_int32, vp]
+    L.wh_set_boundary_data.argtypes = [vp, C.c_int32, vp]
     L.wh_prepare.argtypes = [vp, C.c_double, C.POINTER(TimeInfo)]
     L.wh_prepare_batch.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(TimeInfo)]
     L.wh_iterate.argtypes = [vp, C.c_int32, vp, vp]
@@ -264,6 +266,10 @@ class Solver:
             self._check(self.L.wh_add_grid(self.h, C.byref(d), C.byref(gid)))
             f = np.ascontiguousarray(problem.f[gi], np.float64)
             self._check(self.L.wh_set_forcing(self.h, gid.value, _ptr(f)))
+            gb = getattr(problem, "g", None)
+            if gb is not None and gb[gi] is not None:
+                ga = np.ascontiguousarray(gb[gi], np.float64)
+                self._check(self.L.wh_set_boundary_data(self.h, gid.value, _ptr(ga)))
         it = problem.interp
         arrs = [np.ascontiguousarray(a, np.int32) for a in
                 (it.recv_grid, it.recv_i, it.recv_j, it.donor_grid, it.donor_i0, it.donor_j0)]
@@ -482,6 +488,11 @@ class Solver:
         """Replace the forcing of one grid (host array); re-run prepare() afterwards."""
         arr = np.ascontiguousarray(f, np.float64)
         self._check(self.L.wh_set_forcing(self.h, gid, _ptr(arr)))
+
+    def set_boundary_data(self, gid, g):
+        """Dirichlet data of one grid (host array, or None to remove); re-run prepare()."""
+        arr = None if g is None else np.ascontiguousarray(g, np.float64)
+        self._check(self.L.wh_set_boundary_data(self.h, gid, _ptr(arr)))
 
     def dot(self, x, y):
         out = C.c_double()

@@ -325,3 +325,36 @@ def test_state_validation_on_host(W):
     assert L.wh_set_state(h, None, 0) == -1
     assert L.wh_set_state(h, buf.ctypes.data, buf.size) == -3  # not prepared
     L.wh_destroy(h)
+
+
+def test_boundary_data_validation_on_host(W):
+    """wh_set_boundary_data checks its arguments without touching the device: a bad grid
+    or non-finite data is refused and leaves the context as it was; NULL removes the data;
+    order-4 curvilinear grids with a Dirichlet side and 3D contexts refuse data."""
+    L = W.lib()
+    prob = G.unit_square_problem(16, 4, 3.0)
+    h = _ctx(W, 4)
+    d, keep = _desc(W, prob.grids[0])
+    gid = C.c_int32()
+    assert L.wh_add_grid(h, C.byref(d), C.byref(gid)) == 0
+    good = np.ones(16 * 16)
+    bad = good.copy()
+    bad[5] = np.nan
+    assert L.wh_set_boundary_data(h, 1, good.ctypes.data) == -1
+    assert L.wh_set_boundary_data(h, 0, bad.ctypes.data) == -1
+    assert L.wh_set_boundary_data(h, 0, good.ctypes.data) == 0
+    assert L.wh_set_boundary_data(h, 0, None) == 0
+    L.wh_destroy(h)
+    A = G.annulus_grid("annulus", 64, 10, 0.5, 0.8, 1.5, 4, inner_bc=G.BC_DIRICHLET)
+    h = _ctx(W, 4)
+    d, keep = _desc(W, A)
+    assert L.wh_add_grid(h, C.byref(d), C.byref(gid)) == 0
+    assert L.wh_set_boundary_data(h, 0, np.ones(64 * 10).ctypes.data) == -7
+    L.wh_destroy(h)
+    from paper_2504_03074_gb300 import grids3 as G3
+    h = _ctx(W, order=2)
+    cube = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
+    d3, keep3 = _desc3(W, cube)
+    assert L.wh_add_grid3(h, C.byref(d3), C.byref(gid)) == 0
+    assert L.wh_set_boundary_data(h, 0, np.ones(9 ** 3).ctypes.data) == -3
+    L.wh_destroy(h)
