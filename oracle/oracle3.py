@@ -60,6 +60,7 @@ def lib(openmp=False):
             L.o3_add_grid.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
                                       C.c_double, C.c_double, C.c_double, vp, vp, vp]
             L.o3_set_forcing.argtypes = [vp, C.c_int, vp]
+            L.o3_set_boundary.argtypes = [vp, C.c_int, vp]
             L.o3_set_interp.argtypes = [vp, C.c_long] + [vp] * 11
             L.o3_prepare.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
             L.o3_iterate.restype = C.c_int
@@ -101,6 +102,11 @@ class Oracle3:
                 raise ValueError(self.L.o3_error(self.h).decode())
             f = np.ascontiguousarray(problem.f[gi], np.float64)
             self.L.o3_set_forcing(self.h, gi, _p(f))
+            gb = getattr(problem, "g", None)
+            if gb is not None and gb[gi] is not None:
+                ga = np.ascontiguousarray(gb[gi], np.float64)
+                self._keep.append(ga)
+                self.L.o3_set_boundary(self.h, gi, _p(ga))
         it = problem.interp
         arrs = [np.ascontiguousarray(a, np.int32) for a in
                 (it.recv_grid, it.recv_i, it.recv_j, it.recv_k, it.donor_grid, it.donor_i0,

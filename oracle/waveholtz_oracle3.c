@@ -24,9 +24,12 @@
  *   - tensor-product Lagrange interpolation from 3 x 3 x 3 donor stencils (Sec. 3.1);
  *   - the trapezoid-rule filter (Eq. updateDiscreteExplicit, Sec. 4.2), T-bar = Np Nt dt.
  *
+ * Boundary data: Dirichlet points carry W_b = g_b cos(omega_e t) with g given per point
+ * (o3_set_boundary; 0 when not given), switched off with the forcing.
+ *
  * Ghost rules at second order (the paper defers them to its reference on overset wave
- * solvers); boundary data g = 0:
- *   Dirichlet: W_b = 0; ghosts are never read.
+ * solvers):
+ *   Dirichlet: W_b = g_b cos(omega_e t); ghosts are never read.
  *   Neumann:   centred normal derivative D0 W = 0 along the boundary's normal grid axis,
  *              i.e. W_{-1} = W_{+1}.  This is the normal derivative when the normal grid
  *              axis is orthogonal to the two tangential axes, which is required.
@@ -58,6 +61,7 @@ typedef struct {
   signed char *mask; /* extended */
   double *rx;      /* curvilinear: 9 extended arrays, rx[(3 k + m) E + q] = dr_k / dx_m */
   double *c2, *f;  /* extended */
+  double *gb;      /* extended; Dirichlet boundary data (read at Dirichlet points) */
   double *coef;    /* curvilinear: C_N extended arrays */
   long offset;
 } o3_grid;
@@ -275,6 +279,7 @@ int o3_add_grid(o3_problem *P, int n0, int n1, int n2, int kind, const int *bc, 
   G->mask = (signed char *)calloc(E, 1);
   G->c2 = (double *)malloc(E * sizeof(double));
   G->f = (double *)calloc(E, sizeof(double));
+  G->gb = (double *)calloc(E, sizeof(double));
   for (long q = 0; q < E; ++q) G->c2[q] = 1.0;
   for (int k = 0; k < n2; ++k)
     for (int j = 0; j < n1; ++j)
@@ -300,6 +305,15 @@ int o3_set_forcing(o3_problem *P, int gidx, const double *f) {
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i)
         G->f[at(G, i, j, k)] = f[((long)k * G->n[1] + j) * G->n[0] + i];
+  return 0;
+}
+
+int o3_set_boundary(o3_problem *P, int gidx, const double *g) {
+  o3_grid *G = &P->G[gidx];
+  for (int k = 0; k < G->n[2]; ++k)
+    for (int j = 0; j < G->n[1]; ++j)
+      for (int i = 0; i < G->n[0]; ++i)
+        G->gb[at(G, i, j, k)] = g[((long)k * G->n[1] + j) * G->n[0] + i];
   return 0;
 }
 
@@ -369,7 +383,7 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
           long q = at(G, i, j, k);
           signed char m = G->mask[q];
           double v = v_in[G->offset + ((long)k * G->n[1] + j) * G->n[0] + i];
-          W0[g][q] = (m == O3_DISC || m == O3_INTERP) ? v : 0.0;
+          W0[g][q] = (m == O3_DISC || m == O3_INTERP) ? v : (m == O3_DIRICHLET ? fs * G->gb[q] : 0.0);
         }
     apply_bc(P, g, W0[g]);
   }
@@ -399,6 +413,13 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
               Wp[g][q] = W0[g][q] + 0.5 * dt * dt * (L - fs * G->f[q]);
             else
               Wp[g][q] = 2.0 * W0[g][q] - Wm[g][q] + dt * dt * (L - fs * G->f[q] * cos(we * tn));
+          }
+      /* Dirichlet points: the boundary data at t^{n+1} */
+      for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+          for (int i = 0; i < G->n[0]; ++i) {
+            long q = at(G, i, j, k);
+            if (G->mask[q] == O3_DIRICHLET) Wp[g][q] = fs * G->gb[q] * cos(we * (n + 1) * dt);
           }
       apply_bc(P, g, Wp[g]);
     }
@@ -464,7 +485,7 @@ void o3_free(o3_problem *P) {
   if (!P) return;
   for (int g = 0; g < P->ngrids; ++g) {
     o3_grid *G = &P->G[g];
-    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->coef);
+    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->gb); free(G->coef);
   }
   free(P->rg); free(P->ri); free(P->rj); free(P->rk);
   free(P->dg); free(P->di); free(P->dj); free(P->dk);

@@ -114,6 +114,7 @@ class Problem3:
     meta: dict = field(default_factory=dict)
     order: int = ORDER
     dim: int = 3
+    g: list | None = None         # per-grid compact Dirichlet data (read at Dirichlet points)
 
     @property
     def n_active(self):
@@ -518,6 +519,19 @@ def box_in_box_problem(nb=12, ni=10, omega=6.0, seed=0, b=20.0):
     f = [gaussian3(g, x0, 1.0, b) for g in grids]
     return Problem3(grids, interp, omega, f, name=f"box-in-box-{nb}^3+{ni}^3",
                     meta=dict(source=x0.tolist(), seed=seed))
+
+
+def with_boundary_data3(problem, fn):
+    """The same problem with Dirichlet data g = fn(x, y, z) on every Dirichlet point (zero
+    elsewhere): the Helmholtz solution takes the value g there."""
+    import copy
+    p = copy.copy(problem)
+    p.g = []
+    for g in problem.grids:
+        X = g.coords()
+        p.g.append(np.where(g.mask == DIRICHLET, fn(X[0], X[1], X[2]), 0.0))
+    p.name = problem.name + "-g"
+    return p
 
 
 def random_state3(problem, seed):

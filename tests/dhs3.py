@@ -81,6 +81,9 @@ def assemble(problem):
                         rhs[r] = problem.f[gi][k, j, i]
                     elif m != G.INTERP:
                         put(r, r, 1.0)
+                        gb = getattr(problem, "g", None)
+                        if m == G.DIRICHLET and gb is not None and gb[gi] is not None:
+                            rhs[r] = gb[gi][k, j, i]  # U = g at Dirichlet points
         # Neumann ghosts next to discretization points
         for s in range(6):
             if g.bc[s] != G.BC_NEUMANN:

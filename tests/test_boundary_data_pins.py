@@ -98,3 +98,45 @@ def test_curvilinear_dirichlet_data_at_order_4_is_refused(oracle_mod):
     p.g = [p.g[0], np.where(A.mask == G.DIRICHLET, 1.0, 0.0)]
     with pytest.raises(ValueError):
         oracle_mod.Oracle(p)
+
+
+# ------------------------------------------------------------------ three dimensions
+
+def test_manufactured_solution_with_boundary_data_3d():
+    """Unit cube, Dirichlet walls carrying u: u = sin(pi x + 0.3) sin(pi y + 0.5)
+    sin(pi z + 0.2), f = (omega^2 - 3 pi^2) u; the 3D oracle's solution converges at
+    second order."""
+    import math
+    from paper_2504_03074_gb300 import grids3 as G3
+    from oracle import oracle3 as O3
+    om = 3.0
+    fn = lambda x, y, z: np.sin(np.pi * x + 0.3) * np.sin(np.pi * y + 0.5) * np.sin(np.pi * z + 0.2)
+    errs = []
+    for n in (9, 17):
+        prob = G3.unit_cube_problem(n, omega=om)
+        X = prob.grids[0].coords()
+        prob.f = [(om ** 2 - 3 * np.pi ** 2) * fn(X[0], X[1], X[2])]
+        prob = G3.with_boundary_data3(prob, fn)
+        orc = O3.Oracle3(prob)
+        from oracle.oracle import gmres
+        v, its, hist = gmres(orc, tol=1e-12, restart=100, max_it=300)
+        errs.append(np.max(np.abs(v - fn(X[0], X[1], X[2]).ravel())))
+    assert math.log2(errs[0] / errs[1]) > 1.7, errs
+
+
+@pytest.mark.parametrize("make", ["cube", "box_in_box"])
+def test_fixed_point_equals_direct_solve_with_boundary_data_3d(make):
+    import dhs3
+    from paper_2504_03074_gb300 import grids3 as G3
+    from oracle import oracle3 as O3
+    fn = lambda x, y, z: 0.5 * np.cos(1.1 * x + 0.6 * y - 0.4 * z) + 0.1 * z
+    base = G3.unit_cube_problem(10, omega=6.0) if make == "cube" else G3.box_in_box_problem()
+    prob = G3.with_boundary_data3(base, fn)
+    orc = O3.Oracle3(prob)
+    U = dhs3.solve(prob)
+    assert np.max(np.abs(U)) > 0.1
+    defect = orc.iterate(U, True) - U
+    assert np.max(np.abs(defect)) < 1e-11 * np.max(np.abs(U))
+    v = G3.random_state3(base, 1)
+    a = O3.Oracle3(base).iterate(v, False)
+    assert np.array_equal(a, orc.iterate(v, False))  # the zero-forcing map ignores g
