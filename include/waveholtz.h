@@ -263,11 +263,13 @@ wh_status wh_set_forcing(wh_ctx *ctx, int32_t grid_id, const double *f);
  * f_b - omega^2 g_b - c^2 (D_tt g)_b with D_tt the fourth-order second difference along
  * the side (centred; wrapped on a periodic side; six-point one-sided at the ends), since
  * the scheme's second time difference of g cos(omega_e t) is exactly -omega^2 g cos.
- * Takes effect at the next wh_prepare.  Two-dimensional contexts; differentiation and
- * wh_set_deflation (Algorithm 3's inflation) then return WH_ERR_STATE, while
- * wh_set_deflation_basis stays exact.  Errors: WH_ERR_ARG (bad grid, non-finite data),
- * WH_ERR_GRID (order 4: a curvilinear grid with a Dirichlet side, or a Dirichlet side of
- * fewer than 6 points), WH_ERR_STATE (3D context). */
+ * Takes effect at the next wh_prepare.  On three-dimensional contexts (order 2, no
+ * Dirichlet ghost rule) the data are set per level by a small kernel before the level's
+ * ghost rules and interpolation, and the temporally blocked FP32 march keeps the units
+ * near such points in single steps.  Differentiation and wh_set_deflation (Algorithm 3's
+ * inflation) then return WH_ERR_STATE, while wh_set_deflation_basis stays exact.
+ * Errors: WH_ERR_ARG (bad grid, non-finite data), WH_ERR_GRID (order 4: a curvilinear grid
+ * with a Dirichlet side, or a Dirichlet side of fewer than 6 points). */
 wh_status wh_set_boundary_data(wh_ctx *ctx, int32_t grid_id, const double *g);
 
 /* Prepare one frequency per instance (batching: several independent Helmholtz problems,

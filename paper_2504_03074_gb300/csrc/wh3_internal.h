@@ -112,6 +112,10 @@ void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
                     double *V, const double *wf, int level);
 void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
                     const double *V, double *vout);
+// Dirichlet points with boundary data at one level: W[idx[t]] = gfac g[t], V += wf[level] W.
+void launch_dirichlet3(bool fp32, cudaStream_t s, int64_t n, const int64_t *idx,
+                       const double *g, void *W, double *V, double gfac, const double *wf,
+                       int level);
 // vout (compact) = W (extended, FP64) at discretization points, zero elsewhere.
 void launch_disc3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
                   const int8_t *mask, const double *W, double *vout);
@@ -124,6 +128,10 @@ void destroy(Ctx3 *c);
 wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std::string &err);
 wh_status set_interp(Ctx3 *c, const wh_interp3_desc *d, std::string &err);
 wh_status set_forcing(Ctx3 *c, int32_t gid, const double *f, std::string &err);
+// Dirichlet boundary data of one grid (compact, read at its Dirichlet points; null removes
+// them): those points hold g cos(omega_e t) while the forcing is on.
+wh_status set_boundary_data(Ctx3 *c, int32_t gid, const double *g, std::string &err);
+bool has_boundary_data(const Ctx3 *c);
 // Prepare one frequency: upload (first time), coefficients, CFL bound, time tables, stencil
 // weights; with fp32 also the FP32 march arrays.  Returns the time setup and sizes.
 wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,

@@ -2398,8 +2398,11 @@ wh_status wh_set_forcing(wh_ctx *ctx, int32_t gid, const double *f) {
 
 wh_status wh_set_boundary_data(wh_ctx *ctx, int32_t gid, const double *g) {
   if (!ctx) return WH_ERR_ARG;
-  if (ctx->dim == 3)
-    return fail(ctx, WH_ERR_STATE, "boundary data are available on 2D contexts");
+  if (ctx->dim == 3) {
+    const wh_status st = wh3::set_boundary_data(ctx->c3, gid, g, ctx->err);
+    if (st == WH_OK) ctx->prepared = false;
+    return st;
+  }
   if (gid < 0 || gid >= (int)ctx->grids.size())
     return fail(ctx, WH_ERR_ARG, "bad boundary data arguments");
   HostGrid &H = ctx->grids[gid];
@@ -2903,7 +2906,7 @@ wh_status wh_solve(wh_ctx *ctx, int32_t method, double tol, int32_t max_it, int3
   const int K = ctx->defl_k;
   if (K > 0) {
     if (ctx->ninst != 1) return finish(fail(ctx, WH_ERR_STATE, "deflation needs one instance"));
-    if (!ctx->defl_basis && ctx->d_gb)
+    if (!ctx->defl_basis && (ctx->d_gb || (ctx->dim == 3 && wh3::has_boundary_data(ctx->c3))))
       return finish(fail(ctx, WH_ERR_STATE,
                          "Algorithm 3's inflation takes g = 0; with Dirichlet data use "
                          "wh_set_deflation_basis (exact for any data)"));

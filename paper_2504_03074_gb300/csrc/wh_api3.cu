@@ -28,6 +28,7 @@ struct HostGrid3 {
   std::vector<double> rx;    // 9 extended planes
   std::vector<double> c2;    // compact, empty for c = 1
   std::vector<double> f;     // compact
+  std::vector<double> gdata; // compact Dirichlet boundary data, empty when none
   int g[3] = {1, 1, 1};
   int e[3] = {0, 0, 0};
 };
@@ -52,6 +53,11 @@ struct Ctx3 {
   double *d_rx = nullptr, *d_coef = nullptr, *d_Wt = nullptr;
   float *d_Wa32 = nullptr, *d_Wb32 = nullptr, *d_F32 = nullptr, *d_Wt32 = nullptr;
   int64_t *d_ridx = nullptr;
+  // Dirichlet points with boundary data: state indices and values
+  int64_t ndir = 0;
+  int64_t *d_dir_idx = nullptr;
+  double *d_dir_g = nullptr;
+  double omega_e = 0.0, dt = 0.0;  // the prepared time setup (host copies)
   int32_t *d_gbase = nullptr, *d_goff = nullptr, *d_gdst = nullptr, *d_gsrc = nullptr;
   double *d_gw = nullptr;
   double *d_tabs = nullptr;
@@ -154,6 +160,9 @@ void free_all(Ctx3 *c) {
   c->d_smax = nullptr;
   c->fp32_ready = false;
   c->d_units = nullptr;
+  c->ndir = 0;
+  c->d_dir_idx = nullptr;
+  c->d_dir_g = nullptr;
   c->d_ctiles = nullptr;
   c->d_ring = nullptr;
   c->d_FM32 = nullptr;
@@ -415,6 +424,32 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
   CK3(cudaMemcpy(c->d_gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK3(cudaMemcpy(c->d_gdst, gdst.data(), gdst.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK3(cudaMemcpy(c->d_gsrc, gsrc.data(), gsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  {
+    // Dirichlet points of the grids with boundary data
+    std::vector<int64_t> di;
+    std::vector<double> dv;
+    for (int g = 0; g < ng; ++g) {
+      const HostGrid3 &H = c->grids[g];
+      if (H.gdata.empty()) continue;
+      const Grid3Dev &D = c->hg[g];
+      for (int k = 0; k < D.n2; ++k)
+        for (int j = 0; j < D.n1; ++j)
+          for (int i = 0; i < D.n0; ++i)
+            if (H.mask[cidx(H, i, j, k)] == WH_DIRICHLET) {
+              di.push_back(D.base + eidx(H, i, j, k));
+              dv.push_back(H.gdata[cidx(H, i, j, k)]);
+            }
+    }
+    c->ndir = (int64_t)di.size();
+    if (c->ndir) {
+      if ((st = alloc3(c, &c->d_dir_idx, di.size(), err)) ||
+          (st = alloc3(c, &c->d_dir_g, dv.size(), err)))
+        return st;
+      CK3(cudaMemcpy(c->d_dir_idx, di.data(), di.size() * sizeof(int64_t),
+                     cudaMemcpyHostToDevice));
+      CK3(cudaMemcpy(c->d_dir_g, dv.data(), dv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+  }
   c->dirty = false;
   c->f_dirty = true;
   return WH_OK;
@@ -490,6 +525,11 @@ wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
     };
     for (int64_t r = 0; r < c->nrecv; ++r)
       if (c->rg[r] == g) mark_near(c->ri[r], c->rj[r], c->rk[r]);
+    if (!H.gdata.empty())  // Dirichlet points with data change in time: single steps there
+      for (int k = 0; k < n2; ++k)
+        for (int j = 0; j < n1; ++j)
+          for (int i = 0; i < n0; ++i)
+            if (H.mask[cidx(H, i, j, k)] == WH_DIRICHLET) mark_near(i, j, k);
     for (size_t t = 0; t < c->nghost_dst.size(); t += 4)
       if (c->nghost_dst[t] == g)
         mark_near(c->nghost_dst[t + 1], c->nghost_dst[t + 2], c->nghost_dst[t + 3]);
@@ -590,12 +630,13 @@ inline float *ring_level(Ctx3 *c, int l) { return c->d_ring + (int64_t)(l % c->r
 
 // Launches of one iteration after init (without init and output).
 int64_t step_launches(const Ctx3 *c, bool fp32) {
-  if (!blocked(c, fp32)) return 1 + 2 * (int64_t)c->M;
+  const int64_t dir = c->ndir ? (int64_t)c->M + 1 : 0;  // Dirichlet data, one per level
+  if (!blocked(c, fp32)) return 1 + 2 * (int64_t)c->M + dir;
   const int K = c->plan_K;
   const int64_t sup = c->M > 1 ? (c->M - 1) / K : 0;
   const int64_t rest = (int64_t)c->M - 1 - sup * K;
   const int64_t cm = c->ctiles.empty() ? 0 : 1;  // coupled march launches per single step
-  return 1 + 2 + sup * (1 + K * (cm + 1)) + 2 * rest;
+  return 1 + 2 + sup * (1 + K * (cm + 1)) + 2 * rest + dir;
 }
 
 // The body of one iteration after init: level-0 ghost rules + interpolation, then M steps.
@@ -607,6 +648,9 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
     const double fs = forcing ? 1.0 : 0.0;
     const int K = c->plan_K;
     auto gather = [&](int level) {
+      if (c->ndir)
+        launch_dirichlet3(true, s, c->ndir, c->d_dir_idx, c->d_dir_g, ring_level(c, level),
+                          c->d_V, fs * std::cos(c->omega_e * level * c->dt), c->tab.wf, level);
       launch_gather3(true, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
                      c->d_gdst, c->d_gsrc, ring_level(c, level), c->d_V, c->tab.wf, level);
     };
@@ -639,6 +683,9 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
   const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
   const double fs = forcing ? 1.0 : 0.0;
   auto gather = [&](void *W, int level) {
+    if (c->ndir)  // Dirichlet data first: receivers may take them as donors
+      launch_dirichlet3(fp32, s, c->ndir, c->d_dir_idx, c->d_dir_g, W, c->d_V,
+                        fs * std::cos(c->omega_e * level * c->dt), c->tab.wf, level);
     launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
                    c->d_gdst, c->d_gsrc, W, c->d_V, c->tab.wf, level);
   };
@@ -837,6 +884,27 @@ wh_status set_forcing(Ctx3 *c, int32_t gid, const double *f, std::string &err) {
   return WH_OK;
 }
 
+wh_status set_boundary_data(Ctx3 *c, int32_t gid, const double *g, std::string &err) {
+  if (gid < 0 || gid >= (int)c->grids.size())
+    return fail3(err, WH_ERR_ARG, "bad boundary data arguments");
+  HostGrid3 &H = c->grids[gid];
+  if (g)
+    for (size_t q = 0; q < H.mask.size(); ++q)
+      if (!std::isfinite(g[q])) return fail3(err, WH_ERR_ARG, "non-finite boundary data");
+  if (g)
+    H.gdata.assign(g, g + H.mask.size());
+  else
+    H.gdata.clear();
+  c->dirty = true;  // the lists of Dirichlet points and the blocking plan change
+  return WH_OK;
+}
+
+bool has_boundary_data(const Ctx3 *c) {
+  for (const auto &H : c->grids)
+    if (!H.gdata.empty()) return true;
+  return false;
+}
+
 wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
                   wh_time_info *ti, int64_t *ncompact, int64_t *nactive, std::string &err) {
   if (c->grids.empty()) return fail3(err, WH_ERR_STATE, "no grids");
@@ -888,6 +956,8 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
   T.n_total = c->ncompact;
   const int M = T.M;
   c->M = M;
+  c->omega_e = T.omega_e;
+  c->dt = dt;
   c->dt2 = dt * dt;
   // tables: fc[0..M], wf[0..M]; fc rounded to FP32
   const int64_t len = 2 * (int64_t)(M + 1);

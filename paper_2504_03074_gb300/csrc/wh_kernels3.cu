@@ -634,6 +634,23 @@ __global__ void __launch_bounds__(256) gather3_kernel(
     W[gdst[g]] = W[gsrc[g]];
 }
 
+// Dirichlet points with boundary data at one level: W = gfac g (gfac = the forcing switch
+// times cos(omega_e t^level)) and the level's filter term.  Runs before the level's ghost
+// rules and interpolation, which may read these points as donors.
+template <typename T>
+__global__ void dirichlet3_kernel(int64_t n, const int64_t *__restrict__ idx,
+                                  const double *__restrict__ g, T *W, double *V, double gfac,
+                                  const double *__restrict__ wf, int level) {
+  const double wl = wf[level];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx[t];
+    const T w = (T)(gfac * g[t]);
+    W[q] = w;
+    V[q] = fma(wl, wh::to_f64(w), V[q]);
+  }
+}
+
 // v_out (compact) = V at every point of every grid (with `mask`: at discretization points,
 // zero elsewhere); blockIdx.y = grid.
 __global__ void finish3_kernel(const Grid3Dev *grids, const int8_t *mask, const double *V,
@@ -662,6 +679,17 @@ unsigned blocks_for(int64_t n, int threads) {
 }
 
 }  // namespace
+
+void launch_dirichlet3(bool fp32, cudaStream_t s, int64_t n, const int64_t *idx,
+                       const double *g, void *W, double *V, double gfac, const double *wf,
+                       int level) {
+  const unsigned nb = blocks_for(n < 1 ? 1 : n, 256);
+  if (fp32)
+    dirichlet3_kernel<float><<<nb, 256, 0, s>>>(n, idx, g, (float *)W, V, gfac, wf, level);
+  else
+    dirichlet3_kernel<double><<<nb, 256, 0, s>>>(n, idx, g, (double *)W, V, gfac, wf, level);
+}
+
 
 void launch_coef3(cudaStream_t s, const Grid3Dev *grids, int gidx, const Grid3Dev &G,
                   const int8_t *mask, const double *rx, const double *c2, double *coef,

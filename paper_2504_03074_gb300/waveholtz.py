@@ -296,6 +296,10 @@ class Solver:
             self._check(self.L.wh_add_grid3(self.h, C.byref(d), C.byref(gid)))
             f = np.ascontiguousarray(problem.f[gi], np.float64)
             self._check(self.L.wh_set_forcing(self.h, gid.value, _ptr(f)))
+            gb = getattr(problem, "g", None)
+            if gb is not None and gb[gi] is not None:
+                ga = np.ascontiguousarray(gb[gi], np.float64)
+                self._check(self.L.wh_set_boundary_data(self.h, gid.value, _ptr(ga)))
         it = problem.interp
         arrs = [np.ascontiguousarray(a, np.int32) for a in
                 (it.recv_grid, it.recv_i, it.recv_j, it.recv_k, it.donor_grid, it.donor_i0,

@@ -330,7 +330,7 @@ def test_state_validation_on_host(W):
 def test_boundary_data_validation_on_host(W):
     """wh_set_boundary_data checks its arguments without touching the device: a bad grid
     or non-finite data is refused and leaves the context as it was; NULL removes the data;
-    order-4 curvilinear grids with a Dirichlet side and 3D contexts refuse data."""
+    order-4 curvilinear grids with a Dirichlet side refuse data; 3D contexts take them."""
     L = W.lib()
     prob = G.unit_square_problem(16, 4, 3.0)
     h = _ctx(W, 4)
@@ -356,5 +356,9 @@ def test_boundary_data_validation_on_host(W):
     cube = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
     d3, keep3 = _desc3(W, cube)
     assert L.wh_add_grid3(h, C.byref(d3), C.byref(gid)) == 0
-    assert L.wh_set_boundary_data(h, 0, np.ones(9 ** 3).ctypes.data) == -3
+    assert L.wh_set_boundary_data(h, 0, np.ones(9 ** 3).ctypes.data) == 0
+    bad3 = np.ones(9 ** 3)
+    bad3[7] = np.inf
+    assert L.wh_set_boundary_data(h, 0, bad3.ctypes.data) == -1
+    assert L.wh_set_boundary_data(h, 1, bad3.ctypes.data) == -1
     L.wh_destroy(h)

@@ -155,15 +155,60 @@ def test_calls_that_take_no_boundary_data_refuse_it(torch, W):
     s.set_boundary_data(0, None)
     s.prepare()
     s.solve(u, W.FPI, tol=1e-30, max_it=2)
-    # curvilinear Dirichlet sides at order 4 and 3D contexts do not take data
+    # curvilinear Dirichlet sides at order 4 do not take data
     A = G.annulus_grid("annulus", 96, 10, 0.5, 0.8, 1.5, 4, inner_bc=G.BC_DIRICHLET)
     p2 = G.Problem([A], G.Interp.empty(4), 4, 4.0, [np.zeros(A.mask.shape)])
     s2 = W.Solver(p2)
     with pytest.raises(W.WHError) as e:
         s2.set_boundary_data(0, np.ones(A.mask.shape))
     assert e.value.status == -7
+
+
+
+# ------------------------------------------------------------------ three dimensions
+
+def _g3(x, y, z):
+    return 0.5 * np.cos(1.1 * x + 0.6 * y - 0.4 * z) + 0.1 * z
+
+
+@pytest.mark.parametrize("make", ["cube", "box_in_box"])
+def test_iteration_with_boundary_data_3d(torch, W, make):
+    """3D contexts: FP64 at 1e-12 and the FP32 march within 1e-4 of the 3D oracle, forcing
+    on and off; on the cube also the temporally blocked FP32 march (the units near the
+    Dirichlet walls with data take single steps) within the same bound."""
     from paper_2504_03074_gb300 import grids3 as G3
-    c = W.Solver(G3.unit_cube_problem(9, omega=4.0))
-    with pytest.raises(W.WHError) as e:
-        c.set_boundary_data(0, np.ones(9 ** 3))
-    assert e.value.status == -3
+    from oracle import oracle3 as O3
+    base = G3.unit_cube_problem(70, omega=6.0) if make == "cube" else G3.box_in_box_problem()
+    prob = G3.with_boundary_data3(base, _g3)
+    orc = O3.Oracle3(prob)
+    act = orc.active()
+    v = G3.random_state3(prob, 5)
+    refs = {f: orc.iterate(v, f) for f in (True, False)}
+    for prec, tol in ((W.FP64, TOL), (W.FP32, 1e-4)):
+        s = W.Solver(prob, precision=prec)
+        s.prepare()
+        depths = (1, 3) if (prec == W.FP32 and make == "cube") else (-1,)
+        for K in depths:
+            if K != -1:
+                s.set_tuning(temporal_depth=K, unit_depth=8)
+                assert (s.get_tuning()["blocked_points"] > 0) == (K > 1)
+            for f in (True, False):
+                got = gpu_iterate(torch, s, v, f)
+                assert rel_err(got, refs[f], act) <= tol, (make, prec, K, f)
+        s.close()
+
+
+def test_gmres_with_boundary_data_3d(torch, W):
+    import dhs3
+    from paper_2504_03074_gb300 import grids3 as G3
+    prob = G3.with_boundary_data3(G3.box_in_box_problem(), _g3)
+    U = dhs3.solve(prob)
+    act = np.concatenate([(g.mask != 0).ravel() for g in prob.grids])
+    for prec in (W.FP64, W.FP32):
+        s = W.Solver(prob, precision=prec)
+        s.prepare()
+        u = torch.zeros(prob.n_total, dtype=torch.float64, device="cuda")
+        st = s.solve(u, W.GMRES, tol=1e-11, max_it=800, restart=200)
+        assert st.converged == 1, (st.status, st.residual)
+        assert rel_err(u.cpu().numpy(), U, act) < 1e-8
+        s.close()
