@@ -2,7 +2,8 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this module.  It wraps the plain C implementation in ``waveholtz_oracle3.c`` (one
-second-order WaveHoltz iteration on a 3D overset grid, FP64, single thread).  The
+WaveHoltz iteration on a 3D overset grid at second order, or at fourth order on Cartesian
+grids, FP64, single thread).  The
 fixed-point iteration, GMRES and the filter functions of ``oracle.oracle`` apply to it
 unchanged (they only call ``iterate``).  It shares no code with the CUDA library; inputs
 come from ``paper_2504_03074_gb300.grids3``.
@@ -54,6 +55,8 @@ def lib(openmp=False):
             vp, dp, cp = C.c_void_p, C.POINTER(C.c_double), C.c_char_p
             L.o3_new.restype = vp
             L.o3_new.argtypes = []
+            L.o3_new_order.restype = vp
+            L.o3_new_order.argtypes = [C.c_int]
             L.o3_error.restype = cp
             L.o3_error.argtypes = [vp]
             L.o3_add_grid.restype = C.c_int
@@ -88,7 +91,10 @@ class Oracle3:
     def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0, openmp=False):
         self.problem = problem
         self.L = lib(openmp)
-        self.h = self.L.o3_new()
+        self.order = int(getattr(problem, "order", 2))
+        self.h = self.L.o3_new_order(self.order)
+        if not self.h:
+            raise ValueError(f"order {self.order}: the 3D oracle takes 2 or 4")
         self._keep = []
         for gi, g in enumerate(problem.grids):
             bc = (C.c_int * 6)(*g.bc)
@@ -118,7 +124,8 @@ class Oracle3:
 
     def prepare(self, omega, cfl=0.9, periods=1, alpha_mode=0):
         out = (C.c_double * 7)()
-        self.L.o3_prepare(self.h, omega, cfl, periods, alpha_mode, out)
+        if self.L.o3_prepare(self.h, omega, cfl, periods, alpha_mode, out) != 0:
+            raise ValueError(self.L.o3_error(self.h).decode())
         self.omega = omega
         self.time = TimeSetup(list(out))
         return self.time
@@ -145,7 +152,7 @@ class Oracle3:
     # --- pieces for pin tests (extended arrays, shape (e2, e1, e0)) ---
     def ext_shape(self, gi):
         g = self.problem.grids[gi]
-        gh = g.ghosts()
+        gh = g.ghosts(self.order)
         return tuple(g.n[a] + 2 * gh[a] for a in (2, 1, 0))
 
     def apply_lap(self, gi, u_ext):

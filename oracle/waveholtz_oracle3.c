@@ -2,7 +2,8 @@
  * waveholtz_oracle3.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
  *
  * A plain, slow, single-threaded FP64 CPU implementation of one WaveHoltz iteration on a
- * three-dimensional overset grid at second order, written from the paper (Appelo, Banks,
+ * three-dimensional overset grid at second order (and at fourth order on Cartesian grids),
+ * written from the paper (Appelo, Banks,
  * Henshaw, Schwendeman, "An optimal O(N) Helmholtz solver for complex geometry using
  * WaveHoltz and overset grids").  Only tests/, the smoke check and the benchmark's
  * CPU-baseline leg may load it.  It shares no code, header or table with the CUDA library
@@ -34,6 +35,16 @@
  *              i.e. W_{-1} = W_{+1}.  This is the normal derivative when the normal grid
  *              axis is orthogonal to the two tangential axes, which is required.
  * Grid lines of a pair of axes declared orthogonal drop the mixed term (a_kl = 0).
+ *
+ * Fourth order (o3_new_order(4)): Cartesian grids only, two ghost layers, the second
+ * difference D+D-(1 - h^2/12 D+D-) per axis (Eq. SecondDerivOrderp with mu < 2), the
+ * stability constant C = sqrt(3)/2 in the time-step bound, Lagrange interpolation of width
+ * 5, and the two-dimensional fourth-order ghost rules applied along each face's normal axis:
+ *   Dirichlet: W_b = 0 (no boundary data at this order); c^2 D_nn W_b = f_b cos(omega_e t)
+ *     (the tangential second differences of the zero boundary values vanish) and
+ *     D+^5 W_{-2} = 0;
+ *   Neumann: fourth-order centred D_n W = 0 and the same extrapolation; a Neumann face
+ *     may only meet periodic or interpolation faces.
  */
 #include <math.h>
 #ifndef M_PI
@@ -55,6 +66,7 @@ enum { C_A00 = 0, C_A11, C_A22, C_A01, C_A02, C_A12, C_B0, C_B1, C_B2, C_N };
 typedef struct {
   int n[3], g[3], e[3];
   int kind;
+  int fourth;      /* fourth-order differences (Cartesian grids of an order-4 problem) */
   int ortho;       /* bit 0: axes (0,1) orthogonal, bit 1: (0,2), bit 2: (1,2) */
   int bc[6];       /* [axis0 lo, axis0 hi, axis1 lo, axis1 hi, axis2 lo, axis2 hi] */
   double h[3];
@@ -67,7 +79,7 @@ typedef struct {
 } o3_grid;
 
 typedef struct {
-  int ngrids;
+  int ngrids, order;
   o3_grid G[O3_MAX_GRIDS];
   long nrecv;
   int *rg, *ri, *rj, *rk, *dg, *di, *dj, *dk;
@@ -99,12 +111,21 @@ static double val(const o3_grid *G, const double *W, int i, int j, int k, const 
   return W[at(G, i + d[0], j + d[1], k + d[2])];
 }
 
-/* D+D- W along axis a (divided). */
+/* D+D- W along axis a (divided); with two ghost layers (fourth order) the fourth-order
+ * difference D+D-(1 - h^2/12 D+D-) = (-W_-2 + 16 W_-1 - 30 W + 16 W_+1 - W_+2) / (12 h^2). */
 static double d2(const o3_grid *G, const double *W, int i, int j, int k, int a) {
   int p[3] = {0, 0, 0}, m[3] = {0, 0, 0}, z[3] = {0, 0, 0};
   p[a] = 1; m[a] = -1;
-  return (val(G, W, i, j, k, p) - 2.0 * val(G, W, i, j, k, z) + val(G, W, i, j, k, m)) /
-         (G->h[a] * G->h[a]);
+  const double s1 = val(G, W, i, j, k, p) - 2.0 * val(G, W, i, j, k, z) + val(G, W, i, j, k, m);
+  if (G->fourth) {
+    int p2[3] = {0, 0, 0}, m2[3] = {0, 0, 0};
+    p2[a] = 2; m2[a] = -2;
+    const double s2 = val(G, W, i, j, k, p2) - 4.0 * val(G, W, i, j, k, p) +
+                      6.0 * val(G, W, i, j, k, z) - 4.0 * val(G, W, i, j, k, m) +
+                      val(G, W, i, j, k, m2);
+    return (s1 - s2 / 12.0) / (G->h[a] * G->h[a]);
+  }
+  return s1 / (G->h[a] * G->h[a]);
 }
 
 /* D0 W along axis a. */
@@ -203,35 +224,67 @@ static double dt_bound(const o3_problem *P) {
   return 1.0 / sqrt(smax);
 }
 
-/* Ghost points of every Neumann side: W_{-1} = W_{+1} next to discretization points. */
-static void apply_bc(const o3_problem *P, int gidx, double *W) {
+/* Ghost points of every physical face at time t; fcos = cos(omega_e t) with the forcing on,
+ * 0 with it off.  Second order: Neumann W_{-1} = W_{+1} next to discretization points.
+ * Fourth order: the rules of the header, per boundary point along the face's normal axis
+ * (U0..U3 the boundary point and three inward, G1, G2 the two ghosts). */
+static void apply_bc(const o3_problem *P, int gidx, double *W, double fcos) {
   const o3_grid *G = &P->G[gidx];
   for (int s = 0; s < 6; ++s) {
-    if (G->bc[s] != O3_BC_NEUMANN) continue;
+    const int code = G->bc[s];
+    if (code != O3_BC_NEUMANN && !(code == O3_BC_DIRICHLET && G->fourth)) continue;
     int a = s / 2, hi = s % 2, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
     for (int v = 0; v < G->n[t2]; ++v)
       for (int u = 0; u < G->n[t1]; ++u) {
-        int ib[3], ig[3], in[3];
-        ib[t1] = ig[t1] = in[t1] = u;
-        ib[t2] = ig[t2] = in[t2] = v;
-        ib[a] = hi ? G->n[a] - 1 : 0;
-        ig[a] = hi ? G->n[a] : -1;
-        in[a] = hi ? G->n[a] - 2 : 1;
-        if (G->mask[at(G, ib[0], ib[1], ib[2])] != O3_DISC) continue;
-        W[at(G, ig[0], ig[1], ig[2])] = W[at(G, in[0], in[1], in[2])];
+        int ip[6][3];  /* offsets -2, -1, 0, 1, 2, 3 along the inward normal */
+        for (int o = 0; o < 6; ++o) {
+          ip[o][t1] = u;
+          ip[o][t2] = v;
+          ip[o][a] = hi ? G->n[a] - 1 - (o - 2) : (o - 2);
+        }
+        const long qb = at(G, ip[2][0], ip[2][1], ip[2][2]);
+        const signed char m = G->mask[qb];
+        if (!G->fourth) {
+          if (m != O3_DISC) continue;
+          W[at(G, ip[1][0], ip[1][1], ip[1][2])] = W[at(G, ip[3][0], ip[3][1], ip[3][2])];
+          continue;
+        }
+        if ((code == O3_BC_NEUMANN && m != O3_DISC) || (code == O3_BC_DIRICHLET && m != O3_DIRICHLET))
+          continue;
+        double U[4];
+        for (int k = 0; k < 4; ++k) U[k] = W[at(G, ip[2 + k][0], ip[2 + k][1], ip[2 + k][2])];
+        const long g1 = at(G, ip[1][0], ip[1][1], ip[1][2]), g2 = at(G, ip[0][0], ip[0][1], ip[0][2]);
+        /* second row, D+^5 W_{-2} = 0:  G2 - 5 G1 + 10 U0 - 10 U1 + 5 U2 - U3 = 0 */
+        double A[2][2], r[2];
+        A[1][0] = -5.0; A[1][1] = 1.0;
+        r[1] = -(10.0 * U[0] - 10.0 * U[1] + 5.0 * U[2] - U[3]);
+        if (code == O3_BC_NEUMANN) {
+          /* 8 (U1 - G1) - (U2 - G2) = 0 */
+          A[0][0] = -8.0; A[0][1] = 1.0;
+          r[0] = -(8.0 * U[1] - U[2]);
+        } else {
+          /* c^2 (-G2 + 16 G1 - 30 U0 + 16 U1 - U2) / (12 h^2) = f_b cos */
+          const double A2 = G->c2[qb] / (12.0 * G->h[a] * G->h[a]);
+          A[0][0] = 16.0 * A2; A[0][1] = -A2;
+          r[0] = G->f[qb] * fcos - A2 * (-30.0 * U[0] + 16.0 * U[1] - U[2]);
+        }
+        const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        W[g1] = (r[0] * A[1][1] - A[0][1] * r[1]) / det;
+        W[g2] = (A[0][0] * r[1] - r[0] * A[1][0]) / det;
       }
   }
 }
 
-/* Every receiver from its 3 x 3 x 3 donor stencil (Sec. 3.1). */
+/* Every receiver from its (p + 1)^3 donor stencil (Sec. 3.1). */
 static void interpolate(const o3_problem *P, double **W) {
+  const int w = P->order + 1;
   for (long r = 0; r < P->nrecv; ++r) {
     const o3_grid *D = &P->G[P->dg[r]];
     double s = 0.0;
-    for (int c = 0; c < 3; ++c)
-      for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a)
-          s += P->wx[r * 3 + a] * P->wy[r * 3 + b] * P->wz[r * 3 + c] *
+    for (int c = 0; c < w; ++c)
+      for (int b = 0; b < w; ++b)
+        for (int a = 0; a < w; ++a)
+          s += P->wx[r * w + a] * P->wy[r * w + b] * P->wz[r * w + c] *
                W[P->dg[r]][at(D, P->di[r] + a, P->dj[r] + b, P->dk[r] + c)];
     W[P->rg[r]][at(&P->G[P->rg[r]], P->ri[r], P->rj[r], P->rk[r])] = s;
   }
@@ -239,7 +292,14 @@ static void interpolate(const o3_problem *P, double **W) {
 
 /* ------------------------------------------------------------ public API */
 
-o3_problem *o3_new(void) { return (o3_problem *)calloc(1, sizeof(o3_problem)); }
+o3_problem *o3_new_order(int order) {
+  if (order != 2 && order != 4) return NULL;
+  o3_problem *P = (o3_problem *)calloc(1, sizeof(o3_problem));
+  if (P) P->order = order;
+  return P;
+}
+
+o3_problem *o3_new(void) { return o3_new_order(2); }
 
 const char *o3_error(const o3_problem *P) { return P->err; }
 
@@ -265,12 +325,27 @@ int o3_add_grid(o3_problem *P, int n0, int n1, int n2, int kind, const int *bc, 
       }
     }
   }
+  if (P->order == 4) {
+    if (kind != O3_CARTESIAN) {
+      snprintf(P->err, sizeof P->err, "fourth order in 3D: Cartesian grids only");
+      return -1;
+    }
+    /* the fourth-order Neumann rule is unstable at corners with another physical side */
+    for (int s = 0; s < 6; ++s)
+      for (int s2 = 0; s2 < 6; ++s2)
+        if (s / 2 != s2 / 2 && bc[s] == O3_BC_NEUMANN &&
+            (bc[s2] == O3_BC_DIRICHLET || bc[s2] == O3_BC_NEUMANN)) {
+          snprintf(P->err, sizeof P->err, "a Neumann face meets another physical face");
+          return -1;
+        }
+  }
   o3_grid *G = &P->G[P->ngrids];
   memset(G, 0, sizeof *G);
   G->n[0] = n0; G->n[1] = n1; G->n[2] = n2;
+  G->fourth = P->order == 4;
   for (int s = 0; s < 6; ++s) G->bc[s] = bc[s];
   for (int a = 0; a < 3; ++a) {
-    G->g[a] = bc[2 * a] == O3_BC_PERIODIC ? 0 : 1;
+    G->g[a] = bc[2 * a] == O3_BC_PERIODIC ? 0 : P->order / 2;
     G->e[a] = G->n[a] + 2 * G->g[a];
   }
   G->kind = kind; G->ortho = kind == O3_CARTESIAN ? 7 : ortho;
@@ -332,8 +407,9 @@ int o3_set_interp(o3_problem *P, long n, const int *rg, const int *ri, const int
   const double *ws[3] = {wx, wy, wz};
   for (int q = 0; q < 3; ++q) {
     free(*wd[q]);
-    *wd[q] = (double *)malloc((n ? n : 1) * 3 * sizeof(double));
-    if (n) memcpy(*wd[q], ws[q], n * 3 * sizeof(double));
+    const int w = P->order + 1;
+    *wd[q] = (double *)malloc((n ? n : 1) * w * sizeof(double));
+    if (n) memcpy(*wd[q], ws[q], n * w * sizeof(double));
   }
   return 0;
 }
@@ -343,7 +419,17 @@ int o3_set_interp(o3_problem *P, long n, const int *rg, const int *ri, const int
 int o3_prepare(o3_problem *P, double omega, double cfl, int Np, int alpha_mode, double *out) {
   for (int g = 0; g < P->ngrids; ++g)
     if (P->G[g].kind == O3_CURVILINEAR) precompute_coeffs(&P->G[g]);
-  double dtmax = cfl * dt_bound(P);
+  if (P->order == 4)
+    for (int g = 0; g < P->ngrids; ++g) {
+      const o3_grid *G = &P->G[g];
+      for (long q = 0; q < ext_size(G); ++q)
+        if (G->mask[q] == O3_DIRICHLET && G->gb[q] != 0.0) {
+          snprintf(P->err, sizeof P->err, "boundary data at fourth order in 3D");
+          return -1;
+        }
+    }
+  /* Eq. dtForCartesian: C = 1 at second order, sqrt(3)/2 at fourth */
+  double dtmax = cfl * (P->order == 4 ? sqrt(3.0) / 2.0 : 1.0) * dt_bound(P);
   int Nt = (int)ceil(2.0 * M_PI / (omega * dtmax));
   if (Nt < 2) Nt = 2;
   double dt = 2.0 / omega * sin(M_PI / Nt);
@@ -385,7 +471,7 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
           double v = v_in[G->offset + ((long)k * G->n[1] + j) * G->n[0] + i];
           W0[g][q] = (m == O3_DISC || m == O3_INTERP) ? v : (m == O3_DIRICHLET ? fs * G->gb[q] : 0.0);
         }
-    apply_bc(P, g, W0[g]);
+    apply_bc(P, g, W0[g], fs);
   }
   interpolate(P, W0);
   for (int n = 0; n < M; ++n) {
@@ -421,7 +507,7 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
             long q = at(G, i, j, k);
             if (G->mask[q] == O3_DIRICHLET) Wp[g][q] = fs * G->gb[q] * cos(we * (n + 1) * dt);
           }
-      apply_bc(P, g, Wp[g]);
+      apply_bc(P, g, Wp[g], fs * cos(we * (n + 1) * dt));
     }
     interpolate(P, Wp);
     for (int g = 0; g < ng; ++g) {
@@ -465,7 +551,7 @@ int o3_apply_lap(o3_problem *P, int gidx, const double *u, double *out) {
 }
 
 int o3_apply_bc(o3_problem *P, int gidx, double *u) {
-  apply_bc(P, gidx, u);
+  apply_bc(P, gidx, u, 0.0);  /* zero forcing */
   return 0;
 }
 

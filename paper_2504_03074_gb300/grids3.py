@@ -1,11 +1,12 @@
-"""Seeded synthetic three-dimensional overset grids (second order): the stand-in for the
+"""Seeded synthetic three-dimensional overset grids: the stand-in for the
 paper's grid generator (Ogen, Sec. 3.1) in 3D.
 
 It builds component grids from analytic mappings x = G_g(r) -- an axis-aligned Cartesian
 box, a spherical shell (periodic in azimuth, a polar band), and orthographic pole patches
 -- cuts the hole of the background, classifies points as discretization / interpolation /
-unused, finds 3 x 3 x 3 donor stencils (explicit interpolation: donors are discretization
-or Dirichlet points only) and their tensor-product Lagrange weights (Sec. 3.1), and
+unused, finds 3 x 3 x 3 donor stencils (5 x 5 x 5 for the fourth-order Cartesian
+problems the CPU oracle takes; explicit interpolation: donors are discretization or
+Dirichlet points only) and their tensor-product Lagrange weights (Sec. 3.1), and
 evaluates Gaussian sources (Eq. gaussianSource).  Like ``grids`` it holds none of the
 WaveHoltz arithmetic: its outputs are the input data that both the CUDA library and the
 CPU oracle consume.
@@ -15,7 +16,7 @@ Array conventions:
 * a grid has ``n = (n0, n1, n2)`` points along parameter axes 0, 1, 2 (boundary points
   included, ghosts excluded; a periodic axis lists each point once);
 * compact per-grid arrays have shape ``(n2, n1, n0)`` in C order (axis 0 fastest);
-* the ghost width is 1 on non-periodic axes and 0 on periodic ones; extended arrays
+* the ghost width is p/2 on non-periodic axes (order p) and 0 on periodic ones; extended arrays
   (metrics) have shape ``(n2 + 2 g2, n1 + 2 g1, n0 + 2 g0)``;
 * sides are ``[axis0-lo, axis0-hi, axis1-lo, axis1-hi, axis2-lo, axis2-hi]``;
 * ``ortho`` is a bit mask of orthogonal axis pairs: bit 0 = (0, 1), bit 1 = (0, 2),
@@ -31,7 +32,7 @@ import numpy as np
 from .grids import (BC_DIRICHLET, BC_NEUMANN, BC_NONE, BC_PERIODIC, CARTESIAN, CURVILINEAR,
                     DIRICHLET, DISC, INTERP, UNUSED, lagrange_weights)
 
-ORDER = 2  # the three-dimensional path is second order
+ORDER = 2  # the three-dimensional CUDA path is second order (the oracle also takes 4)
 _EPS = 1e-9  # index-space tolerance of "inside a grid" (points on a shared boundary)
 
 
@@ -268,26 +269,26 @@ def pole_patch_grid(name, na, nr, A, r_in, width, sign):
 # Donor search (explicit interpolation)
 # ----------------------------------------------------------------------------------
 
-def _stencil(g, fi, fj, fk):
-    """Lower corners of the 3-point stencils nearest (fi, fj, fk), shifted inside."""
+def _stencil(g, fi, fj, fk, w=3):
+    """Lower corners of the w-point stencils nearest (fi, fj, fk), shifted inside."""
     f = [fi, fj, fk]
     c = []
     for a in range(3):
-        i0 = np.rint(f[a]).astype(np.int64) - 1
+        i0 = np.rint(f[a]).astype(np.int64) - w // 2
         if g.bc[2 * a] == BC_PERIODIC:
             i0 = np.mod(i0, g.n[a])
         else:
-            i0 = np.clip(i0, 0, g.n[a] - 3)
+            i0 = np.clip(i0, 0, g.n[a] - w)
         c.append(i0)
     return c
 
 
-def _valid(g, c):
-    """True where all 27 stencil points are discretization or Dirichlet points."""
+def _valid(g, c, w=3):
+    """True where all w^3 stencil points are discretization or Dirichlet points."""
     ok = np.ones(c[0].shape, bool)
-    for dc in range(3):
-        for db in range(3):
-            for da in range(3):
+    for dc in range(w):
+        for db in range(w):
+            for da in range(w):
                 ii = [c[0] + da, c[1] + db, c[2] + dc]
                 for a in range(3):
                     if g.bc[2 * a] == BC_PERIODIC:
@@ -297,9 +298,10 @@ def _valid(g, c):
     return ok
 
 
-def find_donors(grids, recv_gid, pts, order_of_donors):
-    """Donor stencils for receivers of grid ``recv_gid`` at physical points pts (3, N),
-    trying donor grids in the given order; raises if a receiver has no valid stencil."""
+def find_donors(grids, recv_gid, pts, order_of_donors, w=3):
+    """Donor stencils of width w for receivers of grid ``recv_gid`` at physical points
+    pts (3, N), trying donor grids in the given order; raises if a receiver has no valid
+    stencil."""
     N = pts.shape[1]
     out_g = np.full(N, -1, np.int32)
     out_c = np.zeros((3, N), np.int64)
@@ -313,15 +315,15 @@ def find_donors(grids, recv_gid, pts, order_of_donors):
         sel = np.nonzero(ok)[0]
         if sel.size == 0:
             continue
-        c = _stencil(g, fi[sel], fj[sel], fk[sel])
-        v = _valid(g, c)
+        c = _stencil(g, fi[sel], fj[sel], fk[sel], w)
+        v = _valid(g, c, w)
         take = todo[sel[v]]
         out_g[take] = dgid
         for a, fa in enumerate((fi, fj, fk)):
             out_c[a, take] = c[a][v]
             frac = fa[sel[v]] - c[a][v]
             if g.bc[2 * a] == BC_PERIODIC:  # distance along the periodic axis from i0
-                frac = np.mod(frac + 1.0, g.n[a]) - 1.0
+                frac = np.mod(frac + w // 2, g.n[a]) - w // 2
             out_f[a, take] = frac
     if np.any(out_g < 0):
         k = int(np.nonzero(out_g < 0)[0][0])
@@ -331,6 +333,7 @@ def find_donors(grids, recv_gid, pts, order_of_donors):
 
 def check_explicit_interp3(grids, it):
     """Every donor is a discretization or Dirichlet point; receivers are INTERP points."""
+    w = it.wx.shape[1]
     rg = it.recv_grid
     for gid, g in enumerate(grids):
         sel = rg == gid
@@ -346,14 +349,15 @@ def check_explicit_interp3(grids, it):
         c = [it.donor_i0[sel].astype(np.int64), it.donor_j0[sel].astype(np.int64),
              it.donor_k0[sel].astype(np.int64)]
         for a in range(3):
-            if g.bc[2 * a] != BC_PERIODIC and (c[a].min() < 0 or c[a].max() > g.n[a] - 3):
+            if g.bc[2 * a] != BC_PERIODIC and (c[a].min() < 0 or c[a].max() > g.n[a] - w):
                 raise ValueError(f"donor stencil outside grid {gid}")
-        if not np.all(_valid(g, c)):
+        if not np.all(_valid(g, c, w)):
             raise ValueError(f"grid {gid}: a donor stencil touches a non-discretization point")
 
 
-def _assemble(grids, parts):
-    """Concatenate (recv_gid, ijk (3, N), donor g (N), corner (3, N), frac (3, N))."""
+def _assemble(grids, parts, w=3):
+    """Concatenate (recv_gid, ijk (3, N), donor g (N), corner (3, N), frac (3, N)) with
+    width-w Lagrange weights."""
     cols = [[] for _ in range(11)]
     for rgid, ijk, dg, c, f in parts:
         n = ijk.shape[1]
@@ -364,7 +368,7 @@ def _assemble(grids, parts):
         for a in range(3):
             cols[5 + a].append(c[a].astype(np.int32))
         for a in range(3):
-            cols[8 + a].append(lagrange_weights(f[a], 3))
+            cols[8 + a].append(lagrange_weights(f[a], w))
     arrs = [np.concatenate(c) for c in cols]
     return Interp3(*arrs)
 
@@ -432,37 +436,45 @@ def sphere_in_box(nb=320, nphi=256, nth=128, nr=24, npatch=96, box=2.0, r_in=0.5
     return grids, interp
 
 
-def box_in_box(nb=12, ni=10, box=1.0, inner=0.45, hole=0.25):
+def _near(active, reach):
+    """Points within ``reach`` grid lines of an active point along one axis."""
+    near = np.zeros_like(active)
+    for d in range(1, reach + 1):
+        near[d:] |= active[:-d]
+        near[:-d] |= active[d:]
+        near[:, d:] |= active[:, :-d]
+        near[:, :-d] |= active[:, d:]
+        near[:, :, d:] |= active[:, :, :-d]
+        near[:, :, :-d] |= active[:, :, d:]
+    return near
+
+
+def box_in_box(nb=12, ni=10, box=1.0, inner=0.45, hole=0.25, order=ORDER):
     """Two Cartesian grids: background [-box, box]^3 (Dirichlet, nb^3) with a cubic hole
     |x|_inf < hole, and an inner box [-inner, inner]^3 (ni^3) whose faces are
-    interpolation points.  A small overset grid for brute-force checks."""
+    interpolation points.  A small overset grid for brute-force checks.  At order p the
+    interpolation layers are p/2 points thick and the donor stencils p + 1 wide."""
+    r, w = order // 2, order + 1
     B = cartesian_grid3("background", (nb,) * 3, (-box,) * 3, (box,) * 3, [BC_DIRICHLET] * 6)
     I = cartesian_grid3("inner", (ni,) * 3, (-inner,) * 3, (inner,) * 3, [BC_NONE] * 6)
     x = -box + B.h[0] * np.arange(nb)
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     inside = np.maximum(np.maximum(abs(X), abs(Y)), abs(Z)) < hole
-    active = ~inside
-    near = np.zeros_like(active)
-    near[1:] |= active[:-1]
-    near[:-1] |= active[1:]
-    near[:, 1:] |= active[:, :-1]
-    near[:, :-1] |= active[:, 1:]
-    near[:, :, 1:] |= active[:, :, :-1]
-    near[:, :, :-1] |= active[:, :, 1:]
+    near = _near(~inside, r)
     B.mask[inside & near] = INTERP
     B.mask[inside & ~near] = UNUSED
-    I.mask[:, :, 0] = I.mask[:, :, -1] = INTERP
-    I.mask[:, 0, :] = I.mask[:, -1, :] = INTERP
-    I.mask[0, :, :] = I.mask[-1, :, :] = INTERP
+    I.mask[:, :, :r] = I.mask[:, :, -r:] = INTERP
+    I.mask[:, :r, :] = I.mask[:, -r:, :] = INTERP
+    I.mask[:r, :, :] = I.mask[-r:, :, :] = INTERP
     grids = [B, I]
     parts = []
-    for rgid, order in ((0, (1,)), (1, (0,))):
+    for rgid, donors in ((0, (1,)), (1, (0,))):
         g = grids[rgid]
         ijk = _interp_points(g)
         pts = _points_of(g, ijk)
-        dg, c, f = find_donors(grids, rgid, pts, order)
+        dg, c, f = find_donors(grids, rgid, pts, donors, w)
         parts.append((rgid, ijk, dg, c, f))
-    interp = _assemble(grids, parts)
+    interp = _assemble(grids, parts, w)
     check_explicit_interp3(grids, interp)
     return grids, interp
 
@@ -503,22 +515,25 @@ def sphere_problem(nb=320, nphi=256, nth=128, nr=24, npatch=96, omega=30.0, seed
                     meta=dict(source=x0.tolist(), seed=seed))
 
 
-def unit_cube_problem(n=24, omega=10.0, seed=0, bc=BC_DIRICHLET, b=200.0):
-    """One Cartesian grid on [0, 1]^3 with n^3 points, Gaussian at x0 ~ U[0.3, 0.7]^3."""
+def unit_cube_problem(n=24, omega=10.0, seed=0, bc=BC_DIRICHLET, b=200.0, order=ORDER):
+    """One Cartesian grid on [0, 1]^3 with n^3 points, Gaussian at x0 ~ U[0.3, 0.7]^3.
+    ``bc`` is one code for all six faces or a list of six."""
     rng = np.random.default_rng(seed)
     x0 = rng.uniform(0.3, 0.7, size=3)
-    g = cartesian_grid3("cube", (n, n, n), (0.0,) * 3, (1.0,) * 3, [bc] * 6)
+    bcs = list(bc) if isinstance(bc, (list, tuple)) else [bc] * 6
+    g = cartesian_grid3("cube", (n, n, n), (0.0,) * 3, (1.0,) * 3, bcs)
     return Problem3([g], Interp3.empty(), omega, [gaussian3(g, x0, 1.0, b)],
-                    name=f"unit-cube-{n}^3", meta=dict(source=x0.tolist(), seed=seed))
+                    name=f"unit-cube-{n}^3", meta=dict(source=x0.tolist(), seed=seed),
+                    order=order)
 
 
-def box_in_box_problem(nb=12, ni=10, omega=6.0, seed=0, b=20.0):
+def box_in_box_problem(nb=12, ni=10, omega=6.0, seed=0, b=20.0, order=ORDER, hole=0.25):
     rng = np.random.default_rng(seed)
-    grids, interp = box_in_box(nb, ni)
+    grids, interp = box_in_box(nb, ni, hole=hole, order=order)
     x0 = _seeded_point(rng, -0.7, 0.7, 0.5)
     f = [gaussian3(g, x0, 1.0, b) for g in grids]
     return Problem3(grids, interp, omega, f, name=f"box-in-box-{nb}^3+{ni}^3",
-                    meta=dict(source=x0.tolist(), seed=seed))
+                    meta=dict(source=x0.tolist(), seed=seed), order=order)
 
 
 def with_boundary_data3(problem, fn):

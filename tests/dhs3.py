@@ -10,7 +10,11 @@ The converged WaveHoltz iterate equals the direct solution of (Sec. 6, App. B.1)
     U = 0                                              everywhere else.
 
 The rows come from the textbook 7-point stencil, independently of the oracle's C code, and
-are solved with a sparse LU.
+are solved with a sparse LU.  At fourth order (``problem.order == 4``) the second
+differences take the 5-point weights (-1, 16, -30, 16, -1)/12, two ghost layers per face
+carry the rows c^2 D_nn U_b = f_b (Dirichlet; the zero boundary values make the
+tangential terms vanish) or 8 (U_1 - G_1) - (U_2 - G_2) = 0 (Neumann), each with the
+extrapolation D+^5 G_2 = 0, and the interpolation stencils are 5 wide.
 """
 from __future__ import annotations
 
@@ -21,13 +25,55 @@ import scipy.sparse.linalg as spla
 from paper_2504_03074_gb300 import grids as G
 
 
+# off-centre second-difference weights (offset, weight) and the centre weight
+D2W = {2: [(-1, 1.0), (1, 1.0)],
+       4: [(-2, -1.0 / 12), (-1, 16.0 / 12), (1, 16.0 / 12), (2, -1.0 / 12)]}
+D2C = {2: -2.0, 4: -30.0 / 12}
+EXTRAP5 = [1.0, -5.0, 10.0, -10.0, 5.0, -1.0]  # on G2, G1, U0, U1, U2, U3
+
+
+def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done):
+    """The two ghost rows of every boundary point of a Dirichlet or Neumann face."""
+    for s in range(6):
+        code = g.bc[s]
+        if code not in (G.BC_DIRICHLET, G.BC_NEUMANN):
+            continue
+        a, hi = s // 2, s % 2
+        t1, t2 = (a + 1) % 3, (a + 2) % 3
+        for v in range(g.n[t2]):
+            for u in range(g.n[t1]):
+                def pt(o):  # point at offset o along the inward normal (o < 0: ghosts)
+                    ix = [0, 0, 0]
+                    ix[t1], ix[t2] = u, v
+                    ix[a] = g.n[a] - 1 - o if hi else o
+                    return ix
+                b = pt(0)
+                m = g.mask[b[2], b[1], b[0]]
+                if (code == G.BC_NEUMANN and m != G.DISC) or \
+                        (code == G.BC_DIRICHLET and m != G.DIRICHLET):
+                    continue
+                G1, G2 = L.idx(gi, *pt(-1)), L.idx(gi, *pt(-2))
+                U = [L.idx(gi, *pt(o)) for o in range(4)]
+                for c_, col in zip(EXTRAP5, [G2, G1] + U):
+                    put(G2, col, c_)
+                if code == G.BC_NEUMANN:
+                    for c_, col in zip([1.0, -8.0, 8.0, -1.0], [G2, G1, U[1], U[2]]):
+                        put(G1, col, c_)
+                else:
+                    w = c2[b[2], b[1], b[0]] / (12.0 * g.h[a] ** 2)
+                    for c_, col in zip([-1.0, 16.0, -30.0, 16.0, -1.0], [G2, G1] + U[:3]):
+                        put(G1, col, w * c_)
+                    rhs[G1] = problem.f[gi][b[2], b[1], b[0]]
+                done[G1] = done[G2] = True
+
+
 class Layout3:
     def __init__(self, problem):
         self.p = problem
         self.off, self.ext, self.gh = [], [], []
         o = 0
         for g in problem.grids:
-            gh = g.ghosts()
+            gh = g.ghosts(getattr(problem, "order", 2))
             e = tuple(g.n[a] + 2 * gh[a] for a in range(3))
             self.off.append(o)
             self.ext.append(e)
@@ -50,6 +96,7 @@ def assemble(problem):
     """Sparse DHS matrix and right-hand side over every extended point."""
     L = Layout3(problem)
     om2 = problem.omega ** 2
+    order = getattr(problem, "order", 2)
     rows, cols, vals = [], [], []
     rhs = np.zeros(L.N)
     done = np.zeros(L.N, bool)
@@ -72,11 +119,11 @@ def assemble(problem):
                         diag = om2
                         for a in range(3):
                             w = c2[k, j, i] / g.h[a] ** 2
-                            for s in (-1, 1):
+                            for s, cw in D2W[order]:
                                 d = [0, 0, 0]
                                 d[a] = s
-                                put(r, L.idx(gi, i + d[0], j + d[1], k + d[2]), w)
-                            diag -= 2 * w
+                                put(r, L.idx(gi, i + d[0], j + d[1], k + d[2]), w * cw)
+                            diag += w * D2C[order]
                         put(r, r, diag)
                         rhs[r] = problem.f[gi][k, j, i]
                     elif m != G.INTERP:
@@ -84,6 +131,9 @@ def assemble(problem):
                         gb = getattr(problem, "g", None)
                         if m == G.DIRICHLET and gb is not None and gb[gi] is not None:
                             rhs[r] = gb[gi][k, j, i]  # U = g at Dirichlet points
+        if order == 4:
+            fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done)
+            continue
         # Neumann ghosts next to discretization points
         for s in range(6):
             if g.bc[s] != G.BC_NEUMANN:
@@ -109,9 +159,10 @@ def assemble(problem):
         r = L.idx(int(it.recv_grid[q]), int(it.recv_i[q]), int(it.recv_j[q]), int(it.recv_k[q]))
         put(r, r, 1.0)
         dg = int(it.donor_grid[q])
-        for c in range(3):
-            for b in range(3):
-                for a in range(3):
+        wd = order + 1
+        for c in range(wd):
+            for b in range(wd):
+                for a in range(wd):
                     w = it.wx[q, a] * it.wy[q, b] * it.wz[q, c]
                     put(r, L.idx(dg, int(it.donor_i0[q]) + a, int(it.donor_j0[q]) + b,
                                  int(it.donor_k0[q]) + c), -w)
