@@ -179,12 +179,22 @@ def test_box_in_box_fourth_order_generator_invariants():
 
 # ------------------------------------------------------- fixed point = DHS
 
+def _forced(g, omega=5.0):
+    """Order-4 problem on one grid with a Gaussian source centred in [0.3, 0.7]^3."""
+    return G3.Problem3([g], G3.Interp3.empty(), omega,
+                       [G3.gaussian3(g, np.array([0.45, 0.55, 0.6]), 1.0, 20.0)], order=4)
+
+
 @pytest.mark.parametrize("make", [
     lambda: G3.unit_cube_problem(11, omega=5.0, b=20.0, order=4),
-    lambda: G3.unit_cube_problem(10, omega=5.0, b=20.0, order=4, bc=[P, P, P, P, N, D]),
+    # distinct spacings on the three axes
+    lambda: _forced(G3.cartesian_grid3("box", (11, 9, 10), (0.0,) * 3, (1.0, 0.8, 1.1), [D] * 6)),
+    lambda: _forced(_periodic_slab(10, [P, P, P, P, N, D])),
+    lambda: _forced(_periodic_slab(10, [P, P, P, P, D, N])),
     lambda: G3.unit_cube_problem(10, omega=5.0, b=20.0, order=4, bc=[P, P, N, N, P, P]),
     lambda: G3.box_in_box_problem(nb=17, ni=15, order=4, hole=0.1),
-], ids=["dirichlet-cube", "neumann-dirichlet-slab", "neumann-slab", "box-in-box"])
+], ids=["dirichlet-cube", "dirichlet-box", "neumann-dirichlet-slab", "dirichlet-neumann-slab",
+        "neumann-slab", "box-in-box"])
 def test_fixed_point_equals_direct_solve_fourth_order_3d(o3, make):
     """Sec. 6: the converged fourth-order WaveHoltz solution equals the direct solution of
     the fourth-order discrete Helmholtz system (13-point stencil, the two ghost rows per
