@@ -513,6 +513,8 @@ def measure_forms(WH, G, torch, prob, stream, flush, rank, cpu=True):
     stage("forms: 3D roofline probe")
     stage("forms: roofline_probe_3d_512")
     out["roofline_probe_3d_512"] = measure_cube_probe(WH, torch, stream)
+    stage("forms: cube512_order4")
+    out["cube512_order4"] = measure_cube_probe_o4(WH, torch, stream)
     return out
 
 
@@ -656,6 +658,44 @@ def measure_cube_probe(WH, torch, stream):
                 "blocked_kernel_gbs": bbytes / (bms * 1e-3) / 1e9,
                 "blocked_kernel_hbm_frac": bbytes / (bms * 1e-3) / 1e9 / hbm,
                 "blocked_bytes_per_update": 36.0 / t["temporal_depth"]}
+        sp.close()
+        del sp
+    return probe
+
+
+# Algorithmic FP64 FLOP per update of the three-dimensional order-4 march with the fused
+# filter: 6 additions pairing symmetric neighbours, the centre multiply, 6 multiply-adds of
+# the pair sums, the forcing multiply-add, the subtraction of W^{n-1}, the filter
+# multiply-add = 6 + 1 + 12 + 2 + 1 + 2.
+FLOP_PER_LUP_3D_O4 = 24.0
+
+
+def measure_cube_probe_o4(WH, torch, stream):
+    """Three-dimensional fourth order (Cartesian grids): one 512^3 grid on [0, 1]^3
+    (Dirichlet, omega 10, two ghost layers, no interpolation, HBM resident), FP64 and FP32:
+    the 13-point march kernel's device time per launch over one iteration's steps, and whole
+    iterations (CUDA events, inputs larger than L2).  Effective bandwidth counts the
+    compulsory bytes of one update as at second order (49 B FP64, 33 B FP32: state,
+    forcing, FP64 filter read and write, mask); the four further neighbours per update
+    come from cache."""
+    from paper_2504_03074_gb300 import grids3 as G3
+    hbm = float(measured_peaks().get("hbm_gbs", 6793.0))
+    cube = G3.unit_cube_problem(512, omega=10.0, order=4)
+    probe = {"workload": "unit cube 512^3, Dirichlet, omega 10, order 4, no interpolation",
+             "hbm_peak_gbs": hbm}
+    for name, prec, bpl in (("fp64", WH.FP64, 49.0), ("fp32", WH.FP32, 33.0)):
+        sp = WH.Solver(cube, stream=stream, precision=prec)
+        tp = sp.prepare()
+        ms = sp.profile_kernels(reps=1)["march"][0]
+        glups = tp.n_active / (ms * 1e-3) / 1e9
+        it = time_iterations(WH, torch, sp, cube.n_total, stream, None, 2)
+        rec = {"march_us": ms * 1e3, "value": glups, "unit": "GLUP/s", "M": tp.M,
+               "effective_gbs": glups * bpl, "hbm_frac": glups * bpl / hbm,
+               "ms_per_iteration": it * 1e3,
+               "iteration_glups": tp.n_active * tp.M / it / 1e9}
+        if prec == WH.FP64:
+            rec["fp64_frac"] = glups * FLOP_PER_LUP_3D_O4 / 1e3 / FP64_PEAK_TFLOPS
+        probe[name] = rec
         sp.close()
         del sp
     return probe

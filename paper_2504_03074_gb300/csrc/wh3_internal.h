@@ -1,5 +1,6 @@
-// wh3_internal.h -- the three-dimensional (second-order) path of libwaveholtz: device data
-// structures, kernel launchers and the host context (not part of the ABI).
+// wh3_internal.h -- the three-dimensional path of libwaveholtz (second order; fourth order on
+// Cartesian grids): device data structures, kernel launchers and the host context (not part
+// of the ABI).
 #pragma once
 #include <cstdint>
 #include <string>
@@ -15,20 +16,23 @@ namespace wh3 {
 enum Stencil3 : int32_t {
   kConst7 = 0,   // Cartesian grid, c = 1: four constant weights in Grid3Dev::cw
   kPoint7 = 1,   // per-point weights on the 7-point cross (all axis pairs orthogonal, or c(x))
-  kPoint19 = 2   // per-point weights on the 19-point box (a non-orthogonal axis pair)
+  kPoint19 = 2,  // per-point weights on the 19-point box (a non-orthogonal axis pair)
+  kConst13 = 3,  // fourth order, Cartesian grid, c = 1: seven constant weights in cw
+  kPoint13 = 4   // fourth order, Cartesian grid with c(x): per-point weights, 13 planes
 };
 // Per-point weight planes, in this order: centre (with the "2"), then the face neighbours
 // -x +x -y +y -z +z, then (kPoint19) the edge neighbours of pairs (x,y), (x,z), (y,z), each
 // as (-,-) (+,-) (-,+) (+,+).
-constexpr int kNw7 = 7, kNw19 = 19;
+// kPoint13: centre, then per axis a the offsets -1, +1, -2, +2 (planes 1 + 4a .. 4 + 4a).
+constexpr int kNw7 = 7, kNw19 = 19, kNw13 = 13;
 // Coefficient planes of curvilinear grids (c^2 folded in).
 enum { kA00 = 0, kA11, kA22, kA01, kA02, kA12, kB0, kB1, kB2, kNcoef };
 
 // March block: 32 x 8 threads, each marching kTZ points along axis 2.
 constexpr int kTX = 32, kTY = 8, kTZ = 8;
 
-// One component grid in device memory.  Extended arrays (ghosts included, ghost width 1 on
-// non-periodic axes) are stored with axis 0 fastest: (i, j, k) is at
+// One component grid in device memory.  Extended arrays (ghosts included, ghost width p/2 on
+// non-periodic axes at order p) are stored with axis 0 fastest: (i, j, k) is at
 // base + ((k + g2) * e1 + (j + g1)) * e0 + (i + g0).
 struct Grid3Dev {
   int32_t n0, n1, n2;
@@ -46,8 +50,10 @@ struct Grid3Dev {
   int64_t kbase;    // offset of coefficient plane 0 (plane stride ext), curvilinear only
   int64_t rbase;    // offset of metric plane 0 (9 planes, stride ext), curvilinear only
   double h[3];
-  double cw[4];     // kConst7: centre, axis-0, axis-1, axis-2 neighbour weights (dt^2 folded)
-  float cwf[4];     // the same rounded to FP32
+  double cw[7];     // kConst7: centre, axis-0, axis-1, axis-2 neighbour weights (dt^2
+                    // folded); kConst13: centre, then per axis a the +-1 and +-2 weights
+                    // at 1 + 2a and 2 + 2a
+  float cwf[7];     // the same rounded to FP32
 };
 
 // One march tile: 32 x 8 points of the (axis 0, axis 1) plane, kTZ planes deep.
@@ -65,6 +71,16 @@ struct Tile3 {
 constexpr int kUY = 16;
 struct Unit3 {
   int32_t grid, i0, j0, k0, nz, flags;
+};
+
+// Fourth-order ghost rule of one boundary point of a Dirichlet or Neumann face: the points
+// along the inward normal are U_k = W[q0 + k s], k = 0..3, the ghosts G1 = W[q0 - s] and
+// G2 = W[q0 - 2 s].  a2 = c^2 / (12 h_n^2) of the boundary point for a Dirichlet face, 0
+// for a Neumann face.
+struct Ghost4 {
+  int64_t q0;
+  int64_t s;
+  double a2;
 };
 
 // Per-step tables of the prepared frequency.
@@ -116,6 +132,23 @@ void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t m
 void launch_dirichlet3(bool fp32, cudaStream_t s, int64_t n, const int64_t *idx,
                        const double *g, void *W, double *V, double gfac, const double *wf,
                        int level);
+// Fourth order (Cartesian grids): per-point weights of kPoint13 grids, one step of the
+// 13-point march (same arguments as launch_march3), and the level's ghost rules and
+// width-5 interpolation: receiver r's donor (i0 + a, j0 + b, k0 + c) at gbase[r] +
+// goff[a R + r] + goff[(5 + b) R + r] + goff[(10 + c) R + r], weights likewise in gw;
+// each Ghost4 item solves its two ghosts with the forcing term fcl F[q0] (fcl = the forcing
+// switch times cos(omega_e t^level); F the FP64 forcing in the state layout).
+void launch_weight3o4(bool fp32, cudaStream_t s, const Grid3Dev *grids, int gidx,
+                      const Grid3Dev &G, const int8_t *mask, const double *c2, void *Wt,
+                      double dt2);
+void launch_march3o4(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
+                     const Tile3 *tiles, const int8_t *mask, const void *Wn, const void *Wprev,
+                     void *Wout, const void *F, const void *Wt, double *V, Tab3 tab, int n,
+                     double fs);
+void launch_gather3o4(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nitems,
+                      const int64_t *ridx, const int32_t *gbase, const int32_t *goff,
+                      const double *gw, const Ghost4 *items, const double *F, double fcl,
+                      void *W, double *V, const double *wf, int level);
 // vout (compact) = W (extended, FP64) at discretization points, zero elsewhere.
 void launch_disc3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,
                   const int8_t *mask, const double *W, double *vout);

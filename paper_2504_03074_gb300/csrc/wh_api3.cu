@@ -1,7 +1,8 @@
-// wh_api3.cu -- host side of the three-dimensional, second-order path of libwaveholtz.
+// wh_api3.cu -- host side of the three-dimensional path of libwaveholtz (second order; fourth
+// order on Cartesian grids).
 //
 // Validates and uploads a 3D overset grid description (component grids with masks, metrics
-// and c(x)^2; explicit 3 x 3 x 3 interpolation), prepares one frequency (coefficients and
+// and c(x)^2; explicit (p + 1)^3 interpolation), prepares one frequency (coefficients and
 // the CFL bound on the device, Recipe OmegaTildeExplicit, alpha_d of Eq. alphad, stencil
 // weights, per-step tables) and issues one WaveHoltz iteration as init + a CUDA graph of
 // 2M + 1 kernels + output.  The solvers of wh_api.cu (fixed-point iteration, GMRES, the
@@ -36,6 +37,7 @@ struct HostGrid3 {
 }  // namespace
 
 struct Ctx3 {
+  int order = 2;  // 2, or 4 (Cartesian grids only); fixed by the context's options
   std::vector<HostGrid3> grids;
   int64_t nrecv = 0;
   std::vector<int32_t> rg, ri, rj, rk, dg, di, dj, dk;
@@ -68,6 +70,9 @@ struct Ctx3 {
   double dt2 = 0.0;
   Tab3 tab{};
   cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [fp32][forcing]
+  // fourth order: the ghost rules of the boundary points of Dirichlet and Neumann faces
+  int64_t ng4 = 0;
+  Ghost4 *d_g4 = nullptr;
   // Neumann ghost copies (grid, i, j, k of destination and source), kept for the blocking plan
   std::vector<int32_t> nghost_dst, nghost_src;  // 4 ints per copy
   // temporal blocking of the FP32 march: depth K (1 = off), unit depth along axis 2, the
@@ -154,6 +159,8 @@ void free_all(Ctx3 *c) {
   c->d_ridx = nullptr;
   c->d_gbase = c->d_goff = c->d_gdst = c->d_gsrc = nullptr;
   c->d_gw = nullptr;
+  c->ng4 = 0;
+  c->d_g4 = nullptr;
   c->d_tabs = nullptr;
   c->d_ftabs = nullptr;
   c->tabs_cap = 0;
@@ -262,6 +269,74 @@ wh_status check_grid(const HostGrid3 &G, std::string &err) {
   return WH_OK;
 }
 
+// Structural checks at fourth order (Cartesian grids).  A discretization point on a
+// non-periodic side must lie on a Neumann side; every grid point its 13-point stencil reads
+// must be in use, and every ghost it reads must be one that a rule fills: the boundary point
+// of that grid line is a discretization point of a Neumann face or a Dirichlet point of a
+// Dirichlet face.  The rules read the boundary point and three points inward, which may not
+// be receivers (the kernel that applies the rules rewrites receivers at the same time).
+wh_status check_grid4(const HostGrid3 &G, std::string &err) {
+  const int n0 = G.d.n[0], n1 = G.d.n[1], n2 = G.d.n[2];
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n0; ++i) {
+        if (G.mask[cidx(G, i, j, k)] != WH_DISC) continue;
+        const int ix[3] = {i, j, k};
+        for (int a = 0; a < 3; ++a) {
+          const int na = G.d.n[a];
+          if (!periodic(G, a))
+            for (int hi = 0; hi < 2; ++hi)
+              if (ix[a] == (hi ? na - 1 : 0) && G.d.bc[2 * a + hi] != WH_BC_NEUMANN)
+                return fail3(err, WH_ERR_GRID,
+                             "discretization point (%d,%d,%d) lies on a side without a Neumann "
+                             "condition", i, j, k);
+          for (int d = -2; d <= 2; ++d) {
+            if (d == 0) continue;
+            int p[3] = {i, j, k};
+            p[a] += d;
+            if (periodic(G, a) || (p[a] >= 0 && p[a] < na)) {
+              if (mask_at(G, p[0], p[1], p[2]) == WH_UNUSED)
+                return fail3(err, WH_ERR_GRID,
+                             "the stencil of discretization point (%d,%d,%d) reads an unused "
+                             "point", i, j, k);
+              continue;
+            }
+            const int hi = p[a] >= na ? 1 : 0, code = G.d.bc[2 * a + hi];
+            p[a] = hi ? na - 1 : 0;
+            const int mb = mask_at(G, p[0], p[1], p[2]);
+            if (!((code == WH_BC_NEUMANN && mb == WH_DISC) ||
+                  (code == WH_BC_DIRICHLET && mb == WH_DIRICHLET)))
+              return fail3(err, WH_ERR_GRID,
+                           "the stencil of discretization point (%d,%d,%d) reads a ghost point "
+                           "that no boundary rule fills", i, j, k);
+          }
+        }
+      }
+  for (int s = 0; s < 6; ++s) {
+    const int code = G.d.bc[s];
+    if (code != WH_BC_NEUMANN && code != WH_BC_DIRICHLET) continue;
+    const int a = s / 2, hi = s % 2, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    for (int v = 0; v < G.d.n[t2]; ++v)
+      for (int u = 0; u < G.d.n[t1]; ++u) {
+        int p[3];
+        p[t1] = u;
+        p[t2] = v;
+        p[a] = hi ? G.d.n[a] - 1 : 0;
+        const int mb = mask_at(G, p[0], p[1], p[2]);
+        if (mb != (code == WH_BC_NEUMANN ? WH_DISC : WH_DIRICHLET)) continue;
+        for (int kk = 1; kk <= 3; ++kk) {
+          int q[3] = {p[0], p[1], p[2]};
+          q[a] += hi ? -kk : kk;
+          if (mask_at(G, q[0], q[1], q[2]) == WH_INTERP)
+            return fail3(err, WH_ERR_GRID,
+                         "the fourth-order ghost rule of boundary point (%d,%d,%d) reads an "
+                         "interpolation point", p[0], p[1], p[2]);
+        }
+      }
+  }
+  return WH_OK;
+}
+
 // Device layout: extended arrays of all grids in one state array (each starting on a
 // 32-element boundary), tiles, masks, metrics, c^2, forcing, interpolation lists, Neumann
 // ghost lists.
@@ -288,7 +363,10 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
     D.per = (periodic(H, 0) ? 1 : 0) | (periodic(H, 1) ? 2 : 0) | (periodic(H, 2) ? 4 : 0);
     D.kind = H.d.kind;
     D.ortho = H.d.kind == WH_CARTESIAN ? 7 : H.d.ortho;
-    if (H.d.kind == WH_CARTESIAN && H.c2.empty()) {
+    if (c->order == 4) {  // Cartesian grids only
+      D.stencil = H.c2.empty() ? kConst13 : kPoint13;
+      D.nw = H.c2.empty() ? 0 : kNw13;
+    } else if (H.d.kind == WH_CARTESIAN && H.c2.empty()) {
       D.stencil = kConst7;
       D.nw = 0;
     } else if (D.ortho == 7) {
@@ -357,9 +435,10 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
   // interpolation: receiver index; donor corner index, per-axis offsets (wrapped on
   // periodic axes) and per-axis weights, as planes of R entries
   const int64_t R = c->nrecv;
+  const int Wd = c->order + 1;  // donor stencil width
   std::vector<int64_t> ridx(R > 0 ? R : 1);
-  std::vector<int32_t> gbase(R > 0 ? R : 1), goff(R > 0 ? R * 9 : 1);
-  std::vector<double> gw(R > 0 ? R * 9 : 1);
+  std::vector<int32_t> gbase(R > 0 ? R : 1), goff(R > 0 ? R * 3 * Wd : 1);
+  std::vector<double> gw(R > 0 ? R * 3 * Wd : 1);
   for (int64_t r = 0; r < R; ++r) {
     const HostGrid3 &RG = c->grids[c->rg[r]];
     ridx[r] = c->hg[c->rg[r]].base + eidx(RG, c->ri[r], c->rj[r], c->rk[r]);
@@ -369,22 +448,22 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
     const int64_t corner = eidx(DG, c0[0], c0[1], c0[2]);
     gbase[r] = (int32_t)(db + corner);
     for (int a = 0; a < 3; ++a)
-      for (int t = 0; t < 3; ++t) {
+      for (int t = 0; t < Wd; ++t) {
         int d[3] = {c0[0], c0[1], c0[2]};
         d[a] += t;
-        goff[(3 * a + t) * R + r] = (int32_t)(eidx(DG, d[0], d[1], d[2]) - corner);
+        goff[(Wd * a + t) * R + r] = (int32_t)(eidx(DG, d[0], d[1], d[2]) - corner);
       }
-    for (int t = 0; t < 3; ++t) {
-      gw[t * R + r] = c->wx[r * 3 + t];
-      gw[(3 + t) * R + r] = c->wy[r * 3 + t];
-      gw[(6 + t) * R + r] = c->wz[r * 3 + t];
+    for (int t = 0; t < Wd; ++t) {
+      gw[t * R + r] = c->wx[r * Wd + t];
+      gw[(Wd + t) * R + r] = c->wy[r * Wd + t];
+      gw[(2 * Wd + t) * R + r] = c->wz[r * Wd + t];
     }
   }
   // Neumann ghosts next to discretization points
   std::vector<int32_t> gdst, gsrc;
   c->nghost_dst.clear();
   c->nghost_src.clear();
-  for (int g = 0; g < ng; ++g) {
+  for (int g = 0; g < ng && c->order == 2; ++g) {
     const HostGrid3 &H = c->grids[g];
     const int64_t b0 = c->hg[g].base;
     for (int s = 0; s < 6; ++s) {
@@ -424,6 +503,41 @@ wh_status build_layout(Ctx3 *c, std::string &err) {
   CK3(cudaMemcpy(c->d_gw, gw.data(), gw.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK3(cudaMemcpy(c->d_gdst, gdst.data(), gdst.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CK3(cudaMemcpy(c->d_gsrc, gsrc.data(), gsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (c->order == 4) {
+    // the fourth-order ghost rules: one item per boundary point of a Neumann face that is a
+    // discretization point and per Dirichlet point of a Dirichlet face
+    std::vector<Ghost4> items;
+    for (int g = 0; g < ng; ++g) {
+      const HostGrid3 &H = c->grids[g];
+      const Grid3Dev &D = c->hg[g];
+      const int64_t sa[3] = {1, (int64_t)D.e0, (int64_t)D.e0 * D.e1};
+      for (int s = 0; s < 6; ++s) {
+        const int code = H.d.bc[s];
+        if (code != WH_BC_NEUMANN && code != WH_BC_DIRICHLET) continue;
+        const int a = s / 2, hi = s % 2, t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+        for (int v = 0; v < H.d.n[t2]; ++v)
+          for (int u = 0; u < H.d.n[t1]; ++u) {
+            int p[3];
+            p[t1] = u;
+            p[t2] = v;
+            p[a] = hi ? H.d.n[a] - 1 : 0;
+            const int64_t pc = cidx(H, p[0], p[1], p[2]);
+            if (H.mask[pc] != (code == WH_BC_NEUMANN ? WH_DISC : WH_DIRICHLET)) continue;
+            Ghost4 it;
+            it.q0 = D.base + eidx(H, p[0], p[1], p[2]);
+            it.s = hi ? -sa[a] : sa[a];
+            const double c2b = H.c2.empty() ? 1.0 : H.c2[pc];
+            it.a2 = code == WH_BC_DIRICHLET ? c2b / (12.0 * H.d.h[a] * H.d.h[a]) : 0.0;
+            items.push_back(it);
+          }
+      }
+    }
+    c->ng4 = (int64_t)items.size();
+    if ((st = alloc3(c, &c->d_g4, std::max<size_t>(items.size(), 1), err))) return st;
+    if (!items.empty())
+      CK3(cudaMemcpy(c->d_g4, items.data(), items.size() * sizeof(Ghost4),
+                     cudaMemcpyHostToDevice));
+  }
   {
     // Dirichlet points of the grids with boundary data
     std::vector<int64_t> di;
@@ -602,7 +716,9 @@ wh_status plan_blocking(Ctx3 *c, int K, int uz, std::string &err) {
   return WH_OK;
 }
 
-bool blocked(const Ctx3 *c, bool fp32) { return fp32 && c->plan_K > 1 && !c->units.empty(); }
+bool blocked(const Ctx3 *c, bool fp32) {
+  return fp32 && c->order == 2 && c->plan_K > 1 && !c->units.empty();
+}
 
 // The library's choice: depth 3 with 64-plane units when at least kAutoBlockedShare of the
 // points advance in blocked units, else single steps.  Measured: on a 512^3 cube (all
@@ -683,9 +799,15 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
   const void *Wt = fp32 ? (const void *)c->d_Wt32 : (const void *)c->d_Wt;
   const double fs = forcing ? 1.0 : 0.0;
   auto gather = [&](void *W, int level) {
+    const double fcl = fs * std::cos(c->omega_e * level * c->dt);
+    if (c->order == 4) {
+      launch_gather3o4(fp32, s, c->nrecv, c->ng4, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
+                       c->d_g4, c->d_F, fcl, W, c->d_V, c->tab.wf, level);
+      return;
+    }
     if (c->ndir)  // Dirichlet data first: receivers may take them as donors
-      launch_dirichlet3(fp32, s, c->ndir, c->d_dir_idx, c->d_dir_g, W, c->d_V,
-                        fs * std::cos(c->omega_e * level * c->dt), c->tab.wf, level);
+      launch_dirichlet3(fp32, s, c->ndir, c->d_dir_idx, c->d_dir_g, W, c->d_V, fcl, c->tab.wf,
+                        level);
     launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
                    c->d_gdst, c->d_gsrc, W, c->d_V, c->tab.wf, level);
   };
@@ -693,8 +815,12 @@ void launch_steps(Ctx3 *c, bool fp32, int forcing, cudaStream_t s) {
   for (int n = 0; n < c->M; ++n) {
     void *cur = (n & 1) ? Wb : Wa;
     void *oth = (n & 1) ? Wa : Wb;
-    launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth,
-                  oth, F, Wt, c->d_V, c->tab, n, fs);
+    if (c->order == 4)
+      launch_march3o4(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur,
+                      oth, oth, F, Wt, c->d_V, c->tab, n, fs);
+    else
+      launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur, oth,
+                    oth, F, Wt, c->d_V, c->tab, n, fs);
     gather(oth, n + 1);
   }
 }
@@ -745,10 +871,17 @@ wh_status first_step(Ctx3 *c, const double *y, double *wy, double *w1, cudaStrea
   const int ng = (int)c->grids.size();
   launch_init3(false, s, c->d_grids, ng, c->max_ext, c->d_mask, y, c->d_Wa, c->d_V, c->tab.wf);
   // the ghost rules of level 0 only (no receivers)
-  launch_gather3(false, s, 0, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw, c->d_gdst,
-                 c->d_gsrc, c->d_Wa, c->d_V, c->tab.wf, 0);
-  launch_march3(false, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, c->d_Wa,
-                c->d_Wb, c->d_Wb, c->d_F, c->d_Wt, c->d_V, c->tab, 0, 0.0);
+  if (c->order == 4) {
+    launch_gather3o4(false, s, 0, c->ng4, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw, c->d_g4,
+                     c->d_F, 0.0, c->d_Wa, c->d_V, c->tab.wf, 0);
+    launch_march3o4(false, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, c->d_Wa,
+                    c->d_Wb, c->d_Wb, c->d_F, c->d_Wt, c->d_V, c->tab, 0, 0.0);
+  } else {
+    launch_gather3(false, s, 0, c->nghost, c->d_ridx, c->d_gbase, c->d_goff, c->d_gw,
+                   c->d_gdst, c->d_gsrc, c->d_Wa, c->d_V, c->tab.wf, 0);
+    launch_march3(false, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, c->d_Wa,
+                  c->d_Wb, c->d_Wb, c->d_F, c->d_Wt, c->d_V, c->tab, 0, 0.0);
+  }
   launch_disc3(s, c->d_grids, ng, c->max_compact, c->d_mask, c->d_Wa, wy);
   launch_disc3(s, c->d_grids, ng, c->max_compact, c->d_mask, c->d_Wb, w1);
   CK3(cudaGetLastError());
@@ -757,7 +890,10 @@ wh_status first_step(Ctx3 *c, const double *y, double *wy, double *w1, cudaStrea
 
 wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std::string &err) {
   if (!d || !d->mask) return fail3(err, WH_ERR_ARG, "null grid description or mask");
-  if (order != 2) return fail3(err, WH_ERR_ARG, "three-dimensional grids need order 2");
+  if (order != 2 && order != 4)
+    return fail3(err, WH_ERR_ARG, "three-dimensional grids need order 2 or 4");
+  if (order == 4 && d->kind != WH_CARTESIAN)
+    return fail3(err, WH_ERR_ARG, "fourth order in three dimensions: Cartesian grids only");
   if (d->instance != 0)
     return fail3(err, WH_ERR_ARG, "three-dimensional contexts hold one instance");
   if (d->kind != WH_CARTESIAN && d->kind != WH_CURVILINEAR)
@@ -778,9 +914,18 @@ wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std:
       return fail3(err, WH_ERR_ARG, "axis %d: %d points (need >= %d)", a, d->n[a], p0 ? 3 : 5);
     if (!(d->h[a] > 0) || !std::isfinite(d->h[a]))
       return fail3(err, WH_ERR_ARG, "spacing of axis %d must be > 0", a);
-    H.g[a] = p0 ? 0 : 1;
+    H.g[a] = p0 ? 0 : order / 2;
     H.e[a] = d->n[a] + 2 * H.g[a];
   }
+  if (order == 4)
+    // the fourth-order Neumann rule is unstable at corners with another physical face
+    for (int s = 0; s < 6; ++s)
+      for (int s2 = 0; s2 < 6; ++s2)
+        if (s / 2 != s2 / 2 && d->bc[s] == WH_BC_NEUMANN &&
+            (d->bc[s2] == WH_BC_NEUMANN || d->bc[s2] == WH_BC_DIRICHLET))
+          return fail3(err, WH_ERR_ARG,
+                       "fourth order: a Neumann face may only meet periodic or interpolation "
+                       "faces");
   if (d->kind == WH_CURVILINEAR)
     for (int s = 0; s < 6; ++s) {
       if (d->bc[s] != WH_BC_NEUMANN) continue;
@@ -801,8 +946,9 @@ wh_status add_grid(Ctx3 *c, const wh_grid3_desc *d, int order, int32_t *id, std:
     for (double v : H.c2)
       if (!(v > 0) || !std::isfinite(v)) return fail3(err, WH_ERR_ARG, "c^2 must be > 0");
   }
-  wh_status st = check_grid(H, err);
+  wh_status st = order == 4 ? check_grid4(H, err) : check_grid(H, err);
   if (st) return st;
+  c->order = order;
   c->grids.push_back(std::move(H));
   c->dirty = true;
   if (id) *id = (int32_t)c->grids.size() - 1;
@@ -816,6 +962,7 @@ wh_status set_interp(Ctx3 *c, const wh_interp3_desc *d, std::string &err) {
                 !d->donor_i0 || !d->donor_j0 || !d->donor_k0 || !d->wx || !d->wy || !d->wz))
     return fail3(err, WH_ERR_ARG, "null interpolation array");
   const int ng = (int)c->grids.size();
+  const int W = c->order + 1;  // donor stencil width
   std::vector<std::vector<int8_t>> seen(ng);
   for (int g = 0; g < ng; ++g) seen[g].assign(c->grids[g].mask.size(), 0);
   for (int64_t r = 0; r < n; ++r) {
@@ -834,21 +981,21 @@ wh_status set_interp(Ctx3 *c, const wh_interp3_desc *d, std::string &err) {
     const HostGrid3 &DG = c->grids[dgid];
     const int c0[3] = {d->donor_i0[r], d->donor_j0[r], d->donor_k0[r]};
     for (int a = 0; a < 3; ++a)
-      if (!periodic(DG, a) && (c0[a] < 0 || c0[a] + 2 >= DG.d.n[a]))
+      if (!periodic(DG, a) && (c0[a] < 0 || c0[a] + W - 1 >= DG.d.n[a]))
         return fail3(err, WH_ERR_GRID, "receiver %lld: donor stencil outside its grid",
                      (long long)r);
-    for (int cc = 0; cc < 3; ++cc)
-      for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) {
+    for (int cc = 0; cc < W; ++cc)
+      for (int b = 0; b < W; ++b)
+        for (int a = 0; a < W; ++a) {
           const int m = mask_at(DG, c0[0] + a, c0[1] + b, c0[2] + cc);
           if (m != WH_DISC && m != WH_DIRICHLET)
             return fail3(err, WH_ERR_GRID,
                          "receiver %lld: a donor is not a discretization or Dirichlet point "
                          "(explicit interpolation)", (long long)r);
         }
-    for (int a = 0; a < 3; ++a)
-      if (!std::isfinite(d->wx[r * 3 + a]) || !std::isfinite(d->wy[r * 3 + a]) ||
-          !std::isfinite(d->wz[r * 3 + a]))
+    for (int a = 0; a < W; ++a)
+      if (!std::isfinite(d->wx[r * W + a]) || !std::isfinite(d->wy[r * W + a]) ||
+          !std::isfinite(d->wz[r * W + a]))
         return fail3(err, WH_ERR_ARG, "receiver %lld: weight not finite", (long long)r);
   }
   for (int g = 0; g < ng; ++g)
@@ -864,9 +1011,9 @@ wh_status set_interp(Ctx3 *c, const wh_interp3_desc *d, std::string &err) {
   cp(c->di, d->donor_i0);
   cp(c->dj, d->donor_j0);
   cp(c->dk, d->donor_k0);
-  c->wx.assign(d->wx, d->wx + 3 * n);
-  c->wy.assign(d->wy, d->wy + 3 * n);
-  c->wz.assign(d->wz, d->wz + 3 * n);
+  c->wx.assign(d->wx, d->wx + W * n);
+  c->wy.assign(d->wy, d->wy + W * n);
+  c->wz.assign(d->wz, d->wz + W * n);
   c->nrecv = n;
   c->dirty = true;
   return WH_OK;
@@ -888,6 +1035,8 @@ wh_status set_boundary_data(Ctx3 *c, int32_t gid, const double *g, std::string &
   if (gid < 0 || gid >= (int)c->grids.size())
     return fail3(err, WH_ERR_ARG, "bad boundary data arguments");
   HostGrid3 &H = c->grids[gid];
+  if (g && c->order != 2)
+    return fail3(err, WH_ERR_ARG, "boundary data need order 2 in three dimensions");
   if (g)
     for (size_t q = 0; q < H.mask.size(); ++q)
       if (!std::isfinite(g[q])) return fail3(err, WH_ERR_ARG, "non-finite boundary data");
@@ -934,8 +1083,9 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
   std::memcpy(&smax, &bits, sizeof smax);
   if (!(smax > 0) || !std::isfinite(smax))
     return fail3(err, WH_ERR_GRID, "no discretization point");
-  // Eq. dtForCartesian at second order (C = 1), Recipe OmegaTildeExplicit, Eq. alphad
-  const double dtmax = opt.cfl / std::sqrt(smax);
+  // Eq. dtForCartesian (C = 1 at second order, sqrt(3)/2 at fourth), Recipe
+  // OmegaTildeExplicit, Eq. alphad
+  const double dtmax = opt.cfl * (c->order == 4 ? std::sqrt(3.0) / 2.0 : 1.0) / std::sqrt(smax);
   int Nt = (int)std::ceil(2.0 * M_PI / (omega * dtmax));
   if (Nt < 2) Nt = 2;
   double dt = 2.0 / omega * std::sin(M_PI / Nt);
@@ -983,13 +1133,23 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
   c->tab.dt2h = 0.5 * dt * dt;
   c->tab.dt2hf = (float)(0.5 * dt * dt);
   // constant weights (Cartesian, c = 1): centre 2 - 2 dt^2 sum 1/h^2, neighbours dt^2/h^2
+  // fourth order (kConst13): centre 2 - (30/12) dt^2 sum 1/h^2, per axis the +-1 neighbours
+  // (16/12) dt^2/h^2 and the +-2 neighbours -(1/12) dt^2/h^2
   for (auto &D : c->hg) {
-    if (D.stencil != kConst7) continue;
+    if (D.stencil != kConst7 && D.stencil != kConst13) continue;
     double x[3];
     for (int a = 0; a < 3; ++a) x[a] = c->dt2 / (D.h[a] * D.h[a]);
-    D.cw[0] = 2.0 - 2.0 * (x[0] + x[1] + x[2]);
-    for (int a = 0; a < 3; ++a) D.cw[1 + a] = x[a];
-    for (int a = 0; a < 4; ++a) D.cwf[a] = (float)D.cw[a];
+    if (D.stencil == kConst7) {
+      D.cw[0] = 2.0 - 2.0 * (x[0] + x[1] + x[2]);
+      for (int a = 0; a < 3; ++a) D.cw[1 + a] = x[a];
+    } else {
+      D.cw[0] = 2.0 - 2.5 * (x[0] + x[1] + x[2]);
+      for (int a = 0; a < 3; ++a) {
+        D.cw[1 + 2 * a] = x[a] * (16.0 / 12.0);
+        D.cw[2 + 2 * a] = -x[a] / 12.0;
+      }
+    }
+    for (int a = 0; a < 7; ++a) D.cwf[a] = (float)D.cw[a];
   }
   CK3(cudaMemcpy(c->d_grids, c->hg.data(), ng * sizeof(Grid3Dev), cudaMemcpyHostToDevice));
   CK3(cudaStreamSynchronize(cudaStreamLegacy));
@@ -1000,7 +1160,14 @@ wh_status prepare(Ctx3 *c, const wh_options &opt, double omega, cudaStream_t s,
       return st;
   }
   for (int g = 0; g < ng; ++g) {
-    if (c->hg[g].stencil == kConst7) continue;
+    if (c->hg[g].stencil == kConst7 || c->hg[g].stencil == kConst13) continue;
+    if (c->hg[g].stencil == kPoint13) {
+      launch_weight3o4(false, s, c->d_grids, g, c->hg[g], c->d_mask, c->d_c2, c->d_Wt, c->dt2);
+      if (fp32)
+        launch_weight3o4(true, s, c->d_grids, g, c->hg[g], c->d_mask, c->d_c2, c->d_Wt32,
+                         c->dt2);
+      continue;
+    }
     launch_weight3(false, s, c->d_grids, g, c->hg[g], c->d_mask, c->d_coef, c->d_c2, c->d_Wt,
                    c->dt2);
     if (fp32)
@@ -1130,12 +1297,20 @@ wh_status profile(Ctx3 *c, bool fp32, cudaStream_t s, int reps, double *ms, int3
         void *cur = (n & 1) ? Wb : Wa;
         void *oth = (n & 1) ? Wa : Wb;
         timed(0, [&] {
-          launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask, cur,
-                        oth, oth, F, Wt, c->d_V, c->tab, n, 0.0);
+          if (c->order == 4)
+            launch_march3o4(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask,
+                            cur, oth, oth, F, Wt, c->d_V, c->tab, n, 0.0);
+          else
+            launch_march3(fp32, s, (int)c->tiles.size(), c->d_grids, c->d_tiles, c->d_mask,
+                          cur, oth, oth, F, Wt, c->d_V, c->tab, n, 0.0);
         });
         timed(1, [&] {
-          launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff,
-                         c->d_gw, c->d_gdst, c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
+          if (c->order == 4)
+            launch_gather3o4(fp32, s, c->nrecv, c->ng4, c->d_ridx, c->d_gbase, c->d_goff,
+                             c->d_gw, c->d_g4, c->d_F, 0.0, oth, c->d_V, c->tab.wf, n + 1);
+          else
+            launch_gather3(fp32, s, c->nrecv, c->nghost, c->d_ridx, c->d_gbase, c->d_goff,
+                           c->d_gw, c->d_gdst, c->d_gsrc, oth, c->d_V, c->tab.wf, n + 1);
         });
       }
     }

@@ -1,5 +1,5 @@
-// wh_kernels3.cu -- CUDA kernels of the three-dimensional, second-order WaveHoltz path
-// (sm_103a).
+// wh_kernels3.cu -- CUDA kernels of the three-dimensional WaveHoltz path (sm_103a): second
+// order on any grid, fourth order on Cartesian grids (march3o4 / gather3o4 at the end).
 //
 // One WaveHoltz iteration (Algorithm 1) on a 3D overset grid is
 //   init3 -> gather3(level 0) -> [march3(n) -> gather3(level n + 1)] for n < M -> finish3:
@@ -672,6 +672,164 @@ __global__ void convert_kernel(const double *src, T *dst, int64_t n) {
     dst[t] = (T)src[t];
 }
 
+// ------------------------------------------------------- fourth order (Cartesian grids)
+
+// Per-point weights of a kPoint13 grid with dt^2 c(x)^2 folded in: the second difference
+// D+D-(1 - h^2/12 D+D-) = (-W_-2 + 16 W_-1 - 30 W + 16 W_+1 - W_+2) / (12 h^2) per axis
+// (Eq. SecondDerivOrderp, mu < 2), so with x_a = dt^2 c^2 / h_a^2 the centre (with the "2"
+// of the leapfrog) is 2 - (30/12) sum_a x_a, the +-1 neighbours (16/12) x_a and the +-2
+// neighbours -(1/12) x_a.
+template <typename T>
+__global__ void weight3o4_kernel(const Grid3Dev *grids, int gidx, const int8_t *mask,
+                                 const double *c2, T *Wt, double dt2) {
+  const Grid3Dev G = grids[gidx];
+  const int64_t npts = (int64_t)G.n0 * G.n1 * G.n2;
+  const int64_t E = G.ext;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npts;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % G.n0), j = (int)((t / G.n0) % G.n1), k = (int)(t / ((int64_t)G.n0 * G.n1));
+    const int64_t q = at3(G, i, j, k), ql = q - G.base;
+    if (mask[q] != kDisc) continue;
+    T *W = Wt + G.wbase + ql;
+    double centre = 2.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double x = dt2 * c2[q] / (G.h[a] * G.h[a]);
+      centre -= 2.5 * x;
+      W[(1 + 4 * a) * E] = W[(2 + 4 * a) * E] = (T)(x * (16.0 / 12.0));
+      W[(3 + 4 * a) * E] = W[(4 + 4 * a) * E] = (T)(-x / 12.0);
+    }
+    W[0] = (T)centre;
+  }
+}
+
+// One step n -> n + 1 of the fourth-order march (Eq. WaveSchemeexplicit with the 13-point
+// Laplacian above) with the fused filter term of level n + 1.  Block = one Tile3; each
+// thread marches kTZ points along axis 2.  The +-1 and +-2 neighbours wrap on periodic axes
+// and reach the two ghost layers on the others.  W^{n+1} overwrites W^{n-1} in place.
+template <typename T>
+__global__ void __launch_bounds__(kTX *kTY) march3o4_kernel(
+    const Grid3Dev *__restrict__ grids, const Tile3 *__restrict__ tiles,
+    const int8_t *__restrict__ mask, const T *__restrict__ Wn, const T *Wprev, T *Wout,
+    const T *__restrict__ F, const T *__restrict__ Wt, double *__restrict__ V, Tab3 tab, int n,
+    double fs) {
+  const Tile3 tl = tiles[blockIdx.x];
+  const Grid3Dev &G = grids[tl.grid];
+  const int i = tl.i0 + threadIdx.x, j = tl.j0 + threadIdx.y;
+  if (i >= G.n0 || j >= G.n1) return;
+  const bool first = n == 0;
+  const double wfn = tab.wf[n + 1];
+  const T fcn = first ? fsel<T>(tab.dt2h, tab.dt2hf) : fsel<T>(tab.fc[n], tab.fcf[n]);
+  const T fsT = (T)fs;
+  const int kend = min(tl.k0 + kTZ, G.n2);
+  const int64_t e0 = G.e0, pl = (int64_t)G.e0 * G.e1, E = G.ext;
+  const int dd[4] = {-1, 1, -2, 2};
+  int64_t ox[4], oy[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    ox[t] = (int64_t)(wrap(i + dd[t], G.n0, G.per & 1) - i);
+    oy[t] = (int64_t)(wrap(j + dd[t], G.n1, G.per & 2) - j) * e0;
+  }
+  const bool cst = G.stencil == kConst13;
+  T cw[7];
+#pragma unroll
+  for (int t = 0; t < 7; ++t) cw[t] = fsel<T>(G.cw[t], G.cwf[t]);
+  for (int k = tl.k0; k < kend; ++k) {
+    const int64_t q = at3(G, i, j, k);
+    if (mask[q] != kDisc) continue;
+    int64_t oz[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) oz[t] = (int64_t)(wrap(k + dd[t], G.n2, G.per & 4) - k) * pl;
+    T S;
+    if (cst) {
+      S = cw[0] * Wn[q] + cw[1] * (Wn[q + ox[0]] + Wn[q + ox[1]]) +
+          cw[2] * (Wn[q + ox[2]] + Wn[q + ox[3]]) + cw[3] * (Wn[q + oy[0]] + Wn[q + oy[1]]) +
+          cw[4] * (Wn[q + oy[2]] + Wn[q + oy[3]]) + cw[5] * (Wn[q + oz[0]] + Wn[q + oz[1]]) +
+          cw[6] * (Wn[q + oz[2]] + Wn[q + oz[3]]);
+    } else {
+      const T *w = Wt + G.wbase + (q - G.base);
+      S = w[0] * Wn[q];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        S += w[(1 + t) * E] * Wn[q + ox[t]] + w[(5 + t) * E] * Wn[q + oy[t]] +
+             w[(9 + t) * E] * Wn[q + oz[t]];
+    }
+    const T out = first ? (T)0.5 * S - fcn * fsT * F[q] : S - Wprev[q] - fcn * fsT * F[q];
+    Wout[q] = out;
+    V[q] += wfn * wh::to_f64(out);
+  }
+}
+
+// The ghost rules and the interpolation of one level at fourth order (Algorithm 2: after
+// every grid has advanced).  Receivers: the width-5 tensor product evaluated axis by axis,
+// one thread per receiver, with the receiver's filter term.  Ghost items: per boundary point
+// of a Dirichlet or Neumann face the two ghosts from a 2 x 2 solve of
+//   row 1, Dirichlet: c^2 (-G2 + 16 G1 - 30 U0 + 16 U1 - U2) / (12 h^2) = fcl f_b
+//          (the scheme at the boundary point, where W stays 0);
+//          Neumann: the centred fourth-order normal derivative 8 (U1 - G1) - (U2 - G2) = 0;
+//   row 2: the extrapolation D+^5 G2 = G2 - 5 G1 + 10 U0 - 10 U1 + 5 U2 - U3 = 0,
+// in FP64 from the level's values.  Donors and the points the rules read are discretization
+// or Dirichlet points (the host checks both), so neither part reads what the other writes.
+template <typename T>
+__global__ void __launch_bounds__(256) gather3o4_kernel(
+    int64_t nrecv, int64_t nitems, const int64_t *__restrict__ ridx,
+    const int32_t *__restrict__ gbase, const int32_t *__restrict__ goff,
+    const double *__restrict__ gw, const Ghost4 *__restrict__ items,
+    const double *__restrict__ F, double fcl, T *W, double *V, const double *__restrict__ wf,
+    int level) {
+  const double wl = wf[level];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrecv; r += stride) {
+    int32_t o[15];
+    double w[15];
+#pragma unroll
+    for (int t = 0; t < 15; ++t) {
+      o[t] = goff[t * nrecv + r];
+      w[t] = gw[t * nrecv + r];
+    }
+    const int64_t b0 = gbase[r];
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double col = 0.0;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        const T *x = W + b0 + o[5 + b] + o[10 + c];
+        double row = 0.0;
+#pragma unroll
+        for (int a = 0; a < 5; ++a) row = fma(w[a], wh::to_f64(x[o[a]]), row);
+        col = fma(w[5 + b], row, col);
+      }
+      s = fma(w[10 + c], col, s);
+    }
+    const T v = (T)s;
+    const int64_t q = ridx[r];
+    W[q] = v;
+    V[q] += wl * wh::to_f64(v);
+  }
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nitems; t += stride) {
+    const Ghost4 it = items[t];
+    double U[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) U[k] = wh::to_f64(W[it.q0 + k * it.s]);
+    const double a10 = -5.0, a11 = 1.0;
+    const double r1 = -(10.0 * U[0] - 10.0 * U[1] + 5.0 * U[2] - U[3]);
+    double a00, a01, r0;
+    if (it.a2 == 0.0) {
+      a00 = -8.0;
+      a01 = 1.0;
+      r0 = -(8.0 * U[1] - U[2]);
+    } else {
+      a00 = 16.0 * it.a2;
+      a01 = -it.a2;
+      r0 = fcl * F[it.q0] - it.a2 * (-30.0 * U[0] + 16.0 * U[1] - U[2]);
+    }
+    const double det = a00 * a11 - a01 * a10;
+    W[it.q0 - it.s] = (T)((r0 * a11 - a01 * r1) / det);
+    W[it.q0 - 2 * it.s] = (T)((a00 * r1 - r0 * a10) / det);
+  }
+}
+
 unsigned blocks_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b > 152 * 32) b = 152 * 32;
@@ -794,6 +952,52 @@ void launch_gather3(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nghost,
   else
     gather3_kernel<double><<<nb, threads, 0, s>>>(nrecv, nghost, ridx, gbase, goff, gw, gdst,
                                                   gsrc, (double *)W, V, wf, level);
+}
+
+void launch_weight3o4(bool fp32, cudaStream_t s, const Grid3Dev *grids, int gidx,
+                      const Grid3Dev &G, const int8_t *mask, const double *c2, void *Wt,
+                      double dt2) {
+  const int64_t n = (int64_t)G.n0 * G.n1 * G.n2;
+  if (fp32)
+    weight3o4_kernel<float><<<blocks_for(n, 256), 256, 0, s>>>(grids, gidx, mask, c2,
+                                                               (float *)Wt, dt2);
+  else
+    weight3o4_kernel<double><<<blocks_for(n, 256), 256, 0, s>>>(grids, gidx, mask, c2,
+                                                                (double *)Wt, dt2);
+}
+
+void launch_march3o4(bool fp32, cudaStream_t s, int ntiles, const Grid3Dev *grids,
+                     const Tile3 *tiles, const int8_t *mask, const void *Wn, const void *Wprev,
+                     void *Wout, const void *F, const void *Wt, double *V, Tab3 tab, int n,
+                     double fs) {
+  if (ntiles < 1) return;
+  dim3 tb(kTX, kTY);
+  if (fp32)
+    march3o4_kernel<float><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const float *)Wn,
+                                                 (const float *)Wprev, (float *)Wout,
+                                                 (const float *)F, (const float *)Wt, V, tab,
+                                                 n, fs);
+  else
+    march3o4_kernel<double><<<ntiles, tb, 0, s>>>(grids, tiles, mask, (const double *)Wn,
+                                                  (const double *)Wprev, (double *)Wout,
+                                                  (const double *)F, (const double *)Wt, V,
+                                                  tab, n, fs);
+}
+
+void launch_gather3o4(bool fp32, cudaStream_t s, int64_t nrecv, int64_t nitems,
+                      const int64_t *ridx, const int32_t *gbase, const int32_t *goff,
+                      const double *gw, const Ghost4 *items, const double *F, double fcl,
+                      void *W, double *V, const double *wf, int level) {
+  const int threads = 256;
+  int64_t need = nrecv > nitems ? nrecv : nitems;
+  if (need < 1) need = 1;
+  const unsigned nb = blocks_for(need, threads);
+  if (fp32)
+    gather3o4_kernel<float><<<nb, threads, 0, s>>>(nrecv, nitems, ridx, gbase, goff, gw, items,
+                                                   F, fcl, (float *)W, V, wf, level);
+  else
+    gather3o4_kernel<double><<<nb, threads, 0, s>>>(nrecv, nitems, ridx, gbase, goff, gw, items,
+                                                    F, fcl, (double *)W, V, wf, level);
 }
 
 void launch_finish3(cudaStream_t s, const Grid3Dev *grids, int ngrids, int64_t max_compact,

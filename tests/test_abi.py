@@ -180,17 +180,36 @@ def _interp3(W, it, **override):
 
 
 def test_grid3_validation_on_host(W):
-    """Three-dimensional grids: order 2 only, no mixing with 2D grids, Neumann axes must be
-    orthogonal, discretization points may not sit on non-Neumann sides or read unused
-    points, and interpolation data must be explicit and complete."""
+    """Three-dimensional grids: order 4 on Cartesian grids only, no mixing with 2D grids,
+    Neumann axes must be orthogonal, discretization points may not sit on non-Neumann sides
+    or read unused points, and interpolation data must be explicit and complete."""
     from paper_2504_03074_gb300 import grids3 as G3
     L = W.lib()
     gid = C.c_int32()
     cube = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [1] * 6)
-    # order 4 context: rejected
+    # order 4: Cartesian grids only, a Neumann face meets no other physical face, every
+    # ghost the 13-point stencil reads is filled by a rule, no boundary data
     h = _ctx(W, order=4)
     d, keep = _desc3(W, cube)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0, L.wh_last_error(h)
+    gdat = np.ones((9, 9, 9))
+    assert L.wh_set_boundary_data(h, 0, gdat.ctypes.data) == -1
+    patch = G3.pole_patch_grid("p", 9, 6, 0.5, 0.5, 0.3, 1.0)
+    d, keep = _desc3(W, patch)
     assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -1
+    neu = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [G.BC_NEUMANN] * 6)
+    d, keep = _desc3(W, neu)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -1
+    # faces without a rule whose ghosts the stencil of index-1 points would read
+    open_box = G3.cartesian_grid3("c", (9, 9, 9), (0, 0, 0), (1, 1, 1), [G.BC_NONE] * 6)
+    open_box.mask[:] = G.INTERP
+    open_box.mask[1:-1, 1:-1, 1:-1] = G.DISC
+    d, keep = _desc3(W, open_box)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -7
+    L.wh_destroy(h)
+    h = _ctx(W, order=2)
+    d, keep = _desc3(W, open_box)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0, L.wh_last_error(h)
     L.wh_destroy(h)
     # 2D and 3D grids do not mix
     h = _ctx(W, order=2)
