@@ -139,16 +139,21 @@ typedef struct {
   const double *wx, *wy;
 } wh_interp_desc;
 
-/* Three-dimensional grids (second order, Sec. 3 in three space dimensions).  A context
- * takes either two-dimensional grids (wh_add_grid / wh_set_interp) or three-dimensional ones
- * (wh_add_grid3 / wh_set_interp3), fixed by the first grid added; 3D contexts need
- * opt.order = 2 and hold one instance.  Compact 3D vectors hold n0*n1*n2 values per grid
- * with axis 0 fastest (index (k*n1 + j)*n0 + i); the ghost width is 1 on non-periodic axes
- * and 0 on periodic ones, and extended arrays cover [-g_a, n_a + g_a) per axis in the same
- * order.  Sides are [axis0-lo, axis0-hi, axis1-lo, axis1-hi, axis2-lo, axis2-hi].
+/* Three-dimensional grids (Sec. 3 in three space dimensions).  A context takes either
+ * two-dimensional grids (wh_add_grid / wh_set_interp) or three-dimensional ones
+ * (wh_add_grid3 / wh_set_interp3), fixed by the first grid added; 3D contexts hold one
+ * instance and take opt.order = 2 on any grid or opt.order = 4 on Cartesian grids only
+ * (second difference D+D-(1 - h^2/12 D+D-) per axis, Eq. SecondDerivOrderp; two ghost
+ * layers filled per boundary point of a Dirichlet face by the compatibility condition
+ * c^2 D_nn W_b = f_b cos(omega_e t) and of a Neumann face by the centred fourth-order
+ * D_n W = 0, each with the extrapolation D+^5 W_{-2} = 0; time-step constant sqrt(3)/2).
+ * Compact 3D vectors hold n0*n1*n2 values per grid with axis 0 fastest (index
+ * (k*n1 + j)*n0 + i); the ghost width is order/2 on non-periodic axes and 0 on periodic
+ * ones, and extended arrays cover [-g_a, n_a + g_a) per axis in the same order.  Sides are [axis0-lo, axis0-hi, axis1-lo, axis1-hi, axis2-lo, axis2-hi].
  *   n[3]    points per axis (boundary points included; a periodic axis lists each point
  *           once); n >= 5 on non-periodic axes, >= 3 on periodic ones.
- *   kind    WH_CARTESIAN (h physical) or WH_CURVILINEAR (h the parameter spacing).
+ *   kind    WH_CARTESIAN (h physical) or WH_CURVILINEAR (h the parameter spacing; order 2
+ *           only).
  *   bc[6]   per-side WH_BC_*; periodic sides come in pairs.  Discretization points may lie
  *           on a non-periodic side only if it is a Neumann side, and their inward neighbour
  *           must be a discretization or Dirichlet point.
@@ -158,13 +163,18 @@ typedef struct {
  *           two (the centred rule W_{-1} = W_{+1} is then the normal derivative).  Ignored
  *           on Cartesian grids.
  *   mask    n0*n1*n2 int8 point classes (WH_UNUSED ... WH_DIRICHLET).  A discretization
- *           point's stencil (the 7-point cross and the edge points of non-orthogonal pairs)
- *           must read no unused point.
+ *           point's stencil (the 7-point cross and the edge points of non-orthogonal pairs;
+ *           at order 4 the 13-point cross) must read no unused point.  At order 4 every
+ *           ghost it reads must be filled by a rule (the boundary point of that grid line is
+ *           a discretization point of a Neumann face or a Dirichlet point of a Dirichlet
+ *           face), the rules' three inward points may not be interpolation points, and a
+ *           Neumann face may only meet periodic or interpolation faces.
  *   rx      curvilinear: 9 extended arrays, array 3k+m = dr_k/dx_m.
  *   c2      n0*n1*n2 values of c(x)^2 > 0, or NULL for c = 1.
  * Host pointers, copied during the call.  Errors: WH_ERR_ARG (bad sizes, codes, spacing,
- * orthogonality of a Neumann axis), WH_ERR_GRID (stencils reading unused points, Neumann
- * inward neighbours), WH_ERR_STATE (a two-dimensional context). */
+ * orthogonality of a Neumann axis; at order 4 a curvilinear grid or a Neumann face meeting
+ * another physical face), WH_ERR_GRID (stencils reading unused points or unfilled ghosts,
+ * Neumann inward neighbours), WH_ERR_STATE (a two-dimensional context). */
 typedef struct {
   int32_t n[3];
   int32_t kind;
@@ -179,11 +189,11 @@ typedef struct {
 
 /* Three-dimensional interpolation data (Sec. 3.1): receiver k of grid recv_grid[k] at
  * (recv_i, recv_j, recv_k) takes sum_{a,b,c} wx[k][a] wy[k][b] wz[k][c]
- * u_donor(i0 + a, j0 + b, k0 + c), a, b, c = 0..2, from grid donor_grid[k] with lower corner
- * (donor_i0, donor_j0, donor_k0), wrapping on periodic axes.  Every donor must be a
- * WH_DISC or WH_DIRICHLET point (explicit interpolation), every receiver a WH_INTERP point,
- * and each WH_INTERP point listed exactly once (else WH_ERR_GRID).  Host pointers; wx, wy,
- * wz are [n][3] FP64. */
+ * u_donor(i0 + a, j0 + b, k0 + c), a, b, c = 0..p (p the order: stencils of width p + 1),
+ * from grid donor_grid[k] with lower corner (donor_i0, donor_j0, donor_k0), wrapping on
+ * periodic axes.  Every donor must be a WH_DISC or WH_DIRICHLET point (explicit
+ * interpolation), every receiver a WH_INTERP point, and each WH_INTERP point listed exactly
+ * once (else WH_ERR_GRID).  Host pointers; wx, wy, wz are [n][p + 1] FP64. */
 typedef struct {
   int64_t n;
   const int32_t *recv_grid, *recv_i, *recv_j, *recv_k;
@@ -268,8 +278,9 @@ wh_status wh_set_forcing(wh_ctx *ctx, int32_t grid_id, const double *f);
  * ghost rules and interpolation, and the temporally blocked FP32 march keeps the units
  * near such points in single steps.  Differentiation and wh_set_deflation (Algorithm 3's
  * inflation) then return WH_ERR_STATE, while wh_set_deflation_basis stays exact.
- * Errors: WH_ERR_ARG (bad grid, non-finite data), WH_ERR_GRID (order 4: a curvilinear grid
- * with a Dirichlet side, or a Dirichlet side of fewer than 6 points). */
+ * Errors: WH_ERR_ARG (bad grid, non-finite data, a three-dimensional context of order 4),
+ * WH_ERR_GRID (order 4: a curvilinear grid with a Dirichlet side, or a Dirichlet side of
+ * fewer than 6 points). */
 wh_status wh_set_boundary_data(wh_ctx *ctx, int32_t grid_id, const double *g);
 
 /* Prepare one frequency per instance (batching: several independent Helmholtz problems,
@@ -475,8 +486,9 @@ wh_status wh_set_coefficient(wh_ctx *ctx, int32_t grid_id, const double *c2);
  *                 shared memory and registers (recomputing a halo of depth points); the
  *                 rest (the overset coupling region) advances one step at a time with the
  *                 ghost rules and interpolation after each.  Results are bit-identical to
- *                 depth 1.  Ignored by the FP64 march and by two-dimensional contexts (-1 or
- *                 1 there).
+ *                 depth 1.  Ignored by the FP64 march, by fourth-order three-dimensional
+ *                 contexts (no point is blocked: blocked_points stays 0) and by
+ *                 two-dimensional contexts (-1 or 1 there).
  *   unit_depth    planes along axis 2 of a blocked unit: a multiple of 8 in [8, 256];
  *                 library: 64.
  *   ms_per_iteration, candidates: filled by wh_autotune; blocked_points (points that

@@ -731,6 +731,64 @@ __global__ void __launch_bounds__(kTX *kTY) march3o4_kernel(
     oy[t] = (int64_t)(wrap(j + dd[t], G.n1, G.per & 2) - j) * e0;
   }
   const bool cst = G.stencil == kConst13;
+  if constexpr (sizeof(T) == 4) {
+    if (cst && G.per == 0) {
+      // FP32, constant weights, no periodic axis (two ghost layers everywhere): a register
+      // queue of W^n at planes k - 2 .. k + 2, and the next plane's loads issued before
+      // this plane's arithmetic.  Every load stays in the extended array: planes -2 .. n2 + 1
+      // (the prefetched plane k + 3 only while k + 1 < kend <= n2), columns i - 2 .. i + 2.
+      const float c0 = G.cwf[0], c1x = G.cwf[1], c2x = G.cwf[2], c1y = G.cwf[3],
+                  c2y = G.cwf[4], c1z = G.cwf[5], c2z = G.cwf[6];
+      const float fcs = fcn * fsT;
+      int64_t q = at3(G, i, j, tl.k0);
+      float wm2 = Wn[q - 2 * pl], wm = Wn[q - pl], wc = Wn[q], wp = Wn[q + pl],
+            wp2 = Wn[q + 2 * pl];
+      float sx1 = Wn[q - 1] + Wn[q + 1], sx2 = Wn[q - 2] + Wn[q + 2];
+      float sy1 = Wn[q - e0] + Wn[q + e0], sy2 = Wn[q - 2 * e0] + Wn[q + 2 * e0];
+      int8_t mk = mask[q];
+      float fq = F[q], wo = first ? 0.0f : Wprev[q];
+      double vq = V[q];
+      for (int k = tl.k0; k < kend; ++k, q += pl) {
+        float wp3 = 0.0f, nx1 = 0.0f, nx2 = 0.0f, ny1 = 0.0f, ny2 = 0.0f, fq2 = 0.0f,
+              wo2 = 0.0f;
+        int8_t mk2 = 0;
+        double vq2 = 0.0;
+        if (k + 1 < kend) {
+          const int64_t q1 = q + pl;
+          wp3 = Wn[q1 + 2 * pl];
+          nx1 = Wn[q1 - 1] + Wn[q1 + 1];
+          nx2 = Wn[q1 - 2] + Wn[q1 + 2];
+          ny1 = Wn[q1 - e0] + Wn[q1 + e0];
+          ny2 = Wn[q1 - 2 * e0] + Wn[q1 + 2 * e0];
+          mk2 = mask[q1];
+          fq2 = F[q1];
+          if (!first) wo2 = Wprev[q1];
+          vq2 = V[q1];
+        }
+        if (mk == kDisc) {
+          const float S = c0 * wc + c1x * sx1 + c2x * sx2 + c1y * sy1 + c2y * sy2 +
+                          c1z * (wm + wp) + c2z * (wm2 + wp2);
+          const float out = first ? 0.5f * S - fcs * fq : S - wo - fcs * fq;
+          Wout[q] = out;
+          V[q] = fma(wfn, wh::to_f64(out), vq);
+        }
+        wm2 = wm;
+        wm = wc;
+        wc = wp;
+        wp = wp2;
+        wp2 = wp3;
+        sx1 = nx1;
+        sx2 = nx2;
+        sy1 = ny1;
+        sy2 = ny2;
+        mk = mk2;
+        fq = fq2;
+        wo = wo2;
+        vq = vq2;
+      }
+      return;
+    }
+  }
   T cw[7];
 #pragma unroll
   for (int t = 0; t < 7; ++t) cw[t] = fsel<T>(G.cw[t], G.cwf[t]);
