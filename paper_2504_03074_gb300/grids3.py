@@ -32,7 +32,7 @@ import numpy as np
 from .grids import (BC_DIRICHLET, BC_NEUMANN, BC_NONE, BC_PERIODIC, CARTESIAN, CURVILINEAR,
                     DIRICHLET, DISC, INTERP, UNUSED, lagrange_weights)
 
-ORDER = 2  # the three-dimensional CUDA path is second order (the oracle also takes 4)
+ORDER = 2  # default order; 4 is taken on Cartesian grids (library and oracle)
 _EPS = 1e-9  # index-space tolerance of "inside a grid" (points on a shared boundary)
 
 
