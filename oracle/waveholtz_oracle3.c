@@ -36,10 +36,12 @@
  *              axis is orthogonal to the two tangential axes, which is required.
  * Grid lines of a pair of axes declared orthogonal drop the mixed term (a_kl = 0).
  *
- * Fourth order (o3_new_order(4)): Cartesian grids only, two ghost layers, the second
- * difference D+D-(1 - h^2/12 D+D-) per axis (Eq. SecondDerivOrderp with mu < 2), the
- * stability constant C = sqrt(3)/2 in the time-step bound, Lagrange interpolation of width
- * 5, and the two-dimensional fourth-order ghost rules applied along each face's normal axis:
+ * Fourth order (o3_new_order(4)): two ghost layers, the second difference
+ * D+D-(1 - h^2/12 D+D-) per axis (Eq. SecondDerivOrderp with mu < 2), on curvilinear grids
+ * also the first difference D0(1 - h^2/6 D+D-) and its tensor product for the mixed terms
+ * (and for b_k from the metrics), the stability constant C = sqrt(3)/2 in the time-step
+ * bound, Lagrange interpolation of width 5, and the two-dimensional fourth-order ghost
+ * rules applied along each face's normal axis (Dirichlet faces on Cartesian grids only):
  *   Dirichlet: W_b = 0 (no boundary data at this order); c^2 D_nn W_b = f_b cos(omega_e t)
  *     (the tangential second differences of the zero boundary values vanish) and
  *     D+^5 W_{-2} = 0;
@@ -128,22 +130,38 @@ static double d2(const o3_grid *G, const double *W, int i, int j, int k, int a) 
   return s1 / (G->h[a] * G->h[a]);
 }
 
-/* D0 W along axis a. */
+/* First-difference weights of offsets -2..2: D0 (second order) and, with two ghost layers,
+ * D0(1 - h^2/6 D+D-) = (W_-2 - 8 W_-1 + 8 W_+1 - W_+2) / (12 h) (fourth order). */
+static const double D1W2[5] = {0.0, -0.5, 0.0, 0.5, 0.0};
+static const double D1W4[5] = {1.0 / 12.0, -8.0 / 12.0, 0.0, 8.0 / 12.0, -1.0 / 12.0};
+
+/* First difference of W along axis a (divided). */
 static double d1(const o3_grid *G, const double *W, int i, int j, int k, int a) {
-  int p[3] = {0, 0, 0}, m[3] = {0, 0, 0};
-  p[a] = 1; m[a] = -1;
-  return (val(G, W, i, j, k, p) - val(G, W, i, j, k, m)) / (2.0 * G->h[a]);
+  const double *w = G->fourth ? D1W4 : D1W2;
+  double s = 0.0;
+  for (int o = -2; o <= 2; ++o) {
+    if (w[o + 2] == 0.0) continue;
+    int d[3] = {0, 0, 0};
+    d[a] = o;
+    s += w[o + 2] * val(G, W, i, j, k, d);
+  }
+  return s / G->h[a];
 }
 
-/* D0_a D0_b W, a != b. */
+/* Mixed difference along axes a != b: the product of the two first differences above
+ * (D0_a D0_b at second order, its fourth-order counterpart with two ghost layers). */
 static double d11(const o3_grid *G, const double *W, int i, int j, int k, int a, int b) {
-  int pp[3] = {0, 0, 0}, pm[3] = {0, 0, 0}, mp[3] = {0, 0, 0}, mm[3] = {0, 0, 0};
-  pp[a] = 1; pp[b] = 1;
-  pm[a] = 1; pm[b] = -1;
-  mp[a] = -1; mp[b] = 1;
-  mm[a] = -1; mm[b] = -1;
-  return (val(G, W, i, j, k, pp) - val(G, W, i, j, k, pm) - val(G, W, i, j, k, mp) +
-          val(G, W, i, j, k, mm)) / (4.0 * G->h[a] * G->h[b]);
+  const double *w = G->fourth ? D1W4 : D1W2;
+  double s = 0.0;
+  for (int oa = -2; oa <= 2; ++oa)
+    for (int ob = -2; ob <= 2; ++ob) {
+      if (w[oa + 2] == 0.0 || w[ob + 2] == 0.0) continue;
+      int d[3] = {0, 0, 0};
+      d[a] = oa;
+      d[b] = ob;
+      s += w[oa + 2] * w[ob + 2] * val(G, W, i, j, k, d);
+    }
+  return s / (G->h[a] * G->h[b]);
 }
 
 /* c^2 L_h W at (i, j, k) (Sec. 3.1 mapping method; Cartesian: c^2 sum D+D-). */
@@ -326,10 +344,12 @@ int o3_add_grid(o3_problem *P, int n0, int n1, int n2, int kind, const int *bc, 
     }
   }
   if (P->order == 4) {
-    if (kind != O3_CARTESIAN) {
-      snprintf(P->err, sizeof P->err, "fourth order in 3D: Cartesian grids only");
-      return -1;
-    }
+    if (kind != O3_CARTESIAN)
+      for (int s = 0; s < 6; ++s)
+        if (bc[s] == O3_BC_DIRICHLET) {
+          snprintf(P->err, sizeof P->err, "fourth order in 3D: no Dirichlet face on a curvilinear grid");
+          return -1;
+        }
     /* the fourth-order Neumann rule is unstable at corners with another physical side */
     for (int s = 0; s < 6; ++s)
       for (int s2 = 0; s2 < 6; ++s2)

@@ -163,15 +163,16 @@ def cartesian_grid3(name, n, lo, hi, bc):
     return g
 
 
-def shell_grid(name, nphi, nth, nr, r_in, width, th_lo_deg, th_hi_deg):
+def shell_grid(name, nphi, nth, nr, r_in, width, th_lo_deg, th_hi_deg, order=ORDER):
     """Spherical shell x = r (sin th cos phi, sin th sin phi, cos th).
 
     Axis 0: phi = 2 pi t0 (periodic, nphi points), axis 1: th = th_lo + (th_hi - th_lo) t1
     (nth points), axis 2: r = r_in + width t2 (nr points).  Side axis2-lo is the sphere
     (Neumann); the polar edges and the outer shell are interpolation points.  All three
     pairs of grid lines are orthogonal.  Metrics are analytic and also evaluated on the
-    ghost lines.
+    ghost lines (order/2 of them); the interpolation layers are order/2 points thick.
     """
+    gw = order // 2
     th0, th1 = math.radians(th_lo_deg), math.radians(th_hi_deg)
     d0, d1, d2 = 1.0 / nphi, 1.0 / (nth - 1), 1.0 / (nr - 1)
     dth = th1 - th0
@@ -193,8 +194,8 @@ def shell_grid(name, nphi, nth, nr, r_in, width, th_lo_deg, th_hi_deg):
 
     # inverse metrics on the extended extent (no ghosts on the periodic axis 0)
     t0 = np.arange(nphi) * d0
-    t1 = np.arange(-1, nth + 1) * d1
-    t2 = np.arange(-1, nr + 1) * d2
+    t1 = np.arange(-gw, nth + gw) * d1
+    t2 = np.arange(-gw, nr + gw) * d2
     T2, T1, T0 = np.meshgrid(t2, t1, t0, indexing="ij")
     ph, th, r = 2 * np.pi * T0, th0 + dth * T1, r_in + width * T2
     sp, cp, st, ct = np.sin(ph), np.cos(ph), np.sin(th), np.cos(th)
@@ -206,23 +207,25 @@ def shell_grid(name, nphi, nth, nr, r_in, width, th_lo_deg, th_hi_deg):
     # grad r = (sin th cos phi, sin th sin phi, cos th);  t2 = (r - r_in) / width
     rx[6], rx[7], rx[8] = st * cp / width, st * sp / width, ct / width
     mask = np.full((nr, nth, nphi), DISC, np.int8)
-    mask[:, 0, :] = INTERP
-    mask[:, -1, :] = INTERP
-    mask[-1, :, :] = INTERP
+    mask[:, :gw, :] = INTERP
+    mask[:, -gw:, :] = INTERP
+    mask[-gw:, :, :] = INTERP
     bc = [BC_PERIODIC, BC_PERIODIC, BC_NONE, BC_NONE, BC_NEUMANN, BC_NONE]
     g = Grid3(name, CURVILINEAR, (nphi, nth, nr), bc, (d0, d1, d2), mask, 7, rx)
     g.mapping = dict(map=fmap, inverse=inv, r_in=r_in, width=width, th=(th0, th1))
     return g
 
 
-def pole_patch_grid(name, na, nr, A, r_in, width, sign):
+def pole_patch_grid(name, na, nr, A, r_in, width, sign, order=ORDER):
     """Orthographic pole patch x = r (a, b, sign sqrt(1 - a^2 - b^2)), a, b in [-A, A].
 
     Axes 0, 1: a, b (na points each), axis 2: r = r_in + width t2 (nr points).  Side
     axis2-lo is the sphere (Neumann); the four (a, b) edges and the outer layer are
     interpolation points.  The radial lines are orthogonal to the (a, b) surfaces (pairs
-    (0, 2) and (1, 2)); a and b lines are not (the mixed a-b term is present).
+    (0, 2) and (1, 2)); a and b lines are not (the mixed a-b term is present).  Ghost
+    lines and interpolation layers are order/2 deep, as for the shell.
     """
+    gw = order // 2
     d0 = d1 = 1.0 / (na - 1)
     d2 = 1.0 / (nr - 1)
 
@@ -241,8 +244,8 @@ def pole_patch_grid(name, na, nr, A, r_in, width, sign):
               (fj <= na - 1 + _EPS) & (fk >= -_EPS) & (fk <= nr - 1 + _EPS))
         return fi, fj, fk, ok
 
-    t = np.arange(-1, na + 1) * d0
-    t2 = np.arange(-1, nr + 1) * d2
+    t = np.arange(-gw, na + gw) * d0
+    t2 = np.arange(-gw, nr + gw) * d2
     T2, T1, T0 = np.meshgrid(t2, t, t, indexing="ij")
     a, b, r = -A + 2 * A * T0, -A + 2 * A * T1, r_in + width * T2
     c = sign * np.sqrt(1.0 - a * a - b * b)  # unit vector s = (a, b, c)
@@ -254,11 +257,11 @@ def pole_patch_grid(name, na, nr, A, r_in, width, sign):
     rx[3:6] /= 2 * A
     rx[6], rx[7], rx[8] = a / width, b / width, c / width
     mask = np.full((nr, na, na), DISC, np.int8)
-    mask[:, :, 0] = INTERP
-    mask[:, :, -1] = INTERP
-    mask[:, 0, :] = INTERP
-    mask[:, -1, :] = INTERP
-    mask[-1, :, :] = INTERP
+    mask[:, :, :gw] = INTERP
+    mask[:, :, -gw:] = INTERP
+    mask[:, :gw, :] = INTERP
+    mask[:, -gw:, :] = INTERP
+    mask[-gw:, :, :] = INTERP
     bc = [BC_NONE, BC_NONE, BC_NONE, BC_NONE, BC_NEUMANN, BC_NONE]
     g = Grid3(name, CURVILINEAR, (na, na, nr), bc, (d0, d1, d2), mask, 6, rx)
     g.mapping = dict(map=fmap, inverse=inv, A=A, sign=sign, r_in=r_in, width=width)
@@ -390,48 +393,42 @@ def _points_of(g, ijk):
 # ----------------------------------------------------------------------------------
 
 def sphere_in_box(nb=320, nphi=256, nth=128, nr=24, npatch=96, box=2.0, r_in=0.5,
-                  width=0.3, band=(15.0, 165.0), patch_deg=24.0, r_hole=0.65):
+                  width=0.3, band=(15.0, 165.0), patch_deg=24.0, r_hole=0.65, order=ORDER):
     """Cartesian background [-box, box]^3 (nb^3 points, Dirichlet) + spherical shell
     (nphi x nth x nr, polar band) + two orthographic pole patches (npatch^2 x nr).
 
-    Background points with |x| < r_hole are cut out; the cut points that are 7-point
-    stencil neighbours of a background discretization point become interpolation points.
-    Donors: background receivers from the shell, else a patch; shell receivers from a
-    patch, else the background; patch receivers from the shell, else the background.
-    Returns (grids, interp).
+    Background points with |x| < r_hole are cut out; the cut points within order/2 grid
+    lines (along an axis) of a background discretization point become interpolation
+    points.  Donors (stencils of width order + 1): background receivers from the shell,
+    else a patch; shell receivers from a patch, else the background; patch receivers from
+    the shell, else the background.  Returns (grids, interp).
     """
+    w = order + 1
     B = cartesian_grid3("background", (nb, nb, nb), (-box,) * 3, (box,) * 3,
                         [BC_DIRICHLET] * 6)
-    S = shell_grid("shell", nphi, nth, nr, r_in, width, band[0], band[1])
+    S = shell_grid("shell", nphi, nth, nr, r_in, width, band[0], band[1], order)
     A = math.sin(math.radians(patch_deg))
-    PN = pole_patch_grid("north", npatch, nr, A, r_in, width, 1.0)
-    PS = pole_patch_grid("south", npatch, nr, A, r_in, width, -1.0)
+    PN = pole_patch_grid("north", npatch, nr, A, r_in, width, 1.0, order)
+    PS = pole_patch_grid("south", npatch, nr, A, r_in, width, -1.0, order)
     # hole cutting, plane by plane
     x = -box + B.h[0] * np.arange(nb)
     inside = np.zeros((nb, nb, nb), bool)
     X2 = x[None, :] ** 2 + x[:, None] ** 2
     for k in range(nb):
         inside[k] = X2 + x[k] ** 2 < r_hole * r_hole
-    active = ~inside
-    near = np.zeros_like(active)
-    near[1:] |= active[:-1]
-    near[:-1] |= active[1:]
-    near[:, 1:] |= active[:, :-1]
-    near[:, :-1] |= active[:, 1:]
-    near[:, :, 1:] |= active[:, :, :-1]
-    near[:, :, :-1] |= active[:, :, 1:]
+    near = _near(~inside, order // 2)
     B.mask[inside & near] = INTERP
     B.mask[inside & ~near] = UNUSED
-    del inside, active, near
+    del inside, near
     grids = [B, S, PN, PS]
     parts = []
-    for rgid, order in ((0, (1, 2, 3)), (1, (2, 3, 0)), (2, (1, 0)), (3, (1, 0))):
+    for rgid, donors in ((0, (1, 2, 3)), (1, (2, 3, 0)), (2, (1, 0)), (3, (1, 0))):
         g = grids[rgid]
         ijk = _interp_points(g)
         pts = _points_of(g, ijk)
-        dg, c, f = find_donors(grids, rgid, pts, order)
+        dg, c, f = find_donors(grids, rgid, pts, donors, w)
         parts.append((rgid, ijk, dg, c, f))
-    interp = _assemble(grids, parts)
+    interp = _assemble(grids, parts, w)
     check_explicit_interp3(grids, interp)
     return grids, interp
 
@@ -501,18 +498,19 @@ def _seeded_point(rng, lo, hi, rmin):
 
 
 def sphere_problem(nb=320, nphi=256, nth=128, nr=24, npatch=96, omega=30.0, seed=0,
-                   width=0.3, r_hole=0.65, patch_deg=24.0, b=200.0):
+                   width=0.3, r_hole=0.65, patch_deg=24.0, b=200.0, order=ORDER,
+                   band=(15.0, 165.0), box=2.0):
     """Sphere-in-box: Gaussian point source seeded in the background away from the
     sphere.  Coarse test grids need a wider shell and a larger hole radius so that every
     receiver still has a full donor stencil."""
     rng = np.random.default_rng(seed)
     grids, interp = sphere_in_box(nb, nphi, nth, nr, npatch, width=width, r_hole=r_hole,
-                                  patch_deg=patch_deg)
-    x0 = _seeded_point(rng, -1.5, 1.5, 1.0)
+                                  patch_deg=patch_deg, order=order, band=band, box=box)
+    x0 = _seeded_point(rng, -0.75 * box, 0.75 * box, 1.0)
     f = [gaussian3(g, x0, 1.0, b) for g in grids]
     return Problem3(grids, interp, omega, f,
-                    name=f"sphere-in-box-{nb}^3+{nphi}x{nth}x{nr}+2x{npatch}^2x{nr}-o2",
-                    meta=dict(source=x0.tolist(), seed=seed))
+                    name=f"sphere-in-box-{nb}^3+{nphi}x{nth}x{nr}+2x{npatch}^2x{nr}-o{order}",
+                    meta=dict(source=x0.tolist(), seed=seed), order=order)
 
 
 def unit_cube_problem(n=24, omega=10.0, seed=0, bc=BC_DIRICHLET, b=200.0, order=ORDER):

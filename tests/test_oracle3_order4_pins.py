@@ -268,9 +268,12 @@ def test_overset_solution_fourth_order_3d(o3):
 # ------------------------------------------------------- what it refuses
 
 def test_fourth_order_refusals(o3):
-    """Curvilinear grids, a Neumann face meeting another physical face, and Dirichlet data
-    at fourth order are refused, as is an order other than 2 or 4."""
-    g = G3.pole_patch_grid("north", 9, 5, 0.5, 0.5, 0.3, 1.0)
+    """A curvilinear grid with a Dirichlet face, a Neumann face meeting another physical
+    face, and Dirichlet data at fourth order are refused, as is an order other than 2 or
+    4."""
+    g = G3.pole_patch_grid("north", 12, 8, 0.5, 0.5, 0.3, 1.0, order=4)
+    o3.Oracle3(_single(g))  # Neumann sphere face, interpolation edges: taken
+    g.bc[5] = D
     with pytest.raises(ValueError):
         o3.Oracle3(_single(g))
     with pytest.raises(ValueError):
@@ -281,3 +284,171 @@ def test_fourth_order_refusals(o3):
     with pytest.raises(ValueError):
         o3.Oracle3(p)
     assert o3.lib().o3_new_order(3) is None
+
+
+# ---------------------------------------------- curvilinear grids (the sphere-in-box family)
+
+def _smooth(X):
+    return np.sin(2.0 * X[0] + 0.3) * np.cos(X[1]) * np.exp(0.5 * X[2])
+
+
+def _lap_error(o3, g):
+    orc = o3.Oracle3(_single(g))
+    X = _ext_coords(g)
+    out = _interior(g, orc.apply_lap(0, _smooth(X)))
+    ref = _interior(g, (-4.0 - 1.0 + 0.25) * _smooth(X))
+    return np.max(np.abs(out - ref)[g.mask == G.DISC])
+
+
+@pytest.mark.parametrize("kind", ["shell", "patch"])
+def test_mapped_laplacian_fourth_order(o3, kind):
+    """The mapped Laplacian (Sec. 3.1) at fourth order -- D+D-(1 - h^2/12 D+D-), the first
+    difference D0(1 - h^2/6 D+D-), its tensor product for the mixed a-b term of the pole
+    patch, and b_k from fourth-order differences of the metrics -- converges at fourth order
+    on a spherical shell and on an orthographic pole patch (Neumann layer included, exact
+    ghost values)."""
+    errs = []
+    for s in (2, 4):
+        if kind == "shell":
+            g = G3.shell_grid("shell", 32 * s, 16 * s + 1 - s, 8 * s + 1 - s, 0.5, 0.3,
+                              40.0, 140.0, order=4)
+        else:
+            g = G3.pole_patch_grid("north", 16 * s + 1 - s, 8 * s + 1 - s,
+                                   math.sin(math.radians(25.0)), 1.5, 0.3, 1.0, order=4)
+        errs.append(_lap_error(o3, g))
+    assert 3.7 < math.log2(errs[0] / errs[1]) < 4.4, errs
+
+
+def _affine_grid(n, B, bc, gw=2):
+    """A curvilinear grid x = B t (B constant, columns not orthogonal), t in [0, 1]^3 on
+    non-periodic axes and [0, 1) on periodic ones; interpolation layers gw thick on the
+    faces without a condition."""
+    h = tuple(1.0 / (m if bc[2 * a] == P else m - 1) for a, m in enumerate(n))
+    gh = tuple(0 if bc[2 * a] == P else gw for a in range(3))
+    ext = [n[a] + 2 * gh[a] for a in range(3)]
+    Binv = np.linalg.inv(B)
+    rx = np.empty((9, ext[2], ext[1], ext[0]))
+    for k in range(3):
+        for m in range(3):
+            rx[3 * k + m] = Binv[k, m]
+    mask = np.full((n[2], n[1], n[0]), G.DISC, np.int8)
+    sl = [np.s_[:, :, :gw], np.s_[:, :, -gw:], np.s_[:, :gw, :], np.s_[:, -gw:, :],
+          np.s_[:gw], np.s_[-gw:]]
+    for s in range(6):
+        if bc[s] == G.BC_NONE:
+            mask[sl[s]] = G.INTERP
+    ortho = 0
+    for p, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        if abs(B[:, a] @ B[:, b]) < 1e-15:
+            ortho |= 1 << p
+    g = G3.Grid3("affine", G3.CURVILINEAR, tuple(n), list(bc), h, mask, ortho, rx)
+    g.mapping = dict(map=lambda t0, t1, t2: np.einsum("ij,j...->i...", B,
+                                                      np.stack([t0, t1, t2])))
+    return g
+
+
+def test_mapped_laplacian_exact_on_quartics_affine(o3):
+    """Under an affine map with no orthogonal pair (every mixed term present, b_k = 0) the
+    fourth-order mapped Laplacian is exact on polynomials of degree <= 4."""
+    B = np.array([[1.0, 0.35, -0.2], [0.1, 0.9, 0.3], [-0.25, 0.15, 1.1]])
+    g = _affine_grid((11, 10, 12), B, [G.BC_NONE] * 6)
+    assert g.ortho == 0
+    orc = o3.Oracle3(_single(g))
+    x, y, z = _ext_coords(g)
+    u = x ** 4 + 2 * x ** 2 * y * z - y ** 3 * z + 0.5 * z ** 4 + x * y * z + x * x * y * y
+    lap = (12 * x ** 2 + 4 * y * z + 2 * y * y) + (-6 * y * z + 2 * x * x) + 6 * z ** 2
+    out = _interior(g, orc.apply_lap(0, u))
+    assert np.allclose(out[g.mask == G.DISC], _interior(g, lap)[g.mask == G.DISC],
+                       rtol=1e-10, atol=1e-9)
+
+
+def test_curvilinear_description_of_a_slab_equals_cartesian(o3):
+    """A periodic/Neumann slab described as a curvilinear grid (x = diag(L) t) gives the
+    Cartesian fourth-order operator and, through the curvilinear Neumann ghost rule, the
+    same WaveHoltz iteration as the Cartesian description (the Cartesian path is pinned
+    above)."""
+    n, L = (12, 10, 14), (1.0, 0.8, 0.9)
+    bc = [P, P, P, P, N, N]
+    cart = G3.cartesian_grid3("s", n, (0.0,) * 3, (11 / 12, 0.8 * 9 / 10, 0.9), bc)
+    curv = _affine_grid(n, np.diag(L), bc)
+    assert curv.ortho == 7
+    f = G3.gaussian3(cart, np.array([0.4, 0.35, 0.45]), 1.0, 20.0)
+    po = [G3.Problem3([g], G3.Interp3.empty(), 6.0, [f], order=4) for g in (cart, curv)]
+    oc, ov = (o3.Oracle3(p) for p in po)
+    assert oc.time.M == ov.time.M and ov.time.dt == pytest.approx(oc.time.dt, rel=1e-13)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(oc.ext_shape(0))
+    a, b = oc.apply_lap(0, u), ov.apply_lap(0, u)
+    disc = np.zeros(u.shape, bool)
+    _interior(cart, disc)[...] = cart.mask == G.DISC
+    assert np.max(np.abs(a - b)[disc]) < 1e-12 * np.max(np.abs(a)[disc])
+    v = G3.random_state3(po[0], 4)
+    for forcing in (True, False):
+        r1, r2 = oc.iterate(v, forcing), ov.iterate(v, forcing)
+        assert np.max(np.abs(r1 - r2)) < 1e-12 * np.max(np.abs(r1))
+
+
+def test_neumann_ghost_rule_on_the_sphere_fourth_order(o3):
+    """On the shell's sphere face the fourth-order Neumann rule with the fifth-order
+    extrapolation reproduces, at both ghost layers, a smooth function with zero normal
+    derivative there, with errors that fall at least as h^4."""
+    errs = []
+    for s in (1, 2):
+        g = G3.shell_grid("shell", 32 * s, 16 * s + 1 - s, 8 * s + 1 - s, 0.5, 0.3, 40.0,
+                          140.0, order=4)
+        orc = o3.Oracle3(_single(g))
+        gh = g.ghosts(4)
+        t = [np.arange(-gh[a], g.n[a] + gh[a]) * g.h[a] for a in range(3)]
+        T2, T1, T0 = np.meshgrid(t[2], t[1], t[0], indexing="ij")
+        ph, th = 2 * np.pi * T0, math.radians(40.0) + math.radians(100.0) * T1
+        rr = 0.3 * T2  # r - r_in
+        u = np.cos(2 * ph) * np.sin(th) ** 2 * (1 + 2 * rr ** 2) * np.exp(-rr ** 3)
+        w = u.copy()
+        w[:gh[2]] = 0.0
+        out = orc.apply_bc(0, w)
+        cols = np.zeros(u.shape[1:], bool)  # columns whose sphere point is a disc. point
+        cols[gh[1]:gh[1] + g.n[1], :] = g.mask[0] == G.DISC
+        errs.append(np.max(np.abs(out[:gh[2]] - u[:gh[2]])[:, cols]))
+    assert math.log2(errs[0] / errs[1]) > 4.0, errs
+
+
+def _sphere4(s):
+    return G3.sphere_problem(nb=48 * s, nphi=96 * s, nth=64 * s, nr=16 * s, npatch=40 * s,
+                             width=0.8, r_hole=0.83, patch_deg=38.0, omega=6.0, order=4,
+                             box=1.5)
+
+
+def test_sphere_in_box_fourth_order_generator_invariants():
+    """Order-4 sphere-in-box: interpolation layers two points thick on the shell and the
+    patches, width-5 donor stencils of discretization or Dirichlet points only (explicit
+    interpolation), weights summing to 1 per axis, every interpolation point listed once."""
+    prob = _sphere4(1)
+    it = prob.interp
+    assert it.wx.shape[1] == 5
+    G3.check_explicit_interp3(prob.grids, it)
+    for w in (it.wx, it.wy, it.wz):
+        assert np.allclose(w.sum(axis=1), 1.0, atol=1e-13)
+    keys = set(zip(it.recv_grid.tolist(), it.recv_i.tolist(), it.recv_j.tolist(),
+                   it.recv_k.tolist()))
+    assert len(keys) == it.n
+    S = prob.grids[1]
+    assert np.all(S.mask[-2:] == G.INTERP) and np.all(S.mask[:, :2] == G.INTERP)
+    assert np.all(S.mask[:-2, 2:-2] == G.DISC)
+
+
+def test_sphere_interpolation_fifth_order(o3):
+    """Width-5 Lagrange interpolation on the order-4 sphere-in-box grids (curvilinear donors
+    and receivers) converges at fifth order under refinement (> 4.3 at these sizes)."""
+    errs = []
+    for s in (1, 2):
+        prob = _sphere4(s)
+        orc = o3.Oracle3(prob)
+        us = [_smooth(_ext_coords(g)) for g in prob.grids]
+        got = orc.interpolate(us)
+        e = 0.0
+        for gi, g in enumerate(prob.grids):
+            rec = np.zeros(orc.ext_shape(gi), bool)
+            _interior(g, rec)[...] = g.mask == G.INTERP
+            e = max(e, float(np.max(np.abs(got[gi] - us[gi])[rec])))
+        errs.append(e)
+    assert math.log2(errs[0] / errs[1]) > 4.3, errs
