@@ -2,8 +2,8 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this module.  It wraps the plain C implementation in ``waveholtz_oracle3.c`` (one
-WaveHoltz iteration on a 3D overset grid at second order, or at fourth order on Cartesian
-grids, FP64, single thread).  The
+WaveHoltz iteration on a 3D overset grid at second or fourth order, FP64, single
+thread).  The
 fixed-point iteration, GMRES and the filter functions of ``oracle.oracle`` apply to it
 unchanged (they only call ``iterate``).  It shares no code with the CUDA library; inputs
 come from ``paper_2504_03074_gb300.grids3``.
