@@ -2,7 +2,7 @@
  * waveholtz_oracle3.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
  *
  * A plain, slow, single-threaded FP64 CPU implementation of one WaveHoltz iteration on a
- * three-dimensional overset grid at second order (and at fourth order on Cartesian grids),
+ * three-dimensional overset grid at second order (and at fourth order),
  * written from the paper (Appelo, Banks,
  * Henshaw, Schwendeman, "An optimal O(N) Helmholtz solver for complex geometry using
  * WaveHoltz and overset grids").  Only tests/, the smoke check and the benchmark's
