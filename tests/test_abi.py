@@ -276,6 +276,48 @@ def test_grid3_validation_on_host(W):
     L.wh_destroy(h)
 
 
+def test_grid3_order4_validation_on_host(W):
+    """Fourth-order 3D host checks: a ghost rule that would read a receiver, a 13-point
+    stencil that reaches an unused point two lines away, and a width-5 donor stencil that
+    leaves its grid are refused (WH_ERR_GRID); the order-4 box-in-box is taken whole."""
+    from paper_2504_03074_gb300 import grids3 as G3
+    L = W.lib()
+    gid = C.c_int32()
+    h = _ctx(W, order=4)
+    # a receiver two points inside a Dirichlet face, on the line of a rule's inward points
+    bad = G3.cartesian_grid3("c", (12, 12, 12), (0, 0, 0), (1, 1, 1), [G.BC_DIRICHLET] * 6)
+    bad.mask[5, 5, 2] = G.INTERP
+    d, keep = _desc3(W, bad)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -7
+    assert b"interpolation point" in L.wh_last_error(h)
+    # an unused point behind a layer of receivers, two lines from discretization points
+    bad = G3.cartesian_grid3("c", (12, 12, 12), (0, 0, 0), (1, 1, 1), [G.BC_DIRICHLET] * 6)
+    bad.mask[5:8, 5:8, 5:8] = G.INTERP
+    bad.mask[6, 6, 6] = G.UNUSED
+    d, keep = _desc3(W, bad)
+    assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == -7
+    assert b"unused" in L.wh_last_error(h)
+    L.wh_destroy(h)
+    # the order-4 box-in-box: grids and width-5 interpolation taken; a donor corner moved so
+    # that its 5-point stencil leaves the donor grid is refused (width 3 would still fit)
+    prob = G3.box_in_box_problem(nb=17, ni=15, order=4, hole=0.1)
+    h = _ctx(W, order=4)
+    keeps = []
+    for g in prob.grids:
+        d, keep = _desc3(W, g)
+        keeps.append(keep)
+        assert L.wh_add_grid3(h, C.byref(d), C.byref(gid)) == 0, L.wh_last_error(h)
+    it = prob.interp
+    ok, keep = _interp3(W, it)
+    assert L.wh_set_interp3(h, C.byref(ok)) == 0, L.wh_last_error(h)
+    di = np.ascontiguousarray(it.donor_i0, np.int32).copy()
+    sel = int(np.nonzero(it.donor_grid == 0)[0][0])
+    di[sel] = prob.grids[0].n[0] - 4
+    desc, keep = _interp3(W, it, donor_i0=di)
+    assert L.wh_set_interp3(h, C.byref(desc)) == -7
+    L.wh_destroy(h)
+
+
 def test_deflation_validation_on_host(W):
     """wh_set_deflation checks its arguments without touching the device, on 2D and 3D
     contexts alike."""
