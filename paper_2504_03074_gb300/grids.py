@@ -503,6 +503,190 @@ def bodies_in_square(nb, bodies, order, box=2.0):
 
 
 # ----------------------------------------------------------------------------------
+# The knife edge: a thin plate with a rounded tip standing on the bottom wall
+# ----------------------------------------------------------------------------------
+
+def _gauss01(n, lo=0.0, hi=1.0):
+    """Gauss-Legendre nodes and weights on [lo, hi]."""
+    g, w = np.polynomial.legendre.leggauss(n)
+    return lo + 0.5 * (hi - lo) * (g + 1.0), 0.5 * (hi - lo) * w
+
+
+class KnifeOutline:
+    """Outline of the knife, traversed by arclength sigma from its base on the right
+    (x = width/2, y = 0) up the right side, around the tip and down the left side: straight
+    sides of height y_s joined by a tip of arclength ell whose curvature
+    kappa = (2 pi / ell) sin^2(pi u), u = (sigma - y_s) / ell, turns the tangent by pi with
+    kappa and kappa' continuous at the joins (the paper's rounded tip, smooth enough for
+    fourth-order metrics).  ell and y_s are set by the width and the height of the apex.
+    Beyond [0, S] the sides continue straight below the wall (ghost lines)."""
+
+    def __init__(self, width=0.02, height=0.5):
+        self.width, self.height = width, height
+        self.w2 = 0.5 * width
+        u, w = _gauss01(64)
+        self.ell = width / -float(np.sum(w * np.cos(self.phi_tip(u))))
+        u, w = _gauss01(64, 0.0, 0.5)
+        self.ys = height - self.ell * float(np.sum(w * np.sin(self.phi_tip(u))))
+        self.S = 2.0 * self.ys + self.ell
+        self.kmax = 2.0 * math.pi / self.ell
+
+    @staticmethod
+    def phi_tip(u):
+        """Tangent angle over the tip: pi/2 + pi u - sin(2 pi u) / 2, u in [0, 1]."""
+        return 0.5 * np.pi + np.pi * u - 0.5 * np.sin(2.0 * np.pi * u)
+
+    def frame(self, sigma):
+        """Point (x, y), tangent angle phi and curvature kappa at arclength sigma."""
+        sigma = np.asarray(sigma, np.float64)
+        u = np.clip((sigma - self.ys) / self.ell, 0.0, 1.0)
+        g, w = _gauss01(40)
+        ph = self.phi_tip(u[..., None] * g)  # tip: quadrature of the unit tangent over [0, u]
+        tx = self.w2 + self.ell * u * np.sum(w * np.cos(ph), axis=-1)
+        ty = self.ys + self.ell * u * np.sum(w * np.sin(ph), axis=-1)
+        right, left = sigma < self.ys, sigma > self.ys + self.ell
+        x = np.where(right, self.w2, np.where(left, -self.w2, tx))
+        y = np.where(right, sigma, np.where(left, self.ys - (sigma - self.ys - self.ell), ty))
+        phi = np.where(right, 0.5 * np.pi, np.where(left, 1.5 * np.pi, self.phi_tip(u)))
+        kap = np.where(right | left, 0.0, self.kmax * np.sin(np.pi * u) ** 2)
+        return x, y, phi, kap
+
+
+class _KnifeMap:
+    """The knife grid's mapping x = gamma(sigma) + d n(sigma): sigma = S t0 along the
+    outline, d = W q(t1) along the outward normal n = (sin phi, -cos phi), with
+    q(s) = (e^{beta s} - 1) / (e^beta - 1).  Orthogonal; the outline is convex, so
+    outward offsets never fold (dx/dsigma = (1 + d kappa) times the tangent)."""
+
+    def __init__(self, outline, W, beta):
+        self.o, self.W, self.beta = outline, W, beta
+        self.eb = math.exp(beta) - 1.0
+        sig = np.linspace(-0.05, outline.S + 0.05, 20001)
+        x, y, _, _ = outline.frame(sig)
+        from scipy.spatial import cKDTree
+        self._sig, self._tree = sig, cKDTree(np.stack([x, y], axis=1))
+
+    def q(self, s):
+        return (np.exp(self.beta * s) - 1.0) / self.eb
+
+    def dq(self, s):
+        return self.beta * np.exp(self.beta * s) / self.eb
+
+    def xy(self, t0, t1):
+        x, y, phi, _ = self.o.frame(self.o.S * t0)
+        d = self.W * self.q(t1)
+        return x + d * np.sin(phi), y - d * np.cos(phi)
+
+    def rx(self, t0, t1):
+        """dt0/dx, dt0/dy, dt1/dx, dt1/dy (analytic in the outline's frame)."""
+        _, _, phi, kap = self.o.frame(self.o.S * t0)
+        d = self.W * self.q(t1)
+        j0 = self.o.S * (1.0 + d * kap)
+        j1 = self.W * self.dq(t1)
+        return np.cos(phi) / j0, np.sin(phi) / j0, np.sin(phi) / j1, -np.cos(phi) / j1
+
+    def param(self, x, y):
+        """(sigma, d) of physical points: the nearest outline sample, then Newton on
+        (p - gamma(sigma)) . t(sigma) = 0 (derivative -(1 + kappa d))."""
+        x, y = np.asarray(x, np.float64), np.asarray(y, np.float64)
+        _, k = self._tree.query(np.stack([x.ravel(), y.ravel()], axis=1))
+        sig = self._sig[k].reshape(x.shape)
+        for _ in range(8):
+            gx, gy, phi, kap = self.o.frame(sig)
+            tx, ty = np.cos(phi), np.sin(phi)
+            f = (x - gx) * tx + (y - gy) * ty
+            d = (x - gx) * ty - (y - gy) * tx
+            sig = sig + f / np.maximum(1.0 + kap * d, 0.25)
+        gx, gy, phi, _ = self.o.frame(sig)
+        d = (x - gx) * np.sin(phi) - (y - gy) * np.cos(phi)
+        return sig, d
+
+    def index(self, x, y, n0, n1):
+        """Fractional (i, j) indices of physical points in the knife grid."""
+        sig, d = self.param(x, y)
+        with np.errstate(invalid="ignore"):
+            s = np.log1p(d / self.W * self.eb) / self.beta
+        return sig / self.o.S * (n0 - 1), s * (n1 - 1), d
+
+
+def knife_edge(j=32, order=4, width=0.02, height=0.5, wfac=12.0, n1=16, cut=0.4, beta=1.5):
+    """The knife-edge overset grid (Sec. 6): a Cartesian background on
+    [-0.5, 0.5] x [0, 0.55] with spacing 1/(10 j), Dirichlet on every side, and one
+    body-fitted grid hugging the whole knife (a thin plate of the given width whose rounded
+    tip reaches the given height, standing on the bottom wall): axis 0 along the outline
+    (spacing half the background's), axis 1 outward over W = wfac background spacings
+    (n1 lines stretched toward the knife).  Its sides: the two ends lie on the bottom wall
+    and the knife surface, all Dirichlet; the outer order/2 lines are interpolation points
+    (donors on the background), as are the wall points of those lines.  Background points
+    within cut W of the knife (or inside it) are cut out; those within order/2 index layers
+    of an active background point become interpolation points (donors on the knife grid),
+    the rest unused.  The paper covers the same knife with a tip grid and two side grids;
+    one grid along the whole outline keeps every component orthogonal.  Returns
+    (grids, interp, outline)."""
+    h = 1.0 / (10 * j)
+    nx, ny = 10 * j + 1, int(round(0.55 / h)) + 1
+    B = cartesian_grid("background", nx, ny, -0.5, 0.5, 0.0, (ny - 1) * h, [BC_DIRICHLET] * 4,
+                       order)
+    ko = KnifeOutline(width, height)
+    W = wfac * h
+    m = _KnifeMap(ko, W, beta)
+    g1 = order // 2
+    n0 = int(math.ceil(2.0 * ko.S / h)) + 1
+    if 1.0 + ko.kmax * W * m.q(-g1 / (n1 - 1)) <= 0.25:
+        raise ValueError("the knife grid's ghost lines fold at the tip: refine or widen")
+    if height + W + (order // 2 + 1) * h > (ny - 1) * h:
+        raise ValueError("the knife grid reaches the top wall: refine or lower the knife")
+    d0, d1 = 1.0 / (n0 - 1), 1.0 / (n1 - 1)
+    t0e = (np.arange(-g1, n0 + g1) * d0)[None, :]
+    t1e = (np.arange(-g1, n1 + g1) * d1)[:, None]
+    shape = (n1 + 2 * g1, n0 + 2 * g1)
+    rx = np.stack([np.broadcast_to(v, shape) for v in m.rx(t0e, t1e)])
+    X, Y = m.xy((np.arange(n0) * d0)[None, :], (np.arange(n1) * d1)[:, None])
+    X, Y = np.broadcast_to(X, (n1, n0)).copy(), np.broadcast_to(Y, (n1, n0)).copy()
+    mask = np.full((n1, n0), DISC, np.int8)
+    mask[0, :] = DIRICHLET
+    mask[:, 0] = DIRICHLET
+    mask[:, -1] = DIRICHLET
+    mask[n1 - g1:, :] = INTERP
+    K = Grid("knife", CURVILINEAR, (n0, n1), [BC_DIRICHLET, BC_DIRICHLET, BC_DIRICHLET, BC_NONE],
+             (d0, d1), mask, np.stack([X, Y]), True, np.ascontiguousarray(rx))
+    K.mapping = dict(knife=m)
+    # hole cutting
+    XB, YB = B.xy
+    _, _, dB = m.index(XB, YB, n0, n1)
+    inside = dB < cut * W
+    active = ~inside
+    near = np.zeros_like(active)
+    pad = np.pad(active, g1)
+    for dj in range(-g1, g1 + 1):
+        for di in range(-g1, g1 + 1):
+            near |= pad[g1 + dj:g1 + dj + ny, g1 + di:g1 + di + nx]
+    B.mask[inside & near] = INTERP
+    B.mask[inside & ~near] = UNUSED
+    recv = []
+    jb, ib = np.nonzero(B.mask == INTERP)
+    fi, fj, d = m.index(XB[jb, ib], YB[jb, ib], n0, n1)
+    if d.size and not np.all(d > 0.0):
+        raise ValueError("background interpolation points lie inside the knife")
+    i0, j0, wx, wy = _donors(fi, fj, K, order, n1 - 1 - g1, False)
+    recv.append((0, ib, jb, 1, i0, j0, wx, wy))
+    jk, ik = np.nonzero(K.mask == INTERP)
+    fi, fj = _cart_param(B, X[jk, ik], Y[jk, ik])
+    i0, j0, wx, wy = _donors(fi, fj, B, order, ny - 1, False)
+    recv.append((1, ik, jk, 0, i0, j0, wx, wy))
+    cols = list(zip(*recv))
+    interp = Interp(
+        np.concatenate([np.full(len(r[1]), r[0], np.int32) for r in recv]),
+        np.concatenate(cols[1]).astype(np.int32), np.concatenate(cols[2]).astype(np.int32),
+        np.concatenate([np.full(len(r[1]), r[3], np.int32) for r in recv]),
+        np.concatenate(cols[4]).astype(np.int32), np.concatenate(cols[5]).astype(np.int32),
+        np.concatenate(cols[6]), np.concatenate(cols[7]))
+    grids = [B, K]
+    check_explicit_interp(grids, interp, order)
+    return grids, interp, ko
+
+
+# ----------------------------------------------------------------------------------
 # Sources and coefficients
 # ----------------------------------------------------------------------------------
 
@@ -625,6 +809,17 @@ def ellipses_problem(nb=512, order=4, omega=20.0, seed=0, scale=1):
               Body((0.6, 1.05), 0.3, 0.3, 0.3, 256 * s, 24 * s)]
     return bodies_problem(nb, bodies, order=order, omega=omega, seed=seed,
                           name="ellipses-in-square")
+
+
+def knife_edge_problem(j=32, order=4, omega=100.0, width=0.02, height=0.5, source=(-0.2, 0.2),
+                       b=1000.0, **kw):
+    """The knife edge (Sec. 6) with a Gaussian source at ``source`` (the paper's
+    (-0.2, 0.2)); sizes and shape as in ``knife_edge``."""
+    grids, interp, ko = knife_edge(j, order, width, height, **kw)
+    f = [gaussian(g.xy, source, 1.0, b) for g in grids]
+    return Problem(grids, interp, order, omega, f,
+                   name=f"knife-edge-j{j}-w{width:g}-h{height:g}-o{order}",
+                   meta=dict(source=list(source), outline=dict(ell=ko.ell, ys=ko.ys, S=ko.S)))
 
 
 def with_boundary_data(problem, fn):
