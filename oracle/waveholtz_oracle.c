@@ -46,7 +46,10 @@
  *     Cartesian grids only when g is given, and the extrapolation D+^5 W_{-2} = 0.
  *   order 4, Neumann: fourth-order centred normal derivative D_n W = 0 and the same
  *     extrapolation.
- * The boundary grid lines must be orthogonal to the boundary, and a Neumann side may
+ * Non-orthogonal grids with physical sides (order 2 only): a Dirichlet side reads no
+ * ghost; a Neumann side's rule is the normal derivative with its tangential term (see
+ * apply_bc), along a periodic side.
+ * The boundary grid lines must otherwise be orthogonal to the boundary, and a Neumann side may
  * only meet periodic or interpolation sides (both checked).
  */
 #include <math.h>
@@ -306,7 +309,20 @@ static void apply_bc(const or_problem *P, int gidx, double *W, double fcos) {
       if (code == OR_BC_NEUMANN) {
         if (m != OR_DISC) continue;
         if (P->order == 2) {
-          W[gq[0]] = U[1]; /* D0 W = 0 */
+          /* D0 W = 0 along the normal axis a; on a non-orthogonal grid the normal
+           * derivative grad r_a . grad W = a_aa W_{r_a} + a_at W_{r_t} (a_kl =
+           * grad r_k . grad r_l) keeps its tangential term, D0 along the (periodic) side:
+           * G1 = U1 +- 2 h_a (a_at / a_aa) D0_t W_b (+ on a low side, - on a high one) */
+          double corr = 0.0;
+          if (!G->orthogonal) {
+            int ip, jp, im, jm;
+            side_point(G, s, t + 1, 0, &ip, &jp);
+            side_point(G, s, t - 1, 0, &im, &jm);
+            const double ann = G->coef[(a == 0 ? 0 : 2) * E + qb], ant = G->coef[E + qb];
+            const double T = (W[at(G, ip, jp)] - W[at(G, im, jm)]) / (2.0 * G->h[ta]);
+            corr = ((s % 2) ? -2.0 : 2.0) * G->h[a] * ant / ann * T;
+          }
+          W[gq[0]] = U[1] + corr;
         } else {
           /* Solve  8(U1 - G1) - (U2 - G2) = 0  and  G2 - 5G1 + 10U0 - 10U1 + 5U2 - U3 = 0. */
           double A[2][2] = {{-8.0, 1.0}, {-5.0, 1.0}};
@@ -385,8 +401,17 @@ int or_add_grid(or_problem *P, int n0, int n1, int kind, const int *bc, int orth
     neu |= bc[s] == OR_BC_NEUMANN;
   }
   if (kind == OR_CURVILINEAR && !orthogonal && phys) {
-    snprintf(P->err, sizeof P->err, "non-orthogonal grid with a physical boundary");
-    return -1;
+    /* order 2 only: a Dirichlet side reads no ghost there, and a Neumann side's normal
+     * derivative takes its tangential term along the side, which must be periodic */
+    int ok = P->order == 2;
+    for (int s = 0; s < 4; ++s)
+      if (bc[s] == OR_BC_NEUMANN && bc[2 * (1 - s / 2)] != OR_BC_PERIODIC) ok = 0;
+    if (!ok) {
+      snprintf(P->err, sizeof P->err,
+               "non-orthogonal grid with a physical boundary: order 2 only, Neumann sides "
+               "along a periodic axis");
+      return -1;
+    }
   }
   if (neu) {
     /* a Neumann side may only meet periodic or interpolation sides: the fourth-order

@@ -832,6 +832,39 @@ def with_boundary_data(problem, fn):
     return p
 
 
+def sheared_channel_grid(name, n0, n1, shear, L, bc=BC_NEUMANN, order=2):
+    """A channel periodic in x (period 1) with walls at y = 0 and y = L, on the
+    non-orthogonal grid x = xi + shear * eta, y = L eta (xi periodic in [0, 1), eta in
+    [0, 1]): the xi lines cross the walls at an angle (a_01 = -shear / L^2 != 0).
+    Constant inverse metrics dxi/dx = 1, dxi/dy = -shear / L, deta/dx = 0, deta/dy = 1/L;
+    the walls carry ``bc`` (Dirichlet or Neumann)."""
+    g1 = order // 2
+    d0, d1 = 1.0 / n0, 1.0 / (n1 - 1)
+    xi = (np.arange(n0) * d0)[None, :]
+    eta = (np.arange(n1) * d1)[:, None]
+    X = np.broadcast_to(xi + shear * eta, (n1, n0)).copy()
+    Y = np.broadcast_to(L * eta, (n1, n0)).copy()
+    rx = np.empty((4, n1 + 2 * g1, n0))
+    rx[0], rx[1], rx[2], rx[3] = 1.0, -shear / L, 0.0, 1.0 / L
+    mask = np.full((n1, n0), DISC, np.int8)
+    if bc == BC_DIRICHLET:
+        mask[0, :] = mask[-1, :] = DIRICHLET
+    g = Grid(name, CURVILINEAR, (n0, n1), [BC_PERIODIC, BC_PERIODIC, bc, bc], (d0, d1), mask,
+             np.stack([X, Y]), shear == 0.0, rx)
+    g.mapping = dict(shear=shear, L=L)
+    return g
+
+
+def sheared_channel_problem(n0=32, n1=17, shear=0.4, L=0.6, bc=BC_NEUMANN, order=2,
+                            omega=7.0, seed=0, b=60.0):
+    """One sheared channel grid with a Gaussian source seeded inside."""
+    rng = np.random.default_rng(seed)
+    g = sheared_channel_grid("channel", n0, n1, shear, L, bc, order)
+    x0 = (rng.uniform(0.3, 0.7), rng.uniform(0.3, 0.7) * L)
+    return Problem([g], Interp.empty(order), order, omega, [gaussian(g.xy, x0, 1.0, b)],
+                   name=f"sheared-channel-{n0}x{n1}-s{shear:g}", meta=dict(source=x0))
+
+
 def sheared_torus_problem(n0=32, n1=28, order=4, omega=9.0, seed=0):
     """One non-orthogonal, doubly periodic curvilinear grid (mixed terms everywhere)."""
     rng = np.random.default_rng(seed)

@@ -12,7 +12,8 @@ Helmholtz equations (Sec. 6, Eq. HelmholtzDiscrete of App. B.1):
 This module writes those rows as a scipy sparse matrix from textbook stencil tables,
 independently of the oracle's C code (it shares no routine with it), and solves them
 with a sparse LU.  Ghost rules (g = 0, orthogonal boundary lines):
-order 2 Neumann: U_{-1} - U_{+1} = 0;
+order 2 Neumann: U_{-1} - U_{+1} = 0 (on a non-orthogonal grid the normal derivative
+a_nn D0_n U + a_nt D0_t U = 0 along the side);
 order 4 Neumann: 8(U_1 - G_1) - (U_2 - G_2) = 0 and D+^5 G_2 = 0;
 order 4 Dirichlet: c^2 (a_nn D_nn U + b_n D_n U)_b = f_b and D+^5 G_2 = 0.
 With Dirichlet data g (``problem.g``): U = g at Dirichlet points, and the order-4
@@ -185,8 +186,20 @@ def assemble(problem, omega):
                 gq = [pt(-k) for k in range(1, r + 1)]
                 U = [pt(k) for k in range(4)]
                 if code == G.BC_NEUMANN and order == 2:
-                    put(gq[0], gq[0], 1.0)
-                    put(gq[0], U[1], -1.0)
+                    # grad r_a . grad U = a_aa U_{r_a} + a_at U_{r_t} = 0 with centred
+                    # differences; a_at = 0 on orthogonal grids (U_{-1} - U_{+1} = 0)
+                    ann, ant = 1.0, 0.0
+                    if g.kind == G.CURVILINEAR and not g.orthogonal:
+                        ann, ant = coef[0 if a == 0 else 2][bj, bi], coef[1][bj, bi]
+                    sg = -1.0 if hi else 1.0  # +r_a points inward on a low side
+                    put(gq[0], gq[0], sg * -ann / (2 * g.h[a]))
+                    put(gq[0], U[1], sg * ann / (2 * g.h[a]))
+                    if ant != 0.0:
+                        ta = 1 - a
+                        for dt_, wgt in ((1, 1.0), (-1, -1.0)):
+                            tt = t + dt_
+                            col = lay.idx(gi, bi, tt) if a == 0 else lay.idx(gi, tt, bj)
+                            put(gq[0], col, wgt * ant / (2 * g.h[ta]))
                     filled[gq[0]] = True
                     continue
                 # second row: fifth-order extrapolation of G2

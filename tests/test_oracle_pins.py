@@ -441,9 +441,10 @@ def test_overset_self_convergence(oracle_mod):
 # ----------------------------------------------------------------- rejected input
 
 def test_rejects_unsupported_grids(oracle_mod):
-    T = G.sheared_torus_grid("t", 16, 16, 0.1, 0.1, 2)
+    # physical sides on a non-orthogonal grid are defined at order 2 only
+    T = G.sheared_torus_grid("t", 16, 16, 0.1, 0.1, 4)
     T.bc = [G.BC_DIRICHLET] * 4
-    prob = G.Problem([T], G.Interp.empty(2), 2, 3.0, [np.zeros(T.mask.shape)])
+    prob = G.Problem([T], G.Interp.empty(4), 4, 3.0, [np.zeros(T.mask.shape)])
     with pytest.raises(ValueError):
         oracle_mod.Oracle(prob)
     for bcs in ([G.BC_DIRICHLET, G.BC_DIRICHLET, G.BC_NEUMANN, G.BC_NEUMANN],
