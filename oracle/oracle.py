@@ -66,6 +66,7 @@ def lib(openmp=False):
                                       C.c_double, vp, vp, vp]
             L.or_set_forcing.argtypes = [vp, C.c_int, vp]
             L.or_set_boundary.argtypes = [vp, C.c_int, vp]
+            L.or_set_neumann.argtypes = [vp, C.c_int, vp]
             L.or_set_interp.argtypes = [vp, C.c_long] + [vp] * 8
             L.or_prepare.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
             L.or_iterate.restype = C.c_int
@@ -125,6 +126,11 @@ class Oracle:
                 ga = np.ascontiguousarray(gb[gi], np.float64)
                 self._keep.append(ga)
                 self.L.or_set_boundary(self.h, gi, _p(ga))
+            gn = getattr(problem, "gn", None)
+            if gn is not None and gn[gi] is not None:
+                gna = np.ascontiguousarray(gn[gi], np.float64)
+                self._keep.append(gna)
+                self.L.or_set_neumann(self.h, gi, _p(gna))
         it = problem.interp
         arrs = [np.ascontiguousarray(a, np.int32) for a in
                 (it.recv_grid, it.recv_i, it.recv_j, it.donor_grid, it.donor_i0, it.donor_j0)]

@@ -32,6 +32,8 @@
  * Boundary data: Dirichlet sides carry W_b = g_b cos(omega_e t) with g given per boundary
  * point (or_set_boundary; 0 when not given), switched off with the forcing (the map
  * W_h(., 0) has g = 0).  The Helmholtz solution then takes the value g on those sides.
+ * Neumann sides likewise take dW/dn = gn_b cos(omega_e t) (or_set_neumann; outward normal),
+ * so that the solution's normal derivative is gn there.
  *
  * Ghost-point rules (the paper defers them to its reference on high-order overset wave
  * solvers):
@@ -78,6 +80,7 @@ typedef struct {
   double *f;     /* extended */
   double *gb;    /* extended; Dirichlet boundary data g (used at Dirichlet points) */
   int has_g;
+  double *gn;    /* extended; Neumann data dU/dn (outward normal) at Neumann boundary points */
   double *coef;  /* curvilinear: 5 extended arrays c^2 a11, c^2 a12, c^2 a22, c^2 b1, c^2 b2 */
   long offset;   /* offset of this grid in the concatenated compact vector */
 } or_grid;
@@ -308,6 +311,16 @@ static void apply_bc(const or_problem *P, int gidx, double *W, double fcos) {
       }
       if (code == OR_BC_NEUMANN) {
         if (m != OR_DISC) continue;
+        /* Neumann data: dW/dn = gn cos(omega_e t) along the outward unit normal
+         * -+ grad r_a / |grad r_a|; with |grad r_a| = sqrt(a_aa) (c^2 taken out) the
+         * normal-axis difference gains 2 h gn fcos / sqrt(a_aa) (order 2) or
+         * -12 h gn fcos / sqrt(a_aa) on the undivided fourth-order row, on either side */
+        double gnq = 0.0;
+        if (G->gn[qb] != 0.0) {
+          const double aa = G->kind == OR_CARTESIAN ? 1.0
+                            : G->coef[(a == 0 ? 0 : 2) * E + qb] / G->c2[qb];
+          gnq = G->gn[qb] * fcos / sqrt(aa);
+        }
         if (P->order == 2) {
           /* D0 W = 0 along the normal axis a; on a non-orthogonal grid the normal
            * derivative grad r_a . grad W = a_aa W_{r_a} + a_at W_{r_t} (a_kl =
@@ -322,11 +335,12 @@ static void apply_bc(const or_problem *P, int gidx, double *W, double fcos) {
             const double T = (W[at(G, ip, jp)] - W[at(G, im, jm)]) / (2.0 * G->h[ta]);
             corr = ((s % 2) ? -2.0 : 2.0) * G->h[a] * ant / ann * T;
           }
-          W[gq[0]] = U[1] + corr;
+          W[gq[0]] = U[1] + corr + 2.0 * G->h[a] * gnq;
         } else {
           /* Solve  8(U1 - G1) - (U2 - G2) = 0  and  G2 - 5G1 + 10U0 - 10U1 + 5U2 - U3 = 0. */
           double A[2][2] = {{-8.0, 1.0}, {-5.0, 1.0}};
-          double r[2] = {-(8.0 * U[1] - U[2]), -(10.0 * U[0] - 10.0 * U[1] + 5.0 * U[2] - U[3])};
+          double r[2] = {-(8.0 * U[1] - U[2]) - 12.0 * G->h[a] * gnq,
+                         -(10.0 * U[0] - 10.0 * U[1] + 5.0 * U[2] - U[3])};
           double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
           W[gq[0]] = (r[0] * A[1][1] - A[0][1] * r[1]) / det;
           W[gq[1]] = (A[0][0] * r[1] - r[0] * A[1][0]) / det;
@@ -438,6 +452,7 @@ int or_add_grid(or_problem *P, int n0, int n1, int kind, const int *bc, int orth
   G->c2 = (double *)malloc(E * sizeof(double));
   G->f = (double *)calloc(E, sizeof(double));
   G->gb = (double *)calloc(E, sizeof(double));
+  G->gn = (double *)calloc(E, sizeof(double));
   for (long q = 0; q < E; ++q) G->c2[q] = 1.0;
   for (int j = 0; j < n1; ++j)
     for (int i = 0; i < n0; ++i) {
@@ -468,6 +483,16 @@ int or_set_boundary(or_problem *P, int gidx, const double *g) {
   for (int j = 0; j < G->n[1]; ++j)
     for (int i = 0; i < G->n[0]; ++i) G->gb[at(G, i, j)] = g[(long)j * G->n[0] + i];
   G->has_g = 1;
+  P->prepared = 0;
+  return 0;
+}
+
+/* Neumann data of grid gidx (compact n1 x n0, read at the discretization points of its
+ * Neumann sides): the outward normal derivative of the Helmholtz solution there. */
+int or_set_neumann(or_problem *P, int gidx, const double *gn) {
+  or_grid *G = &P->G[gidx];
+  for (int j = 0; j < G->n[1]; ++j)
+    for (int i = 0; i < G->n[0]; ++i) G->gn[at(G, i, j)] = gn[(long)j * G->n[0] + i];
   P->prepared = 0;
   return 0;
 }
@@ -658,7 +683,7 @@ void or_free(or_problem *P) {
   if (!P) return;
   for (int g = 0; g < P->ngrids; ++g) {
     or_grid *G = &P->G[g];
-    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->gb); free(G->coef);
+    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->gb); free(G->gn); free(G->coef);
   }
   free(P->rg); free(P->ri); free(P->rj); free(P->dg); free(P->di); free(P->dj);
   free(P->wx); free(P->wy);

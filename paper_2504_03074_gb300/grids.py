@@ -101,6 +101,8 @@ class Problem:
     name: str = ""
     meta: dict = field(default_factory=dict)
     g: list | None = None         # per-grid compact Dirichlet data (read at Dirichlet points)
+    gn: list | None = None        # per-grid compact Neumann data dU/dn (outward normal), read
+                                  # at the discretization points of Neumann sides
 
     @property
     def n_active(self):
@@ -863,6 +865,40 @@ def sheared_channel_problem(n0=32, n1=17, shear=0.4, L=0.6, bc=BC_NEUMANN, order
     x0 = (rng.uniform(0.3, 0.7), rng.uniform(0.3, 0.7) * L)
     return Problem([g], Interp.empty(order), order, omega, [gaussian(g.xy, x0, 1.0, b)],
                    name=f"sheared-channel-{n0}x{n1}-s{shear:g}", meta=dict(source=x0))
+
+
+def with_neumann_data(problem, grad):
+    """The same problem with Neumann data on every Neumann side: gn = grad u . n at its
+    discretization points, n the outward unit normal (-+ grad r_a / |grad r_a| from the
+    grid's inverse metrics on a low / high side of axis a; the axis direction on Cartesian
+    grids) and grad(x, y) -> (u_x, u_y) the gradient of the intended solution."""
+    import copy
+    p = copy.copy(problem)
+    p.gn = []
+    for g in problem.grids:
+        gn = np.zeros(g.mask.shape)
+        gh = g.ghosts(problem.order)
+        for s in range(4):
+            if g.bc[s] != BC_NEUMANN:
+                continue
+            a, hi = s // 2, s % 2
+            sl = (slice(None), -1 if hi else 0) if a == 0 else (-1 if hi else 0, slice(None))
+            pts = g.mask[sl] == DISC
+            x, y = g.xy[0][sl], g.xy[1][sl]
+            if g.kind == CARTESIAN:
+                nx, ny = (1.0, 0.0) if a == 0 else (0.0, 1.0)
+                nx, ny = np.full(x.shape, nx), np.full(x.shape, ny)
+            else:
+                rx = g.rx[:, gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]]
+                nx, ny = rx[2 * a][sl], rx[2 * a + 1][sl]
+                nrm = np.hypot(nx, ny)
+                nx, ny = nx / nrm, ny / nrm
+            sign = 1.0 if hi else -1.0
+            ux, uy = grad(x, y)
+            gn[sl] = np.where(pts, sign * (ux * nx + uy * ny), 0.0)
+        p.gn.append(gn)
+    p.name = problem.name + "-gn"
+    return p
 
 
 def sheared_torus_problem(n0=32, n1=28, order=4, omega=9.0, seed=0):

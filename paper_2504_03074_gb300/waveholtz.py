@@ -226,6 +226,9 @@ class Solver:
     def __init__(self, problem, periods=1, cfl=0.9, alpha_mode=0, precision=FP64, stream=None,
                  launch_mode=GRAPH, barrier_spin_limit=0, trajectory_bytes=0,
                  resident_blocks=0):
+        gn = getattr(problem, "gn", None)
+        if gn is not None and any(x is not None and np.any(x != 0) for x in gn):
+            raise ValueError("the library takes no Neumann data (dU/dn != 0)")
         self.L = lib()
         self.problem = problem
         opt = Options()

@@ -13,7 +13,8 @@ This module writes those rows as a scipy sparse matrix from textbook stencil tab
 independently of the oracle's C code (it shares no routine with it), and solves them
 with a sparse LU.  Ghost rules (g = 0, orthogonal boundary lines):
 order 2 Neumann: U_{-1} - U_{+1} = 0 (on a non-orthogonal grid the normal derivative
-a_nn D0_n U + a_nt D0_t U = 0 along the side);
+a_nn D0_n U + a_nt D0_t U = 0 along the side); with Neumann data gn (``problem.gn``) the
+normal derivative along the outward unit normal equals gn instead of 0;
 order 4 Neumann: 8(U_1 - G_1) - (U_2 - G_2) = 0 and D+^5 G_2 = 0;
 order 4 Dirichlet: c^2 (a_nn D_nn U + b_n D_n U)_b = f_b and D+^5 G_2 = 0.
 With Dirichlet data g (``problem.g``): U = g at Dirichlet points, and the order-4
@@ -185,15 +186,27 @@ def assemble(problem, omega):
                     continue
                 gq = [pt(-k) for k in range(1, r + 1)]
                 U = [pt(k) for k in range(4)]
+                # Neumann data dU/dn = gn (outward unit normal -+ grad r_a / |grad r_a|):
+                # |grad r_a| = sqrt(a_aa) without c^2 (1 on Cartesian grids)
+                gnv = 0.0
+                gns = getattr(problem, "gn", None)
+                if code == G.BC_NEUMANN and gns is not None and gns[gi] is not None:
+                    gnv = gns[gi][bj, bi]
+                a_geo = 1.0 if g.kind == G.CARTESIAN else \
+                    coef[0 if a == 0 else 2][bj, bi] / c2[bj, bi]
                 if code == G.BC_NEUMANN and order == 2:
-                    # grad r_a . grad U = a_aa U_{r_a} + a_at U_{r_t} = 0 with centred
-                    # differences; a_at = 0 on orthogonal grids (U_{-1} - U_{+1} = 0)
-                    ann, ant = 1.0, 0.0
-                    if g.kind == G.CURVILINEAR and not g.orthogonal:
-                        ann, ant = coef[0 if a == 0 else 2][bj, bi], coef[1][bj, bi]
+                    # grad r_a . grad U = a_aa U_{r_a} + a_at U_{r_t} = -+ gn |grad r_a| with
+                    # centred differences (rows scaled by c^2 on curvilinear grids); a_at = 0
+                    # on orthogonal grids (U_{-1} - U_{+1} = 0 without data)
+                    ann, ant, scale = 1.0, 0.0, 1.0
+                    if g.kind == G.CURVILINEAR:
+                        ann, scale = coef[0 if a == 0 else 2][bj, bi], c2[bj, bi]
+                        if not g.orthogonal:
+                            ant = coef[1][bj, bi]
                     sg = -1.0 if hi else 1.0  # +r_a points inward on a low side
                     put(gq[0], gq[0], sg * -ann / (2 * g.h[a]))
                     put(gq[0], U[1], sg * ann / (2 * g.h[a]))
+                    rhs[gq[0]] = -sg * scale * gnv * np.sqrt(a_geo)
                     if ant != 0.0:
                         ta = 1 - a
                         for dt_, wgt in ((1, 1.0), (-1, -1.0)):
@@ -208,9 +221,11 @@ def assemble(problem, omega):
                 filled[gq[1]] = True
                 filled[gq[0]] = True
                 if code == G.BC_NEUMANN:
-                    # fourth-order centred normal derivative = 0 (undivided)
+                    # fourth-order centred derivative along the inward normal line
+                    # (undivided) = -12 h gn / |grad r_a|
                     for c_, col in zip([1.0, -8.0, 8.0, -1.0], [gq[1], gq[0], U[1], U[2]]):
                         put(gq[0], col, c_)
+                    rhs[gq[0]] = -12.0 * g.h[a] * gnv / np.sqrt(a_geo)
                 else:
                     if g.kind == G.CARTESIAN:
                         ann, bn = c2[bj, bi], 0.0

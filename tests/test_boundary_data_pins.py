@@ -140,3 +140,108 @@ def test_fixed_point_equals_direct_solve_with_boundary_data_3d(make):
     v = G3.random_state3(base, 1)
     a = O3.Oracle3(base).iterate(v, False)
     assert np.array_equal(a, orc.iterate(v, False))  # the zero-forcing map ignores g
+
+
+# ------------------------------------------------------------------ Neumann data (2D)
+
+def _u(x, y):
+    return np.cos(2 * np.pi * x) * (np.cos(3 * y) + y * y)
+
+
+def _grad_u(x, y):
+    return (-2 * np.pi * np.sin(2 * np.pi * x) * (np.cos(3 * y) + y * y),
+            np.cos(2 * np.pi * x) * (-3 * np.sin(3 * y) + 2 * y))
+
+
+def _lap_u(x, y):
+    return -4 * np.pi ** 2 * _u(x, y) + np.cos(2 * np.pi * x) * (-9 * np.cos(3 * y) + 2)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_manufactured_solution_with_neumann_data(oracle_mod, order):
+    """dU/dn = gn on the walls of a periodic channel (outward normal), with a solution
+    whose normal derivative does not vanish there: the WaveHoltz solution converges at
+    order p."""
+    om, errs = 3.0, []
+    for n in (24, 48):
+        p = G.channel_problem(n, order, om, bc=G.BC_NEUMANN)
+        x, y = p.grids[0].xy
+        p.f = [_lap_u(x, y) + om ** 2 * _u(x, y)]
+        p = G.with_neumann_data(p, _grad_u)
+        v, its, hist = oracle_mod.gmres(oracle_mod.Oracle(p), tol=1e-12, restart=200,
+                                        max_it=600)
+        errs.append(np.max(np.abs(v.reshape(x.shape) - _u(x, y))))
+    rate = math.log2(errs[0] / errs[1])
+    assert order - 0.3 < rate < order + 0.4, errs
+
+
+def _disk_c2():
+    p = G.disk_problem(nb=48, nth=96, nr=10, order=4, omega=4.0, width=0.8, r_cut=0.75)
+    p.c2 = [G.bumps_c2(g.xy, [(0.6, 0.4), (-0.5, -0.6)]) for g in p.grids]
+    return p
+
+
+NEUMANN_CASES = [
+    ("disk-o4-c(x)", _disk_c2),
+    ("channel-o2", lambda: G.channel_problem(30, 2, 5.0, bc=G.BC_NEUMANN)),
+    ("channel-o4", lambda: G.channel_problem(30, 4, 5.0, bc=G.BC_NEUMANN)),
+    ("sheared-channel-o2", lambda: G.sheared_channel_problem(shear=0.4)),
+]
+
+
+@pytest.mark.parametrize("name,make", NEUMANN_CASES, ids=[c[0] for c in NEUMANN_CASES])
+def test_fixed_point_equals_direct_solve_with_neumann_data(oracle_mod, name, make):
+    """The fixed point with Neumann data equals the direct solve whose Neumann rows carry
+    gn on their right sides (tests/dhs.py); the zero-forcing map ignores gn."""
+    import dhs
+    base = make()
+    p = G.with_neumann_data(base, _grad_u)
+    assert max(np.max(np.abs(x)) for x in p.gn) > 0.3
+    orc = oracle_mod.Oracle(p)
+    U = dhs.solve(p)
+    act = orc.active()
+    assert np.max(np.abs(orc.iterate(U, True) - U)[act]) < 1e-12 * np.max(np.abs(U))
+    v = G.random_state(base, 2)
+    assert np.array_equal(orc.iterate(v, False), oracle_mod.Oracle(base).iterate(v, False))
+
+
+def test_overset_disk_with_dirichlet_and_neumann_data_fourth_order(oracle_mod):
+    """Disk-in-square at order 4 with Dirichlet data on the box and Neumann data on the
+    disk (the annulus's curvilinear side, outward normal pointing into the disk): fixed
+    point equal to the direct solve, and a manufactured solution converging at fourth
+    order through the overset interpolation (finer level on the all-cores build)."""
+    import dhs
+
+    def u(x, y):
+        return np.cos(1.5 * x + 0.5 * y) + 0.3 * np.sin(0.7 * x - 1.1 * y)
+
+    def grad(x, y):
+        return (-1.5 * np.sin(1.5 * x + 0.5 * y) + 0.21 * np.cos(0.7 * x - 1.1 * y),
+                -0.5 * np.sin(1.5 * x + 0.5 * y) - 0.33 * np.cos(0.7 * x - 1.1 * y))
+
+    def lap(x, y):
+        return -2.5 * np.cos(1.5 * x + 0.5 * y) - 0.3 * 1.7 * np.sin(0.7 * x - 1.1 * y)
+
+    om, errs = 4.0, []
+    for s in (1, 2):
+        p = G.disk_problem(nb=48 * s, nth=96 * s, nr=10 * s, order=4, omega=om, width=0.8,
+                           r_cut=0.75)
+        p.f = [lap(*g.xy) + om ** 2 * u(*g.xy) for g in p.grids]
+        p = G.with_neumann_data(G.with_boundary_data(p, u), grad)
+        orc = oracle_mod.Oracle(p, openmp=s > 1)
+        if s == 1:
+            U = dhs.solve(p)
+            assert np.max(np.abs(orc.iterate(U, True) - U)[orc.active()]) < \
+                1e-12 * np.max(np.abs(U))
+        v, its, hist = oracle_mod.gmres(orc, tol=1e-12, restart=300, max_it=900)
+        ref = np.concatenate([u(*g.xy).ravel() for g in p.grids])
+        errs.append(np.max(np.abs(v - ref)[orc.active()]))
+    assert 3.5 < math.log2(errs[0] / errs[1]) < 4.5, errs
+
+
+def test_library_refuses_neumann_data():
+    """The GPU binding takes no Neumann data and says so (before any device work)."""
+    from paper_2504_03074_gb300 import waveholtz as W
+    p = G.with_neumann_data(G.channel_problem(16, 2, 5.0, bc=G.BC_NEUMANN), _grad_u)
+    with pytest.raises(ValueError):
+        W.Solver(p)
