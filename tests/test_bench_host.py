@@ -73,3 +73,11 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+
+
+def test_recorded_traffic_matches_the_profiled_kernel_source():
+    """The roofline's measured DRAM traffic is reported only while the march kernel's
+    source is the one the ncu counters were taken from (profiles/traffic.txt keys it by
+    the source hash); this fails as soon as that source changes without a new capture."""
+    import bench
+    assert bench.recorded_traffic("march_kernel") is not None, bench.kernel_sha()
