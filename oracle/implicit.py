@@ -219,6 +219,17 @@ class ImplicitOracle:
             out.append(Vg[gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]].ravel())
         return np.concatenate(out)
 
+    # the spatial operator's pieces (the same as the explicit oracle's): for the
+    # eigenvalues lambda^2 of a deflation set
+    def ext_shape(self, gi):
+        return self.orc.ext_shape(gi)
+
+    def apply_bc(self, gi, u_ext, fcos):
+        return self.orc.apply_bc(gi, u_ext, fcos)
+
+    def apply_lap(self, gi, u_ext):
+        return self.orc.apply_lap(gi, u_ext)
+
     def zeros(self):
         return np.zeros(self.problem.n_total)
 

@@ -143,3 +143,29 @@ def test_implicit_refusals(imp):
     p = G.with_boundary_data(G.unit_square_problem(16, 2, 10.0), lambda x, y: 1.0 + x)
     with pytest.raises(ValueError):
         imp.ImplicitOracle(p)
+
+
+def test_implicit_eigenvalues_and_deflation_on_the_knife_edge(imp):
+    """On the overset knife edge: the slowest eigenvalues of the zero-forcing implicit map
+    (ARPACK on S) equal beta_d(lambda_i; omega_i, T-tilde, alpha_d) of their own spatial
+    eigenvalues (Rayleigh quotients; Theorem FullyDiscreteImplicitWaveHoltzConvergenceRate);
+    and deflating them with the exact inflation (Sec. 4.4, Algorithm 3's purpose: the WH +
+    implicit + deflation combination of Sec. 7) reaches the direct solution in fewer GMRES
+    products."""
+    import dhs
+    from oracle import deflation as D
+    from oracle.oracle import beta_d_sum, gmres
+    p = G.knife_edge_problem(order=2, j=8, omega=20.0, width=0.04, height=0.3, b=300.0)
+    orc = imp.ImplicitOracle(p, n_its=10)
+    T = orc.time
+    Phi, lam2, beta = D.wave_eigenpairs(orc, 8, tol=1e-12)
+    theory = beta_d_sum(imp.lambda_implicit(np.sqrt(lam2), T["dt"]), T["omega_i"], T["dt"],
+                        T["Nt"], T["alpha"], T["periods"])
+    assert np.max(np.abs(beta - theory)) < 1e-8, (beta, theory)
+    U = dhs.solve(p)
+    act = orc.active()
+    u, its_d, _ = D.deflated_gmres_schur(orc, Phi, D.rayleigh_matrix(orc, Phi), tol=1e-12,
+                                         restart=200, max_it=600)
+    assert np.max(np.abs(u - U)[act]) < 1e-9 * np.max(np.abs(U))
+    _, its_p, _ = gmres(orc, tol=1e-12, restart=200, max_it=600)
+    assert its_d < 0.8 * its_p, (its_d, its_p)
