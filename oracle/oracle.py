@@ -67,6 +67,8 @@ def lib(openmp=False):
             L.or_set_forcing.argtypes = [vp, C.c_int, vp]
             L.or_set_boundary.argtypes = [vp, C.c_int, vp]
             L.or_set_neumann.argtypes = [vp, C.c_int, vp]
+            L.or_set_dissipation.restype = C.c_int
+            L.or_set_dissipation.argtypes = [vp, C.c_double]
             L.or_set_interp.argtypes = [vp, C.c_long] + [vp] * 8
             L.or_prepare.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, dp]
             L.or_iterate.restype = C.c_int
@@ -104,10 +106,13 @@ class TimeSetup:
 class Oracle:
     """One overset Helmholtz problem held by the C oracle."""
 
-    def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0, openmp=False):
+    def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0, openmp=False,
+                 nu=0.0):
         self.problem = problem
         self.L = lib(openmp)
         self.h = self.L.or_new(problem.order)
+        if self.L.or_set_dissipation(self.h, float(nu)) != 0:
+            raise ValueError("the dissipation coefficient must be >= 0")
         self._keep = []
         for gi, g in enumerate(problem.grids):
             bc = (C.c_int * 4)(*g.bc)

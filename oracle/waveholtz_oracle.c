@@ -94,6 +94,7 @@ typedef struct {
   /* time setup */
   double omega, dt, omega_e, alpha, cfl;
   int Nt, Np, M, prepared;
+  double nu;     /* dissipation of the deviation from the periodic motion (0: none) */
   char err[256];
 } or_problem;
 
@@ -374,6 +375,28 @@ static void apply_bc(const or_problem *P, int gidx, double *W, double fcos) {
   }
 }
 
+/* Dissipation of the march's deviation from the periodic motion of the iterate (the
+ * paper's upwind-dissipation variant leaves the form to its reference; this is the reading
+ * used here): sum_a (-D+D-)^(p/2) h_a^p applied to Y = (W^n - W^{n-1}) - V0 (cos(omega_e
+ * t^n) - cos(omega_e t^{n-1})), V0 the level-0 state after its boundary rules and
+ * interpolation.  The operator is positive semi-definite and damps the grid-scale modes;
+ * Y vanishes on W^n = V0 cos(omega_e t^n), so a fixed point of the iteration -- the
+ * discrete Helmholtz solution -- stays one (the "additional correction" the paper asks for
+ * to keep the exact match with the direct solve). */
+static double dissipation(const or_problem *P, const or_grid *G, const double *Wn,
+                          const double *Wm, const double *V0, int i, int j, double dc) {
+  static const double c1[3] = {-1.0, 2.0, -1.0}, c2[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+  const int r = P->order / 2;
+  const double *c = r == 1 ? c1 : c2;
+  double s = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int k = -r; k <= r; ++k) {
+      const long q = a == 0 ? at(G, i + k, j) : at(G, i, j + k);
+      s += c[k + r] * ((Wn[q] - Wm[q]) - V0[q] * dc);
+    }
+  return s;
+}
+
 /* Interpolate every receiver from its donor stencil (Sec. 3.1). */
 static void interpolate(const or_problem *P, double **W) {
   int w = P->order + 1;
@@ -489,6 +512,13 @@ int or_set_boundary(or_problem *P, int gidx, const double *g) {
 
 /* Neumann data of grid gidx (compact n1 x n0, read at the discretization points of its
  * Neumann sides): the outward normal derivative of the Helmholtz solution there. */
+/* Dissipation coefficient nu >= 0 of the march (0: the plain scheme). */
+int or_set_dissipation(or_problem *P, double nu) {
+  if (!(nu >= 0.0)) return -1;
+  P->nu = nu;
+  return 0;
+}
+
 int or_set_neumann(or_problem *P, int gidx, const double *gn) {
   or_grid *G = &P->G[gidx];
   for (int j = 0; j < G->n[1]; ++j)
@@ -559,8 +589,10 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
   int ng = P->ngrids, M = P->M;
   double dt = P->dt, we = P->omega_e, fs = forcing ? 1.0 : 0.0;
   double *Wm[OR_MAX_GRIDS], *W0[OR_MAX_GRIDS], *Wp[OR_MAX_GRIDS], *V[OR_MAX_GRIDS];
+  double *Vr[OR_MAX_GRIDS]; /* level 0 after its boundary rules and interpolation */
   for (int g = 0; g < ng; ++g) {
     long E = ext_size(&P->G[g]);
+    Vr[g] = (double *)calloc(E, sizeof(double));
     Wm[g] = (double *)calloc(E, sizeof(double));
     W0[g] = (double *)calloc(E, sizeof(double));
     Wp[g] = (double *)calloc(E, sizeof(double));
@@ -582,6 +614,7 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
     apply_bc(P, g, W0[g], fs);
   }
   interpolate(P, W0);
+  for (int g = 0; g < ng; ++g) memcpy(Vr[g], W0[g], ext_size(&P->G[g]) * sizeof(double));
   for (int n = 0; n < M; ++n) {
     double tn = n * dt;
     double wn = FILTER_W(n);
@@ -608,6 +641,9 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
             Wp[g][q] = W0[g][q] + 0.5 * dt * dt * (L - fs * G->f[q]);
           else /* W^{n+1} = 2W^n - W^{n-1} + dt^2 (c^2 L W^n - f cos(omega_e t^n)) */
             Wp[g][q] = 2.0 * W0[g][q] - Wm[g][q] + dt * dt * (L - fs * G->f[q] * cos(we * tn));
+          if (n > 0 && P->nu > 0.0)
+            Wp[g][q] -= P->nu * dissipation(P, G, W0[g], Wm[g], Vr[g], i, j,
+                                            cos(we * tn) - cos(we * (tn - dt)));
         }
       /* Dirichlet points: the boundary data at t^{n+1} */
       for (int j = 0; j < G->n[1]; ++j)
@@ -638,7 +674,7 @@ int or_iterate(or_problem *P, int forcing, const double *v_in, double *v_out) {
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i)
         v_out[G->offset + (long)j * G->n[0] + i] = V[g][at(G, i, j)];
-    free(Wm[g]); free(W0[g]); free(Wp[g]); free(V[g]);
+    free(Wm[g]); free(W0[g]); free(Wp[g]); free(V[g]); free(Vr[g]);
   }
   return 0;
 }
