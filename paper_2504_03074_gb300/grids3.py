@@ -268,6 +268,79 @@ def pole_patch_grid(name, na, nr, A, r_in, width, sign, order=ORDER):
     return g
 
 
+def cylinder_shell_grid(name, nth, nr, nz, r_in, r_out, lz, bc_in, bc_out, order=ORDER,
+                        beta=0.0):
+    """Annular cylinder x = r (cos th, sin th), z: axis 0 th = 2 pi t0 (periodic, nth
+    points), axis 1 r = r_in + (r_out - r_in) q(t1) (nr points, stretched toward r_out by
+    beta > 0), axis 2 z = lz t2 (periodic, nz points).  Sides axis1-lo / -hi (r_in, r_out)
+    carry bc_in / bc_out (Dirichlet, Neumann or an interpolation face); all pairs of grid
+    lines are orthogonal.  Metrics are analytic, on order/2 ghost lines too; a face with
+    BC_NONE has order/2 interpolation layers."""
+    gw = order // 2
+    d0, d1, d2 = 1.0 / nth, 1.0 / (nr - 1), 1.0 / nz
+    w = r_out - r_in
+    eb = math.expm1(beta) if beta else 0.0
+
+    def q(t):
+        return t if not beta else 1.0 - np.expm1(beta * (1.0 - t)) / eb
+
+    def dq(t):
+        return np.ones_like(t) if not beta else beta * np.exp(beta * (1.0 - t)) / eb
+
+    def fmap(t0, t1, t2):
+        th, r = 2 * np.pi * t0, r_in + w * q(t1)
+        return np.stack([r * np.cos(th), r * np.sin(th), lz * np.asarray(t2) + 0.0 * th])
+
+    def inv(x, y, z):
+        r = np.hypot(x, y)
+        th = np.mod(np.arctan2(y, x), 2 * np.pi)
+        u = (r - r_in) / w
+        with np.errstate(invalid="ignore", divide="ignore"):
+            t1 = u if not beta else 1.0 - np.log1p(eb * (1.0 - u)) / beta
+        fk = np.mod(z / lz, 1.0) * nz
+        ok = (t1 >= -_EPS) & (t1 <= 1.0 + _EPS)
+        return th / (2 * np.pi) * nth, t1 * (nr - 1), fk, ok
+
+    t0 = np.arange(nth) * d0
+    t1 = np.arange(-gw, nr + gw) * d1
+    t2 = np.arange(nz) * d2
+    T2, T1, T0 = np.meshgrid(t2, t1, t0, indexing="ij")
+    th, r = 2 * np.pi * T0, r_in + w * q(T1)
+    rx = np.zeros((9,) + T0.shape)
+    # grad th = (-sin th, cos th, 0) / r, t0 = th / (2 pi); grad r = (cos th, sin th, 0),
+    # t1 = q^{-1}((r - r_in) / w); t2 = z / lz
+    rx[0], rx[1] = -np.sin(th) / r / (2 * np.pi), np.cos(th) / r / (2 * np.pi)
+    rx[3], rx[4] = np.cos(th) / (w * dq(T1)), np.sin(th) / (w * dq(T1))
+    rx[8] = 1.0 / lz
+    mask = np.full((nz, nr, nth), DISC, np.int8)
+    for code, sl in ((bc_in, np.s_[:, :gw, :]), (bc_out, np.s_[:, -gw:, :])):
+        if code == BC_NONE:
+            mask[sl] = INTERP
+    if bc_in == BC_DIRICHLET:
+        mask[:, 0, :] = DIRICHLET
+    if bc_out == BC_DIRICHLET:
+        mask[:, -1, :] = DIRICHLET
+    bc = [BC_PERIODIC, BC_PERIODIC, bc_in, bc_out, BC_PERIODIC, BC_PERIODIC]
+    g = Grid3(name, CURVILINEAR, (nth, nr, nz), bc, (d0, d1, d2), mask, 7, rx)
+    g.mapping = dict(map=fmap, inverse=inv, r_in=r_in, r_out=r_out, lz=lz)
+    return g
+
+
+def annular_cylinder_problem(nth=32, nr=9, nz=10, r_in=0.3, r_out=0.6, lz=1.0,
+                             bc_in=BC_DIRICHLET, bc_out=BC_DIRICHLET, order=ORDER,
+                             omega=5.0, seed=0, b=40.0):
+    """One closed curvilinear grid (periodic in th and z): a Gaussian source seeded in the
+    annulus."""
+    rng = np.random.default_rng(seed)
+    g = cylinder_shell_grid("annulus", nth, nr, nz, r_in, r_out, lz, bc_in, bc_out, order)
+    rr, th, z = rng.uniform(r_in + 0.3 * (r_out - r_in), r_out - 0.3 * (r_out - r_in)), \
+        rng.uniform(0, 2 * np.pi), rng.uniform(0.3, 0.7) * lz
+    x0 = np.array([rr * np.cos(th), rr * np.sin(th), z])
+    return Problem3([g], Interp3.empty(), omega, [gaussian3(g, x0, 1.0, b)],
+                    name=f"annular-cylinder-{nth}x{nr}x{nz}-o{order}",
+                    meta=dict(source=x0.tolist(), seed=seed), order=order)
+
+
 # ----------------------------------------------------------------------------------
 # Donor search (explicit interpolation)
 # ----------------------------------------------------------------------------------

@@ -9,8 +9,9 @@ The converged WaveHoltz iterate equals the direct solution of (Sec. 6, App. B.1)
     U_ghost - U_inward = 0                             at Neumann ghost points,
     U = 0                                              everywhere else.
 
-The rows come from the textbook 7-point stencil, independently of the oracle's C code, and
-are solved with a sparse LU.  At fourth order (``problem.order == 4``) the second
+The rows come from the textbook 7-point stencil (on curvilinear grids the mapped Laplacian
+with metric coefficients and mixed terms), independently of the oracle's C code, and are
+solved with a sparse LU.  At fourth order (``problem.order == 4``) the second
 differences take the 5-point weights (-1, 16, -30, 16, -1)/12, two ghost layers per face
 carry the rows c^2 D_nn U_b = f_b (Dirichlet; the zero boundary values make the
 tangential terms vanish) or 8 (U_1 - G_1) - (U_2 - G_2) = 0 (Neumann), each with the
@@ -67,6 +68,78 @@ def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done):
                 done[G1] = done[G2] = True
 
 
+# full difference tables (offsets -p/2 .. p/2) for curvilinear rows
+D2F = {2: np.array([1.0, -2.0, 1.0]), 4: np.array([-1.0, 16.0, -30.0, 16.0, -1.0]) / 12.0}
+D1F = {2: np.array([-0.5, 0.0, 0.5]), 4: np.array([1.0, -8.0, 0.0, 8.0, -1.0]) / 12.0}
+
+
+def curvilinear_coefficients(problem, gi, order):
+    """c^2 a_kl (3 x 3) and c^2 b_k (3) at the grid's points, shape (n2, n1, n0): the
+    mapping method of Sec. 3.1, a_kl = sum_m dr_k/dx_m dr_l/dx_m and
+    b_k = sum_m sum_l dr_l/dx_m D_l(dr_k/dx_m) with D_l the order-p centred first
+    difference of the (analytic, ghost-extended) metrics; a_kl of pairs declared orthogonal
+    dropped."""
+    g = problem.grids[gi]
+    gh = g.ghosts(order)
+    r = order // 2
+    rx = g.rx  # (9, e2, e1, e0): rx[3k + m] = dr_k/dx_m
+    n0, n1, n2 = g.n
+    sl = (slice(gh[2], gh[2] + n2), slice(gh[1], gh[1] + n1), slice(gh[0], gh[0] + n0))
+
+    def shifted(arr, a, k):
+        ax = 2 - a  # array axis of parameter axis a
+        if g.bc[2 * a] == G.BC_PERIODIC:
+            return np.roll(arr, -k, axis=ax)[sl]
+        s2 = list(sl)
+        s2[ax] = slice(sl[ax].start + k, sl[ax].stop + k)
+        return arr[tuple(s2)]
+
+    def d1(arr, a):
+        return sum(D1F[order][k + r] * shifted(arr, a, k) for k in range(-r, r + 1)) / g.h[a]
+
+    inner = rx[(slice(None),) + sl]
+    c2 = np.ones((n2, n1, n0)) if problem.c2 is None else problem.c2[gi]
+    A = np.empty((3, 3, n2, n1, n0))
+    for k in range(3):
+        for l in range(3):
+            A[k, l] = c2 * sum(inner[3 * k + m] * inner[3 * l + m] for m in range(3))
+    for p_, (a, b) in enumerate(((0, 1), (0, 2), (1, 2))):
+        if g.ortho >> p_ & 1:
+            A[a, b] = A[b, a] = 0.0
+    B = np.empty((3, n2, n1, n0))
+    for k in range(3):
+        B[k] = c2 * sum(inner[3 * l + m] * d1(rx[3 * k + m], l) for m in range(3)
+                        for l in range(3))
+    return A, B
+
+
+def curvilinear_row(put, L, gi, g, i, j, k, A, B, order, r_row):
+    """The mapped Laplacian's row at (i, j, k): sum_a A_aa D2_a + B_a D1_a + 2 sum_{a<b}
+    A_ab D1_a D1_b (the centre weight is added by the caller's put accumulation)."""
+    rr = order // 2
+    for a in range(3):
+        for s_ in range(-rr, rr + 1):
+            d = [0, 0, 0]
+            d[a] = s_
+            w = (A[a, a, k, j, i] * D2F[order][s_ + rr] / g.h[a] ** 2 +
+                 B[a, k, j, i] * D1F[order][s_ + rr] / g.h[a])
+            if w != 0.0:
+                put(r_row, L.idx(gi, i + d[0], j + d[1], k + d[2]), w)
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        ab = A[a, b, k, j, i]
+        if ab == 0.0:
+            continue
+        for sa in range(-rr, rr + 1):
+            for sb in range(-rr, rr + 1):
+                w = D1F[order][sa + rr] * D1F[order][sb + rr]
+                if w == 0.0:
+                    continue
+                d = [0, 0, 0]
+                d[a], d[b] = sa, sb
+                put(r_row, L.idx(gi, i + d[0], j + d[1], k + d[2]),
+                    2.0 * ab * w / (g.h[a] * g.h[b]))
+
+
 class Layout3:
     def __init__(self, problem):
         self.p = problem
@@ -107,7 +180,9 @@ def assemble(problem):
         vals.append(v)
 
     for gi, g in enumerate(problem.grids):
-        assert g.kind == G.CARTESIAN
+        curv = g.kind == G.CURVILINEAR
+        if curv:
+            A, B = curvilinear_coefficients(problem, gi, order)
         c2 = np.ones(g.mask.shape) if problem.c2 is None else problem.c2[gi]
         for k in range(g.n[2]):
             for j in range(g.n[1]):
@@ -115,7 +190,11 @@ def assemble(problem):
                     m = g.mask[k, j, i]
                     r = L.idx(gi, i, j, k)
                     done[r] = True
-                    if m == G.DISC:
+                    if m == G.DISC and curv:
+                        put(r, r, om2)
+                        curvilinear_row(put, L, gi, g, i, j, k, A, B, order, r)
+                        rhs[r] = problem.f[gi][k, j, i]
+                    elif m == G.DISC:
                         diag = om2
                         for a in range(3):
                             w = c2[k, j, i] / g.h[a] ** 2
@@ -175,7 +254,9 @@ def assemble(problem):
 def solve(problem):
     """Direct DHS solution as a compact vector (grids concatenated, axis 0 fastest)."""
     A, rhs, L = assemble(problem)
-    U = spla.spsolve(A.tocsc(), rhs)
+    lu = spla.splu(A.tocsc())
+    U = lu.solve(rhs)
+    U = U + lu.solve(rhs - A @ U)  # one step of iterative refinement
     out = []
     for gi, g in enumerate(problem.grids):
         gh, e = L.gh[gi], L.ext[gi]
