@@ -41,7 +41,9 @@
  * also the first difference D0(1 - h^2/6 D+D-) and its tensor product for the mixed terms
  * (and for b_k from the metrics), the stability constant C = sqrt(3)/2 in the time-step
  * bound, Lagrange interpolation of width 5, and the two-dimensional fourth-order ghost
- * rules applied along each face's normal axis (Dirichlet faces on Cartesian grids only):
+ * rules applied along each face's normal axis (on a curvilinear grid a Dirichlet face's
+ * compatibility condition takes c^2 (a_nn D_nn + b_n D_n); its normal axis must be
+ * orthogonal to the others):
  *   Dirichlet: W_b = 0 (no boundary data at this order); c^2 D_nn W_b = f_b cos(omega_e t)
  *     (the tangential second differences of the zero boundary values vanish) and
  *     D+^5 W_{-2} = 0;
@@ -248,6 +250,7 @@ static double dt_bound(const o3_problem *P) {
  * (U0..U3 the boundary point and three inward, G1, G2 the two ghosts). */
 static void apply_bc(const o3_problem *P, int gidx, double *W, double fcos) {
   const o3_grid *G = &P->G[gidx];
+  const long E = ext_size(G);
   for (int s = 0; s < 6; ++s) {
     const int code = G->bc[s];
     if (code != O3_BC_NEUMANN && !(code == O3_BC_DIRICHLET && G->fourth)) continue;
@@ -281,10 +284,19 @@ static void apply_bc(const o3_problem *P, int gidx, double *W, double fcos) {
           A[0][0] = -8.0; A[0][1] = 1.0;
           r[0] = -(8.0 * U[1] - U[2]);
         } else {
-          /* c^2 (-G2 + 16 G1 - 30 U0 + 16 U1 - U2) / (12 h^2) = f_b cos */
-          const double A2 = G->c2[qb] / (12.0 * G->h[a] * G->h[a]);
-          A[0][0] = 16.0 * A2; A[0][1] = -A2;
-          r[0] = G->f[qb] * fcos - A2 * (-30.0 * U[0] + 16.0 * U[1] - U[2]);
+          /* c^2 (a_nn D_nn W + b_n D_n W)_b = f_b cos, D_nn = (-G2 + 16 G1 - 30 U0 +
+           * 16 U1 - U2) / (12 h^2) and D_n along +r_a, i.e. +-(-U2 + 8 U1 - 8 G1 + G2) /
+           * (12 h) with + on a low side (Cartesian grids: a_nn = 1, b_n = 0) */
+          double ann = G->c2[qb], bn = 0.0;
+          if (G->kind == O3_CURVILINEAR) {
+            ann = G->coef[(C_A00 + a) * E + qb];
+            bn = G->coef[(C_B0 + a) * E + qb];
+          }
+          const double A2 = ann / (12.0 * G->h[a] * G->h[a]);
+          const double B1 = (hi ? -1.0 : 1.0) * bn / (12.0 * G->h[a]);
+          A[0][0] = 16.0 * A2 - 8.0 * B1; A[0][1] = -A2 + B1;
+          r[0] = G->f[qb] * fcos - A2 * (-30.0 * U[0] + 16.0 * U[1] - U[2]) -
+                 B1 * (8.0 * U[1] - U[2]);
         }
         const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
         W[g1] = (r[0] * A[1][1] - A[0][1] * r[1]) / det;
@@ -344,12 +356,21 @@ int o3_add_grid(o3_problem *P, int n0, int n1, int n2, int kind, const int *bc, 
     }
   }
   if (P->order == 4) {
+    /* a Dirichlet face's fourth-order rule on a curvilinear grid takes the normal axis's
+     * own terms only: that axis must be orthogonal to the two others */
     if (kind != O3_CARTESIAN)
-      for (int s = 0; s < 6; ++s)
-        if (bc[s] == O3_BC_DIRICHLET) {
-          snprintf(P->err, sizeof P->err, "fourth order in 3D: no Dirichlet face on a curvilinear grid");
-          return -1;
+      for (int s = 0; s < 6; ++s) {
+        if (bc[s] != O3_BC_DIRICHLET) continue;
+        for (int b = 0; b < 3; ++b) {
+          const int a = s / 2;
+          if (b == a) continue;
+          if (!(ortho >> pair_of(a < b ? a : b, a < b ? b : a) & 1)) {
+            snprintf(P->err, sizeof P->err,
+                     "fourth order: a Dirichlet face's normal axis must be orthogonal to the others");
+            return -1;
+          }
         }
+      }
     /* the fourth-order Neumann rule is unstable at corners with another physical side */
     for (int s = 0; s < 6; ++s)
       for (int s2 = 0; s2 < 6; ++s2)

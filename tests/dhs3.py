@@ -33,8 +33,10 @@ D2C = {2: -2.0, 4: -30.0 / 12}
 EXTRAP5 = [1.0, -5.0, 10.0, -10.0, 5.0, -1.0]  # on G2, G1, U0, U1, U2, U3
 
 
-def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done):
-    """The two ghost rows of every boundary point of a Dirichlet or Neumann face."""
+def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done, coef=None):
+    """The two ghost rows of every boundary point of a Dirichlet or Neumann face; on a
+    curvilinear grid (coef = (A, B) of curvilinear_coefficients) the Dirichlet row is
+    c^2 (a_nn D_nn + b_n D_n) U_b = f_b with D_n along +r_a."""
     for s in range(6):
         code = g.bc[s]
         if code not in (G.BC_DIRICHLET, G.BC_NEUMANN):
@@ -61,9 +63,16 @@ def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done):
                     for c_, col in zip([1.0, -8.0, 8.0, -1.0], [G2, G1, U[1], U[2]]):
                         put(G1, col, c_)
                 else:
-                    w = c2[b[2], b[1], b[0]] / (12.0 * g.h[a] ** 2)
-                    for c_, col in zip([-1.0, 16.0, -30.0, 16.0, -1.0], [G2, G1] + U[:3]):
-                        put(G1, col, w * c_)
+                    ann, bn = c2[b[2], b[1], b[0]], 0.0
+                    if coef is not None:
+                        ann = coef[0][a, a, b[2], b[1], b[0]]
+                        bn = coef[1][a, b[2], b[1], b[0]]
+                    w = ann / (12.0 * g.h[a] ** 2)
+                    # +r_a is inward on a low side: D_n = (G2 - 8 G1 + 8 U1 - U2) / (12 h)
+                    wb = (-1.0 if hi else 1.0) * bn / (12.0 * g.h[a])
+                    for c_, d_, col in zip([-1.0, 16.0, -30.0, 16.0, -1.0],
+                                           [1.0, -8.0, 0.0, 8.0, -1.0], [G2, G1] + U[:3]):
+                        put(G1, col, w * c_ + wb * d_)
                     rhs[G1] = problem.f[gi][b[2], b[1], b[0]]
                 done[G1] = done[G2] = True
 
@@ -211,7 +220,8 @@ def assemble(problem):
                         if m == G.DIRICHLET and gb is not None and gb[gi] is not None:
                             rhs[r] = gb[gi][k, j, i]  # U = g at Dirichlet points
         if order == 4:
-            fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done)
+            fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done,
+                                    (A, B) if curv else None)
             continue
         # Neumann ghosts next to discretization points
         for s in range(6):

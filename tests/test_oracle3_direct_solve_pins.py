@@ -18,7 +18,8 @@ def o3():
     return oracle3
 
 
-@pytest.mark.parametrize("order,bc_in,bc_out", [(2, D, D), (2, N, N), (2, D, N), (4, N, N)])
+@pytest.mark.parametrize("order,bc_in,bc_out", [(2, D, D), (2, N, N), (2, D, N), (4, N, N),
+                                               (4, D, D), (4, D, N)])
 def test_annular_cylinder_fixed_point_equals_direct_solve(o3, order, bc_in, bc_out):
     """An annular cylinder (periodic in th and z, metric terms b_th = 0, b_r = 1/r in the
     mapped Laplacian): the oracle's fixed point equals the direct solve to 1e-12, and its
@@ -62,3 +63,28 @@ def test_mapped_laplacian_rows_equal_direct_assembly(o3, kind, order):
     disc[gh[2]:gh[2] + g.n[2], gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]] = g.mask == G.DISC
     disc = disc.ravel()
     assert np.max(np.abs(Au[disc] - lap[disc])) < 1e-11 * np.max(np.abs(lap[disc]))
+
+
+def test_annular_cylinder_dirichlet_solution_fourth_order(o3):
+    """u = (r^2 - a^2)(b^2 - r^2) cos(2 th) cos(2 pi z) vanishes on both walls; with
+    f = Lap u + omega^2 u the solution on the curvilinear annular cylinder (order-4
+    Dirichlet compatibility rows with a_nn and b_n) converges at fourth order."""
+    import math
+    from oracle.oracle import gmres
+    a, b, om = 0.3, 0.6, 4.0
+    errs = []
+    for s_ in (1, 2):
+        p = G3.annular_cylinder_problem(nth=32 * s_, nr=8 * s_ + 1, nz=10 * s_, r_in=a, r_out=b,
+                                        order=4, omega=om)
+        x, y, z = p.grids[0].coords()
+        r, th = np.hypot(x, y), np.arctan2(y, x)
+        R = (r * r - a * a) * (b * b - r * r)
+        R1 = -4 * r ** 3 + 2 * (a * a + b * b) * r
+        R2 = -12 * r * r + 2 * (a * a + b * b)
+        ang = np.cos(2 * th) * np.cos(2 * np.pi * z)
+        u = R * ang
+        lap = (R2 + R1 / r - 4 * R / (r * r) - (2 * np.pi) ** 2 * R) * ang
+        p.f = [lap + om ** 2 * u]
+        v, its, hist = gmres(o3.Oracle3(p), tol=1e-12, restart=200, max_it=600)
+        errs.append(np.max(np.abs(v - u.ravel())))
+    assert 3.6 < math.log2(errs[0] / errs[1]) < 4.5, errs

@@ -268,12 +268,14 @@ def test_overset_solution_fourth_order_3d(o3):
 # ------------------------------------------------------- what it refuses
 
 def test_fourth_order_refusals(o3):
-    """A curvilinear grid with a Dirichlet face, a Neumann face meeting another physical
-    face, and Dirichlet data at fourth order are refused, as is an order other than 2 or
-    4."""
+    """A curvilinear Dirichlet face whose normal axis is not orthogonal to the others, a
+    Neumann face meeting another physical face, and Dirichlet data at fourth order are
+    refused, as is an order other than 2 or 4."""
     g = G3.pole_patch_grid("north", 12, 8, 0.5, 0.5, 0.3, 1.0, order=4)
     o3.Oracle3(_single(g))  # Neumann sphere face, interpolation edges: taken
-    g.bc[5] = D
+    g.bc[5] = D  # the radial axis is orthogonal to a and b: taken
+    o3.Oracle3(_single(g))
+    g.bc[0] = g.bc[1] = D  # the a axis is not orthogonal to b
     with pytest.raises(ValueError):
         o3.Oracle3(_single(g))
     with pytest.raises(ValueError):
