@@ -326,6 +326,65 @@ def cylinder_shell_grid(name, nth, nr, nz, r_in, r_out, lz, bc_in, bc_out, order
     return g
 
 
+def pipe(j=2, order=ORDER, radius=0.5, lz=1.0, wfac=None, wmax=0.3, cut=0.5, shift=1):
+    """The paper's solid pipe (Sec. 6): the inside of a cylinder of the given radius,
+    periodic in z over [0, lz), Dirichlet on the curved wall; target spacing h = 1/(10 j).
+    A Cartesian background over [-radius, radius]^2 x [0, lz) (periodic in z) with the
+    points beyond r_cut = r_in + cut W cut out (those within order/2 index layers of an
+    active point become interpolation points), and a cylindrical shell of width
+    W = min(wfac h, wmax) along the wall (r_in = radius - W; inner order/2 layers
+    interpolated from the background; the wall Dirichlet).  Donor stencils of width
+    order + 1 hold discretization or Dirichlet points only: centred stencils need a shell
+    about 12 h wide at order 4 (wfac defaults to 8 at order 2, 12 at order 4, so j >= 3
+    there under the cap); with ``shift`` > 0 (default 1) off-centred stencils, moved by
+    up to that many points per axis, are taken where centred ones are not valid, which
+    makes order 4 on the coarsest grid (j = 2, shell 6 h wide) possible.
+    Returns (grids, interp)."""
+    h = 1.0 / (10 * j)
+    if wfac is None:
+        wfac = 8.0 if order == 2 else 12.0
+    W = min(wfac * h, wmax)
+    r_in = radius - W
+    w = order + 1
+    nxy = int(round(2 * radius / h)) + 1
+    nz = int(round(lz / h))
+    B = cartesian_grid3("background", (nxy, nxy, nz), (-radius, -radius, 0.0),
+                        (radius, radius, lz * (nz - 1) / nz),
+                        [BC_NONE, BC_NONE, BC_NONE, BC_NONE, BC_PERIODIC, BC_PERIODIC])
+    nth = int(round(2 * np.pi * radius / h))
+    nr = int(round(W / h)) + 1
+    S = cylinder_shell_grid("shell", nth, nr, nz, r_in, radius, lz, BC_NONE, BC_DIRICHLET,
+                            order)
+    x = -radius + B.h[0] * np.arange(nxy)
+    rr = np.hypot(x[None, :], x[:, None])
+    outside = np.broadcast_to(rr > r_in + cut * W, (nz, nxy, nxy)).copy()
+    near = _near(~outside, order // 2)
+    B.mask[outside & near] = INTERP
+    B.mask[outside & ~near] = UNUSED
+    grids = [B, S]
+    parts = []
+    for rgid, donors in ((0, (1,)), (1, (0,))):
+        g = grids[rgid]
+        ijk = _interp_points(g)
+        pts = _points_of(g, ijk)
+        dg, c, f = find_donors(grids, rgid, pts, donors, w, shift)
+        parts.append((rgid, ijk, dg, c, f))
+    interp = _assemble(grids, parts, w)
+    check_explicit_interp3(grids, interp)
+    return grids, interp
+
+
+def pipe_problem(j=2, order=ORDER, omega=8.5, source=(0.1, 0.1, 0.5), amp=150.0, b=10.0,
+                 **kw):
+    """The pipe with the paper's Gaussian source (amplitude 150, exponent 10, centred at
+    (0.1, 0.1, 0.5))."""
+    grids, interp = pipe(j, order, **kw)
+    x0 = np.array(source, np.float64)
+    f = [gaussian3(g, x0, amp, b) for g in grids]
+    return Problem3(grids, interp, omega, f, name=f"pipe-j{j}-o{order}",
+                    meta=dict(source=list(source)), order=order)
+
+
 def annular_cylinder_problem(nth=32, nr=9, nz=10, r_in=0.3, r_out=0.6, lz=1.0,
                              bc_in=BC_DIRICHLET, bc_out=BC_DIRICHLET, order=ORDER,
                              omega=5.0, seed=0, b=40.0):
@@ -374,10 +433,19 @@ def _valid(g, c, w=3):
     return ok
 
 
-def find_donors(grids, recv_gid, pts, order_of_donors, w=3):
+def _shifts(s):
+    """Stencil offsets d in {-s..s}^3 other than 0, nearest first (by |d|_1, then |d|_inf)."""
+    r = range(-s, s + 1)
+    ds = [(a, b, c) for c in r for b in r for a in r if (a, b, c) != (0, 0, 0)]
+    return sorted(ds, key=lambda d: (sum(map(abs, d)), max(map(abs, d))))
+
+
+def find_donors(grids, recv_gid, pts, order_of_donors, w=3, shift=0):
     """Donor stencils of width w for receivers of grid ``recv_gid`` at physical points
     pts (3, N), trying donor grids in the given order; raises if a receiver has no valid
-    stencil."""
+    stencil.  With shift > 0 a receiver whose centred stencil touches a point that is not
+    a discretization or Dirichlet point takes the nearest valid stencil moved by up to
+    ``shift`` points per axis (off-centred Lagrange interpolation, same width)."""
     N = pts.shape[1]
     out_g = np.full(N, -1, np.int32)
     out_c = np.zeros((3, N), np.int64)
@@ -393,6 +461,22 @@ def find_donors(grids, recv_gid, pts, order_of_donors, w=3):
             continue
         c = _stencil(g, fi[sel], fj[sel], fk[sel], w)
         v = _valid(g, c, w)
+        for d in (_shifts(shift) if shift > 0 else ()):
+            if np.all(v):
+                break
+            bad = np.nonzero(~v)[0]
+            cs = []
+            for a in range(3):
+                ca = c[a][bad] + d[a]
+                if g.bc[2 * a] == BC_PERIODIC:
+                    ca = np.mod(ca, g.n[a])
+                else:
+                    ca = np.clip(ca, 0, g.n[a] - w)
+                cs.append(ca)
+            vb = _valid(g, cs, w)
+            for a in range(3):
+                c[a][bad[vb]] = cs[a][vb]
+            v[bad[vb]] = True
         take = todo[sel[v]]
         out_g[take] = dgid
         for a, fa in enumerate((fi, fj, fk)):
