@@ -689,6 +689,332 @@ def knife_edge(j=32, order=4, width=0.02, height=0.5, wfac=12.0, n1=16, cut=0.4,
 
 
 # ----------------------------------------------------------------------------------
+# The double ellipse (Penrose's unilluminable room)
+# ----------------------------------------------------------------------------------
+
+class _Segment:
+    """A straight piece of an outline from p0 to p1, by arclength (straight beyond both
+    ends).  frame(s) -> (x, y, tx, ty, kappa)."""
+
+    def __init__(self, p0, p1):
+        self.p0 = np.asarray(p0, np.float64)
+        d = np.asarray(p1, np.float64) - self.p0
+        self.L = float(np.hypot(d[0], d[1]))
+        self.t = d / self.L
+
+    def frame(self, s):
+        s = np.asarray(s, np.float64)
+        z = np.zeros_like(s)
+        return (self.p0[0] + s * self.t[0], self.p0[1] + s * self.t[1], z + self.t[0],
+                z + self.t[1], z)
+
+
+class _EllipseArc:
+    """The arc theta from th0 to th1 of the ellipse c + (a cos theta, b sin theta), by
+    arclength s from th0 (the ellipse continues beyond both ends).  theta(s) by Newton on
+    s(theta), the integral of the speed sqrt(a^2 sin^2 + b^2 cos^2) from a table of
+    12-point Gauss-Legendre panels plus one partial panel.  kappa = dphi/ds, positive where
+    the tangent turns counterclockwise."""
+
+    def __init__(self, center, a, b, th0, th1, ext=0.5, panels=2048):
+        self.c = np.asarray(center, np.float64)
+        self.a, self.b = float(a), float(b)
+        self.th0, self.sg = float(th0), 1.0 if th1 > th0 else -1.0
+        psi_end = abs(th1 - th0)
+        self.lo, self.dpsi = -ext, (psi_end + 2.0 * ext) / panels
+        self.gx, self.gw = _gauss01(12)
+        nodes = self.lo + self.dpsi * np.arange(panels)
+        seg = self.dpsi * np.sum(self.gw * self._speed(nodes[:, None] + self.dpsi * self.gx),
+                                 axis=1)
+        self.cum = np.concatenate([[0.0], np.cumsum(seg)])
+        self.s0 = 0.0
+        self.s0 = float(self._s(np.array([0.0]))[0])
+        self.L = float(self._s(np.array([psi_end]))[0])
+
+    def _speed(self, psi):
+        th = self.th0 + self.sg * psi
+        return np.hypot(self.a * np.sin(th), self.b * np.cos(th))
+
+    def _s(self, psi):
+        k = np.clip(np.floor((psi - self.lo) / self.dpsi).astype(np.int64), 0,
+                    len(self.cum) - 2)
+        base = self.lo + k * self.dpsi
+        d = psi - base
+        part = d * np.sum(self.gw * self._speed(base[..., None] + d[..., None] * self.gx),
+                          axis=-1)
+        return self.cum[k] + part - self.s0
+
+    def frame(self, s):
+        s = np.asarray(s, np.float64)
+        psi = s / max(self.a, self.b)
+        for _ in range(60):
+            step = (self._s(psi) - s) / self._speed(psi)
+            psi = psi - step
+            if np.all(np.abs(step) < 1e-14):
+                break
+        th = self.th0 + self.sg * psi
+        sp = np.hypot(self.a * np.sin(th), self.b * np.cos(th))
+        tx = -self.sg * self.a * np.sin(th) / sp
+        ty = self.sg * self.b * np.cos(th) / sp
+        kap = self.sg * self.a * self.b / sp ** 3
+        return self.c[0] + self.a * np.cos(th), self.c[1] + self.b * np.sin(th), tx, ty, kap
+
+
+class _Outline:
+    """Pieces joined end to end with a continuous tangent, by arclength sigma in [0, S]
+    (the first and last pieces continue beyond the ends)."""
+
+    def __init__(self, pieces):
+        self.pieces = pieces
+        self.starts = np.concatenate([[0.0], np.cumsum([p.L for p in pieces])])
+        self.S = float(self.starts[-1])
+
+    def frame(self, sigma):
+        sigma = np.asarray(sigma, np.float64)
+        k = np.searchsorted(self.starts[1:-1], sigma, side="right")
+        out = [np.zeros_like(sigma) for _ in range(5)]
+        for i, p in enumerate(self.pieces):
+            sel = k == i
+            if np.any(sel):
+                for o, v in zip(out, p.frame(sigma[sel] - self.starts[i])):
+                    o[sel] = v
+        return tuple(out)
+
+
+class _OffsetMap:
+    """x = gamma(sigma) + d n(sigma) with sigma = S t0 along an outline, d = W t1 along the
+    right-hand normal n = (t_y, -t_x) (into the fluid), uniform in both.  Orthogonal:
+    dx/dsigma = (1 + kappa d) t, dx/dd = n."""
+
+    def __init__(self, outline, W, ext):
+        self.o, self.W = outline, W
+        sig = np.linspace(-ext, outline.S + ext, int((outline.S + 2 * ext) / (W / 400.0)) + 2)
+        x, y, _, _, _ = outline.frame(sig)
+        from scipy.spatial import cKDTree
+        self._sig, self._tree = sig, cKDTree(np.stack([x, y], axis=1))
+
+    def xy(self, t0, t1):
+        x, y, tx, ty, _ = self.o.frame(self.o.S * t0)
+        d = self.W * t1
+        return x + d * ty, y - d * tx
+
+    def rx(self, t0, t1):
+        """dt0/dx, dt0/dy, dt1/dx, dt1/dy (analytic in the outline's frame)."""
+        _, _, tx, ty, kap = self.o.frame(self.o.S * t0)
+        j0 = self.o.S * (1.0 + self.W * t1 * kap)
+        return tx / j0, ty / j0, ty / self.W, -tx / self.W
+
+    def param(self, x, y):
+        """(sigma, d) of physical points: the nearest outline sample, then Newton on
+        (p - gamma(sigma)) . t(sigma) = 0 (derivative -(1 + kappa d)); the last residual."""
+        x, y = np.asarray(x, np.float64), np.asarray(y, np.float64)
+        _, k = self._tree.query(np.stack([x.ravel(), y.ravel()], axis=1))
+        sig = self._sig[k].reshape(x.shape)
+        for _ in range(12):
+            gx, gy, tx, ty, kap = self.o.frame(sig)
+            f = (x - gx) * tx + (y - gy) * ty
+            d = (x - gx) * ty - (y - gy) * tx
+            sig = sig + f / np.maximum(1.0 + kap * d, 0.25)
+        gx, gy, tx, ty, _ = self.o.frame(sig)
+        f = (x - gx) * tx + (y - gy) * ty
+        return sig, (x - gx) * ty - (y - gy) * tx, f
+
+
+def _offset_grid(name, outline, W, h, order, ends_physical):
+    """The grid of an _OffsetMap: axis 0 along the outline (spacing about h), axis 1 into
+    the fluid (W / h intervals).  The wall row is Dirichlet; the outer order/2 rows are
+    interpolation points; the end columns are Dirichlet sides (ends_physical) or order/2
+    interpolation columns (their wall points stay Dirichlet)."""
+    g1 = order // 2
+    m = _OffsetMap(outline, W, (g1 + 2) * h)
+    n0 = int(math.ceil(outline.S / h)) + 1
+    n1 = int(round(W / h)) + 1
+    d0, d1 = 1.0 / (n0 - 1), 1.0 / (n1 - 1)
+    t0e = (np.arange(-g1, n0 + g1) * d0)[None, :]
+    t1e = (np.arange(-g1, n1 + g1) * d1)[:, None]
+    shape = (n1 + 2 * g1, n0 + 2 * g1)
+    rx = np.stack([np.broadcast_to(v, shape) for v in m.rx(t0e, t1e)])
+    X, Y = m.xy((np.arange(n0) * d0)[None, :], (np.arange(n1) * d1)[:, None])
+    X, Y = np.broadcast_to(X, (n1, n0)).copy(), np.broadcast_to(Y, (n1, n0)).copy()
+    mask = np.full((n1, n0), DISC, np.int8)
+    if ends_physical:
+        mask[:, 0] = mask[:, -1] = DIRICHLET
+    else:
+        mask[:, :g1] = mask[:, n0 - g1:] = INTERP
+    mask[n1 - g1:, :] = INTERP
+    mask[0, :] = DIRICHLET
+    side = BC_DIRICHLET if ends_physical else BC_NONE
+    g = Grid(name, CURVILINEAR, (n0, n1), [side, side, BC_DIRICHLET, BC_NONE], (d0, d1), mask,
+             np.stack([X, Y]), True, np.ascontiguousarray(rx))
+    g.mapping = dict(offset=m)
+    return g
+
+
+class DoubleEllipseRoom:
+    """Penrose's unilluminable room as the paper builds it (Sec. 6): the left and right
+    walls are half-ellipses with semi-axes (a2, b2) = (3, 6) centred at (-+a1, 0); the top
+    and bottom walls are half-ellipses with semi-axes (a1, b1) = (2, 1) centred at
+    (0, +-f), f = sqrt(b2^2 - a2^2), whose ends sit at the large ellipses' foci
+    (-+a1, +-f); vertical segments x = -+a1 from the foci to the large ellipses' ends
+    (-+a1, +-b2) close the four alcoves.  The room spans [-5, 5] x [-6, 6]."""
+
+    a1, b1, a2, b2 = 2.0, 1.0, 3.0, 6.0
+
+    def __init__(self):
+        self.f = math.sqrt(self.b2 ** 2 - self.a2 ** 2)
+
+    def inside(self, x, y):
+        a1, f = self.a1, self.f
+        left = ((x + a1) / self.a2) ** 2 + (y / self.b2) ** 2 < 1.0
+        right = ((x - a1) / self.a2) ** 2 + (y / self.b2) ** 2 < 1.0
+        with np.errstate(invalid="ignore"):
+            cap = f - self.b1 * np.sqrt(np.clip(1.0 - (x / a1) ** 2, 0.0, None))
+        mid = (np.abs(x) < a1) & (np.abs(y) < cap)
+        return np.where(x <= -a1, left, np.where(x >= a1, right, mid))
+
+    def outlines(self, y0):
+        """The four walls as outlines traversed with the fluid on the right: the left and
+        right half-ellipses (end to end), and the top and bottom walls from y = +-y0 on
+        one alcove segment, around the small half-ellipse, to y = +-y0 on the other."""
+        a1, b1, a2, b2, f = self.a1, self.b1, self.a2, self.b2, self.f
+        pi = math.pi
+        left = _Outline([_EllipseArc((-a1, 0.0), a2, b2, 1.5 * pi, 0.5 * pi)])
+        right = _Outline([_EllipseArc((a1, 0.0), a2, b2, 0.5 * pi, -0.5 * pi)])
+        top = _Outline([_Segment((-a1, y0), (-a1, f)), _EllipseArc((0.0, f), a1, b1, pi, 2 * pi),
+                        _Segment((a1, f), (a1, y0))])
+        bottom = _Outline([_Segment((a1, -y0), (a1, -f)), _EllipseArc((0.0, -f), a1, b1, 0.0, pi),
+                           _Segment((-a1, -f), (-a1, -y0))])
+        return left, right, top, bottom
+
+
+def _find_donors2(grids, index_fns, xq, yq, candidates, order, shift=1):
+    """Width-(order+1) donor stencils for points (xq, yq): for each stencil offset (centred
+    first, then moved by up to ``shift`` points per axis, nearest first; shifted inward
+    at a grid's edge), each candidate grid in turn; a stencil is valid when it holds
+    discretization or Dirichlet points only.  Returns (donor grid, i0, j0, wx, wy); raises if a point has
+    none."""
+    w = order + 1
+    N = xq.size
+    dg = np.full(N, -1, np.int64)
+    i0 = np.zeros(N, np.int64)
+    j0 = np.zeros(N, np.int64)
+    fi_all, fj_all = np.zeros(N), np.zeros(N)
+    frac = {}
+    for c in candidates:
+        fi, fj, ok = index_fns[c](xq, yq)
+        frac[c] = (fi, fj, ok)
+    r = range(-shift, shift + 1)
+    offs = sorted(((a, b) for b in r for a in r), key=lambda o: (abs(o[0]) + abs(o[1]),
+                                                                 max(abs(o[0]), abs(o[1]))))
+    for oa, ob in offs:
+        for c in candidates:
+            todo = np.nonzero(dg < 0)[0]
+            if todo.size == 0:
+                break
+            g = grids[c]
+            fi, fj, ok = (v[todo] for v in frac[c])
+            ci = np.rint(np.where(ok, fi, 0.0)).astype(np.int64) - order // 2 + oa
+            cj = np.rint(np.where(ok, fj, 0.0)).astype(np.int64) - order // 2 + ob
+            # near a grid's edge the stencil is shifted inward (one-sided interpolation)
+            ci, cj = np.clip(ci, 0, g.n[0] - w), np.clip(cj, 0, g.n[1] - w)
+            val = ok.copy()
+            for b in range(w):
+                for a in range(w):
+                    m = g.mask[cj + b, ci + a]
+                    val &= (m == DISC) | (m == DIRICHLET)
+            take = todo[val]
+            dg[take], i0[take], j0[take] = c, ci[val], cj[val]
+            fi_all[take], fj_all[take] = fi[val], fj[val]
+    if np.any(dg < 0):
+        k = int(np.nonzero(dg < 0)[0][0])
+        raise ValueError(f"point {k} at ({xq[k]:.4f}, {yq[k]:.4f}) has no donor stencil")
+    return dg, i0, j0, lagrange_weights(fi_all - i0, w), lagrange_weights(fj_all - j0, w)
+
+
+def double_ellipse(j=2, order=4, wfac=12.0, cut=0.4, shift=1):
+    """The double-ellipse overset grid (Sec. 6) with target spacing h = 1/(10 j), j >= 2:
+    a Cartesian background over the room's bounding box (three spacings of margin), and a
+    grid of width W = wfac h along each of the four walls.  The two large half-ellipse
+    grids end on the alcove segments, where their end columns are Dirichlet sides; the top
+    and bottom grids follow segment, small half-ellipse and segment from y = +-(b2 - W / 2)
+    and end in order/2 interpolation columns inside the large grids.  Background points
+    outside the room or within cut W of a wall are cut out; those within order/2 index
+    layers of an active point become interpolation points.  The paper covers the same room
+    with nine grids (four curved, four small Cartesian grids on the alcove segments and the
+    background); following each segment with the wall grid of the small ellipse keeps the
+    component count at five.  Donor stencils are centred where valid, else moved by up to
+    ``shift`` points per axis.  Returns (grids, interp, room)."""
+    room = DoubleEllipseRoom()
+    h = 1.0 / (10 * j)
+    W = wfac * h
+    if W >= room.b2 - room.f - 2.0 * h:
+        raise ValueError("the wall grids are wider than the alcove segments: refine (j >= 2)")
+    g1 = order // 2
+    left, right, top, bottom = room.outlines(room.b2 - 0.5 * W)
+    walls = [_offset_grid("left", left, W, h, order, True),
+             _offset_grid("right", right, W, h, order, True),
+             _offset_grid("top", top, W, h, order, False),
+             _offset_grid("bottom", bottom, W, h, order, False)]
+    mx, my = room.a1 + room.a2 + 3 * h, room.b2 + 3 * h
+    nx, ny = int(round(2 * mx / h)) + 1, int(round(2 * my / h)) + 1
+    B = cartesian_grid("background", nx, ny, -mx, mx, -my, my, [BC_NONE] * 4, order)
+    grids = [B] + walls
+    XB, YB = B.xy
+    dist = np.full(XB.shape, np.inf)
+    pts = np.stack([XB.ravel(), YB.ravel()], axis=1)
+    for g in walls:
+        o = g.mapping["offset"].o
+        sig = np.linspace(0.0, o.S, int(o.S / (h / 50.0)) + 2)
+        x, y, _, _, _ = o.frame(sig)
+        from scipy.spatial import cKDTree
+        d, _ = cKDTree(np.stack([x, y], axis=1)).query(pts)
+        dist = np.minimum(dist, d.reshape(XB.shape))
+    cutm = ~room.inside(XB, YB) | (dist < cut * W)
+    active = ~cutm
+    near = np.zeros_like(active)
+    pad = np.pad(active, g1)
+    for dj in range(-g1, g1 + 1):
+        for di in range(-g1, g1 + 1):
+            near |= pad[g1 + dj:g1 + dj + ny, g1 + di:g1 + di + nx]
+    B.mask[cutm & near] = INTERP
+    B.mask[cutm & ~near] = UNUSED
+
+    def cart_index(x, y):
+        fi, fj = _cart_param(B, x, y)
+        return fi, fj, np.ones(fi.shape, bool)
+
+    def wall_index(g):
+        m = g.mapping["offset"]
+
+        def fn(x, y):
+            sig, d, res = m.param(x, y)
+            ok = (np.abs(res) < 1e-9) & (d > -1e-12) & (d < m.W * (1 + 1e-12)) & \
+                 (sig > -1e-12) & (sig < m.o.S * (1 + 1e-12))
+            return sig / m.o.S * (g.n[0] - 1), d / m.W * (g.n[1] - 1), ok
+        return fn
+
+    index_fns = [cart_index] + [wall_index(g) for g in walls]
+    recv = []
+    for rg, cands in ((0, (1, 2, 3, 4)), (1, (0, 3, 4)), (2, (0, 3, 4)), (3, (0, 1, 2)),
+                      (4, (0, 1, 2))):
+        g = grids[rg]
+        jr, ir = np.nonzero(g.mask == INTERP)
+        X, Y = g.xy
+        dgr, i0, j0, wx, wy = _find_donors2(grids, index_fns, X[jr, ir], Y[jr, ir], cands,
+                                            order, shift)
+        recv.append((rg, ir, jr, dgr, i0, j0, wx, wy))
+    cols = list(zip(*recv))
+    interp = Interp(
+        np.concatenate([np.full(len(r[1]), r[0], np.int32) for r in recv]),
+        np.concatenate(cols[1]).astype(np.int32), np.concatenate(cols[2]).astype(np.int32),
+        np.concatenate(cols[3]).astype(np.int32),
+        np.concatenate(cols[4]).astype(np.int32), np.concatenate(cols[5]).astype(np.int32),
+        np.concatenate(cols[6]), np.concatenate(cols[7]))
+    check_explicit_interp(grids, interp, order)
+    return grids, interp, room
+
+
+# ----------------------------------------------------------------------------------
 # Sources and coefficients
 # ----------------------------------------------------------------------------------
 
@@ -822,6 +1148,16 @@ def knife_edge_problem(j=32, order=4, omega=100.0, width=0.02, height=0.5, sourc
     return Problem(grids, interp, order, omega, f,
                    name=f"knife-edge-j{j}-w{width:g}-h{height:g}-o{order}",
                    meta=dict(source=list(source), outline=dict(ell=ko.ell, ys=ko.ys, S=ko.S)))
+
+
+def double_ellipse_problem(j=2, order=4, omega=5.56, source=(0.0, 1.0), amp=400.0, b=10.0,
+                           **kw):
+    """The double ellipse (Sec. 6) with the paper's Gaussian source (amplitude 400,
+    exponent 10, centred at (0, 1)) and omega = 5.56, Dirichlet walls."""
+    grids, interp, room = double_ellipse(j, order, **kw)
+    f = [gaussian(g.xy, source, amp, b) for g in grids]
+    return Problem(grids, interp, order, omega, f, name=f"double-ellipse-j{j}-o{order}",
+                   meta=dict(source=list(source)))
 
 
 def with_boundary_data(problem, fn):
