@@ -152,6 +152,14 @@ def test_room_solution_fourth_order():
     assert 3.7 < math.log(errs[0] / errs[1]) / math.log(1.5) < 4.8, errs
 
 
+@pytest.mark.parametrize("order", [2, 4])
+def test_room_taken_by_the_library_host_checks(rooms, order):
+    """The library's host-side validation (grid descriptions and interpolation data) takes
+    the room's five grids (no device work)."""
+    from host_checks import library_takes
+    library_takes(rooms[order])
+
+
 def test_room_refuses_walls_wider_than_the_alcoves():
     """At j = 1 the wall grids (12 h = 1.2) would be wider than the alcove segments
     (b2 - f = 0.80): refused."""

@@ -3,7 +3,6 @@ checked against what they must satisfy, the oracle's fixed point on it against t
 independent direct solve, the library's host-side validation takes it, and implicit
 time-stepping (Sec. 4.5) reaches the same solution with far fewer time steps there
 (CPU only)."""
-import ctypes as C
 import math
 
 import numpy as np
@@ -132,39 +131,9 @@ def test_knife_edge_implicit_time_stepping():
 def test_knife_edge_taken_by_the_library_host_checks():
     """The library's host-side validation (grid descriptions and interpolation data) takes
     the knife-edge grids at orders 2 and 4 (no device work)."""
-    from paper_2504_03074_gb300 import build
-    build.build()
-    from paper_2504_03074_gb300 import waveholtz as W
-    L = W.lib()
+    from host_checks import library_takes
     for order in (2, 4):
-        p = G.knife_edge_problem(order=order, **SMALL)
-        opt = W.Options()
-        L.wh_options_default(C.byref(opt))
-        opt.order = order
-        h = C.c_void_p()
-        assert L.wh_create(C.byref(opt), C.byref(h)) == 0
-        keep, gid = [], C.c_int32()
-        for g in p.grids:
-            d = W.GridDesc()
-            d.n[0], d.n[1] = g.n
-            d.kind = g.kind
-            for s in range(4):
-                d.bc[s] = g.bc[s]
-            d.orthogonal, d.instance = int(g.orthogonal), 0
-            d.h[0], d.h[1] = g.h
-            keep.append(np.ascontiguousarray(g.mask, np.int8))
-            d.mask = keep[-1].ctypes.data
-            if g.rx is not None:
-                keep.append(np.ascontiguousarray(g.rx))
-                d.rx = keep[-1].ctypes.data
-            assert L.wh_add_grid(h, C.byref(d), C.byref(gid)) == 0, L.wh_last_error(h)
-        it = p.interp
-        arrs = [np.ascontiguousarray(a, np.int32) for a in
-                (it.recv_grid, it.recv_i, it.recv_j, it.donor_grid, it.donor_i0, it.donor_j0)]
-        arrs += [np.ascontiguousarray(a) for a in (it.wx, it.wy)]
-        desc = W.InterpDesc(it.n, *[a.ctypes.data for a in arrs])
-        assert L.wh_set_interp(h, C.byref(desc)) == 0, L.wh_last_error(h)
-        L.wh_destroy(h)
+        library_takes(G.knife_edge_problem(order=order, **SMALL))
 
 
 def test_knife_edge_refuses_grids_that_do_not_fit():
