@@ -176,3 +176,15 @@ def test_pipe_solution_second_order(o3):
         ref = np.concatenate([u.ravel() for u in us])
         errs.append(np.max(np.abs(v - ref)[orc.active()]))
     assert 1.8 < math.log2(errs[0] / errs[1]) < 2.4, errs
+
+
+def test_pipe_library_host_checks():
+    """The library's host checks take the pipe at order 2 (the kernels of the sphere-in-box:
+    a curvilinear shell periodic in theta and z, a Cartesian background periodic in z);
+    at order 4 they refuse the curvilinear shell with a message (the library's fourth-order
+    3D path is Cartesian only)."""
+    from host_checks import library_status3
+    st, msg = library_status3(G3.pipe_problem(order=2, **SMALL[2]))
+    assert st == 0, msg
+    st, msg = library_status3(G3.pipe_problem(order=4, **SMALL[4]))
+    assert st != 0 and msg
