@@ -3,9 +3,10 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
 this module.  It follows the paper's implicit variant (the scheme of Eq. implicitScheme,
 the corrected form Eq. WaveSchemeImplicit / waveImplicitOrder2, Recipe
-OmegaTildeImplicit) on the two-dimensional overset grids of ``oracle.oracle``, whose C
-pieces (the mapped Laplacian ``apply_lap``, the ghost rules ``apply_bc``, the overset
-``interpolate``) serve as its steps.  Nothing here comes from the CUDA library.
+OmegaTildeImplicit) on the two-dimensional overset grids of ``oracle.oracle`` and the
+three-dimensional ones of ``oracle.oracle3``, whose C pieces (the mapped Laplacian
+``apply_lap``, the ghost rules ``apply_bc``, the overset ``interpolate``) serve as its
+steps.  Nothing here comes from the CUDA library.
 
 What it computes (one iteration v -> W_h(v, f)):
 
@@ -67,17 +68,30 @@ def lambda_implicit(lam_h, dt):
 
 
 class ImplicitOracle:
-    """The implicit WaveHoltz map on one 2D overset problem (``grids.Problem``)."""
+    """The implicit WaveHoltz map on one overset problem (``grids.Problem`` in two
+    dimensions, ``grids3.Problem3`` in three)."""
 
     def __init__(self, problem, n_its=10, periods=1):
         gb = getattr(problem, "g", None)
         if gb is not None and any(x is not None and np.any(x != 0) for x in gb):
             raise ValueError("Dirichlet boundary data are not taken with implicit time-stepping")
         self.problem = problem
-        self.orc = Oracle(problem)  # the operator pieces (its own time setup is not used)
+        # the operator pieces (their own time setup is not used): the 2D oracle, or the 3D
+        # one for a three-dimensional problem (interpolation with a third index)
+        self.dim = 3 if hasattr(problem.interp, "recv_k") else 2
+        if self.dim == 3:
+            from .oracle3 import Oracle3
+            self.orc = Oracle3(problem)
+        else:
+            self.orc = Oracle(problem)
         self.time = implicit_time_setup(problem.omega, n_its, periods)
         self._layout()
         self._assemble()
+
+    def _interior(self, gi):
+        """The slice of grid gi's points in its extended (ghosted) array."""
+        g, gh = self.problem.grids[gi], self.gh[gi]
+        return tuple(slice(gh[a], gh[a] + g.n[a]) for a in reversed(range(self.dim)))
 
     # ---------------------------------------------------------------- layout
     def _layout(self):
@@ -86,18 +100,18 @@ class ImplicitOracle:
         for gi, g in enumerate(self.problem.grids):
             sh = self.orc.ext_shape(gi)
             gh = g.ghosts(self.problem.order)
-            m = np.full(sh, UNUSED, np.int8)
-            m[gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]] = g.mask
             self.shapes.append(sh)
             self.offs.append(o)
             self.gh.append(gh)
+            m = np.full(sh, UNUSED, np.int8)
+            m[self._interior(gi)] = g.mask
             self.mask_ext.append(m)
-            o += sh[0] * sh[1]
+            o += int(np.prod(sh))
         self.N = o
         self.mask = np.concatenate([m.ravel() for m in self.mask_ext])
 
     def _split(self, w):
-        return [w[o:o + s[0] * s[1]].reshape(s).copy() for o, s in zip(self.offs, self.shapes)]
+        return [w[o:o + int(np.prod(s))].reshape(s).copy() for o, s in zip(self.offs, self.shapes)]
 
     def _join(self, ws):
         return np.concatenate([w.ravel() for w in ws])
@@ -120,11 +134,13 @@ class ImplicitOracle:
             aff[o:o + r.size] = self.orc.apply_bc(gi, np.zeros(self.shapes[gi]), 1.0).ravel()
         it = self.problem.interp
         recv = np.zeros(self.N, bool)
+        idx = [it.recv_i, it.recv_j] + ([it.recv_k] if self.dim == 3 else [])
         for q in range(it.n):
             gi = int(it.recv_grid[q])
             gh = self.gh[gi]
-            i, j = int(it.recv_i[q]) + gh[0], int(it.recv_j[q]) + gh[1]
-            recv[self.offs[gi] + j * self.shapes[gi][1] + i] = True
+            ijk = [int(idx[a][q]) + gh[a] for a in range(self.dim)]
+            recv[self.offs[gi] + int(np.ravel_multi_index(tuple(reversed(ijk)),
+                                                          self.shapes[gi]))] = True
         if np.any(ghost & recv):
             raise ValueError("a point is both a ghost and a receiver")
         self.ghost, self.recv = ghost, recv
@@ -134,7 +150,7 @@ class ImplicitOracle:
         Lr, Lc, Lv, Cr, Cc, Cv = [], [], [], [], [], []
         for gi in range(ng):
             o, sh = self.offs[gi], self.shapes[gi]
-            size = sh[0] * sh[1]
+            size = int(np.prod(sh))
             d_loc = disc[o:o + size]
             g_loc = ghost[o:o + size]
             for j in range(size):
@@ -166,7 +182,7 @@ class ImplicitOracle:
         # discretization rows: I - dt^2/2 L; constraint rows: I - C; all other rows: I
         self.A = (I - 0.5 * dt * dt * self.L - C).tocsc()
         self.lu = spla.splu(self.A)
-        self.f = self._join([np.pad(f, ((gh[1], gh[1]), (gh[0], gh[0])))
+        self.f = self._join([np.pad(f, [(gh[a], gh[a]) for a in reversed(range(self.dim))])
                              for f, gh in zip(self.problem.f, self.gh)])
 
     # ------------------------------------------------------------- the map
@@ -174,13 +190,12 @@ class ImplicitOracle:
         ws = []
         o = 0
         for gi, g in enumerate(self.problem.grids):
-            gh = self.gh[gi]
             w = np.zeros(self.shapes[gi])
-            vg = v[o:o + g.n[0] * g.n[1]].reshape(g.n[1], g.n[0])
+            vg = v[o:o + g.mask.size].reshape(g.mask.shape)
             keep = (g.mask == DISC) | (g.mask == INTERP)
-            w[gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]] = np.where(keep, vg, 0.0)
+            w[self._interior(gi)] = np.where(keep, vg, 0.0)
             ws.append(self.orc.apply_bc(gi, w, fs))
-            o += g.n[0] * g.n[1]
+            o += g.mask.size
         return self._join(self.orc.interpolate(ws))
 
     def _rhs_constraints(self, fcos):
@@ -213,10 +228,8 @@ class ImplicitOracle:
         V += np.where(active, wf(M) * Wc, 0.0)
         out = []
         for gi, g in enumerate(self.problem.grids):
-            gh = self.gh[gi]
-            Vg = V[self.offs[gi]:self.offs[gi] + self.shapes[gi][0] * self.shapes[gi][1]]
-            Vg = Vg.reshape(self.shapes[gi])
-            out.append(Vg[gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]].ravel())
+            Vg = V[self.offs[gi]:self.offs[gi] + int(np.prod(self.shapes[gi]))]
+            out.append(Vg.reshape(self.shapes[gi])[self._interior(gi)].ravel())
         return np.concatenate(out)
 
     # the spatial operator's pieces (the same as the explicit oracle's): for the

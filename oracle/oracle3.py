@@ -70,6 +70,7 @@ def lib(openmp=False):
             L.o3_iterate.argtypes = [vp, C.c_int, vp, vp]
             L.o3_apply_lap.argtypes = [vp, C.c_int, vp, vp]
             L.o3_apply_bc.argtypes = [vp, C.c_int, vp]
+            L.o3_apply_bc_forced.argtypes = [vp, C.c_int, vp, C.c_double]
             L.o3_get_coef.restype = C.c_int
             L.o3_get_coef.argtypes = [vp, C.c_int, C.c_int, vp]
             L.o3_interpolate.argtypes = [vp, vp]
@@ -161,9 +162,10 @@ class Oracle3:
         self.L.o3_apply_lap(self.h, gi, _p(u), _p(out))
         return out
 
-    def apply_bc(self, gi, u_ext):
+    def apply_bc(self, gi, u_ext, fcos=0.0):
+        """The ghost rules of grid gi on a copy of u_ext, with forcing factor fcos."""
         u = np.array(u_ext, np.float64, order="C")
-        self.L.o3_apply_bc(self.h, gi, _p(u))
+        self.L.o3_apply_bc_forced(self.h, gi, _p(u), float(fcos))
         return u
 
     def coef(self, gi, which):

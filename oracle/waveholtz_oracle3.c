@@ -596,6 +596,13 @@ int o3_apply_bc(o3_problem *P, int gidx, double *u) {
   return 0;
 }
 
+/* The ghost rules with the forcing factor fcos (the order-4 Dirichlet compatibility
+ * condition's f_b cos(omega t) term), for the implicit scheme's level systems. */
+int o3_apply_bc_forced(o3_problem *P, int gidx, double *u, double fcos) {
+  apply_bc(P, gidx, u, fcos);
+  return 0;
+}
+
 int o3_get_coef(o3_problem *P, int gidx, int which, double *out) {
   o3_grid *G = &P->G[gidx];
   if (!G->coef || which < 0 || which >= C_N) return -1;

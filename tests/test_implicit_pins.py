@@ -169,3 +169,60 @@ def test_implicit_eigenvalues_and_deflation_on_the_knife_edge(imp):
     assert np.max(np.abs(u - U)[act]) < 1e-9 * np.max(np.abs(U))
     _, its_p, _ = gmres(orc, tol=1e-12, restart=200, max_it=600)
     assert its_d < 0.8 * its_p, (its_d, its_p)
+
+
+# ------------------------------------------------------------- three dimensions
+
+def test_eigenmodes_are_scaled_by_beta_d_implicit_3d(imp):
+    """The same theorem in three dimensions: sine modes of the Dirichlet unit cube
+    (eigenvectors of the 7-point Laplacian, -lambda^2 = -sum_a (4/h^2) sin^2(pi m_a h / 2))
+    are eigenvectors of the zero-forcing implicit map with eigenvalue beta_d(lambda_i)."""
+    from paper_2504_03074_gb300 import grids3 as G3
+    from oracle.oracle import beta_d_sum
+    n = 11
+    orc = imp.ImplicitOracle(G3.unit_cube_problem(n, omega=6.0), n_its=10, periods=2)
+    T = orc.time
+    h = 1.0 / (n - 1)
+    x = np.arange(n) * h
+    rng = np.random.default_rng(3)
+    v = np.zeros((n, n, n))
+    expect = np.zeros_like(v)
+    for m in ((1, 1, 1), (2, 3, 1), (5, 4, 7), (9, 9, 8)):
+        phi = (np.sin(m[2] * np.pi * x)[:, None, None] * np.sin(m[1] * np.pi * x)[None, :, None]
+               * np.sin(m[0] * np.pi * x)[None, None, :])
+        lam = math.sqrt(sum(4 / h ** 2 * math.sin(k * math.pi * h / 2) ** 2 for k in m))
+        b = beta_d_sum(imp.lambda_implicit(lam, T["dt"]), T["omega_i"], T["dt"], T["Nt"],
+                       T["alpha"], 2)[0]
+        c = rng.standard_normal()
+        v += c * phi
+        expect += c * b * phi
+    out = orc.iterate(v.ravel(), False).reshape(n, n, n)
+    assert np.max(np.abs(out - expect)) < 1e-13 * np.max(np.abs(v))
+
+
+def _cases3():
+    from paper_2504_03074_gb300 import grids3 as G3
+    return [
+        ("cube-o2", lambda: G3.unit_cube_problem(9, omega=5.0, b=20.0)),
+        ("cube-o4", lambda: G3.unit_cube_problem(9, omega=5.0, b=20.0, order=4)),
+        ("box-in-box-o2", lambda: G3.box_in_box_problem()),
+        # the paper's implicit pipe run is fourth order (Sec. 6); a shorter period here
+        ("pipe-o4", lambda: G3.pipe_problem(j=2, order=4, lz=0.3)),
+    ]
+
+
+@pytest.mark.parametrize("k", range(4), ids=["cube-o2", "cube-o4", "box-in-box-o2", "pipe-o4"])
+def test_implicit_fixed_point_equals_direct_solve_3d(imp, k):
+    """In three dimensions too the direct discrete solution (tests/dhs3.py) is a fixed point
+    of the implicit map (Cartesian cubes at orders 2 and 4, the box-in-box overset grid,
+    the pipe at order 4 with the paper's source), and GMRES on the implicit map reaches it."""
+    import dhs3
+    from oracle.oracle import gmres
+    name, make = _cases3()[k]
+    prob = make()
+    orc = imp.ImplicitOracle(prob, n_its=10)
+    U = dhs3.solve(prob)
+    act = orc.active()
+    assert np.max(np.abs(orc.iterate(U, True) - U)[act]) < 1e-12 * np.max(np.abs(U)), name
+    v, its, hist = gmres(orc, tol=1e-12, restart=150, max_it=300)
+    assert np.max(np.abs(v - U)[act]) < 1e-10 * np.max(np.abs(U)), (name, its)
