@@ -71,6 +71,8 @@ def lib(openmp=False):
             L.o3_apply_lap.argtypes = [vp, C.c_int, vp, vp]
             L.o3_apply_bc.argtypes = [vp, C.c_int, vp]
             L.o3_apply_bc_forced.argtypes = [vp, C.c_int, vp, C.c_double]
+            L.o3_set_dissipation.restype = C.c_int
+            L.o3_set_dissipation.argtypes = [vp, C.c_double]
             L.o3_get_coef.restype = C.c_int
             L.o3_get_coef.argtypes = [vp, C.c_int, C.c_int, vp]
             L.o3_interpolate.argtypes = [vp, vp]
@@ -89,13 +91,19 @@ def _p(a):
 class Oracle3:
     """One three-dimensional overset Helmholtz problem held by the C oracle."""
 
-    def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0, openmp=False):
+    def __init__(self, problem, omega=None, cfl=0.9, periods=1, alpha_mode=0, openmp=False,
+                 nu=0.0):
+        """nu > 0 turns on the dissipative march (the upwind-dissipation variant: the
+        deviation of the march from the iterate's periodic motion is damped, so that the
+        discrete Helmholtz solution stays the fixed point)."""
         self.problem = problem
         self.L = lib(openmp)
         self.order = int(getattr(problem, "order", 2))
         self.h = self.L.o3_new_order(self.order)
         if not self.h:
             raise ValueError(f"order {self.order}: the 3D oracle takes 2 or 4")
+        if self.L.o3_set_dissipation(self.h, float(nu)) != 0:
+            raise ValueError("the dissipation coefficient must be >= 0")
         self._keep = []
         for gi, g in enumerate(problem.grids):
             bc = (C.c_int * 6)(*g.bc)

@@ -90,6 +90,7 @@ typedef struct {
   double *wx, *wy, *wz;
   double omega, dt, omega_e, alpha, cfl;
   int Nt, Np, M, prepared;
+  double nu;  /* dissipation of the deviation from the periodic motion (0: none) */
   char err[256];
 } o3_problem;
 
@@ -486,18 +487,46 @@ int o3_prepare(o3_problem *P, double omega, double cfl, int Np, int alpha_mode, 
   return 0;
 }
 
+/* Dissipation of the march's deviation from the periodic motion of the iterate (the
+ * paper's upwind-dissipation variant leaves the form to its reference; the same reading as
+ * in two dimensions): sum_a (-D+D-)^(p/2) h_a^p applied to Y = (W^n - W^{n-1}) -
+ * V0 (cos(omega_e t^n) - cos(omega_e t^{n-1})), V0 the level-0 state after its boundary
+ * rules and interpolation.  Positive semi-definite, it damps grid-scale modes; Y vanishes
+ * on W^n = V0 cos(omega_e t^n), so the discrete Helmholtz solution stays a fixed point. */
+static double dissipation(const o3_problem *P, const o3_grid *G, const double *Wn,
+                          const double *Wm, const double *V0, int i, int j, int k, double dc) {
+  static const double c1[3] = {-1.0, 2.0, -1.0}, c2[5] = {1.0, -4.0, 6.0, -4.0, 1.0};
+  const int r = P->order / 2;
+  const double *c = r == 1 ? c1 : c2;
+  double s = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int o = -r; o <= r; ++o) {
+      const long q = at(G, i + (a == 0 ? o : 0), j + (a == 1 ? o : 0), k + (a == 2 ? o : 0));
+      s += c[o + r] * ((Wn[q] - Wm[q]) - V0[q] * dc);
+    }
+  return s;
+}
+
+int o3_set_dissipation(o3_problem *P, double nu) {
+  if (!(nu >= 0.0)) return -1;
+  P->nu = nu;
+  return 0;
+}
+
 /* One WaveHoltz iteration v_out = W_h(v_in, f) (forcing = 1) or W_h(v_in, 0). */
 int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
   if (!P->prepared) return -1;
   int ng = P->ngrids, M = P->M;
   double dt = P->dt, we = P->omega_e, fs = forcing ? 1.0 : 0.0;
   double *Wm[O3_MAX_GRIDS], *W0[O3_MAX_GRIDS], *Wp[O3_MAX_GRIDS], *V[O3_MAX_GRIDS];
+  double *Vr[O3_MAX_GRIDS]; /* level 0 after its boundary rules and interpolation */
   for (int g = 0; g < ng; ++g) {
     long E = ext_size(&P->G[g]);
     Wm[g] = (double *)calloc(E, sizeof(double));
     W0[g] = (double *)calloc(E, sizeof(double));
     Wp[g] = (double *)calloc(E, sizeof(double));
     V[g] = (double *)calloc(E, sizeof(double));
+    Vr[g] = (double *)calloc(E, sizeof(double));
   }
   /* filter weight of level n: (2/Tbar) sigma_n dt (cos(omega_e t^n) - alpha/2) */
 #define FILTER_W(n) ((2.0 / (M * dt)) * (((n) == 0 || (n) == M) ? 0.5 : 1.0) * dt * \
@@ -515,6 +544,7 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
     apply_bc(P, g, W0[g], fs);
   }
   interpolate(P, W0);
+  for (int g = 0; g < ng; ++g) memcpy(Vr[g], W0[g], ext_size(&P->G[g]) * sizeof(double));
   for (int n = 0; n < M; ++n) {
     double tn = n * dt, wn = FILTER_W(n);
     for (int g = 0; g < ng; ++g) {
@@ -540,6 +570,9 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
               Wp[g][q] = W0[g][q] + 0.5 * dt * dt * (L - fs * G->f[q]);
             else
               Wp[g][q] = 2.0 * W0[g][q] - Wm[g][q] + dt * dt * (L - fs * G->f[q] * cos(we * tn));
+            if (n > 0 && P->nu > 0.0)
+              Wp[g][q] -= P->nu * dissipation(P, G, W0[g], Wm[g], Vr[g], i, j, k,
+                                              cos(we * tn) - cos(we * (tn - dt)));
           }
       /* Dirichlet points: the boundary data at t^{n+1} */
       for (int k = 0; k < G->n[2]; ++k)
@@ -572,7 +605,7 @@ int o3_iterate(o3_problem *P, int forcing, const double *v_in, double *v_out) {
       for (int j = 0; j < G->n[1]; ++j)
         for (int i = 0; i < G->n[0]; ++i)
           v_out[G->offset + ((long)k * G->n[1] + j) * G->n[0] + i] = V[g][at(G, i, j, k)];
-    free(Wm[g]); free(W0[g]); free(Wp[g]); free(V[g]);
+    free(Wm[g]); free(W0[g]); free(Wp[g]); free(V[g]); free(Vr[g]);
   }
   return 0;
 }
