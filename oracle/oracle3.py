@@ -71,6 +71,7 @@ def lib(openmp=False):
             L.o3_apply_lap.argtypes = [vp, C.c_int, vp, vp]
             L.o3_apply_bc.argtypes = [vp, C.c_int, vp]
             L.o3_apply_bc_forced.argtypes = [vp, C.c_int, vp, C.c_double]
+            L.o3_set_neumann.argtypes = [vp, C.c_int, vp]
             L.o3_set_dissipation.restype = C.c_int
             L.o3_set_dissipation.argtypes = [vp, C.c_double]
             L.o3_get_coef.restype = C.c_int
@@ -122,6 +123,11 @@ class Oracle3:
                 ga = np.ascontiguousarray(gb[gi], np.float64)
                 self._keep.append(ga)
                 self.L.o3_set_boundary(self.h, gi, _p(ga))
+            gnn = getattr(problem, "gn", None)
+            if gnn is not None and gnn[gi] is not None:
+                ga = np.ascontiguousarray(gnn[gi], np.float64)
+                self._keep.append(ga)
+                self.L.o3_set_neumann(self.h, gi, _p(ga))
         it = problem.interp
         arrs = [np.ascontiguousarray(a, np.int32) for a in
                 (it.recv_grid, it.recv_i, it.recv_j, it.recv_k, it.donor_grid, it.donor_i0,

@@ -78,6 +78,8 @@ typedef struct {
   double *rx;      /* curvilinear: 9 extended arrays, rx[(3 k + m) E + q] = dr_k / dx_m */
   double *c2, *f;  /* extended */
   double *gb;      /* extended; Dirichlet boundary data (read at Dirichlet points) */
+  double *gn;      /* extended; Neumann data du/dn along the outward normal (read at the
+                      discretization points of Neumann faces) */
   double *coef;    /* curvilinear: C_N extended arrays */
   long offset;
 } o3_grid;
@@ -266,9 +268,23 @@ static void apply_bc(const o3_problem *P, int gidx, double *W, double fcos) {
         }
         const long qb = at(G, ip[2][0], ip[2][1], ip[2][2]);
         const signed char m = G->mask[qb];
+        /* Neumann data: du/dn = gn cos along the outward normal -+grad r_a / |grad r_a| is
+         * du/dr_a = -+gq, gq = gn cos / |grad r_a| (|grad r_a| = 1 on Cartesian grids) */
+        double gq = 0.0;
+        if (code == O3_BC_NEUMANN && G->gn[qb] != 0.0) {
+          double nrm = 1.0;
+          if (G->kind == O3_CURVILINEAR) {
+            double s2 = 0.0;
+            for (int mm = 0; mm < 3; ++mm) s2 += G->rx[(3 * a + mm) * E + qb] * G->rx[(3 * a + mm) * E + qb];
+            nrm = sqrt(s2);
+          }
+          gq = G->gn[qb] * fcos / nrm;
+        }
         if (!G->fourth) {
           if (m != O3_DISC) continue;
-          W[at(G, ip[1][0], ip[1][1], ip[1][2])] = W[at(G, ip[3][0], ip[3][1], ip[3][2])];
+          /* centred D0 along the inward direction: (U1 - G1) / (2 h) = -gq */
+          W[at(G, ip[1][0], ip[1][1], ip[1][2])] = W[at(G, ip[3][0], ip[3][1], ip[3][2])] +
+                                                   2.0 * G->h[a] * gq;
           continue;
         }
         if ((code == O3_BC_NEUMANN && m != O3_DISC) || (code == O3_BC_DIRICHLET && m != O3_DIRICHLET))
@@ -281,9 +297,9 @@ static void apply_bc(const o3_problem *P, int gidx, double *W, double fcos) {
         A[1][0] = -5.0; A[1][1] = 1.0;
         r[1] = -(10.0 * U[0] - 10.0 * U[1] + 5.0 * U[2] - U[3]);
         if (code == O3_BC_NEUMANN) {
-          /* 8 (U1 - G1) - (U2 - G2) = 0 */
+          /* 8 (U1 - G1) - (U2 - G2) = -12 h gq (the fourth-order D_n inward, undivided) */
           A[0][0] = -8.0; A[0][1] = 1.0;
-          r[0] = -(8.0 * U[1] - U[2]);
+          r[0] = -(8.0 * U[1] - U[2]) - 12.0 * G->h[a] * gq;
         } else {
           /* c^2 (a_nn D_nn W + b_n D_n W)_b = f_b cos, D_nn = (-G2 + 16 G1 - 30 U0 +
            * 16 U1 - U2) / (12 h^2) and D_n along +r_a, i.e. +-(-U2 + 8 U1 - 8 G1 + G2) /
@@ -397,6 +413,7 @@ int o3_add_grid(o3_problem *P, int n0, int n1, int n2, int kind, const int *bc, 
   G->c2 = (double *)malloc(E * sizeof(double));
   G->f = (double *)calloc(E, sizeof(double));
   G->gb = (double *)calloc(E, sizeof(double));
+  G->gn = (double *)calloc(E, sizeof(double));
   for (long q = 0; q < E; ++q) G->c2[q] = 1.0;
   for (int k = 0; k < n2; ++k)
     for (int j = 0; j < n1; ++j)
@@ -431,6 +448,18 @@ int o3_set_boundary(o3_problem *P, int gidx, const double *g) {
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i)
         G->gb[at(G, i, j, k)] = g[((long)k * G->n[1] + j) * G->n[0] + i];
+  return 0;
+}
+
+/* Neumann data (compact; read at the discretization points of Neumann faces): the ghost
+ * rule makes the outward normal derivative gn cos(omega_e t) instead of 0, switched off with
+ * the forcing. */
+int o3_set_neumann(o3_problem *P, int gidx, const double *gn) {
+  o3_grid *G = &P->G[gidx];
+  for (int k = 0; k < G->n[2]; ++k)
+    for (int j = 0; j < G->n[1]; ++j)
+      for (int i = 0; i < G->n[0]; ++i)
+        G->gn[at(G, i, j, k)] = gn[((long)k * G->n[1] + j) * G->n[0] + i];
   return 0;
 }
 
@@ -652,7 +681,7 @@ void o3_free(o3_problem *P) {
   if (!P) return;
   for (int g = 0; g < P->ngrids; ++g) {
     o3_grid *G = &P->G[g];
-    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->gb); free(G->coef);
+    free(G->mask); free(G->rx); free(G->c2); free(G->f); free(G->gb); free(G->gn); free(G->coef);
   }
   free(P->rg); free(P->ri); free(P->rj); free(P->rk);
   free(P->dg); free(P->di); free(P->dj); free(P->dk);

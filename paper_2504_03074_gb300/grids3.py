@@ -116,6 +116,8 @@ class Problem3:
     order: int = ORDER
     dim: int = 3
     g: list | None = None         # per-grid compact Dirichlet data (read at Dirichlet points)
+    gn: list | None = None        # per-grid compact Neumann data du/dn (outward normal), read
+                                  # at the discretization points of Neumann faces
 
     @property
     def n_active(self):
@@ -383,6 +385,44 @@ def pipe_problem(j=2, order=ORDER, omega=8.5, source=(0.1, 0.1, 0.5), amp=150.0,
     f = [gaussian3(g, x0, amp, b) for g in grids]
     return Problem3(grids, interp, omega, f, name=f"pipe-j{j}-o{order}",
                     meta=dict(source=list(source)), order=order)
+
+
+def with_neumann_data3(problem, grad):
+    """The same problem with Neumann data on every Neumann face: gn = grad u . n at its
+    discretization points, n the outward unit normal (-+ grad r_a / |grad r_a| from the
+    inverse metrics on a low / high face of axis a; the axis direction on Cartesian grids),
+    grad(x, y, z) -> (u_x, u_y, u_z) the gradient of the intended solution."""
+    import copy
+    p = copy.copy(problem)
+    p.gn = []
+    for g in problem.grids:
+        gn = np.zeros(g.mask.shape)
+        gh = g.ghosts(problem.order)
+        X = g.coords()
+        for s in range(6):
+            if g.bc[s] != BC_NEUMANN:
+                continue
+            a, hi = s // 2, s % 2
+            sl = [slice(None)] * 3
+            sl[2 - a] = -1 if hi else 0
+            sl = tuple(sl)
+            pts = g.mask[sl] == DISC
+            if g.kind == CARTESIAN:
+                nv = [np.full(pts.shape, 1.0 if m == a else 0.0) for m in range(3)]
+            else:
+                rx = g.rx[:, gh[2]:gh[2] + g.n[2], gh[1]:gh[1] + g.n[1], gh[0]:gh[0] + g.n[0]]
+                nv = [rx[3 * a + m][sl] for m in range(3)]
+                nrm = np.sqrt(nv[0] ** 2 + nv[1] ** 2 + nv[2] ** 2)
+                nv = [v / nrm for v in nv]
+            du = grad(X[0][sl], X[1][sl], X[2][sl])
+            sign = 1.0 if hi else -1.0
+            if np.any(pts & (gn[sl] != 0.0)):
+                raise ValueError("Neumann data where two Neumann faces meet (one value per "
+                                 "point cannot hold both normals)")
+            gn[sl] = np.where(pts, sign * (du[0] * nv[0] + du[1] * nv[1] + du[2] * nv[2]), 0.0)
+        p.gn.append(gn)
+    p.name = problem.name + "-gn"
+    return p
 
 
 def annular_cylinder_problem(nth=32, nr=9, nz=10, r_in=0.3, r_out=0.6, lz=1.0,

@@ -33,6 +33,21 @@ D2C = {2: -2.0, 4: -30.0 / 12}
 EXTRAP5 = [1.0, -5.0, 10.0, -10.0, 5.0, -1.0]  # on G2, G1, U0, U1, U2, U3
 
 
+def _neumann_data(problem, gi, g, b, a):
+    """gn / |grad r_a| at boundary point b (i, j, k) of a Neumann face of axis a: the
+    parameter derivative du/dr_a along the inward direction is -(that), read from the
+    problem's Neumann data (zero when it has none)."""
+    gnl = getattr(problem, "gn", None)
+    if gnl is None or gnl[gi] is None:
+        return 0.0
+    val = gnl[gi][b[2], b[1], b[0]]
+    if g.kind == G.CARTESIAN or val == 0.0:
+        return val
+    gh = g.ghosts(problem.order)
+    r = g.rx[:, b[2] + gh[2], b[1] + gh[1], b[0] + gh[0]]
+    return val / np.sqrt(r[3 * a] ** 2 + r[3 * a + 1] ** 2 + r[3 * a + 2] ** 2)
+
+
 def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done, coef=None):
     """The two ghost rows of every boundary point of a Dirichlet or Neumann face; on a
     curvilinear grid (coef = (A, B) of curvilinear_coefficients) the Dirichlet row is
@@ -60,8 +75,10 @@ def fourth_order_ghost_rows(problem, gi, g, L, c2, put, rhs, done, coef=None):
                 for c_, col in zip(EXTRAP5, [G2, G1] + U):
                     put(G2, col, c_)
                 if code == G.BC_NEUMANN:
+                    # the undivided inward D_n equals -12 h du/dn-data / |grad r_a|
                     for c_, col in zip([1.0, -8.0, 8.0, -1.0], [G2, G1, U[1], U[2]]):
                         put(G1, col, c_)
+                    rhs[G1] = -12.0 * g.h[a] * _neumann_data(problem, gi, g, b, a)
                 else:
                     ann, bn = c2[b[2], b[1], b[0]], 0.0
                     if coef is not None:
@@ -243,6 +260,7 @@ def assemble(problem):
                     done[r] = True
                     put(r, r, 1.0)
                     put(r, L.idx(gi, *inw), -1.0)
+                    rhs[r] = 2.0 * g.h[a] * _neumann_data(problem, gi, g, ib, a)
     it = problem.interp
     for q in range(it.n):
         r = L.idx(int(it.recv_grid[q]), int(it.recv_i[q]), int(it.recv_j[q]), int(it.recv_k[q]))
